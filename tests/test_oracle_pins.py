@@ -1,0 +1,347 @@
+"""Pins for the FP64 oracle against facts fixed outside the oracle itself.
+
+Each test checks the oracle against something other than its own formula:
+hand-derived cases (tests/golden), library routines (np.cov, eigvalsh, svd),
+exhaustive enumeration over the faces of F, the projection's variational
+inequality over all vertices of F, finite differences, and the FISTA
+Lyapunov inequality.  All run on the CPU in a few seconds.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from synth import CFG_SMALL, factor_returns, gaussian_sketch, power_start
+from oracle.center import center_factor
+from oracle.projection import (PROJ_INFEASIBLE, PROJ_OK, active_set, project_F,
+                               project_halfspace, project_simplex)
+from oracle.npga import (fw_gap, gradient, initial_point, kkt_residual, lin_min_F,
+                         npga, objective, power_norm2, solver_gap, step_size, vertices_F)
+from oracle.bruteforce import project_bruteforce, qp_bruteforce
+from oracle import strmodel
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "hand_cases.json")))
+
+
+def small_problem(n=30, T=200, seed=3, pct=60.0):
+    R = factor_returns(CFG_SMALL.scaled(n, T, seed=seed), np.float32).astype(np.float64)
+    mu, L, tr = center_factor(R)
+    return R, mu, L, float(np.percentile(mu, pct))
+
+
+# ---------------------------------------------------------------- centering
+def test_center_matches_numpy_cov():
+    R, mu, L, _ = small_problem(40, 300)
+    np.testing.assert_allclose(L @ L.T, np.cov(R, ddof=1), rtol=1e-12, atol=1e-18)
+    np.testing.assert_allclose(mu, np.mean(R, axis=1), rtol=1e-13)
+    assert np.max(np.abs(L.sum(axis=1))) < 1e-14
+    _, _, tr = center_factor(R)
+    assert tr == pytest.approx(np.trace(np.cov(R, ddof=1)), rel=1e-12)
+
+
+def test_objective_matches_explicit_sigma():
+    R, mu, L, _ = small_problem(CFG_SMALL.n, CFG_SMALL.T)
+    Sigma = np.cov(R, ddof=1)
+    x = np.random.default_rng(0).dirichlet(np.ones(L.shape[0]))
+    assert objective(L, 0.0, x) == pytest.approx(x @ Sigma @ x, rel=1e-12)
+    assert objective(L, 0.3, x) == pytest.approx(x @ Sigma @ x + 0.3 * x @ x, rel=1e-12)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 2e-4])
+def test_gradient_matches_finite_differences(gamma):
+    _, _, L, _ = small_problem(12, 80)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(12)
+    g = gradient(L, gamma, x)
+    h = 1e-6
+    fd = np.array([(objective(L, gamma, x + h * e) - objective(L, gamma, x - h * e)) / (2 * h)
+                   for e in np.eye(12)])
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-12)
+
+
+# --------------------------------------------------------------- projection
+@pytest.mark.parametrize("case", GOLD["simplex"])
+def test_simplex_hand_cases(case):
+    x, tau = project_simplex(np.array(case["v"]))
+    np.testing.assert_allclose(x, case["x"], atol=1e-15)
+    assert tau == pytest.approx(case["tau"], abs=1e-15)
+
+
+@pytest.mark.parametrize("case", GOLD["projection_F"])
+def test_projection_hand_cases(case):
+    p = project_F(np.array(case["v"]), np.array(case["mu"]), case["R"], case["mode"])
+    assert p.status == PROJ_OK
+    np.testing.assert_allclose(p.x, case["x"], atol=1e-13)
+    if case["nu"] is not None:
+        assert p.nu == pytest.approx(case["nu"], rel=1e-10, abs=1e-12)
+        assert p.tau == pytest.approx(case["tau"], rel=1e-10, abs=1e-12)
+
+
+def test_simplex_matches_bruteforce_and_fixes_simplex_points():
+    rng = np.random.default_rng(2)
+    for n in range(1, 8):
+        for _ in range(20):
+            v = rng.standard_normal(n)
+            x, _ = project_simplex(v)
+            # R below min mu: F is the whole simplex.
+            ref = project_bruteforce(v, np.zeros(n), -1.0)
+            np.testing.assert_allclose(x, ref, atol=1e-12)
+        p = rng.dirichlet(np.ones(n))
+        np.testing.assert_allclose(project_simplex(p)[0], p, atol=1e-15)
+
+
+def test_halfspace_closed_form():
+    rng = np.random.default_rng(3)
+    mu = rng.uniform(0.0, 0.01, 9)
+    y = rng.standard_normal(9)
+    R = float(mu @ y) + 0.05
+    p = project_halfspace(y, mu, R)
+    assert mu @ p == pytest.approx(R, rel=1e-13)
+    d = p - y                      # the move is along mu
+    np.testing.assert_allclose(d / np.linalg.norm(d), mu / np.linalg.norm(mu), atol=1e-12)
+    np.testing.assert_allclose(project_halfspace(p, mu, R), p, atol=0)
+
+
+@pytest.mark.parametrize("mode", ["ge", "eq"])
+def test_projection_matches_bruteforce(mode):
+    rng = np.random.default_rng(4 if mode == "ge" else 5)
+    checked = 0
+    for _ in range(150):
+        n = int(rng.integers(1, 8))
+        v = rng.standard_normal(n) * 0.5
+        mu = rng.uniform(-1e-3, 2e-3, n)
+        R = float(rng.uniform(mu.min(), mu.max())) if n > 1 else float(mu[0])
+        p = project_F(v, mu, R, mode)
+        ref = project_bruteforce(v, mu, R, mode)
+        assert p.status == PROJ_OK
+        np.testing.assert_allclose(p.x, ref, atol=1e-10)
+        checked += 1
+    assert checked == 150
+
+
+def test_projection_variational_inequality_over_all_vertices():
+    rng = np.random.default_rng(6)
+    for n in (50, 200, 400):
+        mu = rng.uniform(-2e-4, 6e-4, n)
+        v = rng.standard_normal(n) * 3e-3 + 1.0 / n
+        R = float(np.percentile(mu, 80))
+        p = project_F(v, mu, R)
+        assert p.status == PROJ_OK
+        x = p.x
+        assert x.min() >= 0 and abs(x.sum() - 1) < 1e-13 and mu @ x >= R - 1e-15
+        # <v - p, q - p> <= 0 for every vertex q of F (exact for a polytope).
+        r = v - x
+        worst = -np.inf
+        for i, j, lam in vertices_F(mu, R):
+            q = np.zeros(n)
+            q[i] += lam
+            q[j] += 1.0 - lam
+            worst = max(worst, float(r @ (q - x)))
+        assert worst <= 1e-14
+
+
+def test_phi_is_nondecreasing_in_nu():
+    rng = np.random.default_rng(7)
+    mu = rng.uniform(-2e-4, 6e-4, 300)
+    v = rng.standard_normal(300) * 1e-3
+    nus = np.linspace(0.0, 50.0, 400)
+    phi = [float(mu @ project_simplex(v + nu * mu)[0]) for nu in nus]
+    assert np.all(np.diff(phi) >= -1e-18)
+
+
+def test_projection_edge_cases():
+    mu = np.array([0.01, 0.02, 0.03])
+    v = np.array([0.2, 0.3, 0.5])
+    assert project_F(v, mu, 0.031).status == PROJ_INFEASIBLE
+    assert project_F(v, mu, 0.005, "eq").status == PROJ_INFEASIBLE
+    # Equality mode with a target below mu^T Pi_Delta(v): nu < 0.
+    p = project_F(v, mu, 0.015, "eq")
+    assert p.status == PROJ_OK and p.nu < 0 and mu @ p.x == pytest.approx(0.015, abs=1e-15)
+    np.testing.assert_allclose(p.x, project_bruteforce(v, mu, 0.015, "eq"), atol=1e-12)
+    # n = 1: the only feasible point.
+    p = project_F(np.array([-3.0]), np.array([1e-3]), 5e-4)
+    assert p.status == PROJ_OK and p.x[0] == 1.0
+    # Ties in v and mu are harmless: the projection is unique.
+    vv = np.array([0.3, 0.3, 0.3, 0.1])
+    mm = np.array([0.01, 0.01, 0.02, 0.02])
+    p = project_F(vv, mm, 0.018)
+    np.testing.assert_allclose(p.x, project_bruteforce(vv, mm, 0.018), atol=1e-12)
+    act, deg = active_set(vv, mm, p.nu, p.tau)
+    assert np.array_equal(act[~deg], (p.x > 0)[~deg])
+
+
+# --------------------------------------------------------- power and NPGA
+def test_power_method_approaches_lambda_max_from_below():
+    _, _, L, _ = small_problem(CFG_SMALL.n, CFG_SMALL.T)
+    lam_max = np.linalg.eigvalsh(L @ L.T)[-1]
+    r = power_start(L.shape[0])
+    prev = 0.0
+    for it in (1, 2, 5, 10, 50, 200, 1500):
+        lam = power_norm2(L, r, it)
+        assert lam <= lam_max * (1 + 1e-12)
+        assert lam >= prev * (1 - 1e-12)        # Rayleigh quotient increases
+        prev = lam
+    # The top eigenvalues of this panel are clustered, so convergence is slow.
+    assert prev == pytest.approx(lam_max, rel=1e-9)
+    assert step_size(lam_max, 0.0, 0.0) == pytest.approx(1.0 / (2.0 * lam_max))
+
+
+def test_npga_hand_case():
+    c = GOLD["npga"][0]
+    L, mu = np.array(c["L"]), np.array(c["mu"])
+    lam = power_norm2(L, np.array([1.0, 1.0]), 50)
+    x0 = initial_point(mu, c["R"])
+    res = npga(L, 0.0, mu, c["R"], x0, step_size(lam, 0.0), eps=1e-12, max_iter=5000)
+    assert res.converged
+    np.testing.assert_allclose(res.x, c["x"], atol=1e-10)
+    assert res.f == pytest.approx(c["f"], rel=1e-9)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 5e-5])
+def test_npga_matches_bruteforce_qp(gamma):
+    for seed in range(4):
+        n = 6 + seed % 3
+        R, mu, L, Rt = small_problem(n, 60, seed=10 + seed, pct=70)
+        Sigma = L @ L.T + gamma * np.eye(n)
+        ref = qp_bruteforce(Sigma, mu, Rt)
+        lam = power_norm2(L, power_start(n), 200)
+        x0 = initial_point(mu, Rt)
+        res = npga(L, gamma, mu, Rt, x0, step_size(lam, gamma), eps=1e-11, max_iter=200000)
+        assert res.converged
+        np.testing.assert_allclose(res.x, ref, atol=1e-7)
+        gap = fw_gap(L, gamma, mu, Rt, res.x)
+        f_star = float(ref @ Sigma @ ref)
+        assert -1e-18 <= res.f - f_star <= gap + 1e-18
+
+
+def test_npga_fista_lyapunov_inequality():
+    """Beck--Teboulle (2009) Lemma 4.1 holds along Algorithm 1's iterates.
+
+    With v_k = f(x^k) - f*, u_k = t_{k-1} x^k - (t_{k-1} - 1) x^{k-1} - x*:
+    2 alpha t_{k-1}^2 v_k + ||u_k||^2 is nonincreasing for alpha <= 1/L_f.
+    A wrong momentum, step or extrapolation breaks it on these
+    ill-conditioned 8-asset, 10-period panels (condition numbers 1e2..2e3).
+    """
+    for seed in (20, 22, 23, 24, 25):
+        R, mu, L, Rt = small_problem(8, 10, seed=seed, pct=65)
+        Sigma = L @ L.T
+        xs = qp_bruteforce(Sigma, mu, Rt)
+        fs = float(xs @ Sigma @ xs)
+        alpha = 1.0 / (2.0 * np.linalg.eigvalsh(Sigma)[-1])
+        x0 = initial_point(mu, Rt)
+        K = 150
+        traj = npga(L, 0.0, mu, Rt, x0, alpha, eps=0.0, max_iter=K, kkt_every=0,
+                    record=True).trajectory
+        assert len(traj) == K + 1 and np.array_equal(traj[0], x0)
+        t = [1.0]
+        for _ in range(K + 1):
+            t.append(0.5 * (1 + np.sqrt(1 + 4 * t[-1] ** 2)))
+        E = []
+        for k in range(1, K + 1):
+            u = t[k - 1] * traj[k] - (t[k - 1] - 1) * traj[k - 1] - xs
+            E.append(2 * alpha * t[k - 1] ** 2 * (objective(L, 0.0, traj[k]) - fs) + u @ u)
+        assert np.max(np.diff(E)) <= 1e-9 * max(E)
+        # And the O(1/k^2) rate of Theorem 1(a): f - f* <= 2||x^0 - x*||^2 / (alpha (k+1)^2).
+        for k in range(1, K + 1):
+            assert objective(L, 0.0, traj[k]) - fs <= 2 * (x0 - xs) @ (x0 - xs) / (alpha * (k + 1) ** 2)
+
+
+def test_npga_linear_rate_with_ridge():
+    """With gamma > 0 the KKT residual decays geometrically (Theorem 1(b) regime)."""
+    R, mu, L, Rt = small_problem(60, 300, seed=5)
+    gamma = 5e-4
+    lam = power_norm2(L, power_start(60), 100)
+    x0 = initial_point(mu, Rt)
+    res = npga(L, gamma, mu, Rt, x0, step_size(lam, gamma), eps=1e-13, max_iter=3000, kkt_every=1)
+    assert res.converged
+    ks = np.array([k for k, _ in res.kkt_history[5:]])
+    rs = np.array([r for _, r in res.kkt_history[5:]])
+    slope = np.polyfit(ks, np.log(np.maximum(rs, 1e-300)), 1)[0]
+    assert slope < -0.02
+
+
+def test_npga_small_config_kkt_and_certificates():
+    R, mu, L, Rt = small_problem(CFG_SMALL.n, CFG_SMALL.T, seed=CFG_SMALL.seed)
+    lam = power_norm2(L, power_start(L.shape[0]), 50)
+    a = step_size(lam, 0.0)
+    x0 = initial_point(mu, Rt)
+    res = npga(L, 0.0, mu, Rt, x0, a, eps=1e-6, max_iter=20000)
+    assert res.converged and res.kkt <= 1e-6
+    x = res.x
+    assert x.min() >= 0 and abs(x.sum() - 1) < 1e-12 and mu @ x >= Rt - 1e-15
+    assert kkt_residual(L, 0.0, mu, Rt, x, a) == pytest.approx(res.kkt)
+    # FW gap bounds f - f*; a long run gives f* from below within it.
+    gap = fw_gap(L, 0.0, mu, Rt, x)
+    ref = npga(L, 0.0, mu, Rt, x0, a, eps=1e-12, max_iter=200000)
+    assert 0.0 <= res.f - ref.f <= gap + 1e-18
+    assert solver_gap(res.f, ref.f) < 1e-3
+
+
+def test_lin_min_F_matches_vertex_scan_and_gap_metric():
+    rng = np.random.default_rng(9)
+    mu = rng.uniform(-1e-3, 1e-3, 40)
+    g = rng.standard_normal(40)
+    R = 2e-4
+    best = min(lam * g[i] + (1 - lam) * g[j] for i, j, lam in vertices_F(mu, R))
+    assert lin_min_F(g, mu, R) == pytest.approx(best, abs=1e-15)
+    assert solver_gap(1.1, 1.0) == pytest.approx(0.1)
+    assert solver_gap(0.9, 1.0) == 0.0
+    assert solver_gap(1.0, 0.0) == pytest.approx(1e12)
+
+
+# ---------------------------------------------------------------- STR
+def test_str_spectrum_identities():
+    _, _, L, _ = small_problem(60, 400, seed=2)
+    Phi_t = gaussian_sketch(400, 120, seed=3)
+    Lt = strmodel.sketch(L, Phi_t)
+    k = 10
+    L_eff, sigma, Uk = strmodel.truncate(Lt, k)
+    # Library SVD of tilde L gives the same singular values.
+    sv = np.linalg.svd(Lt, compute_uv=False)
+    np.testing.assert_allclose(sigma, sv[:k], rtol=1e-10)
+    np.testing.assert_allclose(L_eff.T @ L_eff, np.diag(sigma ** 2), atol=1e-12 * sigma[0] ** 2)
+    gamma = strmodel.ridge_default(np.sum(L * L), 60)
+    Sh = strmodel.str_covariance(L_eff, gamma)
+    ev = np.sort(np.linalg.eigvalsh(Sh))[::-1]
+    want = np.sort(np.concatenate([sigma ** 2 + gamma, np.full(60 - k, gamma)]))[::-1]
+    np.testing.assert_allclose(ev, want, rtol=1e-9, atol=1e-12 * ev[0])
+    assert ev[0] / ev[-1] == pytest.approx((sigma[0] ** 2 + gamma) / gamma, rel=1e-8)
+    # hat L hat L^T = hat Sigma with V_l from the SVD of tilde L (App. D.3).
+    _, _, Vt = np.linalg.svd(Lt, full_matrices=False)
+    Lhat = strmodel.structured_factor(L, Phi_t, Vt[:k].T, gamma)
+    np.testing.assert_allclose(Lhat @ Lhat.T, Sh, rtol=1e-9, atol=1e-12 * ev[0])
+    # Truncation error is lambda_{l+1} of tilde Sigma (Eckart--Young).
+    Kt = Lt @ Lt.T
+    assert np.linalg.norm(Kt - L_eff @ L_eff.T, 2) == pytest.approx(sv[k] ** 2, rel=1e-8)
+
+
+def test_sketch_embedding_bound_and_moments():
+    rng_shape = (80, 3000)
+    _, _, L, _ = small_problem(*rng_shape, seed=4)
+    s = 1500
+    Phi_t = gaussian_sketch(rng_shape[1], s, seed=5)
+    # Moments of Phi: mean 0, variance 1/s.
+    assert abs(Phi_t.mean()) < 5.0 / np.sqrt(Phi_t.size) / np.sqrt(s)
+    assert Phi_t.var() * s == pytest.approx(1.0, rel=0.01)
+    Sigma = L @ L.T
+    Lt = strmodel.sketch(L, Phi_t)
+    # Empirical epsilon of the subspace embedding for Im(L^T).
+    U, _, _ = np.linalg.svd(L.T, full_matrices=False)
+    G = (Phi_t @ U)
+    eps = np.linalg.norm(G.T @ G - np.eye(U.shape[1]), 2)
+    assert eps < 1.0
+    assert np.linalg.norm(Lt @ Lt.T - Sigma, 2) <= eps * np.linalg.norm(Sigma, 2) * (1 + 1e-10)
+    x = np.random.default_rng(1).dirichlet(np.ones(80))
+    q, qt = x @ Sigma @ x, np.sum((Lt.T @ x) ** 2)
+    assert (1 - eps) * q <= qt <= (1 + eps) * q
+
+
+def test_knee_rank_and_kappa_ridge():
+    lam = np.array([100.0, 50.0, 40.0, 5.0, 4.9, 4.8, 0.1])
+    # lam_{i+1}/lam_i = .5 .8 .125 .98 .98 .02 and lam_i/lam_1 = 1 .5 .4 .05 .049 .048:
+    # with rho = .6, tau = .1 admits i in {1, 3}; tau = 1e-2 also admits i = 6.
+    assert strmodel.knee_rank(lam, 0.1, 0.6) == 3
+    assert strmodel.knee_rank(lam, 1e-2, 0.6) == 6
+    g = strmodel.gamma_for_kappa(10.0, 101.0)
+    assert (100.0 + g) / g == pytest.approx(101.0)
