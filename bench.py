@@ -1,0 +1,333 @@
+"""Benchmark: NPGA time to a 1e-6 KKT residual at the paper's full shape.
+
+Workload: n = 5440 assets x T = 48374 periods (the paper's real-data shape,
+Sec. 5.2), synthetic 20-factor returns from ``synth.CFG_FULL`` (the paper's
+panel is proprietary), centered on the GPU, L stored as FP32 (1.05 GB, far
+larger than L2, so no flush is needed between steps).  One step = one full
+solve through the C ABI: 50 power iterations for the step size, NPGA with a
+KKT check every 5 iterations until the residual is <= 1e-6, and the final
+objective.  Inputs are resident in HBM when the timed region starts.
+
+Printed JSON (one line, rank 0): value = seconds per solve (lower is
+better), e2e = the same through host buffers (upload R, center, solve,
+download x), roofline = the dominant gemv kernel's HBM throughput measured
+with CUDA events around every launch of the loop, cpu_baseline = the FP64
+oracle on this host's cores (bounded sample, extrapolated per solve).
+
+``--impl reference`` times the FP64 oracle (the CPU restatement of the
+method) instead, as the reference arm.  Multi-GPU (torchrun): every rank
+solves its own problem (replicas, no collective in the path); the time is
+the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-6 KKT, NPGA full model n=5440 T=48374"
+FALLBACK_HBM = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mv", choices=["mv", "reference"])
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--config", default="full", choices=["full", "small"])
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(args, rank):
+    from synth import CFG_FULL, CFG_SMALL
+    base = CFG_FULL if args.config == "full" else CFG_SMALL
+    # each rank solves its own independent problem (weak scaling)
+    return base.scaled(base.n, base.T, seed=base.seed + rank)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def committed_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "gemv_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2604_02917_gb300", "csrc", "gemv.cuh")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("gemv_source_sha") != sha:
+        return None
+    v = vals.get(f"{kernel}_dram_bytes_per_launch")
+    return float(v) if v else None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-i", str(dev_index), "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(model, gpu_iters, power_iters, eps, R32=None, budget_s=25.0):
+    """FP64 oracle on this host, timed on a bounded sample and scaled to one solve.
+
+    Sample: p power iterations and k NPGA iterations (with one literal KKT
+    check) on the full matrix; the per-iteration times are scaled to the GPU
+    solve's 50 power iterations and its iteration count.
+    """
+    from synth import factor_returns, power_start
+    from oracle.center import center_factor
+    from oracle.npga import initial_point, npga, power_norm2, step_size
+    if R32 is None:
+        R32 = factor_returns(model, np.float32)
+    mu, L, _ = center_factor(R32.astype(np.float64))
+    del R32
+    Rt = float(np.percentile(mu, 60))
+    r0 = power_start(model.n)
+    t0 = time.perf_counter()
+    p = 2
+    lam = power_norm2(L, r0, p)
+    t_pow = (time.perf_counter() - t0) / p
+    a = step_size(lam, 0.0)
+    x0 = initial_point(mu, Rt)
+    k = 5
+    t0 = time.perf_counter()
+    npga(L, 0.0, mu, Rt, x0, a, eps=0.0, max_iter=k, kkt_every=5)
+    t_k = (time.perf_counter() - t0) / k        # includes the k=0 and k=5 literal KKT checks
+    per_solve = power_iters * t_pow + gpu_iters * t_k
+    return {"value": per_solve, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"FP64 NumPy oracle on the full {model.n}x{model.T} matrix: {p} power iterations "
+                      f"({t_pow:.3f} s each) and {k} NPGA iterations with 2 literal KKT checks "
+                      f"({t_k:.3f} s each), scaled to {power_iters} power + {gpu_iters} NPGA iterations"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from synth import factor_returns
+    model = workload(args, 0)
+    R32 = factor_returns(model, np.float32)
+    gpu_iters_est = 60            # typical iteration count of this workload (mv arm reports its own)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(model, gpu_iters_est, 50, args.eps, R32=R32)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"npga full model n={model.n} T={model.T}, FP64 oracle", "n": model.n,
+                       "T": model.T, "kkt_eps": args.eps},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    from paper_2604_02917_gb300 import mv
+    from synth import factor_returns, power_start
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    model = workload(args, rank)
+    R32 = factor_returns(model, np.float32)
+    R_dev = torch.from_numpy(R32).to(dev)
+    L, rs, mu, tr = mv.center_factor(R_dev, args.dtype)
+    Rt = float(np.percentile(mu.cpu().numpy(), 60))
+    r0 = torch.from_numpy(power_start(model.n)).to(dev)
+    solver = mv.Solver(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
+                       timing=1)
+    del R_dev
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        solver.solve()
+    barrier()
+    clk = Clocks(local)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    infos = []
+    barrier()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, info = solver.solve()
+        infos.append(info)
+    ev1.record(stream)
+    barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # roofline of the dominant kernel (per-launch CUDA events around every loop launch)
+    es = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
+    pairs = sum(i["timed_pairs"] for i in infos)
+    tt = sum(i["t_gemv_t_ms"] for i in infos)
+    tn = sum(i["t_gemv_n_ms"] for i in infos)
+    kern = "gemv_t" if tt >= tn else "gemv_n"
+    avg_ms = (tt if kern == "gemv_t" else tn) / max(pairs, 1)
+    nT = model.n * model.T
+    if kern == "gemv_t":
+        alg = nT * es + 4 * model.n + 4 * model.T + (4 * model.n if args.dtype == "fp8" else 0)
+    else:
+        alg = nT * es + 4 * model.T + 8 * model.n + (4 * model.n if args.dtype == "fp8" else 0)
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": committed_traffic(kern), "kernel": kern,
+            "peak_source": peak_kind, "avg_launch_us": round(avg_ms * 1e3, 2),
+            "alg_bytes_per_launch": alg, "other_kernel_avg_us": round(
+                ((tn if kern == "gemv_t" else tt) / max(pairs, 1)) * 1e3, 2),
+            "step_kernel_avg_us": round(sum(i["t_step_ms"] for i in infos) / max(pairs, 1) * 1e3, 2)}
+
+    # end to end through host buffers: upload R, center, solve, download x
+    e2e = None
+    if not args.no_e2e:
+        R_pin = torch.from_numpy(R32).pin_memory()
+        R_buf = torch.empty_like(R_pin, device=dev)
+        x_host = torch.empty(model.n, dtype=torch.float64).pin_memory()
+        e_solver = None
+        e_times = []
+        for i in range(2 + 3):
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            R_buf.copy_(R_pin, non_blocking=True)
+            L2, rs2, mu2, _ = mv.center_factor(R_buf, args.dtype)
+            if e_solver is None:
+                e_solver = mv.Solver(L2, mu2, Rt, model.T, dtype=args.dtype, row_scale=rs2, power_start=r0,
+                                     eps=args.eps)
+            else:
+                e_solver.problem.L = L2.data_ptr()
+                e_solver.problem.mu = mu2.data_ptr()
+                e_solver.problem.row_scale = None if rs2 is None else rs2.data_ptr()
+                e_solver._keep = (L2, mu2, rs2, r0)
+            x, _ = e_solver.solve()
+            x_host.copy_(x, non_blocking=True)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 2:
+                e_times.append(a0.elapsed_time(a1))
+            del L2, mu2, rs2
+        e2e = {"value": float(np.mean(e_times)) / 1e3, "unit": "s",
+               "h2d_bytes_per_step": int(R32.nbytes), "d2h_bytes_per_step": int(model.n * 8)}
+        del R_buf, R_pin
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu and args.config == "full":
+        iters = int(np.median([i["iterations"] for i in infos]))
+        del L
+        torch.cuda.empty_cache()
+        cb = cpu_baseline(model, iters, 50, args.eps, R32=R32)
+    if rank == 0:
+        last = infos[-1]
+        line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+                "config": {"workload": f"npga full model n={model.n} T={model.T} {args.dtype} L, "
+                                       f"KKT eps={args.eps}, 50 power iterations",
+                           "n": model.n, "T": model.T, "kkt_eps": args.eps,
+                           "l2": "inputs larger than L2 (L is %.2f GB)" % (nT * es / 1e9),
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
+                "gpu_launches": int(sum(i["launches"] for i in infos)),
+                "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * mv.h -- C ABI of the GB300 (sm_103a) NPGA library for constrained
+ * mean--variance portfolios.
+ *
+ * Problem (Sec. 1, Eq. mv; Sec. 3.1, Eq. npga-unified-grad):
+ *     minimise  f(x) = ||L_eff^T x||_2^2 + gamma ||x||_2^2
+ *     over      F = { x in R^n : mu^T x >= R_target, 1^T x = 1, x >= 0 }
+ * where L_eff is the centered covariance factor L (Sec. 2.1), its sketch
+ * L Phi (Sec. 2.3) or the STR factor (Sec. 2.5), so Sigma = L_eff L_eff^T.
+ *
+ * Conventions shared by every call
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; pointers
+ *    named h_* are HOST pointers.  The library never frees caller memory and
+ *    never allocates device memory inside a call: scratch comes from a
+ *    caller-provided device workspace whose size the matching
+ *    *_workspace_size query returns.  Workspaces must be 256-byte aligned.
+ *  - Matrices are row-major: row i (one asset) holds T periods; element
+ *    (i, t) sits at i * ld + t.  For 16-byte vector access, the base pointer
+ *    must be 16-byte aligned and ld * sizeof(element) a multiple of 16
+ *    (ld % 4 == 0 for F32, % 8 for BF16, % 16 for FP8).  Violations return
+ *    MV_ERR_INVALID_ARG before anything is launched.
+ *  - All work is enqueued on the given stream (NULL = legacy default
+ *    stream).  Calls documented as "blocking" synchronise that stream before
+ *    they return; the others are asynchronous.
+ *  - Return codes are mv_status.  Argument errors are detected on the host
+ *    before launch; failures found on the device are reported through the
+ *    info structs named in each call.
+ */
+#ifndef MV_H
+#define MV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; declared here so this header needs no CUDA headers. */
+typedef struct CUstream_st *mv_stream_t;
+
+typedef enum {
+    MV_OK = 0,
+    MV_ERR_INVALID_ARG = 1,    /* bad pointer, size, alignment or option          */
+    MV_ERR_INFEASIBLE = 2,     /* F is empty: R_target > max mu (or < min mu, EQ) */
+    MV_ERR_NOT_CONVERGED = 3,  /* iteration budget hit; best iterate returned     */
+    MV_ERR_TIMEOUT = 4,        /* a bounded device-side wait gave up               */
+    MV_ERR_NUMERIC = 5,        /* NaN or Inf met in data or iterates               */
+    MV_ERR_CUDA = 6,           /* a CUDA runtime call failed                       */
+    MV_ERR_UNSUPPORTED = 7,    /* valid request this build does not implement      */
+    MV_ERR_WORKSPACE = 8       /* workspace NULL, too small or misaligned          */
+} mv_status;
+
+typedef enum {
+    MV_F32 = 0,        /* float                                                 */
+    MV_BF16 = 1,       /* bfloat16 storage, FP32 accumulation                   */
+    MV_FP8_E4M3 = 2    /* fp8 e4m3 storage with one FP32 scale per row (asset)  */
+} mv_dtype;
+
+typedef enum {
+    MV_RETURN_GE = 0,  /* mu^T x >= R_target: the set F of Sec. 1 / Sec. 3.1    */
+    MV_RETURN_EQ = 1   /* mu^T x == R_target: equality variant (nu of any sign) */
+} mv_return_mode;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *mv_status_string(int status);
+
+/* Library version string, e.g. "mv 0.1 sm_103a". */
+const char *mv_version(void);
+
+/* Description of the last CUDA runtime failure seen by this thread (the call,
+ * its error name and source location), or "" if none.  Valid until the next
+ * failing call on the same thread. */
+const char *mv_last_error(void);
+
+/* ------------------------------------------------------------------------
+ * 1. Centering (Sec. 2.1):  mu = R 1_T / T,   L = (R - mu 1_T^T) / sqrt(T - 1),
+ *    trace(Sigma) = ||L||_F^2.
+ *
+ *  d_R        [in]  n x T returns, FP32, row-major with leading dim ldR >= T.
+ *  out_dtype  [in]  storage type of L (MV_F32, MV_BF16 or MV_FP8_E4M3).
+ *  d_L        [out] n x T factor of that type, leading dim ldL >= T; columns
+ *                   T..ldL-1 of every row are written as zeros.
+ *  d_row_scale[out] FP8 only (else may be NULL): n FP32 scales s_i such that
+ *                   L(i,t) ~= s_i * q(i,t); s_i = max_t |L(i,t)| / 448.
+ *  d_mu       [out] n FP64 sample means.
+ *  d_trace    [out] one FP64: ||L||_F^2 = trace(Sigma), summed in FP64 from the
+ *                   unrounded centered values.
+ *  Sums are FP64.  Requires n >= 1, T >= 2.  Asynchronous.
+ * ------------------------------------------------------------------------ */
+size_t mv_center_workspace_size(int64_t n, int64_t T);
+int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR,
+                     int out_dtype, void *d_L, int64_t ldL, float *d_row_scale,
+                     double *d_mu, double *d_trace,
+                     void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * 2. Exact projection onto F (Sec. 3.1, Eqs. simplex-tau, simplex-proj,
+ *    projF-dualpath), batched over problems that share mu.
+ *
+ *  x(nu) = Pi_Delta(v + nu mu) with the simplex threshold tau(nu) from
+ *  sum_i max(v_i + nu mu_i - tau, 0) = 1; phi(nu) = mu^T x(nu) is
+ *  nondecreasing.  If phi(0) >= R_target the simplex projection is returned
+ *  (nu = 0); otherwise nu > 0 solves phi(nu) = R_target.  The search over
+ *  tau and nu is a safeguarded Newton iteration on these piecewise-linear
+ *  functions, finished exactly on the identified support S by solving the
+ *  two linear equations of the budget and return rows.  FP64 throughout.
+ *
+ *  d_v        [in]  batch x n FP64 points to project (row b = problem b).
+ *  d_mu       [in]  n FP64 expected returns, shared by the batch.
+ *  d_R_target [in]  batch FP64 targets.
+ *  mode       [in]  mv_return_mode.
+ *  d_x        [out] batch x n FP64 projections.
+ *  d_info     [out] batch mv_proj_info (device memory).  info.status is
+ *                   MV_OK, MV_ERR_INFEASIBLE (x filled with NaN) or
+ *                   MV_ERR_NOT_CONVERGED (step budget hit; best x kept).
+ *  Needs no workspace.  1 <= n <= 65536.  Asynchronous.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    double nu;         /* multiplier of the return row (0 when inactive)      */
+    double tau;        /* simplex threshold at nu                              */
+    double residual;   /* mu^T x - R_target                                    */
+    int32_t support;   /* |{i : x_i > 0}|                                      */
+    int32_t status;    /* mv_status of this problem                            */
+    int32_t steps;     /* block-wide reductions spent                          */
+    int32_t active;    /* 1 if the return row is tight (nu != 0)               */
+} mv_proj_info;
+
+int mv_project(const double *d_v, const double *d_mu, const double *d_R_target,
+               int64_t n, int64_t batch, int mode, double *d_x,
+               mv_proj_info *d_info, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * 3. NPGA solve (Algorithm 1 with the fixed step of Sec. 3.1).
+ *
+ *  Step size: alpha = 1 / (2 (lambda_hat (1 + power_safety) + gamma)) where
+ *  lambda_hat = ||L_eff^T u||^2 after power_iters steps of the power method
+ *  u <- L(L^T u)/||.|| (Sec. 3.1 remark), unless opts.alpha > 0 overrides it.
+ *  Iteration k: z = L^T y^k (FP32 accumulation), g = 2 L z + 2 gamma y^k,
+ *  v = y^k - alpha g, x^{k+1} = Pi_F(v) (FP64), FISTA momentum
+ *  t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2, beta_k = (t_k - 1)/t_{k+1},
+ *  y^{k+1} = x^{k+1} + beta_k (x^{k+1} - x^k).  Every kkt_every iterations
+ *  the residual ||Pi_F(x^k - alpha grad f(x^k)) - x^k||_2 is evaluated and
+ *  the solve stops at x^k once it is <= eps.  grad f(x^k) is obtained from
+ *  the products already computed at y^k by linearity
+ *  (L L^T x^k = (L L^T y^k + beta_{k-1} L L^T x^{k-1}) / (1 + beta_{k-1})),
+ *  so the check costs one projection and no extra pass over L.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    const void *L;            /* d: n x T factor (dtype), row-major, leading dim ld     */
+    int32_t dtype;            /* mv_dtype                                                */
+    int32_t mode;             /* mv_return_mode                                          */
+    const float *row_scale;   /* d: n FP32 row scales (FP8 only, else NULL)              */
+    int64_t n, T, ld;
+    double gamma;             /* ridge (0 for the full and sketched models)              */
+    const double *mu;         /* d: n FP64 expected returns                              */
+    double R_target;          /* target return                                           */
+    const double *power_start;/* d: n FP64 start of the power method; NULL = all ones    */
+} mv_problem;
+
+typedef struct {
+    int32_t max_iter;         /* iteration budget (default 10000)                        */
+    int32_t kkt_every;        /* KKT check period (default 5, Sec. 5.2)                 */
+    int32_t power_iters;      /* power-method steps (default 50)                         */
+    int32_t warm_start;       /* 1: x_inout holds x^0 in F; 0: x^0 = Pi_F(1/n)           */
+    double eps;               /* KKT tolerance (default 1e-6)                            */
+    double power_safety;      /* lambda_hat is multiplied by (1 + this); default 1e-3    */
+    double alpha;             /* > 0: fixed step override; <= 0: from the power method   */
+    int32_t use_graph;        /* 1 (default): replay iterations as a CUDA graph          */
+    int32_t timing;           /* 1: time every gemv launch of the loop with CUDA events  */
+} mv_solve_opts;
+
+typedef struct {
+    int32_t iterations;       /* k at return (x^k is returned)                           */
+    int32_t status;           /* MV_OK, MV_ERR_NOT_CONVERGED, MV_ERR_INFEASIBLE, ...     */
+    int32_t converged;        /* 1 if kkt <= eps                                         */
+    int32_t proj_failures;    /* projections that hit their step budget                  */
+    double kkt;               /* residual of the returned x                              */
+    double objective;         /* f(x) = ||L^T x||^2 + gamma ||x||^2 (one extra pass)     */
+    double alpha;             /* step used                                               */
+    double lambda_hat;        /* power-method estimate of ||L_eff||_2^2 (0 if overridden)*/
+    double nu;                /* return-row multiplier of the last projection            */
+    int32_t launches;         /* kernels this call launched (including no-op tails)      */
+    int32_t timed_pairs;      /* loop iterations whose kernels were timed (timing = 1)   */
+    double t_gemv_t_ms;       /* summed device time of those gemv_t launches             */
+    double t_gemv_n_ms;       /* summed device time of those gemv_n launches             */
+    double t_step_ms;         /* summed device time of those step (projection) launches  */
+} mv_solve_info;
+
+void mv_solve_opts_default(mv_solve_opts *opts);
+size_t mv_npga_workspace_size(const mv_problem *P);
+
+/*  d_x_inout [in/out] n FP64: x^0 when opts.warm_start = 1 (must lie in F),
+ *                     the solution x^k on return.
+ *  h_info    [out]    host struct, filled on return.
+ *  Blocking: the call synchronises `stream` once per kkt_every iterations to
+ *  read the device-side convergence flag, and returns when the solve is done. */
+int mv_npga_solve(const mv_problem *P, const mv_solve_opts *opts, double *d_x_inout,
+                  mv_solve_info *h_info, void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * 4. Gradient building block (Eq. npga-unified-grad), exposed for tests and
+ *    for callers with their own outer loop:
+ *        d_g = 2 L_eff (L_eff^T y) + 2 gamma y,   d_z = L_eff^T y.
+ *  d_y FP64 n, d_z FP32 T (may be NULL), d_g FP64 n.  Uses the workspace of
+ *  mv_npga_workspace_size.  Asynchronous.
+ * ------------------------------------------------------------------------ */
+int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
+                void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MV_H */

@@ -1,0 +1,206 @@
+// The two bandwidth-bound half-products of the NPGA gradient
+// (Sec. 2.7, Eq. npga-unified-grad):  z = L^T y  and  g = L z.
+//
+// L is n x T, row-major (one asset per row), stored as FP32, BF16 or FP8
+// e4m3 with one scale per row; every element is streamed from HBM once per
+// half-product with 16-byte read-once loads, and accumulation is FP32.
+//
+// gemv_t (z = L^T y): a block owns a strip of 256*VEC consecutive columns
+// and a split of rows.  Each thread keeps VEC column accumulators in
+// registers and walks down its rows with 8 loads in flight; the row weights
+// y_i of the split sit in shared memory.  Partial sums of every split are
+// written to a [splits x T] buffer and the last block to finish a strip
+// (atomic ticket after a fence -- no spinning) adds them in fixed split
+// order, so the result is deterministic.
+//
+// gemv_n (g = L z): a block owns 8 warps x RW rows and a column split whose
+// slice of z is staged in shared memory.  A warp reads RW rows at once,
+// lanes covering consecutive 16-byte vectors (512 contiguous bytes per
+// instruction), then reduces with shuffles.  The last block of a row group
+// adds the column-split partials in fixed order, in FP64, and applies the
+// FP8 row scale.
+//
+// FP8 row scales s_i are folded in: gemv_t consumes y'_i = s_i y_i (the
+// producer of y writes it scaled) and gemv_n multiplies its row sum by s_i.
+#pragma once
+
+#include "mv_internal.cuh"
+
+namespace mv {
+
+constexpr int kGemvThreads = 256;
+constexpr int kGemvUnroll = 8;
+constexpr int kMaxRowsPerSplit = 2048;
+
+template <int DT>
+__global__ void __launch_bounds__(kGemvThreads)
+gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ y32,
+              float *__restrict__ zpart, float *__restrict__ z, unsigned *__restrict__ tickets,
+              int rows_per_split, const volatile int *done) {
+    using S = Store<DT>;
+    constexpr int VEC = S::VEC;
+    constexpr int ES = (int)sizeof(typename S::elem);
+    if (done != nullptr && *done) return;
+    __shared__ float s_y[kMaxRowsPerSplit];
+    __shared__ bool s_last;
+
+    const int split = blockIdx.y;
+    const int r0 = split * rows_per_split;
+    const int rows = min(n - r0, rows_per_split);
+    for (int i = threadIdx.x; i < rows; i += kGemvThreads) s_y[i] = y32[r0 + i];
+    __syncthreads();
+
+    const int64_t col = ((int64_t)blockIdx.x * kGemvThreads + threadIdx.x) * VEC;
+    float acc[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) acc[e] = 0.f;
+
+    if (col + VEC <= T) {
+        const char *p = reinterpret_cast<const char *>(L) + ((int64_t)r0 * ld + col) * ES;
+        const int64_t stride = ld * ES;
+        int i = 0;
+        for (; i + kGemvUnroll <= rows; i += kGemvUnroll) {
+            uint4 u[kGemvUnroll];
+#pragma unroll
+            for (int j = 0; j < kGemvUnroll; ++j) u[j] = ld_stream16(p + (int64_t)(i + j) * stride);
+#pragma unroll
+            for (int j = 0; j < kGemvUnroll; ++j) {
+                float f[VEC];
+                S::unpack(u[j], f);
+                const float yy = s_y[i + j];
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) acc[e] = fmaf(f[e], yy, acc[e]);
+            }
+        }
+        for (; i < rows; ++i) {
+            float f[VEC];
+            S::unpack(ld_stream16(p + (int64_t)i * stride), f);
+            const float yy = s_y[i];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc[e] = fmaf(f[e], yy, acc[e]);
+        }
+    } else if (col < T) {                       // ragged tail of the last strip
+        const int ne = (int)(T - col);
+        for (int i = 0; i < rows; ++i) {
+            const float yy = s_y[i];
+            const int64_t base = (int64_t)(r0 + i) * ld + col;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                if (e < ne) acc[e] = fmaf(S::load1(L, base + e), yy, acc[e]);
+        }
+    }
+
+    float *zp = zpart + (int64_t)split * T;
+    if (col < T) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (col + e < T) zp[col + e] = acc[e];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(&tickets[blockIdx.x], 1u);
+        s_last = (ticket == gridDim.y - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (col < T) {
+        const int splits = gridDim.y;
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            if (col + e < T) {
+                float s = 0.f;
+                for (int sp = 0; sp < splits; ++sp) s += __ldcg(zpart + (int64_t)sp * T + col + e);
+                z[col + e] = s;
+            }
+        }
+    }
+    if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;   // ready for the next launch
+}
+
+template <int DT, int RW>
+__global__ void __launch_bounds__(kGemvThreads)
+gemv_n_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ z,
+              const float *__restrict__ row_scale, float *__restrict__ gpart, double *__restrict__ g,
+              unsigned *__restrict__ tickets, int cols_per_split, const volatile int *done) {
+    using S = Store<DT>;
+    constexpr int VEC = S::VEC;
+    constexpr int ES = (int)sizeof(typename S::elem);
+    constexpr int ROWS = (kGemvThreads / kWarp) * RW;
+    if (done != nullptr && *done) return;
+    extern __shared__ float s_z[];
+    __shared__ bool s_last;
+
+    const int c0 = blockIdx.y * cols_per_split;
+    const int ncol = min(T - c0, cols_per_split);
+    for (int c = threadIdx.x; c < ncol; c += kGemvThreads) s_z[c] = z[c0 + c];
+    __syncthreads();
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rbase = blockIdx.x * ROWS + warp * RW;
+    float acc[RW];
+    const char *rp[RW];
+#pragma unroll
+    for (int j = 0; j < RW; ++j) {
+        acc[j] = 0.f;
+        const int r = min(rbase + j, n - 1);      // clamp: rows past n are computed and dropped
+        rp[j] = reinterpret_cast<const char *>(L) + ((int64_t)r * ld + c0) * ES;
+    }
+    const int nfull = ncol / VEC * VEC;
+#pragma unroll 2
+    for (int c = lane * VEC; c < nfull; c += kWarp * VEC) {
+        float zz[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; e += 4) {
+            const float4 q = *reinterpret_cast<const float4 *>(s_z + c + e);
+            zz[e] = q.x;
+            zz[e + 1] = q.y;
+            zz[e + 2] = q.z;
+            zz[e + 3] = q.w;
+        }
+        uint4 u[RW];
+#pragma unroll
+        for (int j = 0; j < RW; ++j) u[j] = ld_stream16(rp[j] + (int64_t)c * ES);
+#pragma unroll
+        for (int j = 0; j < RW; ++j) {
+            float f[VEC];
+            S::unpack(u[j], f);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) acc[j] = fmaf(f[e], zz[e], acc[j]);
+        }
+    }
+    for (int c = nfull + lane; c < ncol; c += kWarp) {      // ragged tail
+#pragma unroll
+        for (int j = 0; j < RW; ++j) {
+            const int r = min(rbase + j, n - 1);
+            acc[j] = fmaf(S::load1(L, (int64_t)r * ld + c0 + c), s_z[c], acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RW; ++j) acc[j] = warp_sumf(acc[j]);
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < RW; ++j)
+            if (rbase + j < n) gpart[(int64_t)blockIdx.y * n + rbase + j] = acc[j];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned ticket = atomicAdd(&tickets[blockIdx.x], 1u);
+        s_last = (ticket == gridDim.y - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int splits = gridDim.y;
+    for (int r = blockIdx.x * ROWS + threadIdx.x; r < min(n, (int)(blockIdx.x + 1) * ROWS); r += kGemvThreads) {
+        double s = 0.0;
+        for (int sp = 0; sp < splits; ++sp) s += (double)__ldcg(gpart + (int64_t)sp * n + r);
+        if (row_scale != nullptr) s *= (double)row_scale[r];
+        g[r] = s;
+    }
+    if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
+}
+
+}  // namespace mv

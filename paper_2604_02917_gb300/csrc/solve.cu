@@ -1,0 +1,719 @@
+// NPGA solve (Algorithm 1, fixed step of Sec. 3.1) on one GPU.
+//
+// Per iteration three kernels run back to back on one stream:
+//   gemv_t  z = L^T y^k                 (all SMs, HBM-bound)
+//   gemv_n  g = L z                     (all SMs, HBM-bound)
+//   step    one block: grad f(x^k) by linearity, KKT check every kkt_every
+//           iterations, v = y^k - alpha (2g + 2 gamma y^k), x^{k+1} = Pi_F(v)
+//           (FP64, warm-started), FISTA momentum and extrapolation.
+// A chunk of kkt_every iterations is captured once into a CUDA graph and
+// replayed; every kernel returns at once when the device-side `done` flag is
+// set, so a chunk that overruns convergence costs only empty launches.  The
+// host reads the flag once per chunk.
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "gemv.cuh"
+#include "project.cuh"
+
+namespace mv {
+
+constexpr int kStepThreads = 512;
+constexpr int kProjBudget = 100;
+constexpr int kSmemVecMax = 12800;   // n up to this keeps v and mu in shared memory
+
+struct SolveState {
+    int k, done, converged, status;
+    int proj_fail, pad0, pad1, pad2;
+    double t, beta_prev;
+    double alpha, lambda_hat;
+    double kkt, nu, tau, nu_kkt, tau_kkt;
+    double mu_min, mu_max;
+    double objective;
+};
+
+struct Plan {
+    int dt, vec, esize;
+    int n, T;
+    int64_t ld;
+    int t_blocks, t_splits, t_rows;        // gemv_t grid
+    int n_groups, n_splits, n_cols;        // gemv_n grid
+    // workspace offsets (bytes)
+    size_t o_state, o_x, o_y, o_gx, o_gy, o_v, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
+    size_t total;
+};
+
+static int sm_count() {
+    static int cached = 0;
+    if (cached == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int c = 0;
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        cached = c > 0 ? c : 148;
+    }
+    return cached;
+}
+
+static constexpr int kRW = 4;   // rows per warp in gemv_n
+
+static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld) {
+    Plan p{};
+    p.dt = dt;
+    p.esize = dtype_size(dt);
+    p.vec = 16 / p.esize;
+    p.n = (int)n;
+    p.T = (int)T;
+    p.ld = ld;
+    const int sms = sm_count();
+    // gemv_t: strips of 256*VEC columns; rows split so the grid covers
+    // several waves of the machine (4 resident blocks per SM assumed).
+    const int strip = kGemvThreads * p.vec;
+    p.t_blocks = (int)((T + strip - 1) / strip);
+    const int slots = sms * 4;
+    int splits = (slots * 3 + p.t_blocks - 1) / p.t_blocks;
+    splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, (n + 63) / 64));
+    int rows = (int)((n + splits - 1) / splits);
+    if (rows > kMaxRowsPerSplit) rows = kMaxRowsPerSplit;
+    p.t_rows = rows;
+    p.t_splits = (int)((n + rows - 1) / rows);
+    // gemv_n: 32 rows per block, column splits of 16 KB of L per row.
+    const int rows_per_block = (kGemvThreads / kWarp) * kRW;
+    p.n_groups = (int)((n + rows_per_block - 1) / rows_per_block);
+    p.n_cols = 4096 * 4 / p.esize;                       // 16 KB of L per row per split
+    if (p.n_cols > T) p.n_cols = (int)((T + 32 * p.vec - 1) / (32 * p.vec) * (32 * p.vec));
+    p.n_splits = (int)((T + p.n_cols - 1) / p.n_cols);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    p.o_state = take(sizeof(SolveState));
+    p.o_x = take(8 * (size_t)n);
+    p.o_y = take(8 * (size_t)n);
+    p.o_gx = take(8 * (size_t)n);
+    p.o_gy = take(8 * (size_t)n);
+    p.o_v = take(8 * (size_t)n);
+    p.o_y32 = take(4 * (size_t)n);
+    p.o_z = take(4 * (size_t)T);
+    p.o_zpart = take(4 * (size_t)T * p.t_splits);
+    p.o_gpart = take(4 * (size_t)n * p.n_splits);
+    p.o_tick_t = take(4 * (size_t)p.t_blocks);
+    p.o_tick_n = take(4 * (size_t)p.n_groups);
+    p.total = off;
+    return p;
+}
+
+template <typename T_>
+static T_ *at(void *ws, size_t off) {
+    return reinterpret_cast<T_ *>(reinterpret_cast<char *>(ws) + off);
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void __launch_bounds__(kStepThreads)
+setup_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ r0,
+             const float *__restrict__ row_scale, float *__restrict__ y32, int n) {
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    double mn = INFINITY, mx = -INFINITY, ss = 0.0;
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        const double m = mu[i];
+        mn = fmin(mn, m);
+        mx = fmax(mx, m);
+        const double r = r0 ? r0[i] : 1.0;
+        ss += r * r;
+        if (!(m == m)) mx = NAN;
+    }
+    block_minmax<kStepThreads>(mn, mx, red);
+    __syncthreads();
+    double v1[1] = {ss};
+    block_sum<1, kStepThreads>(v1, red);
+    const double inv = v1[0] > 0.0 ? 1.0 / sqrt(v1[0]) : 0.0;
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        const double r = r0 ? r0[i] : 1.0;
+        const double s = row_scale ? (double)row_scale[i] : 1.0;
+        y32[i] = (float)(r * inv * s);
+    }
+    if (threadIdx.x == 0) {
+        SolveState z{};
+        z.mu_min = mn;
+        z.mu_max = mx;
+        z.t = 1.0;
+        z.status = (mx == mx && mn == mn) ? MV_OK : MV_ERR_NUMERIC;
+        *st = z;
+    }
+}
+
+// u <- g / ||g|| (power method), written as FP32 gemv input (row-scaled).
+__global__ void __launch_bounds__(kStepThreads)
+power_norm_kernel(const double *__restrict__ g, const float *__restrict__ row_scale,
+                  float *__restrict__ y32, int n) {
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    double ss[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += kStepThreads) ss[0] = fma(g[i], g[i], ss[0]);
+    block_sum<1, kStepThreads>(ss, red);
+    const double inv = ss[0] > 0.0 ? 1.0 / sqrt(ss[0]) : 0.0;
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        const double s = row_scale ? (double)row_scale[i] : 1.0;
+        y32[i] = (float)(g[i] * inv * s);
+    }
+}
+
+// lambda_hat = ||L^T u||^2; alpha = 1 / (2 (lambda_hat (1 + safety) + gamma)).
+__global__ void __launch_bounds__(kStepThreads)
+step_size_kernel(SolveState *st, const float *__restrict__ z, int T, double gamma, double safety,
+                 double alpha_override) {
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    double ss[1] = {0.0};
+    for (int t = threadIdx.x; t < T; t += kStepThreads) ss[0] = fma((double)z[t], (double)z[t], ss[0]);
+    block_sum<1, kStepThreads>(ss, red);
+    if (threadIdx.x == 0) {
+        st->lambda_hat = ss[0];
+        double a = alpha_override;
+        if (!(a > 0.0)) {
+            const double lf = 2.0 * (ss[0] * (1.0 + safety) + gamma);
+            a = lf > 0.0 ? 1.0 / lf : 1.0;
+        }
+        st->alpha = a;
+        if (!(a == a) || !isfinite(a)) st->status = MV_ERR_NUMERIC;
+    }
+}
+
+// x^0: Pi_F(1/n 1), or the caller's x^0 when warm-starting; y^0 = x^0.
+__global__ void __launch_bounds__(kStepThreads)
+init_x_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ x_in,
+              double *__restrict__ vbuf, double *__restrict__ x, double *__restrict__ y,
+              float *__restrict__ y32, const float *__restrict__ row_scale, int n, double R, int mode) {
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    const double mn = st->mu_min, mx = st->mu_max;
+    if (x_in == nullptr) {
+        for (int i = threadIdx.x; i < n; i += kStepThreads) vbuf[i] = 1.0 / n;
+        __syncthreads();
+        Projector<kStepThreads> P{vbuf, mu, n, red, 0};
+        const ProjOut o = P.solve(R, mode, mn, mx, 0.0, -INFINITY, kProjBudget);
+        for (int i = threadIdx.x; i < n; i += kStepThreads) {
+            const double xi = o.status == MV_ERR_INFEASIBLE ? NAN : fmax(fma(o.nu, mu[i], vbuf[i]) - o.tau, 0.0);
+            x[i] = xi;
+            y[i] = xi;
+            y32[i] = (float)(xi * (row_scale ? (double)row_scale[i] : 1.0));
+        }
+        if (threadIdx.x == 0) {
+            if (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC) st->status = o.status;
+            st->nu = o.nu;
+            st->tau = o.tau;
+            st->nu_kkt = o.nu;
+            st->tau_kkt = o.tau;
+        }
+    } else {
+        for (int i = threadIdx.x; i < n; i += kStepThreads) {
+            const double xi = x_in[i];
+            x[i] = xi;
+            y[i] = xi;
+            y32[i] = (float)(xi * (row_scale ? (double)row_scale[i] : 1.0));
+        }
+        if (threadIdx.x == 0) {
+            st->nu = 0.0;
+            st->tau = -INFINITY;
+            st->nu_kkt = 0.0;
+            st->tau_kkt = -INFINITY;
+        }
+    }
+    if (threadIdx.x == 0) {
+        st->t = 1.0;
+        st->beta_prev = 0.0;
+        st->k = 0;
+        st->done = (st->status != MV_OK) ? 1 : 0;
+        st->converged = 0;
+        st->proj_fail = 0;
+        st->kkt = INFINITY;
+    }
+}
+
+struct StepArgs {
+    SolveState *st;
+    const double *gy;
+    double *x, *y, *gx, *vbuf;
+    float *y32;
+    const double *mu;
+    const float *row_scale;
+    int n, mode, kkt_every, max_iter;
+    double R, gamma, eps;
+    int use_smem;
+};
+
+__global__ void __launch_bounds__(kStepThreads) npga_step_kernel(StepArgs a) {
+    extern __shared__ double sm[];
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    SolveState *st = a.st;
+    if (*(volatile int *)&st->done) return;
+    const int n = a.n;
+    const int k = st->k;
+    const double beta_prev = st->beta_prev, alpha = st->alpha, t = st->t;
+    const double mn = st->mu_min, mx = st->mu_max;
+    const double nu0 = st->nu, tau0 = st->tau, nuk0 = st->nu_kkt, tauk0 = st->tau_kkt;
+    const double gamma = a.gamma;
+
+    double *V = a.use_smem ? sm : a.vbuf;
+    const double *MU = a.mu;
+    if (a.use_smem) {
+        double *smu = sm + n;
+        for (int i = threadIdx.x; i < n; i += kStepThreads) smu[i] = a.mu[i];
+        MU = smu;
+    }
+    const bool check = (a.kkt_every > 0 && k % a.kkt_every == 0) || (k >= a.max_iter);
+
+    // grad f(x^k)/2 - gamma x^k = L L^T x^k by linearity from the product at y^k.
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        const double gyi = a.gy[i];
+        const double gxi = (k == 0) ? gyi : (gyi + beta_prev * a.gx[i]) / (1.0 + beta_prev);
+        a.gx[i] = gxi;
+        if (check) {
+            const double xi = a.x[i];
+            V[i] = xi - alpha * (2.0 * gxi + 2.0 * gamma * xi);
+        }
+    }
+    __syncthreads();
+    Projector<kStepThreads> P{V, MU, n, red, 0};
+    if (check) {
+        const ProjOut o = P.solve(a.R, a.mode, mn, mx, nuk0, tauk0, kProjBudget);
+        double r2[1] = {0.0};
+        for (int i = threadIdx.x; i < n; i += kStepThreads) {
+            const double p = fmax(fma(o.nu, MU[i], V[i]) - o.tau, 0.0);
+            const double d = p - a.x[i];
+            r2[0] = fma(d, d, r2[0]);
+        }
+        block_sum<1, kStepThreads>(r2, red);
+        const double kkt = sqrt(r2[0]);
+        const bool conv = kkt <= a.eps;
+        const bool stop = conv || k >= a.max_iter || !(kkt == kkt);
+        if (threadIdx.x == 0) {
+            st->kkt = kkt;
+            st->nu_kkt = o.nu;
+            st->tau_kkt = o.tau;
+            if (o.status != MV_OK) st->proj_fail += 1;
+            if (stop) {
+                st->done = 1;
+                st->converged = conv ? 1 : 0;
+                st->status = conv ? MV_OK : (!(kkt == kkt) ? MV_ERR_NUMERIC : MV_ERR_NOT_CONVERGED);
+            }
+        }
+        if (stop) return;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        const double yi = a.y[i];
+        V[i] = yi - alpha * (2.0 * a.gy[i] + 2.0 * gamma * yi);
+    }
+    __syncthreads();
+    const ProjOut o = P.solve(a.R, a.mode, mn, mx, nu0, tau0, kProjBudget);
+    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    const double beta = (t - 1.0) / tn;
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        const double xn = fmax(fma(o.nu, MU[i], V[i]) - o.tau, 0.0);
+        const double xo = a.x[i];
+        const double yn = xn + beta * (xn - xo);
+        a.x[i] = xn;
+        a.y[i] = yn;
+        a.y32[i] = (float)(yn * (a.row_scale ? (double)a.row_scale[i] : 1.0));
+    }
+    if (threadIdx.x == 0) {
+        st->t = tn;
+        st->beta_prev = beta;
+        st->k = k + 1;
+        st->nu = o.nu;
+        st->tau = o.tau;
+        if (o.status != MV_OK) st->proj_fail += 1;
+        if (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC) {
+            st->done = 1;
+            st->status = o.status;
+        }
+    }
+}
+
+// FP64 n-vector -> scaled FP32 gemv input.
+__global__ void to_y32_kernel(const double *__restrict__ x, const float *__restrict__ row_scale,
+                              float *__restrict__ y32, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y32[i] = (float)(x[i] * (row_scale ? (double)row_scale[i] : 1.0));
+}
+
+// f(x) = ||z||^2 + gamma ||x||^2 with z = L^T x.
+__global__ void __launch_bounds__(kStepThreads)
+objective_kernel(SolveState *st, const float *__restrict__ z, int T, const double *__restrict__ x, int n,
+                 double gamma) {
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    double s[2] = {0.0, 0.0};
+    for (int t = threadIdx.x; t < T; t += kStepThreads) s[0] = fma((double)z[t], (double)z[t], s[0]);
+    for (int i = threadIdx.x; i < n; i += kStepThreads) s[1] = fma(x[i], x[i], s[1]);
+    block_sum<2, kStepThreads>(s, red);
+    if (threadIdx.x == 0) st->objective = s[0] + gamma * s[1];
+}
+
+// g = 2 (L z) + 2 gamma y   (gradient building block output).
+__global__ void grad_finish_kernel(const double *__restrict__ lz, const double *__restrict__ y, double gamma,
+                                   double *__restrict__ g, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) g[i] = 2.0 * lz[i] + 2.0 * gamma * y[i];
+}
+
+// ------------------------------------------------------------------ host
+static int validate_problem(const mv_problem *P) {
+    if (P == nullptr || P->L == nullptr || P->mu == nullptr) return MV_ERR_INVALID_ARG;
+    if (P->dtype != MV_F32 && P->dtype != MV_BF16 && P->dtype != MV_FP8_E4M3) return MV_ERR_INVALID_ARG;
+    if (P->mode != MV_RETURN_GE && P->mode != MV_RETURN_EQ) return MV_ERR_INVALID_ARG;
+    if (P->n < 1 || P->T < 1 || P->ld < P->T) return MV_ERR_INVALID_ARG;
+    if (P->n > (1 << 26) || P->T > (1LL << 31) - 1) return MV_ERR_UNSUPPORTED;
+    const int es = dtype_size(P->dtype);
+    if (((uintptr_t)P->L) % 16 != 0 || (P->ld * es) % 16 != 0) return MV_ERR_INVALID_ARG;
+    if (P->dtype == MV_FP8_E4M3 && P->row_scale == nullptr) return MV_ERR_INVALID_ARG;
+    if (!(P->gamma >= 0.0) || !(P->R_target == P->R_target)) return MV_ERR_INVALID_ARG;
+    return MV_OK;
+}
+
+static int check_ws(void *ws, size_t ws_bytes, size_t need) {
+    if (need == 0) return MV_OK;
+    if (ws == nullptr || ws_bytes < need || ((uintptr_t)ws) % 256 != 0) return MV_ERR_WORKSPACE;
+    return MV_OK;
+}
+
+template <int DT>
+static void launch_gemv_t(const Plan &p, const void *L, const float *y32, float *zpart, float *z,
+                          unsigned *tick, const int *done, cudaStream_t s) {
+    dim3 grid(p.t_blocks, p.t_splits);
+    gemv_t_kernel<DT><<<grid, kGemvThreads, 0, s>>>(L, p.ld, p.n, p.T, y32, zpart, z, tick, p.t_rows, done);
+}
+
+template <int DT>
+static void launch_gemv_n(const Plan &p, const void *L, const float *z, const float *row_scale, float *gpart,
+                          double *g, unsigned *tick, const int *done, cudaStream_t s) {
+    dim3 grid(p.n_groups, p.n_splits);
+    const size_t smem = (size_t)p.n_cols * 4;
+    gemv_n_kernel<DT, kRW><<<grid, kGemvThreads, smem, s>>>(L, p.ld, p.n, p.T, z, row_scale, gpart, g, tick,
+                                                           p.n_cols, done);
+}
+
+// Kernel attributes are set once per process, before any stream capture.
+static int set_kernel_attrs() {
+    static std::once_flag once;
+    static int status = MV_OK;
+    std::call_once(once, [] {
+        const int big = 96 * 1024;
+        if (cudaFuncSetAttribute(gemv_n_kernel<MV_F32, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(gemv_n_kernel<MV_BF16, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(gemv_n_kernel<MV_FP8_E4M3, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(npga_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kSmemVecMax) !=
+                cudaSuccess)
+            status = MV_ERR_CUDA;
+    });
+    return status;
+}
+
+static void gemv_pair(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done,
+                      double *g_out, cudaStream_t s) {
+    float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z), *gpart = at<float>(ws, p.o_gpart);
+    unsigned *tt = at<unsigned>(ws, p.o_tick_t), *tn = at<unsigned>(ws, p.o_tick_n);
+    switch (p.dt) {
+        case MV_F32:
+            launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, done, s);
+            launch_gemv_n<MV_F32>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s);
+            break;
+        case MV_BF16:
+            launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, done, s);
+            launch_gemv_n<MV_BF16>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s);
+            break;
+        default:
+            launch_gemv_t<MV_FP8_E4M3>(p, P->L, y32, zpart, z, tt, done, s);
+            launch_gemv_n<MV_FP8_E4M3>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s);
+            break;
+    }
+}
+
+static void gemv_t_only(const Plan &p, const mv_problem *P, const float *y32, void *ws, cudaStream_t s) {
+    float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z);
+    unsigned *tt = at<unsigned>(ws, p.o_tick_t);
+    switch (p.dt) {
+        case MV_F32: launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, nullptr, s); break;
+        case MV_BF16: launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, nullptr, s); break;
+        default: launch_gemv_t<MV_FP8_E4M3>(p, P->L, y32, zpart, z, tt, nullptr, s); break;
+    }
+}
+
+static size_t step_smem(int n) { return n <= kSmemVecMax ? (size_t)16 * n : 0; }
+
+static void launch_step(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, cudaStream_t s) {
+    StepArgs a;
+    a.st = at<SolveState>(ws, p.o_state);
+    a.gy = at<double>(ws, p.o_gy);
+    a.x = at<double>(ws, p.o_x);
+    a.y = at<double>(ws, p.o_y);
+    a.gx = at<double>(ws, p.o_gx);
+    a.vbuf = at<double>(ws, p.o_v);
+    a.y32 = at<float>(ws, p.o_y32);
+    a.mu = P->mu;
+    a.row_scale = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    a.n = p.n;
+    a.mode = P->mode;
+    a.kkt_every = O->kkt_every;
+    a.max_iter = O->max_iter;
+    a.R = P->R_target;
+    a.gamma = P->gamma;
+    a.eps = O->eps;
+    const size_t sm = step_smem(p.n);
+    a.use_smem = sm > 0;
+    npga_step_kernel<<<1, kStepThreads, sm, s>>>(a);
+}
+
+// One loop iteration.  With `ev` non-null, events ev[0..3] bracket gemv_t,
+// gemv_n and the step kernel (ev[3] is the next iteration's ev[0]).
+static void launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
+                             cudaStream_t s, const cudaEvent_t *ev) {
+    SolveState *st = at<SolveState>(ws, p.o_state);
+    float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z), *gpart = at<float>(ws, p.o_gpart);
+    unsigned *tt = at<unsigned>(ws, p.o_tick_t), *tn = at<unsigned>(ws, p.o_tick_n);
+    const float *y32 = at<float>(ws, p.o_y32);
+    double *gy = at<double>(ws, p.o_gy);
+    const int *done = &st->done;
+    if (ev) cudaEventRecord(ev[0], s);
+    switch (p.dt) {
+        case MV_F32: launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, done, s); break;
+        case MV_BF16: launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, done, s); break;
+        default: launch_gemv_t<MV_FP8_E4M3>(p, P->L, y32, zpart, z, tt, done, s); break;
+    }
+    if (ev) cudaEventRecord(ev[1], s);
+    switch (p.dt) {
+        case MV_F32: launch_gemv_n<MV_F32>(p, P->L, z, P->row_scale, gpart, gy, tn, done, s); break;
+        case MV_BF16: launch_gemv_n<MV_BF16>(p, P->L, z, P->row_scale, gpart, gy, tn, done, s); break;
+        default: launch_gemv_n<MV_FP8_E4M3>(p, P->L, z, P->row_scale, gpart, gy, tn, done, s); break;
+    }
+    if (ev) cudaEventRecord(ev[2], s);
+    launch_step(p, P, O, ws, s);
+    if (ev) cudaEventRecord(ev[3], s);
+}
+
+// Process-wide pool of timing events, reused so cached graphs stay valid.
+static std::mutex g_ev_mu;
+static std::vector<cudaEvent_t> g_events;
+static int timing_events(int count, const cudaEvent_t **out) {
+    std::lock_guard<std::mutex> lock(g_ev_mu);
+    if ((int)g_events.size() < count) {
+        while ((int)g_events.size() < count) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return MV_ERR_CUDA;
+            g_events.push_back(e);
+        }
+    }
+    *out = g_events.data();
+    return MV_OK;
+}
+
+// One cached graph per distinct (problem, options, workspace) triple.
+struct GraphKey {
+    const void *L, *mu, *rs, *ws;
+    int64_t n, T, ld;
+    int dt, mode, kkt_every, max_iter, chunk;
+    double R, gamma, eps;
+    const void *ev;
+    bool operator==(const GraphKey &o) const {
+        return L == o.L && mu == o.mu && rs == o.rs && ws == o.ws && n == o.n && T == o.T && ld == o.ld &&
+               dt == o.dt && mode == o.mode && kkt_every == o.kkt_every && max_iter == o.max_iter &&
+               chunk == o.chunk && R == o.R && gamma == o.gamma && eps == o.eps && ev == o.ev;
+    }
+};
+struct GraphKeyHash {
+    size_t operator()(const GraphKey &k) const {
+        size_t h = (size_t)k.L ^ ((size_t)k.ws << 1) ^ ((size_t)k.n * 1315423911u) ^ ((size_t)k.T << 7);
+        h ^= std::hash<double>()(k.R) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+        return h;
+    }
+};
+static std::mutex g_graph_mu;
+static std::unordered_map<GraphKey, cudaGraphExec_t, GraphKeyHash> g_graphs;
+
+static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
+                           const cudaEvent_t *ev, cudaGraphExec_t *out) {
+    GraphKey key{P->L, P->mu, P->row_scale, ws, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
+                 O->max_iter, chunk, P->R_target, P->gamma, O->eps, (const void *)ev};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(g_graph_mu);
+    auto it = g_graphs.find(key);
+    if (it != g_graphs.end()) {
+        *out = it->second;
+        return MV_OK;
+    }
+    cudaStream_t cs;
+    MV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t graph;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return MV_ERR_CUDA;
+    }
+    for (int c = 0; c < chunk; ++c) launch_iteration(p, P, O, ws, cs, ev ? ev + 3 * c : nullptr);
+    cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return MV_ERR_CUDA;
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return MV_ERR_CUDA;
+    if (g_graphs.size() > 32) {
+        for (auto &kv : g_graphs) cudaGraphExecDestroy(kv.second);
+        g_graphs.clear();
+    }
+    g_graphs.emplace(key, exec);
+    *out = exec;
+    (void)dev;
+    return MV_OK;
+}
+
+}  // namespace mv
+
+using namespace mv;
+
+extern "C" {
+
+void mv_solve_opts_default(mv_solve_opts *o) {
+    if (!o) return;
+    o->max_iter = 10000;
+    o->kkt_every = 5;
+    o->power_iters = 50;
+    o->warm_start = 0;
+    o->eps = 1e-6;
+    o->power_safety = 1e-3;
+    o->alpha = 0.0;
+    o->use_graph = 1;
+    o->timing = 0;
+}
+
+size_t mv_npga_workspace_size(const mv_problem *P) {
+    if (validate_problem(P) != MV_OK) return 0;
+    return make_plan(P->dtype, P->n, P->T, P->ld).total;
+}
+
+int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g, void *d_ws, size_t ws_bytes,
+                mv_stream_t stream) {
+    MV_TRY(validate_problem(P));
+    if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    MV_TRY(check_ws(d_ws, ws_bytes, p.total));
+    MV_TRY(set_kernel_attrs());
+    cudaStream_t s = (cudaStream_t)stream;
+    float *y32 = at<float>(d_ws, p.o_y32);
+    double *lz = at<double>(d_ws, p.o_gy);
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(d_y, rs, y32, p.n);
+    gemv_pair(p, P, y32, d_ws, nullptr, lz, s);
+    grad_finish_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(lz, d_y, P->gamma, d_g, p.n);
+    if (d_z) MV_CUDA_TRY(cudaMemcpyAsync(d_z, at<float>(d_ws, p.o_z), 4 * (size_t)p.T, cudaMemcpyDeviceToDevice, s));
+    MV_CUDA_TRY(cudaGetLastError());
+    return MV_OK;
+}
+
+int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_inout, mv_solve_info *h_info,
+                  void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    MV_TRY(validate_problem(P));
+    if (d_x_inout == nullptr || h_info == nullptr) return MV_ERR_INVALID_ARG;
+    mv_solve_opts O;
+    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
+    if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    MV_TRY(check_ws(d_ws, ws_bytes, p.total));
+    MV_TRY(set_kernel_attrs());
+    cudaStream_t s = (cudaStream_t)stream;
+    SolveState *st = at<SolveState>(d_ws, p.o_state);
+    float *y32 = at<float>(d_ws, p.o_y32);
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    *h_info = mv_solve_info{};
+
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
+    setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
+    // Power method for ||L_eff||_2^2 (skipped when the step is given).
+    if (!(O.alpha > 0.0)) {
+        for (int it = 0; it < O.power_iters; ++it) {
+            gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s);
+            power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<double>(d_ws, p.o_gy), rs, y32, p.n);
+        }
+        gemv_t_only(p, P, y32, d_ws, s);
+    }
+    step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0) ? 0 : p.T, P->gamma,
+                                                O.power_safety, O.alpha);
+    init_x_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, O.warm_start ? d_x_inout : nullptr, at<double>(d_ws, p.o_v),
+                                             at<double>(d_ws, p.o_x), at<double>(d_ws, p.o_y), y32, rs, p.n,
+                                             P->R_target, P->mode);
+    MV_CUDA_TRY(cudaGetLastError());
+
+    const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
+    int launches = 4 + (O.alpha > 0.0 ? 0 : 3 * O.power_iters + 1);
+    const cudaEvent_t *ev = nullptr;
+    if (O.timing) MV_TRY(timing_events(3 * chunk + 1, &ev));
+    cudaGraphExec_t exec = nullptr;
+    if (O.use_graph) MV_TRY(get_chunk_graph(p, P, &O, d_ws, chunk, ev, &exec));
+    // max_iter + 1 iterations may run: the last one only evaluates the KKT residual.
+    const int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
+    SolveState hs{};
+    int k_prev = 0, timed = 0;
+    double t_t = 0.0, t_n = 0.0, t_s = 0.0;
+    for (int64_t c = 0; c < max_chunks; ++c) {
+        if (exec) {
+            MV_CUDA_TRY(cudaGraphLaunch(exec, s));
+        } else {
+            for (int i = 0; i < chunk; ++i) launch_iteration(p, P, &O, d_ws, s, ev ? ev + 3 * i : nullptr);
+            MV_CUDA_TRY(cudaGetLastError());
+        }
+        launches += 3 * chunk;
+        MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MV_CUDA_TRY(cudaStreamSynchronize(s));
+        if (ev) {
+            // Iterations that did real work in this chunk: the completed steps
+            // plus, on the chunk that converged, the final checking iteration.
+            int pairs = hs.k - k_prev + (hs.done ? 1 : 0);
+            pairs = pairs < 0 ? 0 : (pairs > chunk ? chunk : pairs);
+            for (int i = 0; i < pairs; ++i) {
+                float a = 0.f, b = 0.f, d = 0.f;
+                MV_CUDA_TRY(cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]));
+                MV_CUDA_TRY(cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]));
+                MV_CUDA_TRY(cudaEventElapsedTime(&d, ev[3 * i + 2], ev[3 * i + 3]));
+                t_t += a;
+                t_n += b;
+                t_s += d;
+            }
+            timed += pairs;
+        }
+        k_prev = hs.k;
+        if (hs.done) break;
+    }
+    launches += 3;
+    // Objective of the returned iterate: one more pass z = L^T x.
+    to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(at<double>(d_ws, p.o_x), rs, y32, p.n);
+    gemv_t_only(p, P, y32, d_ws, s);
+    objective_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), p.T, at<double>(d_ws, p.o_x), p.n,
+                                                P->gamma);
+    MV_CUDA_TRY(cudaMemcpyAsync(d_x_inout, at<double>(d_ws, p.o_x), 8 * (size_t)p.n, cudaMemcpyDeviceToDevice, s));
+    MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
+    MV_CUDA_TRY(cudaGetLastError());
+    h_info->iterations = hs.k;
+    h_info->status = hs.done ? hs.status : MV_ERR_NOT_CONVERGED;
+    h_info->converged = hs.converged;
+    h_info->proj_failures = hs.proj_fail;
+    h_info->kkt = hs.kkt;
+    h_info->objective = hs.objective;
+    h_info->alpha = hs.alpha;
+    h_info->lambda_hat = hs.lambda_hat;
+    h_info->nu = hs.nu;
+    h_info->launches = launches;
+    h_info->timed_pairs = timed;
+    h_info->t_gemv_t_ms = t_t;
+    h_info->t_gemv_n_ms = t_n;
+    h_info->t_step_ms = t_s;
+    return h_info->status;
+}
+
+}  // extern "C"

@@ -1,0 +1,261 @@
+"""ctypes binding of libmv (include/mv.h): argument marshalling only.
+
+Every function here allocates its outputs and workspace with PyTorch on the
+current CUDA device, passes raw device pointers and the current stream to
+the C ABI, and raises ``MvError`` on a non-OK status.  No arithmetic of the
+method happens in Python.  If ``libmv.so`` has not been built the first call
+raises ``RuntimeError`` -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmv.so")
+
+MV_OK, MV_ERR_INVALID_ARG, MV_ERR_INFEASIBLE, MV_ERR_NOT_CONVERGED = 0, 1, 2, 3
+MV_ERR_TIMEOUT, MV_ERR_NUMERIC, MV_ERR_CUDA, MV_ERR_UNSUPPORTED, MV_ERR_WORKSPACE = 4, 5, 6, 7, 8
+MV_F32, MV_BF16, MV_FP8_E4M3 = 0, 1, 2
+MV_RETURN_GE, MV_RETURN_EQ = 0, 1
+
+DTYPES = {"f32": MV_F32, "bf16": MV_BF16, "fp8": MV_FP8_E4M3}
+_ESIZE = {MV_F32: 4, MV_BF16: 2, MV_FP8_E4M3: 1}
+_TORCH = {MV_F32: torch.float32, MV_BF16: torch.bfloat16, MV_FP8_E4M3: torch.uint8}
+MODES = {"ge": MV_RETURN_GE, "eq": MV_RETURN_EQ}
+
+# Every symbol include/mv.h declares (checked by the CPU test suite).
+EXPORTS = [
+    "mv_status_string", "mv_version", "mv_center_workspace_size", "mv_center_factor", "mv_project",
+    "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
+]
+
+
+class MvError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        extra = ""
+        if status == MV_ERR_CUDA:
+            extra = " -- " + lib().mv_last_error().decode()
+        super().__init__(f"{where}: {status_string(status)} (status {status}){extra}")
+
+
+class ProjInfo(C.Structure):
+    _fields_ = [("nu", C.c_double), ("tau", C.c_double), ("residual", C.c_double),
+                ("support", C.c_int32), ("status", C.c_int32), ("steps", C.c_int32),
+                ("active", C.c_int32)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("L", C.c_void_p), ("dtype", C.c_int32), ("mode", C.c_int32),
+                ("row_scale", C.c_void_p), ("n", C.c_int64), ("T", C.c_int64), ("ld", C.c_int64),
+                ("gamma", C.c_double), ("mu", C.c_void_p), ("R_target", C.c_double),
+                ("power_start", C.c_void_p)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("max_iter", C.c_int32), ("kkt_every", C.c_int32), ("power_iters", C.c_int32),
+                ("warm_start", C.c_int32), ("eps", C.c_double), ("power_safety", C.c_double),
+                ("alpha", C.c_double), ("use_graph", C.c_int32), ("timing", C.c_int32)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("status", C.c_int32), ("converged", C.c_int32),
+                ("proj_failures", C.c_int32), ("kkt", C.c_double), ("objective", C.c_double),
+                ("alpha", C.c_double), ("lambda_hat", C.c_double), ("nu", C.c_double),
+                ("launches", C.c_int32), ("timed_pairs", C.c_int32), ("t_gemv_t_ms", C.c_double),
+                ("t_gemv_n_ms", C.c_double), ("t_step_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load libmv.so once; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmv.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, dbl, sz = C.c_void_p, C.c_int64, C.c_int, C.c_double, C.c_size_t
+        L.mv_status_string.restype = C.c_char_p
+        L.mv_status_string.argtypes = [i32]
+        L.mv_version.restype = C.c_char_p
+        L.mv_last_error.restype = C.c_char_p
+        L.mv_center_workspace_size.restype = sz
+        L.mv_center_workspace_size.argtypes = [i64, i64]
+        L.mv_center_factor.restype = i32
+        L.mv_center_factor.argtypes = [vp, i64, i64, i64, i32, vp, i64, vp, vp, vp, vp, sz, vp]
+        L.mv_project.restype = i32
+        L.mv_project.argtypes = [vp, vp, vp, i64, i64, i32, vp, vp, vp]
+        L.mv_solve_opts_default.restype = None
+        L.mv_solve_opts_default.argtypes = [C.POINTER(SolveOpts)]
+        L.mv_npga_workspace_size.restype = sz
+        L.mv_npga_workspace_size.argtypes = [C.POINTER(Problem)]
+        L.mv_npga_solve.restype = i32
+        L.mv_npga_solve.argtypes = [C.POINTER(Problem), C.POINTER(SolveOpts), vp, C.POINTER(SolveInfo),
+                                    vp, sz, vp]
+        L.mv_gradient.restype = i32
+        L.mv_gradient.argtypes = [C.POINTER(Problem), vp, vp, vp, vp, sz, vp]
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().mv_status_string(int(status)).decode()
+
+
+def version() -> str:
+    return lib().mv_version().decode()
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(status, where, allow=()):
+    if status != MV_OK and status not in allow:
+        raise MvError(status, where)
+    return status
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator returns 512-byte aligned blocks.
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def padded_ld(T: int, dtype: int) -> int:
+    """Smallest leading dimension >= T whose row pitch is a multiple of 16 bytes."""
+    v = 16 // _ESIZE[dtype]
+    return (T + v - 1) // v * v
+
+
+# ------------------------------------------------------------------ calls
+def center_factor(R: torch.Tensor, out_dtype: str = "f32", ld: int | None = None):
+    """mu, L, trace(Sigma) from an n x T FP32 return panel on the GPU (Sec. 2.1).
+
+    Returns (L, row_scale, mu, trace) where L is n x ld (columns T.. are 0),
+    row_scale is an n FP32 tensor for FP8 (else None), mu is FP64 n and trace
+    an FP64 scalar tensor.
+    """
+    assert R.is_cuda and R.dtype == torch.float32 and R.dim() == 2
+    dt = DTYPES[out_dtype]
+    n, T = R.shape
+    ldR = R.stride(0)
+    if R.stride(1) != 1:
+        raise ValueError("R must be row-major")
+    ld = padded_ld(T, dt) if ld is None else int(ld)
+    dev = R.device
+    L = torch.empty((n, ld), dtype=_TORCH[dt], device=dev)
+    rs = torch.empty(n, dtype=torch.float32, device=dev) if dt == MV_FP8_E4M3 else None
+    mu = torch.empty(n, dtype=torch.float64, device=dev)
+    tr = torch.empty(1, dtype=torch.float64, device=dev)
+    wsz = lib().mv_center_workspace_size(n, T)
+    ws = _workspace(wsz, dev)
+    _check(lib().mv_center_factor(_ptr(R), n, T, ldR, dt, _ptr(L), ld, _ptr(rs), _ptr(mu), _ptr(tr),
+                                  _ptr(ws), ws.numel(), _stream()), "mv_center_factor")
+    return L, rs, mu, tr
+
+
+def project(v: torch.Tensor, mu: torch.Tensor, R_target, mode: str = "ge"):
+    """Exact projection onto F of each row of v (batch x n or n), FP64."""
+    squeeze = v.dim() == 1
+    v2 = v.reshape(1, -1) if squeeze else v
+    assert v2.is_cuda and v2.dtype == torch.float64 and v2.is_contiguous()
+    batch, n = v2.shape
+    Rt = torch.as_tensor(R_target, dtype=torch.float64, device=v.device).reshape(-1)
+    if Rt.numel() == 1 and batch > 1:
+        Rt = Rt.expand(batch).contiguous()
+    x = torch.empty_like(v2)
+    info = torch.zeros(batch * C.sizeof(ProjInfo), dtype=torch.uint8, device=v.device)
+    _check(lib().mv_project(_ptr(v2), _ptr(mu.contiguous()), _ptr(Rt), n, batch, MODES[mode], _ptr(x),
+                            _ptr(info), _stream()), "mv_project")
+    raw = info.cpu().numpy().tobytes()
+    infos = [ProjInfo.from_buffer_copy(raw[i * C.sizeof(ProjInfo):(i + 1) * C.sizeof(ProjInfo)])
+             for i in range(batch)]
+    out = [{k: getattr(p, k) for k, _ in ProjInfo._fields_} for p in infos]
+    return (x[0], out[0]) if squeeze else (x, out)
+
+
+def make_problem(L: torch.Tensor, mu: torch.Tensor, R_target: float, T: int, gamma: float = 0.0,
+                 dtype: str = "f32", row_scale: torch.Tensor | None = None, mode: str = "ge",
+                 power_start: torch.Tensor | None = None) -> Problem:
+    assert L.is_cuda and L.dim() == 2 and L.stride(1) == 1
+    p = Problem()
+    p.L = L.data_ptr()
+    p.dtype = DTYPES[dtype]
+    p.mode = MODES[mode]
+    p.row_scale = None if row_scale is None else row_scale.data_ptr()
+    p.n, p.T, p.ld = L.shape[0], int(T), L.stride(0)
+    p.gamma = float(gamma)
+    p.mu = mu.data_ptr()
+    p.R_target = float(R_target)
+    p.power_start = None if power_start is None else power_start.data_ptr()
+    return p
+
+
+def solve_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().mv_solve_opts_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """Holds a problem, its workspace and the device solution buffer.
+
+    ``solve()`` calls mv_npga_solve; reusing one Solver reuses the cached
+    CUDA graph and workspace, which is what a benchmark loop wants.
+    """
+
+    def __init__(self, L, mu, R_target, T, gamma=0.0, dtype="f32", row_scale=None, mode="ge",
+                 power_start=None, **opts):
+        self._keep = (L, mu, row_scale, power_start)
+        self.problem = make_problem(L, mu, R_target, T, gamma, dtype, row_scale, mode, power_start)
+        self.opts = solve_opts(**opts)
+        self.ws_bytes = lib().mv_npga_workspace_size(C.byref(self.problem))
+        if self.ws_bytes == 0:
+            raise MvError(MV_ERR_INVALID_ARG, "mv_npga_workspace_size")
+        self.ws = _workspace(self.ws_bytes, L.device)
+        self.x = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
+
+    def solve(self, x0: torch.Tensor | None = None, allow=(MV_ERR_NOT_CONVERGED,)):
+        if x0 is not None:
+            self.x.copy_(x0)
+            self.opts.warm_start = 1
+        info = SolveInfo()
+        st = lib().mv_npga_solve(C.byref(self.problem), C.byref(self.opts), _ptr(self.x), C.byref(info),
+                                 _ptr(self.ws), self.ws.numel(), _stream())
+        _check(st, "mv_npga_solve", allow)
+        return self.x, info.as_dict()
+
+    def gradient(self, y: torch.Tensor):
+        z = torch.empty(self.problem.T, dtype=torch.float32, device=y.device)
+        g = torch.empty_like(y)
+        _check(lib().mv_gradient(C.byref(self.problem), _ptr(y), _ptr(z), _ptr(g), _ptr(self.ws),
+                                 self.ws.numel(), _stream()), "mv_gradient")
+        return z, g
+
+
+def npga_solve(L, mu, R_target, T, gamma=0.0, dtype="f32", row_scale=None, mode="ge", x0=None,
+               power_start=None, **opts):
+    """One-shot NPGA solve; returns (x, info dict)."""
+    s = Solver(L, mu, R_target, T, gamma, dtype, row_scale, mode, power_start, **opts)
+    return s.solve(x0)
+
+
+def gradient(L, y, T, gamma=0.0, dtype="f32", row_scale=None):
+    """(z, g) with z = L^T y (FP32) and g = 2 L z + 2 gamma y (FP64)."""
+    mu = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
+    s = Solver(L, mu, 0.0, T, gamma, dtype, row_scale)
+    return s.gradient(y)

@@ -1,0 +1,124 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every
+symbol include/mv.h declares, and rejects bad arguments on the host before
+anything is launched.  No GPU is touched."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mv.h")
+
+
+@pytest.fixture(scope="module")
+def mvmod():
+    from paper_2604_02917_gb300 import build, mv
+    if not os.path.exists(mv.LIB_PATH):
+        build.build()
+    mv.lib()
+    return mv
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mv_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(mvmod):
+    lib = mvmod.lib()
+    names = declared_functions()
+    assert "mv_npga_solve" in names and "mv_project" in names and "mv_center_factor" in names
+    for name in names:
+        assert hasattr(lib, name), f"{name} declared in mv.h but not exported"
+    assert set(names) <= set(mvmod.EXPORTS) | set(names)
+    for name in mvmod.EXPORTS:
+        assert name in names, f"binding lists {name} that mv.h does not declare"
+
+
+def test_status_strings_and_version(mvmod):
+    assert mvmod.version().startswith("mv ")
+    for s in range(0, 9):
+        assert mvmod.status_string(s).startswith("MV_")
+    assert "unknown" in mvmod.status_string(99)
+
+
+def _c_layout(tmp_path):
+    """sizeof/offsetof of the mv.h structs as the C compiler lays them out."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    fields = {
+        "mv_proj_info": ["nu", "tau", "residual", "support", "status", "steps", "active"],
+        "mv_problem": ["L", "dtype", "mode", "row_scale", "n", "T", "ld", "gamma", "mu", "R_target",
+                       "power_start"],
+        "mv_solve_opts": ["max_iter", "kkt_every", "power_iters", "warm_start", "eps", "power_safety",
+                          "alpha", "use_graph", "timing"],
+        "mv_solve_info": ["iterations", "status", "converged", "proj_failures", "kkt", "objective",
+                          "alpha", "lambda_hat", "nu", "launches", "timed_pairs", "t_gemv_t_ms",
+                          "t_gemv_n_ms", "t_step_ms"],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mv.h"', "int main(void){"]
+    for st, fs in fields.items():
+        lines.append(f'printf("{st} size %zu\\n", sizeof({st}));')
+        for f in fs:
+            lines.append(f'printf("{st} {f} %zu\\n", offsetof({st}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    return {tuple(l.split()[:2]): int(l.split()[2]) for l in out.strip().splitlines()}
+
+
+def test_struct_layouts_match_header(mvmod, tmp_path):
+    lay = _c_layout(tmp_path)
+    pairs = {"mv_proj_info": mvmod.ProjInfo, "mv_problem": mvmod.Problem,
+             "mv_solve_opts": mvmod.SolveOpts, "mv_solve_info": mvmod.SolveInfo}
+    for cname, py in pairs.items():
+        assert C.sizeof(py) == lay[(cname, "size")], cname
+        for f, _ in py._fields_:
+            assert getattr(py, f).offset == lay[(cname, f)], (cname, f)
+    o = mvmod.solve_opts()
+    assert o.max_iter == 10000 and o.kkt_every == 5 and o.power_iters == 50
+    assert o.eps == 1e-6 and o.power_safety == 1e-3 and o.use_graph == 1
+
+
+def test_host_side_argument_errors(mvmod):
+    lib = mvmod.lib()
+    # mv_project with null pointers / bad sizes: rejected before any launch.
+    assert lib.mv_project(None, None, None, 10, 1, 0, None, None, None) == mvmod.MV_ERR_INVALID_ARG
+    fake = C.c_void_p(256)
+    assert lib.mv_project(fake, fake, fake, 0, 1, 0, fake, fake, None) == mvmod.MV_ERR_INVALID_ARG
+    assert lib.mv_project(fake, fake, fake, 70000, 1, 0, fake, fake, None) == mvmod.MV_ERR_INVALID_ARG
+    assert lib.mv_project(fake, fake, fake, 10, 1, 7, fake, fake, None) == mvmod.MV_ERR_INVALID_ARG
+    # Problem validation: misaligned pitch, bad dtype, missing FP8 scales.
+    p = mvmod.Problem()
+    p.L, p.mu, p.n, p.T, p.ld, p.dtype = 4096, 4096, 10, 7, 7, mvmod.MV_F32
+    assert lib.mv_npga_workspace_size(C.byref(p)) == 0          # ld*4 not a multiple of 16
+    p.ld = 8
+    assert lib.mv_npga_workspace_size(C.byref(p)) > 0
+    p.dtype = 9
+    assert lib.mv_npga_workspace_size(C.byref(p)) == 0
+    p.dtype = mvmod.MV_FP8_E4M3
+    p.ld = 16
+    assert lib.mv_npga_workspace_size(C.byref(p)) == 0          # FP8 needs row scales
+    info = mvmod.SolveInfo()
+    p.dtype = mvmod.MV_F32
+    st = lib.mv_npga_solve(C.byref(p), None, fake, C.byref(info), None, 0, None)
+    assert st == mvmod.MV_ERR_WORKSPACE
+    assert lib.mv_center_factor(None, 3, 4, 4, 0, None, 4, None, None, None, None, 0, None) == \
+        mvmod.MV_ERR_INVALID_ARG
+    assert lib.mv_center_factor(fake, 3, 1, 4, 0, fake, 4, None, fake, fake, fake, 1024, None) == \
+        mvmod.MV_ERR_INVALID_ARG                                   # T < 2
+
+
+def test_padded_ld(mvmod):
+    assert mvmod.padded_ld(48374, mvmod.MV_F32) == 48376
+    assert mvmod.padded_ld(48374, mvmod.MV_BF16) == 48376
+    assert mvmod.padded_ld(48374, mvmod.MV_FP8_E4M3) == 48384
+    assert mvmod.padded_ld(1000, mvmod.MV_F32) == 1000
