@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
     ap.add_argument("--config", default="full", choices=["full", "small"])
     ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--shape", default=None, help="n,T override (profiling runs on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -62,8 +63,11 @@ def dist_env():
 def workload(args, rank):
     from synth import CFG_FULL, CFG_SMALL
     base = CFG_FULL if args.config == "full" else CFG_SMALL
+    n, T = base.n, base.T
+    if args.shape:
+        n, T = (int(v) for v in args.shape.split(","))
     # each rank solves its own independent problem (weak scaling)
-    return base.scaled(base.n, base.T, seed=base.seed + rank)
+    return base.scaled(n, T, seed=base.seed + rank)
 
 
 def peaks():
@@ -306,7 +310,7 @@ def main():
         del R_buf, R_pin
 
     cb = None
-    if rank == 0 and world == 1 and not args.no_cpu and args.config == "full":
+    if rank == 0 and world == 1 and not args.no_cpu:
         iters = int(np.median([i["iterations"] for i in infos]))
         del L
         torch.cuda.empty_cache()

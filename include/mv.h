@@ -114,7 +114,8 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR,
  *  d_info     [out] batch mv_proj_info (device memory).  info.status is
  *                   MV_OK, MV_ERR_INFEASIBLE (x filled with NaN) or
  *                   MV_ERR_NOT_CONVERGED (step budget hit; best x kept).
- *  Needs no workspace.  1 <= n <= 65536.  Asynchronous.
+ *  Needs no workspace.  1 <= n <= 32768, batch <= 65535.  One cluster of up to
+ *  16 thread blocks per problem.  Asynchronous.
  * ------------------------------------------------------------------------ */
 typedef struct {
     double nu;         /* multiplier of the return row (0 when inactive)      */
@@ -151,7 +152,7 @@ typedef struct {
     int32_t dtype;            /* mv_dtype                                                */
     int32_t mode;             /* mv_return_mode                                          */
     const float *row_scale;   /* d: n FP32 row scales (FP8 only, else NULL)              */
-    int64_t n, T, ld;
+    int64_t n, T, ld;         /* 1 <= n <= 32768 assets, T >= 1 periods, ld >= T         */
     double gamma;             /* ridge (0 for the full and sketched models)              */
     const double *mu;         /* d: n FP64 expected returns                              */
     double R_target;          /* target return                                           */
@@ -167,7 +168,8 @@ typedef struct {
     double power_safety;      /* lambda_hat is multiplied by (1 + this); default 1e-3    */
     double alpha;             /* > 0: fixed step override; <= 0: from the power method   */
     int32_t use_graph;        /* 1 (default): replay iterations as a CUDA graph          */
-    int32_t timing;           /* 1: time every gemv launch of the loop with CUDA events  */
+    int32_t timing;           /* 1: time every loop launch with CUDA events (kernels are
+                                 then issued from the host instead of a graph)           */
 } mv_solve_opts;
 
 typedef struct {
@@ -185,6 +187,8 @@ typedef struct {
     double t_gemv_t_ms;       /* summed device time of those gemv_t launches             */
     double t_gemv_n_ms;       /* summed device time of those gemv_n launches             */
     double t_step_ms;         /* summed device time of those step (projection) launches  */
+    int32_t proj_steps;       /* block-wide reductions spent by all projections          */
+    int32_t reserved;
 } mv_solve_info;
 
 void mv_solve_opts_default(mv_solve_opts *opts);

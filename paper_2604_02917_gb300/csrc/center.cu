@@ -106,6 +106,7 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int ou
     if (out_dtype == MV_FP8_E4M3 && d_row_scale == nullptr) return MV_ERR_INVALID_ARG;
     const size_t need = mv_center_workspace_size(n, T);
     if (d_ws == nullptr || ws_bytes < need || ((uintptr_t)d_ws) % 256 != 0) return MV_ERR_WORKSPACE;
+    (void)cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
     double *rowsq = reinterpret_cast<double *>(d_ws);
     switch (out_dtype) {

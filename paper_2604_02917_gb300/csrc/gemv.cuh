@@ -35,7 +35,7 @@ constexpr int kMaxRowsPerSplit = 2048;
 template <int DT>
 __global__ void __launch_bounds__(kGemvThreads)
 gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ y32,
-              float *__restrict__ zpart, float *__restrict__ z, unsigned *__restrict__ tickets,
+              float *__restrict__ zpart, int64_t zstride, float *__restrict__ z, unsigned *__restrict__ tickets,
               int rows_per_split, const volatile int *done) {
     using S = Store<DT>;
     constexpr int VEC = S::VEC;
@@ -90,8 +90,14 @@ gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float 
         }
     }
 
-    float *zp = zpart + (int64_t)split * T;
-    if (col < T) {
+    // Partial sums of this split; rows of zpart are 64-byte aligned (zstride).
+    float *zp = zpart + (int64_t)split * zstride;
+    const bool full = (col + VEC <= T);
+    if (full) {
+#pragma unroll
+        for (int e = 0; e < VEC; e += 4)
+            *reinterpret_cast<float4 *>(zp + col + e) = make_float4(acc[e], acc[e + 1], acc[e + 2], acc[e + 3]);
+    } else if (col < T) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e)
             if (col + e < T) zp[col + e] = acc[e];
@@ -105,14 +111,51 @@ gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float 
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (col < T) {
-        const int splits = gridDim.y;
+    // Last block of the strip: add the splits in fixed order, 4 splits of
+    // 16-byte loads in flight at a time.
+    const int splits = gridDim.y;
+    if (full) {
+        float sacc[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) sacc[e] = 0.f;
+        int sp = 0;
+        for (; sp + 4 <= splits; sp += 4) {
+            float4 q[4][VEC / 4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int e4 = 0; e4 < VEC / 4; ++e4)
+                    q[u][e4] = __ldcg(reinterpret_cast<const float4 *>(zpart + (int64_t)(sp + u) * zstride + col) + e4);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int e4 = 0; e4 < VEC / 4; ++e4) {
+                    sacc[4 * e4 + 0] += q[u][e4].x;
+                    sacc[4 * e4 + 1] += q[u][e4].y;
+                    sacc[4 * e4 + 2] += q[u][e4].z;
+                    sacc[4 * e4 + 3] += q[u][e4].w;
+                }
+        }
+        for (; sp < splits; ++sp) {
+#pragma unroll
+            for (int e4 = 0; e4 < VEC / 4; ++e4) {
+                const float4 q = __ldcg(reinterpret_cast<const float4 *>(zpart + (int64_t)sp * zstride + col) + e4);
+                sacc[4 * e4 + 0] += q.x;
+                sacc[4 * e4 + 1] += q.y;
+                sacc[4 * e4 + 2] += q.z;
+                sacc[4 * e4 + 3] += q.w;
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < VEC; e += 4)
+            *reinterpret_cast<float4 *>(z + col + e) = make_float4(sacc[e], sacc[e + 1], sacc[e + 2], sacc[e + 3]);
+    } else if (col < T) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             if (col + e < T) {
-                float s = 0.f;
-                for (int sp = 0; sp < splits; ++sp) s += __ldcg(zpart + (int64_t)sp * T + col + e);
-                z[col + e] = s;
+                float sm = 0.f;
+                for (int sp = 0; sp < splits; ++sp) sm += __ldcg(zpart + (int64_t)sp * zstride + col + e);
+                z[col + e] = sm;
             }
         }
     }
@@ -123,7 +166,7 @@ template <int DT, int RW>
 __global__ void __launch_bounds__(kGemvThreads)
 gemv_n_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ z,
               const float *__restrict__ row_scale, float *__restrict__ gpart, double *__restrict__ g,
-              unsigned *__restrict__ tickets, int cols_per_split, const volatile int *done) {
+              float *__restrict__ g32, unsigned *__restrict__ tickets, int cols_per_split, const volatile int *done) {
     using S = Store<DT>;
     constexpr int VEC = S::VEC;
     constexpr int ES = (int)sizeof(typename S::elem);
@@ -199,6 +242,7 @@ gemv_n_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float 
         for (int sp = 0; sp < splits; ++sp) s += (double)__ldcg(gpart + (int64_t)sp * n + r);
         if (row_scale != nullptr) s *= (double)row_scale[r];
         g[r] = s;
+        if (g32 != nullptr) g32[r] = (float)s;
     }
     if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
 }

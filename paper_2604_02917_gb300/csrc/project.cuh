@@ -1,189 +1,609 @@
-// Block-cooperative exact projection onto F = {mu^T x >= R, 1^T x = 1, x >= 0}
-// (Sec. 3.1, Eqs. simplex-tau, simplex-proj, projF-dualpath), FP64.
+// Cluster-cooperative exact projection onto F = {mu^T x >= R, 1^T x = 1, x >= 0}
+// (Sec. 3.1, Eqs. simplex-tau, simplex-proj, projF-dualpath).
 //
-// One thread block owns one problem.  Every step is one block-wide reduction
-// of five FP64 sums over a candidate support S = {i : v_i + nu mu_i > tau}:
-//     |S|, sum_S v, sum_S mu, sum_S mu v, sum_S mu^2.
-// From these the two scalar searches of the paper are driven:
-//
-//  * inner (simplex threshold, Eq. simplex-tau): h(tau) = sum max(w - tau, 0) - 1
-//    is convex, decreasing and piecewise linear in tau.  A Newton step from
-//    any tau lands at or left of the root, and from the left the iterates
-//    rise monotonically with nested supports, so the iteration ends exactly
-//    when |S| stops changing:  tau = (sum_S w - 1) / |S|.  This replaces the
-//    sort of the paper by a few reductions and yields the same threshold.
-//
-//  * outer (return multiplier, Eq. projF-dualpath): phi(nu) = mu^T x(nu) is
-//    continuous, nondecreasing and piecewise linear.  On the support S found
-//    at the current nu, the budget and return rows
+// Search (the same mathematics as the paper's scalar dual search):
+//  * inner -- the simplex threshold at fixed nu: h(tau) = sum max(w - tau, 0) - 1
+//    (w = v + nu mu) is convex, decreasing, piecewise linear.  A Newton step
+//    from any tau lands at or left of the root, and from the left the
+//    supports are nested, so the iteration ends exactly when |S| stops
+//    changing: tau = (sum_S w - 1)/|S|.  It replaces the paper's sort.
+//  * outer -- phi(nu) = mu^T x(nu) is continuous, nondecreasing, piecewise
+//    linear.  On the support S at the current nu the budget and return rows
 //        |S| tau - nu sum_S mu = sum_S v - 1
 //        sum_S mu tau - nu sum_S mu^2 = sum_S mu v - R
-//    give the exact (tau, nu) of that linear piece (a Newton step on phi).
-//    The iteration keeps a bracket psi(lo) < 0 <= psi(hi) with psi = phi - R,
-//    falls back to the paper's geometric expansion nu = 1, 2, 4, ... and to
-//    bisection when the Newton point leaves the bracket, and stops when the
-//    support at nu reproduces nu (the exact finish).  When psi(0) >= 0 the
-//    return row is inactive and the simplex projection is the answer.
+//    give the exact (tau, nu) of that piece (a Newton step on phi).  A
+//    bracket psi(lo) < 0 <= psi(hi), psi = phi - R, is kept; the paper's
+//    geometric expansion nu = 1, 2, 4, ... and bisection take over when the
+//    Newton point leaves it; the search stops when the support at nu
+//    reproduces nu (exact finish).  psi(0) >= 0 means the return row is
+//    inactive and the simplex projection is the answer.
 //
+// Arithmetic designed for GB300, whose FP64 rate is ~2 lane-ops/clk/SM:
+//  * every step is one reduction of |S|, sum_S v, sum_S mu, sum_S mu v,
+//    sum_S mu^2; the sums are EXACT 128-bit integer additions of fixed-point
+//    images of the FP64 values (62-bit magnitudes scaled by the largest
+//    element, converted with integer bit operations, so each image carries
+//    the full FP64 mantissa), so no FP64 add runs per element or in the
+//    reduction tree and the sums are at least as accurate as FP64 ones;
+//  * membership w_i > tau is decided in FP32 with a proven error margin;
+//    only elements inside the margin repeat the test in FP64 (same result as
+//    an FP64 evaluation of fma(nu, mu_i, v_i) > tau);
+//  * the n elements are split over a cluster of CL thread blocks (one SM
+//    each); block sums are exchanged through distributed shared memory and
+//    added in rank order by every block, so all blocks hold bit-identical
+//    sums and take identical decisions; the O(1) scalar FP64 logic runs on
+//    one thread per block.
 // The warm start (nu, tau of the previous call) only changes where the
 // search begins, never the point it returns: the projection is unique.
 #pragma once
+
+#include <cooperative_groups.h>
 
 #include "mv_internal.cuh"
 
 namespace mv {
 
+namespace cg = cooperative_groups;
+
+constexpr int kProjNT = 256;          // threads per block
+constexpr int kProjMaxCL = 16;        // largest cluster
+constexpr int kProjMaxLocal = 2048;   // elements per block (n <= 16 * 2048)
+constexpr int kProjMaxN = kProjMaxCL * kProjMaxLocal;
+constexpr int kFixBits = 62;          // fixed-point magnitude bound 2^62 (sums kept in 128 bits)
+
+// round(d * 2^s) with integer operations only; |d| 2^s must stay below 2^62.
+__device__ __forceinline__ long long to_fixed(double d, int s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e == 0) return 0;                                    // zero or subnormal
+    const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = e - 1075 + s;
+    long long r;
+    if (sh >= 0) {
+        r = (long long)(m << (sh > 9 ? 9 : sh));
+    } else if (sh > -64) {
+        r = (long long)((m + (1ull << (-sh - 1))) >> (-sh));
+    } else {
+        r = 0;
+    }
+    return (b >> 63) ? -r : r;
+}
+
+// Biased exponent field of |d| (0 for zero).
+__device__ __forceinline__ int exp_field(double d) {
+    return (int)(((unsigned long long)__double_as_longlong(d) >> 52) & 0x7ff);
+}
+
+// 2^-s as an exact double (0 below the normal range).
+__device__ __forceinline__ double pow2_neg(int s) {
+    const int e = 1023 - s;
+    if (e <= 0) return 0.0;
+    if (e >= 2047) return INFINITY;
+    return __longlong_as_double((long long)e << 52);
+}
+
+// Scale s such that every |q| whose exponent field is <= e satisfies |q| 2^s < 2^kFixBits.
+__host__ __device__ __forceinline__ int fixed_scale(int e) { return e == 0 ? 0 : kFixBits + 1022 - e; }
+
+// Signed 128-bit accumulator (two's complement, lo word unsigned).
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+__device__ __forceinline__ void add128(I128 &a, long long x) {
+    const unsigned long long nlo = a.lo + (unsigned long long)x;
+    a.hi += (x >> 63) + (nlo < a.lo ? 1 : 0);
+    a.lo = nlo;
+}
+__device__ __forceinline__ void add128(I128 &a, const I128 &b) {
+    const unsigned long long nlo = a.lo + b.lo;
+    a.hi += b.hi + (nlo < a.lo ? 1 : 0);
+    a.lo = nlo;
+}
+__device__ __forceinline__ double i128_to_double(const I128 &a) {
+    return (double)a.hi * 18446744073709551616.0 + (double)a.lo;
+}
+__device__ __forceinline__ I128 warp_sum_128(I128 v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        I128 w;
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        add128(v, w);
+    }
+    return v;
+}
 struct ProjSums {
     double cnt, sv, sm, smv, smm;
 };
 
 struct ProjOut {
     double nu, tau;
-    ProjSums s;
     int status;
     int steps;
 };
 
-template <int NT>
-struct Projector {
-    const double *V;    // n points (shared or global memory)
-    const double *MU;   // n expected returns
-    int n;
-    double *red;        // (NT/32 + 1) * 5 doubles of shared memory
-    int steps;
+// Shared-memory workspace of one block of the projector.
+struct ProjSmem {
+    I128 part[2][kProjMaxCL][6];        // DSMEM slots: [parity][source rank][sum]
+    double dpart[2][kProjMaxCL];
+    int emax[kProjMaxCL][4];
+    I128 wred[kProjNT / kWarp][6];
+    double wredd[kProjNT / kWarp];
+    int wmax[kProjNT / kWarp][4];
+    // broadcast of the scalar state (written by thread 0)
+    double nu, tau, dbcast, dmin, dmax;
+    double mpart[2][kProjMaxCL][2];
+    float nu32, tau32;
+    int done, status, steps;
+    int s_v, s_m, s_mv, s_mm;
+    double p_v, p_m, p_mv, p_mm;        // 2^-s of the four scales
+    int parity;
+};
 
-    __device__ __forceinline__ ProjSums support_sums(double nu, double tau) {
-        double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-        for (int i = threadIdx.x; i < n; i += NT) {
-            const double v = V[i], m = MU[i];
-            const double w = fma(nu, m, v);
-            if (w > tau) {
-                acc[0] += 1.0;
-                acc[1] += v;
-                acc[2] += m;
-                acc[3] = fma(m, v, acc[3]);
-                acc[4] = fma(m, m, acc[4]);
-            } else if (!(w == w)) {
-                acc[1] = NAN;                 // poison the sums: reported as MV_ERR_NUMERIC
+// Must run once per block before the first reduction (all threads).
+__device__ inline void proj_smem_init(ProjSmem *sh) {
+    if (threadIdx.x == 0) sh->parity = 0;
+    __syncthreads();
+}
+
+// Per-element arrays of the block's slice, in shared memory.
+struct ProjElems {
+    double *v, *mu;               // FP64 values
+    float *v32, *mu32;            // FP32 images for screening
+    long long *V, *M, *MV, *MM;   // fixed-point images
+    int n;                        // elements in this block's slice
+};
+
+__host__ __device__ inline size_t proj_elem_bytes(int n_local) {
+    return (size_t)n_local * (8 + 8 + 4 + 4 + 8 * 4) + 64;
+}
+
+__device__ inline ProjElems carve_elems(void *base, int n_local) {
+    ProjElems e;
+    char *p = reinterpret_cast<char *>(base);
+    e.v = reinterpret_cast<double *>(p);
+    p += 8 * (size_t)n_local;
+    e.mu = reinterpret_cast<double *>(p);
+    p += 8 * (size_t)n_local;
+    e.V = reinterpret_cast<long long *>(p);
+    p += 8 * (size_t)n_local;
+    e.M = reinterpret_cast<long long *>(p);
+    p += 8 * (size_t)n_local;
+    e.MV = reinterpret_cast<long long *>(p);
+    p += 8 * (size_t)n_local;
+    e.MM = reinterpret_cast<long long *>(p);
+    p += 8 * (size_t)n_local;
+    e.v32 = reinterpret_cast<float *>(p);
+    p += 4 * (size_t)n_local;
+    e.mu32 = reinterpret_cast<float *>(p);
+    e.n = n_local;
+    return e;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_max_i(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int CL>
+__device__ __forceinline__ void cluster_barrier() {
+    if constexpr (CL > 1) {
+        cg::this_cluster().sync();
+    } else {
+        __syncthreads();
+    }
+}
+
+template <int CL>
+__device__ __forceinline__ int cluster_rank() {
+    if constexpr (CL > 1) {
+        return (int)cg::this_cluster().block_rank();
+    } else {
+        return 0;
+    }
+}
+
+template <int CL>
+struct ClusterProj {
+    ProjSmem *sh;
+    ProjElems el;
+
+    // Block-then-cluster sum of 6 128-bit values; lane 0 of warp 0 of every
+    // block ends with the same totals in `out` (integer sums: exact, so the
+    // order of addition does not matter).  Warp 0 does the cross-warp and
+    // cross-block steps in parallel: lane k < 6 adds value k over the warps,
+    // lane r < CL stores the totals into block r, lane r then loads block r's
+    // slot and a shuffle tree adds them.
+    __device__ void reduce6(I128 (&a)[6], I128 (&out)[6]) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = warp_sum_128(a[k]);
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sh->wred[warp][k] = a[k];
+        }
+        __syncthreads();
+        const int par = sh->parity;
+        if (warp == 0) {
+            I128 t{0ull, 0ll};
+            if (lane < 6)
+                for (int w = 0; w < kProjNT / kWarp; ++w) add128(t, sh->wred[w][lane]);
+            const int me = cluster_rank<CL>();
+            I128 tk[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                tk[k].lo = __shfl_sync(0xffffffffu, t.lo, k);
+                tk[k].hi = __shfl_sync(0xffffffffu, t.hi, k);
+            }
+            if (lane < CL) {
+                I128 *dst;
+                if constexpr (CL > 1) {
+                    dst = cg::this_cluster().map_shared_rank(&sh->part[par][me][0], lane);
+                } else {
+                    dst = &sh->part[par][0][0];
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k) dst[k] = tk[k];
             }
         }
-        block_sum<5, NT>(acc, red);
-        ++steps;
-        return ProjSums{acc[0], acc[1], acc[2], acc[3], acc[4]};
-    }
-
-    // Newton on the simplex threshold at fixed nu.  tau may start anywhere
-    // (-inf gives the all-assets start).  Returns false if the budget ran out.
-    __device__ bool simplex_tau(double nu, double &tau, ProjSums &s, int budget) {
-        if (!(tau == tau)) tau = -INFINITY;
-        s = support_sums(nu, tau);
-        for (int it = 0; it < budget; ++it) {
-            if (s.cnt == 0.0) {          // tau >= max w: restart from the left
-                tau = -INFINITY;
-                s = support_sums(nu, tau);
-                continue;
+        cluster_barrier<CL>();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                I128 v = lane < CL ? sh->part[par][lane][k] : I128{0ull, 0ll};
+                out[k] = warp_sum_128(v);
             }
-            const double tn = (fma(nu, s.sm, s.sv) - 1.0) / s.cnt;
-            const ProjSums s2 = support_sums(nu, tn);
-            const bool same = (s2.cnt == s.cnt);
-            tau = tn;
-            s = s2;
-            if (same) return true;
+            if (lane == 0) sh->parity = par ^ 1;
         }
-        return false;
+        // The next exchange writes the other parity; the one after reuses this
+        // one only after another cluster barrier, so no reader is overtaken.
     }
 
-    // Full search.  mode: MV_RETURN_GE or MV_RETURN_EQ.
-    __device__ ProjOut solve(double R, int mode, double mu_min, double mu_max,
-                             double nu_hint, double tau_hint, int budget) {
-        ProjOut o;
-        o.steps = 0;
-        steps = 0;
-        o.status = MV_OK;
-        if (!(R <= mu_max) || (mode == MV_RETURN_EQ && !(R >= mu_min))) {
-            o.status = MV_ERR_INFEASIBLE;
-            o.nu = o.tau = NAN;
-            o.s = ProjSums{0, 0, 0, 0, 0};
-            return o;
+    // Cluster sum of one double per thread, added in a fixed order (every
+    // block gets the same value); result returned to all threads.
+    __device__ double reduce_double(double x) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        x = warp_sum(x);
+        if (lane == 0) sh->wredd[warp] = x;
+        __syncthreads();
+        const int par = sh->parity;
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kProjNT / kWarp; ++w) t += sh->wredd[w];
+            const int me = cluster_rank<CL>();
+            if constexpr (CL > 1) {
+                cg::cluster_group cl = cg::this_cluster();
+                for (int r = 0; r < CL; ++r) *cl.map_shared_rank(&sh->dpart[par][me], r) = t;
+            } else {
+                sh->dpart[par][0] = t;
+            }
         }
-        const double scaleR = fmax(fabs(R), fmax(fabs(mu_max), fabs(mu_min)));
+        cluster_barrier<CL>();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int r = 0; r < CL; ++r) t += sh->dpart[par][r];
+            sh->dbcast = t;
+            sh->parity = par ^ 1;
+        }
+        __syncthreads();
+        const double r = sh->dbcast;
+        __syncthreads();
+        return r;
+    }
+
+    // Cluster-wide min and max of one double per thread; result to all threads.
+    __device__ void reduce_minmax(double &mn, double &mx) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        mn = warp_min(mn);
+        mx = warp_max(mx);
+        if (lane == 0) {
+            sh->wredd[warp] = mn;
+            sh->wred[warp][0].hi = __double_as_longlong(mx);
+        }
+        __syncthreads();
+        const int par = sh->parity;
+        if (threadIdx.x == 0) {
+            double a = INFINITY, b = -INFINITY;
+            for (int w = 0; w < kProjNT / kWarp; ++w) {
+                a = fmin(a, sh->wredd[w]);
+                b = fmax(b, __longlong_as_double(sh->wred[w][0].hi));
+            }
+            const int me = cluster_rank<CL>();
+            if constexpr (CL > 1) {
+                cg::cluster_group cl = cg::this_cluster();
+                for (int r = 0; r < CL; ++r) {
+                    double *dst = cl.map_shared_rank(&sh->mpart[par][me][0], r);
+                    dst[0] = a;
+                    dst[1] = b;
+                }
+            } else {
+                sh->mpart[par][0][0] = a;
+                sh->mpart[par][0][1] = b;
+            }
+        }
+        cluster_barrier<CL>();
+        if (threadIdx.x == 0) {
+            double a = INFINITY, b = -INFINITY;
+            for (int r = 0; r < CL; ++r) {
+                a = fmin(a, sh->mpart[par][r][0]);
+                b = fmax(b, sh->mpart[par][r][1]);
+            }
+            sh->dmin = a;
+            sh->dmax = b;
+            sh->parity = par ^ 1;
+        }
+        __syncthreads();
+        mn = sh->dmin;
+        mx = sh->dmax;
+        __syncthreads();
+    }
+
+    // Cluster-wide maxima of the exponent fields of |v|, |mu|, |mu v|, mu^2,
+    // then the fixed-point images of the slice.  Expects el.v and el.mu set.
+    __device__ void prepare() {
+        int e[4] = {0, 0, 0, 0};
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            const double v = el.v[i], m = el.mu[i];
+            const double mv = m * v, mm = m * m;
+            e[0] = max(e[0], exp_field(v));
+            e[1] = max(e[1], exp_field(m));
+            e[2] = max(e[2], exp_field(mv));
+            e[3] = max(e[3], exp_field(mm));
+            el.MV[i] = __double_as_longlong(mv);   // converted in place below
+            el.MM[i] = __double_as_longlong(mm);
+            el.v32[i] = (float)v;
+            el.mu32[i] = (float)m;
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) e[k] = warp_max_i(e[k]);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) sh->wmax[warp][k] = e[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int t[4] = {0, 0, 0, 0};
+            for (int w = 0; w < kProjNT / kWarp; ++w)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) t[k] = max(t[k], sh->wmax[w][k]);
+            const int me = cluster_rank<CL>();
+            if constexpr (CL > 1) {
+                cg::cluster_group cl = cg::this_cluster();
+                for (int r = 0; r < CL; ++r) {
+                    int *dst = cl.map_shared_rank(&sh->emax[me][0], r);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) dst[k] = t[k];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) sh->emax[0][k] = t[k];
+            }
+        }
+        cluster_barrier<CL>();
+        if (threadIdx.x == 0) {
+            int t[4] = {0, 0, 0, 0};
+            for (int r = 0; r < CL; ++r)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) t[k] = max(t[k], sh->emax[r][k]);
+            sh->s_v = fixed_scale(t[0]);
+            sh->s_m = fixed_scale(t[1]);
+            sh->s_mv = fixed_scale(t[2]);
+            sh->s_mm = fixed_scale(t[3]);
+            // 2^-s as exact doubles (s in [-10, 2100]: build the bits, clamp to 0)
+            sh->p_v = pow2_neg(sh->s_v);
+            sh->p_m = pow2_neg(sh->s_m);
+            sh->p_mv = pow2_neg(sh->s_mv);
+            sh->p_mm = pow2_neg(sh->s_mm);
+        }
+        __syncthreads();
+        const int sv = sh->s_v, sm = sh->s_m, smv = sh->s_mv, smm = sh->s_mm;
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            el.V[i] = to_fixed(el.v[i], sv);
+            el.M[i] = to_fixed(el.mu[i], sm);
+            el.MV[i] = to_fixed(__longlong_as_double(el.MV[i]), smv);
+            el.MM[i] = to_fixed(__longlong_as_double(el.MM[i]), smm);
+        }
+        // emax slots are rewritten only by the next prepare(), after at least
+        // one more cluster barrier.
+        __syncthreads();
+    }
+
+    // Sums over S = {i : fma(nu, mu_i, v_i) > tau}; totals valid in thread 0.
+    __device__ void support_sums(double nu, double tau, float nu32, float tau32, I128 (&out)[6]) {
+        I128 a[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = I128{0ull, 0ll};
+        const float anu = fabsf(nu32), atau = isinf(tau32) ? 0.f : fabsf(tau32);
+        const float c = 2.384185791015625e-07f;   // 2^-22
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            const float v32 = el.v32[i], m32 = el.mu32[i];
+            const float d = fmaf(nu32, m32, v32) - tau32;
+            const float margin = c * (fmaf(anu, fabsf(m32), fabsf(v32)) + atau);
+            bool in;
+            if (d > margin) {
+                in = true;
+            } else if (d < -margin) {
+                in = false;
+            } else {
+                const double w = fma(nu, el.mu[i], el.v[i]);   // exact decision in FP64
+                in = (w > tau);
+                if (!(w == w)) a[5].lo = 1;                      // NaN seen
+            }
+            if (in) {
+                a[0].lo += 1;
+                add128(a[1], el.V[i]);
+                add128(a[2], el.M[i]);
+                add128(a[3], el.MV[i]);
+                add128(a[4], el.MM[i]);
+            }
+        }
+        reduce6(a, out);
+    }
+
+    // Full search.  Returns (nu, tau, status) identically in all threads.
+    __device__ ProjOut solve(double R, int mode, double mu_min, double mu_max, double nu_hint, double tau_hint,
+                             int budget) {
+        // Thread-0-owned search state.
+        double lo = -INFINITY, hi = INFINITY, nu = 0.0, tau = -INFINITY, prev_cnt = -1.0;
+        bool have_lo = false, have_hi = false, zero_done = false, first = true;
+        int outer = 0, inner = 0, status = MV_OK;
         const bool ge = (mode == MV_RETURN_GE);
-        double lo = -INFINITY, hi = INFINITY;   // psi(lo) < 0 <= psi(hi)
-        bool have_lo = false, have_hi = false, zero_done = false;
-        double nu = (nu_hint == nu_hint) ? nu_hint : 0.0;
-        if (ge && !(nu > 0.0)) nu = 0.0;
-        double tau = tau_hint;
-        ProjSums s;
-        for (int it = 0; it < budget; ++it) {
-            if (!simplex_tau(nu, tau, s, 96)) {
-                o.status = MV_ERR_NOT_CONVERGED;
-                break;
-            }
-            if (!(tau == tau) || !isfinite(s.sv) || !isfinite(s.smv)) {
-                o.status = MV_ERR_NUMERIC;
-                break;
-            }
-            if (nu == 0.0) zero_done = true;
-            const double a = s.cnt, b = s.sm, c = s.smm;
-            const double det = a * c - b * b;            // |S| sum_S (mu - mean)^2
-            const bool flat = !(det > 1e-13 * a * c);    // mu constant on S
-            double psi;
-            if (flat) {
-                psi = b / a - R;                         // phi = mean of mu on S
+        if (threadIdx.x == 0) {
+            sh->steps = 0;
+            sh->done = 0;
+            if (!(R <= mu_max) || (!ge && !(R >= mu_min))) {
+                sh->done = 1;
+                sh->status = MV_ERR_INFEASIBLE;
+                sh->nu = NAN;
+                sh->tau = NAN;
             } else {
-                psi = (fma(nu, c, s.smv) - tau * b) - R;
+                nu = (nu_hint == nu_hint) ? nu_hint : 0.0;
+                if (ge && !(nu > 0.0)) nu = 0.0;
+                tau = (tau_hint == tau_hint) ? tau_hint : -INFINITY;
+                sh->nu = nu;
+                sh->tau = tau;
+                sh->nu32 = (float)nu;
+                sh->tau32 = (float)tau;
+                sh->status = MV_OK;
             }
-            if (ge && nu == 0.0 && psi >= 0.0) break;    // return row inactive
-            if (psi == 0.0) break;
-            double nu_c = NAN;
-            if (flat) {
-                if (fabs(psi) <= 1e-12 * scaleR) break;  // target met on a flat piece
-            } else {
-                const double d1 = s.sv - 1.0, d2 = s.smv - R;
-                nu_c = (b * d1 - a * d2) / det;
-                if (fabs(nu_c - nu) <= 1e-13 * fmax(1.0, fabs(nu))) break;   // exact finish
-            }
-            if (psi < 0.0) {
-                lo = nu;
-                have_lo = true;
-            } else {
-                hi = nu;
-                have_hi = true;
-            }
-            double nxt = nu_c;
-            if (ge && nxt == nxt && nxt <= 0.0 && !zero_done) nxt = 0.0;
-            const bool inside = (nxt == nxt) && (!have_lo || nxt > lo) && (!have_hi || nxt < hi) &&
-                                (!ge || nxt >= 0.0);
-            if (!inside) {
-                if (have_lo && have_hi) {
-                    nxt = 0.5 * (lo + hi);
-                } else if (have_lo) {                    // expand right: 1, 2, 4, ...
-                    nxt = (lo < 0.0) ? 0.0 : (lo == 0.0 ? 1.0 : 2.0 * lo);
-                    if (nxt == 0.0 && zero_done) nxt = 1.0;
-                } else {                                 // expand left (EQ) or test nu = 0 (GE)
-                    if (ge) {
-                        nxt = 0.0;
+        }
+        __syncthreads();
+        double scaleR = 0.0;
+        if (threadIdx.x == 0) scaleR = fmax(fabs(R), fmax(fabs(mu_max), fabs(mu_min)));
+        while (true) {
+            if (sh->done) break;                       // uniform: read after a barrier
+            const double enu = sh->nu, etau = sh->tau;
+            const float enu32 = sh->nu32, etau32 = sh->tau32;
+            I128 S[6];
+            support_sums(enu, etau, enu32, etau32, S);
+            if (threadIdx.x == 0) {
+                sh->steps += 1;
+                const double cnt = (double)S[0].lo;
+                const double sv = i128_to_double(S[1]) * sh->p_v;
+                const double sm = i128_to_double(S[2]) * sh->p_m;
+                const double smv = i128_to_double(S[3]) * sh->p_mv;
+                const double smm = i128_to_double(S[4]) * sh->p_mm;
+                bool finish = false;
+                double next_nu = enu, next_tau = etau;
+                if (S[5].lo != 0) {
+                    status = MV_ERR_NUMERIC;
+                    finish = true;
+                } else if (cnt == 0.0) {               // tau >= max w: restart from the left
+                    next_tau = -INFINITY;
+                    first = true;
+                    if (++inner > 96) {
+                        status = MV_ERR_NOT_CONVERGED;
+                        finish = true;
+                    }
+                } else if (first || cnt != prev_cnt) {  // inner Newton step
+                    first = false;
+                    prev_cnt = cnt;
+                    next_tau = (fma(enu, sm, sv) - 1.0) / cnt;
+                    if (++inner > 96) {
+                        status = MV_ERR_NOT_CONVERGED;
+                        finish = true;
+                    }
+                } else {
+                    // inner converged: etau is the threshold at enu, S its support
+                    inner = 0;
+                    nu = enu;
+                    tau = etau;
+                    if (nu == 0.0) zero_done = true;
+                    const double a = cnt, b = sm, c = smm;
+                    const double det = a * c - b * b;
+                    const bool flat = !(det > 1e-13 * a * c);
+                    const double psi = flat ? (b / a - R) : ((fma(nu, c, smv) - tau * b) - R);
+                    double nu_c = NAN;
+                    if (ge && nu == 0.0 && psi >= 0.0) {
+                        finish = true;                 // return row inactive
+                    } else if (psi == 0.0) {
+                        finish = true;
+                    } else if (flat && fabs(psi) <= 1e-12 * scaleR) {
+                        finish = true;                 // target met on a flat piece
                     } else {
-                        nxt = (hi > 0.0) ? 0.0 : (hi == 0.0 ? -1.0 : 2.0 * hi);
-                        if (nxt == 0.0 && zero_done) nxt = -1.0;
+                        if (!flat) {
+                            nu_c = (b * (sv - 1.0) - a * (smv - R)) / det;
+                            if (fabs(nu_c - nu) <= 1e-13 * fmax(1.0, fabs(nu))) finish = true;   // exact finish
+                        }
+                        if (!finish) {
+                            if (psi < 0.0) {
+                                lo = nu;
+                                have_lo = true;
+                            } else {
+                                hi = nu;
+                                have_hi = true;
+                            }
+                            double nxt = nu_c;
+                            if (ge && nxt == nxt && nxt <= 0.0 && !zero_done) nxt = 0.0;
+                            const bool inside = (nxt == nxt) && (!have_lo || nxt > lo) && (!have_hi || nxt < hi) &&
+                                                (!ge || nxt >= 0.0);
+                            if (!inside) {
+                                if (have_lo && have_hi) {
+                                    nxt = 0.5 * (lo + hi);
+                                } else if (have_lo) {          // expand right: 1, 2, 4, ...
+                                    nxt = (lo < 0.0) ? 0.0 : (lo == 0.0 ? 1.0 : 2.0 * lo);
+                                    if (nxt == 0.0 && zero_done) nxt = 1.0;
+                                } else if (ge) {
+                                    nxt = 0.0;
+                                } else {                       // expand left (equality mode)
+                                    nxt = (hi > 0.0) ? 0.0 : (hi == 0.0 ? -1.0 : 2.0 * hi);
+                                    if (nxt == 0.0 && zero_done) nxt = -1.0;
+                                }
+                            }
+                            if (nxt == nu || ++outer >= budget) {
+                                status = MV_ERR_NOT_CONVERGED;
+                                finish = true;
+                            } else {
+                                next_nu = nxt;
+                                next_tau = (fma(nxt, b, sv) - 1.0) / a;   // threshold this support predicts
+                                first = true;
+                            }
+                        }
                     }
                 }
+                if (finish) {
+                    sh->done = 1;
+                    sh->status = status;
+                    sh->nu = nu;
+                    sh->tau = tau;
+                    if (status == MV_ERR_NUMERIC || (status == MV_ERR_NOT_CONVERGED && !(tau == tau))) {
+                        sh->nu = enu;
+                        sh->tau = etau;
+                    }
+                } else {
+                    sh->nu = next_nu;
+                    sh->tau = next_tau;
+                    sh->nu32 = (float)next_nu;
+                    sh->tau32 = (float)next_tau;
+                }
             }
-            if (nxt == nu) {                             // bracket exhausted in FP64
-                o.status = MV_ERR_NOT_CONVERGED;
-                break;
-            }
-            // Start the inner search from the threshold this support predicts.
-            tau = (fma(nxt, b, s.sv) - 1.0) / a;
-            nu = nxt;
-            if (it == budget - 1) o.status = MV_ERR_NOT_CONVERGED;
+            __syncthreads();
         }
-        o.nu = nu;
-        o.tau = tau;
-        o.s = s;
-        o.steps = steps;
+        ProjOut o;
+        o.nu = sh->nu;
+        o.tau = sh->tau;
+        o.status = sh->status;
+        o.steps = sh->steps;
+        __syncthreads();   // all threads read the result before the slots are reused
         return o;
     }
 };
+
+// Cluster size used for a problem of n assets: about 512 elements per block
+// (two per thread), at most 16 blocks.
+inline int proj_cluster_size(int64_t n) {
+    if (n <= 512) return 1;
+    if (n <= 1024) return 2;
+    if (n <= 2048) return 4;
+    if (n <= 4096) return 8;
+    return 16;
+}
 
 }  // namespace mv

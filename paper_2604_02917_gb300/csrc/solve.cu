@@ -10,6 +10,8 @@
 // replayed; every kernel returns at once when the device-side `done` flag is
 // set, so a chunk that overruns convergence costs only empty launches.  The
 // host reads the flag once per chunk.
+#include <stdlib.h>
+
 #include <mutex>
 #include <unordered_map>
 #include <vector>
@@ -21,11 +23,10 @@ namespace mv {
 
 constexpr int kStepThreads = 512;
 constexpr int kProjBudget = 100;
-constexpr int kSmemVecMax = 12800;   // n up to this keeps v and mu in shared memory
 
 struct SolveState {
     int k, done, converged, status;
-    int proj_fail, pad0, pad1, pad2;
+    int proj_fail, proj_steps, pad1, pad2;
     double t, beta_prev;
     double alpha, lambda_hat;
     double kkt, nu, tau, nu_kkt, tau_kkt;
@@ -37,10 +38,12 @@ struct Plan {
     int dt, vec, esize;
     int n, T;
     int64_t ld;
+    int cl;                                // cluster size of the step kernel
     int t_blocks, t_splits, t_rows;        // gemv_t grid
     int n_groups, n_splits, n_cols;        // gemv_n grid
     // workspace offsets (bytes)
-    size_t o_state, o_x, o_y, o_gx, o_gy, o_v, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
+    size_t o_state, o_x, o_y, o_gx, o_gy, o_g32, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
+    int64_t zstride;                       // row pitch (floats) of the gemv_t partials
     size_t total;
 };
 
@@ -66,6 +69,12 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld) {
     p.n = (int)n;
     p.T = (int)T;
     p.ld = ld;
+    p.cl = proj_cluster_size(n);
+    // Tuning override of the step kernel's cluster size (1, 2, 4, 8 or 16).
+    if (const char *env = getenv("MV_STEP_CLUSTER")) {
+        const int c = atoi(env);
+        if ((c == 1 || c == 2 || c == 4 || c == 8 || c == 16) && (n + c - 1) / c <= kProjMaxLocal) p.cl = c;
+    }
     const int sms = sm_count();
     // gemv_t: strips of 256*VEC columns; rows split so the grid covers
     // several waves of the machine (4 resident blocks per SM assumed).
@@ -95,10 +104,11 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld) {
     p.o_y = take(8 * (size_t)n);
     p.o_gx = take(8 * (size_t)n);
     p.o_gy = take(8 * (size_t)n);
-    p.o_v = take(8 * (size_t)n);
+    p.o_g32 = take(4 * (size_t)n);
     p.o_y32 = take(4 * (size_t)n);
-    p.o_z = take(4 * (size_t)T);
-    p.o_zpart = take(4 * (size_t)T * p.t_splits);
+    p.o_z = take(4 * (size_t)T + 64);
+    p.zstride = (T + 15) / 16 * 16;
+    p.o_zpart = take(4 * (size_t)p.zstride * p.t_splits);
     p.o_gpart = take(4 * (size_t)n * p.n_splits);
     p.o_tick_t = take(4 * (size_t)p.t_blocks);
     p.o_tick_n = take(4 * (size_t)p.n_groups);
@@ -145,19 +155,41 @@ setup_kernel(SolveState *st, const double *__restrict__ mu, const double *__rest
     }
 }
 
-// u <- g / ||g|| (power method), written as FP32 gemv input (row-scaled).
+// u <- g / ||g|| (power method) from the FP32 copy of g, written as the FP32
+// gemv input (row-scaled).  FP32 arithmetic: u only sets the direction.
 __global__ void __launch_bounds__(kStepThreads)
-power_norm_kernel(const double *__restrict__ g, const float *__restrict__ row_scale,
-                  float *__restrict__ y32, int n) {
-    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
-    double ss[1] = {0.0};
-    for (int i = threadIdx.x; i < n; i += kStepThreads) ss[0] = fma(g[i], g[i], ss[0]);
-    block_sum<1, kStepThreads>(ss, red);
-    const double inv = ss[0] > 0.0 ? 1.0 / sqrt(ss[0]) : 0.0;
-    for (int i = threadIdx.x; i < n; i += kStepThreads) {
-        const double s = row_scale ? (double)row_scale[i] : 1.0;
-        y32[i] = (float)(g[i] * inv * s);
+power_norm_kernel(const float *__restrict__ g32, const float *__restrict__ row_scale, float *__restrict__ y32,
+                  int n) {
+    __shared__ float red[kStepThreads / kWarp + 1];
+    float ss = 0.f;
+    for (int i = threadIdx.x; i < n; i += kStepThreads) ss = fmaf(g32[i], g32[i], ss);
+    ss = warp_sumf(ss);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < kStepThreads / kWarp ? red[threadIdx.x] : 0.f;
+        t = warp_sumf(t);
+        if (threadIdx.x == 0) red[kStepThreads / kWarp] = t;
     }
+    __syncthreads();
+    const float tot = red[kStepThreads / kWarp];
+    const float inv = tot > 0.f ? rsqrtf(tot) : 0.f;
+    for (int i = threadIdx.x; i < n; i += kStepThreads)
+        y32[i] = g32[i] * inv * (row_scale ? row_scale[i] : 1.f);
+}
+
+// Compensated FP32 sum of squares of an FP32 vector; FP64 only across threads.
+__device__ __forceinline__ double sumsq_f32(const float *__restrict__ z, int T, double *red) {
+    float s = 0.f, c = 0.f;
+    for (int t = threadIdx.x; t < T; t += kStepThreads) {
+        const float y = fmaf(z[t], z[t], -c);
+        const float u = s + y;
+        c = (u - s) - y;
+        s = u;
+    }
+    double v[1] = {(double)s - (double)c};
+    block_sum<1, kStepThreads>(v, red);
+    return v[0];
 }
 
 // lambda_hat = ||L^T u||^2; alpha = 1 / (2 (lambda_hat (1 + safety) + gamma)).
@@ -165,14 +197,12 @@ __global__ void __launch_bounds__(kStepThreads)
 step_size_kernel(SolveState *st, const float *__restrict__ z, int T, double gamma, double safety,
                  double alpha_override) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
-    double ss[1] = {0.0};
-    for (int t = threadIdx.x; t < T; t += kStepThreads) ss[0] = fma((double)z[t], (double)z[t], ss[0]);
-    block_sum<1, kStepThreads>(ss, red);
+    const double lam = sumsq_f32(z, T, red);
     if (threadIdx.x == 0) {
-        st->lambda_hat = ss[0];
+        st->lambda_hat = lam;
         double a = alpha_override;
         if (!(a > 0.0)) {
-            const double lf = 2.0 * (ss[0] * (1.0 + safety) + gamma);
+            const double lf = 2.0 * (lam * (1.0 + safety) + gamma);
             a = lf > 0.0 ? 1.0 / lf : 1.0;
         }
         st->alpha = a;
@@ -181,51 +211,67 @@ step_size_kernel(SolveState *st, const float *__restrict__ z, int T, double gamm
 }
 
 // x^0: Pi_F(1/n 1), or the caller's x^0 when warm-starting; y^0 = x^0.
-__global__ void __launch_bounds__(kStepThreads)
+// Runs as one cluster of CL blocks (the projection of project.cuh).
+template <int CL>
+__global__ void __launch_bounds__(kProjNT)
 init_x_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ x_in,
-              double *__restrict__ vbuf, double *__restrict__ x, double *__restrict__ y,
-              float *__restrict__ y32, const float *__restrict__ row_scale, int n, double R, int mode) {
-    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+              double *__restrict__ x, double *__restrict__ y, float *__restrict__ y32,
+              const float *__restrict__ row_scale, int n, double R, int mode) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ ProjSmem psm;
+    const int rank = cluster_rank<CL>();
+    const int nl = (n + CL - 1) / CL;
+    const int r0 = min(n, rank * nl);
+    const int r1 = min(n, r0 + nl);
     const double mn = st->mu_min, mx = st->mu_max;
     if (x_in == nullptr) {
-        for (int i = threadIdx.x; i < n; i += kStepThreads) vbuf[i] = 1.0 / n;
-        __syncthreads();
-        Projector<kStepThreads> P{vbuf, mu, n, red, 0};
-        const ProjOut o = P.solve(R, mode, mn, mx, 0.0, -INFINITY, kProjBudget);
-        for (int i = threadIdx.x; i < n; i += kStepThreads) {
-            const double xi = o.status == MV_ERR_INFEASIBLE ? NAN : fmax(fma(o.nu, mu[i], vbuf[i]) - o.tau, 0.0);
-            x[i] = xi;
-            y[i] = xi;
-            y32[i] = (float)(xi * (row_scale ? (double)row_scale[i] : 1.0));
+        ProjElems el = carve_elems(dsm, nl);
+        el.n = r1 - r0;
+        proj_smem_init(&psm);
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            el.v[i] = 1.0 / n;
+            el.mu[i] = mu[r0 + i];
         }
-        if (threadIdx.x == 0) {
+        __syncthreads();
+        ClusterProj<CL> P{&psm, el};
+        P.prepare();
+        const ProjOut o = P.solve(R, mode, mn, mx, 0.0, -INFINITY, kProjBudget);
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            const double xi = o.status == MV_ERR_INFEASIBLE ? NAN : fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
+            x[r0 + i] = xi;
+            y[r0 + i] = xi;
+            y32[r0 + i] = (float)(xi * (row_scale ? (double)row_scale[r0 + i] : 1.0));
+        }
+        if (rank == 0 && threadIdx.x == 0) {
             if (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC) st->status = o.status;
             st->nu = o.nu;
             st->tau = o.tau;
             st->nu_kkt = o.nu;
             st->tau_kkt = o.tau;
         }
+        cluster_barrier<CL>();
     } else {
-        for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        for (int i = r0 + threadIdx.x; i < r1; i += kProjNT) {
             const double xi = x_in[i];
             x[i] = xi;
             y[i] = xi;
             y32[i] = (float)(xi * (row_scale ? (double)row_scale[i] : 1.0));
         }
-        if (threadIdx.x == 0) {
+        if (rank == 0 && threadIdx.x == 0) {
             st->nu = 0.0;
             st->tau = -INFINITY;
             st->nu_kkt = 0.0;
             st->tau_kkt = -INFINITY;
         }
     }
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
         st->t = 1.0;
         st->beta_prev = 0.0;
         st->k = 0;
         st->done = (st->status != MV_OK) ? 1 : 0;
         st->converged = 0;
         st->proj_fail = 0;
+        st->proj_steps = 0;
         st->kkt = INFINITY;
     }
 }
@@ -233,102 +279,123 @@ init_x_kernel(SolveState *st, const double *__restrict__ mu, const double *__res
 struct StepArgs {
     SolveState *st;
     const double *gy;
-    double *x, *y, *gx, *vbuf;
+    double *x, *y, *gx;
     float *y32;
     const double *mu;
     const float *row_scale;
     int n, mode, kkt_every, max_iter;
     double R, gamma, eps;
-    int use_smem;
 };
 
-__global__ void __launch_bounds__(kStepThreads) npga_step_kernel(StepArgs a) {
-    extern __shared__ double sm[];
-    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+// One NPGA step on a cluster of CL blocks; block r owns assets [r0, r1).
+template <int CL>
+__global__ void __launch_bounds__(kProjNT) npga_step_kernel(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ ProjSmem psm;
     SolveState *st = a.st;
+    // Every block reads the flag before the first cluster barrier; the flag is
+    // only written after later barriers, so the whole cluster agrees.
     if (*(volatile int *)&st->done) return;
     const int n = a.n;
+    const int rank = cluster_rank<CL>();
+    const int nl = (n + CL - 1) / CL;
+    const int r0 = min(n, rank * nl);
+    const int r1 = min(n, r0 + nl);
     const int k = st->k;
     const double beta_prev = st->beta_prev, alpha = st->alpha, t = st->t;
     const double mn = st->mu_min, mx = st->mu_max;
     const double nu0 = st->nu, tau0 = st->tau, nuk0 = st->nu_kkt, tauk0 = st->tau_kkt;
     const double gamma = a.gamma;
-
-    double *V = a.use_smem ? sm : a.vbuf;
-    const double *MU = a.mu;
-    if (a.use_smem) {
-        double *smu = sm + n;
-        for (int i = threadIdx.x; i < n; i += kStepThreads) smu[i] = a.mu[i];
-        MU = smu;
+    ProjElems el = carve_elems(dsm, nl);
+    el.n = r1 - r0;
+    // Scalars are computed once (FP64 is scarce on this part) and broadcast.
+    __shared__ double sc[4];
+    if (threadIdx.x == 0) {
+        sc[0] = 1.0 / (1.0 + beta_prev);
+        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+        sc[1] = tn;
+        sc[2] = (t - 1.0) / tn;
     }
+    proj_smem_init(&psm);
+    const double inv1pb = sc[0], tn = sc[1], beta = sc[2];
     const bool check = (a.kkt_every > 0 && k % a.kkt_every == 0) || (k >= a.max_iter);
 
-    // grad f(x^k)/2 - gamma x^k = L L^T x^k by linearity from the product at y^k.
-    for (int i = threadIdx.x; i < n; i += kStepThreads) {
-        const double gyi = a.gy[i];
-        const double gxi = (k == 0) ? gyi : (gyi + beta_prev * a.gx[i]) / (1.0 + beta_prev);
-        a.gx[i] = gxi;
+    // L L^T x^k by linearity from the product at y^k; KKT point x - alpha grad f(x).
+    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+        const int gi = r0 + i;
+        el.mu[i] = a.mu[gi];
+        const double gyi = a.gy[gi];
+        const double gxi = (k == 0) ? gyi : (gyi + beta_prev * a.gx[gi]) * inv1pb;
+        a.gx[gi] = gxi;
         if (check) {
-            const double xi = a.x[i];
-            V[i] = xi - alpha * (2.0 * gxi + 2.0 * gamma * xi);
+            const double xi = a.x[gi];
+            el.v[i] = xi - alpha * (2.0 * gxi + 2.0 * gamma * xi);
         }
     }
     __syncthreads();
-    Projector<kStepThreads> P{V, MU, n, red, 0};
+    ClusterProj<CL> P{&psm, el};
     if (check) {
+        P.prepare();
         const ProjOut o = P.solve(a.R, a.mode, mn, mx, nuk0, tauk0, kProjBudget);
-        double r2[1] = {0.0};
-        for (int i = threadIdx.x; i < n; i += kStepThreads) {
-            const double p = fmax(fma(o.nu, MU[i], V[i]) - o.tau, 0.0);
-            const double d = p - a.x[i];
-            r2[0] = fma(d, d, r2[0]);
+        double r2 = 0.0;
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            const double p = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
+            const double d = p - a.x[r0 + i];
+            r2 = fma(d, d, r2);
         }
-        block_sum<1, kStepThreads>(r2, red);
-        const double kkt = sqrt(r2[0]);
-        const bool conv = kkt <= a.eps;
-        const bool stop = conv || k >= a.max_iter || !(kkt == kkt);
-        if (threadIdx.x == 0) {
+        r2 = P.reduce_double(r2);          // identical in every block
+        const bool conv = r2 <= a.eps * a.eps;
+        const bool stop = conv || k >= a.max_iter || !(r2 == r2);
+        if (rank == 0 && threadIdx.x == 0) {
+            const double kkt = sqrt(r2);
             st->kkt = kkt;
             st->nu_kkt = o.nu;
             st->tau_kkt = o.tau;
+            st->proj_steps += o.steps;
             if (o.status != MV_OK) st->proj_fail += 1;
             if (stop) {
                 st->done = 1;
                 st->converged = conv ? 1 : 0;
-                st->status = conv ? MV_OK : (!(kkt == kkt) ? MV_ERR_NUMERIC : MV_ERR_NOT_CONVERGED);
+                st->status = conv ? MV_OK : (!(r2 == r2) ? MV_ERR_NUMERIC : MV_ERR_NOT_CONVERGED);
             }
         }
-        if (stop) return;
+        if (stop) {
+            cluster_barrier<CL>();
+            return;
+        }
         __syncthreads();
     }
-    for (int i = threadIdx.x; i < n; i += kStepThreads) {
-        const double yi = a.y[i];
-        V[i] = yi - alpha * (2.0 * a.gy[i] + 2.0 * gamma * yi);
+    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+        const int gi = r0 + i;
+        const double yi = a.y[gi];
+        el.v[i] = yi - alpha * (2.0 * a.gy[gi] + 2.0 * gamma * yi);
     }
     __syncthreads();
+    P.prepare();
     const ProjOut o = P.solve(a.R, a.mode, mn, mx, nu0, tau0, kProjBudget);
-    const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-    const double beta = (t - 1.0) / tn;
-    for (int i = threadIdx.x; i < n; i += kStepThreads) {
-        const double xn = fmax(fma(o.nu, MU[i], V[i]) - o.tau, 0.0);
-        const double xo = a.x[i];
+    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+        const int gi = r0 + i;
+        const double xn = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
+        const double xo = a.x[gi];
         const double yn = xn + beta * (xn - xo);
-        a.x[i] = xn;
-        a.y[i] = yn;
-        a.y32[i] = (float)(yn * (a.row_scale ? (double)a.row_scale[i] : 1.0));
+        a.x[gi] = xn;
+        a.y[gi] = yn;
+        a.y32[gi] = (float)(yn * (a.row_scale ? (double)a.row_scale[gi] : 1.0));
     }
-    if (threadIdx.x == 0) {
+    if (rank == 0 && threadIdx.x == 0) {
         st->t = tn;
         st->beta_prev = beta;
         st->k = k + 1;
         st->nu = o.nu;
         st->tau = o.tau;
         if (o.status != MV_OK) st->proj_fail += 1;
+        st->proj_steps += o.steps;
         if (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC) {
             st->done = 1;
             st->status = o.status;
         }
     }
+    cluster_barrier<CL>();   // no block leaves while a peer may still address its shared memory
 }
 
 // FP64 n-vector -> scaled FP32 gemv input.
@@ -343,11 +410,12 @@ __global__ void __launch_bounds__(kStepThreads)
 objective_kernel(SolveState *st, const float *__restrict__ z, int T, const double *__restrict__ x, int n,
                  double gamma) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
-    double s[2] = {0.0, 0.0};
-    for (int t = threadIdx.x; t < T; t += kStepThreads) s[0] = fma((double)z[t], (double)z[t], s[0]);
-    for (int i = threadIdx.x; i < n; i += kStepThreads) s[1] = fma(x[i], x[i], s[1]);
-    block_sum<2, kStepThreads>(s, red);
-    if (threadIdx.x == 0) st->objective = s[0] + gamma * s[1];
+    const double zz = sumsq_f32(z, T, red);
+    double s[1] = {0.0};
+    if (gamma != 0.0)
+        for (int i = threadIdx.x; i < n; i += kStepThreads) s[0] = fma(x[i], x[i], s[0]);
+    block_sum<1, kStepThreads>(s, red);
+    if (threadIdx.x == 0) st->objective = zz + gamma * s[0];
 }
 
 // g = 2 (L z) + 2 gamma y   (gradient building block output).
@@ -363,7 +431,7 @@ static int validate_problem(const mv_problem *P) {
     if (P->dtype != MV_F32 && P->dtype != MV_BF16 && P->dtype != MV_FP8_E4M3) return MV_ERR_INVALID_ARG;
     if (P->mode != MV_RETURN_GE && P->mode != MV_RETURN_EQ) return MV_ERR_INVALID_ARG;
     if (P->n < 1 || P->T < 1 || P->ld < P->T) return MV_ERR_INVALID_ARG;
-    if (P->n > (1 << 26) || P->T > (1LL << 31) - 1) return MV_ERR_UNSUPPORTED;
+    if (P->n > kProjMaxN || P->T > (1LL << 31) - 1) return MV_ERR_UNSUPPORTED;
     const int es = dtype_size(P->dtype);
     if (((uintptr_t)P->L) % 16 != 0 || (P->ld * es) % 16 != 0) return MV_ERR_INVALID_ARG;
     if (P->dtype == MV_FP8_E4M3 && P->row_scale == nullptr) return MV_ERR_INVALID_ARG;
@@ -381,53 +449,67 @@ template <int DT>
 static void launch_gemv_t(const Plan &p, const void *L, const float *y32, float *zpart, float *z,
                           unsigned *tick, const int *done, cudaStream_t s) {
     dim3 grid(p.t_blocks, p.t_splits);
-    gemv_t_kernel<DT><<<grid, kGemvThreads, 0, s>>>(L, p.ld, p.n, p.T, y32, zpart, z, tick, p.t_rows, done);
+    gemv_t_kernel<DT><<<grid, kGemvThreads, 0, s>>>(L, p.ld, p.n, p.T, y32, zpart, p.zstride, z, tick, p.t_rows,
+                                                     done);
 }
 
 template <int DT>
 static void launch_gemv_n(const Plan &p, const void *L, const float *z, const float *row_scale, float *gpart,
-                          double *g, unsigned *tick, const int *done, cudaStream_t s) {
+                          double *g, unsigned *tick, const int *done, cudaStream_t s, float *g32 = nullptr) {
     dim3 grid(p.n_groups, p.n_splits);
     const size_t smem = (size_t)p.n_cols * 4;
-    gemv_n_kernel<DT, kRW><<<grid, kGemvThreads, smem, s>>>(L, p.ld, p.n, p.T, z, row_scale, gpart, g, tick,
+    gemv_n_kernel<DT, kRW><<<grid, kGemvThreads, smem, s>>>(L, p.ld, p.n, p.T, z, row_scale, gpart, g, g32, tick,
                                                            p.n_cols, done);
 }
 
 // Kernel attributes are set once per process, before any stream capture.
+template <typename Kern>
+static bool cluster_attrs(Kern k, int CL) {
+    const int smem = (int)proj_elem_bytes(kProjMaxLocal);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
+    if (CL > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return false;
+    return true;
+}
+
 static int set_kernel_attrs() {
     static std::once_flag once;
     static int status = MV_OK;
     std::call_once(once, [] {
         const int big = 96 * 1024;
-        if (cudaFuncSetAttribute(gemv_n_kernel<MV_F32, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(gemv_n_kernel<MV_BF16, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(gemv_n_kernel<MV_FP8_E4M3, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(npga_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 16 * kSmemVecMax) !=
-                cudaSuccess)
-            status = MV_ERR_CUDA;
+        bool ok = cudaFuncSetAttribute(gemv_n_kernel<MV_F32, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) ==
+                      cudaSuccess &&
+                  cudaFuncSetAttribute(gemv_n_kernel<MV_BF16, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) ==
+                      cudaSuccess &&
+                  cudaFuncSetAttribute(gemv_n_kernel<MV_FP8_E4M3, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       big) == cudaSuccess;
+        ok = ok && cluster_attrs(npga_step_kernel<1>, 1) && cluster_attrs(npga_step_kernel<2>, 2) &&
+             cluster_attrs(npga_step_kernel<4>, 4) && cluster_attrs(npga_step_kernel<8>, 8) &&
+             cluster_attrs(npga_step_kernel<16>, 16);
+        ok = ok && cluster_attrs(init_x_kernel<1>, 1) && cluster_attrs(init_x_kernel<2>, 2) &&
+             cluster_attrs(init_x_kernel<4>, 4) && cluster_attrs(init_x_kernel<8>, 8) &&
+             cluster_attrs(init_x_kernel<16>, 16);
+        if (!ok) status = record_cuda_error(cudaGetLastError(), "kernel attributes", __FILE__, __LINE__);
     });
     return status;
 }
 
 static void gemv_pair(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done,
-                      double *g_out, cudaStream_t s) {
+                      double *g_out, cudaStream_t s, float *g32 = nullptr) {
     float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z), *gpart = at<float>(ws, p.o_gpart);
     unsigned *tt = at<unsigned>(ws, p.o_tick_t), *tn = at<unsigned>(ws, p.o_tick_n);
     switch (p.dt) {
         case MV_F32:
             launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, done, s);
-            launch_gemv_n<MV_F32>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s);
+            launch_gemv_n<MV_F32>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s, g32);
             break;
         case MV_BF16:
             launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, done, s);
-            launch_gemv_n<MV_BF16>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s);
+            launch_gemv_n<MV_BF16>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s, g32);
             break;
         default:
             launch_gemv_t<MV_FP8_E4M3>(p, P->L, y32, zpart, z, tt, done, s);
-            launch_gemv_n<MV_FP8_E4M3>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s);
+            launch_gemv_n<MV_FP8_E4M3>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s, g32);
             break;
     }
 }
@@ -442,7 +524,24 @@ static void gemv_t_only(const Plan &p, const mv_problem *P, const float *y32, vo
     }
 }
 
-static size_t step_smem(int n) { return n <= kSmemVecMax ? (size_t)16 * n : 0; }
+template <typename Kern, typename... Args>
+static cudaError_t launch_cluster(Kern kern, int CL, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)CL);
+    cfg.blockDim = dim3(kProjNT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+static size_t step_smem(int n, int CL) { return proj_elem_bytes((n + CL - 1) / CL); }
 
 static void launch_step(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, cudaStream_t s) {
     StepArgs a;
@@ -451,7 +550,6 @@ static void launch_step(const Plan &p, const mv_problem *P, const mv_solve_opts 
     a.x = at<double>(ws, p.o_x);
     a.y = at<double>(ws, p.o_y);
     a.gx = at<double>(ws, p.o_gx);
-    a.vbuf = at<double>(ws, p.o_v);
     a.y32 = at<float>(ws, p.o_y32);
     a.mu = P->mu;
     a.row_scale = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
@@ -462,9 +560,29 @@ static void launch_step(const Plan &p, const mv_problem *P, const mv_solve_opts 
     a.R = P->R_target;
     a.gamma = P->gamma;
     a.eps = O->eps;
-    const size_t sm = step_smem(p.n);
-    a.use_smem = sm > 0;
-    npga_step_kernel<<<1, kStepThreads, sm, s>>>(a);
+    const size_t sm = step_smem(p.n, p.cl);
+    switch (p.cl) {
+        case 1: launch_cluster(npga_step_kernel<1>, 1, sm, s, a); break;
+        case 2: launch_cluster(npga_step_kernel<2>, 2, sm, s, a); break;
+        case 4: launch_cluster(npga_step_kernel<4>, 4, sm, s, a); break;
+        case 8: launch_cluster(npga_step_kernel<8>, 8, sm, s, a); break;
+        default: launch_cluster(npga_step_kernel<16>, 16, sm, s, a); break;
+    }
+}
+
+static void launch_init_x(const Plan &p, const mv_problem *P, const double *x_in, void *ws, cudaStream_t s) {
+    SolveState *st = at<SolveState>(ws, p.o_state);
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    double *x = at<double>(ws, p.o_x), *y = at<double>(ws, p.o_y);
+    float *y32 = at<float>(ws, p.o_y32);
+    const size_t sm = step_smem(p.n, p.cl);
+    switch (p.cl) {
+        case 1: launch_cluster(init_x_kernel<1>, 1, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
+        case 2: launch_cluster(init_x_kernel<2>, 2, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
+        case 4: launch_cluster(init_x_kernel<4>, 4, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
+        case 8: launch_cluster(init_x_kernel<8>, 8, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
+        default: launch_cluster(init_x_kernel<16>, 16, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
+    }
 }
 
 // One loop iteration.  With `ev` non-null, events ev[0..3] bracket gemv_t,
@@ -601,6 +719,7 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
+    (void)cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
     float *y32 = at<float>(d_ws, p.o_y32);
     double *lz = at<double>(d_ws, p.o_gy);
@@ -625,6 +744,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
+    (void)cudaGetLastError();   // start from a clean error state
     cudaStream_t s = (cudaStream_t)stream;
     SolveState *st = at<SolveState>(d_ws, p.o_state);
     float *y32 = at<float>(d_ws, p.o_y32);
@@ -637,24 +757,24 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     // Power method for ||L_eff||_2^2 (skipped when the step is given).
     if (!(O.alpha > 0.0)) {
         for (int it = 0; it < O.power_iters; ++it) {
-            gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s);
-            power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<double>(d_ws, p.o_gy), rs, y32, p.n);
+            gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
+            power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
         }
         gemv_t_only(p, P, y32, d_ws, s);
     }
     step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0) ? 0 : p.T, P->gamma,
                                                 O.power_safety, O.alpha);
-    init_x_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, O.warm_start ? d_x_inout : nullptr, at<double>(d_ws, p.o_v),
-                                             at<double>(d_ws, p.o_x), at<double>(d_ws, p.o_y), y32, rs, p.n,
-                                             P->R_target, P->mode);
+    launch_init_x(p, P, O.warm_start ? d_x_inout : nullptr, d_ws, s);
     MV_CUDA_TRY(cudaGetLastError());
 
     const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
     int launches = 4 + (O.alpha > 0.0 ? 0 : 3 * O.power_iters + 1);
     const cudaEvent_t *ev = nullptr;
     if (O.timing) MV_TRY(timing_events(3 * chunk + 1, &ev));
+    // Events recorded by graph nodes cannot be timed, so a timed solve issues
+    // its kernels from the host (same kernels, same order).
     cudaGraphExec_t exec = nullptr;
-    if (O.use_graph) MV_TRY(get_chunk_graph(p, P, &O, d_ws, chunk, ev, &exec));
+    if (O.use_graph && !O.timing) MV_TRY(get_chunk_graph(p, P, &O, d_ws, chunk, nullptr, &exec));
     // max_iter + 1 iterations may run: the last one only evaluates the KKT residual.
     const int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
     SolveState hs{};
@@ -713,6 +833,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     h_info->t_gemv_t_ms = t_t;
     h_info->t_gemv_n_ms = t_n;
     h_info->t_step_ms = t_s;
+    h_info->proj_steps = hs.proj_steps;
     return h_info->status;
 }
 

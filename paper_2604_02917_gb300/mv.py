@@ -66,7 +66,8 @@ class SolveInfo(C.Structure):
                 ("proj_failures", C.c_int32), ("kkt", C.c_double), ("objective", C.c_double),
                 ("alpha", C.c_double), ("lambda_hat", C.c_double), ("nu", C.c_double),
                 ("launches", C.c_int32), ("timed_pairs", C.c_int32), ("t_gemv_t_ms", C.c_double),
-                ("t_gemv_n_ms", C.c_double), ("t_step_ms", C.c_double)]
+                ("t_gemv_n_ms", C.c_double), ("t_step_ms", C.c_double), ("proj_steps", C.c_int32),
+                ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

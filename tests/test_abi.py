@@ -59,7 +59,7 @@ def _c_layout(tmp_path):
                           "alpha", "use_graph", "timing"],
         "mv_solve_info": ["iterations", "status", "converged", "proj_failures", "kkt", "objective",
                           "alpha", "lambda_hat", "nu", "launches", "timed_pairs", "t_gemv_t_ms",
-                          "t_gemv_n_ms", "t_step_ms"],
+                          "t_gemv_n_ms", "t_step_ms", "proj_steps", "reserved"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mv.h"', "int main(void){"]
     for st, fs in fields.items():
@@ -94,7 +94,7 @@ def test_host_side_argument_errors(mvmod):
     assert lib.mv_project(None, None, None, 10, 1, 0, None, None, None) == mvmod.MV_ERR_INVALID_ARG
     fake = C.c_void_p(256)
     assert lib.mv_project(fake, fake, fake, 0, 1, 0, fake, fake, None) == mvmod.MV_ERR_INVALID_ARG
-    assert lib.mv_project(fake, fake, fake, 70000, 1, 0, fake, fake, None) == mvmod.MV_ERR_INVALID_ARG
+    assert lib.mv_project(fake, fake, fake, 40000, 1, 0, fake, fake, None) == mvmod.MV_ERR_INVALID_ARG
     assert lib.mv_project(fake, fake, fake, 10, 1, 7, fake, fake, None) == mvmod.MV_ERR_INVALID_ARG
     # Problem validation: misaligned pitch, bad dtype, missing FP8 scales.
     p = mvmod.Problem()

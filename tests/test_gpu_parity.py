@@ -94,7 +94,7 @@ def test_project_hand_cases(mv):
 
 
 @pytest.mark.parametrize("mode", ["ge", "eq"])
-@pytest.mark.parametrize("n", [1, 2, 3, 7, 64, 513, 2000, 5440, 13001])
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 64, 513, 1025, 2000, 5440, 13001, 32768])
 def test_project_random_parity(mv, n, mode):
     rng = np.random.default_rng(1000 + n + (7 if mode == "eq" else 0))
     batch = 6
