@@ -212,6 +212,36 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *opts, double *d_x_in
 int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
                 void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * 5. Allocation-free gradient.  The paper has no counterpart: this is a
+ *    service for callers that cannot allocate device memory -- code that is
+ *    handed only pre-allocated input and output buffers by a host framework
+ *    that owns the device memory pool (plug-ins, user-defined functions), or
+ *    a latency-bound loop that cannot absorb the device-wide synchronisation
+ *    cudaMalloc implies.
+ *
+ *  Same inputs, outputs and result as mv_gradient, but no workspace
+ *  argument: the scratch lives in one file-scope device array of
+ *  MV_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
+ *  the library keeps until the process exits.  The call allocates nothing
+ *  (no cudaMalloc, cudaFree or allocating library routine).
+ *  - Limit: problems whose workspace (mv_npga_workspace_size) exceeds
+ *    MV_NOALLOC_SCRATCH_BYTES are rejected on the host with
+ *    MV_ERR_UNSUPPORTED before anything is launched; mv_last_error() then
+ *    states the bytes needed.  (5440 x 48374 FP32 fits.)
+ *  - The first call on a device looks up the array's device address with
+ *    that device current; make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind; the call clears what must start at zero.  Calls whose work
+ *    overlaps on the GPU (different streams, or different host threads)
+ *    race on the array and must be serialised by the caller.
+ *  Asynchronous.
+ * ------------------------------------------------------------------------ */
+#define MV_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
+                        mv_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

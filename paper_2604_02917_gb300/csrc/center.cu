@@ -22,6 +22,11 @@ int record_cuda_error(cudaError_t e, const char *what, const char *file, int lin
     return MV_ERR_CUDA;
 }
 
+int record_message(int status, const char *msg) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+    return status;
+}
+
 constexpr int kCenterThreads = 512;
 
 template <int DT>

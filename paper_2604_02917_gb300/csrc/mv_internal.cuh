@@ -16,6 +16,8 @@ constexpr int kWarp = 32;
 
 // Records the failing call for mv_last_error() and returns MV_ERR_CUDA.
 int record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+// Records a message for mv_last_error() and returns `status`.
+int record_message(int status, const char *msg);
 
 #define MV_CUDA_TRY(expr)                                                     \
     do {                                                                      \

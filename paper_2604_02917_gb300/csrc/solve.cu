@@ -838,3 +838,65 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free gradient: mv_gradient with its scratch in a fixed device
+// array rather than a caller workspace, for callers that may not allocate
+// device memory (they only receive input and output buffers from a host
+// framework that owns the memory pool, or cannot pay cudaMalloc's implicit
+// synchronisation in a latency-bound loop).
+namespace mv {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MV_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[128];   // device address of the array, per device ordinal
+
+// Set-up, once per device, with that device current: the host-side name of
+// the array is only a stand-in, so its device address is looked up here.
+static int noalloc_scratch(void **out) {
+    int dev = 0;
+    MV_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return record_message(MV_ERR_UNSUPPORTED, "mv_gradient_noalloc: device ordinal >= 128");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (g_noalloc_addr[dev] == nullptr) {
+        void *p = nullptr;
+        MV_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return MV_OK;
+}
+
+}  // namespace mv
+
+extern "C" int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
+                                   mv_stream_t stream) {
+    MV_TRY(validate_problem(P));
+    if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    if (p.total > MV_NOALLOC_SCRATCH_BYTES) {
+        char msg[200];
+        snprintf(msg, sizeof(msg),
+                 "mv_gradient_noalloc: this problem needs %zu bytes of scratch; the fixed array holds %zu",
+                 p.total, (size_t)MV_NOALLOC_SCRATCH_BYTES);
+        return record_message(MV_ERR_UNSUPPORTED, msg);
+    }
+    void *ws = nullptr;
+    MV_TRY(noalloc_scratch(&ws));
+    MV_TRY(set_kernel_attrs());
+    (void)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    float *y32 = at<float>(ws, p.o_y32);
+    double *lz = at<double>(ws, p.o_gy);
+    // The array keeps the previous call's contents: the gemv tickets must start at zero.
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(d_y, rs, y32, p.n);
+    gemv_pair(p, P, y32, ws, nullptr, lz, s);
+    grad_finish_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(lz, d_y, P->gamma, d_g, p.n);
+    if (d_z) MV_CUDA_TRY(cudaMemcpyAsync(d_z, at<float>(ws, p.o_z), 4 * (size_t)p.T, cudaMemcpyDeviceToDevice, s));
+    MV_CUDA_TRY(cudaGetLastError());
+    return MV_OK;
+}

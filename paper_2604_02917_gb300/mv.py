@@ -30,14 +30,18 @@ MODES = {"ge": MV_RETURN_GE, "eq": MV_RETURN_EQ}
 EXPORTS = [
     "mv_status_string", "mv_version", "mv_center_workspace_size", "mv_center_factor", "mv_project",
     "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
+    "mv_gradient_noalloc",
 ]
+
+# Size of the library's fixed scratch array used by mv_gradient_noalloc.
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class MvError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
         extra = ""
-        if status == MV_ERR_CUDA:
+        if status in (MV_ERR_CUDA, MV_ERR_UNSUPPORTED):
             extra = " -- " + lib().mv_last_error().decode()
         super().__init__(f"{where}: {status_string(status)} (status {status}){extra}")
 
@@ -103,6 +107,8 @@ def lib():
                                     vp, sz, vp]
         L.mv_gradient.restype = i32
         L.mv_gradient.argtypes = [C.POINTER(Problem), vp, vp, vp, vp, sz, vp]
+        L.mv_gradient_noalloc.restype = i32
+        L.mv_gradient_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -260,3 +266,15 @@ def gradient(L, y, T, gamma=0.0, dtype="f32", row_scale=None):
     mu = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
     s = Solver(L, mu, 0.0, T, gamma, dtype, row_scale)
     return s.gradient(y)
+
+
+def gradient_noalloc(L, y, T, gamma=0.0, dtype="f32", row_scale=None):
+    """(z, g) as ``gradient`` but through mv_gradient_noalloc: the library uses
+    its fixed scratch array instead of a workspace (outputs still come from
+    PyTorch here).  Calls overlapping on the GPU race on that array."""
+    mu = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
+    p = make_problem(L, mu, 0.0, T, gamma, dtype, row_scale)
+    z = torch.empty(T, dtype=torch.float32, device=y.device)
+    g = torch.empty_like(y)
+    _check(lib().mv_gradient_noalloc(C.byref(p), _ptr(y), _ptr(z), _ptr(g), _stream()), "mv_gradient_noalloc")
+    return z, g
