@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--shape", default=None, help="n,T override (profiling runs on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP8 + FP32-refinement lines")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -309,6 +310,30 @@ def main():
                "h2d_bytes_per_step": int(R32.nbytes), "d2h_bytes_per_step": int(model.n * 8)}
         del R_buf, R_pin
 
+    # Low-precision storage + FP32 refinement on the same workload and GPU.
+    variants = {}
+    if not args.no_variants and args.dtype == "f32":
+        R_dev = torch.from_numpy(R32).to(dev)
+        for vdt in ("bf16", "fp8"):
+            Llo, rslo, _, _ = mv.center_factor(R_dev, vdt)
+            rsv = mv.RefinedSolver(Llo, L, mu, Rt, model.T, dtype=vdt, row_scale=rslo, power_start=r0,
+                                   eps_lo=1e-5, eps=args.eps)
+            for _ in range(args.warmup):
+                rsv.solve()
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for _ in range(args.steps):
+                _, vi = rsv.solve()
+            v1.record(stream)
+            torch.cuda.synchronize()
+            variants[vdt + "+fp32_refine"] = {
+                "value": v0.elapsed_time(v1) / args.steps / 1e3, "unit": "s", "iterations": vi["iterations"],
+                "refine_iterations": vi["refine_iterations"], "kkt": vi["kkt"], "objective": vi["objective"],
+                "rel_obj_vs_fp32": (vi["objective"] - infos[-1]["objective"]) / infos[-1]["objective"]}
+            del Llo, rslo, rsv
+        del R_dev
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = int(np.median([i["iterations"] for i in infos]))
@@ -327,7 +352,8 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single"},
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
-                "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks}
+                "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
+                "variants": variants}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -188,7 +188,7 @@ typedef struct {
     double t_gemv_n_ms;       /* summed device time of those gemv_n launches             */
     double t_step_ms;         /* summed device time of those step (projection) launches  */
     int32_t proj_steps;       /* block-wide reductions spent by all projections          */
-    int32_t reserved;
+    int32_t refine_iterations;/* mv_npga_solve_refined: iterations of the FP32 phase     */
 } mv_solve_info;
 
 void mv_solve_opts_default(mv_solve_opts *opts);
@@ -201,6 +201,26 @@ size_t mv_npga_workspace_size(const mv_problem *P);
  *  read the device-side convergence flag, and returns when the solve is done. */
 int mv_npga_solve(const mv_problem *P, const mv_solve_opts *opts, double *d_x_inout,
                   mv_solve_info *h_info, void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * 3b. Low-precision solve with FP32 refinement (an extension: the paper does
+ *     not state its precision).  The bandwidth-bound products stream L in
+ *     BF16 (half the bytes) or FP8 e4m3 with row scales (a quarter); the
+ *     result is then refined on the FP32 copy of the same factor.
+ *
+ *  Phase 1: mv_npga_solve(P_lo) to a KKT residual <= eps_lo, with its own
+ *  power method.  Phase 2: mv_npga_solve(P_hi) warm-started from that point,
+ *  with the fixed step alpha_lo / (1 + 1e-2) (the spectral norms of the two
+ *  copies differ by far less than 1%, so the step stays admissible) and no
+ *  second power method, until the KKT residual of P_hi is <= opts->eps.
+ *  P_lo and P_hi must describe the same problem (n, T, gamma, mu, target,
+ *  mode); P_hi->dtype must be MV_F32.  Workspace: the larger of the two
+ *  mv_npga_workspace_size values.  h_info: iterations = both phases,
+ *  refine_iterations = phase 2, kkt/objective/alpha of phase 2.  Blocking.
+ * ------------------------------------------------------------------------ */
+int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const mv_solve_opts *opts,
+                          double eps_lo, double *d_x_inout, mv_solve_info *h_info,
+                          void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * 4. Gradient building block (Eq. npga-unified-grad), exposed for tests and

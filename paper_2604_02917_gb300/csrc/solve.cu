@@ -837,6 +837,43 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     return h_info->status;
 }
 
+int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const mv_solve_opts *O_in, double eps_lo,
+                          double *d_x_inout, mv_solve_info *h_info, void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    MV_TRY(validate_problem(P_lo));
+    MV_TRY(validate_problem(P_hi));
+    if (h_info == nullptr || d_x_inout == nullptr || !(eps_lo >= 0.0)) return MV_ERR_INVALID_ARG;
+    if (P_hi->dtype != MV_F32 || P_lo->n != P_hi->n || P_lo->T != P_hi->T || P_lo->gamma != P_hi->gamma ||
+        P_lo->mu != P_hi->mu || P_lo->R_target != P_hi->R_target || P_lo->mode != P_hi->mode)
+        return MV_ERR_INVALID_ARG;
+    mv_solve_opts O;
+    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
+    mv_solve_opts O1 = O;
+    O1.eps = eps_lo;
+    mv_solve_info i1{};
+    int st = mv_npga_solve(P_lo, &O1, d_x_inout, &i1, d_ws, ws_bytes, stream);
+    if (st != MV_OK && st != MV_ERR_NOT_CONVERGED) {
+        *h_info = i1;
+        return st;
+    }
+    mv_solve_opts O2 = O;
+    O2.warm_start = 1;
+    O2.alpha = i1.alpha / (1.0 + 1e-2);
+    mv_solve_info i2{};
+    st = mv_npga_solve(P_hi, &O2, d_x_inout, &i2, d_ws, ws_bytes, stream);
+    *h_info = i2;
+    h_info->iterations = i1.iterations + i2.iterations;
+    h_info->refine_iterations = i2.iterations;
+    h_info->lambda_hat = i1.lambda_hat;
+    h_info->proj_failures = i1.proj_failures + i2.proj_failures;
+    h_info->proj_steps = i1.proj_steps + i2.proj_steps;
+    h_info->launches = i1.launches + i2.launches;
+    h_info->timed_pairs = i1.timed_pairs + i2.timed_pairs;
+    h_info->t_gemv_t_ms = i1.t_gemv_t_ms + i2.t_gemv_t_ms;
+    h_info->t_gemv_n_ms = i1.t_gemv_n_ms + i2.t_gemv_n_ms;
+    h_info->t_step_ms = i1.t_step_ms + i2.t_step_ms;
+    return st;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

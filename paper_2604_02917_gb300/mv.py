@@ -30,7 +30,7 @@ MODES = {"ge": MV_RETURN_GE, "eq": MV_RETURN_EQ}
 EXPORTS = [
     "mv_status_string", "mv_version", "mv_center_workspace_size", "mv_center_factor", "mv_project",
     "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
-    "mv_gradient_noalloc",
+    "mv_gradient_noalloc", "mv_npga_solve_refined",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -71,7 +71,7 @@ class SolveInfo(C.Structure):
                 ("alpha", C.c_double), ("lambda_hat", C.c_double), ("nu", C.c_double),
                 ("launches", C.c_int32), ("timed_pairs", C.c_int32), ("t_gemv_t_ms", C.c_double),
                 ("t_gemv_n_ms", C.c_double), ("t_step_ms", C.c_double), ("proj_steps", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("refine_iterations", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -107,6 +107,9 @@ def lib():
                                     vp, sz, vp]
         L.mv_gradient.restype = i32
         L.mv_gradient.argtypes = [C.POINTER(Problem), vp, vp, vp, vp, sz, vp]
+        L.mv_npga_solve_refined.restype = i32
+        L.mv_npga_solve_refined.argtypes = [C.POINTER(Problem), C.POINTER(Problem), C.POINTER(SolveOpts), dbl, vp,
+                                            C.POINTER(SolveInfo), vp, sz, vp]
         L.mv_gradient_noalloc.restype = i32
         L.mv_gradient_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp, vp]
         _lib = L
@@ -252,6 +255,31 @@ class Solver:
         _check(lib().mv_gradient(C.byref(self.problem), _ptr(y), _ptr(z), _ptr(g), _ptr(self.ws),
                                  self.ws.numel(), _stream()), "mv_gradient")
         return z, g
+
+
+class RefinedSolver:
+    """Low-precision solve (BF16 or FP8 copy of L) refined on the FP32 copy
+    (mv_npga_solve_refined); reuses workspace and graphs across calls."""
+
+    def __init__(self, L_lo, L_hi, mu, R_target, T, gamma=0.0, dtype="bf16", row_scale=None, mode="ge",
+                 power_start=None, eps_lo=1e-5, **opts):
+        self._keep = (L_lo, L_hi, mu, row_scale, power_start)
+        self.p_lo = make_problem(L_lo, mu, R_target, T, gamma, dtype, row_scale, mode, power_start)
+        self.p_hi = make_problem(L_hi, mu, R_target, T, gamma, "f32", None, mode, power_start)
+        self.opts = solve_opts(**opts)
+        self.eps_lo = float(eps_lo)
+        nb = max(lib().mv_npga_workspace_size(C.byref(self.p_lo)), lib().mv_npga_workspace_size(C.byref(self.p_hi)))
+        if nb == 0:
+            raise MvError(MV_ERR_INVALID_ARG, "mv_npga_workspace_size")
+        self.ws = _workspace(nb, L_hi.device)
+        self.x = torch.zeros(L_hi.shape[0], dtype=torch.float64, device=L_hi.device)
+
+    def solve(self, allow=(MV_ERR_NOT_CONVERGED,)):
+        info = SolveInfo()
+        st = lib().mv_npga_solve_refined(C.byref(self.p_lo), C.byref(self.p_hi), C.byref(self.opts), self.eps_lo,
+                                         _ptr(self.x), C.byref(info), _ptr(self.ws), self.ws.numel(), _stream())
+        _check(st, "mv_npga_solve_refined", allow)
+        return self.x, info.as_dict()
 
 
 def npga_solve(L, mu, R_target, T, gamma=0.0, dtype="f32", row_scale=None, mode="ge", x0=None,

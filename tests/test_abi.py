@@ -59,7 +59,7 @@ def _c_layout(tmp_path):
                           "alpha", "use_graph", "timing"],
         "mv_solve_info": ["iterations", "status", "converged", "proj_failures", "kkt", "objective",
                           "alpha", "lambda_hat", "nu", "launches", "timed_pairs", "t_gemv_t_ms",
-                          "t_gemv_n_ms", "t_step_ms", "proj_steps", "reserved"],
+                          "t_gemv_n_ms", "t_step_ms", "proj_steps", "refine_iterations"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mv.h"', "int main(void){"]
     for st, fs in fields.items():

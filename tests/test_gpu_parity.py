@@ -262,3 +262,41 @@ def test_npga_full_size_kkt(mv):
     f = objective(L_o, 0.0, x)
     assert info["objective"] == pytest.approx(f, rel=1e-5)
     assert fw_gap(L_o, 0.0, mu_o, Rt, x) >= 0.0
+
+
+# ------------------------------------------------------------------ low precision
+@pytest.mark.parametrize("dt", ["bf16", "fp8"])
+def test_npga_low_precision_model_parity(mv, dt):
+    """The solve on the BF16 / FP8 copy matches the oracle on that same (dequantized) matrix."""
+    n, T = 700, 5003
+    R32, R64 = panel(n, T, seed=31, base=CFG_FULL)
+    L, rs, mu, _ = mv.center_factor(gpu(R32), dt)
+    Lq = dequant(mv, L, rs, T, dt)
+    mu_o = center_factor(R64)[0]
+    Rt = float(np.percentile(mu_o, 60))
+    x, info = mv.npga_solve(L, mu, Rt, T, dtype=dt, row_scale=rs, eps=1e-6)
+    assert info["converged"] == 1
+    x = x.cpu().numpy()
+    ref = oracle_solution(Lq, mu_o, Rt)
+    assert np.max(np.abs(x - ref.x)) <= 1e-4
+    assert (objective(Lq, 0.0, x) - ref.f) / ref.f <= 1e-5
+
+
+@pytest.mark.parametrize("dt", ["bf16", "fp8"])
+def test_npga_refined_reaches_fp32_optimum(mv, dt):
+    """Low-precision phase + FP32 refinement lands on the FP32 model's optimum."""
+    n, T = 900, 6001
+    R32, R64 = panel(n, T, seed=32, base=CFG_FULL)
+    Rd = gpu(R32)
+    L32, _, mu, _ = mv.center_factor(Rd, "f32")
+    Llo, rs, _, _ = mv.center_factor(Rd, dt)
+    mu_o, L_o, _ = center_factor(R64)
+    Rt = float(np.percentile(mu_o, 60))
+    s = mv.RefinedSolver(Llo, L32, mu, Rt, T, dtype=dt, row_scale=rs, eps_lo=1e-5, eps=1e-6)
+    x, info = s.solve()
+    assert info["converged"] == 1 and info["kkt"] <= 1e-6 and info["refine_iterations"] >= 0
+    x = x.cpu().numpy()
+    ref = oracle_solution(L_o, mu_o, Rt)
+    assert np.max(np.abs(x - ref.x)) <= 1e-4
+    assert (objective(L_o, 0.0, x) - ref.f) / ref.f <= 1e-5
+    assert kkt_residual(L_o, 0.0, mu_o, Rt, x, info["alpha"]) <= 1.05e-6
