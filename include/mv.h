@@ -223,6 +223,48 @@ int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const 
                           void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * 3c. Sketch (Sec. 2.3; STR step 1 of Sec. 2.5):  tilde L = L Phi.
+ *
+ *  A BF16 x BF16 -> FP32 GEMM on the tcgen05 tensor cores (accumulator in
+ *  tensor memory, operands staged by TMA with the 128-byte swizzle).
+ *  d_L      [in]  n x T BF16, row-major, leading dim ldL (ldL*2 % 16 == 0).
+ *  d_Phi_t  [in]  m x T BF16 = Phi transposed: row j holds sketch column j
+ *                 (entries N(0, 1/m) for the Gaussian JL sketch), ldP*2 % 16 == 0.
+ *  d_L_sketch [out] n x m FP32, row-major, leading dim ldS >= m.
+ *  All pointers 16-byte aligned.  Blocking: returns MV_ERR_TIMEOUT if a
+ *  pipeline wait exceeded its 2 s bound (no hang), MV_ERR_CUDA if the tensor
+ *  map could not be encoded.
+ * ------------------------------------------------------------------------ */
+int mv_sketch(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m,
+              int64_t ldP, float *d_L_sketch, int64_t ldS, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * 3d. Truncate + ridge (Sec. 2.5 steps 2-3; App. D.3), FP64.
+ *
+ *  From tilde L (n x m FP32) computes the k largest eigenpairs of the FP64
+ *  Gram matrix K = tilde L tilde L^T (eigenvalues sigma_i^2, eigenvectors U)
+ *  and writes L_eff = U_k diag(sigma_k) (n x k FP32, row-major, columns in
+ *  descending sigma) and sigma (k FP64, descending).  The ridge returned in
+ *  *h_gamma_out is `gamma` if gamma >= 0, else 1e-4 * trace_sigma / n.
+ *  One-time step; uses cuBLAS (DSYRK) and cuSOLVER (DSYEVDX) loaded at run
+ *  time: MV_ERR_UNSUPPORTED if they cannot be loaded.  Workspace:
+ *  mv_str_workspace_size(n, m, k) bytes (FP64 copies of tilde L and K plus
+ *  the eigensolver's buffer).  Blocking.  MV_ERR_NUMERIC if the eigensolver
+ *  reports a failure.
+ * ------------------------------------------------------------------------ */
+size_t mv_str_workspace_size(int64_t n, int64_t m, int64_t k);
+int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, int64_t k, double gamma,
+                    double trace_sigma, float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out,
+                    void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/*  mv_sketch followed by mv_str_truncate (the whole STR build of Sec. 2.5);
+ *  d_L_sketch receives tilde L.  Workspace as mv_str_workspace_size.  Blocking. */
+int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m,
+                  int64_t ldP, int64_t k, double gamma, double trace_sigma, float *d_L_sketch, int64_t ldS,
+                  float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out, void *d_ws,
+                  size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * 4. Gradient building block (Eq. npga-unified-grad), exposed for tests and
  *    for callers with their own outer loop:
  *        d_g = 2 L_eff (L_eff^T y) + 2 gamma y,   d_z = L_eff^T y.

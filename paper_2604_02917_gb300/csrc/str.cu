@@ -1,0 +1,200 @@
+// Truncate and ridge stages of STR (Sec. 2.5 steps 2-3, App. D.3), FP64.
+//
+// The thin SVD of tilde L (n x m) is obtained from the eigendecomposition of
+// the n x n Gram matrix K = tilde L tilde L^T: its eigenvalues are sigma_i^2
+// and its eigenvectors are U.  The top-k pairs give the effective factor
+// L_eff = U_k diag(sigma_k) (n x k), whose L_eff L_eff^T equals
+// tilde L_k tilde L_k^T (App. D.3), and the ridge is gamma (or
+// 1e-4 tr(Sigma)/n when the caller passes gamma < 0).
+//
+// This one-time FP64 step uses two NVIDIA libraries, loaded at run time so
+// that libmv itself loads without them: cuBLAS DSYRK for the Gram matrix (a
+// plain library GEMM) and cuSOLVER DSYEVDX for the k largest eigenpairs.
+// Everything else (FP64 widening, assembling L_eff and sigma) is in the
+// kernels below.
+#include <dlfcn.h>
+#include <stdio.h>
+
+#include <mutex>
+
+#include "mv_internal.cuh"
+
+namespace mv {
+
+// ------------------------------------------------------------------ runtime-loaded libraries
+typedef int (*fn_cublasCreate)(void **);
+typedef int (*fn_cublasSetStream)(void *, cudaStream_t);
+typedef int (*fn_cublasDsyrk)(void *, int, int, int, int, const double *, const double *, int, const double *,
+                              double *, int);
+typedef int (*fn_cusolverCreate)(void **);
+typedef int (*fn_cusolverSetStream)(void *, cudaStream_t);
+typedef int (*fn_syevdx_bs)(void *, int, int, int, int, const double *, int, double, double, int, int, int *,
+                            const double *, int *);
+typedef int (*fn_syevdx)(void *, int, int, int, int, double *, int, double, double, int, int, int *, double *,
+                         double *, int, int *);
+
+constexpr int kOpT = 1, kFillLower = 0, kEigVector = 1, kEigRangeI = 1002;
+
+struct Linalg {
+    void *blas = nullptr, *solver = nullptr;
+    void *hb = nullptr, *hs = nullptr;
+    fn_cublasSetStream b_set_stream = nullptr;
+    fn_cublasDsyrk dsyrk = nullptr;
+    fn_cusolverSetStream s_set_stream = nullptr;
+    fn_syevdx_bs syevdx_bs = nullptr;
+    fn_syevdx syevdx = nullptr;
+    bool ok = false;
+};
+
+static void *open_first(const char *const *names) {
+    for (int i = 0; names[i]; ++i) {
+        void *h = dlopen(names[i], RTLD_NOW | RTLD_GLOBAL);
+        if (h) return h;
+    }
+    return nullptr;
+}
+
+static Linalg *linalg() {
+    static Linalg L;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *blas_names[] = {"libcublas.so.13", "/usr/local/cuda/lib64/libcublas.so.13", "libcublas.so", nullptr};
+        const char *solver_names[] = {"libcusolver.so.12", "/usr/local/cuda/lib64/libcusolver.so.12",
+                                      "libcusolver.so", nullptr};
+        void *lb = open_first(blas_names);
+        void *ls = open_first(solver_names);
+        if (!lb || !ls) return;
+        auto bcreate = (fn_cublasCreate)dlsym(lb, "cublasCreate_v2");
+        L.b_set_stream = (fn_cublasSetStream)dlsym(lb, "cublasSetStream_v2");
+        L.dsyrk = (fn_cublasDsyrk)dlsym(lb, "cublasDsyrk_v2");
+        auto screate = (fn_cusolverCreate)dlsym(ls, "cusolverDnCreate");
+        L.s_set_stream = (fn_cusolverSetStream)dlsym(ls, "cusolverDnSetStream");
+        L.syevdx_bs = (fn_syevdx_bs)dlsym(ls, "cusolverDnDsyevdx_bufferSize");
+        L.syevdx = (fn_syevdx)dlsym(ls, "cusolverDnDsyevdx");
+        if (!bcreate || !L.b_set_stream || !L.dsyrk || !screate || !L.s_set_stream || !L.syevdx_bs || !L.syevdx)
+            return;
+        if (bcreate(&L.hb) != 0 || screate(&L.hs) != 0) return;
+        L.ok = true;
+    });
+    return L.ok ? &L : nullptr;
+}
+
+// ------------------------------------------------------------------ kernels
+__global__ void widen_kernel(const float *__restrict__ src, int n, int m, int64_t ld, double *__restrict__ dst) {
+    const int64_t total = (int64_t)n * m;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = idx / m, j = idx - i * m;
+        dst[idx] = (double)src[i * ld + j];
+    }
+}
+
+// Eigenpairs come back in ascending order in the first k columns of the
+// column-major n x n array; column c of L_eff takes the (c+1)-th largest.
+__global__ void leff_kernel(const double *__restrict__ U, const double *__restrict__ W, int n, int k,
+                            float *__restrict__ L_eff, int64_t ldE, double *__restrict__ sigma) {
+    const int64_t total = (int64_t)n * k;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / k), c = (int)(idx - (int64_t)i * k);
+        const int src = k - 1 - c;
+        const double s = sqrt(fmax(W[src], 0.0));
+        L_eff[(int64_t)i * ldE + c] = (float)(U[(int64_t)src * n + i] * s);
+        if (i == 0) sigma[c] = s;
+    }
+}
+
+struct StrPlan {
+    size_t o_a, o_k, o_w, o_work, o_info, total;
+    int lwork;
+};
+
+static int str_plan(int64_t n, int64_t m, int64_t k, StrPlan *p) {
+    Linalg *L = linalg();
+    if (!L) return record_message(MV_ERR_UNSUPPORTED, "STR truncation needs cuBLAS and cuSOLVER (not found)");
+    int meig = 0, lwork = 0;
+    if (L->syevdx_bs(L->hs, kEigVector, kEigRangeI, kFillLower, (int)n, nullptr, (int)n, 0.0, 0.0,
+                     (int)(n - k + 1), (int)n, &meig, nullptr, &lwork) != 0)
+        return record_message(MV_ERR_CUDA, "cusolverDnDsyevdx_bufferSize failed");
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    p->o_a = take(8 * (size_t)n * m);
+    p->o_k = take(8 * (size_t)n * n);
+    p->o_w = take(8 * (size_t)n);
+    p->o_work = take(8 * (size_t)lwork);
+    p->o_info = take(sizeof(int));
+    p->total = off;
+    p->lwork = lwork;
+    return MV_OK;
+}
+
+}  // namespace mv
+
+using namespace mv;
+
+extern "C" {
+
+size_t mv_str_workspace_size(int64_t n, int64_t m, int64_t k) {
+    if (n < 1 || m < 1 || k < 1 || k > n || n >= (1 << 30) || m >= (1 << 30)) return 0;
+    StrPlan p;
+    if (str_plan(n, m, k, &p) != MV_OK) return 0;
+    return p.total;
+}
+
+int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, int64_t k, double gamma,
+                    double trace_sigma, float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out,
+                    void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    if (!d_L_sketch || !d_L_eff || !d_sigma) return MV_ERR_INVALID_ARG;
+    if (n < 1 || m < 1 || k < 1 || k > n || ldS < m || ldE < k || n >= (1 << 30) || m >= (1 << 30))
+        return MV_ERR_INVALID_ARG;
+    StrPlan p;
+    MV_TRY(str_plan(n, m, k, &p));
+    if (d_ws == nullptr || ws_bytes < p.total || ((uintptr_t)d_ws) % 256) return MV_ERR_WORKSPACE;
+    Linalg *L = linalg();
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    char *ws = reinterpret_cast<char *>(d_ws);
+    double *A = reinterpret_cast<double *>(ws + p.o_a);
+    double *K = reinterpret_cast<double *>(ws + p.o_k);
+    double *W = reinterpret_cast<double *>(ws + p.o_w);
+    double *work = reinterpret_cast<double *>(ws + p.o_work);
+    int *info = reinterpret_cast<int *>(ws + p.o_info);
+    widen_kernel<<<1024, 256, 0, s>>>(d_L_sketch, (int)n, (int)m, ldS, A);
+    MV_CUDA_TRY(cudaGetLastError());
+    // Row-major n x m tilde L is the column-major m x n matrix A; K = A^T A.
+    if (L->b_set_stream(L->hb, s) != 0) return record_message(MV_ERR_CUDA, "cublasSetStream failed");
+    const double one = 1.0, zero = 0.0;
+    if (L->dsyrk(L->hb, kFillLower, kOpT, (int)n, (int)m, &one, A, (int)m, &zero, K, (int)n) != 0)
+        return record_message(MV_ERR_CUDA, "cublasDsyrk failed");
+    if (L->s_set_stream(L->hs, s) != 0) return record_message(MV_ERR_CUDA, "cusolverDnSetStream failed");
+    int meig = 0;
+    if (L->syevdx(L->hs, kEigVector, kEigRangeI, kFillLower, (int)n, K, (int)n, 0.0, 0.0, (int)(n - k + 1), (int)n,
+                  &meig, W, work, p.lwork, info) != 0)
+        return record_message(MV_ERR_CUDA, "cusolverDnDsyevdx failed");
+    leff_kernel<<<1024, 256, 0, s>>>(K, W, (int)n, (int)k, d_L_eff, ldE, d_sigma);
+    MV_CUDA_TRY(cudaGetLastError());
+    int hinfo = 0;
+    MV_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hinfo != 0 || meig != (int)k) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "cusolverDnDsyevdx: info=%d, %d of %lld eigenpairs", hinfo, meig, (long long)k);
+        return record_message(MV_ERR_NUMERIC, msg);
+    }
+    if (h_gamma_out) *h_gamma_out = gamma >= 0.0 ? gamma : 1e-4 * trace_sigma / (double)n;
+    return MV_OK;
+}
+
+int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m, int64_t ldP,
+                  int64_t k, double gamma, double trace_sigma, float *d_L_sketch, int64_t ldS, float *d_L_eff,
+                  int64_t ldE, double *d_sigma, double *h_gamma_out, void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    MV_TRY(mv_sketch(d_L, n, T, ldL, d_Phi_t, m, ldP, d_L_sketch, ldS, stream));
+    return mv_str_truncate(d_L_sketch, n, m, ldS, k, gamma, trace_sigma, d_L_eff, ldE, d_sigma, h_gamma_out, d_ws,
+                           ws_bytes, stream);
+}
+
+}  // extern "C"

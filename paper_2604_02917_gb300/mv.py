@@ -30,7 +30,8 @@ MODES = {"ge": MV_RETURN_GE, "eq": MV_RETURN_EQ}
 EXPORTS = [
     "mv_status_string", "mv_version", "mv_center_workspace_size", "mv_center_factor", "mv_project",
     "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
-    "mv_gradient_noalloc", "mv_npga_solve_refined",
+    "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
+    "mv_sketch_str",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -110,6 +111,16 @@ def lib():
         L.mv_npga_solve_refined.restype = i32
         L.mv_npga_solve_refined.argtypes = [C.POINTER(Problem), C.POINTER(Problem), C.POINTER(SolveOpts), dbl, vp,
                                             C.POINTER(SolveInfo), vp, sz, vp]
+        L.mv_str_workspace_size.restype = sz
+        L.mv_str_workspace_size.argtypes = [i64, i64, i64]
+        L.mv_str_truncate.restype = i32
+        L.mv_str_truncate.argtypes = [vp, i64, i64, i64, i64, dbl, dbl, vp, i64, vp, C.POINTER(C.c_double), vp, sz,
+                                      vp]
+        L.mv_sketch_str.restype = i32
+        L.mv_sketch_str.argtypes = [vp, i64, i64, i64, vp, i64, i64, i64, dbl, dbl, vp, i64, vp, i64, vp,
+                                    C.POINTER(C.c_double), vp, sz, vp]
+        L.mv_sketch.restype = i32
+        L.mv_sketch.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
         L.mv_gradient_noalloc.restype = i32
         L.mv_gradient_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp, vp]
         _lib = L
@@ -306,3 +317,46 @@ def gradient_noalloc(L, y, T, gamma=0.0, dtype="f32", row_scale=None):
     g = torch.empty_like(y)
     _check(lib().mv_gradient_noalloc(C.byref(p), _ptr(y), _ptr(z), _ptr(g), _stream()), "mv_gradient_noalloc")
     return z, g
+
+
+def sketch(L_bf16: torch.Tensor, T: int, Phi_t: torch.Tensor) -> torch.Tensor:
+    """tilde L = L Phi (Sec. 2.3): L is n x ld BF16 (from center_factor), Phi_t is
+    m x ldP BF16 holding Phi transposed (row j = sketch column j).  Returns the
+    n x m FP32 product (tcgen05 BF16 GEMM, FP32 accumulation).  Blocking."""
+    assert L_bf16.dtype == torch.bfloat16 and Phi_t.dtype == torch.bfloat16
+    n, m = L_bf16.shape[0], Phi_t.shape[0]
+    ldS = (m + 3) // 4 * 4
+    out = torch.empty((n, ldS), dtype=torch.float32, device=L_bf16.device)
+    _check(lib().mv_sketch(_ptr(L_bf16), n, T, L_bf16.stride(0), _ptr(Phi_t), m, Phi_t.stride(0), _ptr(out), ldS,
+                           _stream()), "mv_sketch")
+    return out[:, :m]
+
+
+def bf16_rows(A, ld=None) -> torch.Tensor:
+    """Host array (rows x cols) -> device BF16 tensor with a 16-byte row pitch
+    (input preparation: rounding to BF16 is done by PyTorch)."""
+    A = torch.as_tensor(A)
+    r, c = A.shape
+    ld = (c + 7) // 8 * 8 if ld is None else ld
+    out = torch.zeros((r, ld), dtype=torch.bfloat16, device="cuda")
+    out[:, :c] = A.to(device="cuda", dtype=torch.bfloat16)
+    return out
+
+
+def str_truncate(L_sketch: torch.Tensor, k: int, gamma: float = -1.0, trace_sigma: float = 0.0):
+    """Top-k FP64 truncation + ridge of tilde L (Sec. 2.5): returns (L_eff n x k
+    FP32, sigma k FP64, gamma).  gamma < 0 selects 1e-4 tr(Sigma)/n."""
+    assert L_sketch.dtype == torch.float32 and L_sketch.stride(1) == 1
+    n, m = L_sketch.shape
+    nb = lib().mv_str_workspace_size(n, m, k)
+    if nb == 0:
+        raise MvError(MV_ERR_UNSUPPORTED, "mv_str_workspace_size")
+    ws = _workspace(nb, L_sketch.device)
+    ldE = (k + 3) // 4 * 4
+    L_eff = torch.zeros((n, ldE), dtype=torch.float32, device=L_sketch.device)
+    sigma = torch.empty(k, dtype=torch.float64, device=L_sketch.device)
+    g = C.c_double(0.0)
+    _check(lib().mv_str_truncate(_ptr(L_sketch), n, m, L_sketch.stride(0), k, float(gamma), float(trace_sigma),
+                                 _ptr(L_eff), ldE, _ptr(sigma), C.byref(g), _ptr(ws), ws.numel(), _stream()),
+           "mv_str_truncate")
+    return L_eff, sigma, g.value
