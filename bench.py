@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--shape", default=None, help="n,T override (profiling runs on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP8 + FP32-refinement lines")
+    ap.add_argument("--no-str", action="store_true", help="skip the sketch / STR measurement")
+    ap.add_argument("--sketch-m", type=int, default=8192)
+    ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -334,6 +337,56 @@ def main():
             del Llo, rslo, rsv
         del R_dev
 
+    # Sketch (tcgen05 BF16 GEMM) + FP64 truncation + NPGA on the STR model.
+    str_res = None
+    if not args.no_str and args.dtype == "f32":
+        from synth import gaussian_sketch
+        R_dev = torch.from_numpy(R32).to(dev)
+        Lb, _, _, trd = mv.center_factor(R_dev, "bf16")
+        del R_dev
+        Phi_t = mv.bf16_rows(gaussian_sketch(model.T, args.sketch_m, seed=2, dtype=np.float32))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        mv.sketch(Lb, model.T, Phi_t)                      # warm-up
+        sk_ms = []
+        for _ in range(3):
+            e[0].record(stream)
+            Ls = mv.sketch(Lb, model.T, Phi_t)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            sk_ms.append(e[0].elapsed_time(e[1]))
+        flop = 2.0 * model.n * model.T * args.sketch_m
+        e[2].record(stream)
+        L_eff, sigma, gamma = mv.str_truncate(Ls, args.str_k, -1.0, float(trd.cpu()))
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        tr_ms = e[2].elapsed_time(e[3])
+        ssv = mv.Solver(L_eff, mu, Rt, args.str_k, gamma=gamma, power_start=r0, eps=args.eps)
+        for _ in range(args.warmup):
+            ssv.solve()
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(args.steps):
+            xs, si = ssv.solve()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        s_ms = e[0].elapsed_time(e[1]) / args.steps
+        _, gfull = mv.gradient(L, xs, model.T)             # 2 L L^T x on the full FP32 model
+        f_str_full = float(torch.dot(xs, gfull).item()) / 2.0
+        f_full = infos[-1]["objective"]
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16_peak = float(json.load(f).get("bf16_tflops", 1900.0))
+        tflops = flop / (min(sk_ms) * 1e-3) / 1e12
+        str_res = {"sketch": {"m": args.sketch_m, "ms": min(sk_ms), "tflop": flop / 1e12,
+                              "achieved_tflops": round(tflops, 1), "peak_tflops": bf16_peak,
+                              "frac": round(tflops / bf16_peak, 4), "bound": "tensor"},
+                   "truncate": {"k": args.str_k, "ms": tr_ms, "gamma": gamma, "sigma_1": float(sigma[0]),
+                                "sigma_k": float(sigma[-1])},
+                   "solve": {"value": s_ms / 1e3, "unit": "s", "iterations": si["iterations"], "kkt": si["kkt"],
+                             "step_kernel_share": None},
+                   "full_model_gap": (f_str_full - f_full) / f_full,
+                   "build_plus_solve_s": (min(sk_ms) + tr_ms + s_ms) / 1e3}
+        del Lb, Phi_t, Ls, L_eff, ssv
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = int(np.median([i["iterations"] for i in infos]))
@@ -353,7 +406,7 @@ def main():
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "variants": variants}
+                "variants": variants, "str": str_res}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

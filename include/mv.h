@@ -223,6 +223,28 @@ int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const 
                           void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * 3e. Efficient frontier: one factor, many targets (batched NPGA).
+ *
+ *  Solves the problem of P (L stored as MV_BF16) for n_targets <= 128
+ *  targets R_b at once (up to 128 points on the efficient frontier).  The
+ *  half-products of all targets are skinny tensor-core GEMMs
+ *  Z = L^T [y_1..y_B], G = L Z (tcgen05, BF16 operands, FP32 accumulation)
+ *  with the vector operands carried as a BF16 hi + lo pair, so accuracy is
+ *  that of the BF16 model; L^T is formed once in the workspace.  One shared
+ *  power method sets alpha; each target has its own FISTA state, KKT test
+ *  and stopping point; a chunk of kkt_every iterations is replayed as one
+ *  CUDA graph.  P->R_target is ignored.
+ *  d_R_targets [in]  n_targets FP64 targets (device).
+ *  d_X         [out] n_targets x n FP64 solutions (row b = target b).
+ *  h_infos     [out] n_targets host mv_solve_info (objective = BF16 model).
+ *  Returns the first non-OK per-target status (or MV_OK).  Blocking.
+ * ------------------------------------------------------------------------ */
+size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets);
+int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64_t n_targets,
+                           const mv_solve_opts *opts, double *d_X, mv_solve_info *h_infos,
+                           void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * 3c. Sketch (Sec. 2.3; STR step 1 of Sec. 2.5):  tilde L = L Phi.
  *
  *  A BF16 x BF16 -> FP32 GEMM on the tcgen05 tensor cores (accumulator in

@@ -1,0 +1,265 @@
+// tcgen05 BF16 GEMM  C = A B^T  (A: M x K, B: N x K, both K-major BF16;
+// FP32 accumulation in tensor memory).  Shared by the sketch (sketch.cu) and
+// the batched frontier solve (frontier.cu).
+//
+// One CTA computes a 128 x BN tile with a K loop in steps of 64:
+//   warp 0, one thread : TMA producer -- 128x64 A box and BNx64 B box per
+//                        stage (128-byte swizzle), S-stage ring of mbarriers;
+//   warp 1, one thread : MMA issuer -- four 128xBNx16 tcgen05.mma per stage
+//                        into a 128 x BN FP32 accumulator in TMEM, then
+//                        tcgen05.commit frees the stage;
+//   warps 2..5         : epilogue -- tcgen05.ld 32 lanes x 32 columns at a
+//                        time (warp w reads TMEM lanes 32*(w%4) ..).
+// Epilogues: kEpiF32 stores C row-major in FP32; kEpiPairSplitT (BN = 2B)
+// adds columns b and B+b of the tile (the hi and lo parts of a split
+// operand), splits the FP32 sum into BF16 hi + lo and stores both
+// transposed (rows b and B+b of a 2B x M BF16 matrix).
+// Out-of-range rows/columns/K of the boxes are zero-filled by TMA.  Every
+// mbarrier wait is bounded in time; on timeout an error code is recorded
+// in the translation unit's g_gemm_err and the CTA winds down.
+#pragma once
+
+#include <stdio.h>
+
+#include <cudaTypedefs.h>
+
+#include "umma.cuh"
+
+namespace mv {
+
+constexpr int kGemmThreads = 192;
+constexpr int kBM = 128, kBK = 64;
+constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
+
+static __device__ int g_gemm_err;
+
+template <int BN>
+struct GemmCfg {
+    static constexpr int S = (BN >= 256) ? 4 : (BN >= 128 ? 6 : 8);   // pipeline stages (<= 192 KB)
+    static constexpr uint32_t A_BYTES = kBM * kBK * 2;
+    static constexpr uint32_t B_BYTES = BN * kBK * 2;
+    static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+    static constexpr size_t SMEM = 1024 + (size_t)S * STAGE + (2 * S + 1) * 8 + 16;
+};
+
+constexpr int kEpiF32 = 0, kEpiPairSplitT = 1;
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                    float *__restrict__ C, int M, int N, int K, int64_t ldc, __nv_bfloat16 *__restrict__ Ct,
+                    int64_t ldct) {
+    using Cfg = GemmCfg<BN>;
+    constexpr int S = Cfg::S;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + S * Cfg::A_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * Cfg::STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 1);
+    const uint32_t full0 = umma::smem_u32(bars), empty0 = umma::smem_u32(bars + S), accum = umma::smem_u32(bars + 2 * S);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    const int nk = (K + kBK - 1) / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            umma::mbar_init(full0 + 8 * s, 1);
+            umma::mbar_init(empty0 + 8 * s, 1);
+        }
+        umma::mbar_init(accum, 1);
+        umma::mbar_fence_init();
+    }
+    if (warp == 1) {
+        umma::tmem_alloc(umma::smem_u32(tmem_slot), BN);
+        umma::tmem_relinquish();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            umma::prefetch_tensormap(&tmA);
+            umma::prefetch_tensormap(&tmB);
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % S;
+                const uint32_t ph = (uint32_t)(kt / S) & 1u;
+                if (!umma::mbar_wait(empty0 + 8 * s, ph ^ 1u, kWaitNs)) {
+                    atomicExch(&g_gemm_err, 1);
+                    break;
+                }
+                umma::mbar_arrive_expect_tx(full0 + 8 * s, Cfg::STAGE);
+                umma::tma_load_2d(umma::smem_u32(sA + s * Cfg::A_BYTES), &tmA, kt * kBK, m0, full0 + 8 * s);
+                umma::tma_load_2d(umma::smem_u32(sB + s * Cfg::B_BYTES), &tmB, kt * kBK, n0, full0 + 8 * s);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = umma::idesc_bf16_f32(kBM, BN);
+            bool ok = true;
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % S;
+                const uint32_t ph = (uint32_t)(kt / S) & 1u;
+                if (!umma::mbar_wait(full0 + 8 * s, ph, kWaitNs)) {
+                    atomicExch(&g_gemm_err, 2);
+                    ok = false;
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint64_t da = umma::desc_kmajor_sw128(umma::smem_u32(sA + s * Cfg::A_BYTES));
+                const uint64_t db = umma::desc_kmajor_sw128(umma::smem_u32(sB + s * Cfg::B_BYTES));
+#pragma unroll
+                for (int k = 0; k < kBK / 16; ++k)   // +32 bytes along K per 16-element step
+                    umma::mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kt | k) != 0 ? 1u : 0u);
+                umma::mma_commit(empty0 + 8 * s);
+            }
+            if (ok) umma::mma_commit(accum);
+        }
+        __syncwarp();
+    } else {
+        // Epilogue: warp w owns TMEM lanes 32*(w%4) .. +31, i.e. tile rows.
+        const bool ok = umma::mbar_wait(accum, 0, 4 * kWaitNs);
+        __syncwarp();
+        umma::fence_after_sync();
+        if (ok) {
+            const int lane_base = (warp & 3) * 32;
+            const int row = m0 + lane_base + lane;
+            const uint32_t tl = tmem + ((uint32_t)lane_base << 16);
+            if constexpr (EPI == kEpiF32) {
+                float *crow = C + (int64_t)row * ldc;
+#pragma unroll 1
+                for (int c = 0; c < BN / 32; ++c) {
+                    uint32_t r[32];
+                    umma::tmem_ld_32x32b_x32(tl + (uint32_t)(c * 32), r);
+                    umma::tmem_ld_wait();
+                    const int col0 = n0 + c * 32;
+                    if (row < M) {
+                        if (col0 + 32 <= N && (ldc & 3) == 0) {
+#pragma unroll
+                            for (int j = 0; j < 32; j += 4)
+                                *reinterpret_cast<float4 *>(crow + col0 + j) =
+                                    make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                                __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (col0 + j < N) crow[col0 + j] = __uint_as_float(r[j]);
+                        }
+                    }
+                }
+            } else {
+                constexpr int HB = BN / 2;          // columns b and HB + b hold the hi and lo parts
+#pragma unroll 1
+                for (int c = 0; c < HB / 32; ++c) {
+                    uint32_t a[32], b[32];
+                    umma::tmem_ld_32x32b_x32(tl + (uint32_t)(c * 32), a);
+                    umma::tmem_ld_32x32b_x32(tl + (uint32_t)(HB + c * 32), b);
+                    umma::tmem_ld_wait();
+                    if (row < M) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int bcol = c * 32 + j;
+                            const float zf = __uint_as_float(a[j]) + __uint_as_float(b[j]);
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(zf);
+                            const __nv_bfloat16 lo = __float2bfloat16_rn(zf - __bfloat162float(hi));
+                            Ct[(int64_t)bcol * ldct + row] = hi;
+                            Ct[(int64_t)(HB + bcol) * ldct + row] = lo;
+                        }
+                    }
+                }
+            }
+        } else if (lane == 0) {
+            atomicExch(&g_gemm_err, 3);
+        }
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    if (warp == 1) umma::tmem_dealloc(tmem, BN);
+}
+
+// ------------------------------------------------------------------ host
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D BF16 tensor map over a rows x cols row-major matrix (leading dim ld),
+// box = box_rows x 64 columns, 128-byte swizzle, zero fill out of range.
+static int make_map_bf16(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+    auto enc = tensor_map_encoder();
+    if (enc == nullptr) return record_message(MV_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char msg[128];
+        snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return record_message(MV_ERR_CUDA, msg);
+    }
+    return MV_OK;
+}
+
+template <int BN, int EPI>
+static int gemm_set_attrs() {
+    static int st = -1;
+    if (st < 0)
+        st = cudaFuncSetAttribute(gemm_bf16_tn_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)GemmCfg<BN>::SMEM) == cudaSuccess
+                 ? MV_OK
+                 : MV_ERR_CUDA;
+    return st;
+}
+
+// Enqueue C = A B^T with prebuilt tensor maps (no synchronisation; capturable).
+template <int BN, int EPI>
+static void gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int64_t N, int64_t K, float *C,
+                        int64_t ldc, __nv_bfloat16 *Ct, int64_t ldct, cudaStream_t s) {
+    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN));
+    gemm_bf16_tn_kernel<BN, EPI><<<grid, kGemmThreads, GemmCfg<BN>::SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K, ldc,
+                                                                               Ct, ldct);
+}
+
+// C = A B^T for BF16 K-major A (M x K) and B (N x K), FP32 row-major C;
+// blocking (reads the device error word after the launch).
+template <int BN>
+static int gemm_bf16_tn(const void *A, int64_t M, int64_t lda, const void *B, int64_t N, int64_t ldb, int64_t K,
+                        float *C, int64_t ldc, cudaStream_t s) {
+    CUtensorMap ta, tb;
+    MV_TRY(make_map_bf16(&ta, A, M, K, lda, kBM));
+    MV_TRY(make_map_bf16(&tb, B, N, K, ldb, BN));
+    MV_TRY((gemm_set_attrs<BN, kEpiF32>()));
+    int zero = 0;
+    MV_CUDA_TRY(cudaMemcpyToSymbolAsync(g_gemm_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    gemm_launch<BN, kEpiF32>(ta, tb, M, N, K, C, ldc, nullptr, 0, s);
+    MV_CUDA_TRY(cudaGetLastError());
+    int err = 0;
+    MV_CUDA_TRY(cudaMemcpyFromSymbolAsync(&err, g_gemm_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err != 0) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "tcgen05 GEMM pipeline wait timed out (stage code %d)", err);
+        return record_message(MV_ERR_TIMEOUT, msg);
+    }
+    return MV_OK;
+}
+
+}  // namespace mv

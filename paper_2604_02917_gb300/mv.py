@@ -31,7 +31,7 @@ EXPORTS = [
     "mv_status_string", "mv_version", "mv_center_workspace_size", "mv_center_factor", "mv_project",
     "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
     "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
-    "mv_sketch_str",
+    "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -119,6 +119,11 @@ def lib():
         L.mv_sketch_str.restype = i32
         L.mv_sketch_str.argtypes = [vp, i64, i64, i64, vp, i64, i64, i64, dbl, dbl, vp, i64, vp, i64, vp,
                                     C.POINTER(C.c_double), vp, sz, vp]
+        L.mv_frontier_workspace_size.restype = sz
+        L.mv_frontier_workspace_size.argtypes = [C.POINTER(Problem), i64]
+        L.mv_npga_solve_frontier.restype = i32
+        L.mv_npga_solve_frontier.argtypes = [C.POINTER(Problem), vp, i64, C.POINTER(SolveOpts), vp,
+                                             C.POINTER(SolveInfo), vp, sz, vp]
         L.mv_sketch.restype = i32
         L.mv_sketch.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
         L.mv_gradient_noalloc.restype = i32
@@ -360,3 +365,27 @@ def str_truncate(L_sketch: torch.Tensor, k: int, gamma: float = -1.0, trace_sigm
                                  _ptr(L_eff), ldE, _ptr(sigma), C.byref(g), _ptr(ws), ws.numel(), _stream()),
            "mv_str_truncate")
     return L_eff, sigma, g.value
+
+
+class FrontierSolver:
+    """Batched NPGA over many targets sharing one BF16 factor
+    (mv_npga_solve_frontier); reuses the workspace across calls."""
+
+    def __init__(self, L_bf16, mu, R_targets, T, gamma=0.0, mode="ge", power_start=None, **opts):
+        self.Rt = torch.as_tensor(R_targets, dtype=torch.float64).reshape(-1).to(L_bf16.device)
+        self._keep = (L_bf16, mu, power_start)
+        self.problem = make_problem(L_bf16, mu, 0.0, T, gamma, "bf16", None, mode, power_start)
+        self.opts = solve_opts(**opts)
+        self.nt = self.Rt.numel()
+        nb = lib().mv_frontier_workspace_size(C.byref(self.problem), self.nt)
+        if nb == 0:
+            raise MvError(MV_ERR_INVALID_ARG, "mv_frontier_workspace_size")
+        self.ws = _workspace(nb, L_bf16.device)
+        self.X = torch.zeros((self.nt, L_bf16.shape[0]), dtype=torch.float64, device=L_bf16.device)
+
+    def solve(self, allow=(MV_ERR_NOT_CONVERGED,)):
+        infos = (SolveInfo * self.nt)()
+        st = lib().mv_npga_solve_frontier(C.byref(self.problem), _ptr(self.Rt), self.nt, C.byref(self.opts),
+                                          _ptr(self.X), infos, _ptr(self.ws), self.ws.numel(), _stream())
+        _check(st, "mv_npga_solve_frontier", allow)
+        return self.X, [i.as_dict() for i in infos]

@@ -1,0 +1,54 @@
+"""GPU parity of the batched efficient-frontier solve (one BF16 factor, many
+targets; skinny tcgen05 GEMMs) against the FP64 oracle on the same BF16
+matrix.  Besides per-target parity, the frontier must be monotone: with the
+return row active, the minimum variance cannot decrease as the target rises."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from synth import CFG_FULL, CFG_SMALL, factor_returns, power_start
+from oracle.center import center_factor
+from oracle.npga import initial_point, npga, objective, power_norm2, step_size
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mv():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_02917_gb300 import mv as m
+    m.lib()
+    return m
+
+
+def oracle_opt(L64, mu, Rt):
+    lam = power_norm2(L64, power_start(L64.shape[0]), 300)
+    return npga(L64, 0.0, mu, Rt, initial_point(mu, Rt), step_size(lam, 0.0), eps=1e-11, max_iter=200000)
+
+
+@pytest.mark.parametrize("model,nt", [(CFG_SMALL, 64), (CFG_FULL.scaled(700, 3001, seed=61), 5)])
+def test_frontier_parity(mv, model, nt):
+    R = factor_returns(model, np.float32)
+    Lb, _, mu, _ = mv.center_factor(torch.from_numpy(R).cuda(), "bf16")
+    mu_o = center_factor(R.astype(np.float64))[0]
+    targets = np.linspace(np.percentile(mu_o, 10), np.percentile(mu_o, 90), nt)
+    fs = mv.FrontierSolver(Lb, mu, targets, model.T, eps=1e-7)
+    X, infos = fs.solve()
+    X = X.cpu().numpy()
+    assert all(i["converged"] == 1 for i in infos)
+    Lq = Lb[:, :model.T].float().double().cpu().numpy()      # the BF16 model the GPU holds
+    f = np.array([objective(Lq, 0.0, X[b]) for b in range(nt)])
+    for b in range(nt):
+        assert X[b].min() >= 0 and abs(X[b].sum() - 1) < 1e-12 and mu_o @ X[b] >= targets[b] - 1e-15
+        assert infos[b]["objective"] == pytest.approx(f[b], rel=1e-4)
+    check = range(nt) if nt <= 8 else range(0, nt, 9)
+    for b in check:
+        ref = oracle_opt(Lq, mu_o, targets[b])
+        assert np.max(np.abs(X[b] - ref.x)) <= 1e-4
+        assert (f[b] - ref.f) / ref.f <= 1e-5
+    # monotone frontier where the return row binds
+    active = [b for b in range(nt) if abs(mu_o @ X[b] - targets[b]) < 1e-12]
+    fa = f[active]
+    assert np.all(np.diff(fa) >= -1e-12 * fa.max())
