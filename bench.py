@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP8 + FP32-refinement lines")
     ap.add_argument("--no-str", action="store_true", help="skip the sketch / STR measurement")
     ap.add_argument("--sketch-m", type=int, default=8192)
+    ap.add_argument("--no-frontier", action="store_true", help="skip the 64-target frontier measurement")
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -387,6 +388,42 @@ def main():
                    "build_plus_solve_s": (min(sk_ms) + tr_ms + s_ms) / 1e3}
         del Lb, Phi_t, Ls, L_eff, ssv
 
+    # 64-point efficient frontier (shared BF16 factor, skinny tcgen05 GEMMs).
+    frontier = None
+    if not args.no_frontier and args.dtype == "f32":
+        from synth import CFG_SMALL
+        frontier = {}
+        for tag, fm in (("200x1000", CFG_SMALL), ("full_shape", model)):
+            Rf = factor_returns(fm, np.float32) if fm is not model else R32
+            Rfd = torch.from_numpy(Rf).to(dev)
+            Lfb, _, muf, _ = mv.center_factor(Rfd, "bf16")
+            muh = muf.cpu().numpy()
+            targets = np.linspace(np.percentile(muh, 10), np.percentile(muh, 90), 64)
+            fsv = mv.FrontierSolver(Lfb, muf, targets, fm.T, eps=args.eps)
+            fsv.solve()
+            torch.cuda.synchronize()
+            reps = 3 if tag == "full_shape" else 5
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(reps):
+                _, finfo = fsv.solve()
+            f1.record(stream)
+            torch.cuda.synchronize()
+            entry = {"targets": 64, "value": f0.elapsed_time(f1) / reps / 1e3, "unit": "s",
+                     "max_iterations": max(i["iterations"] for i in finfo),
+                     "all_converged": all(i["converged"] == 1 for i in finfo), "dtype": "bf16"}
+            if tag == "200x1000":
+                # the same 64 targets as independent FP32 solves, one after another
+                Lf32, _, _, _ = mv.center_factor(Rfd, "f32")
+                t0 = time.perf_counter()
+                for r in targets:
+                    mv.npga_solve(Lf32, muf, float(r), fm.T, eps=args.eps)
+                torch.cuda.synchronize()
+                entry["fp32_sequential_64_solves_s"] = time.perf_counter() - t0
+                del Lf32
+            frontier[tag] = entry
+            del Rfd, Lfb, fsv
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = int(np.median([i["iterations"] for i in infos]))
@@ -406,7 +443,7 @@ def main():
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "variants": variants, "str": str_res}
+                "variants": variants, "str": str_res, "frontier": frontier}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
