@@ -170,6 +170,8 @@ typedef struct {
     int32_t use_graph;        /* 1 (default): replay iterations as a CUDA graph          */
     int32_t timing;           /* 1: time every loop launch with CUDA events (kernels are
                                  then issued from the host instead of a graph)           */
+    int32_t checkpoint_every; /* mv_npga_backward: iterations between checkpoints (50)   */
+    int32_t reserved;
 } mv_solve_opts;
 
 typedef struct {
@@ -285,6 +287,30 @@ int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void
                   int64_t ldP, int64_t k, double gamma, double trace_sigma, float *d_L_sketch, int64_t ldS,
                   float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out, void *d_ws,
                   size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * 3f. Adjoint of the unrolled solve (an extension; the paper does not
+ *     differentiate its solver).
+ *
+ *  The forward is Algorithm 1 unrolled for exactly K = opts->max_iter
+ *  iterations (no early stop; mv_npga_solve with the same opts and eps = 0,
+ *  kkt_every = 0 gives the same x_K) from x^0 = d_x0 (NULL: Pi_F(1/n 1)),
+ *  with alpha from opts (power method or override).  alpha, x^0 and
+ *  R_target are treated as constants.  Given d loss / d x_K, the call returns
+ *      d_dmu [out] n FP64  d loss / d mu  (through the projection's return row)
+ *      d_dL  [out] n x ldD FP32  d loss / d L  (overwritten)
+ *  Reverse sweep: the forward is recomputed segment by segment from
+ *  checkpoints taken every opts->checkpoint_every iterations; each backward
+ *  step applies the projection's Jacobian on the active set
+ *  (P = I - C (C^T C)^{-1} C^T on the support, C = [1, mu] or [1]) and the
+ *  transposed products (two GEMV passes); dL accumulates
+ *  -2 alpha (v_bar z_k^T + y_k (L^T v_bar)^T) per segment with one FP32 GEMM
+ *  (cuBLAS SGEMM, loaded at run time).  FP32 factor only.  Blocking.
+ * ------------------------------------------------------------------------ */
+size_t mv_backward_workspace_size(const mv_problem *P, const mv_solve_opts *opts);
+int mv_npga_backward(const mv_problem *P, const mv_solve_opts *opts, const double *d_x0,
+                     const double *d_dloss_dx, double *d_dmu, float *d_dL, int64_t ldD,
+                     mv_solve_info *h_info, void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * 4. Gradient building block (Eq. npga-unified-grad), exposed for tests and

@@ -26,6 +26,8 @@ typedef int (*fn_cublasCreate)(void **);
 typedef int (*fn_cublasSetStream)(void *, cudaStream_t);
 typedef int (*fn_cublasDsyrk)(void *, int, int, int, int, const double *, const double *, int, const double *,
                               double *, int);
+typedef int (*fn_cublasSgemm)(void *, int, int, int, int, int, const float *, const float *, int, const float *, int,
+                              const float *, float *, int);
 typedef int (*fn_cusolverCreate)(void **);
 typedef int (*fn_cusolverSetStream)(void *, cudaStream_t);
 typedef int (*fn_syevdx_bs)(void *, int, int, int, int, const double *, int, double, double, int, int, int *,
@@ -40,6 +42,7 @@ struct Linalg {
     void *hb = nullptr, *hs = nullptr;
     fn_cublasSetStream b_set_stream = nullptr;
     fn_cublasDsyrk dsyrk = nullptr;
+    fn_cublasSgemm sgemm = nullptr;
     fn_cusolverSetStream s_set_stream = nullptr;
     fn_syevdx_bs syevdx_bs = nullptr;
     fn_syevdx syevdx = nullptr;
@@ -67,16 +70,29 @@ static Linalg *linalg() {
         auto bcreate = (fn_cublasCreate)dlsym(lb, "cublasCreate_v2");
         L.b_set_stream = (fn_cublasSetStream)dlsym(lb, "cublasSetStream_v2");
         L.dsyrk = (fn_cublasDsyrk)dlsym(lb, "cublasDsyrk_v2");
+        L.sgemm = (fn_cublasSgemm)dlsym(lb, "cublasSgemm_v2");
         auto screate = (fn_cusolverCreate)dlsym(ls, "cusolverDnCreate");
         L.s_set_stream = (fn_cusolverSetStream)dlsym(ls, "cusolverDnSetStream");
         L.syevdx_bs = (fn_syevdx_bs)dlsym(ls, "cusolverDnDsyevdx_bufferSize");
         L.syevdx = (fn_syevdx)dlsym(ls, "cusolverDnDsyevdx");
-        if (!bcreate || !L.b_set_stream || !L.dsyrk || !screate || !L.s_set_stream || !L.syevdx_bs || !L.syevdx)
+        if (!bcreate || !L.b_set_stream || !L.dsyrk || !L.sgemm || !screate || !L.s_set_stream || !L.syevdx_bs || !L.syevdx)
             return;
         if (bcreate(&L.hb) != 0 || screate(&L.hs) != 0) return;
         L.ok = true;
     });
     return L.ok ? &L : nullptr;
+}
+
+// Column-major C (m x n) = alpha A B^T + beta C with A m x k, B n x k
+// (cuBLAS SGEMM; a plain library GEMM used by the adjoint's dL update).
+int linalg_sgemm_nt(cudaStream_t s, int m, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
+                    float beta, float *C, int ldc) {
+    Linalg *L = linalg();
+    if (!L) return record_message(MV_ERR_UNSUPPORTED, "cuBLAS not found");
+    if (L->b_set_stream(L->hb, s) != 0) return record_message(MV_ERR_CUDA, "cublasSetStream failed");
+    if (L->sgemm(L->hb, 0, kOpT, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc) != 0)
+        return record_message(MV_ERR_CUDA, "cublasSgemm failed");
+    return MV_OK;
 }
 
 // ------------------------------------------------------------------ kernels

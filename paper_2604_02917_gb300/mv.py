@@ -31,7 +31,8 @@ EXPORTS = [
     "mv_status_string", "mv_version", "mv_center_workspace_size", "mv_center_factor", "mv_project",
     "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
     "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
-    "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier",
+    "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
+    "mv_npga_backward",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -63,7 +64,8 @@ class Problem(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("kkt_every", C.c_int32), ("power_iters", C.c_int32),
                 ("warm_start", C.c_int32), ("eps", C.c_double), ("power_safety", C.c_double),
-                ("alpha", C.c_double), ("use_graph", C.c_int32), ("timing", C.c_int32)]
+                ("alpha", C.c_double), ("use_graph", C.c_int32), ("timing", C.c_int32),
+                ("checkpoint_every", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -124,6 +126,11 @@ def lib():
         L.mv_npga_solve_frontier.restype = i32
         L.mv_npga_solve_frontier.argtypes = [C.POINTER(Problem), vp, i64, C.POINTER(SolveOpts), vp,
                                              C.POINTER(SolveInfo), vp, sz, vp]
+        L.mv_backward_workspace_size.restype = sz
+        L.mv_backward_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(SolveOpts)]
+        L.mv_npga_backward.restype = i32
+        L.mv_npga_backward.argtypes = [C.POINTER(Problem), C.POINTER(SolveOpts), vp, vp, vp, vp, i64,
+                                       C.POINTER(SolveInfo), vp, sz, vp]
         L.mv_sketch.restype = i32
         L.mv_sketch.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
         L.mv_gradient_noalloc.restype = i32
@@ -389,3 +396,45 @@ class FrontierSolver:
                                           _ptr(self.X), infos, _ptr(self.ws), self.ws.numel(), _stream())
         _check(st, "mv_npga_solve_frontier", allow)
         return self.X, [i.as_dict() for i in infos]
+
+
+def npga_backward(L, mu, R_target, T, dloss_dx, iters, gamma=0.0, mode="ge", x0=None, power_start=None,
+                  checkpoint_every=50, **opts):
+    """(d loss/d mu, d loss/d L, info) of the K-iteration unrolled solve (mv_npga_backward)."""
+    p = make_problem(L, mu, R_target, T, gamma, "f32", None, mode, power_start)
+    o = solve_opts(max_iter=int(iters), checkpoint_every=int(checkpoint_every), eps=0.0, kkt_every=0, **opts)
+    nb = lib().mv_backward_workspace_size(C.byref(p), C.byref(o))
+    if nb == 0:
+        raise MvError(MV_ERR_INVALID_ARG, "mv_backward_workspace_size")
+    ws = _workspace(nb, L.device)
+    dmu = torch.empty(L.shape[0], dtype=torch.float64, device=L.device)
+    dL = torch.empty_like(L)
+    info = SolveInfo()
+    _check(lib().mv_npga_backward(C.byref(p), C.byref(o), _ptr(x0), _ptr(dloss_dx.contiguous()), _ptr(dmu),
+                                  _ptr(dL), L.stride(0), C.byref(info), _ptr(ws), ws.numel(), _stream()),
+           "mv_npga_backward")
+    return dmu, dL, info.as_dict()
+
+
+class NPGAFunction(torch.autograd.Function):
+    """x_K = NPGA unrolled for `iters` iterations, differentiable in mu and L.
+
+    forward(L, mu, R_target, T, iters, gamma, checkpoint_every) runs
+    mv_npga_solve with eps = 0 and no KKT checks (exactly `iters`
+    iterations); backward calls mv_npga_backward.  alpha (power method), x^0
+    and R_target are constants, as in the adjoint's conventions."""
+
+    @staticmethod
+    def forward(ctx, L, mu, R_target, T, iters, gamma=0.0, checkpoint_every=50):
+        x, info = npga_solve(L, mu, R_target, T, gamma=gamma, eps=0.0, kkt_every=0, max_iter=int(iters))
+        ctx.save_for_backward(L, mu)
+        ctx.args = (float(R_target), int(T), int(iters), float(gamma), int(checkpoint_every))
+        return x.clone()
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        L, mu = ctx.saved_tensors
+        R_target, T, iters, gamma, ck = ctx.args
+        dmu, dL, _ = npga_backward(L, mu, R_target, T, grad_x.to(torch.float64), iters, gamma=gamma,
+                                   checkpoint_every=ck)
+        return dL, dmu, None, None, None, None, None

@@ -56,7 +56,7 @@ def _c_layout(tmp_path):
         "mv_problem": ["L", "dtype", "mode", "row_scale", "n", "T", "ld", "gamma", "mu", "R_target",
                        "power_start"],
         "mv_solve_opts": ["max_iter", "kkt_every", "power_iters", "warm_start", "eps", "power_safety",
-                          "alpha", "use_graph", "timing"],
+                          "alpha", "use_graph", "timing", "checkpoint_every", "reserved"],
         "mv_solve_info": ["iterations", "status", "converged", "proj_failures", "kkt", "objective",
                           "alpha", "lambda_hat", "nu", "launches", "timed_pairs", "t_gemv_t_ms",
                           "t_gemv_n_ms", "t_step_ms", "proj_steps", "refine_iterations"],
