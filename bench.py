@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-str", action="store_true", help="skip the sketch / STR measurement")
     ap.add_argument("--sketch-m", type=int, default=8192)
     ap.add_argument("--no-frontier", action="store_true", help="skip the 64-target frontier measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -424,6 +425,31 @@ def main():
             frontier[tag] = entry
             del Rfd, Lfb, fsv
 
+    # Adjoint of 500 unrolled iterations at 2000 x 10000 (checkpoints every 50).
+    adj = None
+    if not args.no_adjoint and args.dtype == "f32":
+        from synth import CFG_SMALL
+        am = CFG_SMALL.scaled(2000, 10000, seed=0)
+        Ra = factor_returns(am, np.float32)
+        La, _, mua, _ = mv.center_factor(torch.from_numpy(Ra).to(dev), "f32")
+        Rta = float(np.percentile(mua.cpu().numpy(), 60))
+        K = 500
+        g = torch.randn(am.n, dtype=torch.float64, device=dev, generator=torch.Generator(device=dev).manual_seed(0))
+        mv.npga_solve(La, mua, Rta, am.T, eps=0.0, kkt_every=0, max_iter=K)
+        mv.npga_backward(La, mua, Rta, am.T, g, K, checkpoint_every=50)
+        torch.cuda.synchronize()
+        a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a0.record(stream)
+        mv.npga_solve(La, mua, Rta, am.T, eps=0.0, kkt_every=0, max_iter=K)
+        a1.record(stream)
+        mv.npga_backward(La, mua, Rta, am.T, g, K, checkpoint_every=50)
+        a2.record(stream)
+        torch.cuda.synchronize()
+        fwd, bwd = a0.elapsed_time(a1), a1.elapsed_time(a2)
+        adj = {"n": am.n, "T": am.T, "iterations": K, "checkpoint_every": 50, "forward_s": fwd / 1e3,
+               "backward_s": bwd / 1e3, "backward_over_forward": bwd / fwd}
+        del La, Ra
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = int(np.median([i["iterations"] for i in infos]))
@@ -443,7 +469,7 @@ def main():
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "variants": variants, "str": str_res, "frontier": frontier}
+                "variants": variants, "str": str_res, "frontier": frontier, "adjoint": adj}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -247,6 +247,28 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
                            void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * 3g. Batch of independent problems of uneven size (n_i, T_i all different).
+ *
+ *  Solves count problems (same dtype; each with its own L, n, T, ld, gamma,
+ *  mu, R_target, mode and power start) with the semantics of mv_npga_solve,
+ *  in lock-step: each GEMV half-product is ONE grouped launch over a tile
+ *  list that spans every problem's grid (row splits of 512 rows), and each
+ *  projection step is one launch with one thread-block cluster per problem.
+ *  Each problem has its own step size, FISTA state and KKT test; a converged
+ *  problem's tiles return at once.  Chunks of kkt_every iterations replay as
+ *  one CUDA graph.
+ *  h_x_dev [in]  host array of count device pointers; x_i (n_i FP64) is
+ *                written to h_x_dev[i] on return.
+ *  h_infos [out] count host mv_solve_info.
+ *  Workspace: mv_batch_workspace_size(probs, count).  Returns the first
+ *  non-OK per-problem status (or MV_OK).  Blocking.
+ * ------------------------------------------------------------------------ */
+size_t mv_batch_workspace_size(const mv_problem *probs, int64_t count);
+int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_opts *opts,
+                        double *const *h_x_dev, mv_solve_info *h_infos, void *d_ws, size_t ws_bytes,
+                        mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * 3c. Sketch (Sec. 2.3; STR step 1 of Sec. 2.5):  tilde L = L Phi.
  *
  *  A BF16 x BF16 -> FP32 GEMM on the tcgen05 tensor cores (accumulator in

@@ -32,25 +32,24 @@ constexpr int kGemvThreads = 256;
 constexpr int kGemvUnroll = 8;
 constexpr int kMaxRowsPerSplit = 2048;
 
+// One block of z = L^T y: column strip `strip`, row split `split` of `nsplits`.
 template <int DT>
-__global__ void __launch_bounds__(kGemvThreads)
-gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ y32,
-              float *__restrict__ zpart, int64_t zstride, float *__restrict__ z, unsigned *__restrict__ tickets,
-              int rows_per_split, const volatile int *done) {
+__device__ __forceinline__ void gemv_t_body(const void *__restrict__ L, int64_t ld, int n, int T,
+                                            const float *__restrict__ y32, float *__restrict__ zpart, int64_t zstride,
+                                            float *__restrict__ z, unsigned *__restrict__ tickets, int rows_per_split,
+                                            int strip, int split, int nsplits) {
     using S = Store<DT>;
     constexpr int VEC = S::VEC;
     constexpr int ES = (int)sizeof(typename S::elem);
-    if (done != nullptr && *done) return;
     __shared__ float s_y[kMaxRowsPerSplit];
     __shared__ bool s_last;
 
-    const int split = blockIdx.y;
     const int r0 = split * rows_per_split;
     const int rows = min(n - r0, rows_per_split);
     for (int i = threadIdx.x; i < rows; i += kGemvThreads) s_y[i] = y32[r0 + i];
     __syncthreads();
 
-    const int64_t col = ((int64_t)blockIdx.x * kGemvThreads + threadIdx.x) * VEC;
+    const int64_t col = ((int64_t)strip * kGemvThreads + threadIdx.x) * VEC;
     float acc[VEC];
 #pragma unroll
     for (int e = 0; e < VEC; ++e) acc[e] = 0.f;
@@ -105,15 +104,15 @@ gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float 
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(&tickets[blockIdx.x], 1u);
-        s_last = (ticket == gridDim.y - 1);
+        const unsigned ticket = atomicAdd(&tickets[strip], 1u);
+        s_last = (ticket == (unsigned)nsplits - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     // Last block of the strip: add the splits in fixed order, 4 splits of
     // 16-byte loads in flight at a time.
-    const int splits = gridDim.y;
+    const int splits = nsplits;
     if (full) {
         float sacc[VEC];
 #pragma unroll
@@ -159,29 +158,39 @@ gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float 
             }
         }
     }
-    if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;   // ready for the next launch
+    if (threadIdx.x == 0) tickets[strip] = 0u;   // ready for the next launch
 }
 
-template <int DT, int RW>
+template <int DT>
 __global__ void __launch_bounds__(kGemvThreads)
-gemv_n_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ z,
-              const float *__restrict__ row_scale, float *__restrict__ gpart, double *__restrict__ g,
-              float *__restrict__ g32, unsigned *__restrict__ tickets, int cols_per_split, const volatile int *done) {
+gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ y32,
+              float *__restrict__ zpart, int64_t zstride, float *__restrict__ z, unsigned *__restrict__ tickets,
+              int rows_per_split, const volatile int *done) {
+    if (done != nullptr && *done) return;
+    gemv_t_body<DT>(L, ld, n, T, y32, zpart, zstride, z, tickets, rows_per_split, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// One block of g = L z: row group `grp`, column split `split` of `nsplits`.
+template <int DT, int RW>
+__device__ __forceinline__ void gemv_n_body(const void *__restrict__ L, int64_t ld, int n, int T,
+                                            const float *__restrict__ z, const float *__restrict__ row_scale,
+                                            float *__restrict__ gpart, double *__restrict__ g, float *__restrict__ g32,
+                                            unsigned *__restrict__ tickets, int cols_per_split, int grp, int split,
+                                            int nsplits) {
     using S = Store<DT>;
     constexpr int VEC = S::VEC;
     constexpr int ES = (int)sizeof(typename S::elem);
     constexpr int ROWS = (kGemvThreads / kWarp) * RW;
-    if (done != nullptr && *done) return;
     extern __shared__ float s_z[];
     __shared__ bool s_last;
 
-    const int c0 = blockIdx.y * cols_per_split;
+    const int c0 = split * cols_per_split;
     const int ncol = min(T - c0, cols_per_split);
     for (int c = threadIdx.x; c < ncol; c += kGemvThreads) s_z[c] = z[c0 + c];
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rbase = blockIdx.x * ROWS + warp * RW;
+    const int rbase = grp * ROWS + warp * RW;
     float acc[RW];
     const char *rp[RW];
 #pragma unroll
@@ -225,26 +234,78 @@ gemv_n_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float 
     if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < RW; ++j)
-            if (rbase + j < n) gpart[(int64_t)blockIdx.y * n + rbase + j] = acc[j];
+            if (rbase + j < n) gpart[(int64_t)split * n + rbase + j] = acc[j];
     }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned ticket = atomicAdd(&tickets[blockIdx.x], 1u);
-        s_last = (ticket == gridDim.y - 1);
+        const unsigned ticket = atomicAdd(&tickets[grp], 1u);
+        s_last = (ticket == (unsigned)nsplits - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    const int splits = gridDim.y;
-    for (int r = blockIdx.x * ROWS + threadIdx.x; r < min(n, (int)(blockIdx.x + 1) * ROWS); r += kGemvThreads) {
+    const int splits = nsplits;
+    for (int r = grp * ROWS + threadIdx.x; r < min(n, (grp + 1) * ROWS); r += kGemvThreads) {
         double s = 0.0;
         for (int sp = 0; sp < splits; ++sp) s += (double)__ldcg(gpart + (int64_t)sp * n + r);
         if (row_scale != nullptr) s *= (double)row_scale[r];
         g[r] = s;
         if (g32 != nullptr) g32[r] = (float)s;
     }
-    if (threadIdx.x == 0) tickets[blockIdx.x] = 0u;
+    if (threadIdx.x == 0) tickets[grp] = 0u;
+}
+
+template <int DT, int RW>
+__global__ void __launch_bounds__(kGemvThreads)
+gemv_n_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ z,
+              const float *__restrict__ row_scale, float *__restrict__ gpart, double *__restrict__ g,
+              float *__restrict__ g32, unsigned *__restrict__ tickets, int cols_per_split, const volatile int *done) {
+    if (done != nullptr && *done) return;
+    gemv_n_body<DT, RW>(L, ld, n, T, z, row_scale, gpart, g, g32, tickets, cols_per_split, blockIdx.x, blockIdx.y,
+                        gridDim.y);
+}
+
+// ---------------------------------------------------------------- grouped form
+// Many independent problems in one launch: block b runs tile tiles[b] =
+// (problem, strip or row group, split) of the problem's own grid, skipping
+// problems whose `done` flag is set.
+struct GemvProb {
+    const void *L;
+    int64_t ld;
+    int n, T;
+    const float *y32;
+    float *zpart;
+    int64_t zstride;
+    float *z;
+    unsigned *tick_t;
+    int t_rows, t_splits;
+    float *gpart;
+    double *gy;
+    float *g32;
+    unsigned *tick_n;
+    int n_cols, n_splits;
+    const float *row_scale;
+    const int *done;
+};
+
+template <int DT>
+__global__ void __launch_bounds__(kGemvThreads)
+gemv_t_grouped(const GemvProb *__restrict__ probs, const int4 *__restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const GemvProb &p = probs[t.x];
+    if (*(const volatile int *)p.done) return;
+    gemv_t_body<DT>(p.L, p.ld, p.n, p.T, p.y32, p.zpart, p.zstride, p.z, p.tick_t, p.t_rows, t.y, t.z, p.t_splits);
+}
+
+template <int DT, int RW>
+__global__ void __launch_bounds__(kGemvThreads)
+gemv_n_grouped(const GemvProb *__restrict__ probs, const int4 *__restrict__ tiles) {
+    const int4 t = tiles[blockIdx.x];
+    const GemvProb &p = probs[t.x];
+    if (*(const volatile int *)p.done) return;
+    gemv_n_body<DT, RW>(p.L, p.ld, p.n, p.T, p.z, p.row_scale, p.gpart, p.gy, p.g32, p.tick_n, p.n_cols, t.y, t.z,
+                        p.n_splits);
 }
 
 }  // namespace mv

@@ -62,7 +62,7 @@ static int sm_count() {
 
 static constexpr int kRW = 4;   // rows per warp in gemv_n
 
-static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld) {
+static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows = 0) {
     Plan p{};
     p.dt = dt;
     p.esize = dtype_size(dt);
@@ -84,6 +84,7 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld) {
     const int slots = sms * 4;
     int splits = (slots * 3 + p.t_blocks - 1) / p.t_blocks;
     splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, (n + 63) / 64));
+    if (grouped_rows > 0) splits = (int)((n + grouped_rows - 1) / grouped_rows);   // many problems share the GPU
     int rows = (int)((n + splits - 1) / splits);
     if (rows > kMaxRowsPerSplit) rows = kMaxRowsPerSplit;
     p.t_rows = rows;
@@ -123,8 +124,7 @@ static T_ *at(void *ws, size_t off) {
 }
 
 // ------------------------------------------------------------------ kernels
-__global__ void __launch_bounds__(kStepThreads)
-setup_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ r0,
+__device__ __forceinline__ void setup_body(SolveState *st, const double *__restrict__ mu, const double *__restrict__ r0,
              const float *__restrict__ row_scale, float *__restrict__ y32, int n) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
     double mn = INFINITY, mx = -INFINITY, ss = 0.0;
@@ -156,10 +156,15 @@ setup_kernel(SolveState *st, const double *__restrict__ mu, const double *__rest
     }
 }
 
+__global__ void __launch_bounds__(kStepThreads)
+setup_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ r0,
+             const float *__restrict__ row_scale, float *__restrict__ y32, int n) {
+    setup_body(st, mu, r0, row_scale, y32, n);
+}
+
 // u <- g / ||g|| (power method) from the FP32 copy of g, written as the FP32
 // gemv input (row-scaled).  FP32 arithmetic: u only sets the direction.
-__global__ void __launch_bounds__(kStepThreads)
-power_norm_kernel(const float *__restrict__ g32, const float *__restrict__ row_scale, float *__restrict__ y32,
+__device__ __forceinline__ void power_norm_body(const float *__restrict__ g32, const float *__restrict__ row_scale, float *__restrict__ y32,
                   int n) {
     __shared__ float red[kStepThreads / kWarp + 1];
     float ss = 0.f;
@@ -179,6 +184,12 @@ power_norm_kernel(const float *__restrict__ g32, const float *__restrict__ row_s
         y32[i] = g32[i] * inv * (row_scale ? row_scale[i] : 1.f);
 }
 
+__global__ void __launch_bounds__(kStepThreads)
+power_norm_kernel(const float *__restrict__ g32, const float *__restrict__ row_scale, float *__restrict__ y32,
+                  int n) {
+    power_norm_body(g32, row_scale, y32, n);
+}
+
 // Compensated FP32 sum of squares of an FP32 vector; FP64 only across threads.
 __device__ __forceinline__ double sumsq_f32(const float *__restrict__ z, int T, double *red) {
     float s = 0.f, c = 0.f;
@@ -194,8 +205,7 @@ __device__ __forceinline__ double sumsq_f32(const float *__restrict__ z, int T, 
 }
 
 // lambda_hat = ||L^T u||^2; alpha = 1 / (2 (lambda_hat (1 + safety) + gamma)).
-__global__ void __launch_bounds__(kStepThreads)
-step_size_kernel(SolveState *st, const float *__restrict__ z, int T, double gamma, double safety,
+__device__ __forceinline__ void step_size_body(SolveState *st, const float *__restrict__ z, int T, double gamma, double safety,
                  double alpha_override) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
     const double lam = sumsq_f32(z, T, red);
@@ -211,15 +221,20 @@ step_size_kernel(SolveState *st, const float *__restrict__ z, int T, double gamm
     }
 }
 
+__global__ void __launch_bounds__(kStepThreads)
+step_size_kernel(SolveState *st, const float *__restrict__ z, int T, double gamma, double safety,
+                 double alpha_override) {
+    step_size_body(st, z, T, gamma, safety, alpha_override);
+}
+
 // x^0: Pi_F(1/n 1), or the caller's x^0 when warm-starting; y^0 = x^0.
 // Runs as one cluster of CL blocks (the projection of project.cuh).
 template <int CL>
-__global__ void __launch_bounds__(kProjNT)
-init_x_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ x_in,
-              double *__restrict__ x, double *__restrict__ y, float *__restrict__ y32,
-              const float *__restrict__ row_scale, int n, double R, int mode) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ ProjSmem psm;
+__device__ __forceinline__ void init_x_body(SolveState *st, const double *__restrict__ mu,
+                                            const double *__restrict__ x_in, double *__restrict__ x,
+                                            double *__restrict__ y, float *__restrict__ y32,
+                                            const float *__restrict__ row_scale, int n, double R, int mode,
+                                            unsigned char *dsm, ProjSmem &psm) {
     const int rank = cluster_rank<CL>();
     const int nl = (n + CL - 1) / CL;
     const int r0 = min(n, rank * nl);
@@ -277,6 +292,16 @@ init_x_kernel(SolveState *st, const double *__restrict__ mu, const double *__res
     }
 }
 
+template <int CL>
+__global__ void __launch_bounds__(kProjNT)
+init_x_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ x_in,
+              double *__restrict__ x, double *__restrict__ y, float *__restrict__ y32,
+              const float *__restrict__ row_scale, int n, double R, int mode) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ ProjSmem psm;
+    init_x_body<CL>(st, mu, x_in, x, y, y32, row_scale, n, R, mode, dsm, psm);
+}
+
 struct StepArgs {
     SolveState *st;
     const double *gy;
@@ -290,9 +315,7 @@ struct StepArgs {
 
 // One NPGA step on a cluster of CL blocks; block r owns assets [r0, r1).
 template <int CL>
-__global__ void __launch_bounds__(kProjNT) npga_step_kernel(StepArgs a) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ ProjSmem psm;
+__device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char *dsm, ProjSmem &psm) {
     SolveState *st = a.st;
     // Every block reads the flag before the first cluster barrier; the flag is
     // only written after later barriers, so the whole cluster agrees.
@@ -399,6 +422,22 @@ __global__ void __launch_bounds__(kProjNT) npga_step_kernel(StepArgs a) {
     cluster_barrier<CL>();   // no block leaves while a peer may still address its shared memory
 }
 
+template <int CL>
+__global__ void __launch_bounds__(kProjNT) npga_step_kernel(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ ProjSmem psm;
+    npga_step_body<CL>(a, dsm, psm);
+}
+
+// Grouped form: cluster b runs the step of problem b.
+template <int CL>
+__global__ void __launch_bounds__(kProjNT) npga_step_grouped(const StepArgs *__restrict__ args) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ ProjSmem psm;
+    const StepArgs a = args[blockIdx.x / CL];
+    npga_step_body<CL>(a, dsm, psm);
+}
+
 // FP64 n-vector -> scaled FP32 gemv input.
 __global__ void to_y32_kernel(const double *__restrict__ x, const float *__restrict__ row_scale,
                               float *__restrict__ y32, int n) {
@@ -407,8 +446,7 @@ __global__ void to_y32_kernel(const double *__restrict__ x, const float *__restr
 }
 
 // f(x) = ||z||^2 + gamma ||x||^2 with z = L^T x.
-__global__ void __launch_bounds__(kStepThreads)
-objective_kernel(SolveState *st, const float *__restrict__ z, int T, const double *__restrict__ x, int n,
+__device__ __forceinline__ void objective_body(SolveState *st, const float *__restrict__ z, int T, const double *__restrict__ x, int n,
                  double gamma) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
     const double zz = sumsq_f32(z, T, red);
@@ -417,6 +455,12 @@ objective_kernel(SolveState *st, const float *__restrict__ z, int T, const doubl
         for (int i = threadIdx.x; i < n; i += kStepThreads) s[0] = fma(x[i], x[i], s[0]);
     block_sum<1, kStepThreads>(s, red);
     if (threadIdx.x == 0) st->objective = zz + gamma * s[0];
+}
+
+__global__ void __launch_bounds__(kStepThreads)
+objective_kernel(SolveState *st, const float *__restrict__ z, int T, const double *__restrict__ x, int n,
+                 double gamma) {
+    objective_body(st, z, T, x, n, gamma);
 }
 
 // g = 2 (L z) + 2 gamma y   (gradient building block output).
@@ -1665,6 +1709,389 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     h_info->kkt = hs.kkt;
     h_info->launches = launches;
     return MV_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batch of independent problems of uneven size in one launch per kernel:
+// the GEMV pair runs as one grouped launch over a tile list spanning every
+// problem, the projection step as one launch of one cluster per problem.
+namespace mv {
+
+struct GOne {
+    SolveState *st;
+    const double *mu, *r0, *x_in;
+    const float *row_scale;
+    float *y32;
+    const float *g32, *z;
+    double *x, *y;
+    int n, T, mode;
+    double gamma, safety, alpha_override, R;
+};
+
+__global__ void __launch_bounds__(kStepThreads) setup_grouped(const GOne *__restrict__ A) {
+    const GOne a = A[blockIdx.x];
+    setup_body(a.st, a.mu, a.r0, a.row_scale, a.y32, a.n);
+}
+__global__ void __launch_bounds__(kStepThreads) power_norm_grouped(const GOne *__restrict__ A) {
+    const GOne a = A[blockIdx.x];
+    power_norm_body(a.g32, a.row_scale, a.y32, a.n);
+}
+__global__ void __launch_bounds__(kStepThreads) step_size_grouped(const GOne *__restrict__ A) {
+    const GOne a = A[blockIdx.x];
+    step_size_body(a.st, a.z, a.alpha_override > 0.0 ? 0 : a.T, a.gamma, a.safety, a.alpha_override);
+}
+__global__ void __launch_bounds__(kStepThreads) objective_grouped(const GOne *__restrict__ A) {
+    const GOne a = A[blockIdx.x];
+    objective_body(a.st, a.z, a.T, a.x, a.n, a.gamma);
+}
+__global__ void __launch_bounds__(kStepThreads) to_y32_grouped(const GOne *__restrict__ A) {
+    const GOne a = A[blockIdx.x];
+    for (int i = threadIdx.x; i < a.n; i += kStepThreads)
+        a.y32[i] = (float)(a.x[i] * (a.row_scale ? (double)a.row_scale[i] : 1.0));
+}
+template <int CL>
+__global__ void __launch_bounds__(kProjNT) init_x_grouped(const GOne *__restrict__ A) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ ProjSmem psm;
+    const GOne a = A[blockIdx.x / CL];
+    init_x_body<CL>(a.st, a.mu, a.x_in, a.x, a.y, a.y32, a.row_scale, a.n, a.R, a.mode, dsm, psm);
+}
+
+template <typename Kern, typename Arg>
+static cudaError_t launch_clusters(Kern kern, int CL, int count, size_t smem, cudaStream_t s, Arg arg) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(count * CL));
+    cfg.blockDim = dim3(kProjNT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
+static int batch_attrs() {
+    static std::once_flag once;
+    static int st = MV_OK;
+    std::call_once(once, [] {
+        bool ok = cluster_attrs(npga_step_grouped<1>, 1) && cluster_attrs(npga_step_grouped<2>, 2) &&
+                  cluster_attrs(npga_step_grouped<4>, 4) && cluster_attrs(npga_step_grouped<8>, 8) &&
+                  cluster_attrs(npga_step_grouped<16>, 16) && cluster_attrs(init_x_grouped<1>, 1) &&
+                  cluster_attrs(init_x_grouped<2>, 2) && cluster_attrs(init_x_grouped<4>, 4) &&
+                  cluster_attrs(init_x_grouped<8>, 8) && cluster_attrs(init_x_grouped<16>, 16);
+        const int big = 96 * 1024;
+        ok = ok &&
+             cudaFuncSetAttribute(gemv_n_grouped<MV_F32, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(gemv_n_grouped<MV_BF16, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize, big) ==
+                 cudaSuccess &&
+             cudaFuncSetAttribute(gemv_n_grouped<MV_FP8_E4M3, kRW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  big) == cudaSuccess;
+        if (!ok) st = record_cuda_error(cudaGetLastError(), "batch kernel attributes", __FILE__, __LINE__);
+    });
+    return st;
+}
+
+constexpr int kBatchRowsPerSplit = 512;
+
+struct BatchLayout {
+    std::vector<Plan> plans;
+    std::vector<size_t> base;       // workspace offset of each problem's plan
+    size_t o_gp, o_gp_all, o_sa, o_one, o_tt, o_tn, o_zero;
+    int nt_tiles, nn_tiles, cl, max_ncols, max_n;
+    size_t total;
+};
+
+static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo) {
+    Lo->plans.clear();
+    Lo->base.clear();
+    int64_t ntt = 0, nnt = 0;
+    int max_n = 1, max_ncols = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        MV_TRY(validate_problem(probs + i));
+        if (probs[i].dtype != probs[0].dtype) return record_message(MV_ERR_INVALID_ARG, "batch: mixed dtypes");
+        Plan p = make_plan(probs[i].dtype, probs[i].n, probs[i].T, probs[i].ld, kBatchRowsPerSplit);
+        ntt += (int64_t)p.t_blocks * p.t_splits;
+        nnt += (int64_t)p.n_groups * p.n_splits;
+        max_n = std::max(max_n, p.n);
+        max_ncols = std::max(max_ncols, p.n_cols);
+        Lo->plans.push_back(p);
+    }
+    if (ntt >= (1LL << 31) || nnt >= (1LL << 31)) return MV_ERR_UNSUPPORTED;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    Lo->o_gp = take(sizeof(GemvProb) * (size_t)count);
+    Lo->o_gp_all = take(sizeof(GemvProb) * (size_t)count);
+    Lo->o_sa = take(sizeof(StepArgs) * (size_t)count);
+    Lo->o_one = take(sizeof(GOne) * (size_t)count);
+    Lo->o_tt = take(sizeof(int4) * (size_t)ntt);
+    Lo->o_tn = take(sizeof(int4) * (size_t)nnt);
+    Lo->o_zero = take(sizeof(int));
+    for (int64_t i = 0; i < count; ++i) Lo->base.push_back(take(Lo->plans[i].total));
+    Lo->nt_tiles = (int)ntt;
+    Lo->nn_tiles = (int)nnt;
+    Lo->cl = proj_cluster_size(max_n);
+    Lo->max_ncols = max_ncols;
+    Lo->max_n = max_n;
+    Lo->total = off;
+    return MV_OK;
+}
+
+template <int DT>
+static void batch_gemv(const BatchLayout &Lo, void *ws, bool all, bool with_n, cudaStream_t s) {
+    const GemvProb *gp = at<GemvProb>(ws, all ? Lo.o_gp_all : Lo.o_gp);
+    gemv_t_grouped<DT><<<Lo.nt_tiles, kGemvThreads, 0, s>>>(gp, at<int4>(ws, Lo.o_tt));
+    if (with_n)
+        gemv_n_grouped<DT, kRW><<<Lo.nn_tiles, kGemvThreads, (size_t)Lo.max_ncols * 4, s>>>(gp, at<int4>(ws, Lo.o_tn));
+}
+
+static void batch_gemv_any(int dt, const BatchLayout &Lo, void *ws, bool all, bool with_n, cudaStream_t s) {
+    if (dt == MV_F32) batch_gemv<MV_F32>(Lo, ws, all, with_n, s);
+    else if (dt == MV_BF16) batch_gemv<MV_BF16>(Lo, ws, all, with_n, s);
+    else batch_gemv<MV_FP8_E4M3>(Lo, ws, all, with_n, s);
+}
+
+static cudaError_t batch_step(const BatchLayout &Lo, void *ws, int count, cudaStream_t s) {
+    const size_t smem = proj_elem_bytes((Lo.max_n + Lo.cl - 1) / Lo.cl);
+    const StepArgs *sa = at<StepArgs>(ws, Lo.o_sa);
+    switch (Lo.cl) {
+        case 1: return launch_clusters(npga_step_grouped<1>, 1, count, smem, s, sa);
+        case 2: return launch_clusters(npga_step_grouped<2>, 2, count, smem, s, sa);
+        case 4: return launch_clusters(npga_step_grouped<4>, 4, count, smem, s, sa);
+        case 8: return launch_clusters(npga_step_grouped<8>, 8, count, smem, s, sa);
+        default: return launch_clusters(npga_step_grouped<16>, 16, count, smem, s, sa);
+    }
+}
+
+}  // namespace mv
+
+extern "C" {
+
+size_t mv_batch_workspace_size(const mv_problem *probs, int64_t count) {
+    if (probs == nullptr || count < 1 || count > 65535) return 0;
+    BatchLayout Lo;
+    if (batch_layout(probs, count, &Lo) != MV_OK) return 0;
+    return Lo.total;
+}
+
+int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_opts *O_in, double *const *h_x_dev,
+                        mv_solve_info *h_infos, void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    if (probs == nullptr || h_x_dev == nullptr || h_infos == nullptr || count < 1 || count > 65535)
+        return MV_ERR_INVALID_ARG;
+    mv_solve_opts O;
+    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
+    if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
+    if (O.power_iters == 0 && !(O.alpha > 0.0)) return MV_ERR_INVALID_ARG;
+    BatchLayout Lo;
+    MV_TRY(batch_layout(probs, count, &Lo));
+    MV_TRY(check_ws(d_ws, ws_bytes, Lo.total));
+    MV_TRY(set_kernel_attrs());
+    MV_TRY(batch_attrs());
+    (void)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    void *ws = d_ws;
+    const int cnt = (int)count, dt = probs[0].dtype;
+    // descriptors
+    std::vector<GemvProb> gp(cnt), gpa(cnt);
+    std::vector<StepArgs> sa(cnt);
+    std::vector<GOne> one(cnt);
+    std::vector<int4> tt, tn;
+    tt.reserve(Lo.nt_tiles);
+    tn.reserve(Lo.nn_tiles);
+    const int *zero = at<int>(ws, Lo.o_zero);
+    for (int i = 0; i < cnt; ++i) {
+        const Plan &p = Lo.plans[i];
+        char *w = reinterpret_cast<char *>(ws) + Lo.base[i];
+        const mv_problem &P = probs[i];
+        const float *rs = P.dtype == MV_FP8_E4M3 ? P.row_scale : nullptr;
+        SolveState *st = at<SolveState>(w, p.o_state);
+        GemvProb g;
+        g.L = P.L;
+        g.ld = P.ld;
+        g.n = p.n;
+        g.T = p.T;
+        g.y32 = at<float>(w, p.o_y32);
+        g.zpart = at<float>(w, p.o_zpart);
+        g.zstride = p.zstride;
+        g.z = at<float>(w, p.o_z);
+        g.tick_t = at<unsigned>(w, p.o_tick_t);
+        g.t_rows = p.t_rows;
+        g.t_splits = p.t_splits;
+        g.gpart = at<float>(w, p.o_gpart);
+        g.gy = at<double>(w, p.o_gy);
+        g.g32 = at<float>(w, p.o_g32);
+        g.tick_n = at<unsigned>(w, p.o_tick_n);
+        g.n_cols = p.n_cols;
+        g.n_splits = p.n_splits;
+        g.row_scale = rs;
+        g.done = &st->done;
+        gp[i] = g;
+        g.done = zero;
+        gpa[i] = g;
+        StepArgs a;
+        a.st = st;
+        a.gy = at<double>(w, p.o_gy);
+        a.x = at<double>(w, p.o_x);
+        a.y = at<double>(w, p.o_y);
+        a.gx = at<double>(w, p.o_gx);
+        a.y32 = at<float>(w, p.o_y32);
+        a.mu = P.mu;
+        a.row_scale = rs;
+        a.n = p.n;
+        a.mode = P.mode;
+        a.kkt_every = O.kkt_every;
+        a.max_iter = O.max_iter;
+        a.R = P.R_target;
+        a.gamma = P.gamma;
+        a.eps = O.eps;
+        sa[i] = a;
+        GOne o;
+        o.st = st;
+        o.mu = P.mu;
+        o.r0 = P.power_start;
+        o.x_in = nullptr;
+        o.row_scale = rs;
+        o.y32 = at<float>(w, p.o_y32);
+        o.g32 = at<float>(w, p.o_g32);
+        o.z = at<float>(w, p.o_z);
+        o.x = at<double>(w, p.o_x);
+        o.y = at<double>(w, p.o_y);
+        o.n = p.n;
+        o.T = p.T;
+        o.mode = P.mode;
+        o.gamma = P.gamma;
+        o.safety = O.power_safety;
+        o.alpha_override = O.alpha > 0.0 ? O.alpha : 0.0;
+        o.R = P.R_target;
+        one[i] = o;
+        for (int b = 0; b < p.t_blocks; ++b)
+            for (int sp = 0; sp < p.t_splits; ++sp) tt.push_back(make_int4(i, b, sp, 0));
+        for (int gq = 0; gq < p.n_groups; ++gq)
+            for (int sp = 0; sp < p.n_splits; ++sp) tn.push_back(make_int4(i, gq, sp, 0));
+        MV_CUDA_TRY(cudaMemsetAsync(w + p.o_tick_t, 0, 4 * (size_t)p.t_blocks, s));
+        MV_CUDA_TRY(cudaMemsetAsync(w + p.o_tick_n, 0, 4 * (size_t)p.n_groups, s));
+    }
+    MV_CUDA_TRY(cudaMemsetAsync(at<int>(ws, Lo.o_zero), 0, sizeof(int), s));
+    MV_CUDA_TRY(cudaMemcpyAsync(at<GemvProb>(ws, Lo.o_gp), gp.data(), sizeof(GemvProb) * cnt, cudaMemcpyHostToDevice, s));
+    MV_CUDA_TRY(cudaMemcpyAsync(at<GemvProb>(ws, Lo.o_gp_all), gpa.data(), sizeof(GemvProb) * cnt,
+                                cudaMemcpyHostToDevice, s));
+    MV_CUDA_TRY(cudaMemcpyAsync(at<StepArgs>(ws, Lo.o_sa), sa.data(), sizeof(StepArgs) * cnt, cudaMemcpyHostToDevice, s));
+    MV_CUDA_TRY(cudaMemcpyAsync(at<GOne>(ws, Lo.o_one), one.data(), sizeof(GOne) * cnt, cudaMemcpyHostToDevice, s));
+    MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tt), tt.data(), sizeof(int4) * tt.size(), cudaMemcpyHostToDevice, s));
+    MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tn), tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, s));
+    MV_CUDA_TRY(cudaStreamSynchronize(s));   // host descriptor buffers may now be released
+
+    const GOne *d_one = at<GOne>(ws, Lo.o_one);
+    int launches = 0;
+    setup_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
+    if (!(O.alpha > 0.0)) {
+        for (int it = 0; it < O.power_iters; ++it) {
+            batch_gemv_any(dt, Lo, ws, true, true, s);
+            power_norm_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
+            launches += 3;
+        }
+        if (O.power_iters > 0) {
+            batch_gemv_any(dt, Lo, ws, true, false, s);
+            ++launches;
+        }
+    }
+    step_size_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
+    {
+        const size_t smem = proj_elem_bytes((Lo.max_n + Lo.cl - 1) / Lo.cl);
+        cudaError_t e;
+        switch (Lo.cl) {
+            case 1: e = launch_clusters(init_x_grouped<1>, 1, cnt, smem, s, d_one); break;
+            case 2: e = launch_clusters(init_x_grouped<2>, 2, cnt, smem, s, d_one); break;
+            case 4: e = launch_clusters(init_x_grouped<4>, 4, cnt, smem, s, d_one); break;
+            case 8: e = launch_clusters(init_x_grouped<8>, 8, cnt, smem, s, d_one); break;
+            default: e = launch_clusters(init_x_grouped<16>, 16, cnt, smem, s, d_one); break;
+        }
+        MV_CUDA_TRY(e);
+    }
+    launches += 3;
+    MV_CUDA_TRY(cudaGetLastError());
+
+    const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
+    cudaGraphExec_t exec = nullptr;
+    if (O.use_graph) {
+        cudaStream_t cs;
+        MV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            for (int c = 0; c < chunk; ++c) {
+                batch_gemv_any(dt, Lo, ws, false, true, cs);
+                batch_step(Lo, ws, cnt, cs);
+            }
+            if (cudaStreamEndCapture(cs, &graph) == cudaSuccess) {
+                if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+                cudaGraphDestroy(graph);
+            }
+        }
+        cudaStreamDestroy(cs);
+        (void)cudaGetLastError();
+    }
+    std::vector<SolveState> hs(cnt);
+    const int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
+    for (int64_t c = 0; c < max_chunks; ++c) {
+        if (exec) {
+            MV_CUDA_TRY(cudaGraphLaunch(exec, s));
+        } else {
+            for (int i = 0; i < chunk; ++i) {
+                batch_gemv_any(dt, Lo, ws, false, true, s);
+                MV_CUDA_TRY(batch_step(Lo, ws, cnt, s));
+            }
+        }
+        launches += 3 * chunk;
+        for (int i = 0; i < cnt; ++i)
+            MV_CUDA_TRY(cudaMemcpyAsync(&hs[i], reinterpret_cast<char *>(ws) + Lo.base[i] + Lo.plans[i].o_state,
+                                        sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+        MV_CUDA_TRY(cudaStreamSynchronize(s));
+        bool all = true;
+        for (int i = 0; i < cnt; ++i) all = all && hs[i].done;
+        if (all) break;
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    // objectives: z = L^T x for every problem, then ||z||^2 + gamma ||x||^2
+    to_y32_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
+    batch_gemv_any(dt, Lo, ws, true, false, s);
+    objective_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
+    launches += 3;
+    MV_CUDA_TRY(cudaGetLastError());
+    for (int i = 0; i < cnt; ++i) {
+        MV_CUDA_TRY(cudaMemcpyAsync(h_x_dev[i], reinterpret_cast<char *>(ws) + Lo.base[i] + Lo.plans[i].o_x,
+                                    8 * (size_t)Lo.plans[i].n, cudaMemcpyDeviceToDevice, s));
+        MV_CUDA_TRY(cudaMemcpyAsync(&hs[i], reinterpret_cast<char *>(ws) + Lo.base[i] + Lo.plans[i].o_state,
+                                    sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    }
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
+    int worst = MV_OK;
+    for (int i = 0; i < cnt; ++i) {
+        mv_solve_info &I = h_infos[i];
+        I = mv_solve_info{};
+        I.iterations = hs[i].k;
+        I.status = hs[i].done ? hs[i].status : MV_ERR_NOT_CONVERGED;
+        I.converged = hs[i].converged;
+        I.proj_failures = hs[i].proj_fail;
+        I.proj_steps = hs[i].proj_steps;
+        I.kkt = hs[i].kkt;
+        I.objective = hs[i].objective;
+        I.alpha = hs[i].alpha;
+        I.lambda_hat = hs[i].lambda_hat;
+        I.nu = hs[i].nu;
+        I.launches = launches;
+        if (I.status != MV_OK && worst == MV_OK) worst = I.status;
+    }
+    return worst;
 }
 
 int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const mv_solve_opts *O_in, double eps_lo,

@@ -32,7 +32,7 @@ EXPORTS = [
     "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
     "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
     "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
-    "mv_npga_backward",
+    "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -131,6 +131,11 @@ def lib():
         L.mv_npga_backward.restype = i32
         L.mv_npga_backward.argtypes = [C.POINTER(Problem), C.POINTER(SolveOpts), vp, vp, vp, vp, i64,
                                        C.POINTER(SolveInfo), vp, sz, vp]
+        L.mv_batch_workspace_size.restype = sz
+        L.mv_batch_workspace_size.argtypes = [C.POINTER(Problem), i64]
+        L.mv_npga_solve_batch.restype = i32
+        L.mv_npga_solve_batch.argtypes = [C.POINTER(Problem), i64, C.POINTER(SolveOpts), C.POINTER(C.c_void_p),
+                                          C.POINTER(SolveInfo), vp, sz, vp]
         L.mv_sketch.restype = i32
         L.mv_sketch.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
         L.mv_gradient_noalloc.restype = i32
@@ -438,3 +443,33 @@ class NPGAFunction(torch.autograd.Function):
         dmu, dL, _ = npga_backward(L, mu, R_target, T, grad_x.to(torch.float64), iters, gamma=gamma,
                                    checkpoint_every=ck)
         return dL, dmu, None, None, None, None, None
+
+
+class BatchSolver:
+    """Independent problems of uneven size solved together (mv_npga_solve_batch).
+
+    ``problems`` is a list of dicts with keys L, mu, R_target, T and optional
+    gamma, row_scale, power_start, mode; all L share one dtype."""
+
+    def __init__(self, problems, dtype="f32", **opts):
+        self._keep = problems
+        self.count = len(problems)
+        self.probs = (Problem * self.count)()
+        for i, q in enumerate(problems):
+            self.probs[i] = make_problem(q["L"], q["mu"], q["R_target"], q["T"], q.get("gamma", 0.0), dtype,
+                                         q.get("row_scale"), q.get("mode", "ge"), q.get("power_start"))
+        self.opts = solve_opts(**opts)
+        nb = lib().mv_batch_workspace_size(self.probs, self.count)
+        if nb == 0:
+            raise MvError(MV_ERR_INVALID_ARG, "mv_batch_workspace_size")
+        dev = problems[0]["L"].device
+        self.ws = _workspace(nb, dev)
+        self.xs = [torch.zeros(q["L"].shape[0], dtype=torch.float64, device=dev) for q in problems]
+        self._xp = (C.c_void_p * self.count)(*[x.data_ptr() for x in self.xs])
+
+    def solve(self, allow=(MV_ERR_NOT_CONVERGED,)):
+        infos = (SolveInfo * self.count)()
+        st = lib().mv_npga_solve_batch(self.probs, self.count, C.byref(self.opts), self._xp, infos, _ptr(self.ws),
+                                       self.ws.numel(), _stream())
+        _check(st, "mv_npga_solve_batch", allow)
+        return self.xs, [i.as_dict() for i in infos]
