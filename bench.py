@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--sketch-m", type=int, default=8192)
     ap.add_argument("--no-frontier", action="store_true", help="skip the 64-target frontier measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem uneven batch")
+    ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -450,6 +452,37 @@ def main():
                "backward_s": bwd / 1e3, "backward_over_forward": bwd / fwd}
         del La, Ra
 
+    # 256 independent problems, n ~ U[500,5000], T ~ U[2000,20000] (grouped launches).
+    batch = None
+    if not args.no_batch and args.dtype == "f32":
+        from synth import factor_returns_device, uneven_problem_sizes
+        models = uneven_problem_sizes(args.batch_count)
+        probs = []
+        for bm in models:
+            Rb = factor_returns_device(bm, dev)
+            Lb_, _, mub, _ = mv.center_factor(Rb, "f32")
+            del Rb
+            Rtb = float(torch.quantile(mub, 0.6).item())
+            probs.append({"L": Lb_, "mu": mub, "R_target": Rtb, "T": bm.T})
+        bsv = mv.BatchSolver(probs, eps=args.eps)
+        bsv.solve()
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        _, binfos = bsv.solve()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bt = b0.elapsed_time(b1) / 1e3
+        elems = sum(bm.n * bm.T for bm in models)
+        iters = [i["iterations"] for i in binfos]
+        # bytes streamed: 2 passes of every L per power iteration (50) and per NPGA iteration it ran
+        moved = sum(2 * 4 * bm.n * bm.T * (50 + it + 1) for bm, it in zip(models, iters))
+        batch = {"problems": len(models), "elements": elems, "value": bt, "unit": "s",
+                 "problems_per_s": len(models) / bt, "all_converged": all(i["converged"] == 1 for i in binfos),
+                 "iterations_min": min(iters), "iterations_max": max(iters),
+                 "aggregate_GBps": moved / bt / 1e9, "data": "synthetic, drawn on the GPU (torch seeded stream)"}
+        del probs, bsv
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         iters = int(np.median([i["iterations"] for i in infos]))
@@ -469,7 +502,7 @@ def main():
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "variants": variants, "str": str_res, "frontier": frontier, "adjoint": adj}
+                "variants": variants, "str": str_res, "frontier": frontier, "adjoint": adj, "batch": batch}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

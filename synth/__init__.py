@@ -26,6 +26,7 @@ from dataclasses import dataclass
 import numpy as np
 
 __all__ = [
+    "factor_returns_device",
     "FactorModel",
     "CFG_SMALL",
     "CFG_FULL",
@@ -130,3 +131,32 @@ def uneven_problem_sizes(count: int = 256, seed: int = 1000,
     ns = rng.integers(n_range[0], n_range[1] + 1, size=count)
     Ts = rng.integers(T_range[0], T_range[1] + 1, size=count)
     return [CFG_SMALL.scaled(int(a), int(b), seed=seed + j) for j, (a, b) in enumerate(zip(ns, Ts))]
+
+
+def factor_returns_device(model: FactorModel, device="cuda", dtype=None):
+    """The same factor-model distributions drawn on the GPU with PyTorch's
+    seeded generator (a different random stream from ``factor_returns``).
+
+    Used where drawing billions of numbers on the host would dominate a
+    measurement (the 256-problem uneven batch); parity tests use the NumPy
+    stream so that the oracle sees identical inputs.  Returns an n x T FP32
+    tensor.
+    """
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(model.seed))
+    n, T, k = model.n, model.T, model.n_factors
+    f32 = torch.float32
+    B = torch.randn((n, k), generator=g, device=device, dtype=f32) * model.loading_scale
+    # Student-t(nu) = N(0,1) / sqrt(chi2(nu)/nu); chi2 via a sum of squared normals
+    nrm = torch.randn((k, T), generator=g, device=device, dtype=f32)
+    chi = torch.randn((int(model.t_dof), k, T), generator=g, device=device, dtype=f32).pow_(2).sum(0)
+    t = nrm / torch.sqrt(chi / model.t_dof)
+    f = t * (model.factor_vol / math.sqrt(model.t_dof / (model.t_dof - 2.0)))
+    sig = torch.rand(n, generator=g, device=device, dtype=f32) * (model.idio_hi - model.idio_lo) + model.idio_lo
+    R = torch.randn((n, T), generator=g, device=device, dtype=f32) * sig[:, None]
+    drift = torch.rand(n, generator=g, device=device, dtype=f32) * (model.drift_hi - model.drift_lo) + model.drift_lo
+    R += B @ f
+    R += drift[:, None]
+    return R
