@@ -292,7 +292,7 @@ int mv_sketch(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_
  *  and writes L_eff = U_k diag(sigma_k) (n x k FP32, row-major, columns in
  *  descending sigma) and sigma (k FP64, descending).  The ridge returned in
  *  *h_gamma_out is `gamma` if gamma >= 0, else 1e-4 * trace_sigma / n.
- *  One-time step; uses cuBLAS (DSYRK) and cuSOLVER (DSYEVDX) loaded at run
+ *  One-time step; uses cuBLAS (DSYRK) and cuSOLVER (DSYEVD) loaded at run
  *  time: MV_ERR_UNSUPPORTED if they cannot be loaded.  Workspace:
  *  mv_str_workspace_size(n, m, k) bytes (FP64 copies of tilde L and K plus
  *  the eigensolver's buffer).  Blocking.  MV_ERR_NUMERIC if the eigensolver

@@ -9,7 +9,9 @@
 //
 // This one-time FP64 step uses two NVIDIA libraries, loaded at run time so
 // that libmv itself loads without them: cuBLAS DSYRK for the Gram matrix (a
-// plain library GEMM) and cuSOLVER DSYEVDX for the k largest eigenpairs.
+// plain library GEMM) and cuSOLVER DSYEVD for the eigenpairs (all n of them:
+// on this GPU the full divide-and-conquer solver is several times faster
+// than the selected-range one), of which the k largest are kept.
 // Everything else (FP64 widening, assembling L_eff and sigma) is in the
 // kernels below.
 #include <dlfcn.h>
@@ -30,12 +32,10 @@ typedef int (*fn_cublasSgemm)(void *, int, int, int, int, int, const float *, co
                               const float *, float *, int);
 typedef int (*fn_cusolverCreate)(void **);
 typedef int (*fn_cusolverSetStream)(void *, cudaStream_t);
-typedef int (*fn_syevdx_bs)(void *, int, int, int, int, const double *, int, double, double, int, int, int *,
-                            const double *, int *);
-typedef int (*fn_syevdx)(void *, int, int, int, int, double *, int, double, double, int, int, int *, double *,
-                         double *, int, int *);
+typedef int (*fn_syevd_bs)(void *, int, int, int, const double *, int, const double *, int *);
+typedef int (*fn_syevd)(void *, int, int, int, double *, int, double *, double *, int, int *);
 
-constexpr int kOpT = 1, kFillLower = 0, kEigVector = 1, kEigRangeI = 1002;
+constexpr int kOpT = 1, kFillLower = 0, kEigVector = 1;
 
 struct Linalg {
     void *blas = nullptr, *solver = nullptr;
@@ -44,8 +44,8 @@ struct Linalg {
     fn_cublasDsyrk dsyrk = nullptr;
     fn_cublasSgemm sgemm = nullptr;
     fn_cusolverSetStream s_set_stream = nullptr;
-    fn_syevdx_bs syevdx_bs = nullptr;
-    fn_syevdx syevdx = nullptr;
+    fn_syevd_bs syevd_bs = nullptr;
+    fn_syevd syevd = nullptr;
     bool ok = false;
 };
 
@@ -73,9 +73,10 @@ static Linalg *linalg() {
         L.sgemm = (fn_cublasSgemm)dlsym(lb, "cublasSgemm_v2");
         auto screate = (fn_cusolverCreate)dlsym(ls, "cusolverDnCreate");
         L.s_set_stream = (fn_cusolverSetStream)dlsym(ls, "cusolverDnSetStream");
-        L.syevdx_bs = (fn_syevdx_bs)dlsym(ls, "cusolverDnDsyevdx_bufferSize");
-        L.syevdx = (fn_syevdx)dlsym(ls, "cusolverDnDsyevdx");
-        if (!bcreate || !L.b_set_stream || !L.dsyrk || !L.sgemm || !screate || !L.s_set_stream || !L.syevdx_bs || !L.syevdx)
+        L.syevd_bs = (fn_syevd_bs)dlsym(ls, "cusolverDnDsyevd_bufferSize");
+        L.syevd = (fn_syevd)dlsym(ls, "cusolverDnDsyevd");
+        if (!bcreate || !L.b_set_stream || !L.dsyrk || !L.sgemm || !screate || !L.s_set_stream || !L.syevd_bs ||
+            !L.syevd)
             return;
         if (bcreate(&L.hb) != 0 || screate(&L.hs) != 0) return;
         L.ok = true;
@@ -128,10 +129,9 @@ struct StrPlan {
 static int str_plan(int64_t n, int64_t m, int64_t k, StrPlan *p) {
     Linalg *L = linalg();
     if (!L) return record_message(MV_ERR_UNSUPPORTED, "STR truncation needs cuBLAS and cuSOLVER (not found)");
-    int meig = 0, lwork = 0;
-    if (L->syevdx_bs(L->hs, kEigVector, kEigRangeI, kFillLower, (int)n, nullptr, (int)n, 0.0, 0.0,
-                     (int)(n - k + 1), (int)n, &meig, nullptr, &lwork) != 0)
-        return record_message(MV_ERR_CUDA, "cusolverDnDsyevdx_bufferSize failed");
+    int lwork = 0;
+    if (L->syevd_bs(L->hs, kEigVector, kFillLower, (int)n, nullptr, (int)n, nullptr, &lwork) != 0)
+        return record_message(MV_ERR_CUDA, "cusolverDnDsyevd_bufferSize failed");
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -187,18 +187,17 @@ int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, 
     if (L->dsyrk(L->hb, kFillLower, kOpT, (int)n, (int)m, &one, A, (int)m, &zero, K, (int)n) != 0)
         return record_message(MV_ERR_CUDA, "cublasDsyrk failed");
     if (L->s_set_stream(L->hs, s) != 0) return record_message(MV_ERR_CUDA, "cusolverDnSetStream failed");
-    int meig = 0;
-    if (L->syevdx(L->hs, kEigVector, kEigRangeI, kFillLower, (int)n, K, (int)n, 0.0, 0.0, (int)(n - k + 1), (int)n,
-                  &meig, W, work, p.lwork, info) != 0)
-        return record_message(MV_ERR_CUDA, "cusolverDnDsyevdx failed");
-    leff_kernel<<<1024, 256, 0, s>>>(K, W, (int)n, (int)k, d_L_eff, ldE, d_sigma);
+    if (L->syevd(L->hs, kEigVector, kFillLower, (int)n, K, (int)n, W, work, p.lwork, info) != 0)
+        return record_message(MV_ERR_CUDA, "cusolverDnDsyevd failed");
+    // all n pairs come back ascending: the k largest are the last k columns
+    leff_kernel<<<1024, 256, 0, s>>>(K + (size_t)(n - k) * n, W + (n - k), (int)n, (int)k, d_L_eff, ldE, d_sigma);
     MV_CUDA_TRY(cudaGetLastError());
     int hinfo = 0;
     MV_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
     MV_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hinfo != 0 || meig != (int)k) {
+    if (hinfo != 0) {
         char msg[96];
-        snprintf(msg, sizeof(msg), "cusolverDnDsyevdx: info=%d, %d of %lld eigenpairs", hinfo, meig, (long long)k);
+        snprintf(msg, sizeof(msg), "cusolverDnDsyevd: info=%d", hinfo);
         return record_message(MV_ERR_NUMERIC, msg);
     }
     if (h_gamma_out) *h_gamma_out = gamma >= 0.0 ? gamma : 1e-4 * trace_sigma / (double)n;
