@@ -1,6 +1,6 @@
 // tcgen05 BF16 GEMM  C = A B^T  (A: M x K, B: N x K, both K-major BF16;
 // FP32 accumulation in tensor memory).  Shared by the sketch (sketch.cu) and
-// the batched frontier solve (frontier.cu).
+// the batched frontier solve (the frontier section of solve.cu).
 //
 // One CTA computes a 128 x BN tile with a K loop in steps of 64:
 //   warp 0, one thread : TMA producer -- 128x64 A box and BNx64 B box per
