@@ -88,23 +88,68 @@ def peaks():
         return FALLBACK_HBM, "fallback"
 
 
+# kernel -> (committed ncu summary, source file whose hash the summary records)
+TRAFFIC_FILES = {"gemv_t": ("gemv_traffic.txt", "gemv.cuh"), "gemv_n": ("gemv_traffic.txt", "gemv.cuh"),
+                 "llt": ("llt_traffic.txt", "llt.cuh")}
+
+
 def committed_traffic(kernel):
     """Per-launch DRAM bytes from the committed ncu summary, if it matches this source."""
-    path = os.path.join(ROOT, "profiles", "gemv_traffic.txt")
+    if kernel not in TRAFFIC_FILES:
+        return None
+    fname, srcname = TRAFFIC_FILES[kernel]
+    path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
         return None
     import hashlib
-    src = os.path.join(ROOT, "paper_2604_02917_gb300", "csrc", "gemv.cuh")
+    src = os.path.join(ROOT, "paper_2604_02917_gb300", "csrc", srcname)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
-        if ":" in line:
+        if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("gemv_source_sha") != sha:
+    if vals.get("source_sha", vals.get("gemv_source_sha")) != sha:
         return None
     v = vals.get(f"{kernel}_dram_bytes_per_launch")
     return float(v) if v else None
+
+
+def roofline(infos, model, dtype):
+    """HBM roofline of the solve loop's dominant L pass from the per-launch CUDA events.
+
+    Algorithmic bytes per launch: the factor once (n T e) plus the vectors the
+    pass must read and write (FP8 adds the n row scales)."""
+    es = {"f32": 4, "bf16": 2, "fp8": 1}[dtype]
+    n, T = model.n, model.T
+    nT = n * T
+    sc = 4 * n if dtype == "fp8" else 0
+    pairs = max(sum(i["timed_pairs"] for i in infos), 1)
+    step_us = round(sum(i["t_step_ms"] for i in infos) / pairs * 1e3, 2)
+    if all(i.get("fused", 0) for i in infos):
+        kern = "llt"
+        avg_ms = sum(i["t_fused_ms"] for i in infos) / pairs
+        alg = nT * es + 4 * n + 8 * n + sc          # L, y (FP32), g (FP64)
+        other = None
+    else:
+        tt = sum(i["t_gemv_t_ms"] for i in infos)
+        tn = sum(i["t_gemv_n_ms"] for i in infos)
+        kern = "gemv_t" if tt >= tn else "gemv_n"
+        avg_ms = (tt if kern == "gemv_t" else tn) / pairs
+        if kern == "gemv_t":
+            alg = nT * es + 4 * n + 4 * T + sc
+        else:
+            alg = nT * es + 4 * T + 8 * n + sc
+        other = round(((tn if kern == "gemv_t" else tt) / pairs) * 1e3, 2)
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": committed_traffic(kern), "kernel": kern,
+            "peak_source": peak_kind, "avg_launch_us": round(avg_ms * 1e3, 2),
+            "alg_bytes_per_launch": alg, "step_kernel_avg_us": step_us}
+    if other is not None:
+        roof["other_kernel_avg_us"] = other
+    return roof
 
 
 class Clocks:
@@ -263,25 +308,9 @@ def main():
         ms = float(t.item())
 
     # roofline of the dominant kernel (per-launch CUDA events around every loop launch)
+    roof = roofline(infos, model, args.dtype)
     es = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
-    pairs = sum(i["timed_pairs"] for i in infos)
-    tt = sum(i["t_gemv_t_ms"] for i in infos)
-    tn = sum(i["t_gemv_n_ms"] for i in infos)
-    kern = "gemv_t" if tt >= tn else "gemv_n"
-    avg_ms = (tt if kern == "gemv_t" else tn) / max(pairs, 1)
     nT = model.n * model.T
-    if kern == "gemv_t":
-        alg = nT * es + 4 * model.n + 4 * model.T + (4 * model.n if args.dtype == "fp8" else 0)
-    else:
-        alg = nT * es + 4 * model.T + 8 * model.n + (4 * model.n if args.dtype == "fp8" else 0)
-    achieved = alg / (avg_ms * 1e-3) / 1e9
-    peak, peak_kind = peaks()
-    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": committed_traffic(kern), "kernel": kern,
-            "peak_source": peak_kind, "avg_launch_us": round(avg_ms * 1e3, 2),
-            "alg_bytes_per_launch": alg, "other_kernel_avg_us": round(
-                ((tn if kern == "gemv_t" else tt) / max(pairs, 1)) * 1e3, 2),
-            "step_kernel_avg_us": round(sum(i["t_step_ms"] for i in infos) / max(pairs, 1) * 1e3, 2)}
 
     # end to end through host buffers: upload R, center, solve, download x
     e2e = None
@@ -319,6 +348,25 @@ def main():
 
     # Low-precision storage + FP32 refinement on the same workload and GPU.
     variants = {}
+    if not args.no_variants and info.get("fused", 0):
+        # The same FP32 solve with the two half-products as separate passes.
+        tps = mv.Solver(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
+                        timing=1, two_pass=1)
+        for _ in range(args.warmup):
+            tps.solve()
+        torch.cuda.synchronize()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tinfos = []
+        v0.record(stream)
+        for _ in range(args.steps):
+            _, ti = tps.solve()
+            tinfos.append(ti)
+        v1.record(stream)
+        torch.cuda.synchronize()
+        variants[args.dtype + "_two_pass"] = {
+            "value": v0.elapsed_time(v1) / args.steps / 1e3, "unit": "s", "iterations": ti["iterations"],
+            "kkt": ti["kkt"], "objective": ti["objective"], "roofline": roofline(tinfos, model, args.dtype)}
+        del tps
     if not args.no_variants and args.dtype == "f32":
         R_dev = torch.from_numpy(R32).to(dev)
         for vdt in ("bf16", "fp8"):

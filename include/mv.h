@@ -171,7 +171,9 @@ typedef struct {
     int32_t timing;           /* 1: time every loop launch with CUDA events (kernels are
                                  then issued from the host instead of a graph)           */
     int32_t checkpoint_every; /* mv_npga_backward: iterations between checkpoints (50)   */
-    int32_t reserved;
+    int32_t two_pass;         /* 1: always stream L twice per product (z = L^T y, then
+                                 L z); 0 (default): use the fused single pass for
+                                 L L^T y where it applies (see below)                   */
 } mv_solve_opts;
 
 typedef struct {
@@ -191,12 +193,24 @@ typedef struct {
     double t_step_ms;         /* summed device time of those step (projection) launches  */
     int32_t proj_steps;       /* block-wide reductions spent by all projections          */
     int32_t refine_iterations;/* mv_npga_solve_refined: iterations of the FP32 phase     */
+    int32_t fused;            /* 1 if the loop used the fused single-pass product        */
+    double t_fused_ms;        /* summed device time of the timed fused-pass launches     */
 } mv_solve_info;
 
 void mv_solve_opts_default(mv_solve_opts *opts);
 size_t mv_npga_workspace_size(const mv_problem *P);
 
-/*  d_x_inout [in/out] n FP64: x^0 when opts.warm_start = 1 (must lie in F),
+/*  Fused single pass.  The loop and the power method need only the product
+ *  L L^T y, never z = L^T y itself, so where n >= 1024 and T >= 4096 and a
+ *  shape fits (n up to about 6800) the two half-products run in one pass
+ *  over L: a cluster of 2 to 8 CTAs holds a 32- to 128-byte column block of
+ *  all n rows in shared memory, forms that block's slice of L^T y from it,
+ *  exchanges it through distributed shared memory and adds
+ *  L_block (L_block^T y) to g from the same staged block.  L is then read
+ *  from HBM once per iteration instead of twice.  opts.two_pass = 1 turns
+ *  it off; elsewhere the two-pass kernels run.
+ *
+ *  d_x_inout [in/out] n FP64: x^0 when opts.warm_start = 1 (must lie in F),
  *                     the solution x^k on return.
  *  h_info    [out]    host struct, filled on return.
  *  Blocking: the call synchronises `stream` once per kkt_every iterations to
@@ -339,7 +353,9 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *opts, const doubl
  *    for callers with their own outer loop:
  *        d_g = 2 L_eff (L_eff^T y) + 2 gamma y,   d_z = L_eff^T y.
  *  d_y FP64 n, d_z FP32 T (may be NULL), d_g FP64 n.  Uses the workspace of
- *  mv_npga_workspace_size.  Asynchronous.
+ *  mv_npga_workspace_size.  With d_z NULL the product runs as the fused
+ *  single pass described under mv_npga_solve where that applies.
+ *  Asynchronous.
  * ------------------------------------------------------------------------ */
 int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
                 void *d_ws, size_t ws_bytes, mv_stream_t stream);

@@ -1,0 +1,414 @@
+// Fused Gram product  g = L (L^T y)  in ONE pass over L (Sec. 2.7: the
+// NPGA gradient 2 L L^T y + 2 gamma y and the power method's L L^T u both
+// need only this product, never z = L^T y itself).
+//
+// Column blocking.  L (n x T, row-major) is cut into column blocks of W
+// columns, W * sizeof(elem) = RB bytes (32 by default: one DRAM sector per row).  A
+// thread-block cluster of C CTAs (C = 2, a TPC pair, for n up to about 6000;
+// 4 or 8 beyond) owns one column block at a time: CTA rank r holds rows
+// [r*rpc, (r+1)*rpc) of the block in shared memory (TMA 2-D loads with the
+// RB-byte swizzle, zero fill past n and T).  Per block:
+//   A. each of 16 consumer warps forms the partial column sums of one
+//      16-byte chunk over a share of the CTA's rows, all-reduces them over
+//      the warp and pushes them into every CTA of the cluster with st.async
+//      (distributed shared memory; completion counted in bytes on an mbarrier
+//      of the receiver) -- no block barrier;
+//   B. every CTA adds the partials of each column in a fixed order (the
+//      same bits on all CTAs), giving z_b = L[:, b]^T y, and accumulates
+//      g[rows_r] += L[rows_r, b] z_b  (one thread per row, compensated sums
+//      in registers) from the block still in shared memory.
+// So every element of L is read from HBM once per product instead of once
+// per half-product.  Clusters are persistent and take column blocks
+// round-robin; their per-row partial sums of g go to a [clusters x n]
+// buffer, added in a fixed two-level order in FP64 by the last CTAs to
+// finish (atomic tickets after a fence, no spinning).
+//
+// Roles: one producer warp keeps a 2-stage ring of row blocks in flight
+// (full/empty mbarriers); a stage is ~87 KB per CTA at n = 5440 FP32, about
+// 2 us of this SM's share of HBM bandwidth, against well under 1 us of
+// compute and exchange per block, so the loads stay back to back.  Two
+// exchange slots suffice: a CTA pushes block j+2 only after it received
+// block j+1 from every peer warp, which each peer pushed after it had
+// consumed block j.  One block barrier per column block (after the receive).
+//
+// Every mbarrier wait is bounded in time; on timeout the thread records an
+// error code and carries on with short waits, so no peer is left waiting.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "gemm.cuh"
+#include "llt_api.h"
+
+namespace mv {
+
+constexpr int kLltConsumerWarps = 16;
+constexpr int kLltConsumers = kLltConsumerWarps * 32;
+constexpr int kLltThreads = kLltConsumers + 32; // + one producer warp
+constexpr int kLltSlots = 2;
+constexpr int kLltStages = 2;
+constexpr int kLltRowsPerThread = 8;            // rows of phase B per consumer thread (max)
+constexpr uint64_t kLltWaitNs = 2000000000ull;
+constexpr uint64_t kLltBailNs = 1000000ull;     // after a timeout: 1 ms per wait
+
+struct LltArgs {
+    const float *y32;          // n: gemv input (FP8: pre-multiplied by the row scale)
+    const float *row_scale;    // n or null (FP8)
+    float *gpart;              // [G x n] per-cluster partials
+    double *gq;                // [groups x n] group sums
+    double *g;                 // n: L L^T y (row-scaled)
+    float *g32;                // n or null
+    unsigned *tick1;           // [C x kLltMaxGroups], zero between launches
+    unsigned *tick2;           // [C], zero between launches
+    int *err;                  // error word (0 = fine)
+    const int *done;           // early-exit flag or null
+    int n, T;
+    int rpc, box_rows, nbox, nb, G;
+};
+
+namespace llt {
+
+__device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+// Asynchronous 16-byte store into another CTA's shared memory; the bytes
+// are counted on that CTA's mbarrier.
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, float4 v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
+                     raddr),
+                 "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ bool try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool wait_cluster(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+    if (try_wait_cluster(bar, parity)) return true;
+    const uint64_t t0 = umma::globaltimer();
+    while (true) {
+        if (try_wait_cluster(bar, parity)) return true;
+        if (umma::globaltimer() - t0 > limit_ns) return false;
+    }
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Named barrier over the consumer warps only (the producer never joins it).
+__device__ __forceinline__ void bar_consumers() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kLltConsumers) : "memory");
+}
+// Byte offset of 16-byte chunk c of row r of RB-byte rows under the RB-byte
+// TMA swizzle: the chunk lands at c ^ ((r / (128 / RB)) mod (RB / 16)).
+template <int RB>
+__device__ __forceinline__ int swz(int r, int c) {
+    return r * RB + ((c ^ ((r / (128 / RB)) & (RB / 16 - 1))) << 4);
+}
+
+}  // namespace llt
+
+// Shared-memory layout (bytes) for a given geometry.
+struct LltSmem {
+    size_t stage, o_slots, o_y, o_zc, o_bars, total;
+};
+__host__ __device__ inline LltSmem llt_smem_layout(int rpc, int RB, int W, int C) {
+    LltSmem m{};
+    m.stage = (size_t)rpc * RB;
+    size_t off = m.stage * kLltStages;
+    m.o_slots = off;
+    off += (size_t)kLltSlots * C * (kLltConsumerWarps / (RB / 16)) * W * 4;
+    m.o_y = off;
+    off += (size_t)rpc * 4;
+    m.o_zc = off;
+    off += (size_t)2 * W * 4;
+    off = (off + 15) / 16 * 16;
+    m.o_bars = off;
+    off += 8 * (size_t)(2 * kLltStages + kLltSlots);
+    m.total = off + 1024;                // slack for aligning the dynamic base to 1024 bytes
+    return m;
+}
+
+template <int DT, int C, int RB>
+__global__ void __launch_bounds__(kLltThreads, 1)
+llt_kernel(const __grid_constant__ CUtensorMap tmL, const LltArgs a) {
+    using S = Store<DT>;
+    constexpr int EPC = S::VEC;                        // elements per 16-byte chunk
+    constexpr int NCH = RB / 16;                       // 16-byte chunks per row
+    constexpr int W = RB / (int)sizeof(typename S::elem);
+    constexpr int NG = kLltConsumerWarps / NCH;        // row groups of phase A
+    constexpr int V4 = EPC / 4;                        // float4 pieces of one chunk's partials
+    constexpr int RPT = kLltRowsPerThread;
+    namespace cg = cooperative_groups;
+    if (a.done != nullptr && *(const volatile int *)a.done) return;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const LltSmem L = llt_smem_layout(a.rpc, RB, W, C);
+    float *slots = reinterpret_cast<float *>(sm + L.o_slots);       // [2][C][NG][W]
+    float *s_y = reinterpret_cast<float *>(sm + L.o_y);
+    float *s_zc = reinterpret_cast<float *>(sm + L.o_zc);           // [2][W]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.o_bars);
+    const uint32_t full0 = umma::smem_u32(bars), empty0 = umma::smem_u32(bars + kLltStages);
+    const uint32_t xchg0 = umma::smem_u32(bars + 2 * kLltStages);
+    const uint32_t slots_u32 = umma::smem_u32(slots);
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int cid = blockIdx.x / C;
+    const int row0 = rank * a.rpc;
+    const int nj = (a.nb - cid + a.G - 1) / a.G;       // column blocks of this cluster (>= 1)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t xbytes = (uint32_t)(C * NG * W * 4);
+    const uint32_t stage_tx = (uint32_t)(a.nbox * a.box_rows * RB);
+
+    if (tid == 0) {
+        for (int s = 0; s < kLltStages; ++s) {
+            umma::mbar_init(full0 + 8 * s, 1);
+            umma::mbar_init(empty0 + 8 * s, kLltConsumerWarps);
+        }
+        for (int q = 0; q < kLltSlots; ++q) umma::mbar_init(xchg0 + 8 * q, 1);
+        umma::mbar_fence_init();
+        for (int q = 0; q < kLltSlots && q < nj; ++q) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
+    }
+    for (int i = tid; i < a.rpc; i += kLltThreads) {
+        const int r = row0 + i;
+        s_y[i] = r < a.n ? a.y32[r] : 0.f;
+    }
+    cluster.sync();                                     // peers' barriers exist before any push
+
+    float gs[RPT], gc[RPT];                            // consumers: compensated g of rows tid + 512 k
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) gs[k] = gc[k] = 0.f;
+
+    if (warp == kLltConsumerWarps) {
+        // ---------------- producer: column block j of this cluster -> stage j % 2
+        if (lane == 0) {
+            umma::prefetch_tensormap(&tmL);
+            bool bail = false;
+            for (int j = 0; j < nj; ++j) {
+                const int s = j % kLltStages;
+                if (j >= kLltStages && !umma::mbar_wait(empty0 + 8 * s, (uint32_t)(j / kLltStages - 1) & 1u,
+                                                        bail ? kLltBailNs : kLltWaitNs)) {
+                    atomicExch(a.err, 3);
+                    bail = true;
+                }
+                const int b = cid + j * a.G;
+                const uint32_t dst = umma::smem_u32(sm + (size_t)s * L.stage);
+                umma::mbar_arrive_expect_tx(full0 + 8 * s, stage_tx);
+                for (int i = 0; i < a.nbox; ++i)
+                    umma::tma_load_2d(dst + (uint32_t)(i * a.box_rows * RB), &tmL, b * W,
+                                      row0 + i * a.box_rows, full0 + 8 * s);
+            }
+            // Drain: every stage's last load has landed before the CTA may exit.
+            for (int j = nj - kLltStages < 0 ? 0 : nj - kLltStages; j < nj; ++j)
+                if (!umma::mbar_wait(full0 + 8 * (j % kLltStages), (uint32_t)(j / kLltStages) & 1u, kLltWaitNs))
+                    atomicExch(a.err, 4);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- consumers
+        bool bail = false;
+        const int ch = warp % NCH, grp = warp / NCH;
+        for (int j = 0; j < nj; ++j) {
+            const int s = j % kLltStages, q = j % kLltSlots;
+            if (!umma::mbar_wait(full0 + 8 * s, (uint32_t)(j / kLltStages) & 1u, bail ? kLltBailNs : kLltWaitNs)) {
+                atomicExch(a.err, 1);
+                bail = true;
+            }
+            const uint8_t *sb = sm + (size_t)s * L.stage;
+            // Phase A: warp (chunk ch, row group grp) sums its rows, all-reduces
+            // over the warp and pushes the chunk's partials to every rank.
+            {
+                float acc[EPC];
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) acc[e] = 0.f;
+#pragma unroll 4
+                for (int r = grp * 32 + lane; r < a.rpc; r += 32 * NG) {
+                    const uint4 u = *reinterpret_cast<const uint4 *>(sb + llt::swz<RB>(r, ch));
+                    float f[EPC];
+                    S::unpack(u, f);
+                    const float yy = s_y[r];
+#pragma unroll
+                    for (int e = 0; e < EPC; ++e) acc[e] = fmaf(f[e], yy, acc[e]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int e = 0; e < EPC; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+                if (lane < C * V4) {
+                    const int dst = lane / V4, piece = lane % V4;
+                    float4 v = make_float4(acc[0], acc[1], acc[2], acc[3]);
+#pragma unroll
+                    for (int k = 1; k < V4; ++k)
+                        if (piece == k) v = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+                    const uint32_t local =
+                        slots_u32 + (uint32_t)((((q * C + rank) * NG + grp) * W + ch * EPC + 4 * piece) * 4);
+                    llt::st_async_v4(llt::mapa(local, (uint32_t)dst), v, llt::mapa(xchg0 + 8 * q, (uint32_t)dst));
+                }
+            }
+            // Receive: z_b = sum over ranks and row groups, in a fixed order.
+            float *zc = s_zc + (j & 1) * W;
+            if (tid < W) {
+                if (!llt::wait_cluster(xchg0 + 8 * q, (uint32_t)(j / kLltSlots) & 1u, bail ? kLltBailNs : kLltWaitNs)) {
+                    atomicExch(a.err, 2);
+                    bail = true;
+                }
+                const float *sl = slots + (size_t)q * C * NG * W + tid;
+                float z = 0.f;
+#pragma unroll
+                for (int k = 0; k < C * NG; ++k) z += sl[k * W];
+                zc[tid] = z;
+                if (tid == 0 && j + kLltSlots < nj) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
+            }
+            llt::bar_consumers();
+            // Phase B: g[rows] += L[rows, block j] z_b, one thread per row.  Under
+            // the swizzle the 8 rows of a quarter-warp hit distinct bank groups,
+            // while every thread reads the same z chunk (a broadcast).
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = tid + k * kLltConsumers;
+                if (r < a.rpc) {
+                    float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+                    for (int c = 0; c < NCH; ++c) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(sb + llt::swz<RB>(r, c));
+                        float f[EPC];
+                        S::unpack(u, f);
+#pragma unroll
+                        for (int e = 0; e < EPC; e += 4) {
+                            const float4 zq = *reinterpret_cast<const float4 *>(zc + c * EPC + e);
+                            d0 = fmaf(f[e], zq.x, d0);
+                            d1 = fmaf(f[e + 1], zq.y, d1);
+                            d0 = fmaf(f[e + 2], zq.z, d0);
+                            d1 = fmaf(f[e + 3], zq.w, d1);
+                        }
+                    }
+                    const float yk = (d0 + d1) - gc[k];
+                    const float tk = gs[k] + yk;
+                    gc[k] = (tk - gs[k]) - yk;
+                    gs[k] = tk;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) llt::mbar_arrive(empty0 + 8 * s);      // this warp is done with the stage
+        }
+        // Per-cluster partial of g for this CTA's rows.
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int r = tid + k * kLltConsumers;
+            if (r < a.rpc && row0 + r < a.n) a.gpart[(size_t)cid * a.n + row0 + r] = gs[k] - gc[k];
+        }
+    }
+
+    // Fixed-order two-level reduction of the per-cluster partials of this
+    // rank's rows: the last CTA of each group of kLltFan clusters adds the
+    // group's partials (FP64), the last group adds the group sums.
+    __shared__ int s_flag;
+    const int ngrp = (a.G + kLltFan - 1) / kLltFan, mygrp = cid / kLltFan;
+    const int c0 = mygrp * kLltFan, c1 = min(a.G, c0 + kLltFan);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_flag = atomicAdd(&a.tick1[rank * kLltMaxGroups + mygrp], 1u) == (unsigned)(c1 - c0 - 1);
+    __syncthreads();
+    if (s_flag) {
+        __threadfence();
+        for (int i = tid; i < a.rpc; i += kLltThreads) {
+            const int r = row0 + i;
+            if (r >= a.n) break;
+            double s = 0.0;
+#pragma unroll 8
+            for (int c = c0; c < c1; ++c) s += (double)__ldcg(a.gpart + (size_t)c * a.n + r);
+            a.gq[(size_t)mygrp * a.n + r] = s;
+        }
+        if (tid == 0) a.tick1[rank * kLltMaxGroups + mygrp] = 0u;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_flag = atomicAdd(&a.tick2[rank], 1u) == (unsigned)(ngrp - 1);
+        __syncthreads();
+        if (s_flag) {
+            __threadfence();
+            for (int i = tid; i < a.rpc; i += kLltThreads) {
+                const int r = row0 + i;
+                if (r >= a.n) break;
+                double s = 0.0;
+#pragma unroll 8
+                for (int k = 0; k < ngrp; ++k) s += __ldcg(a.gq + (size_t)k * a.n + r);
+                if (a.row_scale != nullptr) s *= (double)a.row_scale[r];
+                a.g[r] = s;
+                if (a.g32 != nullptr) a.g32[r] = (float)s;
+            }
+            if (tid == 0) a.tick2[rank] = 0u;
+        }
+    }
+    cluster.sync();                                     // no CTA leaves while a peer may still push to it
+}
+
+// ------------------------------------------------------------------ host
+constexpr size_t kLltSmemCap = 221 * 1024;
+
+// Geometry for one (cluster size C, row-segment bytes RB) choice.
+inline bool llt_shape(int64_t n, int64_t T, int esize, int C, int RB, LltPlan *p) {
+    const int W = RB / esize;
+    const int64_t rpc0 = (n + C - 1) / C;
+    const int nbox = (int)((rpc0 + 255) / 256);
+    const int box_rows = (int)(((rpc0 + nbox - 1) / nbox + 7) / 8 * 8);
+    const int rpc = nbox * box_rows;
+    if (rpc > kLltRowsPerThread * kLltConsumers) return false;
+    const size_t smem = llt_smem_layout(rpc, RB, W, C).total;
+    if (smem > kLltSmemCap) return false;
+    p->C = C;
+    p->RB = RB;
+    p->rpc = rpc;
+    p->box_rows = box_rows;
+    p->nbox = nbox;
+    p->nb = (int)((T + W - 1) / W);
+    p->smem = smem;
+    return true;
+}
+
+// The (C, RB) pairs the library instantiates, in order of preference: the
+// widest row segment that fits two stages (TMA row requests of 128 bytes
+// stream near the copy peak, 32-byte ones far below it), then the smaller
+// cluster (a cluster of 2 is a TPC pair, so clusters of 2 tile every SM;
+// clusters of 8 leave SMs of each GPC idle).
+constexpr int kLltShapes[][2] = {{2, 128}, {4, 128}, {2, 64}, {4, 64}, {2, 32}, {8, 128}};
+constexpr int kLltNumShapes = (int)(sizeof(kLltShapes) / sizeof(kLltShapes[0]));
+
+// 2-D tensor map over L for the fused pass: box = RB bytes of columns x box_rows rows,
+// RB-byte swizzle (RB = 32, 64 or 128).
+inline int make_map_llt(CUtensorMap *map, int dt, const void *base, int64_t n, int64_t T, int64_t ld, int box_rows,
+                        int RB) {
+    auto enc = tensor_map_encoder();
+    if (enc == nullptr) return record_message(MV_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int es = dtype_size(dt);
+    const CUtensorMapDataType ty = dt == MV_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dt == MV_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const CUtensorMapSwizzle sw = RB == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                  : RB == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                             : CU_TENSOR_MAP_SWIZZLE_128B;
+    cuuint64_t dims[2] = {(cuuint64_t)T, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+    cuuint32_t box[2] = {(cuuint32_t)(RB / es), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, ty, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char msg[128];
+        snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled (fused pass) failed (%d)", (int)r);
+        return record_message(MV_ERR_CUDA, msg);
+    }
+    return MV_OK;
+}
+
+}  // namespace mv

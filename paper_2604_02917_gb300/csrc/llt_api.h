@@ -1,0 +1,57 @@
+// Host interface of the fused single-pass Gram product g = L L^T y
+// (llt.cuh holds the kernel; llt_host.cu and llt_<dtype>.cu instantiate it).
+// Internal to libmv, not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace mv {
+
+constexpr int kLltMaxCluster = 8;          // largest cluster the pass uses
+constexpr int kLltMaxClusters = 128;       // clusters per launch (upper bound)
+constexpr int kLltFan = 8;                 // clusters per group of the final reduction
+constexpr int kLltMaxGroups = kLltMaxClusters / kLltFan;
+constexpr int64_t kLltMinN = 1024, kLltMinT = 4096;
+
+struct LltPlan {
+    bool ok;
+    int C, RB;                 // cluster size, bytes of one row per column block
+    int rpc, box_rows, nbox;   // rows per CTA, TMA box rows, boxes per stage
+    int nb, G;                 // column blocks, clusters launched
+    size_t smem;               // dynamic shared memory per CTA
+};
+
+// Scratch of the pass inside a caller workspace (offsets from its base).
+struct LltScratch {
+    float *gpart;              // [kLltMaxClusters x n]
+    double *gq;                // [kLltMaxGroups x n]
+    unsigned *tickets;         // zero between launches
+    int *err;                  // error word
+};
+size_t llt_scratch_bytes(int64_t n);
+LltScratch llt_scratch(void *base, int64_t n);
+size_t llt_ticket_bytes();     // bytes of sc.tickets to zero before the first launch
+
+// Geometry for an n x T factor of dtype dt (ok = false where the pass does
+// not apply).  with_device = false skips the device query and only decides
+// whether a shape exists (workspace sizing must not depend on the device).
+// MV_LLT_SHAPE="C,RB" in the environment forces one shape (tuning).
+LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device);
+
+// Enqueues g = L L^T y (row-scaled; FP8 y32 pre-multiplied by the scale) on
+// stream s; capturable.  done (nullable): the launch returns at once if *done.
+int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
+               const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s);
+
+// Per-dtype entry points (llt_<dtype>.cu).
+int llt_max_clusters_f32(int C, int RB, size_t smem);
+int llt_max_clusters_bf16(int C, int RB, size_t smem);
+int llt_max_clusters_fp8(int C, int RB, size_t smem);
+struct LltArgs;
+cudaError_t llt_launch_f32(int C, int RB, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
+cudaError_t llt_launch_bf16(int C, int RB, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
+cudaError_t llt_launch_fp8(int C, int RB, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
+
+}  // namespace mv

@@ -1,0 +1,116 @@
+// Host side of the fused single-pass Gram product (llt.cuh): shape choice,
+// device occupancy query, tensor map and launch.
+#include <stdio.h>
+#include <stdlib.h>
+
+#include <algorithm>
+#include <mutex>
+#include <unordered_map>
+
+#include "llt.cuh"
+
+namespace mv {
+
+size_t llt_ticket_bytes() { return 4 * (size_t)kLltMaxCluster * (kLltMaxGroups + 1); }
+
+size_t llt_scratch_bytes(int64_t n) {
+    return align_up(4 * (size_t)n * kLltMaxClusters, 256) + align_up(8 * (size_t)n * kLltMaxGroups, 256) +
+           align_up(llt_ticket_bytes(), 256) + 256;
+}
+
+LltScratch llt_scratch(void *base, int64_t n) {
+    char *p = reinterpret_cast<char *>(base);
+    LltScratch sc;
+    sc.gpart = reinterpret_cast<float *>(p);
+    p += align_up(4 * (size_t)n * kLltMaxClusters, 256);
+    sc.gq = reinterpret_cast<double *>(p);
+    p += align_up(8 * (size_t)n * kLltMaxGroups, 256);
+    sc.tickets = reinterpret_cast<unsigned *>(p);
+    p += align_up(llt_ticket_bytes(), 256);
+    sc.err = reinterpret_cast<int *>(p);
+    return sc;
+}
+
+static int max_clusters(int dt, int C, int RB, size_t smem) {
+    static std::mutex mu;
+    static std::unordered_map<uint64_t, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    const uint64_t key = ((uint64_t)dev << 56) ^ ((uint64_t)dt << 48) ^ ((uint64_t)C << 40) ^ ((uint64_t)RB << 32) ^
+                         (uint64_t)smem;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int v = dt == MV_F32    ? llt_max_clusters_f32(C, RB, smem)
+            : dt == MV_BF16 ? llt_max_clusters_bf16(C, RB, smem)
+                            : llt_max_clusters_fp8(C, RB, smem);
+    v = std::min(v, kLltMaxClusters);
+    cache.emplace(key, v);
+    return v;
+}
+
+LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device) {
+    LltPlan p{};
+    p.ok = false;
+    const int es = dtype_size(dt);
+    if (es == 0 || n < kLltMinN || T < kLltMinT) return p;
+    int fC = 0, fRB = 0;
+    if (const char *env = getenv("MV_LLT_SHAPE")) {
+        if (sscanf(env, "%d,%d", &fC, &fRB) != 2) fC = fRB = 0;
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = 0; i < kLltNumShapes; ++i) {
+            const int C = kLltShapes[i][0], RB = kLltShapes[i][1];
+            if (pass == 0 && fC != 0 && (C != fC || RB != fRB)) continue;
+            LltPlan q{};
+            if (!llt_shape(n, T, es, C, RB, &q)) continue;
+            if (!with_device) {
+                q.ok = true;
+                q.G = 1;
+                return q;
+            }
+            const int mc = max_clusters(dt, C, RB, q.smem);
+            if (mc < 1) continue;
+            q.G = std::max(1, std::min(mc, q.nb));
+            q.ok = true;
+            return q;
+        }
+        if (fC == 0) break;                  // no override: one pass over the preference list
+    }
+    return p;
+}
+
+int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
+               const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s) {
+    if (!lp.ok) return MV_ERR_UNSUPPORTED;
+    CUtensorMap map;
+    MV_TRY(make_map_llt(&map, dt, L, n, T, ld, lp.box_rows, lp.RB));
+    LltArgs a;
+    a.y32 = y32;
+    a.row_scale = row_scale;
+    a.gpart = sc.gpart;
+    a.gq = sc.gq;
+    a.g = g;
+    a.g32 = g32;
+    a.tick1 = sc.tickets;
+    a.tick2 = sc.tickets + (size_t)kLltMaxCluster * kLltMaxGroups;
+    a.err = sc.err;
+    a.done = done;
+    a.n = (int)n;
+    a.T = (int)T;
+    a.rpc = lp.rpc;
+    a.box_rows = lp.box_rows;
+    a.nbox = lp.nbox;
+    a.nb = lp.nb;
+    a.G = lp.G;
+    const cudaError_t e = dt == MV_F32    ? llt_launch_f32(lp.C, lp.RB, lp.G, lp.smem, &map, a, s)
+                          : dt == MV_BF16 ? llt_launch_bf16(lp.C, lp.RB, lp.G, lp.smem, &map, a, s)
+                                          : llt_launch_fp8(lp.C, lp.RB, lp.G, lp.smem, &map, a, s);
+    if (e != cudaSuccess) return record_cuda_error(e, "fused L L^T pass launch", __FILE__, __LINE__);
+    return MV_OK;
+}
+
+}  // namespace mv

@@ -1,0 +1,87 @@
+// Instantiates the fused pass for one element type (MV_LLT_DT, MV_LLT_SUFFIX):
+// kernel attributes, the occupancy query and the launch for every shape.
+#pragma once
+
+#include "llt.cuh"
+
+#define MV_LLT_CAT2(a, b) a##b
+#define MV_LLT_CAT(a, b) MV_LLT_CAT2(a, b)
+
+namespace mv {
+namespace {
+
+template <int C, int RB>
+int attrs() {
+    static int st = -1;
+    if (st < 0) {
+        const int smem = (int)(kLltSmemCap + 256);
+        st = (cudaFuncSetAttribute(llt_kernel<MV_LLT_DT, C, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(llt_kernel<MV_LLT_DT, C, RB>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess)
+                 ? MV_OK
+                 : MV_ERR_CUDA;
+        if (st != MV_OK) (void)cudaGetLastError();
+    }
+    return st;
+}
+
+cudaLaunchConfig_t config(int C, int G, size_t smem, cudaStream_t s, cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(C * G));
+    cfg.blockDim = dim3(kLltThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <int C, int RB>
+int max_clusters(size_t smem) {
+    if (attrs<C, RB>() != MV_OK) return 0;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = config(C, kLltMaxClusters, smem, nullptr, attr);
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, llt_kernel<MV_LLT_DT, C, RB>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return num;
+}
+
+template <int C, int RB>
+cudaError_t launch(int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s) {
+    if (attrs<C, RB>() != MV_OK) return cudaErrorInvalidValue;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = config(C, G, smem, s, attr);
+    return cudaLaunchKernelEx(&cfg, llt_kernel<MV_LLT_DT, C, RB>, *reinterpret_cast<const CUtensorMap *>(map), a);
+}
+
+}  // namespace
+
+// The instantiated shapes (kLltShapes).
+#define MV_LLT_SWITCH(C, RB, F, ...)                                     \
+    if (C == 2 && RB == 128) return F<2, 128>(__VA_ARGS__);              \
+    if (C == 4 && RB == 128) return F<4, 128>(__VA_ARGS__);              \
+    if (C == 2 && RB == 64) return F<2, 64>(__VA_ARGS__);                \
+    if (C == 4 && RB == 64) return F<4, 64>(__VA_ARGS__);                \
+    if (C == 2 && RB == 32) return F<2, 32>(__VA_ARGS__);                \
+    if (C == 8 && RB == 128) return F<8, 128>(__VA_ARGS__);
+
+int MV_LLT_CAT(llt_max_clusters_, MV_LLT_SUFFIX)(int C, int RB, size_t smem) {
+    MV_LLT_SWITCH(C, RB, max_clusters, smem)
+    return 0;
+}
+
+cudaError_t MV_LLT_CAT(llt_launch_, MV_LLT_SUFFIX)(int C, int RB, int G, size_t smem, const void *map,
+                                                    const LltArgs &a, cudaStream_t s) {
+    MV_LLT_SWITCH(C, RB, launch, G, smem, map, a, s)
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace mv

@@ -18,6 +18,7 @@
 
 #include "gemm.cuh"
 #include "gemv.cuh"
+#include "llt_api.h"
 #include "project.cuh"
 
 namespace mv {
@@ -42,8 +43,11 @@ struct Plan {
     int cl;                                // cluster size of the step kernel
     int t_blocks, t_splits, t_rows;        // gemv_t grid
     int n_groups, n_splits, n_cols;        // gemv_n grid
+    bool use_llt;                          // fused single-pass L L^T y (llt.cuh)
+    LltPlan lp;
     // workspace offsets (bytes)
     size_t o_state, o_x, o_y, o_gx, o_gy, o_g32, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
+    size_t o_llt, o_err;
     int64_t zstride;                       // row pitch (floats) of the gemv_t partials
     size_t total;
 };
@@ -62,7 +66,9 @@ static int sm_count() {
 
 static constexpr int kRW = 4;   // rows per warp in gemv_n
 
-static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows = 0) {
+// The fused pass pays a cluster exchange per 128-byte column block, so it is
+// used where a block holds many rows and there are many blocks.
+static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows = 0, bool fused = false) {
     Plan p{};
     p.dt = dt;
     p.esize = dtype_size(dt);
@@ -114,6 +120,16 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows
     p.o_gpart = take(4 * (size_t)n * p.n_splits);
     p.o_tick_t = take(4 * (size_t)p.t_blocks);
     p.o_tick_n = take(4 * (size_t)p.n_groups);
+    p.use_llt = false;
+    p.lp = LltPlan{};
+    if (fused && llt_plan(dt, n, T, false).ok) {
+        // The scratch is sized without the device query, so the workspace
+        // size does not depend on the device.
+        p.o_llt = take(llt_scratch_bytes(n));
+        p.lp = llt_plan(dt, n, T, true);
+        p.use_llt = p.lp.ok;
+    }
+    p.o_err = take(16);
     p.total = off;
     return p;
 }
@@ -507,6 +523,15 @@ static void launch_gemv_n(const Plan &p, const void *L, const float *z, const fl
                                                            p.n_cols, done);
 }
 
+// g = L L^T y (row-scaled) in one pass over L; capturable (no synchronisation).
+static int launch_llt(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
+                      float *g32, cudaStream_t s) {
+    LltScratch sc = llt_scratch(at<char>(ws, p.o_llt), p.n);
+    sc.err = at<int>(ws, p.o_err);             // read back by the solve
+    return llt_launch(p.lp, p.dt, P->L, p.n, p.T, p.ld, y32, P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr, sc,
+                      done, g_out, g32, s);
+}
+
 // Kernel attributes are set once per process, before any stream capture.
 template <typename Kern>
 static bool cluster_attrs(Kern k, int CL) {
@@ -631,9 +656,10 @@ static void launch_init_x(const Plan &p, const mv_problem *P, const double *x_in
 }
 
 // One loop iteration.  With `ev` non-null, events ev[0..3] bracket gemv_t,
-// gemv_n and the step kernel (ev[3] is the next iteration's ev[0]).
-static void launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
-                             cudaStream_t s, const cudaEvent_t *ev) {
+// gemv_n and the step kernel (ev[3] is the next iteration's ev[0]); with the
+// fused pass, ev[0..1] bracket it and ev[1..2] is empty.
+static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
+                            cudaStream_t s, const cudaEvent_t *ev) {
     SolveState *st = at<SolveState>(ws, p.o_state);
     float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z), *gpart = at<float>(ws, p.o_gpart);
     unsigned *tt = at<unsigned>(ws, p.o_tick_t), *tn = at<unsigned>(ws, p.o_tick_n);
@@ -641,6 +667,14 @@ static void launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_
     double *gy = at<double>(ws, p.o_gy);
     const int *done = &st->done;
     if (ev) cudaEventRecord(ev[0], s);
+    if (p.use_llt) {
+        MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s));
+        if (ev) cudaEventRecord(ev[1], s);
+        if (ev) cudaEventRecord(ev[2], s);
+        launch_step(p, P, O, ws, s);
+        if (ev) cudaEventRecord(ev[3], s);
+        return MV_OK;
+    }
     switch (p.dt) {
         case MV_F32: launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, done, s); break;
         case MV_BF16: launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, done, s); break;
@@ -655,6 +689,7 @@ static void launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_
     if (ev) cudaEventRecord(ev[2], s);
     launch_step(p, P, O, ws, s);
     if (ev) cudaEventRecord(ev[3], s);
+    return MV_OK;
 }
 
 // Process-wide pool of timing events, reused so cached graphs stay valid.
@@ -677,13 +712,13 @@ static int timing_events(int count, const cudaEvent_t **out) {
 struct GraphKey {
     const void *L, *mu, *rs, *ws;
     int64_t n, T, ld;
-    int dt, mode, kkt_every, max_iter, chunk;
+    int dt, mode, kkt_every, max_iter, chunk, fused;
     double R, gamma, eps;
     const void *ev;
     bool operator==(const GraphKey &o) const {
         return L == o.L && mu == o.mu && rs == o.rs && ws == o.ws && n == o.n && T == o.T && ld == o.ld &&
                dt == o.dt && mode == o.mode && kkt_every == o.kkt_every && max_iter == o.max_iter &&
-               chunk == o.chunk && R == o.R && gamma == o.gamma && eps == o.eps && ev == o.ev;
+               chunk == o.chunk && fused == o.fused && R == o.R && gamma == o.gamma && eps == o.eps && ev == o.ev;
     }
 };
 struct GraphKeyHash {
@@ -699,7 +734,7 @@ static std::unordered_map<GraphKey, cudaGraphExec_t, GraphKeyHash> g_graphs;
 static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
                            const cudaEvent_t *ev, cudaGraphExec_t *out) {
     GraphKey key{P->L, P->mu, P->row_scale, ws, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
-                 O->max_iter, chunk, P->R_target, P->gamma, O->eps, (const void *)ev};
+                 O->max_iter, chunk, p.use_llt ? 1 : 0, P->R_target, P->gamma, O->eps, (const void *)ev};
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_graph_mu);
@@ -715,9 +750,14 @@ static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_op
         cudaStreamDestroy(cs);
         return MV_ERR_CUDA;
     }
-    for (int c = 0; c < chunk; ++c) launch_iteration(p, P, O, ws, cs, ev ? ev + 3 * c : nullptr);
+    int lst = MV_OK;
+    for (int c = 0; c < chunk && lst == MV_OK; ++c) lst = launch_iteration(p, P, O, ws, cs, ev ? ev + 3 * c : nullptr);
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
+    if (lst != MV_OK) {
+        if (e == cudaSuccess) cudaGraphDestroy(graph);
+        return lst;
+    }
     if (e != cudaSuccess) return MV_ERR_CUDA;
     cudaGraphExec_t exec;
     e = cudaGraphInstantiate(&exec, graph, 0);
@@ -751,19 +791,19 @@ void mv_solve_opts_default(mv_solve_opts *o) {
     o->use_graph = 1;
     o->timing = 0;
     o->checkpoint_every = 50;
-    o->reserved = 0;
+    o->two_pass = 0;
 }
 
 size_t mv_npga_workspace_size(const mv_problem *P) {
     if (validate_problem(P) != MV_OK) return 0;
-    return make_plan(P->dtype, P->n, P->T, P->ld).total;
+    return make_plan(P->dtype, P->n, P->T, P->ld, 0, true).total;
 }
 
 int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g, void *d_ws, size_t ws_bytes,
                 mv_stream_t stream) {
     MV_TRY(validate_problem(P));
     if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, d_z == nullptr);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();
@@ -774,7 +814,13 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
     const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
     to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(d_y, rs, y32, p.n);
-    gemv_pair(p, P, y32, d_ws, nullptr, lz, s);
+    if (p.use_llt) {
+        MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
+        MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
+        MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, lz, nullptr, s));
+    } else {
+        gemv_pair(p, P, y32, d_ws, nullptr, lz, s);
+    }
     grad_finish_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(lz, d_y, P->gamma, d_g, p.n);
     if (d_z) MV_CUDA_TRY(cudaMemcpyAsync(d_z, at<float>(d_ws, p.o_z), 4 * (size_t)p.T, cudaMemcpyDeviceToDevice, s));
     MV_CUDA_TRY(cudaGetLastError());
@@ -788,7 +834,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, O.two_pass == 0);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();   // start from a clean error state
@@ -800,14 +846,24 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
 
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
+    if (p.use_llt) MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
     setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
     // Power method for ||L_eff||_2^2 (skipped when the step is given).
+    int launches = 4;
     if (!(O.alpha > 0.0)) {
         for (int it = 0; it < O.power_iters; ++it) {
-            gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
+            if (p.use_llt) {
+                MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
+                launches += 2;
+            } else {
+                gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
+                launches += 3;
+            }
             power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
         }
         gemv_t_only(p, P, y32, d_ws, s);
+        launches += 1;
     }
     step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0) ? 0 : p.T, P->gamma,
                                                 O.power_safety, O.alpha);
@@ -815,7 +871,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     MV_CUDA_TRY(cudaGetLastError());
 
     const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
-    int launches = 4 + (O.alpha > 0.0 ? 0 : 3 * O.power_iters + 1);
+    const int per_iter = p.use_llt ? 2 : 3;
     const cudaEvent_t *ev = nullptr;
     if (O.timing) MV_TRY(timing_events(3 * chunk + 1, &ev));
     // Events recorded by graph nodes cannot be timed, so a timed solve issues
@@ -831,10 +887,10 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
         if (exec) {
             MV_CUDA_TRY(cudaGraphLaunch(exec, s));
         } else {
-            for (int i = 0; i < chunk; ++i) launch_iteration(p, P, &O, d_ws, s, ev ? ev + 3 * i : nullptr);
+            for (int i = 0; i < chunk; ++i) MV_TRY(launch_iteration(p, P, &O, d_ws, s, ev ? ev + 3 * i : nullptr));
             MV_CUDA_TRY(cudaGetLastError());
         }
-        launches += 3 * chunk;
+        launches += per_iter * chunk;
         MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         MV_CUDA_TRY(cudaStreamSynchronize(s));
         if (ev) {
@@ -864,10 +920,17 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
                                                 P->gamma);
     MV_CUDA_TRY(cudaMemcpyAsync(d_x_inout, at<double>(d_ws, p.o_x), 8 * (size_t)p.n, cudaMemcpyDeviceToDevice, s));
     MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    int xerr = 0;
+    MV_CUDA_TRY(cudaMemcpyAsync(&xerr, at<int>(d_ws, p.o_err), sizeof(int), cudaMemcpyDeviceToHost, s));
     MV_CUDA_TRY(cudaStreamSynchronize(s));
     MV_CUDA_TRY(cudaGetLastError());
     h_info->iterations = hs.k;
     h_info->status = hs.done ? hs.status : MV_ERR_NOT_CONVERGED;
+    if (xerr != 0) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "fused L L^T pass: pipeline wait timed out (code %d)", xerr);
+        h_info->status = record_message(MV_ERR_TIMEOUT, msg);
+    }
     h_info->converged = hs.converged;
     h_info->proj_failures = hs.proj_fail;
     h_info->kkt = hs.kkt;
@@ -877,8 +940,10 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     h_info->nu = hs.nu;
     h_info->launches = launches;
     h_info->timed_pairs = timed;
-    h_info->t_gemv_t_ms = t_t;
-    h_info->t_gemv_n_ms = t_n;
+    h_info->t_gemv_t_ms = p.use_llt ? 0.0 : t_t;
+    h_info->t_gemv_n_ms = p.use_llt ? 0.0 : t_n;
+    h_info->t_fused_ms = p.use_llt ? t_t : 0.0;
+    h_info->fused = p.use_llt ? 1 : 0;
     h_info->t_step_ms = t_s;
     h_info->proj_steps = hs.proj_steps;
     return h_info->status;
@@ -1620,7 +1685,7 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     int launches = 4;
     for (int k = 0; k < K; ++k) {
         if (k % C == 0) MV_TRY(save_cp(k / C));
-        launch_iteration(p, P, &O, ws, s, nullptr);
+        MV_TRY(launch_iteration(p, P, &O, ws, s, nullptr));
         launches += 3;
     }
     MV_CUDA_TRY(cudaGetLastError());
@@ -1660,7 +1725,7 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
         MV_TRY(load_cp(seg));
         for (int j = 0; j < len; ++j) {
             MV_CUDA_TRY(cudaMemcpyAsync(VY + (size_t)(len + j) * n, y32, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
-            launch_iteration(p, P, &O, ws, s, nullptr);
+            MV_TRY(launch_iteration(p, P, &O, ws, s, nullptr));
             MV_CUDA_TRY(cudaMemcpyAsync(ZW + (size_t)j * T, at<float>(ws, p.o_z), 4 * (size_t)T,
                                         cudaMemcpyDeviceToDevice, s));
             MV_CUDA_TRY(cudaMemcpyAsync(X1 + (size_t)j * n, at<double>(ws, p.o_x), 8 * (size_t)n,

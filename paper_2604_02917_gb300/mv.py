@@ -65,7 +65,7 @@ class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("kkt_every", C.c_int32), ("power_iters", C.c_int32),
                 ("warm_start", C.c_int32), ("eps", C.c_double), ("power_safety", C.c_double),
                 ("alpha", C.c_double), ("use_graph", C.c_int32), ("timing", C.c_int32),
-                ("checkpoint_every", C.c_int32), ("reserved", C.c_int32)]
+                ("checkpoint_every", C.c_int32), ("two_pass", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -74,7 +74,7 @@ class SolveInfo(C.Structure):
                 ("alpha", C.c_double), ("lambda_hat", C.c_double), ("nu", C.c_double),
                 ("launches", C.c_int32), ("timed_pairs", C.c_int32), ("t_gemv_t_ms", C.c_double),
                 ("t_gemv_n_ms", C.c_double), ("t_step_ms", C.c_double), ("proj_steps", C.c_int32),
-                ("refine_iterations", C.c_int32)]
+                ("refine_iterations", C.c_int32), ("fused", C.c_int32), ("t_fused_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -277,11 +277,13 @@ class Solver:
         _check(st, "mv_npga_solve", allow)
         return self.x, info.as_dict()
 
-    def gradient(self, y: torch.Tensor):
-        z = torch.empty(self.problem.T, dtype=torch.float32, device=y.device)
+    def gradient(self, y: torch.Tensor, with_z: bool = True):
+        """(z, g); with ``with_z=False`` z is None and g comes from the fused
+        single pass over L where that applies."""
+        z = torch.empty(self.problem.T, dtype=torch.float32, device=y.device) if with_z else None
         g = torch.empty_like(y)
-        _check(lib().mv_gradient(C.byref(self.problem), _ptr(y), _ptr(z), _ptr(g), _ptr(self.ws),
-                                 self.ws.numel(), _stream()), "mv_gradient")
+        _check(lib().mv_gradient(C.byref(self.problem), _ptr(y), _ptr(z) if with_z else None, _ptr(g),
+                                 _ptr(self.ws), self.ws.numel(), _stream()), "mv_gradient")
         return z, g
 
 
@@ -317,11 +319,12 @@ def npga_solve(L, mu, R_target, T, gamma=0.0, dtype="f32", row_scale=None, mode=
     return s.solve(x0)
 
 
-def gradient(L, y, T, gamma=0.0, dtype="f32", row_scale=None):
-    """(z, g) with z = L^T y (FP32) and g = 2 L z + 2 gamma y (FP64)."""
+def gradient(L, y, T, gamma=0.0, dtype="f32", row_scale=None, with_z=True):
+    """(z, g) with z = L^T y (FP32) and g = 2 L z + 2 gamma y (FP64).
+    ``with_z=False``: z is None and g uses the fused single pass where it applies."""
     mu = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
     s = Solver(L, mu, 0.0, T, gamma, dtype, row_scale)
-    return s.gradient(y)
+    return s.gradient(y, with_z)
 
 
 def gradient_noalloc(L, y, T, gamma=0.0, dtype="f32", row_scale=None):

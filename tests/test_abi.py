@@ -56,10 +56,11 @@ def _c_layout(tmp_path):
         "mv_problem": ["L", "dtype", "mode", "row_scale", "n", "T", "ld", "gamma", "mu", "R_target",
                        "power_start"],
         "mv_solve_opts": ["max_iter", "kkt_every", "power_iters", "warm_start", "eps", "power_safety",
-                          "alpha", "use_graph", "timing", "checkpoint_every", "reserved"],
+                          "alpha", "use_graph", "timing", "checkpoint_every", "two_pass"],
         "mv_solve_info": ["iterations", "status", "converged", "proj_failures", "kkt", "objective",
                           "alpha", "lambda_hat", "nu", "launches", "timed_pairs", "t_gemv_t_ms",
-                          "t_gemv_n_ms", "t_step_ms", "proj_steps", "refine_iterations"],
+                          "t_gemv_n_ms", "t_step_ms", "proj_steps", "refine_iterations", "fused",
+                          "t_fused_ms"],
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mv.h"', "int main(void){"]
     for st, fs in fields.items():

@@ -152,6 +152,71 @@ def test_gradient_parity(mv, dt, shape):
     assert np.max(np.abs(g.cpu().numpy() - g_o)) <= 2e-5 * np.max(np.abs(g_o)) + 1e-30
 
 
+# Fused single pass g = L L^T y (one HBM pass; applies for n >= 1024, T >= 4096).
+# Shapes: exact multiples, ragged T (partial last column block), ragged n (the
+# last CTA of a cluster holds rows past n), and the largest n with 3 stages.
+@pytest.mark.parametrize("dt", ["f32", "bf16", "fp8"])
+@pytest.mark.parametrize("shape", [(1024, 4096), (1030, 4099), (2100, 9001), (5440, 6007)])
+def test_gradient_fused_parity(mv, dt, shape):
+    n, T = shape
+    R32, _ = panel(n, T, seed=7)
+    L, rs, mu, _ = mv.center_factor(gpu(R32), dt)
+    Lq = dequant(mv, L, rs, T, dt)
+    y = np.random.default_rng(3).dirichlet(np.ones(n))
+    gamma = 1e-5
+    zf, gf = mv.gradient(L, gpu(y), T, gamma, dt, rs, with_z=False)
+    assert zf is None
+    _, g2 = mv.gradient(L, gpu(y), T, gamma, dt, rs, with_z=True)
+    g_o = gradient(Lq, gamma, y)
+    gf = gf.cpu().numpy()
+    assert np.max(np.abs(gf - g_o)) <= 2e-5 * np.max(np.abs(g_o))
+    assert np.max(np.abs(gf - g2.cpu().numpy())) <= 2e-5 * np.max(np.abs(g_o))
+    # deterministic: the same bits on a second call
+    _, gf2 = mv.gradient(L, gpu(y), T, gamma, dt, rs, with_z=False)
+    assert np.array_equal(gf, gf2.cpu().numpy())
+
+
+@pytest.mark.parametrize("shape", [(6400, 4100), (8200, 4096), (16000, 4096)])
+def test_gradient_fused_larger_clusters(mv, shape):
+    """n past a 2-CTA cluster's row capacity: clusters of 4 and 8 CTAs."""
+    n, T = shape
+    R32, _ = panel(n, T, seed=8)
+    L, rs, mu, _ = mv.center_factor(gpu(R32), "f32")
+    y = np.random.default_rng(4).dirichlet(np.ones(n))
+    _, gf = mv.gradient(L, gpu(y), T, 0.0, "f32", rs, with_z=False)
+    g_o = gradient(L[:, :T].double().cpu().numpy(), 0.0, y)
+    assert np.max(np.abs(gf.cpu().numpy() - g_o)) <= 2e-5 * np.max(np.abs(g_o))
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+@pytest.mark.parametrize("case", [(1500, 6000, 0.0, "ge", 60), (1100, 4500, 2e-5, "eq", 40)])
+def test_npga_fused_parity(mv, dt, case):
+    n, T, gamma, mode, pct = case
+    R32, R64 = panel(n, T, seed=n + 1, base=CFG_FULL)
+    L, rs, mu, _ = mv.center_factor(gpu(R32), dt)
+    Lq = dequant(mv, L, rs, T, dt)
+    mu_o = mu.cpu().numpy()
+    Rt = float(np.percentile(mu_o, pct))
+    r0 = power_start(n)
+    x, info = mv.npga_solve(L, mu, Rt, T, gamma=gamma, dtype=dt, row_scale=rs, mode=mode, eps=1e-6,
+                            power_start=gpu(r0))
+    assert info["fused"] == 1
+    assert info["converged"] == 1 and info["status"] == 0 and info["kkt"] <= 1e-6
+    assert info["lambda_hat"] == pytest.approx(power_norm2(Lq, r0, 50), rel=1e-5)
+    x = x.cpu().numpy()
+    ref = oracle_solution(Lq, mu_o, Rt, gamma, mode)
+    assert np.max(np.abs(x - ref.x)) <= 1e-4
+    f = objective(Lq, gamma, x)
+    assert (f - ref.f) / ref.f <= 1e-5
+    assert info["objective"] == pytest.approx(f, rel=1e-5)
+    assert kkt_residual(Lq, gamma, mu_o, Rt, x, info["alpha"], mode) <= 1.05e-6
+    # the two-pass loop reaches the same point
+    x2, info2 = mv.npga_solve(L, mu, Rt, T, gamma=gamma, dtype=dt, row_scale=rs, mode=mode, eps=1e-6,
+                              power_start=gpu(r0), two_pass=1)
+    assert info2["fused"] == 0 and info2["converged"] == 1
+    assert np.max(np.abs(x2.cpu().numpy() - x)) <= 1e-5
+
+
 # ------------------------------------------------------------------ NPGA
 def oracle_solution(L64, mu, Rt, gamma=0.0, mode="ge"):
     lam = power_norm2(L64, power_start(L64.shape[0]), 200)
