@@ -62,6 +62,16 @@ typedef enum {
     MV_RETURN_EQ = 1   /* mu^T x == R_target: equality variant (nu of any sign) */
 } mv_return_mode;
 
+/* Storage layout of the factor L (n assets x T periods) in device memory. */
+typedef enum {
+    MV_LAYOUT_NT = 0,  /* n x T row-major (one asset per row), leading dim >= T  */
+    MV_LAYOUT_TN = 1   /* L^T stored: T x n row-major (one period per row),
+                          leading dim >= n.  The solve's products read it in
+                          long runs along assets, which streams faster.  Only
+                          centering, the gradient and the single-problem solves
+                          (plain and refined) accept it.                        */
+} mv_layout;
+
 /* Human-readable name of a status code (static string, never NULL). */
 const char *mv_status_string(int status);
 
@@ -79,8 +89,11 @@ const char *mv_last_error(void);
  *
  *  d_R        [in]  n x T returns, FP32, row-major with leading dim ldR >= T.
  *  out_dtype  [in]  storage type of L (MV_F32, MV_BF16 or MV_FP8_E4M3).
- *  d_L        [out] n x T factor of that type, leading dim ldL >= T; columns
- *                   T..ldL-1 of every row are written as zeros.
+ *  layout     [in]  mv_layout of d_L.
+ *  d_L        [out] the factor in that type: MV_LAYOUT_NT: n x T, leading dim
+ *                   ldL >= T, columns T..ldL-1 of every row written as zeros;
+ *                   MV_LAYOUT_TN: L^T, T x n, leading dim ldL >= n, columns
+ *                   n..ldL-1 written as zeros (a tiled transpose on the way).
  *  d_row_scale[out] FP8 only (else may be NULL): n FP32 scales s_i such that
  *                   L(i,t) ~= s_i * q(i,t); s_i = max_t |L(i,t)| / 448.
  *  d_mu       [out] n FP64 sample means.
@@ -90,7 +103,7 @@ const char *mv_last_error(void);
  * ------------------------------------------------------------------------ */
 size_t mv_center_workspace_size(int64_t n, int64_t T);
 int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR,
-                     int out_dtype, void *d_L, int64_t ldL, float *d_row_scale,
+                     int out_dtype, int layout, void *d_L, int64_t ldL, float *d_row_scale,
                      double *d_mu, double *d_trace,
                      void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
@@ -148,15 +161,18 @@ int mv_project(const double *d_v, const double *d_mu, const double *d_R_target,
  *  so the check costs one projection and no extra pass over L.
  * ------------------------------------------------------------------------ */
 typedef struct {
-    const void *L;            /* d: n x T factor (dtype), row-major, leading dim ld     */
+    const void *L;            /* d: the factor (dtype) in `layout`, leading dim ld       */
     int32_t dtype;            /* mv_dtype                                                */
     int32_t mode;             /* mv_return_mode                                          */
     const float *row_scale;   /* d: n FP32 row scales (FP8 only, else NULL)              */
-    int64_t n, T, ld;         /* 1 <= n <= 32768 assets, T >= 1 periods, ld >= T         */
+    int64_t n, T, ld;         /* 1 <= n <= 32768 assets, T >= 1 periods; ld >= T (NT)
+                                 or ld >= n (TN)                                         */
     double gamma;             /* ridge (0 for the full and sketched models)              */
     const double *mu;         /* d: n FP64 expected returns                              */
     double R_target;          /* target return                                           */
     const double *power_start;/* d: n FP64 start of the power method; NULL = all ones    */
+    int32_t layout;           /* mv_layout of L (MV_LAYOUT_TN: T x n, ld >= n)           */
+    int32_t reserved;         /* 0                                                       */
 } mv_problem;
 
 typedef struct {

@@ -3,7 +3,8 @@
 // One block per asset row.  Pass 1 sums the row in FP64 for mu_i; pass 2
 // accumulates sum_t ((R_it - mu_i) c)^2 in FP64 (and max |.| for the FP8
 // row scale); pass 3 writes L in the storage type, zero-filling columns
-// T..ldL-1.  Passes 2 and 3 re-read a row the block has just streamed, so
+// T..ldL-1.  For the transposed layout (L^T, T x n) pass 3 is replaced by a
+// tiled transpose that reads R again along periods.  Passes 2 and 3 re-read a row the block has just streamed, so
 // they mostly hit L2.  Per-row sums of squares are added in a second,
 // single-block kernel in fixed order, so tr(Sigma) is deterministic.
 #include <stdio.h>
@@ -41,7 +42,9 @@ __device__ __forceinline__ void store_elem(void *L, int64_t idx, double val, flo
     }
 }
 
-template <int DT>
+// WRITE = false: statistics only (mu, row sums of squares, FP8 scale); the
+// transposed layout is then written by transpose_center_kernel.
+template <int DT, bool WRITE>
 __global__ void __launch_bounds__(kCenterThreads)
 center_kernel(const float *__restrict__ R, int64_t ldR, int T, void *__restrict__ L, int64_t ldL,
               float *__restrict__ row_scale, double *__restrict__ mu, double *__restrict__ rowsq) {
@@ -71,13 +74,42 @@ center_kernel(const float *__restrict__ R, int64_t ldR, int T, void *__restrict_
         inv_scale = 1.f / scale;
         if (threadIdx.x == 0) row_scale[i] = scale;
     }
-    for (int64_t t = threadIdx.x; t < ldL; t += kCenterThreads) {
-        const double d = t < T ? ((double)r[t] - mean) * c : 0.0;
-        store_elem<DT>(L, i * ldL + t, d, inv_scale);
+    if constexpr (WRITE) {
+        for (int64_t t = threadIdx.x; t < ldL; t += kCenterThreads) {
+            const double d = t < T ? ((double)r[t] - mean) * c : 0.0;
+            store_elem<DT>(L, i * ldL + t, d, inv_scale);
+        }
     }
     if (threadIdx.x == 0) {
         mu[i] = mean;
         rowsq[i] = q[0];
+    }
+}
+
+// L^T (T x ldM, row t = period t) from R (n x T): 32 x 32 tiles through
+// shared memory, read along periods and written along assets; columns
+// n..ldM-1 are written as zeros.  Values as center_kernel's.
+constexpr int kTile = 32;
+template <int DT>
+__global__ void __launch_bounds__(kTile * 8)
+transpose_center_kernel(const float *__restrict__ R, int64_t ldR, int64_t n, int T, void *__restrict__ M, int64_t ldM,
+                        const float *__restrict__ row_scale, const double *__restrict__ mu) {
+    __shared__ double tile[kTile][kTile + 1];
+    const int64_t i0 = (int64_t)blockIdx.y * kTile;      // assets
+    const int64_t t0 = (int64_t)blockIdx.x * kTile;      // periods
+    const double c = 1.0 / sqrt((double)(T - 1));
+    const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
+    for (int k = ty; k < kTile; k += 8) {
+        const int64_t i = i0 + k, t = t0 + tx;
+        tile[k][tx] = (i < n && t < T) ? ((double)R[i * ldR + t] - mu[i]) * c : 0.0;
+    }
+    __syncthreads();
+    for (int k = ty; k < kTile; k += 8) {
+        const int64_t t = t0 + k, i = i0 + tx;
+        if (t < T && i < ldM) {
+            const float inv = (DT == MV_FP8_E4M3 && i < n) ? 1.f / row_scale[i] : 1.f;
+            store_elem<DT>(M, t * ldM + i, tile[tx][k], inv);
+        }
     }
 }
 
@@ -101,11 +133,14 @@ size_t mv_center_workspace_size(int64_t n, int64_t T) {
     return n > 0 ? align_up((size_t)n * 8, 256) : 0;
 }
 
-int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int out_dtype, void *d_L, int64_t ldL,
-                     float *d_row_scale, double *d_mu, double *d_trace, void *d_ws, size_t ws_bytes,
+int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int out_dtype, int layout, void *d_L,
+                     int64_t ldL, float *d_row_scale, double *d_mu, double *d_trace, void *d_ws, size_t ws_bytes,
                      mv_stream_t stream) {
     if (d_R == nullptr || d_L == nullptr || d_mu == nullptr || d_trace == nullptr) return MV_ERR_INVALID_ARG;
-    if (n < 1 || T < 2 || ldR < T || ldL < T || n > (1LL << 31) - 1 || T > (1LL << 31) - 1) return MV_ERR_INVALID_ARG;
+    if (layout != MV_LAYOUT_NT && layout != MV_LAYOUT_TN) return MV_ERR_INVALID_ARG;
+    const bool tn = layout == MV_LAYOUT_TN;
+    if (n < 1 || T < 2 || ldR < T || ldL < (tn ? n : T) || n > (1LL << 31) - 1 || T > (1LL << 31) - 1)
+        return MV_ERR_INVALID_ARG;
     const int es = dtype_size(out_dtype);
     if (es == 0) return MV_ERR_INVALID_ARG;
     if (out_dtype == MV_FP8_E4M3 && d_row_scale == nullptr) return MV_ERR_INVALID_ARG;
@@ -114,16 +149,41 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int ou
     (void)cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
     double *rowsq = reinterpret_cast<double *>(d_ws);
+    const dim3 tgrid((unsigned)((T + kTile - 1) / kTile), (unsigned)((ldL + kTile - 1) / kTile));
+    if (tn && tgrid.y > 65535u) return MV_ERR_UNSUPPORTED;
     switch (out_dtype) {
         case MV_F32:
-            center_kernel<MV_F32><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL, nullptr, d_mu, rowsq);
+            if (tn) {
+                center_kernel<MV_F32, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
+                                                                                    nullptr, d_mu, rowsq);
+                transpose_center_kernel<MV_F32><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL, nullptr,
+                                                                            d_mu);
+            } else {
+                center_kernel<MV_F32, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL, nullptr,
+                                                                                   d_mu, rowsq);
+            }
             break;
         case MV_BF16:
-            center_kernel<MV_BF16><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL, nullptr, d_mu, rowsq);
+            if (tn) {
+                center_kernel<MV_BF16, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
+                                                                                     nullptr, d_mu, rowsq);
+                transpose_center_kernel<MV_BF16><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL, nullptr,
+                                                                             d_mu);
+            } else {
+                center_kernel<MV_BF16, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL,
+                                                                                    nullptr, d_mu, rowsq);
+            }
             break;
         default:
-            center_kernel<MV_FP8_E4M3><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL, d_row_scale,
-                                                                               d_mu, rowsq);
+            if (tn) {
+                center_kernel<MV_FP8_E4M3, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
+                                                                                         d_row_scale, d_mu, rowsq);
+                transpose_center_kernel<MV_FP8_E4M3><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL,
+                                                                                 d_row_scale, d_mu);
+            } else {
+                center_kernel<MV_FP8_E4M3, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL,
+                                                                                        d_row_scale, d_mu, rowsq);
+            }
             break;
     }
     trace_kernel<<<1, kCenterThreads, 0, s>>>(rowsq, n, d_trace);

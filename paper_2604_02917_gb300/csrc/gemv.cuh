@@ -33,11 +33,15 @@ constexpr int kGemvUnroll = 8;
 constexpr int kMaxRowsPerSplit = 2048;
 
 // One block of z = L^T y: column strip `strip`, row split `split` of `nsplits`.
+// The result goes to z (FP32, may be NULL) and, when z64 is non-NULL, also
+// to z64 in FP64 multiplied by cscale[col] (if non-NULL): the transposed
+// layout uses this kernel for g = L z with the FP8 asset scales.
 template <int DT>
 __device__ __forceinline__ void gemv_t_body(const void *__restrict__ L, int64_t ld, int n, int T,
                                             const float *__restrict__ y32, float *__restrict__ zpart, int64_t zstride,
                                             float *__restrict__ z, unsigned *__restrict__ tickets, int rows_per_split,
-                                            int strip, int split, int nsplits) {
+                                            int strip, int split, int nsplits, double *__restrict__ z64 = nullptr,
+                                            const float *__restrict__ cscale = nullptr) {
     using S = Store<DT>;
     constexpr int VEC = S::VEC;
     constexpr int ES = (int)sizeof(typename S::elem);
@@ -145,16 +149,24 @@ __device__ __forceinline__ void gemv_t_body(const void *__restrict__ L, int64_t 
                 sacc[4 * e4 + 3] += q.w;
             }
         }
+        if (z != nullptr) {
 #pragma unroll
-        for (int e = 0; e < VEC; e += 4)
-            *reinterpret_cast<float4 *>(z + col + e) = make_float4(sacc[e], sacc[e + 1], sacc[e + 2], sacc[e + 3]);
+            for (int e = 0; e < VEC; e += 4)
+                *reinterpret_cast<float4 *>(z + col + e) = make_float4(sacc[e], sacc[e + 1], sacc[e + 2], sacc[e + 3]);
+        }
+        if (z64 != nullptr) {
+#pragma unroll
+            for (int e = 0; e < VEC; ++e)
+                z64[col + e] = (double)sacc[e] * (cscale != nullptr ? (double)cscale[col + e] : 1.0);
+        }
     } else if (col < T) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             if (col + e < T) {
                 float sm = 0.f;
                 for (int sp = 0; sp < splits; ++sp) sm += __ldcg(zpart + (int64_t)sp * zstride + col + e);
-                z[col + e] = sm;
+                if (z != nullptr) z[col + e] = sm;
+                if (z64 != nullptr) z64[col + e] = (double)sm * (cscale != nullptr ? (double)cscale[col + e] : 1.0);
             }
         }
     }
@@ -165,9 +177,11 @@ template <int DT>
 __global__ void __launch_bounds__(kGemvThreads)
 gemv_t_kernel(const void *__restrict__ L, int64_t ld, int n, int T, const float *__restrict__ y32,
               float *__restrict__ zpart, int64_t zstride, float *__restrict__ z, unsigned *__restrict__ tickets,
-              int rows_per_split, const volatile int *done) {
+              int rows_per_split, const volatile int *done, double *__restrict__ z64 = nullptr,
+              const float *__restrict__ cscale = nullptr) {
     if (done != nullptr && *done) return;
-    gemv_t_body<DT>(L, ld, n, T, y32, zpart, zstride, z, tickets, rows_per_split, blockIdx.x, blockIdx.y, gridDim.y);
+    gemv_t_body<DT>(L, ld, n, T, y32, zpart, zstride, z, tickets, rows_per_split, blockIdx.x, blockIdx.y, gridDim.y,
+                    z64, cscale);
 }
 
 // One block of g = L z: row group `grp`, column split `split` of `nsplits`.

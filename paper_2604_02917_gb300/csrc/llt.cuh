@@ -81,6 +81,16 @@ __device__ __forceinline__ void st_async_v4(uint32_t raddr, float4 v, uint32_t r
                  "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar)
                  : "memory");
 }
+__device__ __forceinline__ void st_async_f32(uint32_t raddr, float v, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(raddr), "f"(v),
+                 "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async_v2(uint32_t raddr, float a, float b, uint32_t rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(raddr),
+                 "f"(a), "f"(b), "r"(rbar)
+                 : "memory");
+}
 __device__ __forceinline__ bool try_wait_cluster(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -115,6 +125,51 @@ __device__ __forceinline__ int swz(int r, int c) {
 }
 
 }  // namespace llt
+
+// Fixed-order two-level reduction of the per-cluster partials of the rows
+// [row0, row0 + a.rpc) of this rank: the last CTA of each group of kLltFan
+// clusters adds the group's partials (FP64), the last group adds the group
+// sums, applies the FP8 scale and writes g.  Every thread of the CTA calls it.
+__device__ __forceinline__ void llt_final_reduce(const LltArgs &a, int cid, int rank, int row0) {
+    __shared__ int s_flag;
+    const int tid = threadIdx.x;
+    const int ngrp = (a.G + kLltFan - 1) / kLltFan, mygrp = cid / kLltFan;
+    const int c0 = mygrp * kLltFan, c1 = min(a.G, c0 + kLltFan);
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_flag = atomicAdd(&a.tick1[rank * kLltMaxGroups + mygrp], 1u) == (unsigned)(c1 - c0 - 1);
+    __syncthreads();
+    if (s_flag) {
+        __threadfence();
+        for (int i = tid; i < a.rpc; i += kLltThreads) {
+            const int r = row0 + i;
+            if (r >= a.n) break;
+            double s = 0.0;
+#pragma unroll 8
+            for (int c = c0; c < c1; ++c) s += (double)__ldcg(a.gpart + (size_t)c * a.n + r);
+            a.gq[(size_t)mygrp * a.n + r] = s;
+        }
+        if (tid == 0) a.tick1[rank * kLltMaxGroups + mygrp] = 0u;
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_flag = atomicAdd(&a.tick2[rank], 1u) == (unsigned)(ngrp - 1);
+        __syncthreads();
+        if (s_flag) {
+            __threadfence();
+            for (int i = tid; i < a.rpc; i += kLltThreads) {
+                const int r = row0 + i;
+                if (r >= a.n) break;
+                double s = 0.0;
+#pragma unroll 8
+                for (int k = 0; k < ngrp; ++k) s += __ldcg(a.gq + (size_t)k * a.n + r);
+                if (a.row_scale != nullptr) s *= (double)a.row_scale[r];
+                a.g[r] = s;
+                if (a.g32 != nullptr) a.g32[r] = (float)s;
+            }
+            if (tid == 0) a.tick2[rank] = 0u;
+        }
+    }
+}
 
 // Shared-memory layout (bytes) for a given geometry.
 struct LltSmem {
@@ -309,47 +364,229 @@ llt_kernel(const __grid_constant__ CUtensorMap tmL, const LltArgs a) {
         }
     }
 
-    // Fixed-order two-level reduction of the per-cluster partials of this
-    // rank's rows: the last CTA of each group of kLltFan clusters adds the
-    // group's partials (FP64), the last group adds the group sums.
-    __shared__ int s_flag;
-    const int ngrp = (a.G + kLltFan - 1) / kLltFan, mygrp = cid / kLltFan;
-    const int c0 = mygrp * kLltFan, c1 = min(a.G, c0 + kLltFan);
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) s_flag = atomicAdd(&a.tick1[rank * kLltMaxGroups + mygrp], 1u) == (unsigned)(c1 - c0 - 1);
-    __syncthreads();
-    if (s_flag) {
-        __threadfence();
-        for (int i = tid; i < a.rpc; i += kLltThreads) {
-            const int r = row0 + i;
-            if (r >= a.n) break;
-            double s = 0.0;
-#pragma unroll 8
-            for (int c = c0; c < c1; ++c) s += (double)__ldcg(a.gpart + (size_t)c * a.n + r);
-            a.gq[(size_t)mygrp * a.n + r] = s;
+    llt_final_reduce(a, cid, rank, row0);
+    cluster.sync();                                     // no CTA leaves while a peer may still push to it
+}
+
+// ------------------------------------------------------------------ transposed layout
+// The same product over M = L^T stored T x n (row t = period t).  Column
+// block b of L is the row block [b W, (b+1) W) of M with W * sizeof(elem) =
+// 32 bytes (8 periods FP32, 16 BF16, 32 FP8); CTA rank r of a cluster holds
+// the asset columns [r npc, (r+1) npc) of it, so each TMA box row is a run
+// of kLltBoxCols contiguous assets (1 KB FP32) -- the access streams like a
+// plain copy.  Stage layout: [box k][row w][kLltBoxCols elements].
+//   A. warp (row w, part h) dots its row's chunks with y: z_b[w] partial,
+//      pushed to every rank (RW floats per warp);
+//   B. one thread per 16-byte column chunk: g[cols] += sum_w M[bW+w, cols] z_b[w].
+constexpr int kLltBoxCols = 256;                 // elements per TMA box row
+
+__host__ __device__ inline LltSmem lltt_smem_layout(int npc, int C) {
+    LltSmem m{};
+    m.stage = (size_t)npc * 32;                  // W rows x npc elements, W * esize = 32 bytes
+    size_t off = m.stage * kLltStages;
+    m.o_slots = off;
+    off += (size_t)kLltSlots * C * 32 * 4;       // [2][C][16 warps x RW <= 32 floats]
+    m.o_y = off;
+    off += (size_t)npc * 4;
+    m.o_zc = off;
+    off += (size_t)2 * 32 * 4;
+    off = (off + 15) / 16 * 16;
+    m.o_bars = off;
+    off += 8 * (size_t)(2 * kLltStages + kLltSlots);
+    m.total = off + 1024;
+    return m;
+}
+
+template <int DT, int C>
+__global__ void __launch_bounds__(kLltThreads, 1)
+lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
+    using S = Store<DT>;
+    constexpr int ES = (int)sizeof(typename S::elem);
+    constexpr int EPC = S::VEC;                          // elements per 16-byte chunk
+    constexpr int W = 32 / ES;                           // periods per column block
+    constexpr int RW = W > kLltConsumerWarps ? W / kLltConsumerWarps : 1;      // rows per warp (phase A)
+    constexpr int WPR = W < kLltConsumerWarps ? kLltConsumerWarps / W : 1;     // warps per row (phase A)
+    constexpr int NP = kLltConsumerWarps * RW;           // partials per rank and block
+    constexpr int CPB = kLltBoxCols * ES / 16;           // 16-byte chunks per box row
+    constexpr int BOXB = W * kLltBoxCols * ES;           // bytes of one box
+    constexpr int RPT = (ES == 4) ? 2 : 1;               // column chunks per thread in phase B
+    namespace cg = cooperative_groups;
+    if (a.done != nullptr && *(const volatile int *)a.done) return;
+
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int npc = a.rpc;                               // asset columns of this CTA
+    const LltSmem L = lltt_smem_layout(npc, C);
+    float *slots = reinterpret_cast<float *>(sm + L.o_slots);       // [2][C][NP]
+    float *s_y = reinterpret_cast<float *>(sm + L.o_y);
+    float *s_zc = reinterpret_cast<float *>(sm + L.o_zc);           // [2][W]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L.o_bars);
+    const uint32_t full0 = umma::smem_u32(bars), empty0 = umma::smem_u32(bars + kLltStages);
+    const uint32_t xchg0 = umma::smem_u32(bars + 2 * kLltStages);
+    const uint32_t slots_u32 = umma::smem_u32(slots);
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int cid = blockIdx.x / C;
+    const int col0 = rank * npc;
+    const int nj = (a.nb - cid + a.G - 1) / a.G;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nch = npc * ES / 16;                       // 16-byte chunks of one row of the stage
+    const uint32_t xbytes = (uint32_t)(C * NP * 4);
+    const uint32_t stage_tx = (uint32_t)(a.nbox * BOXB);
+
+    if (tid == 0) {
+        for (int s = 0; s < kLltStages; ++s) {
+            umma::mbar_init(full0 + 8 * s, 1);
+            umma::mbar_init(empty0 + 8 * s, kLltConsumerWarps);
         }
-        if (tid == 0) a.tick1[rank * kLltMaxGroups + mygrp] = 0u;
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) s_flag = atomicAdd(&a.tick2[rank], 1u) == (unsigned)(ngrp - 1);
-        __syncthreads();
-        if (s_flag) {
-            __threadfence();
-            for (int i = tid; i < a.rpc; i += kLltThreads) {
-                const int r = row0 + i;
-                if (r >= a.n) break;
-                double s = 0.0;
-#pragma unroll 8
-                for (int k = 0; k < ngrp; ++k) s += __ldcg(a.gq + (size_t)k * a.n + r);
-                if (a.row_scale != nullptr) s *= (double)a.row_scale[r];
-                a.g[r] = s;
-                if (a.g32 != nullptr) a.g32[r] = (float)s;
+        for (int q = 0; q < kLltSlots; ++q) umma::mbar_init(xchg0 + 8 * q, 1);
+        umma::mbar_fence_init();
+        for (int q = 0; q < kLltSlots && q < nj; ++q) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
+    }
+    for (int i = tid; i < npc; i += kLltThreads) s_y[i] = col0 + i < a.n ? a.y32[col0 + i] : 0.f;
+    cluster.sync();
+
+    float gs[RPT][EPC], gc[RPT][EPC];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k)
+#pragma unroll
+        for (int e = 0; e < EPC; ++e) gs[k][e] = gc[k][e] = 0.f;
+
+    if (warp == kLltConsumerWarps) {
+        if (lane == 0) {
+            umma::prefetch_tensormap(&tmM);
+            bool bail = false;
+            for (int j = 0; j < nj; ++j) {
+                const int s = j % kLltStages;
+                if (j >= kLltStages && !umma::mbar_wait(empty0 + 8 * s, (uint32_t)(j / kLltStages - 1) & 1u,
+                                                        bail ? kLltBailNs : kLltWaitNs)) {
+                    atomicExch(a.err, 3);
+                    bail = true;
+                }
+                const int b = cid + j * a.G;
+                const uint32_t dst = umma::smem_u32(sm + (size_t)s * L.stage);
+                umma::mbar_arrive_expect_tx(full0 + 8 * s, stage_tx);
+                for (int k = 0; k < a.nbox; ++k)
+                    umma::tma_load_2d(dst + (uint32_t)(k * BOXB), &tmM, col0 + k * kLltBoxCols, b * W, full0 + 8 * s);
             }
-            if (tid == 0) a.tick2[rank] = 0u;
+            for (int j = nj - kLltStages < 0 ? 0 : nj - kLltStages; j < nj; ++j)
+                if (!umma::mbar_wait(full0 + 8 * (j % kLltStages), (uint32_t)(j / kLltStages) & 1u, kLltWaitNs))
+                    atomicExch(a.err, 4);
+        }
+        __syncwarp();
+    } else {
+        bool bail = false;
+        for (int j = 0; j < nj; ++j) {
+            const int s = j % kLltStages, q = j % kLltSlots;
+            if (!umma::mbar_wait(full0 + 8 * s, (uint32_t)(j / kLltStages) & 1u, bail ? kLltBailNs : kLltWaitNs)) {
+                atomicExch(a.err, 1);
+                bail = true;
+            }
+            const uint8_t *sb = sm + (size_t)s * L.stage;
+            // Phase A.
+            {
+                float acc[RW];
+#pragma unroll
+                for (int r = 0; r < RW; ++r) acc[r] = 0.f;
+                const int w0 = (WPR > 1) ? (warp % W) : warp * RW, h = (WPR > 1) ? warp / W : 0;
+#pragma unroll 2
+                for (int c = h * 32 + lane; c < nch; c += 32 * WPR) {
+                    const int off = (c / CPB) * BOXB + (c % CPB) * 16;
+                    float yv[EPC];
+#pragma unroll
+                    for (int e = 0; e < EPC; e += 4) {
+                        const float4 q4 = *reinterpret_cast<const float4 *>(s_y + c * EPC + e);
+                        yv[e] = q4.x;
+                        yv[e + 1] = q4.y;
+                        yv[e + 2] = q4.z;
+                        yv[e + 3] = q4.w;
+                    }
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) {
+                        const uint4 u =
+                            *reinterpret_cast<const uint4 *>(sb + off + (w0 + r) * (kLltBoxCols * ES));
+                        float f[EPC];
+                        S::unpack(u, f);
+#pragma unroll
+                        for (int e = 0; e < EPC; ++e) acc[r] = fmaf(f[e], yv[e], acc[r]);
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int r = 0; r < RW; ++r) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+                if (lane < C) {
+                    const uint32_t local = slots_u32 + (uint32_t)(((q * C + rank) * NP + warp * RW) * 4);
+                    const uint32_t rdst = llt::mapa(local, (uint32_t)lane), rbar = llt::mapa(xchg0 + 8 * q, (uint32_t)lane);
+                    if constexpr (RW == 1)
+                        llt::st_async_f32(rdst, acc[0], rbar);
+                    else
+                        llt::st_async_v2(rdst, acc[0], acc[RW - 1], rbar);
+                }
+            }
+            // Receive: z_b[w] = sum over ranks and the row's warps, fixed order.
+            float *zc = s_zc + (j & 1) * W;
+            if (tid < W) {
+                if (!llt::wait_cluster(xchg0 + 8 * q, (uint32_t)(j / kLltSlots) & 1u, bail ? kLltBailNs : kLltWaitNs)) {
+                    atomicExch(a.err, 2);
+                    bail = true;
+                }
+                const float *sl = slots + (size_t)q * C * NP;
+                float z = 0.f;
+#pragma unroll
+                for (int r = 0; r < C; ++r)
+#pragma unroll
+                    for (int hh = 0; hh < WPR; ++hh) z += sl[r * NP + hh * W + tid];
+                zc[tid] = z;
+                if (tid == 0 && j + kLltSlots < nj) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
+            }
+            llt::bar_consumers();
+            // Phase B: one thread per 16-byte column chunk, all W rows of the block.
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int c = tid + k * kLltConsumers;
+                if (c < nch) {
+                    const int off = (c / CPB) * BOXB + (c % CPB) * 16;
+                    float d[EPC];
+#pragma unroll
+                    for (int e = 0; e < EPC; ++e) d[e] = 0.f;
+#pragma unroll
+                    for (int w = 0; w < W; ++w) {
+                        const uint4 u = *reinterpret_cast<const uint4 *>(sb + off + w * (kLltBoxCols * ES));
+                        float f[EPC];
+                        S::unpack(u, f);
+                        const float zw = zc[w];
+#pragma unroll
+                        for (int e = 0; e < EPC; ++e) d[e] = fmaf(f[e], zw, d[e]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < EPC; ++e) {             // compensated running sums over blocks
+                        const float yk = d[e] - gc[k][e];
+                        const float tk = gs[k][e] + yk;
+                        gc[k][e] = (tk - gs[k][e]) - yk;
+                        gs[k][e] = tk;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) llt::mbar_arrive(empty0 + 8 * s);
+        }
+        // Per-cluster partial of g for this CTA's asset columns.
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+            const int c = tid + k * kLltConsumers;
+            if (c < nch) {
+#pragma unroll
+                for (int e = 0; e < EPC; ++e) {
+                    const int col = col0 + c * EPC + e;
+                    if (col < a.n) a.gpart[(size_t)cid * a.n + col] = gs[k][e] - gc[k][e];
+                }
+            }
         }
     }
-    cluster.sync();                                     // no CTA leaves while a peer may still push to it
+    llt_final_reduce(a, cid, rank, col0);
+    cluster.sync();
 }
 
 // ------------------------------------------------------------------ host
@@ -370,6 +607,25 @@ inline bool llt_shape(int64_t n, int64_t T, int esize, int C, int RB, LltPlan *p
     p->rpc = rpc;
     p->box_rows = box_rows;
     p->nbox = nbox;
+    p->nb = (int)((T + W - 1) / W);
+    p->smem = smem;
+    return true;
+}
+
+// Geometry of the transposed-layout pass for cluster size C: npc asset
+// columns per CTA (a multiple of kLltBoxCols), boxes per stage, blocks of
+// W = 32 / esize periods.
+inline bool lltt_shape(int64_t n, int64_t T, int esize, int C, LltPlan *p) {
+    const int64_t npc = ((n + C - 1) / C + kLltBoxCols - 1) / kLltBoxCols * kLltBoxCols;
+    if (npc * esize / 16 > (esize == 4 ? 2 : 1) * kLltConsumers) return false;
+    const size_t smem = lltt_smem_layout((int)npc, C).total;
+    if (smem > kLltSmemCap) return false;
+    const int W = 32 / esize;
+    p->C = C;
+    p->RB = 0;                                  // marks the transposed layout
+    p->rpc = (int)npc;
+    p->box_rows = W;
+    p->nbox = (int)(npc / kLltBoxCols);
     p->nb = (int)((T + W - 1) / W);
     p->smem = smem;
     return true;
@@ -406,6 +662,30 @@ inline int make_map_llt(CUtensorMap *map, int dt, const void *base, int64_t n, i
     if (r != CUDA_SUCCESS) {
         char msg[128];
         snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled (fused pass) failed (%d)", (int)r);
+        return record_message(MV_ERR_CUDA, msg);
+    }
+    return MV_OK;
+}
+
+// 2-D tensor map over M = L^T (T x n, leading dim ld) for the transposed pass:
+// box = kLltBoxCols assets x W periods, no swizzle.
+inline int make_map_lltt(CUtensorMap *map, int dt, const void *base, int64_t n, int64_t T, int64_t ld, int W) {
+    auto enc = tensor_map_encoder();
+    if (enc == nullptr) return record_message(MV_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int es = dtype_size(dt);
+    const CUtensorMapDataType ty = dt == MV_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dt == MV_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)T};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+    cuuint32_t box[2] = {(cuuint32_t)kLltBoxCols, (cuuint32_t)W};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, ty, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char msg[128];
+        snprintf(msg, sizeof(msg), "cuTensorMapEncodeTiled (transposed pass) failed (%d)", (int)r);
         return record_message(MV_ERR_CUDA, msg);
     }
     return MV_OK;

@@ -17,7 +17,8 @@ constexpr int64_t kLltMinN = 1024, kLltMinT = 4096;
 
 struct LltPlan {
     bool ok;
-    int C, RB;                 // cluster size, bytes of one row per column block
+    bool tn;                   // transposed layout (L^T stored T x n)
+    int C, RB;                 // cluster size, bytes of one row per column block (NT)
     int rpc, box_rows, nbox;   // rows per CTA, TMA box rows, boxes per stage
     int nb, G;                 // column blocks, clusters launched
     size_t smem;               // dynamic shared memory per CTA
@@ -38,10 +39,11 @@ size_t llt_ticket_bytes();     // bytes of sc.tickets to zero before the first l
 // not apply).  with_device = false skips the device query and only decides
 // whether a shape exists (workspace sizing must not depend on the device).
 // MV_LLT_SHAPE="C,RB" in the environment forces one shape (tuning).
-LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device);
+LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device, bool tn = false);
 
 // Enqueues g = L L^T y (row-scaled; FP8 y32 pre-multiplied by the scale) on
 // stream s; capturable.  done (nullable): the launch returns at once if *done.
+// For a transposed plan, L points at L^T (T x n, leading dim ld).
 int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
                const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s);
 
@@ -53,5 +55,11 @@ struct LltArgs;
 cudaError_t llt_launch_f32(int C, int RB, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
 cudaError_t llt_launch_bf16(int C, int RB, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
 cudaError_t llt_launch_fp8(int C, int RB, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
+int llt_max_clusters_tn_f32(int C, size_t smem);
+int llt_max_clusters_tn_bf16(int C, size_t smem);
+int llt_max_clusters_tn_fp8(int C, size_t smem);
+cudaError_t llt_launch_tn_f32(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
+cudaError_t llt_launch_tn_bf16(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
+cudaError_t llt_launch_tn_fp8(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
 
 }  // namespace mv

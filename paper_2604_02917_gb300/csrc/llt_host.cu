@@ -31,7 +31,7 @@ LltScratch llt_scratch(void *base, int64_t n) {
     return sc;
 }
 
-static int max_clusters(int dt, int C, int RB, size_t smem) {
+static int max_clusters(int dt, int C, int RB, size_t smem) {   // RB = 0: transposed-layout kernel
     static std::mutex mu;
     static std::unordered_map<uint64_t, int> cache;
     int dev = 0;
@@ -44,7 +44,13 @@ static int max_clusters(int dt, int C, int RB, size_t smem) {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
-    int v = dt == MV_F32    ? llt_max_clusters_f32(C, RB, smem)
+    int v;
+    if (RB == 0)
+        v = dt == MV_F32 ? llt_max_clusters_tn_f32(C, smem)
+            : dt == MV_BF16 ? llt_max_clusters_tn_bf16(C, smem)
+                            : llt_max_clusters_tn_fp8(C, smem);
+    else
+        v = dt == MV_F32 ? llt_max_clusters_f32(C, RB, smem)
             : dt == MV_BF16 ? llt_max_clusters_bf16(C, RB, smem)
                             : llt_max_clusters_fp8(C, RB, smem);
     v = std::min(v, kLltMaxClusters);
@@ -52,11 +58,36 @@ static int max_clusters(int dt, int C, int RB, size_t smem) {
     return v;
 }
 
-LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device) {
+// Transposed layout: the smallest cluster (1, 2, 4 or 8 CTAs) whose asset
+// share fits two stages.
+static LltPlan plan_tn(int dt, int64_t n, int64_t T, bool with_device) {
+    LltPlan p{};
+    p.ok = false;
+    const int es = dtype_size(dt);
+    for (int C = 1; C <= kLltMaxCluster; C *= 2) {
+        LltPlan q{};
+        if (!lltt_shape(n, T, es, C, &q)) continue;
+        q.tn = true;
+        if (!with_device) {
+            q.ok = true;
+            q.G = 1;
+            return q;
+        }
+        const int mc = max_clusters(dt, C, 0, q.smem);
+        if (mc < 1) continue;
+        q.G = std::max(1, std::min(mc, q.nb));
+        q.ok = true;
+        return q;
+    }
+    return p;
+}
+
+LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device, bool tn) {
     LltPlan p{};
     p.ok = false;
     const int es = dtype_size(dt);
     if (es == 0 || n < kLltMinN || T < kLltMinT) return p;
+    if (tn) return plan_tn(dt, n, T, with_device);
     int fC = 0, fRB = 0;
     if (const char *env = getenv("MV_LLT_SHAPE")) {
         if (sscanf(env, "%d,%d", &fC, &fRB) != 2) fC = fRB = 0;
@@ -87,7 +118,10 @@ int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, i
                const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s) {
     if (!lp.ok) return MV_ERR_UNSUPPORTED;
     CUtensorMap map;
-    MV_TRY(make_map_llt(&map, dt, L, n, T, ld, lp.box_rows, lp.RB));
+    if (lp.tn)
+        MV_TRY(make_map_lltt(&map, dt, L, n, T, ld, lp.box_rows));
+    else
+        MV_TRY(make_map_llt(&map, dt, L, n, T, ld, lp.box_rows, lp.RB));
     LltArgs a;
     a.y32 = y32;
     a.row_scale = row_scale;
@@ -106,9 +140,15 @@ int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, i
     a.nbox = lp.nbox;
     a.nb = lp.nb;
     a.G = lp.G;
-    const cudaError_t e = dt == MV_F32    ? llt_launch_f32(lp.C, lp.RB, lp.G, lp.smem, &map, a, s)
-                          : dt == MV_BF16 ? llt_launch_bf16(lp.C, lp.RB, lp.G, lp.smem, &map, a, s)
-                                          : llt_launch_fp8(lp.C, lp.RB, lp.G, lp.smem, &map, a, s);
+    cudaError_t e;
+    if (lp.tn)
+        e = dt == MV_F32    ? llt_launch_tn_f32(lp.C, lp.G, lp.smem, &map, a, s)
+            : dt == MV_BF16 ? llt_launch_tn_bf16(lp.C, lp.G, lp.smem, &map, a, s)
+                            : llt_launch_tn_fp8(lp.C, lp.G, lp.smem, &map, a, s);
+    else
+        e = dt == MV_F32    ? llt_launch_f32(lp.C, lp.RB, lp.G, lp.smem, &map, a, s)
+            : dt == MV_BF16 ? llt_launch_bf16(lp.C, lp.RB, lp.G, lp.smem, &map, a, s)
+                            : llt_launch_fp8(lp.C, lp.RB, lp.G, lp.smem, &map, a, s);
     if (e != cudaSuccess) return record_cuda_error(e, "fused L L^T pass launch", __FILE__, __LINE__);
     return MV_OK;
 }

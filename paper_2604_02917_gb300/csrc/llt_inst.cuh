@@ -62,6 +62,43 @@ cudaError_t launch(int G, size_t smem, const void *map, const LltArgs &a, cudaSt
     return cudaLaunchKernelEx(&cfg, llt_kernel<MV_LLT_DT, C, RB>, *reinterpret_cast<const CUtensorMap *>(map), a);
 }
 
+template <int C>
+int attrs_tn() {
+    static int st = -1;
+    if (st < 0) {
+        const int smem = (int)(kLltSmemCap + 256);
+        st = (cudaFuncSetAttribute(lltt_kernel<MV_LLT_DT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+                  cudaSuccess &&
+              cudaFuncSetAttribute(lltt_kernel<MV_LLT_DT, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+                  cudaSuccess)
+                 ? MV_OK
+                 : MV_ERR_CUDA;
+        if (st != MV_OK) (void)cudaGetLastError();
+    }
+    return st;
+}
+
+template <int C>
+int max_clusters_tn(size_t smem) {
+    if (attrs_tn<C>() != MV_OK) return 0;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = config(C, kLltMaxClusters, smem, nullptr, attr);
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, lltt_kernel<MV_LLT_DT, C>, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return num;
+}
+
+template <int C>
+cudaError_t launch_tn(int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s) {
+    if (attrs_tn<C>() != MV_OK) return cudaErrorInvalidValue;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = config(C, G, smem, s, attr);
+    return cudaLaunchKernelEx(&cfg, lltt_kernel<MV_LLT_DT, C>, *reinterpret_cast<const CUtensorMap *>(map), a);
+}
+
 }  // namespace
 
 // The instantiated shapes (kLltShapes).
@@ -81,6 +118,23 @@ int MV_LLT_CAT(llt_max_clusters_, MV_LLT_SUFFIX)(int C, int RB, size_t smem) {
 cudaError_t MV_LLT_CAT(llt_launch_, MV_LLT_SUFFIX)(int C, int RB, int G, size_t smem, const void *map,
                                                     const LltArgs &a, cudaStream_t s) {
     MV_LLT_SWITCH(C, RB, launch, G, smem, map, a, s)
+    return cudaErrorInvalidValue;
+}
+
+#define MV_LLT_SWITCH_TN(C, F, ...)                   \
+    if (C == 1) return F<1>(__VA_ARGS__);             \
+    if (C == 2) return F<2>(__VA_ARGS__);             \
+    if (C == 4) return F<4>(__VA_ARGS__);             \
+    if (C == 8) return F<8>(__VA_ARGS__);
+
+int MV_LLT_CAT(llt_max_clusters_tn_, MV_LLT_SUFFIX)(int C, size_t smem) {
+    MV_LLT_SWITCH_TN(C, max_clusters_tn, smem)
+    return 0;
+}
+
+cudaError_t MV_LLT_CAT(llt_launch_tn_, MV_LLT_SUFFIX)(int C, int G, size_t smem, const void *map, const LltArgs &a,
+                                                       cudaStream_t s) {
+    MV_LLT_SWITCH_TN(C, launch_tn, G, smem, map, a, s)
     return cudaErrorInvalidValue;
 }
 

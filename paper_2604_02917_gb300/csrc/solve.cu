@@ -40,6 +40,8 @@ struct Plan {
     int dt, vec, esize;
     int n, T;
     int64_t ld;
+    bool tn;                               // L stored transposed (T x n)
+    int gr, gc;                            // rows and columns of the stored matrix
     int cl;                                // cluster size of the step kernel
     int t_blocks, t_splits, t_rows;        // gemv_t grid
     int n_groups, n_splits, n_cols;        // gemv_n grid
@@ -47,7 +49,7 @@ struct Plan {
     LltPlan lp;
     // workspace offsets (bytes)
     size_t o_state, o_x, o_y, o_gx, o_gy, o_g32, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
-    size_t o_llt, o_err;
+    size_t o_llt, o_err, o_zd;
     int64_t zstride;                       // row pitch (floats) of the gemv_t partials
     size_t total;
 };
@@ -68,7 +70,11 @@ static constexpr int kRW = 4;   // rows per warp in gemv_n
 
 // The fused pass pays a cluster exchange per 128-byte column block, so it is
 // used where a block holds many rows and there are many blocks.
-static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows = 0, bool fused = false) {
+// gemv_t (column sums) and gemv_n (row dots) run over the stored matrix:
+// L (n x T) for MV_LAYOUT_NT, where z = L^T y is gemv_t and g = L z is
+// gemv_n; L^T (T x n) for MV_LAYOUT_TN, where the two swap roles.
+static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows = 0, bool fused = false,
+                      bool tn = false) {
     Plan p{};
     p.dt = dt;
     p.esize = dtype_size(dt);
@@ -76,6 +82,10 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows
     p.n = (int)n;
     p.T = (int)T;
     p.ld = ld;
+    p.tn = tn;
+    const int64_t gr = tn ? T : n, gc = tn ? n : T;
+    p.gr = (int)gr;
+    p.gc = (int)gc;
     p.cl = proj_cluster_size(n);
     // Tuning override of the step kernel's cluster size (1, 2, 4, 8 or 16).
     if (const char *env = getenv("MV_STEP_CLUSTER")) {
@@ -86,21 +96,21 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows
     // gemv_t: strips of 256*VEC columns; rows split so the grid covers
     // several waves of the machine (4 resident blocks per SM assumed).
     const int strip = kGemvThreads * p.vec;
-    p.t_blocks = (int)((T + strip - 1) / strip);
+    p.t_blocks = (int)((gc + strip - 1) / strip);
     const int slots = sms * 4;
     int splits = (slots * 3 + p.t_blocks - 1) / p.t_blocks;
-    splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, (n + 63) / 64));
-    if (grouped_rows > 0) splits = (int)((n + grouped_rows - 1) / grouped_rows);   // many problems share the GPU
-    int rows = (int)((n + splits - 1) / splits);
+    splits = (int)std::max<int64_t>(1, std::min<int64_t>(splits, (gr + 63) / 64));
+    if (grouped_rows > 0) splits = (int)((gr + grouped_rows - 1) / grouped_rows);   // many problems share the GPU
+    int rows = (int)((gr + splits - 1) / splits);
     if (rows > kMaxRowsPerSplit) rows = kMaxRowsPerSplit;
     p.t_rows = rows;
-    p.t_splits = (int)((n + rows - 1) / rows);
-    // gemv_n: 32 rows per block, column splits of 16 KB of L per row.
+    p.t_splits = (int)((gr + rows - 1) / rows);
+    // gemv_n: 32 rows per block, column splits of 16 KB of the matrix per row.
     const int rows_per_block = (kGemvThreads / kWarp) * kRW;
-    p.n_groups = (int)((n + rows_per_block - 1) / rows_per_block);
-    p.n_cols = 4096 * 4 / p.esize;                       // 16 KB of L per row per split
-    if (p.n_cols > T) p.n_cols = (int)((T + 32 * p.vec - 1) / (32 * p.vec) * (32 * p.vec));
-    p.n_splits = (int)((T + p.n_cols - 1) / p.n_cols);
+    p.n_groups = (int)((gr + rows_per_block - 1) / rows_per_block);
+    p.n_cols = 4096 * 4 / p.esize;                       // 16 KB per row per split
+    if (p.n_cols > gc) p.n_cols = (int)((gc + 32 * p.vec - 1) / (32 * p.vec) * (32 * p.vec));
+    p.n_splits = (int)((gc + p.n_cols - 1) / p.n_cols);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -115,18 +125,19 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows
     p.o_g32 = take(4 * (size_t)n);
     p.o_y32 = take(4 * (size_t)n);
     p.o_z = take(4 * (size_t)T + 64);
-    p.zstride = (T + 15) / 16 * 16;
+    p.zstride = (gc + 15) / 16 * 16;
     p.o_zpart = take(4 * (size_t)p.zstride * p.t_splits);
-    p.o_gpart = take(4 * (size_t)n * p.n_splits);
+    p.o_gpart = take(4 * (size_t)gr * p.n_splits);
+    p.o_zd = tn ? take(8 * (size_t)T) : 0;
     p.o_tick_t = take(4 * (size_t)p.t_blocks);
     p.o_tick_n = take(4 * (size_t)p.n_groups);
     p.use_llt = false;
     p.lp = LltPlan{};
-    if (fused && llt_plan(dt, n, T, false).ok) {
+    if (fused && llt_plan(dt, n, T, false, tn).ok) {
         // The scratch is sized without the device query, so the workspace
         // size does not depend on the device.
         p.o_llt = take(llt_scratch_bytes(n));
-        p.lp = llt_plan(dt, n, T, true);
+        p.lp = llt_plan(dt, n, T, true, tn);
         p.use_llt = p.lp.ok;
     }
     p.o_err = take(16);
@@ -491,13 +502,24 @@ static int validate_problem(const mv_problem *P) {
     if (P == nullptr || P->L == nullptr || P->mu == nullptr) return MV_ERR_INVALID_ARG;
     if (P->dtype != MV_F32 && P->dtype != MV_BF16 && P->dtype != MV_FP8_E4M3) return MV_ERR_INVALID_ARG;
     if (P->mode != MV_RETURN_GE && P->mode != MV_RETURN_EQ) return MV_ERR_INVALID_ARG;
-    if (P->n < 1 || P->T < 1 || P->ld < P->T) return MV_ERR_INVALID_ARG;
+    if (P->layout != MV_LAYOUT_NT && P->layout != MV_LAYOUT_TN) return MV_ERR_INVALID_ARG;
+    if (P->n < 1 || P->T < 1 || P->ld < (P->layout == MV_LAYOUT_TN ? P->n : P->T)) return MV_ERR_INVALID_ARG;
     if (P->n > kProjMaxN || P->T > (1LL << 31) - 1) return MV_ERR_UNSUPPORTED;
     const int es = dtype_size(P->dtype);
     if (((uintptr_t)P->L) % 16 != 0 || (P->ld * es) % 16 != 0) return MV_ERR_INVALID_ARG;
     if (P->dtype == MV_FP8_E4M3 && P->row_scale == nullptr) return MV_ERR_INVALID_ARG;
     if (!(P->gamma >= 0.0) || !(P->R_target == P->R_target)) return MV_ERR_INVALID_ARG;
     return MV_OK;
+}
+
+static bool is_tn(const mv_problem *P) { return P->layout == MV_LAYOUT_TN; }
+
+// The calls that read L only through the NT-layout kernels.
+static int require_nt(const mv_problem *P, const char *what) {
+    if (!is_tn(P)) return MV_OK;
+    char msg[128];
+    snprintf(msg, sizeof(msg), "%s: the factor must be stored n x T (MV_LAYOUT_NT)", what);
+    return record_message(MV_ERR_UNSUPPORTED, msg);
 }
 
 static int check_ws(void *ws, size_t ws_bytes, size_t need) {
@@ -507,20 +529,59 @@ static int check_ws(void *ws, size_t ws_bytes, size_t need) {
 }
 
 template <int DT>
-static void launch_gemv_t(const Plan &p, const void *L, const float *y32, float *zpart, float *z,
-                          unsigned *tick, const int *done, cudaStream_t s) {
+static void launch_gemv_t(const Plan &p, const void *L, const float *w32, float *out32, double *out64,
+                          const float *cscale, void *ws, const int *done, cudaStream_t s) {
     dim3 grid(p.t_blocks, p.t_splits);
-    gemv_t_kernel<DT><<<grid, kGemvThreads, 0, s>>>(L, p.ld, p.n, p.T, y32, zpart, p.zstride, z, tick, p.t_rows,
-                                                     done);
+    gemv_t_kernel<DT><<<grid, kGemvThreads, 0, s>>>(L, p.ld, p.gr, p.gc, w32, at<float>(ws, p.o_zpart), p.zstride,
+                                                     out32, at<unsigned>(ws, p.o_tick_t), p.t_rows, done, out64, cscale);
 }
 
 template <int DT>
-static void launch_gemv_n(const Plan &p, const void *L, const float *z, const float *row_scale, float *gpart,
-                          double *g, unsigned *tick, const int *done, cudaStream_t s, float *g32 = nullptr) {
+static void launch_gemv_n(const Plan &p, const void *L, const float *w32, const float *rscale, double *out64,
+                          float *out32, void *ws, const int *done, cudaStream_t s) {
     dim3 grid(p.n_groups, p.n_splits);
     const size_t smem = (size_t)p.n_cols * 4;
-    gemv_n_kernel<DT, kRW><<<grid, kGemvThreads, smem, s>>>(L, p.ld, p.n, p.T, z, row_scale, gpart, g, g32, tick,
-                                                           p.n_cols, done);
+    gemv_n_kernel<DT, kRW><<<grid, kGemvThreads, smem, s>>>(L, p.ld, p.gr, p.gc, w32, rscale, at<float>(ws, p.o_gpart),
+                                                           out64, out32, at<unsigned>(ws, p.o_tick_n), p.n_cols, done);
+}
+
+// z = L^T y32 into the FP32 T-vector at o_z (y32 pre-multiplied by the FP8 scales).
+template <int DT>
+static void launch_z_t(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done,
+                       cudaStream_t s) {
+    float *z = at<float>(ws, p.o_z);
+    if (p.tn)
+        launch_gemv_n<DT>(p, P->L, y32, nullptr, at<double>(ws, p.o_zd), z, ws, done, s);
+    else
+        launch_gemv_t<DT>(p, P->L, y32, z, nullptr, nullptr, ws, done, s);
+}
+
+// g = L z (FP64, FP8 scales applied) and optionally its FP32 copy g32.
+template <int DT>
+static void launch_g_t(const Plan &p, const mv_problem *P, const float *z, void *ws, const int *done, double *g,
+                       float *g32, cudaStream_t s) {
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    if (p.tn)
+        launch_gemv_t<DT>(p, P->L, z, g32, g, rs, ws, done, s);
+    else
+        launch_gemv_n<DT>(p, P->L, z, rs, g, g32, ws, done, s);
+}
+
+static void launch_z(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, cudaStream_t s) {
+    switch (p.dt) {
+        case MV_F32: launch_z_t<MV_F32>(p, P, y32, ws, done, s); break;
+        case MV_BF16: launch_z_t<MV_BF16>(p, P, y32, ws, done, s); break;
+        default: launch_z_t<MV_FP8_E4M3>(p, P, y32, ws, done, s); break;
+    }
+}
+
+static void launch_g(const Plan &p, const mv_problem *P, const float *z, void *ws, const int *done, double *g,
+                     float *g32, cudaStream_t s) {
+    switch (p.dt) {
+        case MV_F32: launch_g_t<MV_F32>(p, P, z, ws, done, g, g32, s); break;
+        case MV_BF16: launch_g_t<MV_BF16>(p, P, z, ws, done, g, g32, s); break;
+        default: launch_g_t<MV_FP8_E4M3>(p, P, z, ws, done, g, g32, s); break;
+    }
 }
 
 // g = L L^T y (row-scaled) in one pass over L; capturable (no synchronisation).
@@ -566,32 +627,12 @@ static int set_kernel_attrs() {
 
 static void gemv_pair(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done,
                       double *g_out, cudaStream_t s, float *g32 = nullptr) {
-    float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z), *gpart = at<float>(ws, p.o_gpart);
-    unsigned *tt = at<unsigned>(ws, p.o_tick_t), *tn = at<unsigned>(ws, p.o_tick_n);
-    switch (p.dt) {
-        case MV_F32:
-            launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, done, s);
-            launch_gemv_n<MV_F32>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s, g32);
-            break;
-        case MV_BF16:
-            launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, done, s);
-            launch_gemv_n<MV_BF16>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s, g32);
-            break;
-        default:
-            launch_gemv_t<MV_FP8_E4M3>(p, P->L, y32, zpart, z, tt, done, s);
-            launch_gemv_n<MV_FP8_E4M3>(p, P->L, z, P->row_scale, gpart, g_out, tn, done, s, g32);
-            break;
-    }
+    launch_z(p, P, y32, ws, done, s);
+    launch_g(p, P, at<float>(ws, p.o_z), ws, done, g_out, g32, s);
 }
 
 static void gemv_t_only(const Plan &p, const mv_problem *P, const float *y32, void *ws, cudaStream_t s) {
-    float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z);
-    unsigned *tt = at<unsigned>(ws, p.o_tick_t);
-    switch (p.dt) {
-        case MV_F32: launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, nullptr, s); break;
-        case MV_BF16: launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, nullptr, s); break;
-        default: launch_gemv_t<MV_FP8_E4M3>(p, P->L, y32, zpart, z, tt, nullptr, s); break;
-    }
+    launch_z(p, P, y32, ws, nullptr, s);
 }
 
 template <typename Kern, typename... Args>
@@ -661,8 +702,6 @@ static void launch_init_x(const Plan &p, const mv_problem *P, const double *x_in
 static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
                             cudaStream_t s, const cudaEvent_t *ev) {
     SolveState *st = at<SolveState>(ws, p.o_state);
-    float *zpart = at<float>(ws, p.o_zpart), *z = at<float>(ws, p.o_z), *gpart = at<float>(ws, p.o_gpart);
-    unsigned *tt = at<unsigned>(ws, p.o_tick_t), *tn = at<unsigned>(ws, p.o_tick_n);
     const float *y32 = at<float>(ws, p.o_y32);
     double *gy = at<double>(ws, p.o_gy);
     const int *done = &st->done;
@@ -675,17 +714,9 @@ static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_o
         if (ev) cudaEventRecord(ev[3], s);
         return MV_OK;
     }
-    switch (p.dt) {
-        case MV_F32: launch_gemv_t<MV_F32>(p, P->L, y32, zpart, z, tt, done, s); break;
-        case MV_BF16: launch_gemv_t<MV_BF16>(p, P->L, y32, zpart, z, tt, done, s); break;
-        default: launch_gemv_t<MV_FP8_E4M3>(p, P->L, y32, zpart, z, tt, done, s); break;
-    }
+    launch_z(p, P, y32, ws, done, s);
     if (ev) cudaEventRecord(ev[1], s);
-    switch (p.dt) {
-        case MV_F32: launch_gemv_n<MV_F32>(p, P->L, z, P->row_scale, gpart, gy, tn, done, s); break;
-        case MV_BF16: launch_gemv_n<MV_BF16>(p, P->L, z, P->row_scale, gpart, gy, tn, done, s); break;
-        default: launch_gemv_n<MV_FP8_E4M3>(p, P->L, z, P->row_scale, gpart, gy, tn, done, s); break;
-    }
+    launch_g(p, P, at<float>(ws, p.o_z), ws, done, gy, nullptr, s);
     if (ev) cudaEventRecord(ev[2], s);
     launch_step(p, P, O, ws, s);
     if (ev) cudaEventRecord(ev[3], s);
@@ -796,14 +827,14 @@ void mv_solve_opts_default(mv_solve_opts *o) {
 
 size_t mv_npga_workspace_size(const mv_problem *P) {
     if (validate_problem(P) != MV_OK) return 0;
-    return make_plan(P->dtype, P->n, P->T, P->ld, 0, true).total;
+    return make_plan(P->dtype, P->n, P->T, P->ld, 0, true, is_tn(P)).total;
 }
 
 int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g, void *d_ws, size_t ws_bytes,
                 mv_stream_t stream) {
     MV_TRY(validate_problem(P));
     if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, d_z == nullptr);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, d_z == nullptr, is_tn(P));
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();
@@ -834,7 +865,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, O.two_pass == 0);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, O.two_pass == 0, is_tn(P));
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();   // start from a clean error state
@@ -1272,7 +1303,7 @@ static void frontier_gemm_pair(const CUtensorMap *maps, const Plan &p, const FPl
 extern "C" {
 
 size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets) {
-    if (validate_problem(P) != MV_OK || P->dtype != MV_BF16 || n_targets < 1 || n_targets > 128) return 0;
+    if (validate_problem(P) != MV_OK || is_tn(P) || P->dtype != MV_BF16 || n_targets < 1 || n_targets > 128) return 0;
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
     return make_fplan(p, n_targets).total;
 }
@@ -1281,6 +1312,7 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
                            const mv_solve_opts *O_in, double *d_X, mv_solve_info *h_infos, void *d_ws, size_t ws_bytes,
                            mv_stream_t stream) {
     MV_TRY(validate_problem(P));
+    MV_TRY(require_nt(P, "frontier solve"));
     if (P->dtype != MV_BF16) return record_message(MV_ERR_UNSUPPORTED, "frontier solve: L must be BF16");
     if (d_R_targets == nullptr || d_X == nullptr || h_infos == nullptr || n_targets < 1 || n_targets > 128)
         return MV_ERR_INVALID_ARG;
@@ -1611,7 +1643,7 @@ static BPlan make_bplan(const Plan &p, int K, int C) {
 extern "C" {
 
 size_t mv_backward_workspace_size(const mv_problem *P, const mv_solve_opts *O_in) {
-    if (validate_problem(P) != MV_OK || P->dtype != MV_F32) return 0;
+    if (validate_problem(P) != MV_OK || is_tn(P) || P->dtype != MV_F32) return 0;
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 1 || O.checkpoint_every < 1) return 0;
@@ -1623,6 +1655,7 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
                      double *d_dmu, float *d_dL, int64_t ldD, mv_solve_info *h_info, void *d_ws, size_t ws_bytes,
                      mv_stream_t stream) {
     MV_TRY(validate_problem(P));
+    MV_TRY(require_nt(P, "mv_npga_backward"));
     if (P->dtype != MV_F32) return record_message(MV_ERR_UNSUPPORTED, "mv_npga_backward: FP32 factor only");
     if (!d_dloss_dx || !d_dmu || !d_dL || !h_info || ldD < P->T) return MV_ERR_INVALID_ARG;
     mv_solve_opts O;
@@ -1880,6 +1913,7 @@ static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo)
     int max_n = 1, max_ncols = 0;
     for (int64_t i = 0; i < count; ++i) {
         MV_TRY(validate_problem(probs + i));
+        MV_TRY(require_nt(probs + i, "batch solve"));
         if (probs[i].dtype != probs[0].dtype) return record_message(MV_ERR_INVALID_ARG, "batch: mixed dtypes");
         Plan p = make_plan(probs[i].dtype, probs[i].n, probs[i].T, probs[i].ld, kBatchRowsPerSplit);
         ntt += (int64_t)p.t_blocks * p.t_splits;
@@ -2165,6 +2199,7 @@ int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const 
     MV_TRY(validate_problem(P_hi));
     if (h_info == nullptr || d_x_inout == nullptr || !(eps_lo >= 0.0)) return MV_ERR_INVALID_ARG;
     if (P_hi->dtype != MV_F32 || P_lo->n != P_hi->n || P_lo->T != P_hi->T || P_lo->gamma != P_hi->gamma ||
+        P_lo->layout != P_hi->layout ||
         P_lo->mu != P_hi->mu || P_lo->R_target != P_hi->R_target || P_lo->mode != P_hi->mode)
         return MV_ERR_INVALID_ARG;
     mv_solve_opts O;
@@ -2233,7 +2268,7 @@ extern "C" int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float
                                    mv_stream_t stream) {
     MV_TRY(validate_problem(P));
     if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, false, is_tn(P));
     if (p.total > MV_NOALLOC_SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof(msg),

@@ -20,11 +20,13 @@ MV_OK, MV_ERR_INVALID_ARG, MV_ERR_INFEASIBLE, MV_ERR_NOT_CONVERGED = 0, 1, 2, 3
 MV_ERR_TIMEOUT, MV_ERR_NUMERIC, MV_ERR_CUDA, MV_ERR_UNSUPPORTED, MV_ERR_WORKSPACE = 4, 5, 6, 7, 8
 MV_F32, MV_BF16, MV_FP8_E4M3 = 0, 1, 2
 MV_RETURN_GE, MV_RETURN_EQ = 0, 1
+MV_LAYOUT_NT, MV_LAYOUT_TN = 0, 1
 
 DTYPES = {"f32": MV_F32, "bf16": MV_BF16, "fp8": MV_FP8_E4M3}
 _ESIZE = {MV_F32: 4, MV_BF16: 2, MV_FP8_E4M3: 1}
 _TORCH = {MV_F32: torch.float32, MV_BF16: torch.bfloat16, MV_FP8_E4M3: torch.uint8}
 MODES = {"ge": MV_RETURN_GE, "eq": MV_RETURN_EQ}
+LAYOUTS = {"nt": MV_LAYOUT_NT, "tn": MV_LAYOUT_TN}
 
 # Every symbol include/mv.h declares (checked by the CPU test suite).
 EXPORTS = [
@@ -58,7 +60,7 @@ class Problem(C.Structure):
     _fields_ = [("L", C.c_void_p), ("dtype", C.c_int32), ("mode", C.c_int32),
                 ("row_scale", C.c_void_p), ("n", C.c_int64), ("T", C.c_int64), ("ld", C.c_int64),
                 ("gamma", C.c_double), ("mu", C.c_void_p), ("R_target", C.c_double),
-                ("power_start", C.c_void_p)]
+                ("power_start", C.c_void_p), ("layout", C.c_int32), ("reserved", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -98,7 +100,7 @@ def lib():
         L.mv_center_workspace_size.restype = sz
         L.mv_center_workspace_size.argtypes = [i64, i64]
         L.mv_center_factor.restype = i32
-        L.mv_center_factor.argtypes = [vp, i64, i64, i64, i32, vp, i64, vp, vp, vp, vp, sz, vp]
+        L.mv_center_factor.argtypes = [vp, i64, i64, i64, i32, i32, vp, i64, vp, vp, vp, vp, sz, vp]
         L.mv_project.restype = i32
         L.mv_project.argtypes = [vp, vp, vp, i64, i64, i32, vp, vp, vp]
         L.mv_solve_opts_default.restype = None
@@ -178,28 +180,31 @@ def padded_ld(T: int, dtype: int) -> int:
 
 
 # ------------------------------------------------------------------ calls
-def center_factor(R: torch.Tensor, out_dtype: str = "f32", ld: int | None = None):
+def center_factor(R: torch.Tensor, out_dtype: str = "f32", ld: int | None = None, layout: str = "nt"):
     """mu, L, trace(Sigma) from an n x T FP32 return panel on the GPU (Sec. 2.1).
 
-    Returns (L, row_scale, mu, trace) where L is n x ld (columns T.. are 0),
+    Returns (L, row_scale, mu, trace) where L is n x ld (columns T.. are 0)
+    for layout "nt", or L^T as T x ld (columns n.. are 0) for layout "tn";
     row_scale is an n FP32 tensor for FP8 (else None), mu is FP64 n and trace
     an FP64 scalar tensor.
     """
     assert R.is_cuda and R.dtype == torch.float32 and R.dim() == 2
     dt = DTYPES[out_dtype]
+    lay = LAYOUTS[layout]
     n, T = R.shape
     ldR = R.stride(0)
     if R.stride(1) != 1:
         raise ValueError("R must be row-major")
-    ld = padded_ld(T, dt) if ld is None else int(ld)
+    inner, outer = (T, n) if lay == MV_LAYOUT_NT else (n, T)
+    ld = padded_ld(inner, dt) if ld is None else int(ld)
     dev = R.device
-    L = torch.empty((n, ld), dtype=_TORCH[dt], device=dev)
+    L = torch.empty((outer, ld), dtype=_TORCH[dt], device=dev)
     rs = torch.empty(n, dtype=torch.float32, device=dev) if dt == MV_FP8_E4M3 else None
     mu = torch.empty(n, dtype=torch.float64, device=dev)
     tr = torch.empty(1, dtype=torch.float64, device=dev)
     wsz = lib().mv_center_workspace_size(n, T)
     ws = _workspace(wsz, dev)
-    _check(lib().mv_center_factor(_ptr(R), n, T, ldR, dt, _ptr(L), ld, _ptr(rs), _ptr(mu), _ptr(tr),
+    _check(lib().mv_center_factor(_ptr(R), n, T, ldR, dt, lay, _ptr(L), ld, _ptr(rs), _ptr(mu), _ptr(tr),
                                   _ptr(ws), ws.numel(), _stream()), "mv_center_factor")
     return L, rs, mu, tr
 
@@ -226,14 +231,18 @@ def project(v: torch.Tensor, mu: torch.Tensor, R_target, mode: str = "ge"):
 
 def make_problem(L: torch.Tensor, mu: torch.Tensor, R_target: float, T: int, gamma: float = 0.0,
                  dtype: str = "f32", row_scale: torch.Tensor | None = None, mode: str = "ge",
-                 power_start: torch.Tensor | None = None) -> Problem:
+                 power_start: torch.Tensor | None = None, layout: str = "nt") -> Problem:
+    """mv_problem over L as center_factor returns it (n x ld for "nt", T x ld for "tn")."""
     assert L.is_cuda and L.dim() == 2 and L.stride(1) == 1
     p = Problem()
     p.L = L.data_ptr()
     p.dtype = DTYPES[dtype]
     p.mode = MODES[mode]
+    p.layout = LAYOUTS[layout]
+    p.reserved = 0
     p.row_scale = None if row_scale is None else row_scale.data_ptr()
-    p.n, p.T, p.ld = L.shape[0], int(T), L.stride(0)
+    n = L.shape[0] if p.layout == MV_LAYOUT_NT else mu.shape[0]
+    p.n, p.T, p.ld = n, int(T), L.stride(0)
     p.gamma = float(gamma)
     p.mu = mu.data_ptr()
     p.R_target = float(R_target)
@@ -257,15 +266,15 @@ class Solver:
     """
 
     def __init__(self, L, mu, R_target, T, gamma=0.0, dtype="f32", row_scale=None, mode="ge",
-                 power_start=None, **opts):
+                 power_start=None, layout="nt", **opts):
         self._keep = (L, mu, row_scale, power_start)
-        self.problem = make_problem(L, mu, R_target, T, gamma, dtype, row_scale, mode, power_start)
+        self.problem = make_problem(L, mu, R_target, T, gamma, dtype, row_scale, mode, power_start, layout)
         self.opts = solve_opts(**opts)
         self.ws_bytes = lib().mv_npga_workspace_size(C.byref(self.problem))
         if self.ws_bytes == 0:
             raise MvError(MV_ERR_INVALID_ARG, "mv_npga_workspace_size")
         self.ws = _workspace(self.ws_bytes, L.device)
-        self.x = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
+        self.x = torch.zeros(mu.shape[0], dtype=torch.float64, device=L.device)
 
     def solve(self, x0: torch.Tensor | None = None, allow=(MV_ERR_NOT_CONVERGED,)):
         if x0 is not None:
@@ -292,17 +301,17 @@ class RefinedSolver:
     (mv_npga_solve_refined); reuses workspace and graphs across calls."""
 
     def __init__(self, L_lo, L_hi, mu, R_target, T, gamma=0.0, dtype="bf16", row_scale=None, mode="ge",
-                 power_start=None, eps_lo=1e-5, **opts):
+                 power_start=None, eps_lo=1e-5, layout="nt", **opts):
         self._keep = (L_lo, L_hi, mu, row_scale, power_start)
-        self.p_lo = make_problem(L_lo, mu, R_target, T, gamma, dtype, row_scale, mode, power_start)
-        self.p_hi = make_problem(L_hi, mu, R_target, T, gamma, "f32", None, mode, power_start)
+        self.p_lo = make_problem(L_lo, mu, R_target, T, gamma, dtype, row_scale, mode, power_start, layout)
+        self.p_hi = make_problem(L_hi, mu, R_target, T, gamma, "f32", None, mode, power_start, layout)
         self.opts = solve_opts(**opts)
         self.eps_lo = float(eps_lo)
         nb = max(lib().mv_npga_workspace_size(C.byref(self.p_lo)), lib().mv_npga_workspace_size(C.byref(self.p_hi)))
         if nb == 0:
             raise MvError(MV_ERR_INVALID_ARG, "mv_npga_workspace_size")
         self.ws = _workspace(nb, L_hi.device)
-        self.x = torch.zeros(L_hi.shape[0], dtype=torch.float64, device=L_hi.device)
+        self.x = torch.zeros(mu.shape[0], dtype=torch.float64, device=L_hi.device)
 
     def solve(self, allow=(MV_ERR_NOT_CONVERGED,)):
         info = SolveInfo()
@@ -313,26 +322,26 @@ class RefinedSolver:
 
 
 def npga_solve(L, mu, R_target, T, gamma=0.0, dtype="f32", row_scale=None, mode="ge", x0=None,
-               power_start=None, **opts):
+               power_start=None, layout="nt", **opts):
     """One-shot NPGA solve; returns (x, info dict)."""
-    s = Solver(L, mu, R_target, T, gamma, dtype, row_scale, mode, power_start, **opts)
+    s = Solver(L, mu, R_target, T, gamma, dtype, row_scale, mode, power_start, layout, **opts)
     return s.solve(x0)
 
 
-def gradient(L, y, T, gamma=0.0, dtype="f32", row_scale=None, with_z=True):
+def gradient(L, y, T, gamma=0.0, dtype="f32", row_scale=None, with_z=True, layout="nt"):
     """(z, g) with z = L^T y (FP32) and g = 2 L z + 2 gamma y (FP64).
     ``with_z=False``: z is None and g uses the fused single pass where it applies."""
-    mu = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
-    s = Solver(L, mu, 0.0, T, gamma, dtype, row_scale)
+    mu = torch.zeros(y.shape[0], dtype=torch.float64, device=L.device)
+    s = Solver(L, mu, 0.0, T, gamma, dtype, row_scale, layout=layout)
     return s.gradient(y, with_z)
 
 
-def gradient_noalloc(L, y, T, gamma=0.0, dtype="f32", row_scale=None):
+def gradient_noalloc(L, y, T, gamma=0.0, dtype="f32", row_scale=None, layout="nt"):
     """(z, g) as ``gradient`` but through mv_gradient_noalloc: the library uses
     its fixed scratch array instead of a workspace (outputs still come from
     PyTorch here).  Calls overlapping on the GPU race on that array."""
-    mu = torch.zeros(L.shape[0], dtype=torch.float64, device=L.device)
-    p = make_problem(L, mu, 0.0, T, gamma, dtype, row_scale)
+    mu = torch.zeros(y.shape[0], dtype=torch.float64, device=L.device)
+    p = make_problem(L, mu, 0.0, T, gamma, dtype, row_scale, layout=layout)
     z = torch.empty(T, dtype=torch.float32, device=y.device)
     g = torch.empty_like(y)
     _check(lib().mv_gradient_noalloc(C.byref(p), _ptr(y), _ptr(z), _ptr(g), _stream()), "mv_gradient_noalloc")

@@ -54,7 +54,7 @@ def _c_layout(tmp_path):
     fields = {
         "mv_proj_info": ["nu", "tau", "residual", "support", "status", "steps", "active"],
         "mv_problem": ["L", "dtype", "mode", "row_scale", "n", "T", "ld", "gamma", "mu", "R_target",
-                       "power_start"],
+                       "power_start", "layout", "reserved"],
         "mv_solve_opts": ["max_iter", "kkt_every", "power_iters", "warm_start", "eps", "power_safety",
                           "alpha", "use_graph", "timing", "checkpoint_every", "two_pass"],
         "mv_solve_info": ["iterations", "status", "converged", "proj_failures", "kkt", "objective",
@@ -112,9 +112,9 @@ def test_host_side_argument_errors(mvmod):
     p.dtype = mvmod.MV_F32
     st = lib.mv_npga_solve(C.byref(p), None, fake, C.byref(info), None, 0, None)
     assert st == mvmod.MV_ERR_WORKSPACE
-    assert lib.mv_center_factor(None, 3, 4, 4, 0, None, 4, None, None, None, None, 0, None) == \
+    assert lib.mv_center_factor(None, 3, 4, 4, 0, 0, None, 4, None, None, None, None, 0, None) == \
         mvmod.MV_ERR_INVALID_ARG
-    assert lib.mv_center_factor(fake, 3, 1, 4, 0, fake, 4, None, fake, fake, fake, 1024, None) == \
+    assert lib.mv_center_factor(fake, 3, 1, 4, 0, 0, fake, 4, None, fake, fake, fake, 1024, None) == \
         mvmod.MV_ERR_INVALID_ARG                                   # T < 2
 
 
