@@ -6,7 +6,9 @@ panel is proprietary), centered on the GPU, L stored as FP32 (1.05 GB, far
 larger than L2, so no flush is needed between steps).  One step = one full
 solve through the C ABI: 50 power iterations for the step size, NPGA with a
 KKT check every 5 iterations until the residual is <= 1e-6, and the final
-objective.  Inputs are resident in HBM when the timed region starts.
+objective.  Inputs are resident in HBM when the timed region starts.  L is
+stored transposed (T x n) by default, where the fused single-pass product
+L L^T y streams at copy speed; ``--layout nt`` keeps it n x T.
 
 Printed JSON (one line, rank 0): value = seconds per solve (lower is
 better), e2e = the same through host buffers (upload R, center, solve,
@@ -45,6 +47,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mv", choices=["mv", "reference"])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "fp8"])
+    ap.add_argument("--layout", default="tn", choices=["tn", "nt"],
+                    help="storage of L: tn = L^T (T x n, the fast layout), nt = n x T")
+    ap.add_argument("--two-pass", action="store_true",
+                    help="stream L twice per product (z = L^T y, then L z) instead of the fused single pass")
     ap.add_argument("--config", default="full", choices=["full", "small"])
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--shape", default=None, help="n,T override (profiling runs on a smaller case)")
@@ -90,7 +96,7 @@ def peaks():
 
 # kernel -> (committed ncu summary, source file whose hash the summary records)
 TRAFFIC_FILES = {"gemv_t": ("gemv_traffic.txt", "gemv.cuh"), "gemv_n": ("gemv_traffic.txt", "gemv.cuh"),
-                 "llt": ("llt_traffic.txt", "llt.cuh")}
+                 "llt": ("llt_traffic.txt", "llt.cuh"), "llt_tn": ("llt_traffic.txt", "llt.cuh")}
 
 
 def committed_traffic(kernel):
@@ -115,7 +121,7 @@ def committed_traffic(kernel):
     return float(v) if v else None
 
 
-def roofline(infos, model, dtype):
+def roofline(infos, model, dtype, layout="nt"):
     """HBM roofline of the solve loop's dominant L pass from the per-launch CUDA events.
 
     Algorithmic bytes per launch: the factor once (n T e) plus the vectors the
@@ -127,7 +133,7 @@ def roofline(infos, model, dtype):
     pairs = max(sum(i["timed_pairs"] for i in infos), 1)
     step_us = round(sum(i["t_step_ms"] for i in infos) / pairs * 1e3, 2)
     if all(i.get("fused", 0) for i in infos):
-        kern = "llt"
+        kern = "llt_tn" if layout == "tn" else "llt"
         avg_ms = sum(i["t_fused_ms"] for i in infos) / pairs
         alg = nT * es + 4 * n + 8 * n + sc          # L, y (FP32), g (FP64)
         other = None
@@ -274,11 +280,11 @@ def main():
     model = workload(args, rank)
     R32 = factor_returns(model, np.float32)
     R_dev = torch.from_numpy(R32).to(dev)
-    L, rs, mu, tr = mv.center_factor(R_dev, args.dtype)
+    L, rs, mu, tr = mv.center_factor(R_dev, args.dtype, layout=args.layout)
     Rt = float(np.percentile(mu.cpu().numpy(), 60))
     r0 = torch.from_numpy(power_start(model.n)).to(dev)
     solver = mv.Solver(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
-                       timing=1)
+                       timing=1, layout=args.layout, two_pass=1 if args.two_pass else 0)
     del R_dev
 
     def barrier():
@@ -308,7 +314,7 @@ def main():
         ms = float(t.item())
 
     # roofline of the dominant kernel (per-launch CUDA events around every loop launch)
-    roof = roofline(infos, model, args.dtype)
+    roof = roofline(infos, model, args.dtype, args.layout)
     es = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
     nT = model.n * model.T
 
@@ -326,10 +332,10 @@ def main():
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
             R_buf.copy_(R_pin, non_blocking=True)
-            L2, rs2, mu2, _ = mv.center_factor(R_buf, args.dtype)
+            L2, rs2, mu2, _ = mv.center_factor(R_buf, args.dtype, layout=args.layout)
             if e_solver is None:
                 e_solver = mv.Solver(L2, mu2, Rt, model.T, dtype=args.dtype, row_scale=rs2, power_start=r0,
-                                     eps=args.eps)
+                                     eps=args.eps, layout=args.layout)
             else:
                 e_solver.problem.L = L2.data_ptr()
                 e_solver.problem.mu = mu2.data_ptr()
@@ -348,31 +354,47 @@ def main():
 
     # Low-precision storage + FP32 refinement on the same workload and GPU.
     variants = {}
-    if not args.no_variants and info.get("fused", 0):
-        # The same FP32 solve with the two half-products as separate passes.
-        tps = mv.Solver(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
-                        timing=1, two_pass=1)
+
+    def timed_solves(sv):
         for _ in range(args.warmup):
-            tps.solve()
+            sv.solve()
         torch.cuda.synchronize()
         v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        tinfos = []
+        vinfos = []
         v0.record(stream)
         for _ in range(args.steps):
-            _, ti = tps.solve()
-            tinfos.append(ti)
+            _, vi = sv.solve()
+            vinfos.append(vi)
         v1.record(stream)
         torch.cuda.synchronize()
-        variants[args.dtype + "_two_pass"] = {
-            "value": v0.elapsed_time(v1) / args.steps / 1e3, "unit": "s", "iterations": ti["iterations"],
-            "kkt": ti["kkt"], "objective": ti["objective"], "roofline": roofline(tinfos, model, args.dtype)}
-        del tps
+        return v0.elapsed_time(v1) / args.steps / 1e3, vinfos
+
+    if not args.no_variants:
+        # The same FP32 solve with the two half-products as separate passes, and
+        # in the other layout: the path from two passes over n x T to one pass
+        # over L^T.
+        R_dev = torch.from_numpy(R32).to(dev)
+        other = "nt" if args.layout == "tn" else "tn"
+        Lo, rso, _, _ = mv.center_factor(R_dev, args.dtype, layout=other)
+        del R_dev
+        for name, LL, rr, lay, two in ((f"{args.dtype}_{args.layout}_two_pass", L, rs, args.layout, 1),
+                                       (f"{args.dtype}_{other}_fused", Lo, rso, other, 0),
+                                       (f"{args.dtype}_{other}_two_pass", Lo, rso, other, 1)):
+            sv = mv.Solver(LL, mu, Rt, model.T, dtype=args.dtype, row_scale=rr, power_start=r0, eps=args.eps,
+                           timing=1, two_pass=two, layout=lay)
+            t, vinfos = timed_solves(sv)
+            variants[name] = {"value": t, "unit": "s", "iterations": vinfos[-1]["iterations"],
+                              "kkt": vinfos[-1]["kkt"], "objective": vinfos[-1]["objective"],
+                              "fused": vinfos[-1]["fused"], "roofline": roofline(vinfos, model, args.dtype, lay)}
+            del sv
+        del Lo, rso
     if not args.no_variants and args.dtype == "f32":
         R_dev = torch.from_numpy(R32).to(dev)
         for vdt in ("bf16", "fp8"):
-            Llo, rslo, _, _ = mv.center_factor(R_dev, vdt)
+            # low-precision copy n x T (its faster layout), FP32 refinement on the headline L
+            Llo, rslo, _, _ = mv.center_factor(R_dev, vdt, layout="nt")
             rsv = mv.RefinedSolver(Llo, L, mu, Rt, model.T, dtype=vdt, row_scale=rslo, power_start=r0,
-                                   eps_lo=1e-5, eps=args.eps)
+                                   eps_lo=1e-5, eps=args.eps, layout="nt", layout_hi=args.layout)
             for _ in range(args.warmup):
                 rsv.solve()
             torch.cuda.synchronize()
@@ -407,6 +429,9 @@ def main():
             torch.cuda.synchronize()
             sk_ms.append(e[0].elapsed_time(e[1]))
         flop = 2.0 * model.n * model.T * args.sketch_m
+        t_first = time.perf_counter()
+        mv.str_truncate(Ls, args.str_k, -1.0, float(trd.cpu()))          # first call: library load + set-up
+        t_first = time.perf_counter() - t_first
         e[2].record(stream)
         L_eff, sigma, gamma = mv.str_truncate(Ls, args.str_k, -1.0, float(trd.cpu()))
         e[3].record(stream)
@@ -422,7 +447,7 @@ def main():
         e[1].record(stream)
         torch.cuda.synchronize()
         s_ms = e[0].elapsed_time(e[1]) / args.steps
-        _, gfull = mv.gradient(L, xs, model.T)             # 2 L L^T x on the full FP32 model
+        _, gfull = mv.gradient(L, xs, model.T, layout=args.layout, with_z=False)  # 2 L L^T x, full FP32 model
         f_str_full = float(torch.dot(xs, gfull).item()) / 2.0
         f_full = infos[-1]["objective"]
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -431,7 +456,8 @@ def main():
         str_res = {"sketch": {"m": args.sketch_m, "ms": min(sk_ms), "tflop": flop / 1e12,
                               "achieved_tflops": round(tflops, 1), "peak_tflops": bf16_peak,
                               "frac": round(tflops / bf16_peak, 4), "bound": "tensor"},
-                   "truncate": {"k": args.str_k, "ms": tr_ms, "gamma": gamma, "sigma_1": float(sigma[0]),
+                   "truncate": {"k": args.str_k, "ms": tr_ms, "first_call_s": round(t_first, 3), "gamma": gamma,
+                                "sigma_1": float(sigma[0]),
                                 "sigma_k": float(sigma[-1])},
                    "solve": {"value": s_ms / 1e3, "unit": "s", "iterations": si["iterations"], "kkt": si["kkt"],
                              "step_kernel_share": None},
@@ -542,9 +568,10 @@ def main():
         line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-                "config": {"workload": f"npga full model n={model.n} T={model.T} {args.dtype} L, "
+                "config": {"workload": f"npga full model n={model.n} T={model.T} {args.dtype} L "
+                                       f"({'L^T stored T x n' if args.layout == 'tn' else 'n x T'}), "
                                        f"KKT eps={args.eps}, 50 power iterations",
-                           "n": model.n, "T": model.T, "kkt_eps": args.eps,
+                           "n": model.n, "T": model.T, "kkt_eps": args.eps, "layout": args.layout,
                            "l2": "inputs larger than L2 (L is %.2f GB)" % (nT * es / 1e9),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],

@@ -246,7 +246,8 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *opts, double *d_x_in
  *  copies differ by far less than 1%, so the step stays admissible) and no
  *  second power method, until the KKT residual of P_hi is <= opts->eps.
  *  P_lo and P_hi must describe the same problem (n, T, gamma, mu, target,
- *  mode); P_hi->dtype must be MV_F32.  Workspace: the larger of the two
+ *  mode); P_hi->dtype must be MV_F32.  The two copies may use different
+ *  layouts (each its fastest).  Workspace: the larger of the two
  *  mv_npga_workspace_size values.  h_info: iterations = both phases,
  *  refine_iterations = phase 2, kkt/objective/alpha of phase 2.  Blocking.
  * ------------------------------------------------------------------------ */

@@ -234,6 +234,22 @@ llt_kernel(const __grid_constant__ CUtensorMap tmL, const LltArgs a) {
         umma::mbar_fence_init();
         for (int q = 0; q < kLltSlots && q < nj; ++q) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
     }
+    __syncthreads();
+    // The first stages' loads go out before the cluster barrier: they touch
+    // only this CTA's shared memory and barriers.
+    auto issue = [&](int j) {
+        const int s = j % kLltStages;
+        const int b = cid + j * a.G;
+        const uint32_t dst = umma::smem_u32(sm + (size_t)s * L.stage);
+        umma::mbar_arrive_expect_tx(full0 + 8 * s, stage_tx);
+        for (int i = 0; i < a.nbox; ++i)
+            umma::tma_load_2d(dst + (uint32_t)(i * a.box_rows * RB), &tmL, b * W, row0 + i * a.box_rows,
+                              full0 + 8 * s);
+    };
+    if (warp == kLltConsumerWarps && lane == 0) {
+        umma::prefetch_tensormap(&tmL);
+        for (int j = 0; j < kLltStages && j < nj; ++j) issue(j);
+    }
     for (int i = tid; i < a.rpc; i += kLltThreads) {
         const int r = row0 + i;
         s_y[i] = r < a.n ? a.y32[r] : 0.f;
@@ -247,21 +263,15 @@ llt_kernel(const __grid_constant__ CUtensorMap tmL, const LltArgs a) {
     if (warp == kLltConsumerWarps) {
         // ---------------- producer: column block j of this cluster -> stage j % 2
         if (lane == 0) {
-            umma::prefetch_tensormap(&tmL);
             bool bail = false;
-            for (int j = 0; j < nj; ++j) {
+            for (int j = kLltStages; j < nj; ++j) {
                 const int s = j % kLltStages;
-                if (j >= kLltStages && !umma::mbar_wait(empty0 + 8 * s, (uint32_t)(j / kLltStages - 1) & 1u,
-                                                        bail ? kLltBailNs : kLltWaitNs)) {
+                if (!umma::mbar_wait(empty0 + 8 * s, (uint32_t)(j / kLltStages - 1) & 1u,
+                                     bail ? kLltBailNs : kLltWaitNs)) {
                     atomicExch(a.err, 3);
                     bail = true;
                 }
-                const int b = cid + j * a.G;
-                const uint32_t dst = umma::smem_u32(sm + (size_t)s * L.stage);
-                umma::mbar_arrive_expect_tx(full0 + 8 * s, stage_tx);
-                for (int i = 0; i < a.nbox; ++i)
-                    umma::tma_load_2d(dst + (uint32_t)(i * a.box_rows * RB), &tmL, b * W,
-                                      row0 + i * a.box_rows, full0 + 8 * s);
+                issue(j);
             }
             // Drain: every stage's last load has landed before the CTA may exit.
             for (int j = nj - kLltStages < 0 ? 0 : nj - kLltStages; j < nj; ++j)
@@ -444,6 +454,19 @@ lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
         umma::mbar_fence_init();
         for (int q = 0; q < kLltSlots && q < nj; ++q) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
     }
+    __syncthreads();
+    auto issue = [&](int j) {
+        const int s = j % kLltStages;
+        const int b = cid + j * a.G;
+        const uint32_t dst = umma::smem_u32(sm + (size_t)s * L.stage);
+        umma::mbar_arrive_expect_tx(full0 + 8 * s, stage_tx);
+        for (int k = 0; k < a.nbox; ++k)
+            umma::tma_load_2d(dst + (uint32_t)(k * BOXB), &tmM, col0 + k * kLltBoxCols, b * W, full0 + 8 * s);
+    };
+    if (warp == kLltConsumerWarps && lane == 0) {          // first stages before the cluster barrier
+        umma::prefetch_tensormap(&tmM);
+        for (int j = 0; j < kLltStages && j < nj; ++j) issue(j);
+    }
     for (int i = tid; i < npc; i += kLltThreads) s_y[i] = col0 + i < a.n ? a.y32[col0 + i] : 0.f;
     cluster.sync();
 
@@ -455,20 +478,15 @@ lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
 
     if (warp == kLltConsumerWarps) {
         if (lane == 0) {
-            umma::prefetch_tensormap(&tmM);
             bool bail = false;
-            for (int j = 0; j < nj; ++j) {
+            for (int j = kLltStages; j < nj; ++j) {
                 const int s = j % kLltStages;
-                if (j >= kLltStages && !umma::mbar_wait(empty0 + 8 * s, (uint32_t)(j / kLltStages - 1) & 1u,
-                                                        bail ? kLltBailNs : kLltWaitNs)) {
+                if (!umma::mbar_wait(empty0 + 8 * s, (uint32_t)(j / kLltStages - 1) & 1u,
+                                     bail ? kLltBailNs : kLltWaitNs)) {
                     atomicExch(a.err, 3);
                     bail = true;
                 }
-                const int b = cid + j * a.G;
-                const uint32_t dst = umma::smem_u32(sm + (size_t)s * L.stage);
-                umma::mbar_arrive_expect_tx(full0 + 8 * s, stage_tx);
-                for (int k = 0; k < a.nbox; ++k)
-                    umma::tma_load_2d(dst + (uint32_t)(k * BOXB), &tmM, col0 + k * kLltBoxCols, b * W, full0 + 8 * s);
+                issue(j);
             }
             for (int j = nj - kLltStages < 0 ? 0 : nj - kLltStages; j < nj; ++j)
                 if (!umma::mbar_wait(full0 + 8 * (j % kLltStages), (uint32_t)(j / kLltStages) & 1u, kLltWaitNs))

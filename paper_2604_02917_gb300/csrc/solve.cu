@@ -2199,7 +2199,6 @@ int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const 
     MV_TRY(validate_problem(P_hi));
     if (h_info == nullptr || d_x_inout == nullptr || !(eps_lo >= 0.0)) return MV_ERR_INVALID_ARG;
     if (P_hi->dtype != MV_F32 || P_lo->n != P_hi->n || P_lo->T != P_hi->T || P_lo->gamma != P_hi->gamma ||
-        P_lo->layout != P_hi->layout ||
         P_lo->mu != P_hi->mu || P_lo->R_target != P_hi->R_target || P_lo->mode != P_hi->mode)
         return MV_ERR_INVALID_ARG;
     mv_solve_opts O;

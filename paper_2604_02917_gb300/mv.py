@@ -301,10 +301,11 @@ class RefinedSolver:
     (mv_npga_solve_refined); reuses workspace and graphs across calls."""
 
     def __init__(self, L_lo, L_hi, mu, R_target, T, gamma=0.0, dtype="bf16", row_scale=None, mode="ge",
-                 power_start=None, eps_lo=1e-5, layout="nt", **opts):
+                 power_start=None, eps_lo=1e-5, layout="nt", layout_hi=None, **opts):
         self._keep = (L_lo, L_hi, mu, row_scale, power_start)
         self.p_lo = make_problem(L_lo, mu, R_target, T, gamma, dtype, row_scale, mode, power_start, layout)
-        self.p_hi = make_problem(L_hi, mu, R_target, T, gamma, "f32", None, mode, power_start, layout)
+        self.p_hi = make_problem(L_hi, mu, R_target, T, gamma, "f32", None, mode, power_start,
+                                 layout if layout_hi is None else layout_hi)
         self.opts = solve_opts(**opts)
         self.eps_lo = float(eps_lo)
         nb = max(lib().mv_npga_workspace_size(C.byref(self.p_lo)), lib().mv_npga_workspace_size(C.byref(self.p_hi)))
