@@ -42,8 +42,12 @@ __device__ __forceinline__ void store_elem(void *L, int64_t idx, double val, flo
     }
 }
 
-// WRITE = false: statistics only (mu, row sums of squares, FP8 scale); the
-// transposed layout is then written by transpose_center_kernel.
+// One block per asset row.  Pass 1: mu_i = sum_t R_it / T in FP64, and the
+// FP32 range of the row; the FP8 scale max_t |d_it| / 448 follows exactly
+// from it, because d = ((double)x - mu) c is monotone in x.  Pass 2 (WRITE):
+// d_it in FP64, stored in the storage type, and sum_t d_it^2 for the trace;
+// the re-read of the row mostly hits L2.  With WRITE = false (transposed
+// layout) pass 2 is done by transpose_center_kernel.
 template <int DT, bool WRITE>
 __global__ void __launch_bounds__(kCenterThreads)
 center_kernel(const float *__restrict__ R, int64_t ldR, int T, void *__restrict__ L, int64_t ldL,
@@ -52,72 +56,108 @@ center_kernel(const float *__restrict__ R, int64_t ldR, int T, void *__restrict_
     const int64_t i = blockIdx.x;
     const float *r = R + i * ldR;
     double s[1] = {0.0};
-    for (int t = threadIdx.x; t < T; t += kCenterThreads) s[0] += (double)r[t];
+    float xmin = INFINITY, xmax = -INFINITY;
+    for (int t = threadIdx.x; t < T; t += kCenterThreads) {
+        const float x = r[t];
+        s[0] += (double)x;
+        if constexpr (DT == MV_FP8_E4M3) {
+            xmin = fminf(xmin, x);
+            xmax = fmaxf(xmax, x);
+        }
+    }
     block_sum<1, kCenterThreads>(s, red);
     const double mean = s[0] / (double)T;
     const double c = 1.0 / sqrt((double)(T - 1));
-    double q[1] = {0.0};
-    double amax = 0.0;
-    for (int t = threadIdx.x; t < T; t += kCenterThreads) {
-        const double d = ((double)r[t] - mean) * c;
-        q[0] = fma(d, d, q[0]);
-        amax = fmax(amax, fabs(d));
-    }
-    __syncthreads();
-    block_sum<1, kCenterThreads>(q, red);
     float inv_scale = 1.f;
     if constexpr (DT == MV_FP8_E4M3) {
-        double mn = -amax, mx = amax;
+        double mn = (double)xmin, mx = (double)xmax;
         __syncthreads();
         block_minmax<kCenterThreads>(mn, mx, red);
-        const float scale = mx > 0.0 ? (float)(mx / 448.0) : 1.f;
+        const double amax = fmax((mx - mean) * c, (mean - mn) * c);
+        const float scale = amax > 0.0 ? (float)(amax / 448.0) : 1.f;
         inv_scale = 1.f / scale;
         if (threadIdx.x == 0) row_scale[i] = scale;
     }
     if constexpr (WRITE) {
+        double q[1] = {0.0};
         for (int64_t t = threadIdx.x; t < ldL; t += kCenterThreads) {
             const double d = t < T ? ((double)r[t] - mean) * c : 0.0;
+            q[0] = fma(d, d, q[0]);
             store_elem<DT>(L, i * ldL + t, d, inv_scale);
         }
+        __syncthreads();
+        block_sum<1, kCenterThreads>(q, red);
+        if (threadIdx.x == 0) rowsq[i] = q[0];
     }
-    if (threadIdx.x == 0) {
-        mu[i] = mean;
-        rowsq[i] = q[0];
-    }
+    if (threadIdx.x == 0) mu[i] = mean;
 }
 
-// L^T (T x ldM, row t = period t) from R (n x T): 32 x 32 tiles through
-// shared memory, read along periods and written along assets; columns
-// n..ldM-1 are written as zeros.  Values as center_kernel's.
+// L^T (T x ldM, row t = period t) from R (n x T).  A block owns 32 assets and
+// one of kSlices period slices, walking it in 32 x 32 tiles through shared
+// memory: read along periods, written along assets; columns n..ldM-1 are
+// written as zeros.  Values as center_kernel's; each block leaves
+// sum_t d_it^2 of its slice in sqpart[slice][i] (added in fixed order by
+// trace_kernel).
 constexpr int kTile = 32;
+constexpr int kSlices = 8;
 template <int DT>
 __global__ void __launch_bounds__(kTile * 8)
 transpose_center_kernel(const float *__restrict__ R, int64_t ldR, int64_t n, int T, void *__restrict__ M, int64_t ldM,
-                        const float *__restrict__ row_scale, const double *__restrict__ mu) {
+                        const float *__restrict__ row_scale, const double *__restrict__ mu,
+                        double *__restrict__ sqpart) {
     __shared__ double tile[kTile][kTile + 1];
-    const int64_t i0 = (int64_t)blockIdx.y * kTile;      // assets
-    const int64_t t0 = (int64_t)blockIdx.x * kTile;      // periods
+    const int64_t i0 = (int64_t)blockIdx.y * kTile;        // assets
+    const int slice = blockIdx.x;
+    const int per = ((T + kSlices - 1) / kSlices + kTile - 1) / kTile * kTile;
+    const int tb = slice * per, te = min(T, tb + per);
     const double c = 1.0 / sqrt((double)(T - 1));
     const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
-    for (int k = ty; k < kTile; k += 8) {
-        const int64_t i = i0 + k, t = t0 + tx;
-        tile[k][tx] = (i < n && t < T) ? ((double)R[i * ldR + t] - mu[i]) * c : 0.0;
+    double mloc[4];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int64_t i = i0 + ty + 8 * j;
+        mloc[j] = i < n ? mu[i] : 0.0;
     }
-    __syncthreads();
-    for (int k = ty; k < kTile; k += 8) {
-        const int64_t t = t0 + k, i = i0 + tx;
-        if (t < T && i < ldM) {
-            const float inv = (DT == MV_FP8_E4M3 && i < n) ? 1.f / row_scale[i] : 1.f;
-            store_elem<DT>(M, t * ldM + i, tile[tx][k], inv);
+    float inv = 1.f;
+    if (DT == MV_FP8_E4M3 && i0 + tx < n) inv = 1.f / row_scale[i0 + tx];
+    for (int t0 = tb; t0 < te; t0 += kTile) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = ty + 8 * j;
+            const int64_t i = i0 + k, t = t0 + tx;
+            const double d = (i < n && t < te) ? ((double)R[i * ldR + t] - mloc[j]) * c : 0.0;
+            acc[j] = fma(d, d, acc[j]);
+            tile[k][tx] = d;
         }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = ty + 8 * j;
+            const int64_t t = t0 + k, i = i0 + tx;
+            if (t < te && i < ldM) store_elem<DT>(M, t * ldM + i, tile[tx][k], i < n ? inv : 1.f);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        double v = warp_sum(acc[j]);
+        const int64_t i = i0 + ty + 8 * j;
+        if (tx == 0 && i < n) sqpart[(int64_t)slice * n + i] = v;
     }
 }
 
+// trace(Sigma) = sum_i rowsq_i, each rowsq_i the sum of its `parts` slice
+// partials (parts = 1 for the n x T layout), in a fixed order.
 __global__ void __launch_bounds__(kCenterThreads)
-trace_kernel(const double *__restrict__ rowsq, int64_t n, double *__restrict__ trace) {
+trace_kernel(const double *__restrict__ rowsq, int64_t n, int parts, double *__restrict__ trace) {
     __shared__ double red[(kCenterThreads / kWarp + 1) * 1];
     double s[1] = {0.0};
-    for (int64_t i = threadIdx.x; i < n; i += kCenterThreads) s[0] += rowsq[i];
+    for (int64_t i = threadIdx.x; i < n; i += kCenterThreads) {
+        double r = 0.0;
+        for (int k = 0; k < parts; ++k) r += rowsq[(int64_t)k * n + i];
+        s[0] += r;
+    }
     block_sum<1, kCenterThreads>(s, red);
     if (threadIdx.x == 0) *trace = s[0];
 }
@@ -130,7 +170,7 @@ extern "C" {
 
 size_t mv_center_workspace_size(int64_t n, int64_t T) {
     (void)T;
-    return n > 0 ? align_up((size_t)n * 8, 256) : 0;
+    return n > 0 ? align_up((size_t)n * 8 * kSlices, 256) : 0;
 }
 
 int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int out_dtype, int layout, void *d_L,
@@ -149,7 +189,7 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int ou
     (void)cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
     double *rowsq = reinterpret_cast<double *>(d_ws);
-    const dim3 tgrid((unsigned)((T + kTile - 1) / kTile), (unsigned)((ldL + kTile - 1) / kTile));
+    const dim3 tgrid((unsigned)kSlices, (unsigned)((ldL + kTile - 1) / kTile));
     if (tn && tgrid.y > 65535u) return MV_ERR_UNSUPPORTED;
     switch (out_dtype) {
         case MV_F32:
@@ -157,7 +197,7 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int ou
                 center_kernel<MV_F32, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
                                                                                     nullptr, d_mu, rowsq);
                 transpose_center_kernel<MV_F32><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL, nullptr,
-                                                                            d_mu);
+                                                                            d_mu, rowsq);
             } else {
                 center_kernel<MV_F32, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL, nullptr,
                                                                                    d_mu, rowsq);
@@ -168,7 +208,7 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int ou
                 center_kernel<MV_BF16, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
                                                                                      nullptr, d_mu, rowsq);
                 transpose_center_kernel<MV_BF16><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL, nullptr,
-                                                                             d_mu);
+                                                                            d_mu, rowsq);
             } else {
                 center_kernel<MV_BF16, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL,
                                                                                     nullptr, d_mu, rowsq);
@@ -179,14 +219,14 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int ou
                 center_kernel<MV_FP8_E4M3, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
                                                                                          d_row_scale, d_mu, rowsq);
                 transpose_center_kernel<MV_FP8_E4M3><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL,
-                                                                                 d_row_scale, d_mu);
+                                                                                 d_row_scale, d_mu, rowsq);
             } else {
                 center_kernel<MV_FP8_E4M3, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL,
                                                                                         d_row_scale, d_mu, rowsq);
             }
             break;
     }
-    trace_kernel<<<1, kCenterThreads, 0, s>>>(rowsq, n, d_trace);
+    trace_kernel<<<1, kCenterThreads, 0, s>>>(rowsq, n, tn ? kSlices : 1, d_trace);
     MV_CUDA_TRY(cudaGetLastError());
     return MV_OK;
 }
