@@ -99,10 +99,13 @@ TRAFFIC_FILES = {"gemv_t": ("gemv_traffic.txt", "gemv.cuh"), "gemv_n": ("gemv_tr
                  "llt": ("llt_traffic.txt", "llt.cuh"), "llt_tn": ("llt_traffic.txt", "llt.cuh")}
 
 
-def committed_traffic(kernel):
-    """Per-launch DRAM bytes from the committed ncu summary, if it matches this source."""
+def committed_traffic(kernel, layout="nt"):
+    """Per-launch DRAM bytes from the committed ncu summary, if it matches this source.
+
+    Entries are keyed by kernel, with a ``_tn`` suffix for the transposed layout."""
     if kernel not in TRAFFIC_FILES:
         return None
+    key = kernel if kernel.endswith("_tn") or layout != "tn" else kernel + "_tn"
     fname, srcname = TRAFFIC_FILES[kernel]
     path = os.path.join(ROOT, "profiles", fname)
     if not os.path.exists(path):
@@ -117,7 +120,7 @@ def committed_traffic(kernel):
             vals[k.strip()] = v.strip()
     if vals.get("source_sha", vals.get("gemv_source_sha")) != sha:
         return None
-    v = vals.get(f"{kernel}_dram_bytes_per_launch")
+    v = vals.get(f"{key}_dram_bytes_per_launch")
     return float(v) if v else None
 
 
@@ -150,7 +153,7 @@ def roofline(infos, model, dtype, layout="nt"):
     achieved = alg / (avg_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": committed_traffic(kern), "kernel": kern,
+            "frac": round(achieved / peak, 4), "traffic": committed_traffic(kern, layout), "kernel": kern,
             "peak_source": peak_kind, "avg_launch_us": round(avg_ms * 1e3, 2),
             "alg_bytes_per_launch": alg, "step_kernel_avg_us": step_us}
     if other is not None:
