@@ -325,8 +325,8 @@ def main():
     e2e = None
     if not args.no_e2e:
         R_pin = torch.from_numpy(R32).pin_memory()
-        R_buf = torch.empty_like(R_pin, device=dev)
         x_host = torch.empty(model.n, dtype=torch.float64).pin_memory()
+        cws = torch.empty(mv.lib().mv_center_host_workspace_size(model.n, model.T), dtype=torch.uint8, device=dev)
         e_solver = None
         e_times = []
         for i in range(2 + 3):
@@ -334,8 +334,8 @@ def main():
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            R_buf.copy_(R_pin, non_blocking=True)
-            L2, rs2, mu2, _ = mv.center_factor(R_buf, args.dtype, layout=args.layout)
+            # upload of R overlapped with its centering, chunk by chunk (mv_center_factor_host)
+            L2, rs2, mu2, _ = mv.center_factor_host(R_pin, args.dtype, layout=args.layout, device=dev, ws=cws)
             if e_solver is None:
                 e_solver = mv.Solver(L2, mu2, Rt, model.T, dtype=args.dtype, row_scale=rs2, power_start=r0,
                                      eps=args.eps, layout=args.layout)
@@ -353,7 +353,7 @@ def main():
             del L2, mu2, rs2
         e2e = {"value": float(np.mean(e_times)) / 1e3, "unit": "s",
                "h2d_bytes_per_step": int(R32.nbytes), "d2h_bytes_per_step": int(model.n * 8)}
-        del R_buf, R_pin
+        del R_pin, cws
 
     # Low-precision storage + FP32 refinement on the same workload and GPU.
     variants = {}

@@ -107,6 +107,20 @@ int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR,
                      double *d_mu, double *d_trace,
                      void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
+/*  The same from returns in HOST memory: h_R is n x T FP32 row-major (ldR >= T),
+ *  best page-locked.  The rows are uploaded in chunks of about 64 MB on an
+ *  internal copy stream into two device staging buffers inside the
+ *  workspace, and each chunk is centred on `stream` while the next one is in
+ *  flight, so the upload and the centering overlap.  Outputs as
+ *  mv_center_factor; workspace mv_center_host_workspace_size(n, T) bytes.
+ *  Asynchronous with respect to the host for page-locked h_R; h_R must stay
+ *  valid until `stream` reaches the end of the call's work. */
+size_t mv_center_host_workspace_size(int64_t n, int64_t T);
+int mv_center_factor_host(const float *h_R, int64_t n, int64_t T, int64_t ldR,
+                          int out_dtype, int layout, void *d_L, int64_t ldL, float *d_row_scale,
+                          double *d_mu, double *d_trace,
+                          void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * 2. Exact projection onto F (Sec. 3.1, Eqs. simplex-tau, simplex-proj,
  *    projF-dualpath), batched over problems that share mu.

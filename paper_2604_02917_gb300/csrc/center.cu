@@ -51,10 +51,10 @@ __device__ __forceinline__ void store_elem(void *L, int64_t idx, double val, flo
 template <int DT, bool WRITE>
 __global__ void __launch_bounds__(kCenterThreads)
 center_kernel(const float *__restrict__ R, int64_t ldR, int T, void *__restrict__ L, int64_t ldL,
-              float *__restrict__ row_scale, double *__restrict__ mu, double *__restrict__ rowsq) {
+              float *__restrict__ row_scale, double *__restrict__ mu, double *__restrict__ rowsq, int64_t i_base) {
     __shared__ double red[(kCenterThreads / kWarp + 1) * 2];
-    const int64_t i = blockIdx.x;
-    const float *r = R + i * ldR;
+    const int64_t i = i_base + blockIdx.x;                 // asset; R holds rows i_base ..
+    const float *r = R + (int64_t)blockIdx.x * ldR;
     double s[1] = {0.0};
     float xmin = INFINITY, xmax = -INFINITY;
     for (int t = threadIdx.x; t < T; t += kCenterThreads) {
@@ -97,18 +97,18 @@ center_kernel(const float *__restrict__ R, int64_t ldR, int T, void *__restrict_
 // memory: read along periods, written along assets; columns n..ldM-1 are
 // written as zeros.  Values as center_kernel's; each block leaves
 // sum_t d_it^2 of its slice in sqpart[slice][i] (added in fixed order by
-// trace_kernel).
+// trace_kernel).  The slice count is chosen per call to fill the GPU.
 constexpr int kTile = 32;
-constexpr int kSlices = 8;
+constexpr int kMaxSlices = 64;                  // period slices per asset tile (grid fill), at most
 template <int DT>
 __global__ void __launch_bounds__(kTile * 8)
 transpose_center_kernel(const float *__restrict__ R, int64_t ldR, int64_t n, int T, void *__restrict__ M, int64_t ldM,
                         const float *__restrict__ row_scale, const double *__restrict__ mu,
-                        double *__restrict__ sqpart) {
+                        double *__restrict__ sqpart, int64_t i_base, int slices) {
     __shared__ double tile[kTile][kTile + 1];
-    const int64_t i0 = (int64_t)blockIdx.y * kTile;        // assets
+    const int64_t i0 = i_base + (int64_t)blockIdx.y * kTile;   // assets; R holds rows i_base ..
     const int slice = blockIdx.x;
-    const int per = ((T + kSlices - 1) / kSlices + kTile - 1) / kTile * kTile;
+    const int per = ((T + slices - 1) / slices + kTile - 1) / kTile * kTile;
     const int tb = slice * per, te = min(T, tb + per);
     const double c = 1.0 / sqrt((double)(T - 1));
     const int tx = threadIdx.x % kTile, ty = threadIdx.x / kTile;
@@ -126,7 +126,7 @@ transpose_center_kernel(const float *__restrict__ R, int64_t ldR, int64_t n, int
         for (int j = 0; j < 4; ++j) {
             const int k = ty + 8 * j;
             const int64_t i = i0 + k, t = t0 + tx;
-            const double d = (i < n && t < te) ? ((double)R[i * ldR + t] - mloc[j]) * c : 0.0;
+            const double d = (i < n && t < te) ? ((double)R[(i - i_base) * ldR + t] - mloc[j]) * c : 0.0;
             acc[j] = fma(d, d, acc[j]);
             tile[k][tx] = d;
         }
@@ -162,6 +162,65 @@ trace_kernel(const double *__restrict__ rowsq, int64_t n, int parts, double *__r
     if (threadIdx.x == 0) *trace = s[0];
 }
 
+// Centering of the asset rows [i0, i1) of R, whose row i0 is at R_rows.
+// The last chunk of the transposed layout also zero-fills columns n..ldL-1.
+// Period slices of the transposed write: about 8 blocks per SM over the
+// asset tiles of a chunk of `rows` assets.
+static int center_slices(int64_t rows, int64_t T) {
+    const int64_t tiles = (rows + kTile - 1) / kTile;
+    int64_t sl = (8 * 152 + tiles - 1) / tiles;
+    const int64_t max_by_T = (T + kTile - 1) / kTile;
+    sl = sl < 1 ? 1 : (sl > kMaxSlices ? kMaxSlices : sl);
+    return (int)(sl < max_by_T ? sl : max_by_T);
+}
+
+static void center_chunk(const float *R_rows, int64_t ldR, int64_t n, int64_t T, int out_dtype, bool tn, void *d_L,
+                         int64_t ldL, float *d_row_scale, double *d_mu, double *rowsq, int64_t i0, int64_t i1,
+                         int slices, cudaStream_t s) {
+    const unsigned rows = (unsigned)(i1 - i0);
+    const int64_t wend = (tn && i1 == n) ? ldL : i1;          // transposed: columns written by this chunk
+    const dim3 tgrid((unsigned)slices, (unsigned)((wend - i0 + kTile - 1) / kTile));
+#define MV_CENTER_CASE(DT, RS)                                                                                   \
+    if (tn) {                                                                                                    \
+        center_kernel<DT, false><<<rows, kCenterThreads, 0, s>>>(R_rows, ldR, (int)T, nullptr, 0, RS, d_mu,      \
+                                                                 rowsq, i0);                                     \
+        transpose_center_kernel<DT><<<tgrid, kTile * 8, 0, s>>>(R_rows, ldR, n, (int)T, d_L, ldL, RS, d_mu,      \
+                                                                rowsq, i0, slices);                              \
+    } else {                                                                                                     \
+        center_kernel<DT, true><<<rows, kCenterThreads, 0, s>>>(R_rows, ldR, (int)T, d_L, ldL, RS, d_mu, rowsq,  \
+                                                                i0);                                             \
+    }
+    switch (out_dtype) {
+        case MV_F32: MV_CENTER_CASE(MV_F32, nullptr) break;
+        case MV_BF16: MV_CENTER_CASE(MV_BF16, nullptr) break;
+        default: MV_CENTER_CASE(MV_FP8_E4M3, d_row_scale) break;
+    }
+#undef MV_CENTER_CASE
+}
+
+static int center_args(const void *R, int64_t n, int64_t T, int64_t ldR, int out_dtype, int layout, void *d_L,
+                       int64_t ldL, float *d_row_scale, double *d_mu, double *d_trace) {
+    if (R == nullptr || d_L == nullptr || d_mu == nullptr || d_trace == nullptr) return MV_ERR_INVALID_ARG;
+    if (layout != MV_LAYOUT_NT && layout != MV_LAYOUT_TN) return MV_ERR_INVALID_ARG;
+    const bool tn = layout == MV_LAYOUT_TN;
+    if (n < 1 || T < 2 || ldR < T || ldL < (tn ? n : T) || n > (1LL << 31) - 1 || T > (1LL << 31) - 1)
+        return MV_ERR_INVALID_ARG;
+    if (dtype_size(out_dtype) == 0) return MV_ERR_INVALID_ARG;
+    if (out_dtype == MV_FP8_E4M3 && d_row_scale == nullptr) return MV_ERR_INVALID_ARG;
+    if (tn && (ldL + kTile - 1) / kTile > 65535) return MV_ERR_UNSUPPORTED;
+    return MV_OK;
+}
+
+// Chunked host-to-device pipeline of mv_center_factor_host.
+constexpr int64_t kHostChunkBytes = 64ll << 20;
+
+static int64_t host_chunk_rows(int64_t n, int64_t T) {
+    int64_t m = kHostChunkBytes / (T * 4);
+    m = m / kTile * kTile;
+    if (m < kTile) m = kTile;
+    return m < n ? m : n;
+}
+
 }  // namespace mv
 
 using namespace mv;
@@ -170,63 +229,90 @@ extern "C" {
 
 size_t mv_center_workspace_size(int64_t n, int64_t T) {
     (void)T;
-    return n > 0 ? align_up((size_t)n * 8 * kSlices, 256) : 0;
+    return n > 0 ? align_up((size_t)n * 8 * kMaxSlices, 256) : 0;
 }
 
 int mv_center_factor(const float *d_R, int64_t n, int64_t T, int64_t ldR, int out_dtype, int layout, void *d_L,
                      int64_t ldL, float *d_row_scale, double *d_mu, double *d_trace, void *d_ws, size_t ws_bytes,
                      mv_stream_t stream) {
-    if (d_R == nullptr || d_L == nullptr || d_mu == nullptr || d_trace == nullptr) return MV_ERR_INVALID_ARG;
-    if (layout != MV_LAYOUT_NT && layout != MV_LAYOUT_TN) return MV_ERR_INVALID_ARG;
-    const bool tn = layout == MV_LAYOUT_TN;
-    if (n < 1 || T < 2 || ldR < T || ldL < (tn ? n : T) || n > (1LL << 31) - 1 || T > (1LL << 31) - 1)
-        return MV_ERR_INVALID_ARG;
-    const int es = dtype_size(out_dtype);
-    if (es == 0) return MV_ERR_INVALID_ARG;
-    if (out_dtype == MV_FP8_E4M3 && d_row_scale == nullptr) return MV_ERR_INVALID_ARG;
+    MV_TRY(center_args(d_R, n, T, ldR, out_dtype, layout, d_L, ldL, d_row_scale, d_mu, d_trace));
     const size_t need = mv_center_workspace_size(n, T);
     if (d_ws == nullptr || ws_bytes < need || ((uintptr_t)d_ws) % 256 != 0) return MV_ERR_WORKSPACE;
     (void)cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
+    const bool tn = layout == MV_LAYOUT_TN;
     double *rowsq = reinterpret_cast<double *>(d_ws);
-    const dim3 tgrid((unsigned)kSlices, (unsigned)((ldL + kTile - 1) / kTile));
-    if (tn && tgrid.y > 65535u) return MV_ERR_UNSUPPORTED;
-    switch (out_dtype) {
-        case MV_F32:
-            if (tn) {
-                center_kernel<MV_F32, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
-                                                                                    nullptr, d_mu, rowsq);
-                transpose_center_kernel<MV_F32><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL, nullptr,
-                                                                            d_mu, rowsq);
-            } else {
-                center_kernel<MV_F32, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL, nullptr,
-                                                                                   d_mu, rowsq);
-            }
-            break;
-        case MV_BF16:
-            if (tn) {
-                center_kernel<MV_BF16, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
-                                                                                     nullptr, d_mu, rowsq);
-                transpose_center_kernel<MV_BF16><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL, nullptr,
-                                                                            d_mu, rowsq);
-            } else {
-                center_kernel<MV_BF16, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL,
-                                                                                    nullptr, d_mu, rowsq);
-            }
-            break;
-        default:
-            if (tn) {
-                center_kernel<MV_FP8_E4M3, false><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, nullptr, 0,
-                                                                                         d_row_scale, d_mu, rowsq);
-                transpose_center_kernel<MV_FP8_E4M3><<<tgrid, kTile * 8, 0, s>>>(d_R, ldR, n, (int)T, d_L, ldL,
-                                                                                 d_row_scale, d_mu, rowsq);
-            } else {
-                center_kernel<MV_FP8_E4M3, true><<<(unsigned)n, kCenterThreads, 0, s>>>(d_R, ldR, (int)T, d_L, ldL,
-                                                                                        d_row_scale, d_mu, rowsq);
-            }
-            break;
+    const int slices = center_slices(n, T);
+    center_chunk(d_R, ldR, n, T, out_dtype, tn, d_L, ldL, d_row_scale, d_mu, rowsq, 0, n, slices, s);
+    trace_kernel<<<1, kCenterThreads, 0, s>>>(rowsq, n, tn ? slices : 1, d_trace);
+    MV_CUDA_TRY(cudaGetLastError());
+    return MV_OK;
+}
+
+size_t mv_center_host_workspace_size(int64_t n, int64_t T) {
+    if (n < 1 || T < 2) return 0;
+    const int64_t m = host_chunk_rows(n, T);
+    return mv_center_workspace_size(n, T) + 2 * align_up((size_t)m * (size_t)T * 4, 256);
+}
+
+int mv_center_factor_host(const float *h_R, int64_t n, int64_t T, int64_t ldR, int out_dtype, int layout, void *d_L,
+                          int64_t ldL, float *d_row_scale, double *d_mu, double *d_trace, void *d_ws, size_t ws_bytes,
+                          mv_stream_t stream) {
+    MV_TRY(center_args(h_R, n, T, ldR, out_dtype, layout, d_L, ldL, d_row_scale, d_mu, d_trace));
+    const size_t need = mv_center_host_workspace_size(n, T);
+    if (d_ws == nullptr || ws_bytes < need || ((uintptr_t)d_ws) % 256 != 0) return MV_ERR_WORKSPACE;
+    (void)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool tn = layout == MV_LAYOUT_TN;
+    const int64_t m = host_chunk_rows(n, T);
+    const int slices = center_slices(m, T);
+    char *ws = reinterpret_cast<char *>(d_ws);
+    double *rowsq = reinterpret_cast<double *>(ws);
+    const size_t o_stage = mv_center_workspace_size(n, T), stage_bytes = align_up((size_t)m * (size_t)T * 4, 256);
+    float *stage[2] = {reinterpret_cast<float *>(ws + o_stage), reinterpret_cast<float *>(ws + o_stage + stage_bytes)};
+    // The copies run on a stream of their own, one chunk ahead of the kernels.
+    cudaStream_t cs;
+    MV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t copied[2], used[2], start;
+    for (int b = 0; b < 2; ++b) {
+        MV_CUDA_TRY(cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming));
+        MV_CUDA_TRY(cudaEventCreateWithFlags(&used[b], cudaEventDisableTiming));
     }
-    trace_kernel<<<1, kCenterThreads, 0, s>>>(rowsq, n, tn ? kSlices : 1, d_trace);
+    MV_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    MV_CUDA_TRY(cudaEventRecord(start, s));
+    MV_CUDA_TRY(cudaStreamWaitEvent(cs, start, 0));            // the copies follow earlier work on `stream`
+    int st = MV_OK;
+    int k = 0;
+    for (int64_t i0 = 0; i0 < n && st == MV_OK; i0 += m, ++k) {
+        const int64_t i1 = i0 + m < n ? i0 + m : n;
+        const int b = k & 1;
+        if (k >= 2 && cudaStreamWaitEvent(cs, used[b], 0) != cudaSuccess) st = MV_ERR_CUDA;
+        if (st == MV_OK &&
+            cudaMemcpy2DAsync(stage[b], (size_t)T * 4, h_R + i0 * ldR, (size_t)ldR * 4, (size_t)T * 4,
+                              (size_t)(i1 - i0), cudaMemcpyHostToDevice, cs) != cudaSuccess)
+            st = record_cuda_error(cudaGetLastError(), "cudaMemcpy2DAsync (host R chunk)", __FILE__, __LINE__);
+        if (st == MV_OK && cudaEventRecord(copied[b], cs) != cudaSuccess) st = MV_ERR_CUDA;
+        if (st == MV_OK && cudaStreamWaitEvent(s, copied[b], 0) != cudaSuccess) st = MV_ERR_CUDA;
+        if (st == MV_OK) {
+            center_chunk(stage[b], T, n, T, out_dtype, tn, d_L, ldL, d_row_scale, d_mu, rowsq, i0, i1, slices, s);
+            if (cudaEventRecord(used[b], s) != cudaSuccess) st = MV_ERR_CUDA;
+        }
+    }
+    if (st == MV_OK) trace_kernel<<<1, kCenterThreads, 0, s>>>(rowsq, n, tn ? slices : 1, d_trace);
+    // `stream` waits for every copy before the events and the copy stream go away.
+    cudaEvent_t fin;
+    if (cudaEventCreateWithFlags(&fin, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(fin, cs);
+        cudaStreamWaitEvent(s, fin, 0);
+        cudaEventDestroy(fin);
+    }
+    for (int b = 0; b < 2; ++b) {
+        cudaEventDestroy(copied[b]);
+        cudaEventDestroy(used[b]);
+    }
+    cudaEventDestroy(start);
+    cudaStreamDestroy(cs);
+    MV_TRY(st);
     MV_CUDA_TRY(cudaGetLastError());
     return MV_OK;
 }

@@ -34,7 +34,8 @@ EXPORTS = [
     "mv_solve_opts_default", "mv_npga_workspace_size", "mv_npga_solve", "mv_gradient", "mv_last_error",
     "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
     "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
-    "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch",
+    "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch", "mv_center_host_workspace_size",
+    "mv_center_factor_host",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -101,6 +102,10 @@ def lib():
         L.mv_center_workspace_size.argtypes = [i64, i64]
         L.mv_center_factor.restype = i32
         L.mv_center_factor.argtypes = [vp, i64, i64, i64, i32, i32, vp, i64, vp, vp, vp, vp, sz, vp]
+        L.mv_center_host_workspace_size.restype = sz
+        L.mv_center_host_workspace_size.argtypes = [i64, i64]
+        L.mv_center_factor_host.restype = i32
+        L.mv_center_factor_host.argtypes = [vp, i64, i64, i64, i32, i32, vp, i64, vp, vp, vp, vp, sz, vp]
         L.mv_project.restype = i32
         L.mv_project.argtypes = [vp, vp, vp, i64, i64, i32, vp, vp, vp]
         L.mv_solve_opts_default.restype = None
@@ -206,6 +211,30 @@ def center_factor(R: torch.Tensor, out_dtype: str = "f32", ld: int | None = None
     ws = _workspace(wsz, dev)
     _check(lib().mv_center_factor(_ptr(R), n, T, ldR, dt, lay, _ptr(L), ld, _ptr(rs), _ptr(mu), _ptr(tr),
                                   _ptr(ws), ws.numel(), _stream()), "mv_center_factor")
+    return L, rs, mu, tr
+
+
+def center_factor_host(R: torch.Tensor, out_dtype: str = "f32", ld: int | None = None, layout: str = "nt",
+                       device=None, ws: torch.Tensor | None = None):
+    """center_factor from an n x T FP32 panel in host memory (best pinned): the
+    upload and the centering overlap chunk by chunk (mv_center_factor_host).
+    ``ws`` may pass a reusable workspace of mv_center_host_workspace_size bytes."""
+    assert not R.is_cuda and R.dtype == torch.float32 and R.dim() == 2 and R.stride(1) == 1
+    dt = DTYPES[out_dtype]
+    lay = LAYOUTS[layout]
+    n, T = R.shape
+    inner, outer = (T, n) if lay == MV_LAYOUT_NT else (n, T)
+    ld = padded_ld(inner, dt) if ld is None else int(ld)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    L = torch.empty((outer, ld), dtype=_TORCH[dt], device=dev)
+    rs = torch.empty(n, dtype=torch.float32, device=dev) if dt == MV_FP8_E4M3 else None
+    mu = torch.empty(n, dtype=torch.float64, device=dev)
+    tr = torch.empty(1, dtype=torch.float64, device=dev)
+    wsz = lib().mv_center_host_workspace_size(n, T)
+    if ws is None or ws.numel() < wsz:
+        ws = _workspace(wsz, dev)
+    _check(lib().mv_center_factor_host(C.c_void_p(R.data_ptr()), n, T, R.stride(0), dt, lay, _ptr(L), ld, _ptr(rs),
+                                       _ptr(mu), _ptr(tr), _ptr(ws), ws.numel(), _stream()), "mv_center_factor_host")
     return L, rs, mu, tr
 
 
