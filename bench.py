@@ -542,14 +542,23 @@ def main():
             Rtb = float(torch.quantile(mub, 0.6).item())
             probs.append({"L": Lb_, "mu": mub, "R_target": Rtb, "T": bm.T})
         bsv = mv.BatchSolver(probs, eps=args.eps)
+
+        def timed_batch():
+            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            _, bi = bsv.solve()
+            b1.record(stream)
+            torch.cuda.synchronize()
+            return b0.elapsed_time(b1) / 1e3, bi
+
+        os.environ["MV_BATCH_AUTOTUNE"] = "0"            # the untuned default tiles, for comparison
         bsv.solve()
+        bt_default, _ = timed_batch()
+        del os.environ["MV_BATCH_AUTOTUNE"]
+        bsv.solve()                                      # the first tuned solve times the tile candidates
         torch.cuda.synchronize()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        _, binfos = bsv.solve()
-        b1.record(stream)
-        torch.cuda.synchronize()
-        bt = b0.elapsed_time(b1) / 1e3
+        bt, binfos = timed_batch()
+        t_rows, n_bytes, tuned = bsv.tiles()
         elems = sum(bm.n * bm.T for bm in models)
         iters = [i["iterations"] for i in binfos]
         # bytes streamed: 2 passes of every L per power iteration (50) and per NPGA iteration it ran
@@ -557,7 +566,9 @@ def main():
         batch = {"problems": len(models), "elements": elems, "value": bt, "unit": "s",
                  "problems_per_s": len(models) / bt, "all_converged": all(i["converged"] == 1 for i in binfos),
                  "iterations_min": min(iters), "iterations_max": max(iters),
-                 "aggregate_GBps": moved / bt / 1e9, "data": "synthetic, drawn on the GPU (torch seeded stream)"}
+                 "aggregate_GBps": moved / bt / 1e9, "data": "synthetic, drawn on the GPU (torch seeded stream)",
+                 "tiles": {"gemv_t_rows_per_split": t_rows, "gemv_n_bytes_per_split": n_bytes, "tuned": tuned},
+                 "default_tiles_s": bt_default}
         del probs, bsv
 
     cb = None

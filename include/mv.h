@@ -308,6 +308,15 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
  *  Workspace: mv_batch_workspace_size(probs, count).  Returns the first
  *  non-OK per-problem status (or MV_OK).  Blocking.
  * ------------------------------------------------------------------------ */
+/*  The grouped GEMVs' tiles (rows per split of the column-sum kernel, bytes of L
+ *  per row per split of the row-dot kernel) are tuned on the batch itself: the
+ *  first solve of a batch shape times nine candidates (256/512/1024 rows x
+ *  8/16/32 KB) on one pass each and keeps the fastest for that shape
+ *  (environment MV_BATCH_AUTOTUNE=0 keeps 512 rows x 16 KB).  The workspace
+ *  has room for every candidate.  mv_batch_tiles reports the tiles a shape
+ *  runs with: MV_OK once tuned, MV_ERR_NOT_CONVERGED (and the defaults)
+ *  before. */
+int mv_batch_tiles(const mv_problem *probs, int64_t count, int32_t *h_t_rows, int32_t *h_n_split_bytes);
 size_t mv_batch_workspace_size(const mv_problem *probs, int64_t count);
 int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_opts *opts,
                         double *const *h_x_dev, mv_solve_info *h_infos, void *d_ws, size_t ws_bytes,

@@ -74,7 +74,7 @@ static constexpr int kRW = 4;   // rows per warp in gemv_n
 // L (n x T) for MV_LAYOUT_NT, where z = L^T y is gemv_t and g = L z is
 // gemv_n; L^T (T x n) for MV_LAYOUT_TN, where the two swap roles.
 static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows = 0, bool fused = false,
-                      bool tn = false) {
+                      bool tn = false, int n_bytes = 16384) {
     Plan p{};
     p.dt = dt;
     p.esize = dtype_size(dt);
@@ -108,7 +108,7 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows
     // gemv_n: 32 rows per block, column splits of 16 KB of the matrix per row.
     const int rows_per_block = (kGemvThreads / kWarp) * kRW;
     p.n_groups = (int)((gr + rows_per_block - 1) / rows_per_block);
-    p.n_cols = 4096 * 4 / p.esize;                       // 16 KB per row per split
+    p.n_cols = n_bytes / p.esize;                        // 16 KB per row per split by default
     if (p.n_cols > gc) p.n_cols = (int)((gc + 32 * p.vec - 1) / (32 * p.vec) * (32 * p.vec));
     p.n_splits = (int)((gc + p.n_cols - 1) / p.n_cols);
     size_t off = 0;
@@ -1896,7 +1896,16 @@ static int batch_attrs() {
     return st;
 }
 
-constexpr int kBatchRowsPerSplit = 512;
+// Tiles of the grouped GEMVs: rows per split of gemv_t, bytes of L per row
+// per split of gemv_n.  The solve times every candidate on the batch itself
+// the first time it sees a batch shape and keeps the fastest (the choice is
+// cached per shape signature; MV_BATCH_AUTOTUNE=0 keeps the default).
+struct BatchTiles {
+    int t_rows, n_bytes;
+};
+constexpr BatchTiles kBatchDefault = {512, 16384};
+constexpr BatchTiles kBatchCandidates[] = {{256, 8192}, {256, 16384}, {256, 32768}, {512, 8192}, {512, 16384},
+                                           {512, 32768}, {1024, 8192}, {1024, 16384}, {1024, 32768}};
 
 struct BatchLayout {
     std::vector<Plan> plans;
@@ -1906,7 +1915,7 @@ struct BatchLayout {
     size_t total;
 };
 
-static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo) {
+static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo, BatchTiles tiles = kBatchDefault) {
     Lo->plans.clear();
     Lo->base.clear();
     int64_t ntt = 0, nnt = 0;
@@ -1915,7 +1924,8 @@ static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo)
         MV_TRY(validate_problem(probs + i));
         MV_TRY(require_nt(probs + i, "batch solve"));
         if (probs[i].dtype != probs[0].dtype) return record_message(MV_ERR_INVALID_ARG, "batch: mixed dtypes");
-        Plan p = make_plan(probs[i].dtype, probs[i].n, probs[i].T, probs[i].ld, kBatchRowsPerSplit);
+        Plan p = make_plan(probs[i].dtype, probs[i].n, probs[i].T, probs[i].ld, tiles.t_rows, false, false,
+                           tiles.n_bytes);
         ntt += (int64_t)p.t_blocks * p.t_splits;
         nnt += (int64_t)p.n_groups * p.n_splits;
         max_n = std::max(max_n, p.n);
@@ -1972,35 +1982,11 @@ static cudaError_t batch_step(const BatchLayout &Lo, void *ws, int count, cudaSt
     }
 }
 
-}  // namespace mv
-
-extern "C" {
-
-size_t mv_batch_workspace_size(const mv_problem *probs, int64_t count) {
-    if (probs == nullptr || count < 1 || count > 65535) return 0;
-    BatchLayout Lo;
-    if (batch_layout(probs, count, &Lo) != MV_OK) return 0;
-    return Lo.total;
-}
-
-int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_opts *O_in, double *const *h_x_dev,
-                        mv_solve_info *h_infos, void *d_ws, size_t ws_bytes, mv_stream_t stream) {
-    if (probs == nullptr || h_x_dev == nullptr || h_infos == nullptr || count < 1 || count > 65535)
-        return MV_ERR_INVALID_ARG;
-    mv_solve_opts O;
-    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
-    if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
-    if (O.power_iters == 0 && !(O.alpha > 0.0)) return MV_ERR_INVALID_ARG;
-    BatchLayout Lo;
-    MV_TRY(batch_layout(probs, count, &Lo));
-    MV_TRY(check_ws(d_ws, ws_bytes, Lo.total));
-    MV_TRY(set_kernel_attrs());
-    MV_TRY(batch_attrs());
-    (void)cudaGetLastError();
-    cudaStream_t s = (cudaStream_t)stream;
-    void *ws = d_ws;
-    const int cnt = (int)count, dt = probs[0].dtype;
-    // descriptors
+// Writes every problem's GEMV, step and set-up descriptors and the tile
+// lists of layout Lo into the workspace (blocking: the host copies are freed).
+static int batch_setup(const BatchLayout &Lo, const mv_problem *probs, int64_t count, const mv_solve_opts &O, void *ws,
+                       cudaStream_t s) {
+    const int cnt = (int)count;
     std::vector<GemvProb> gp(cnt), gpa(cnt);
     std::vector<StepArgs> sa(cnt);
     std::vector<GOne> one(cnt);
@@ -2089,6 +2075,131 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
     MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tt), tt.data(), sizeof(int4) * tt.size(), cudaMemcpyHostToDevice, s));
     MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tn), tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, s));
     MV_CUDA_TRY(cudaStreamSynchronize(s));   // host descriptor buffers may now be released
+    return MV_OK;
+}
+
+// Times the grouped GEMV pair of every tile candidate on this batch (one
+// warm pass, then two timed) and returns the fastest; cached per batch shape.
+static uint64_t batch_key(const mv_problem *probs, int64_t count) {
+    uint64_t key = 1469598103934665603ull;                // FNV-1a over the batch shape
+    auto mix = [&](uint64_t v) { key = (key ^ v) * 1099511628211ull; };
+    mix((uint64_t)probs[0].dtype);
+    mix((uint64_t)count);
+    for (int64_t i = 0; i < count; ++i) {
+        mix((uint64_t)probs[i].n);
+        mix((uint64_t)probs[i].T);
+        mix((uint64_t)probs[i].ld);
+    }
+    return key;
+}
+static std::mutex g_tiles_mu;
+static std::unordered_map<uint64_t, BatchTiles> g_tiles;
+
+// The tiles a batch of this shape runs with: MV_OK and the tuned choice, or
+// MV_ERR_NOT_CONVERGED and the defaults if it has not been tuned yet.
+static int batch_tune_lookup(const mv_problem *probs, int64_t count, BatchTiles *out) {
+    std::lock_guard<std::mutex> lock(g_tiles_mu);
+    auto it = g_tiles.find(batch_key(probs, count));
+    if (it == g_tiles.end()) {
+        *out = kBatchDefault;
+        return MV_ERR_NOT_CONVERGED;
+    }
+    *out = it->second;
+    return MV_OK;
+}
+
+static int batch_tune(const mv_problem *probs, int64_t count, const mv_solve_opts &O, void *ws, size_t ws_bytes,
+                      cudaStream_t s, BatchTiles *out) {
+    *out = kBatchDefault;
+    if (const char *env = getenv("MV_BATCH_AUTOTUNE"))
+        if (atoi(env) == 0) return MV_OK;
+    if (batch_tune_lookup(probs, count, out) == MV_OK) return MV_OK;
+    const uint64_t key = batch_key(probs, count);
+    cudaEvent_t e0, e1;
+    MV_CUDA_TRY(cudaEventCreate(&e0));
+    MV_CUDA_TRY(cudaEventCreate(&e1));
+    float best = INFINITY;
+    BatchTiles best_t = kBatchDefault;
+    int st = MV_OK;
+    for (const BatchTiles &c : kBatchCandidates) {
+        BatchLayout Lo;
+        st = batch_layout(probs, count, &Lo, c);
+        if (st != MV_OK) break;
+        if (Lo.total > ws_bytes) continue;
+        st = batch_setup(Lo, probs, count, O, ws, s);
+        if (st != MV_OK) break;
+        setup_grouped<<<(int)count, kStepThreads, 0, s>>>(at<GOne>(ws, Lo.o_one));
+        batch_gemv_any(probs[0].dtype, Lo, ws, true, true, s);
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 2; ++r) batch_gemv_any(probs[0].dtype, Lo, ws, true, true, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            st = record_cuda_error(cudaGetLastError(), "batch tile tuning", __FILE__, __LINE__);
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_t = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    MV_TRY(st);
+    *out = best_t;
+    std::lock_guard<std::mutex> lock(g_tiles_mu);
+    g_tiles[key] = best_t;
+    return MV_OK;
+}
+
+}  // namespace mv
+
+extern "C" {
+
+size_t mv_batch_workspace_size(const mv_problem *probs, int64_t count) {
+    if (probs == nullptr || count < 1 || count > 65535) return 0;
+    size_t total = 0;                              // room for every tile candidate of the tuning
+    for (const BatchTiles &c : kBatchCandidates) {
+        BatchLayout Lo;
+        if (batch_layout(probs, count, &Lo, c) != MV_OK) return 0;
+        total = std::max(total, Lo.total);
+    }
+    return total;
+}
+
+int mv_batch_tiles(const mv_problem *probs, int64_t count, int32_t *h_t_rows, int32_t *h_n_split_bytes) {
+    if (probs == nullptr || h_t_rows == nullptr || h_n_split_bytes == nullptr || count < 1 || count > 65535)
+        return MV_ERR_INVALID_ARG;
+    BatchTiles t = kBatchDefault;
+    const int st = batch_tune_lookup(probs, count, &t);
+    *h_t_rows = t.t_rows;
+    *h_n_split_bytes = t.n_bytes;
+    return st;
+}
+
+int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_opts *O_in, double *const *h_x_dev,
+                        mv_solve_info *h_infos, void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    if (probs == nullptr || h_x_dev == nullptr || h_infos == nullptr || count < 1 || count > 65535)
+        return MV_ERR_INVALID_ARG;
+    mv_solve_opts O;
+    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
+    if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
+    if (O.power_iters == 0 && !(O.alpha > 0.0)) return MV_ERR_INVALID_ARG;
+    BatchLayout Lo;
+    MV_TRY(batch_layout(probs, count, &Lo));
+    MV_TRY(check_ws(d_ws, ws_bytes, Lo.total));
+    MV_TRY(set_kernel_attrs());
+    MV_TRY(batch_attrs());
+    (void)cudaGetLastError();
+    cudaStream_t s = (cudaStream_t)stream;
+    void *ws = d_ws;
+    BatchTiles tiles;
+    MV_TRY(batch_tune(probs, count, O, ws, ws_bytes, s, &tiles));
+    MV_TRY(batch_layout(probs, count, &Lo, tiles));
+    MV_TRY(check_ws(d_ws, ws_bytes, Lo.total));
+    const int cnt = (int)count, dt = probs[0].dtype;
+    MV_TRY(batch_setup(Lo, probs, count, O, ws, s));
 
     const GOne *d_one = at<GOne>(ws, Lo.o_one);
     int launches = 0;

@@ -35,7 +35,7 @@ EXPORTS = [
     "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
     "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
     "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch", "mv_center_host_workspace_size",
-    "mv_center_factor_host",
+    "mv_center_factor_host", "mv_batch_tiles",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -102,6 +102,8 @@ def lib():
         L.mv_center_workspace_size.argtypes = [i64, i64]
         L.mv_center_factor.restype = i32
         L.mv_center_factor.argtypes = [vp, i64, i64, i64, i32, i32, vp, i64, vp, vp, vp, vp, sz, vp]
+        L.mv_batch_tiles.restype = i32
+        L.mv_batch_tiles.argtypes = [C.POINTER(Problem), i64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.mv_center_host_workspace_size.restype = sz
         L.mv_center_host_workspace_size.argtypes = [i64, i64]
         L.mv_center_factor_host.restype = i32
@@ -515,3 +517,10 @@ class BatchSolver:
                                        self.ws.numel(), _stream())
         _check(st, "mv_npga_solve_batch", allow)
         return self.xs, [i.as_dict() for i in infos]
+
+    def tiles(self):
+        """(rows per split, bytes per split, tuned?) of this batch shape's grouped GEMVs."""
+        a, b = C.c_int32(), C.c_int32()
+        st = lib().mv_batch_tiles(self.probs, self.count, C.byref(a), C.byref(b))
+        _check(st, "mv_batch_tiles", (MV_ERR_NOT_CONVERGED,))
+        return a.value, b.value, st == MV_OK

@@ -86,3 +86,23 @@ def test_batch_uneven_config_sample(mv):
         x = xs[j].cpu().numpy()
         assert kkt_residual(L_o, g, mu_o, Rt, x, infos[j]["alpha"]) <= 1.05e-6
         assert x.min() >= 0 and abs(x.sum() - 1) < 1e-12 and mu_o @ x >= Rt - 1e-15
+
+
+def test_batch_tiles_tuned_and_equivalent(mv):
+    """The first solve of a batch shape tunes the grouped GEMV tiles; every
+    candidate gives the same answer up to FP32 summation order."""
+    models = [CFG_SMALL.scaled(n, T, seed=970 + j) for j, (n, T) in enumerate([(300, 2500), (700, 1200), (90, 4000)])]
+    probs, host = make(mv, models)
+    bs = mv.BatchSolver(probs, eps=1e-7)
+    t_rows, n_bytes, tuned = bs.tiles()
+    assert not tuned and (t_rows, n_bytes) == (512, 16384)
+    xs, infos = bs.solve()
+    t_rows, n_bytes, tuned = bs.tiles()
+    assert tuned and t_rows in (256, 512, 1024) and n_bytes in (8192, 16384, 32768)
+    xs = [x.clone() for x in xs]
+    xs2, _ = bs.solve()                                  # cached choice, same bits
+    assert all(torch.equal(a, b) for a, b in zip(xs, xs2))
+    for x, info, (L_o, mu_o, Rt, g) in zip(xs, infos, host):
+        assert info["converged"] == 1
+        ref = oracle_opt(L_o, mu_o, Rt, g)
+        assert np.max(np.abs(x.cpu().numpy() - ref.x)) <= 1e-4
