@@ -473,16 +473,17 @@ def main():
     if not args.no_frontier and args.dtype == "f32":
         from synth import CFG_SMALL
         frontier = {}
-        for tag, fm in (("200x1000", CFG_SMALL), ("full_shape", model)):
+        for tag, fm, fdt in (("200x1000", CFG_SMALL, "bf16"), ("full_shape", model, "bf16"),
+                             ("200x1000_fp8", CFG_SMALL, "fp8"), ("full_shape_fp8", model, "fp8")):
             Rf = factor_returns(fm, np.float32) if fm is not model else R32
             Rfd = torch.from_numpy(Rf).to(dev)
-            Lfb, _, muf, _ = mv.center_factor(Rfd, "bf16")
+            Lfb, rsf, muf, _ = mv.center_factor(Rfd, fdt)
             muh = muf.cpu().numpy()
             targets = np.linspace(np.percentile(muh, 10), np.percentile(muh, 90), 64)
-            fsv = mv.FrontierSolver(Lfb, muf, targets, fm.T, eps=args.eps)
+            fsv = mv.FrontierSolver(Lfb, muf, targets, fm.T, eps=args.eps, dtype=fdt, row_scale=rsf)
             fsv.solve()
             torch.cuda.synchronize()
-            reps = 3 if tag == "full_shape" else 5
+            reps = 3 if tag.startswith("full_shape") else 5
             f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             f0.record(stream)
             for _ in range(reps):
@@ -491,7 +492,7 @@ def main():
             torch.cuda.synchronize()
             entry = {"targets": 64, "value": f0.elapsed_time(f1) / reps / 1e3, "unit": "s",
                      "max_iterations": max(i["iterations"] for i in finfo),
-                     "all_converged": all(i["converged"] == 1 for i in finfo), "dtype": "bf16"}
+                     "all_converged": all(i["converged"] == 1 for i in finfo), "dtype": fdt}
             if tag == "200x1000":
                 # the same 64 targets as independent FP32 solves, one after another
                 Lf32, _, _, _ = mv.center_factor(Rfd, "f32")
@@ -502,7 +503,7 @@ def main():
                 entry["fp32_sequential_64_solves_s"] = time.perf_counter() - t0
                 del Lf32
             frontier[tag] = entry
-            del Rfd, Lfb, fsv
+            del Rfd, Lfb, rsf, fsv
 
     # Adjoint of 500 unrolled iterations at 2000 x 10000 (checkpoints every 50).
     adj = None

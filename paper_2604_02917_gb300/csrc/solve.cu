@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "gemm.cuh"
+#include "gemm_q8.cuh"
 #include "gemv.cuh"
 #include "llt_api.h"
 #include "project.cuh"
@@ -983,7 +984,10 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
-// Efficient frontier: B targets R_b share one factor L (BF16).  The two
+// Efficient frontier: B targets R_b share one factor L (BF16, or FP8 e4m3
+// with row scales s: then the GEMMs read FP8 tiles expanded to BF16 in
+// shared memory (gemm_q8.cuh), s multiplies the split Y operand, since
+// L^T Y = L_q^T (s o Y), and the rows of G, since L Z = s o (L_q Z)).  The two
 // half-products of all B gradients become skinny tensor-core GEMMs:
 //   Z (T x B) = L^T Y,   G (n x B) = L Z,
 // run on tcgen05 (gemm.cuh) with the n x B and T x B operands carried as a
@@ -1008,13 +1012,15 @@ struct FArgs {
     double *X, *Y, *GX;         // B x n (row b = target b)
     __nv_bfloat16 *Ysplit;      // 2B x ldY: BF16 hi rows 0..B-1, lo rows B..2B-1
     int64_t ldY;
+    const float *row_scale;     // FP8 factor: n scales (else null)
     const double *mu, *Rt;
     int n, mode, kkt_every, max_iter;
     double gamma, eps;
 };
 
-__device__ __forceinline__ void write_split(__nv_bfloat16 *Ys, int64_t ldY, int B, int b, int i, double y) {
-    const float yf = (float)y;
+__device__ __forceinline__ void write_split(__nv_bfloat16 *Ys, int64_t ldY, int B, int b, int i, double y,
+                                            const float *rs = nullptr) {
+    const float yf = (float)(rs != nullptr ? y * (double)rs[i] : y);
     const __nv_bfloat16 hi = __float2bfloat16_rn(yf);
     Ys[(int64_t)b * ldY + i] = hi;
     Ys[(int64_t)(B + b) * ldY + i] = __float2bfloat16_rn(yf - __bfloat162float(hi));
@@ -1043,7 +1049,7 @@ __global__ void __launch_bounds__(kProjNT) frontier_init_kernel(FArgs a) {
         const double xi = bad ? 0.0 : fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
         a.X[(int64_t)b * n + gi] = xi;
         a.Y[(int64_t)b * n + gi] = xi;
-        write_split(a.Ysplit, a.ldY, a.B, b, gi, xi);
+        write_split(a.Ysplit, a.ldY, a.B, b, gi, xi, a.row_scale);
     }
     if (rank == 0 && threadIdx.x == 0) {
         FState f{};
@@ -1087,7 +1093,8 @@ __global__ void __launch_bounds__(kProjNT) frontier_step_kernel(FArgs a) {
     for (int i = threadIdx.x; i < el.n; i += kProjNT) {
         const int gi = r0 + i;
         el.mu[i] = a.mu[gi];
-        const double gyi = (double)a.G[(int64_t)gi * a.ldG + b] + (double)a.G[(int64_t)gi * a.ldG + a.B + b];
+        const double gyi = ((double)a.G[(int64_t)gi * a.ldG + b] + (double)a.G[(int64_t)gi * a.ldG + a.B + b]) *
+                           (a.row_scale != nullptr ? (double)a.row_scale[gi] : 1.0);
         const double gxi = (k == 0) ? gyi : (gyi + beta_prev * GXb[gi]) * inv1pb;
         GXb[gi] = gxi;
         if (check) {
@@ -1129,7 +1136,8 @@ __global__ void __launch_bounds__(kProjNT) frontier_step_kernel(FArgs a) {
     }
     for (int i = threadIdx.x; i < el.n; i += kProjNT) {
         const int gi = r0 + i;
-        const double gyi = (double)a.G[(int64_t)gi * a.ldG + b] + (double)a.G[(int64_t)gi * a.ldG + a.B + b];
+        const double gyi = ((double)a.G[(int64_t)gi * a.ldG + b] + (double)a.G[(int64_t)gi * a.ldG + a.B + b]) *
+                           (a.row_scale != nullptr ? (double)a.row_scale[gi] : 1.0);
         const double yi = Yb[gi];
         el.v[i] = yi - alpha * (2.0 * gyi + 2.0 * gamma * yi);
     }
@@ -1143,7 +1151,7 @@ __global__ void __launch_bounds__(kProjNT) frontier_step_kernel(FArgs a) {
         const double yn = xn + beta * (xn - xo);
         Xb[gi] = xn;
         Yb[gi] = yn;
-        write_split(a.Ysplit, a.ldY, a.B, b, gi, yn);
+        write_split(a.Ysplit, a.ldY, a.B, b, gi, yn, a.row_scale);
     }
     if (rank == 0 && threadIdx.x == 0) {
         fs->t = tn;
@@ -1162,13 +1170,14 @@ __global__ void __launch_bounds__(kProjNT) frontier_step_kernel(FArgs a) {
 }
 
 // L (n x T, ld ldL) -> L^T (T x n, ld ldT), BF16, 32x32 tiles through shared memory.
-__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ L, int n, int T, int64_t ldL,
-                                      __nv_bfloat16 *__restrict__ Lt, int64_t ldT) {
-    __shared__ __nv_bfloat16 tile[32][33];
+template <typename E>
+__global__ void transpose_elem_kernel(const E *__restrict__ L, int n, int T, int64_t ldL, E *__restrict__ Lt,
+                                      int64_t ldT) {
+    __shared__ E tile[32][33];
     const int t0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int i = i0 + r, t = t0 + threadIdx.x;
-        tile[r][threadIdx.x] = (i < n && t < T) ? L[(int64_t)i * ldL + t] : __float2bfloat16(0.f);
+        tile[r][threadIdx.x] = (i < n && t < T) ? L[(int64_t)i * ldL + t] : E{};
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -1179,11 +1188,11 @@ __global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ L, int n
 
 // Rows of X (B x n, FP64) -> the BF16 hi/lo operand rows (2B x ldY).
 __global__ void split_rows_kernel(const double *__restrict__ X, int B, int n, __nv_bfloat16 *__restrict__ Ys,
-                                  int64_t ldY) {
+                                  int64_t ldY, const float *__restrict__ rs) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (int64_t)B * n) return;
     const int b = (int)(idx / n), i = (int)(idx - (int64_t)b * n);
-    write_split(Ys, ldY, B, b, i, X[idx]);
+    write_split(Ys, ldY, B, b, i, X[idx], rs);
 }
 
 // f_b = ||L^T x_b||^2 + gamma ||x_b||^2 from Z = L^T X carried as BF16 hi + lo rows.
@@ -1247,6 +1256,9 @@ static int frontier_attrs() {
         ok = ok && gemm_set_attrs<64, kEpiF32>() == MV_OK && gemm_set_attrs<128, kEpiF32>() == MV_OK &&
              gemm_set_attrs<256, kEpiF32>() == MV_OK && gemm_set_attrs<64, kEpiPairSplitT>() == MV_OK &&
              gemm_set_attrs<128, kEpiPairSplitT>() == MV_OK && gemm_set_attrs<256, kEpiPairSplitT>() == MV_OK;
+        ok = ok && gemm_q8_set_attrs<64, kEpiF32>() == MV_OK && gemm_q8_set_attrs<128, kEpiF32>() == MV_OK &&
+             gemm_q8_set_attrs<256, kEpiF32>() == MV_OK && gemm_q8_set_attrs<64, kEpiPairSplitT>() == MV_OK &&
+             gemm_q8_set_attrs<128, kEpiPairSplitT>() == MV_OK && gemm_q8_set_attrs<256, kEpiPairSplitT>() == MV_OK;
         if (!ok) st = record_cuda_error(cudaGetLastError(), "frontier kernel attributes", __FILE__, __LINE__);
     });
     return st;
@@ -1263,7 +1275,7 @@ static FPlan make_fplan(const Plan &p, int64_t nb) {
     FPlan f{};
     f.B = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
     f.BN = 2 * f.B;
-    f.ldLt = (p.n + 7) / 8 * 8;
+    f.ldLt = (p.n + 15) / 16 * 16;                    // row pitch a multiple of 16 bytes for BF16 and FP8
     f.ldY = f.ldLt;
     f.ldZ = ((int64_t)p.T + 7) / 8 * 8;
     size_t off = p.total;
@@ -1272,7 +1284,7 @@ static FPlan make_fplan(const Plan &p, int64_t nb) {
         off = align_up(off + bytes, 256);
         return o;
     };
-    f.o_lt = take(2 * (size_t)p.T * f.ldLt);
+    f.o_lt = take((size_t)p.esize * p.T * f.ldLt);
     f.o_y = take(2 * (size_t)f.BN * f.ldY);
     f.o_z = take(2 * (size_t)f.BN * f.ldZ);
     f.o_g = take(4 * (size_t)p.n * f.BN);
@@ -1288,6 +1300,12 @@ static FPlan make_fplan(const Plan &p, int64_t nb) {
 template <int BN>
 static void frontier_gemms(const CUtensorMap &tLt, const CUtensorMap &tY, const CUtensorMap &tL, const CUtensorMap &tZ,
                            const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
+    if (p.dt == MV_FP8_E4M3) {
+        gemm_q8_launch<BN, kEpiPairSplitT>(tLt, tY, p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(ws, f.o_z), f.ldZ,
+                                           s);
+        gemm_q8_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s);
+        return;
+    }
     gemm_launch<BN, kEpiPairSplitT>(tLt, tY, p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(ws, f.o_z), f.ldZ, s);
     gemm_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s);
 }
@@ -1298,12 +1316,27 @@ static void frontier_gemm_pair(const CUtensorMap *maps, const Plan &p, const FPl
     else frontier_gemms<256>(maps[0], maps[1], maps[2], maps[3], p, f, ws, s);
 }
 
+// L^T X for the objectives, X already written as the split operand.
+static void frontier_ltx(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
+    __nv_bfloat16 *Zt = at<__nv_bfloat16>(ws, f.o_z);
+    if (p.dt == MV_FP8_E4M3) {
+        if (f.BN == 64) gemm_q8_launch<64, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
+        else if (f.BN == 128)
+            gemm_q8_launch<128, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
+        else gemm_q8_launch<256, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
+        return;
+    }
+    if (f.BN == 64) gemm_launch<64, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
+    else if (f.BN == 128) gemm_launch<128, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
+    else gemm_launch<256, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
+}
+
 }  // namespace mv
 
 extern "C" {
 
 size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets) {
-    if (validate_problem(P) != MV_OK || is_tn(P) || P->dtype != MV_BF16 || n_targets < 1 || n_targets > 128) return 0;
+    if (validate_problem(P) != MV_OK || is_tn(P) || P->dtype == MV_F32 || n_targets < 1 || n_targets > 128) return 0;
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
     return make_fplan(p, n_targets).total;
 }
@@ -1313,7 +1346,8 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
                            mv_stream_t stream) {
     MV_TRY(validate_problem(P));
     MV_TRY(require_nt(P, "frontier solve"));
-    if (P->dtype != MV_BF16) return record_message(MV_ERR_UNSUPPORTED, "frontier solve: L must be BF16");
+    if (P->dtype == MV_F32)
+        return record_message(MV_ERR_UNSUPPORTED, "frontier solve: L must be BF16 or FP8 (the tensor-core operand)");
     if (d_R_targets == nullptr || d_X == nullptr || h_infos == nullptr || n_targets < 1 || n_targets > 128)
         return MV_ERR_INVALID_ARG;
     mv_solve_opts O;
@@ -1339,16 +1373,22 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     // Shared step size from the power method on L (the single-problem GEMV path).
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
-    setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, nullptr, y32, p.n);
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
     for (int it = 0; it < O.power_iters; ++it) {
         gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
-        power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), nullptr, y32, p.n);
+        power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
     }
     if (O.power_iters > 0) gemv_t_only(p, P, y32, d_ws, s);
     step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0 || O.power_iters == 0) ? 0 : p.T,
                                                 P->gamma, O.power_safety, O.alpha);
-    transpose_bf16_kernel<<<dim3((unsigned)((p.T + 31) / 32), (unsigned)((p.n + 31) / 32)), dim3(32, 8), 0, s>>>(
-        reinterpret_cast<const __nv_bfloat16 *>(P->L), p.n, p.T, P->ld, at<__nv_bfloat16>(d_ws, f.o_lt), f.ldLt);
+    const dim3 tgrid((unsigned)((p.T + 31) / 32), (unsigned)((p.n + 31) / 32));
+    if (P->dtype == MV_FP8_E4M3)
+        transpose_elem_kernel<uint8_t><<<tgrid, dim3(32, 8), 0, s>>>(
+            reinterpret_cast<const uint8_t *>(P->L), p.n, p.T, P->ld, at<uint8_t>(d_ws, f.o_lt), f.ldLt);
+    else
+        transpose_elem_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, s>>>(
+            reinterpret_cast<const __nv_bfloat16 *>(P->L), p.n, p.T, P->ld, at<__nv_bfloat16>(d_ws, f.o_lt), f.ldLt);
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_y), 0, 2 * (size_t)f.BN * f.ldY, s));
     MV_CUDA_TRY(cudaGetLastError());
 
@@ -1363,6 +1403,7 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     a.GX = at<double>(d_ws, f.o_gx);
     a.Ysplit = at<__nv_bfloat16>(d_ws, f.o_y);
     a.ldY = f.ldY;
+    a.row_scale = rs;
     a.mu = P->mu;
     a.Rt = Rt;
     a.n = p.n;
@@ -1374,9 +1415,14 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     MV_CUDA_TRY(launch_frontier(true, p.cl, a, s));
 
     CUtensorMap maps[4];
-    MV_TRY(make_map_bf16(&maps[0], at<void>(d_ws, f.o_lt), p.T, p.n, f.ldLt, kBM));
+    if (P->dtype == MV_FP8_E4M3) {
+        MV_TRY(make_map_u8(&maps[0], at<void>(d_ws, f.o_lt), p.T, p.n, f.ldLt, kBM));
+        MV_TRY(make_map_u8(&maps[2], P->L, p.n, p.T, P->ld, kBM));
+    } else {
+        MV_TRY(make_map_bf16(&maps[0], at<void>(d_ws, f.o_lt), p.T, p.n, f.ldLt, kBM));
+        MV_TRY(make_map_bf16(&maps[2], P->L, p.n, p.T, P->ld, kBM));
+    }
     MV_TRY(make_map_bf16(&maps[1], at<void>(d_ws, f.o_y), f.BN, p.n, f.ldY, f.BN));
-    MV_TRY(make_map_bf16(&maps[2], P->L, p.n, p.T, P->ld, kBM));
     MV_TRY(make_map_bf16(&maps[3], at<void>(d_ws, f.o_z), f.BN, p.T, f.ldZ, f.BN));
     int zero = 0;
     MV_CUDA_TRY(cudaMemcpyToSymbolAsync(g_gemm_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
@@ -1421,16 +1467,8 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     }
     if (exec) cudaGraphExecDestroy(exec);
     // Objectives: one more L^T X product with X written as the split operand.
-    split_rows_kernel<<<(unsigned)((B * (int64_t)p.n + 255) / 256), 256, 0, s>>>(a.X, B, p.n, a.Ysplit, f.ldY);
-    if (f.BN == 64)
-        gemm_launch<64, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(d_ws, f.o_z),
-                                        f.ldZ, s);
-    else if (f.BN == 128)
-        gemm_launch<128, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(d_ws, f.o_z),
-                                         f.ldZ, s);
-    else
-        gemm_launch<256, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(d_ws, f.o_z),
-                                         f.ldZ, s);
+    split_rows_kernel<<<(unsigned)((B * (int64_t)p.n + 255) / 256), 256, 0, s>>>(a.X, B, p.n, a.Ysplit, f.ldY, rs);
+    frontier_ltx(maps, p, f, d_ws, s);
     frontier_objective_kernel<<<B, kStepThreads, 0, s>>>(at<__nv_bfloat16>(d_ws, f.o_z), f.ldZ, B, p.T, a.X, p.n,
                                                          P->gamma, a.fs);
     launches += 3;

@@ -424,13 +424,14 @@ def str_truncate(L_sketch: torch.Tensor, k: int, gamma: float = -1.0, trace_sigm
 
 
 class FrontierSolver:
-    """Batched NPGA over many targets sharing one BF16 factor
-    (mv_npga_solve_frontier); reuses the workspace across calls."""
+    """Batched NPGA over many targets sharing one BF16 factor, or an FP8 factor
+    with its row scales (mv_npga_solve_frontier); reuses the workspace."""
 
-    def __init__(self, L_bf16, mu, R_targets, T, gamma=0.0, mode="ge", power_start=None, **opts):
+    def __init__(self, L_bf16, mu, R_targets, T, gamma=0.0, mode="ge", power_start=None, dtype="bf16",
+                 row_scale=None, **opts):
         self.Rt = torch.as_tensor(R_targets, dtype=torch.float64).reshape(-1).to(L_bf16.device)
-        self._keep = (L_bf16, mu, power_start)
-        self.problem = make_problem(L_bf16, mu, 0.0, T, gamma, "bf16", None, mode, power_start)
+        self._keep = (L_bf16, mu, power_start, row_scale)
+        self.problem = make_problem(L_bf16, mu, 0.0, T, gamma, dtype, row_scale, mode, power_start)
         self.opts = solve_opts(**opts)
         self.nt = self.Rt.numel()
         nb = lib().mv_frontier_workspace_size(C.byref(self.problem), self.nt)

@@ -52,3 +52,27 @@ def test_frontier_parity(mv, model, nt):
     active = [b for b in range(nt) if abs(mu_o @ X[b] - targets[b]) < 1e-12]
     fa = f[active]
     assert np.all(np.diff(fa) >= -1e-12 * fa.max())
+
+
+@pytest.mark.parametrize("model,nt", [(CFG_SMALL, 64), (CFG_FULL.scaled(700, 3001, seed=62), 7)])
+def test_frontier_fp8_parity(mv, model, nt):
+    """FP8 e4m3 factor with row scales: FP8 tiles expanded to BF16 in shared
+    memory before the tcgen05 MMA; parity against the oracle on the FP8 model."""
+    R = factor_returns(model, np.float32)
+    Lq, rs, mu, _ = mv.center_factor(torch.from_numpy(R).cuda(), "fp8")
+    mu_o = center_factor(R.astype(np.float64))[0]
+    targets = np.linspace(np.percentile(mu_o, 10), np.percentile(mu_o, 90), nt)
+    fs = mv.FrontierSolver(Lq, mu, targets, model.T, eps=1e-7, dtype="fp8", row_scale=rs)
+    X, infos = fs.solve()
+    X = X.cpu().numpy()
+    assert all(i["converged"] == 1 for i in infos)
+    q = Lq[:, :model.T].cpu().view(torch.float8_e4m3fn).float().double().numpy()
+    L8 = q * rs.double().cpu().numpy()[:, None]                 # the FP8 model the GPU holds
+    f = np.array([objective(L8, 0.0, X[b]) for b in range(nt)])
+    for b in range(nt):
+        assert X[b].min() >= 0 and abs(X[b].sum() - 1) < 1e-12 and mu_o @ X[b] >= targets[b] - 1e-15
+        assert infos[b]["objective"] == pytest.approx(f[b], rel=1e-4)
+    for b in (range(nt) if nt <= 8 else range(0, nt, 9)):
+        ref = oracle_opt(L8, mu_o, targets[b])
+        assert np.max(np.abs(X[b] - ref.x)) <= 1e-4
+        assert (f[b] - ref.f) / ref.f <= 1e-5
