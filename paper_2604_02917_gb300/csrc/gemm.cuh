@@ -21,6 +21,8 @@
 
 #include <stdio.h>
 
+#include <algorithm>
+
 #include <cudaTypedefs.h>
 
 #include "umma.cuh"
@@ -44,11 +46,78 @@ struct GemmCfg {
 
 constexpr int kEpiF32 = 0, kEpiPairSplitT = 1;
 
+// Split-K (gridDim.z > 1, F32 epilogue only): CTA z covers k-steps
+// [z nk / Z, (z+1) nk / Z) and writes its partial tile to Cpart[z] (M x N,
+// row pitch N); the last CTA of a tile (atomic ticket after a fence) adds the
+// Z partials in order z = 0 .. Z-1 and writes C, so the result is
+// deterministic.  Run by the four epilogue warps (threads 0..127 of them).
+__device__ __forceinline__ bool splitk_last(unsigned *tickets, int tile, int Z, int et) {
+    __shared__ int s_last;
+    __threadfence();
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+    if (et == 0) s_last = atomicAdd(&tickets[tile], 1u) == (unsigned)(Z - 1);
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+    const bool last = s_last;
+    if (last) __threadfence();
+    return last;
+}
+
+// AND of `ok` over the four epilogue warps (named barrier 2).
+__device__ __forceinline__ bool epilogue_all(bool ok) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)ok)
+        : "memory");
+    return r != 0;
+}
+
+template <int BN>
+__device__ __forceinline__ void splitk_reduce_row(const float *__restrict__ Cpart, int64_t pstride, int Z, int row,
+                                                  int n0, int M, int N, float *__restrict__ C, int64_t ldc) {
+    if (row >= M) return;
+    const float *src = Cpart + (int64_t)row * N + n0;
+    float *dst = C + (int64_t)row * ldc + n0;
+    if (n0 + BN <= N && (N & 3) == 0 && (ldc & 3) == 0) {
+        // float4 columns, eight of them (x Z partials) in flight at a time
+#pragma unroll 1
+        for (int j = 0; j < BN; j += 32) {
+            float4 acc[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int z = 0; z < Z; ++z) {
+                float4 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = __ldcg(reinterpret_cast<const float4 *>(src + z * pstride + j + 4 * u));
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    acc[u].x += v[u].x;
+                    acc[u].y += v[u].y;
+                    acc[u].z += v[u].z;
+                    acc[u].w += v[u].w;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) *reinterpret_cast<float4 *>(dst + j + 4 * u) = acc[u];
+        }
+        return;
+    }
+    for (int j = 0; j < BN && n0 + j < N; ++j) {
+        float acc = 0.f;
+        for (int z = 0; z < Z; ++z) acc += __ldcg(src + (int64_t)z * pstride + j);
+        dst[j] = acc;
+    }
+}
+
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     float *__restrict__ C, int M, int N, int K, int64_t ldc, __nv_bfloat16 *__restrict__ Ct,
-                    int64_t ldct) {
+                    int64_t ldct, float *__restrict__ Cpart = nullptr, unsigned *__restrict__ tickets = nullptr) {
     using Cfg = GemmCfg<BN>;
     constexpr int S = Cfg::S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -61,7 +130,9 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-    const int nk = (K + kBK - 1) / kBK;
+    const int nk_all = (K + kBK - 1) / kBK, Z = gridDim.z;
+    const int kb = (int)((int64_t)blockIdx.z * nk_all / Z), ke = (int)((int64_t)(blockIdx.z + 1) * nk_all / Z);
+    const int nk = ke - kb;                    // k-steps of this CTA (all of them without split-K)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -92,8 +163,8 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     break;
                 }
                 umma::mbar_arrive_expect_tx(full0 + 8 * s, Cfg::STAGE);
-                umma::tma_load_2d(umma::smem_u32(sA + s * Cfg::A_BYTES), &tmA, kt * kBK, m0, full0 + 8 * s);
-                umma::tma_load_2d(umma::smem_u32(sB + s * Cfg::B_BYTES), &tmB, kt * kBK, n0, full0 + 8 * s);
+                umma::tma_load_2d(umma::smem_u32(sA + s * Cfg::A_BYTES), &tmA, (kb + kt) * kBK, m0, full0 + 8 * s);
+                umma::tma_load_2d(umma::smem_u32(sB + s * Cfg::B_BYTES), &tmB, (kb + kt) * kBK, n0, full0 + 8 * s);
             }
         }
         __syncwarp();
@@ -122,7 +193,8 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
         __syncwarp();
     } else {
         // Epilogue: warp w owns TMEM lanes 32*(w%4) .. +31, i.e. tile rows.
-        const bool ok = umma::mbar_wait(accum, 0, 4 * kWaitNs);
+        bool ok = umma::mbar_wait(accum, 0, 4 * kWaitNs);
+        if (EPI == kEpiF32 && gridDim.z > 1) ok = epilogue_all(ok);   // split-K barriers need one verdict
         __syncwarp();
         umma::fence_after_sync();
         if (ok) {
@@ -130,7 +202,10 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
             const int row = m0 + lane_base + lane;
             const uint32_t tl = tmem + ((uint32_t)lane_base << 16);
             if constexpr (EPI == kEpiF32) {
-                float *crow = C + (int64_t)row * ldc;
+                // Without split-K straight to C; with it to this CTA's partial tile.
+                const bool split = Z > 1;
+                const int64_t ld_out = split ? (int64_t)N : ldc;
+                float *crow = (split ? Cpart + (int64_t)blockIdx.z * M * N : C) + (int64_t)row * ld_out;
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t r[32];
@@ -138,7 +213,7 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                     umma::tmem_ld_wait();
                     const int col0 = n0 + c * 32;
                     if (row < M) {
-                        if (col0 + 32 <= N && (ldc & 3) == 0) {
+                        if (col0 + 32 <= N && (ld_out & 3) == 0) {
 #pragma unroll
                             for (int j = 0; j < 32; j += 4)
                                 *reinterpret_cast<float4 *>(crow + col0 + j) =
@@ -149,6 +224,13 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
                             for (int j = 0; j < 32; ++j)
                                 if (col0 + j < N) crow[col0 + j] = __uint_as_float(r[j]);
                         }
+                    }
+                }
+                if (split) {
+                    const int tile = blockIdx.x * gridDim.y + blockIdx.y;
+                    if (splitk_last(tickets, tile, Z, threadIdx.x - 64)) {
+                        splitk_reduce_row<BN>(Cpart, (int64_t)M * N, Z, row, n0, M, N, C, ldc);
+                        if (threadIdx.x == 64) tickets[tile] = 0u;
                     }
                 }
             } else {
@@ -232,10 +314,21 @@ static int gemm_set_attrs() {
 // Enqueue C = A B^T with prebuilt tensor maps (no synchronisation; capturable).
 template <int BN, int EPI>
 static void gemm_launch(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int64_t N, int64_t K, float *C,
-                        int64_t ldc, __nv_bfloat16 *Ct, int64_t ldct, cudaStream_t s) {
-    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN));
+                        int64_t ldc, __nv_bfloat16 *Ct, int64_t ldct, cudaStream_t s, int splits = 1,
+                        float *Cpart = nullptr, unsigned *tickets = nullptr) {
+    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
     gemm_bf16_tn_kernel<BN, EPI><<<grid, kGemmThreads, GemmCfg<BN>::SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K, ldc,
-                                                                               Ct, ldct);
+                                                                               Ct, ldct, Cpart, tickets);
+}
+
+// K-splits for a tile-starved F32 GEMM: enough CTAs for about one wave, each
+// split keeping at least 16 k-steps.
+static int gemm_splits(int64_t M, int64_t N, int64_t K, int BN, int sms) {
+    const int64_t tiles = ((M + kBM - 1) / kBM) * ((N + BN - 1) / BN);
+    const int64_t nk = (K + kBK - 1) / kBK;
+    int64_t z = sms / std::max<int64_t>(tiles, 1);
+    z = std::min<int64_t>(z, nk / 16);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(z, 16));
 }
 
 // C = A B^T for BF16 K-major A (M x K) and B (N x K), FP32 row-major C;

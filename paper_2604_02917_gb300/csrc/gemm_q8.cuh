@@ -44,7 +44,8 @@ __device__ __forceinline__ void mbar_arrive_local(uint32_t bar) {
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kQ8Threads, 1)
 gemm_q8_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, float *__restrict__ C,
-                  int M, int N, int K, int64_t ldc, __nv_bfloat16 *__restrict__ Ct, int64_t ldct) {
+                  int M, int N, int K, int64_t ldc, __nv_bfloat16 *__restrict__ Ct, int64_t ldct,
+                  float *__restrict__ Cpart = nullptr, unsigned *__restrict__ tickets = nullptr) {
     using Cfg = Q8Cfg<BN>;
     constexpr int S = Cfg::S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -59,7 +60,9 @@ gemm_q8_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
-    const int nk = (K + kBK - 1) / kBK;
+    const int nk_all = (K + kBK - 1) / kBK, Z = gridDim.z;   // split-K as in gemm.cuh
+    const int kb = (int)((int64_t)blockIdx.z * nk_all / Z), ke = (int)((int64_t)(blockIdx.z + 1) * nk_all / Z);
+    const int nk = ke - kb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -91,8 +94,8 @@ gemm_q8_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     break;
                 }
                 umma::mbar_arrive_expect_tx(full0 + 8 * s, Cfg::A8_BYTES + Cfg::B_BYTES);
-                umma::tma_load_2d(umma::smem_u32(sA8 + s * Cfg::A8_BYTES), &tmA, kt * kBK, m0, full0 + 8 * s);
-                umma::tma_load_2d(umma::smem_u32(sB + s * Cfg::B_BYTES), &tmB, kt * kBK, n0, full0 + 8 * s);
+                umma::tma_load_2d(umma::smem_u32(sA8 + s * Cfg::A8_BYTES), &tmA, (kb + kt) * kBK, m0, full0 + 8 * s);
+                umma::tma_load_2d(umma::smem_u32(sB + s * Cfg::B_BYTES), &tmB, (kb + kt) * kBK, n0, full0 + 8 * s);
             }
         }
         __syncwarp();
@@ -160,7 +163,8 @@ gemm_q8_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         __syncwarp();
     } else {
         // Epilogue: warps 2..5 own TMEM lanes 32*(w%4) .., i.e. tile rows.
-        const bool ok = umma::mbar_wait(accum, 0, 4 * kWaitNs);
+        bool ok = umma::mbar_wait(accum, 0, 4 * kWaitNs);
+        if (EPI == kEpiF32 && gridDim.z > 1) ok = epilogue_all(ok);
         __syncwarp();
         umma::fence_after_sync();
         if (ok) {
@@ -168,7 +172,9 @@ gemm_q8_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
             const int row = m0 + lane_base + lane;
             const uint32_t tl = tmem + ((uint32_t)lane_base << 16);
             if constexpr (EPI == kEpiF32) {
-                float *crow = C + (int64_t)row * ldc;
+                const bool split = Z > 1;
+                const int64_t ld_out = split ? (int64_t)N : ldc;
+                float *crow = (split ? Cpart + (int64_t)blockIdx.z * M * N : C) + (int64_t)row * ld_out;
 #pragma unroll 1
                 for (int c = 0; c < BN / 32; ++c) {
                     uint32_t rr[32];
@@ -179,6 +185,13 @@ gemm_q8_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
                         for (int j = 0; j < 32; ++j)
                             if (col0 + j < N) crow[col0 + j] = __uint_as_float(rr[j]);
+                    }
+                }
+                if (split) {
+                    const int tile = blockIdx.x * gridDim.y + blockIdx.y;
+                    if (splitk_last(tickets, tile, Z, threadIdx.x - 64)) {
+                        splitk_reduce_row<BN>(Cpart, (int64_t)M * N, Z, row, n0, M, N, C, ldc);
+                        if (threadIdx.x == 64) tickets[tile] = 0u;
                     }
                 }
             } else {
@@ -244,10 +257,11 @@ static int gemm_q8_set_attrs() {
 
 template <int BN, int EPI>
 static void gemm_q8_launch(const CUtensorMap &ta, const CUtensorMap &tb, int64_t M, int64_t N, int64_t K, float *C,
-                           int64_t ldc, __nv_bfloat16 *Ct, int64_t ldct, cudaStream_t s) {
-    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN));
+                           int64_t ldc, __nv_bfloat16 *Ct, int64_t ldct, cudaStream_t s, int splits = 1,
+                           float *Cpart = nullptr, unsigned *tickets = nullptr) {
+    dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + BN - 1) / BN), (unsigned)splits);
     gemm_q8_tn_kernel<BN, EPI><<<grid, kQ8Threads, Q8Cfg<BN>::SMEM, s>>>(ta, tb, C, (int)M, (int)N, (int)K, ldc, Ct,
-                                                                         ldct);
+                                                                         ldct, Cpart, tickets);
 }
 
 }  // namespace mv

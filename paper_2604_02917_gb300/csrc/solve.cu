@@ -1267,8 +1267,9 @@ static int frontier_attrs() {
 struct FPlan {
     int B;          // padded target count (32, 64 or 128)
     int BN;         // 2B: GEMM tile width
+    int splits;     // K-splits of G = L Z (43 row tiles at n = 5440 would leave SMs idle)
     int64_t ldLt, ldY, ldZ;
-    size_t o_lt, o_y, o_z, o_g, o_x, o_yd, o_gx, o_fs, o_rt, total;
+    size_t o_lt, o_y, o_z, o_g, o_x, o_yd, o_gx, o_fs, o_rt, o_gpart, o_gtick, total;
 };
 
 static FPlan make_fplan(const Plan &p, int64_t nb) {
@@ -1293,6 +1294,9 @@ static FPlan make_fplan(const Plan &p, int64_t nb) {
     f.o_gx = take(8 * (size_t)f.B * p.n);
     f.o_fs = take(sizeof(FState) * (size_t)f.B);
     f.o_rt = take(8 * (size_t)f.B);
+    f.splits = gemm_splits(p.n, f.BN, p.T, f.BN, sm_count());
+    f.o_gpart = take(4 * (size_t)f.splits * p.n * f.BN);
+    f.o_gtick = take(4 * (size_t)((p.n + kBM - 1) / kBM) + 64);
     f.total = off;
     return f;
 }
@@ -1300,14 +1304,18 @@ static FPlan make_fplan(const Plan &p, int64_t nb) {
 template <int BN>
 static void frontier_gemms(const CUtensorMap &tLt, const CUtensorMap &tY, const CUtensorMap &tL, const CUtensorMap &tZ,
                            const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
+    float *gpart = at<float>(ws, f.o_gpart);
+    unsigned *gtick = at<unsigned>(ws, f.o_gtick);
     if (p.dt == MV_FP8_E4M3) {
         gemm_q8_launch<BN, kEpiPairSplitT>(tLt, tY, p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(ws, f.o_z), f.ldZ,
                                            s);
-        gemm_q8_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s);
+        gemm_q8_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s, f.splits,
+                                    gpart, gtick);
         return;
     }
     gemm_launch<BN, kEpiPairSplitT>(tLt, tY, p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(ws, f.o_z), f.ldZ, s);
-    gemm_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s);
+    gemm_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s, f.splits, gpart,
+                             gtick);
 }
 
 static void frontier_gemm_pair(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
@@ -1337,7 +1345,7 @@ extern "C" {
 
 size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets) {
     if (validate_problem(P) != MV_OK || is_tn(P) || P->dtype == MV_F32 || n_targets < 1 || n_targets > 128) return 0;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
     return make_fplan(p, n_targets).total;
 }
 
@@ -1353,7 +1361,7 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);   // power method: fused pass
     const FPlan f = make_fplan(p, n_targets);
     MV_TRY(check_ws(d_ws, ws_bytes, f.total));
     MV_TRY(set_kernel_attrs());
@@ -1375,8 +1383,15 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
     const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
     setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
+    if (p.use_llt) {
+        MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
+        MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
+    }
     for (int it = 0; it < O.power_iters; ++it) {
-        gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
+        if (p.use_llt)
+            MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
+        else
+            gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
         power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
     }
     if (O.power_iters > 0) gemv_t_only(p, P, y32, d_ws, s);
@@ -1390,6 +1405,7 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
         transpose_elem_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, s>>>(
             reinterpret_cast<const __nv_bfloat16 *>(P->L), p.n, p.T, P->ld, at<__nv_bfloat16>(d_ws, f.o_lt), f.ldLt);
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_y), 0, 2 * (size_t)f.BN * f.ldY, s));
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_gtick), 0, 4 * (size_t)((p.n + kBM - 1) / kBM) + 64, s));
     MV_CUDA_TRY(cudaGetLastError());
 
     FArgs a;
