@@ -357,6 +357,22 @@ int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, 
                     double trace_sigma, float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out,
                     void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
+/*  mv_str_truncate with the data-driven choices of App. D: the rank is the
+ *  knee of the sketched spectrum lam_i = sigma_i^2(tilde L) (nonincreasing),
+ *      l = max{ i : lam_i / lam_1 >= tau  and  lam_{i+1} / lam_i <= rho }
+ *  (App. D.1; tau in (0, 1] the minimum relative signal level, rho in (0, 1)
+ *  the knee ratio), capped at k_max; and, if kappa_target > 1, the ridge
+ *      gamma = lam_1 / (kappa_target - 1)
+ *  so that the STR covariance has condition number kappa_target (App. D.2);
+ *  otherwise gamma as in mv_str_truncate.  L_eff has k_max columns of which
+ *  the first l are U_l diag(sigma_l) and the rest zero (sigma likewise).
+ *  *h_k_out = l.  MV_ERR_NUMERIC if no i satisfies the rule.  Workspace:
+ *  mv_str_workspace_size(n, m, k_max).  Blocking. */
+int mv_str_truncate_knee(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, double tau, double rho,
+                         int64_t k_max, double kappa_target, double gamma, double trace_sigma, float *d_L_eff,
+                         int64_t ldE, double *d_sigma, int64_t *h_k_out, double *h_gamma_out, void *d_ws,
+                         size_t ws_bytes, mv_stream_t stream);
+
 /*  mv_sketch followed by mv_str_truncate (the whole STR build of Sec. 2.5);
  *  d_L_sketch receives tilde L.  Workspace as mv_str_workspace_size.  Blocking. */
 int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m,

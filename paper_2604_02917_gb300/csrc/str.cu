@@ -121,8 +121,40 @@ __global__ void leff_kernel(const double *__restrict__ U, const double *__restri
     }
 }
 
+// The knee rule of App. D.1 on the eigenvalues W (ascending, n of them):
+// with lam_i = W[n - i] (i = 1 .. n, nonincreasing), writes
+// l = max{i < n : lam_i / lam_1 >= tau and lam_{i+1} / lam_i <= rho}
+// (0 if no i qualifies).  One block.
+__global__ void knee_kernel(const double *__restrict__ W, int n, double tau, double rho, int *out) {
+    __shared__ int best;
+    if (threadIdx.x == 0) best = 0;
+    __syncthreads();
+    const double lam1 = W[n - 1];
+    int mine = 0;
+    for (int i = 1 + threadIdx.x; i < n; i += blockDim.x) {
+        const double li = W[n - i], lnext = W[n - i - 1];
+        if (li / lam1 >= tau && lnext / li <= rho) mine = i;      // i grows along this thread's stride
+    }
+    if (mine > 0) atomicMax(&best, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) *out = best;
+}
+
+// Columns k .. k_max-1 of L_eff and entries k .. k_max-1 of sigma set to zero.
+__global__ void zero_tail_kernel(float *__restrict__ L_eff, int64_t ldE, int n, int k, int k_max,
+                                 double *__restrict__ sigma) {
+    const int w = k_max - k;
+    const int64_t total = (int64_t)n * w;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / w), c = k + (int)(idx - (int64_t)i * w);
+        L_eff[(int64_t)i * ldE + c] = 0.f;
+        if (i == 0) sigma[c] = 0.0;
+    }
+}
+
 struct StrPlan {
-    size_t o_a, o_k, o_w, o_work, o_info, total;
+    size_t o_a, o_k, o_w, o_work, o_info, o_knee, total;
     int lwork;
 };
 
@@ -143,6 +175,7 @@ static int str_plan(int64_t n, int64_t m, int64_t k, StrPlan *p) {
     p->o_w = take(8 * (size_t)n);
     p->o_work = take(8 * (size_t)lwork);
     p->o_info = take(sizeof(int));
+    p->o_knee = take(sizeof(int));
     p->total = off;
     p->lwork = lwork;
     return MV_OK;
@@ -161,19 +194,11 @@ size_t mv_str_workspace_size(int64_t n, int64_t m, int64_t k) {
     return p.total;
 }
 
-int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, int64_t k, double gamma,
-                    double trace_sigma, float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out,
-                    void *d_ws, size_t ws_bytes, mv_stream_t stream) {
-    if (!d_L_sketch || !d_L_eff || !d_sigma) return MV_ERR_INVALID_ARG;
-    if (n < 1 || m < 1 || k < 1 || k > n || ldS < m || ldE < k || n >= (1 << 30) || m >= (1 << 30))
-        return MV_ERR_INVALID_ARG;
-    StrPlan p;
-    MV_TRY(str_plan(n, m, k, &p));
-    if (d_ws == nullptr || ws_bytes < p.total || ((uintptr_t)d_ws) % 256) return MV_ERR_WORKSPACE;
+// FP64 Gram K = tilde L tilde L^T and all its eigenpairs (ascending) into the
+// workspace: eigenvectors overwrite K (column-major), eigenvalues in W.
+static int str_eigen(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, const StrPlan &p, char *ws,
+                     cudaStream_t s) {
     Linalg *L = linalg();
-    cudaStream_t s = (cudaStream_t)stream;
-    (void)cudaGetLastError();
-    char *ws = reinterpret_cast<char *>(d_ws);
     double *A = reinterpret_cast<double *>(ws + p.o_a);
     double *K = reinterpret_cast<double *>(ws + p.o_k);
     double *W = reinterpret_cast<double *>(ws + p.o_w);
@@ -189,9 +214,6 @@ int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, 
     if (L->s_set_stream(L->hs, s) != 0) return record_message(MV_ERR_CUDA, "cusolverDnSetStream failed");
     if (L->syevd(L->hs, kEigVector, kFillLower, (int)n, K, (int)n, W, work, p.lwork, info) != 0)
         return record_message(MV_ERR_CUDA, "cusolverDnDsyevd failed");
-    // all n pairs come back ascending: the k largest are the last k columns
-    leff_kernel<<<1024, 256, 0, s>>>(K + (size_t)(n - k) * n, W + (n - k), (int)n, (int)k, d_L_eff, ldE, d_sigma);
-    MV_CUDA_TRY(cudaGetLastError());
     int hinfo = 0;
     MV_CUDA_TRY(cudaMemcpyAsync(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost, s));
     MV_CUDA_TRY(cudaStreamSynchronize(s));
@@ -200,9 +222,71 @@ int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, 
         snprintf(msg, sizeof(msg), "cusolverDnDsyevd: info=%d", hinfo);
         return record_message(MV_ERR_NUMERIC, msg);
     }
+    return MV_OK;
+}
+
+int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, int64_t k, double gamma,
+                    double trace_sigma, float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out,
+                    void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    if (!d_L_sketch || !d_L_eff || !d_sigma) return MV_ERR_INVALID_ARG;
+    if (n < 1 || m < 1 || k < 1 || k > n || ldS < m || ldE < k || n >= (1 << 30) || m >= (1 << 30))
+        return MV_ERR_INVALID_ARG;
+    StrPlan p;
+    MV_TRY(str_plan(n, m, k, &p));
+    if (d_ws == nullptr || ws_bytes < p.total || ((uintptr_t)d_ws) % 256) return MV_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    char *ws = reinterpret_cast<char *>(d_ws);
+    MV_TRY(str_eigen(d_L_sketch, n, m, ldS, p, ws, s));
+    double *K = reinterpret_cast<double *>(ws + p.o_k);
+    double *W = reinterpret_cast<double *>(ws + p.o_w);
+    // all n pairs come back ascending: the k largest are the last k columns
+    leff_kernel<<<1024, 256, 0, s>>>(K + (size_t)(n - k) * n, W + (n - k), (int)n, (int)k, d_L_eff, ldE, d_sigma);
+    MV_CUDA_TRY(cudaGetLastError());
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
     if (h_gamma_out) *h_gamma_out = gamma >= 0.0 ? gamma : 1e-4 * trace_sigma / (double)n;
     return MV_OK;
 }
+
+int mv_str_truncate_knee(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, double tau, double rho,
+                         int64_t k_max, double kappa_target, double gamma, double trace_sigma, float *d_L_eff,
+                         int64_t ldE, double *d_sigma, int64_t *h_k_out, double *h_gamma_out, void *d_ws,
+                         size_t ws_bytes, mv_stream_t stream) {
+    if (!d_L_sketch || !d_L_eff || !d_sigma || !h_k_out) return MV_ERR_INVALID_ARG;
+    if (n < 2 || m < 1 || k_max < 1 || k_max > n || ldS < m || ldE < k_max || n >= (1 << 30) || m >= (1 << 30))
+        return MV_ERR_INVALID_ARG;
+    if (!(tau > 0.0) || !(rho > 0.0 && rho < 1.0) || !(kappa_target <= 0.0 || kappa_target > 1.0))
+        return MV_ERR_INVALID_ARG;
+    StrPlan p;
+    MV_TRY(str_plan(n, m, k_max, &p));
+    if (d_ws == nullptr || ws_bytes < p.total || ((uintptr_t)d_ws) % 256) return MV_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    (void)cudaGetLastError();
+    char *ws = reinterpret_cast<char *>(d_ws);
+    MV_TRY(str_eigen(d_L_sketch, n, m, ldS, p, ws, s));
+    double *K = reinterpret_cast<double *>(ws + p.o_k);
+    double *W = reinterpret_cast<double *>(ws + p.o_w);
+    int *knee = reinterpret_cast<int *>(ws + p.o_knee);
+    knee_kernel<<<1, 1024, 0, s>>>(W, (int)n, tau, rho, knee);
+    int hk = 0;
+    double lam1 = 0.0;
+    MV_CUDA_TRY(cudaMemcpyAsync(&hk, knee, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MV_CUDA_TRY(cudaMemcpyAsync(&lam1, W + (n - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hk < 1) return record_message(MV_ERR_NUMERIC, "knee rule: no index satisfies the tau and rho conditions");
+    const int64_t k = hk < k_max ? hk : k_max;
+    leff_kernel<<<1024, 256, 0, s>>>(K + (size_t)(n - k) * n, W + (n - k), (int)n, (int)k, d_L_eff, ldE, d_sigma);
+    if (k < k_max) zero_tail_kernel<<<256, 256, 0, s>>>(d_L_eff, ldE, (int)n, (int)k, (int)k_max, d_sigma);
+    MV_CUDA_TRY(cudaGetLastError());
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
+    *h_k_out = k;
+    if (h_gamma_out) {
+        if (kappa_target > 1.0) *h_gamma_out = lam1 / (kappa_target - 1.0);   // App. D.2
+        else *h_gamma_out = gamma >= 0.0 ? gamma : 1e-4 * trace_sigma / (double)n;
+    }
+    return MV_OK;
+}
+
 
 int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m, int64_t ldP,
                   int64_t k, double gamma, double trace_sigma, float *d_L_sketch, int64_t ldS, float *d_L_eff,

@@ -35,7 +35,7 @@ EXPORTS = [
     "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
     "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
     "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch", "mv_center_host_workspace_size",
-    "mv_center_factor_host", "mv_batch_tiles",
+    "mv_center_factor_host", "mv_batch_tiles", "mv_str_truncate_knee",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -127,6 +127,9 @@ def lib():
         L.mv_str_truncate.restype = i32
         L.mv_str_truncate.argtypes = [vp, i64, i64, i64, i64, dbl, dbl, vp, i64, vp, C.POINTER(C.c_double), vp, sz,
                                       vp]
+        L.mv_str_truncate_knee.restype = i32
+        L.mv_str_truncate_knee.argtypes = [vp, i64, i64, i64, dbl, dbl, i64, dbl, dbl, dbl, vp, i64, vp,
+                                           C.POINTER(C.c_int64), C.POINTER(C.c_double), vp, sz, vp]
         L.mv_sketch_str.restype = i32
         L.mv_sketch_str.argtypes = [vp, i64, i64, i64, vp, i64, i64, i64, dbl, dbl, vp, i64, vp, i64, vp,
                                     C.POINTER(C.c_double), vp, sz, vp]
@@ -402,6 +405,30 @@ def bf16_rows(A, ld=None) -> torch.Tensor:
     out = torch.zeros((r, ld), dtype=torch.bfloat16, device="cuda")
     out[:, :c] = A.to(device="cuda", dtype=torch.bfloat16)
     return out
+
+
+def str_truncate_knee(L_sketch: torch.Tensor, tau: float, rho: float, k_max: int, kappa_target: float = 0.0,
+                      gamma: float = -1.0, trace_sigma: float = 0.0):
+    """(L_eff (n x k_max, columns >= l zero), sigma (k_max), l, gamma): the knee-rule rank and
+    the kappa-target ridge of App. D from the FP32 sketch tilde L (n x m)."""
+    assert L_sketch.dtype == torch.float32 and L_sketch.stride(1) == 1
+    n, m = L_sketch.shape
+    ldS = L_sketch.stride(0)
+    dev = L_sketch.device
+    nb = lib().mv_str_workspace_size(n, m, k_max)
+    if nb == 0:
+        raise MvError(MV_ERR_UNSUPPORTED, "mv_str_workspace_size")
+    ldE = (k_max + 3) // 4 * 4
+    L_eff = torch.zeros((n, ldE), dtype=torch.float32, device=dev)
+    sigma = torch.empty(k_max, dtype=torch.float64, device=dev)
+    ws = _workspace(nb, dev)
+    k = C.c_int64(0)
+    g = C.c_double(0.0)
+    _check(lib().mv_str_truncate_knee(_ptr(L_sketch), n, m, ldS, float(tau), float(rho), int(k_max),
+                                      float(kappa_target), float(gamma), float(trace_sigma), _ptr(L_eff), ldE,
+                                      _ptr(sigma), C.byref(k), C.byref(g), _ptr(ws), ws.numel(), _stream()),
+           "mv_str_truncate_knee")
+    return L_eff, sigma, int(k.value), float(g.value)
 
 
 def str_truncate(L_sketch: torch.Tensor, k: int, gamma: float = -1.0, trace_sigma: float = 0.0):

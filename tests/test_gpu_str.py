@@ -104,3 +104,42 @@ def test_str_full_size_properties(mv):
     Le[:, :] = L_eff
     x, info = mv.npga_solve(Le, mu, Rt, k, gamma=gamma, eps=1e-6)
     assert info["converged"] == 1 and info["kkt"] <= 1e-6
+
+
+@pytest.mark.parametrize("tau,rho,kappa", [(1e-3, 0.9, 500.0), (3e-2, 0.8, 0.0)])
+def test_str_knee_rank_and_kappa_ridge(mv, tau, rho, kappa):
+    """App. D: the knee-rule rank l and the kappa-target ridge, against the
+    oracle's knee_rank / gamma_for_kappa on the FP64 spectrum of the same
+    tilde L.  tilde L is a seeded n x m matrix with a designed core-bulk-tail
+    spectrum (the synthetic return panel's idiosyncratic noise swamps its
+    factors, so it has no knee).  The thresholds are checked to sit away from
+    every ratio, so the integer decision is unique."""
+    n, m, k_max = 300, 512, 96
+    rng = np.random.default_rng(43)
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    core = 10.0 * 0.62 ** np.arange(14)                     # factor-like core
+    bulk = np.sort(rng.uniform(0.02, 0.03, n - 14))[::-1]    # flat noise bulk
+    sv = np.concatenate([core, bulk])
+    A = ((U * sv) @ V.T).astype(np.float32)
+    Ls = torch.from_numpy(A).cuda()
+    A64 = A.astype(np.float64)
+    lam = np.sort(np.linalg.eigvalsh(A64 @ A64.T))[::-1]
+    r1 = lam / lam[0]
+    r2 = lam[1:] / lam[:-1]
+    assert np.min(np.abs(r1 - tau)) > 1e-6 * tau and np.min(np.abs(r2 - rho)) > 1e-6
+    l_o = strmodel.knee_rank(lam, tau, rho)
+    assert 1 <= l_o <= k_max
+    L_eff, sigma, l, gamma = mv.str_truncate_knee(Ls, tau, rho, k_max, kappa_target=kappa, gamma=1e-6)
+    assert l == l_o
+    s = sigma.cpu().numpy()
+    assert np.max(np.abs(s[:l] ** 2 - lam[:l])) <= 1e-5 * lam[0]
+    assert np.all(s[l:] == 0.0) and torch.count_nonzero(L_eff[:, l:]) == 0
+    G = L_eff[:, :l].double().cpu().numpy()
+    assert np.max(np.abs(G.T @ G - np.diag(s[:l] ** 2))) <= 1e-5 * lam[0]
+    if kappa > 1.0:
+        assert gamma == pytest.approx(strmodel.gamma_for_kappa(np.sqrt(lam[0]), kappa), rel=1e-6)
+        # kappa(hat Sigma) = (sigma_1^2 + gamma) / gamma = kappa_target (App. D.2)
+        assert (s[0] ** 2 + gamma) / gamma == pytest.approx(kappa, rel=1e-6)
+    else:
+        assert gamma == 1e-6
