@@ -17,6 +17,33 @@
   upper bound on f(x) - f* for convex f; the linear minimisation is done
   exactly over the vertex list of F.
 * ``solver_gap`` -- the relative gap metric of Sec. 5.2.
+
+Explicit covariance (the Sec. 3 remark that NPGA applies unchanged to the
+classical model with Sigma in place of L_eff):
+
+* ``sigma_from_factor`` -- Sigma = L L^T, the sample covariance of Sec. 2.1.
+* ``objective_sigma`` / ``gradient_sigma`` -- f(x) = x^T Sigma x + gamma ||x||^2,
+  grad f(x) = 2 Sigma x + 2 gamma x.
+* ``power_norm2_sigma`` -- the same power method on Sigma: u <- Sigma u /
+  ||Sigma u||, returning the Rayleigh quotient u^T Sigma u (= ||L^T u||^2
+  when Sigma = L L^T).
+* ``npga_sigma`` -- Algorithm 1 with that gradient.
+
+Step-size and momentum variants of Sec. 3.1 (``npga`` / ``npga_sigma``
+keywords):
+
+* ``momentum="constant"`` -- the strongly convex specialisation: beta_k
+  fixed at (1 - sqrt(alpha m_f)) / (1 + sqrt(alpha m_f)) for a lower
+  curvature bound m_f > 0 and a fixed step alpha.
+* ``backtrack=(alpha0, rho)`` -- the accelerated backtracking rule: the
+  trial step starts at the previous accepted step (alpha0 at k = 0) and is
+  multiplied by rho until f(x+) <= f(y) + <grad f(y), x+ - y> +
+  ||x+ - y||^2 / (2 alpha); the KKT residual uses the accepted step.
+  Reading: f is quadratic, so with d = x+ - y the inequality is exactly
+  ||L^T d||^2 + gamma ||d||^2 <= ||d||^2 / (2 alpha) (d^T Sigma d in the
+  explicit form).  That form is evaluated: the printed one subtracts
+  nearly equal objective values and, near the solution, rejects steps on
+  rounding noise alone.
 """
 from __future__ import annotations
 
@@ -71,6 +98,7 @@ class NPGAResult:
     proj_failures: int = 0
     kkt_history: list = field(default_factory=list)
     trajectory: list = field(default_factory=list)   # x^0, x^1, ... if recorded
+    alpha: float = 0.0                               # the (last accepted) step
 
 
 def initial_point(mu, R, mode="ge"):
@@ -79,10 +107,10 @@ def initial_point(mu, R, mode="ge"):
     return project_F(np.full(n, 1.0 / n), mu, R, mode).x
 
 
-def npga(Leff, gamma, mu, R, x0, alpha, eps=1e-6, max_iter=10000,
-         kkt_every=5, mode="ge", record=False) -> NPGAResult:
-    """Algorithm 1 with a fixed step (every benchmark in the paper uses one)."""
-    Leff = np.asarray(Leff, dtype=np.float64)
+def _npga_loop(fval, grad, curv, gamma, mu, R, x0, alpha, eps, max_iter, kkt_every, mode, record,
+               momentum, m_f, backtrack):
+    """Algorithm 1 for f with value ``fval``, gradient ``grad`` and curvature
+    ``curv(d)`` = f(y + d) - f(y) - <grad f(y), d>."""
     mu = np.asarray(mu, dtype=np.float64)
     x = np.array(x0, dtype=np.float64)
     y = x.copy()
@@ -93,30 +121,112 @@ def npga(Leff, gamma, mu, R, x0, alpha, eps=1e-6, max_iter=10000,
     fails = 0
     converged = False
     traj = [x.copy()] if record else []
+    if backtrack is not None:
+        alpha, rho = float(backtrack[0]), float(backtrack[1])
+        if not (alpha > 0.0 and 0.0 < rho < 1.0):
+            raise ValueError("backtracking needs alpha0 > 0 and 0 < rho < 1")
+    if momentum == "constant":
+        if not m_f > 0.0:
+            raise ValueError("constant momentum needs a lower curvature bound m_f > 0")
+        q = np.sqrt(alpha * m_f)
+        beta_c = (1.0 - q) / (1.0 + q)
+    elif momentum != "fista":
+        raise ValueError("momentum is 'fista' or 'constant'")
+
+    def kkt(xk):
+        p = project_F(xk - alpha * grad(xk), mu, R, mode)
+        return float(np.linalg.norm(p.x - xk))
+
     while True:
         if kkt_every > 0 and k % kkt_every == 0:
-            r = kkt_residual(Leff, gamma, mu, R, x, alpha, mode)
+            r = kkt(x)
             hist.append((k, r))
             if r <= eps:
                 converged = True
                 break
         if k >= max_iter:
             break
-        v = y - alpha * gradient(Leff, gamma, y)
-        p = project_F(v, mu, R, mode)
+        gy = grad(y)
+        while True:
+            p = project_F(y - alpha * gy, mu, R, mode)
+            if backtrack is None:
+                break
+            d = p.x - y
+            if curv(d) <= (d @ d) / (2.0 * alpha):
+                break
+            alpha *= rho
         if p.status != PROJ_OK:
             fails += 1
         x_new = p.x
-        t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
-        beta = (t - 1.0) / t_new
+        if momentum == "constant":
+            beta = beta_c
+            t_new = t
+        else:
+            t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+            beta = (t - 1.0) / t_new
         y = x_new + beta * (x_new - x)
         x, t = x_new, t_new
         k += 1
         if record:
             traj.append(x.copy())
     if not converged:
-        r = kkt_residual(Leff, gamma, mu, R, x, alpha, mode)
-    return NPGAResult(x, k, r, objective(Leff, gamma, x), converged, fails, hist, traj)
+        r = kkt(x)
+    res = NPGAResult(x, k, r, fval(x), converged, fails, hist, traj)
+    res.alpha = alpha
+    return res
+
+
+def npga(Leff, gamma, mu, R, x0, alpha, eps=1e-6, max_iter=10000,
+         kkt_every=5, mode="ge", record=False, momentum="fista", m_f=0.0,
+         backtrack=None) -> NPGAResult:
+    """Algorithm 1 on the factor form; a fixed step unless ``backtrack``."""
+    Leff = np.asarray(Leff, dtype=np.float64)
+    return _npga_loop(lambda x: objective(Leff, gamma, x), lambda x: gradient(Leff, gamma, x),
+                      lambda d: objective(Leff, gamma, d), gamma, mu, R, x0, alpha, eps, max_iter, kkt_every,
+                      mode, record, momentum, m_f, backtrack)
+
+
+# ------------------------------------------------------------ explicit Sigma
+def sigma_from_factor(L):
+    """Sigma = L L^T (Sec. 2.1 with L the centered, 1/sqrt(T-1)-scaled panel)."""
+    L = np.asarray(L, dtype=np.float64)
+    return L @ L.T
+
+
+def objective_sigma(Sigma, gamma, x):
+    return float(x @ (Sigma @ x) + gamma * (x @ x))
+
+
+def gradient_sigma(Sigma, gamma, x):
+    return 2.0 * (Sigma @ x) + 2.0 * gamma * x
+
+
+def power_norm2_sigma(Sigma, r, iters: int = 50):
+    """Power-method estimate of ||Sigma||_2 (= ||L||_2^2) from the start vector r."""
+    u = np.asarray(r, dtype=np.float64)
+    u = u / np.linalg.norm(u)
+    for _ in range(iters):
+        w = Sigma @ u
+        nw = np.linalg.norm(w)
+        if nw == 0.0:
+            return 0.0
+        u = w / nw
+    return float(u @ (Sigma @ u))
+
+
+def kkt_residual_sigma(Sigma, gamma, mu, R, x, alpha, mode="ge"):
+    p = project_F(x - alpha * gradient_sigma(Sigma, gamma, x), mu, R, mode)
+    return float(np.linalg.norm(p.x - x))
+
+
+def npga_sigma(Sigma, gamma, mu, R, x0, alpha, eps=1e-6, max_iter=10000,
+               kkt_every=5, mode="ge", record=False, momentum="fista", m_f=0.0,
+               backtrack=None) -> NPGAResult:
+    """Algorithm 1 with grad f(y) = 2 Sigma y + 2 gamma y (explicit covariance)."""
+    Sigma = np.asarray(Sigma, dtype=np.float64)
+    return _npga_loop(lambda x: objective_sigma(Sigma, gamma, x), lambda x: gradient_sigma(Sigma, gamma, x),
+                      lambda d: objective_sigma(Sigma, gamma, d), gamma, mu, R, x0, alpha, eps, max_iter,
+                      kkt_every, mode, record, momentum, m_f, backtrack)
 
 
 def vertices_F(mu, R, mode="ge"):

@@ -17,6 +17,11 @@ F = {x : mu^T x >= R, 1^T x = 1, x >= 0} = Delta intersect H.
       sum_S mu tau - nu sum_S mu^2 = sum_S mu v - R
   and re-verifying x_S > 0 and v_i + nu mu_i - tau <= 0 off S.
   An equality mode (mu^T x = R, nu of either sign) is also provided.
+* ``project_F_dykstra`` -- the safeguard of Sec. 3.1: Dykstra's alternating
+  projections between Delta and H (Bauschke--Borwein), with the correction
+  terms p (for Delta) and q (for H); converges to Pi_F(v).
+* ``project_F_safeguarded`` -- the scalar search with a bracketing budget,
+  falling back to Dykstra when the bracketing does not close within it.
 """
 from __future__ import annotations
 
@@ -27,6 +32,7 @@ import numpy as np
 PROJ_OK = 0
 PROJ_INFEASIBLE = 1
 PROJ_TOLERANCE = 2      # bisection stalled; returned x(nu_hi) unverified
+PROJ_BRACKET = 3        # the bracketing budget ran out before phi(nu) crossed R
 
 
 @dataclass
@@ -129,7 +135,7 @@ def project_F(v, mu, R, mode: str = "ge", max_bracket: int = 200,
             break
         lo, hi = hi, 2.0 * hi
     else:
-        return ProjResult(np.full(n, np.nan), np.nan, np.nan, 0, PROJ_INFEASIBLE, np.nan, True)
+        return ProjResult(np.full(n, np.nan), np.nan, np.nan, 0, PROJ_BRACKET, np.nan, True)
 
     # Bisection until the support is pinned, then the exact finish.
     for _ in range(max_bisect):
@@ -164,3 +170,50 @@ def active_set(v, mu, nu, tau, rel_degenerate: float = 1e-12):
     w = v + nu * np.asarray(mu, dtype=np.float64) - tau
     tol = rel_degenerate * max(1.0, float(np.max(np.abs(v))))
     return w > 0.0, np.abs(w) <= tol
+
+
+def project_hyperplane(y: np.ndarray, mu: np.ndarray, R: float) -> np.ndarray:
+    """Projection onto {x : mu^T x = R}."""
+    y = np.asarray(y, dtype=np.float64)
+    mu = np.asarray(mu, dtype=np.float64)
+    return y + (R - float(mu @ y)) / float(mu @ mu) * mu
+
+
+def project_F_dykstra(v, mu, R, mode: str = "ge", iters: int = 100000, tol: float = 1e-13):
+    """Dykstra's algorithm for Pi_{Delta cap H}(v) (Sec. 3.1 safeguard).
+
+    x^0 = v, p^0 = q^0 = 0;  y = Pi_Delta(x + p), p <- x + p - y;
+    x = Pi_H(y + q), q <- y + q - x.  Stops at a fixed point of the whole
+    state (x, p, q): a sweep that moves none of them by more than
+    tol * max(1, |v|_inf), with x and y in agreement.  (x alone can stand
+    still for many sweeps while the corrections still move.)  Returns
+    (x, sweeps).
+    """
+    v = np.asarray(v, dtype=np.float64)
+    mu = np.asarray(mu, dtype=np.float64)
+    proj_H = (lambda w: project_halfspace(w, mu, R)) if mode == "ge" else (lambda w: project_hyperplane(w, mu, R))
+    x = v.copy()
+    p = np.zeros_like(v)
+    q = np.zeros_like(v)
+    scale = tol * max(1.0, float(np.max(np.abs(v))))
+    for it in range(1, iters + 1):
+        y, _ = project_simplex(x + p)
+        p_new = x + p - y
+        x_new = proj_H(y + q)
+        q_new = y + q - x_new
+        moved = max(float(np.max(np.abs(x_new - x))), float(np.max(np.abs(p_new - p))),
+                    float(np.max(np.abs(q_new - q))))
+        x, p, q = x_new, p_new, q_new
+        if moved <= scale and float(np.max(np.abs(x - y))) <= scale:
+            return y, it
+    return y, iters
+
+
+def project_F_safeguarded(v, mu, R, mode: str = "ge", max_bracket: int = 200,
+                          dykstra_iters: int = 100000) -> ProjResult:
+    """The scalar-search projection; Dykstra when its bracketing budget runs out."""
+    res = project_F(v, mu, R, mode, max_bracket=max_bracket)
+    if res.status != PROJ_BRACKET:
+        return res
+    x, _ = project_F_dykstra(v, mu, R, mode, dykstra_iters)
+    return ProjResult(x, np.nan, np.nan, int((x > 0).sum()), PROJ_OK, float(np.asarray(mu) @ x) - R, True)

@@ -14,10 +14,13 @@ import pytest
 
 from synth import CFG_SMALL, factor_returns, gaussian_sketch, power_start
 from oracle.center import center_factor
-from oracle.projection import (PROJ_INFEASIBLE, PROJ_OK, active_set, project_F,
-                               project_halfspace, project_simplex)
-from oracle.npga import (fw_gap, gradient, initial_point, kkt_residual, lin_min_F,
-                         npga, objective, power_norm2, solver_gap, step_size, vertices_F)
+from oracle.projection import (PROJ_BRACKET, PROJ_INFEASIBLE, PROJ_OK, active_set, project_F,
+                               project_F_dykstra, project_F_safeguarded, project_halfspace,
+                               project_simplex)
+from oracle.npga import (fw_gap, gradient, gradient_sigma, initial_point, kkt_residual,
+                         kkt_residual_sigma, lin_min_F, npga, npga_sigma, objective, objective_sigma,
+                         power_norm2, power_norm2_sigma, sigma_from_factor, solver_gap, step_size,
+                         vertices_F)
 from oracle.bruteforce import project_bruteforce, qp_bruteforce
 from oracle import strmodel
 
@@ -288,6 +291,131 @@ def test_lin_min_F_matches_vertex_scan_and_gap_metric():
     assert solver_gap(1.1, 1.0) == pytest.approx(0.1)
     assert solver_gap(0.9, 1.0) == 0.0
     assert solver_gap(1.0, 0.0) == pytest.approx(1e12)
+
+
+# ------------------------------------------------- explicit Sigma (Sec. 3)
+def test_sigma_form_matches_covariance_and_bruteforce():
+    """Sigma = L L^T is np.cov; its objective, gradient (FD) and power estimate
+    agree with the library; NPGA on Sigma reaches the exhaustive QP optimum."""
+    R, mu, L, Rt = small_problem(40, 300, seed=4)
+    S = sigma_from_factor(L)
+    np.testing.assert_allclose(S, np.cov(R, ddof=1), rtol=1e-12, atol=1e-18)
+    x = np.random.default_rng(3).dirichlet(np.ones(40))
+    assert objective_sigma(S, 0.2, x) == pytest.approx(x @ np.cov(R, ddof=1) @ x + 0.2 * x @ x, rel=1e-12)
+    h = 1e-6
+    fd = np.array([(objective_sigma(S, 0.2, x + h * e) - objective_sigma(S, 0.2, x - h * e)) / (2 * h)
+                   for e in np.eye(40)])
+    np.testing.assert_allclose(gradient_sigma(S, 0.2, x), fd, rtol=1e-6, atol=1e-12)
+    lam_max = np.linalg.eigvalsh(S)[-1]
+    prev = 0.0
+    for it in (1, 5, 50, 2000):
+        lam = power_norm2_sigma(S, power_start(40), it)
+        assert prev * (1 - 1e-12) <= lam <= lam_max * (1 + 1e-12)
+        prev = lam
+    assert prev == pytest.approx(lam_max, rel=1e-9)
+    for gamma in (0.0, 5e-5):
+        for seed in range(3):
+            n = 6 + seed
+            _, mu, L, Rt = small_problem(n, 60, seed=30 + seed, pct=70)
+            S = sigma_from_factor(L)
+            ref = qp_bruteforce(S + gamma * np.eye(n), mu, Rt)
+            a = step_size(np.linalg.eigvalsh(S)[-1], gamma)
+            res = npga_sigma(S, gamma, mu, Rt, initial_point(mu, Rt), a, eps=1e-11, max_iter=200000)
+            assert res.converged
+            np.testing.assert_allclose(res.x, ref, atol=1e-7)
+            assert kkt_residual_sigma(S, gamma, mu, Rt, res.x, a) == pytest.approx(res.kkt)
+
+
+# -------------------------------------------- step and momentum variants (Sec. 3.1)
+def test_constant_momentum_linear_rate():
+    """The strongly convex specialisation (beta = (1 - q)/(1 + q), q = sqrt(alpha m_f))
+    obeys the V-FISTA bound f(x^k) - f* <= (1 - q)^k (f(x^0) - f* + m_f/2 ||x^0 - x*||^2)
+    (Beck, First-Order Methods in Optimization, Thm. 10.7.7) with m_f = 2 (lambda_min + gamma);
+    a wrong beta or a missing extrapolation breaks it."""
+    for seed, gamma in ((40, 2e-5), (41, 1e-4), (42, 5e-6)):
+        _, mu, L, Rt = small_problem(8, 40, seed=seed, pct=65)
+        S = sigma_from_factor(L)
+        ev = np.linalg.eigvalsh(S)
+        Lf, mf = 2 * (ev[-1] + gamma), 2 * (ev[0] + gamma)
+        a = 1.0 / Lf
+        xs = qp_bruteforce(S + gamma * np.eye(8), mu, Rt)
+        fs = objective_sigma(S, gamma, xs)
+        x0 = initial_point(mu, Rt)
+        K = 400
+        traj = npga(L, gamma, mu, Rt, x0, a, eps=0.0, max_iter=K, kkt_every=0, record=True,
+                    momentum="constant", m_f=mf).trajectory
+        q = np.sqrt(a * mf)
+        c0 = objective_sigma(S, gamma, x0) - fs + 0.5 * mf * (x0 - xs) @ (x0 - xs)
+        for k in range(1, K + 1):
+            assert objective_sigma(S, gamma, traj[k]) - fs <= (1 - q) ** k * c0 + 1e-17
+        # the Sigma form follows the same iterates
+        traj2 = npga_sigma(S, gamma, mu, Rt, x0, a, eps=0.0, max_iter=K, kkt_every=0, record=True,
+                           momentum="constant", m_f=mf).trajectory
+        assert max(np.max(np.abs(u - w)) for u, w in zip(traj, traj2)) <= 1e-12
+
+
+def test_backtracking_rule():
+    """A trial step at or below 1/L_f is never shrunk (the iterates are the fixed-step ones);
+    from a 100x too long trial the accepted step stays in [rho/L_f, 100/L_f], every accepted
+    step satisfies the sufficient-decrease inequality, and the run reaches the exhaustive optimum."""
+    _, mu, L, Rt = small_problem(8, 50, seed=44, pct=70)
+    S = sigma_from_factor(L)
+    Lf = 2 * np.linalg.eigvalsh(S)[-1]
+    x0 = initial_point(mu, Rt)
+    fixed = npga(L, 0.0, mu, Rt, x0, 1.0 / Lf, eps=0.0, max_iter=60, kkt_every=0, record=True)
+    bt = npga(L, 0.0, mu, Rt, x0, 0.0, eps=0.0, max_iter=60, kkt_every=0, record=True,
+              backtrack=(1.0 / Lf, 0.5))
+    assert bt.alpha == 1.0 / Lf
+    assert all(np.array_equal(u, w) for u, w in zip(fixed.trajectory, bt.trajectory))
+    rho = 0.6
+    res = npga(L, 0.0, mu, Rt, x0, 0.0, eps=1e-11, max_iter=200000, backtrack=(100.0 / Lf, rho))
+    assert rho / Lf <= res.alpha <= 100.0 / Lf and res.alpha < 100.0 / Lf
+    assert res.converged
+    np.testing.assert_allclose(res.x, qp_bruteforce(S, mu, Rt), atol=1e-7)
+    # the printed inequality holds on an accepted step, and the evaluated quadratic form equals it
+    d = np.random.default_rng(2).standard_normal(8)
+    y = np.random.default_rng(3).standard_normal(8)
+    lhs = objective_sigma(S, 3e-5, y + d) - objective_sigma(S, 3e-5, y) - gradient_sigma(S, 3e-5, y) @ d
+    assert lhs == pytest.approx(objective(L, 3e-5, d), rel=1e-9)
+    short = npga_sigma(S, 0.0, mu, Rt, x0, 0.0, eps=0.0, max_iter=1, kkt_every=0, record=True,
+                       backtrack=(100.0 / Lf, rho))
+    y, x1, a1 = x0, short.trajectory[1], short.alpha
+    d = x1 - y
+    assert objective_sigma(S, 0.0, x1) <= (objective_sigma(S, 0.0, y) + gradient_sigma(S, 0.0, y) @ d
+                                           + d @ d / (2 * a1)) * (1 + 1e-12)
+    # the step before the accepted one failed the test (or was the first trial)
+    if a1 < 100.0 / Lf:
+        a0 = a1 / rho
+        p0 = project_F(y - a0 * gradient_sigma(S, 0.0, y), mu, Rt).x
+        d0 = p0 - y
+        assert objective_sigma(S, 0.0, p0) > (objective_sigma(S, 0.0, y) + gradient_sigma(S, 0.0, y) @ d0
+                                              + d0 @ d0 / (2 * a0))
+
+
+@pytest.mark.parametrize("mode", ["ge", "eq"])
+def test_dykstra_safeguard_matches_exact_projection(mode):
+    """Dykstra's alternating projections reach the exhaustive-search projection;
+    with a one-step bracketing budget the safeguarded projector falls back to it.
+    mu is drawn with both signs, so H is not nearly parallel to the simplex
+    plane (where alternating projections crawl)."""
+    rng = np.random.default_rng(17)
+    fell_back = 0
+    for _ in range(20):
+        n = int(rng.integers(2, 9))
+        v = rng.standard_normal(n) * 0.4
+        mu = np.sort(rng.uniform(-1.0, 1.0, n)) * 1e-2
+        mu[0], mu[-1] = -abs(mu[0]) - 2e-3, abs(mu[-1]) + 2e-3
+        R = float(np.quantile(mu, rng.uniform(0.3, 0.95)))
+        ref = project_bruteforce(v, mu, R, mode)
+        xd, sweeps = project_F_dykstra(v, mu, R, mode)
+        assert sweeps < 100000
+        np.testing.assert_allclose(xd, ref, atol=1e-9)
+        b = project_F(v, mu, R, mode, max_bracket=1)
+        r = project_F_safeguarded(v, mu, R, mode, max_bracket=1)
+        fell_back += b.status == PROJ_BRACKET
+        assert r.status == PROJ_OK
+        np.testing.assert_allclose(r.x, ref, atol=1e-9)
+    assert fell_back >= 5
 
 
 # ---------------------------------------------------------------- STR
