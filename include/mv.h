@@ -65,11 +65,19 @@ typedef enum {
 /* Storage layout of the factor L (n assets x T periods) in device memory. */
 typedef enum {
     MV_LAYOUT_NT = 0,  /* n x T row-major (one asset per row), leading dim >= T  */
-    MV_LAYOUT_TN = 1   /* L^T stored: T x n row-major (one period per row),
+    MV_LAYOUT_TN = 1,  /* L^T stored: T x n row-major (one period per row),
                           leading dim >= n.  The solve's products read it in
                           long runs along assets, which streams faster.  Only
                           centering, the gradient and the single-problem solves
                           (plain and refined) accept it.                        */
+    MV_LAYOUT_SIGMA = 2 /* not a factor: the problem's matrix is the explicit
+                          covariance Sigma itself, n x n FP32 (symmetric; only
+                          the entries on and above the diagonal are read),
+                          leading dim ld >= n (a multiple of 4).  The gradient is
+                          2 Sigma y + 2 gamma y (the classical model of Sec. 3's
+                          remark); T is not read.  Formed by mv_sigma_form.
+                          Accepted by mv_npga_workspace_size, mv_npga_solve,
+                          mv_npga_solve_refined and mv_gradient (with d_z NULL). */
 } mv_layout;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -223,8 +231,10 @@ typedef struct {
     double t_step_ms;         /* summed device time of those step (projection) launches  */
     int32_t proj_steps;       /* block-wide reductions spent by all projections          */
     int32_t refine_iterations;/* mv_npga_solve_refined: iterations of the FP32 phase     */
-    int32_t fused;            /* 1 if the loop used the fused single-pass product        */
-    double t_fused_ms;        /* summed device time of the timed fused-pass launches     */
+    int32_t fused;            /* 1: the loop used the fused single pass over L;
+                                 2: the symmetric pass over an explicit Sigma; 0: two
+                                 passes over L                                            */
+    double t_fused_ms;        /* summed device time of the timed single-pass products    */
 } mv_solve_info;
 
 void mv_solve_opts_default(mv_solve_opts *opts);
@@ -247,6 +257,31 @@ size_t mv_npga_workspace_size(const mv_problem *P);
  *  read the device-side convergence flag, and returns when the solve is done. */
 int mv_npga_solve(const mv_problem *P, const mv_solve_opts *opts, double *d_x_inout,
                   mv_solve_info *h_info, void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
+ * 3a'. Explicit covariance (Sec. 3, remark on the classical model).
+ *
+ *  mv_sigma_form writes Sigma = L L^T (n x n FP32, both triangles, exactly
+ *  symmetric) from the centered factor P->L (MV_LAYOUT_NT; F32, BF16 or
+ *  FP8 e4m3 with row scales).  Tensor cores (tcgen05, BF16 operands, FP32
+ *  accumulation) multiply only the tiles on and above the diagonal:
+ *    MV_BF16 / MV_FP8_E4M3  exact products of the stored values (FP8 values
+ *                           are BF16 values; the row scales multiply the
+ *                           result), FP32 sums;
+ *    MV_F32                 L = H + D split into two BF16 parts and
+ *                           Sigma = H H^T + H D^T + D H^T (three K-passes);
+ *                           per product term the error is below about
+ *                           2^-16 |L_it L_jt|, plus FP32 summation.
+ *  The solve then takes a problem with layout MV_LAYOUT_SIGMA, L = Sigma,
+ *  ld = ldS: each NPGA iteration reads the upper triangle of Sigma once
+ *  (n^2/2 FP32, held in L2 for n up to about 5500) instead of L twice.
+ *  d_ws: mv_sigma_workspace_size(P) bytes (256-byte aligned; the BF16
+ *  split or expansion of L, 2 n T or 4 n T bytes).  Blocking: returns
+ *  after the GEMM, MV_ERR_TIMEOUT if a pipeline wait gave up.
+ * ------------------------------------------------------------------------ */
+size_t mv_sigma_workspace_size(const mv_problem *P);
+int mv_sigma_form(const mv_problem *P, float *d_Sigma, int64_t ldS, void *d_ws, size_t ws_bytes,
+                  mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * 3b. Low-precision solve with FP32 refinement (an extension: the paper does

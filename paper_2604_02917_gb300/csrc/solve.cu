@@ -21,6 +21,7 @@
 #include "gemv.cuh"
 #include "llt_api.h"
 #include "project.cuh"
+#include "symv.cuh"
 
 namespace mv {
 
@@ -48,6 +49,9 @@ struct Plan {
     int n_groups, n_splits, n_cols;        // gemv_n grid
     bool use_llt;                          // fused single-pass L L^T y (llt.cuh)
     LltPlan lp;
+    bool sig;                              // explicit Sigma (symv.cuh) instead of a factor
+    int snb;                               // Sigma tile rows
+    size_t o_spart, o_stick, o_gobj;
     // workspace offsets (bytes)
     size_t o_state, o_x, o_y, o_gx, o_gy, o_g32, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
     size_t o_llt, o_err, o_zd;
@@ -146,6 +150,45 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows
     return p;
 }
 
+// Explicit Sigma (n x n FP32): the product is one symmetric pass (symv.cuh).
+static Plan make_plan_sigma(int64_t n, int64_t ld) {
+    Plan p{};
+    p.dt = MV_F32;
+    p.esize = 4;
+    p.vec = 4;
+    p.n = (int)n;
+    p.T = 0;
+    p.ld = ld;
+    p.gr = p.gc = (int)n;
+    p.sig = true;
+    p.cl = proj_cluster_size(n);
+    if (const char *env = getenv("MV_STEP_CLUSTER")) {
+        const int c = atoi(env);
+        if ((c == 1 || c == 2 || c == 4 || c == 8 || c == 16) && (n + c - 1) / c <= kProjMaxLocal) p.cl = c;
+    }
+    p.snb = (int)((n + kSymTile - 1) / kSymTile);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    p.o_state = take(sizeof(SolveState));
+    p.o_x = take(8 * (size_t)n);
+    p.o_y = take(8 * (size_t)n);
+    p.o_gx = take(8 * (size_t)n);
+    p.o_gy = take(8 * (size_t)n);
+    p.o_g32 = take(4 * (size_t)n);
+    p.o_y32 = take(4 * (size_t)n);
+    p.o_gobj = take(8 * (size_t)n);
+    p.o_spart = take(symv_part_bytes((int)n));
+    p.o_stick = take(4 * (size_t)p.snb);
+    p.o_z = p.o_zpart = p.o_gpart = p.o_tick_t = p.o_tick_n = p.o_g32;   // unused by this form
+    p.o_err = take(16);
+    p.total = off;
+    return p;
+}
+
 template <typename T_>
 static T_ *at(void *ws, size_t off) {
     return reinterpret_cast<T_ *>(reinterpret_cast<char *>(ws) + off);
@@ -232,27 +275,42 @@ __device__ __forceinline__ double sumsq_f32(const float *__restrict__ z, int T, 
     return v[0];
 }
 
-// lambda_hat = ||L^T u||^2; alpha = 1 / (2 (lambda_hat (1 + safety) + gamma)).
+// alpha = 1 / (2 (lambda_hat (1 + safety) + gamma)), or the override.
+__device__ __forceinline__ void set_step(SolveState *st, double lam, double gamma, double safety, double alpha_override) {
+    st->lambda_hat = lam;
+    double a = alpha_override;
+    if (!(a > 0.0)) {
+        const double lf = 2.0 * (lam * (1.0 + safety) + gamma);
+        a = lf > 0.0 ? 1.0 / lf : 1.0;
+    }
+    st->alpha = a;
+    if (!(a == a) || !isfinite(a)) st->status = MV_ERR_NUMERIC;
+}
+
+// lambda_hat = ||L^T u||^2.
 __device__ __forceinline__ void step_size_body(SolveState *st, const float *__restrict__ z, int T, double gamma, double safety,
                  double alpha_override) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
     const double lam = sumsq_f32(z, T, red);
-    if (threadIdx.x == 0) {
-        st->lambda_hat = lam;
-        double a = alpha_override;
-        if (!(a > 0.0)) {
-            const double lf = 2.0 * (lam * (1.0 + safety) + gamma);
-            a = lf > 0.0 ? 1.0 / lf : 1.0;
-        }
-        st->alpha = a;
-        if (!(a == a) || !isfinite(a)) st->status = MV_ERR_NUMERIC;
-    }
+    if (threadIdx.x == 0) set_step(st, lam, gamma, safety, alpha_override);
 }
 
 __global__ void __launch_bounds__(kStepThreads)
 step_size_kernel(SolveState *st, const float *__restrict__ z, int T, double gamma, double safety,
                  double alpha_override) {
     step_size_body(st, z, T, gamma, safety, alpha_override);
+}
+
+// Explicit Sigma: lambda_hat = u^T (Sigma u), the Rayleigh quotient of the
+// unit power vector u (equal to ||L^T u||^2 when Sigma = L L^T).
+__global__ void __launch_bounds__(kStepThreads)
+step_size_sigma_kernel(SolveState *st, const float *__restrict__ u, const double *__restrict__ su, int n, double gamma,
+                       double safety, double alpha_override) {
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    double v[1] = {0.0};
+    for (int i = threadIdx.x; i < n; i += kStepThreads) v[0] = fma((double)u[i], su[i], v[0]);
+    block_sum<1, kStepThreads>(v, red);
+    if (threadIdx.x == 0) set_step(st, v[0], gamma, safety, alpha_override);
 }
 
 // x^0: Pi_F(1/n 1), or the caller's x^0 when warm-starting; y^0 = x^0.
@@ -491,6 +549,19 @@ objective_kernel(SolveState *st, const float *__restrict__ z, int T, const doubl
     objective_body(st, z, T, x, n, gamma);
 }
 
+// Explicit Sigma: f(x) = x^T (Sigma x) + gamma ||x||^2.
+__global__ void __launch_bounds__(kStepThreads)
+objective_sigma_kernel(SolveState *st, const double *__restrict__ x, const double *__restrict__ sx, int n, double gamma) {
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        v[0] = fma(x[i], sx[i], v[0]);
+        v[1] = fma(x[i], x[i], v[1]);
+    }
+    block_sum<2, kStepThreads>(v, red);
+    if (threadIdx.x == 0) st->objective = v[0] + gamma * v[1];
+}
+
 // g = 2 (L z) + 2 gamma y   (gradient building block output).
 __global__ void grad_finish_kernel(const double *__restrict__ lz, const double *__restrict__ y, double gamma,
                                    double *__restrict__ g, int n) {
@@ -503,8 +574,10 @@ static int validate_problem(const mv_problem *P) {
     if (P == nullptr || P->L == nullptr || P->mu == nullptr) return MV_ERR_INVALID_ARG;
     if (P->dtype != MV_F32 && P->dtype != MV_BF16 && P->dtype != MV_FP8_E4M3) return MV_ERR_INVALID_ARG;
     if (P->mode != MV_RETURN_GE && P->mode != MV_RETURN_EQ) return MV_ERR_INVALID_ARG;
-    if (P->layout != MV_LAYOUT_NT && P->layout != MV_LAYOUT_TN) return MV_ERR_INVALID_ARG;
-    if (P->n < 1 || P->T < 1 || P->ld < (P->layout == MV_LAYOUT_TN ? P->n : P->T)) return MV_ERR_INVALID_ARG;
+    if (P->layout != MV_LAYOUT_NT && P->layout != MV_LAYOUT_TN && P->layout != MV_LAYOUT_SIGMA)
+        return MV_ERR_INVALID_ARG;
+    if (P->layout == MV_LAYOUT_SIGMA && P->dtype != MV_F32) return MV_ERR_INVALID_ARG;
+    if (P->n < 1 || P->T < 1 || P->ld < (P->layout == MV_LAYOUT_NT ? P->T : P->n)) return MV_ERR_INVALID_ARG;
     if (P->n > kProjMaxN || P->T > (1LL << 31) - 1) return MV_ERR_UNSUPPORTED;
     const int es = dtype_size(P->dtype);
     if (((uintptr_t)P->L) % 16 != 0 || (P->ld * es) % 16 != 0) return MV_ERR_INVALID_ARG;
@@ -514,10 +587,17 @@ static int validate_problem(const mv_problem *P) {
 }
 
 static bool is_tn(const mv_problem *P) { return P->layout == MV_LAYOUT_TN; }
+static bool is_sigma(const mv_problem *P) { return P->layout == MV_LAYOUT_SIGMA; }
+
+// The plan of a single-problem call: explicit Sigma, or a factor in either layout.
+static Plan plan_for(const mv_problem *P, bool fused) {
+    if (is_sigma(P)) return make_plan_sigma(P->n, P->ld);
+    return make_plan(P->dtype, P->n, P->T, P->ld, 0, fused, is_tn(P));
+}
 
 // The calls that read L only through the NT-layout kernels.
 static int require_nt(const mv_problem *P, const char *what) {
-    if (!is_tn(P)) return MV_OK;
+    if (P->layout == MV_LAYOUT_NT) return MV_OK;
     char msg[128];
     snprintf(msg, sizeof(msg), "%s: the factor must be stored n x T (MV_LAYOUT_NT)", what);
     return record_message(MV_ERR_UNSUPPORTED, msg);
@@ -697,6 +777,23 @@ static void launch_init_x(const Plan &p, const mv_problem *P, const double *x_in
     }
 }
 
+// Sigma y32 -> out64 (and out32) over the upper tiles of Sigma.
+static void launch_symv(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *out64,
+                        float *out32, cudaStream_t s) {
+    SymvArgs a;
+    a.S = reinterpret_cast<const float *>(P->L);
+    a.ld = P->ld;
+    a.n = p.n;
+    a.nb = p.snb;
+    a.y = y32;
+    a.part = at<float>(ws, p.o_spart);
+    a.tickets = at<unsigned>(ws, p.o_stick);
+    a.out64 = out64;
+    a.out32 = out32;
+    a.done = done;
+    symv_launch(a, s);
+}
+
 // One loop iteration.  With `ev` non-null, events ev[0..3] bracket gemv_t,
 // gemv_n and the step kernel (ev[3] is the next iteration's ev[0]); with the
 // fused pass, ev[0..1] bracket it and ev[1..2] is empty.
@@ -707,8 +804,11 @@ static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_o
     double *gy = at<double>(ws, p.o_gy);
     const int *done = &st->done;
     if (ev) cudaEventRecord(ev[0], s);
-    if (p.use_llt) {
-        MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s));
+    if (p.use_llt || p.sig) {
+        if (p.sig)
+            launch_symv(p, P, y32, ws, done, gy, nullptr, s);
+        else
+            MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s));
         if (ev) cudaEventRecord(ev[1], s);
         if (ev) cudaEventRecord(ev[2], s);
         launch_step(p, P, O, ws, s);
@@ -766,7 +866,7 @@ static std::unordered_map<GraphKey, cudaGraphExec_t, GraphKeyHash> g_graphs;
 static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
                            const cudaEvent_t *ev, cudaGraphExec_t *out) {
     GraphKey key{P->L, P->mu, P->row_scale, ws, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
-                 O->max_iter, chunk, p.use_llt ? 1 : 0, P->R_target, P->gamma, O->eps, (const void *)ev};
+                 O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? 1 : 0), P->R_target, P->gamma, O->eps, (const void *)ev};
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_graph_mu);
@@ -828,14 +928,14 @@ void mv_solve_opts_default(mv_solve_opts *o) {
 
 size_t mv_npga_workspace_size(const mv_problem *P) {
     if (validate_problem(P) != MV_OK) return 0;
-    return make_plan(P->dtype, P->n, P->T, P->ld, 0, true, is_tn(P)).total;
+    return plan_for(P, true).total;
 }
 
 int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g, void *d_ws, size_t ws_bytes,
                 mv_stream_t stream) {
     MV_TRY(validate_problem(P));
-    if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, d_z == nullptr, is_tn(P));
+    if (d_y == nullptr || d_g == nullptr || (is_sigma(P) && d_z != nullptr)) return MV_ERR_INVALID_ARG;
+    const Plan p = plan_for(P, d_z == nullptr);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();
@@ -846,7 +946,10 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
     const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
     to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(d_y, rs, y32, p.n);
-    if (p.use_llt) {
+    if (p.sig) {
+        MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_stick), 0, 4 * (size_t)p.snb, s));
+        launch_symv(p, P, y32, d_ws, nullptr, lz, nullptr, s);
+    } else if (p.use_llt) {
         MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
         MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
         MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, lz, nullptr, s));
@@ -866,7 +969,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, O.two_pass == 0, is_tn(P));
+    const Plan p = plan_for(P, O.two_pass == 0);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();   // start from a clean error state
@@ -880,12 +983,16 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
     if (p.use_llt) MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
+    if (p.sig) MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_stick), 0, 4 * (size_t)p.snb, s));
     setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
     // Power method for ||L_eff||_2^2 (skipped when the step is given).
     int launches = 4;
     if (!(O.alpha > 0.0)) {
         for (int it = 0; it < O.power_iters; ++it) {
-            if (p.use_llt) {
+            if (p.sig) {
+                launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s);
+                launches += 2;
+            } else if (p.use_llt) {
                 MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
                 launches += 2;
             } else {
@@ -894,16 +1001,23 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
             }
             power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
         }
-        gemv_t_only(p, P, y32, d_ws, s);
+        if (p.sig)
+            launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), nullptr, s);
+        else
+            gemv_t_only(p, P, y32, d_ws, s);
         launches += 1;
     }
-    step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0) ? 0 : p.T, P->gamma,
-                                                O.power_safety, O.alpha);
+    if (p.sig)
+        step_size_sigma_kernel<<<1, kStepThreads, 0, s>>>(st, y32, at<double>(d_ws, p.o_gy), (O.alpha > 0.0) ? 0 : p.n,
+                                                          P->gamma, O.power_safety, O.alpha);
+    else
+        step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0) ? 0 : p.T, P->gamma,
+                                                    O.power_safety, O.alpha);
     launch_init_x(p, P, O.warm_start ? d_x_inout : nullptr, d_ws, s);
     MV_CUDA_TRY(cudaGetLastError());
 
     const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
-    const int per_iter = p.use_llt ? 2 : 3;
+    const int per_iter = (p.use_llt || p.sig) ? 2 : 3;
     const cudaEvent_t *ev = nullptr;
     if (O.timing) MV_TRY(timing_events(3 * chunk + 1, &ev));
     // Events recorded by graph nodes cannot be timed, so a timed solve issues
@@ -945,11 +1059,17 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
         if (hs.done) break;
     }
     launches += 3;
-    // Objective of the returned iterate: one more pass z = L^T x.
+    // Objective of the returned iterate: one more pass z = L^T x (or Sigma x).
     to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(at<double>(d_ws, p.o_x), rs, y32, p.n);
-    gemv_t_only(p, P, y32, d_ws, s);
-    objective_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), p.T, at<double>(d_ws, p.o_x), p.n,
-                                                P->gamma);
+    if (p.sig) {
+        launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gobj), nullptr, s);
+        objective_sigma_kernel<<<1, kStepThreads, 0, s>>>(st, at<double>(d_ws, p.o_x), at<double>(d_ws, p.o_gobj), p.n,
+                                                          P->gamma);
+    } else {
+        gemv_t_only(p, P, y32, d_ws, s);
+        objective_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), p.T, at<double>(d_ws, p.o_x), p.n,
+                                                    P->gamma);
+    }
     MV_CUDA_TRY(cudaMemcpyAsync(d_x_inout, at<double>(d_ws, p.o_x), 8 * (size_t)p.n, cudaMemcpyDeviceToDevice, s));
     MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     int xerr = 0;
@@ -972,10 +1092,11 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     h_info->nu = hs.nu;
     h_info->launches = launches;
     h_info->timed_pairs = timed;
-    h_info->t_gemv_t_ms = p.use_llt ? 0.0 : t_t;
-    h_info->t_gemv_n_ms = p.use_llt ? 0.0 : t_n;
-    h_info->t_fused_ms = p.use_llt ? t_t : 0.0;
-    h_info->fused = p.use_llt ? 1 : 0;
+    const bool one_pass = p.use_llt || p.sig;
+    h_info->t_gemv_t_ms = one_pass ? 0.0 : t_t;
+    h_info->t_gemv_n_ms = one_pass ? 0.0 : t_n;
+    h_info->t_fused_ms = one_pass ? t_t : 0.0;
+    h_info->fused = p.sig ? 2 : (p.use_llt ? 1 : 0);
     h_info->t_step_ms = t_s;
     h_info->proj_steps = hs.proj_steps;
     return h_info->status;
@@ -1344,7 +1465,9 @@ static void frontier_ltx(const CUtensorMap *maps, const Plan &p, const FPlan &f,
 extern "C" {
 
 size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets) {
-    if (validate_problem(P) != MV_OK || is_tn(P) || P->dtype == MV_F32 || n_targets < 1 || n_targets > 128) return 0;
+    if (validate_problem(P) != MV_OK || P->layout != MV_LAYOUT_NT || P->dtype == MV_F32 || n_targets < 1 ||
+        n_targets > 128)
+        return 0;
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
     return make_fplan(p, n_targets).total;
 }
@@ -1697,7 +1820,7 @@ static BPlan make_bplan(const Plan &p, int K, int C) {
 extern "C" {
 
 size_t mv_backward_workspace_size(const mv_problem *P, const mv_solve_opts *O_in) {
-    if (validate_problem(P) != MV_OK || is_tn(P) || P->dtype != MV_F32) return 0;
+    if (validate_problem(P) != MV_OK || P->layout != MV_LAYOUT_NT || P->dtype != MV_F32) return 0;
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 1 || O.checkpoint_every < 1) return 0;
@@ -2432,6 +2555,7 @@ extern "C" int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float
                                    mv_stream_t stream) {
     MV_TRY(validate_problem(P));
     if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
+    if (is_sigma(P)) return record_message(MV_ERR_UNSUPPORTED, "mv_gradient_noalloc: explicit Sigma is not supported");
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, false, is_tn(P));
     if (p.total > MV_NOALLOC_SCRATCH_BYTES) {
         char msg[200];

@@ -20,13 +20,13 @@ MV_OK, MV_ERR_INVALID_ARG, MV_ERR_INFEASIBLE, MV_ERR_NOT_CONVERGED = 0, 1, 2, 3
 MV_ERR_TIMEOUT, MV_ERR_NUMERIC, MV_ERR_CUDA, MV_ERR_UNSUPPORTED, MV_ERR_WORKSPACE = 4, 5, 6, 7, 8
 MV_F32, MV_BF16, MV_FP8_E4M3 = 0, 1, 2
 MV_RETURN_GE, MV_RETURN_EQ = 0, 1
-MV_LAYOUT_NT, MV_LAYOUT_TN = 0, 1
+MV_LAYOUT_NT, MV_LAYOUT_TN, MV_LAYOUT_SIGMA = 0, 1, 2
 
 DTYPES = {"f32": MV_F32, "bf16": MV_BF16, "fp8": MV_FP8_E4M3}
 _ESIZE = {MV_F32: 4, MV_BF16: 2, MV_FP8_E4M3: 1}
 _TORCH = {MV_F32: torch.float32, MV_BF16: torch.bfloat16, MV_FP8_E4M3: torch.uint8}
 MODES = {"ge": MV_RETURN_GE, "eq": MV_RETURN_EQ}
-LAYOUTS = {"nt": MV_LAYOUT_NT, "tn": MV_LAYOUT_TN}
+LAYOUTS = {"nt": MV_LAYOUT_NT, "tn": MV_LAYOUT_TN, "sigma": MV_LAYOUT_SIGMA}
 
 # Every symbol include/mv.h declares (checked by the CPU test suite).
 EXPORTS = [
@@ -35,7 +35,8 @@ EXPORTS = [
     "mv_gradient_noalloc", "mv_npga_solve_refined", "mv_sketch", "mv_str_workspace_size", "mv_str_truncate",
     "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
     "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch", "mv_center_host_workspace_size",
-    "mv_center_factor_host", "mv_batch_tiles", "mv_str_truncate_knee",
+    "mv_center_factor_host", "mv_batch_tiles", "mv_str_truncate_knee", "mv_sigma_workspace_size",
+    "mv_sigma_form",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -102,6 +103,10 @@ def lib():
         L.mv_center_workspace_size.argtypes = [i64, i64]
         L.mv_center_factor.restype = i32
         L.mv_center_factor.argtypes = [vp, i64, i64, i64, i32, i32, vp, i64, vp, vp, vp, vp, sz, vp]
+        L.mv_sigma_workspace_size.restype = sz
+        L.mv_sigma_workspace_size.argtypes = [C.POINTER(Problem)]
+        L.mv_sigma_form.restype = i32
+        L.mv_sigma_form.argtypes = [C.POINTER(Problem), vp, i64, vp, sz, vp]
         L.mv_batch_tiles.restype = i32
         L.mv_batch_tiles.argtypes = [C.POINTER(Problem), i64, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.mv_center_host_workspace_size.restype = sz
@@ -266,7 +271,8 @@ def project(v: torch.Tensor, mu: torch.Tensor, R_target, mode: str = "ge"):
 def make_problem(L: torch.Tensor, mu: torch.Tensor, R_target: float, T: int, gamma: float = 0.0,
                  dtype: str = "f32", row_scale: torch.Tensor | None = None, mode: str = "ge",
                  power_start: torch.Tensor | None = None, layout: str = "nt") -> Problem:
-    """mv_problem over L as center_factor returns it (n x ld for "nt", T x ld for "tn")."""
+    """mv_problem over L as center_factor returns it (n x ld for "nt", T x ld for "tn"),
+    or over an explicit n x ld covariance from sigma_form ("sigma"; T is not read)."""
     assert L.is_cuda and L.dim() == 2 and L.stride(1) == 1
     p = Problem()
     p.L = L.data_ptr()
@@ -276,12 +282,28 @@ def make_problem(L: torch.Tensor, mu: torch.Tensor, R_target: float, T: int, gam
     p.reserved = 0
     p.row_scale = None if row_scale is None else row_scale.data_ptr()
     n = L.shape[0] if p.layout == MV_LAYOUT_NT else mu.shape[0]
-    p.n, p.T, p.ld = n, int(T), L.stride(0)
+    p.n, p.T, p.ld = n, max(1, int(T)), L.stride(0)
     p.gamma = float(gamma)
     p.mu = mu.data_ptr()
     p.R_target = float(R_target)
     p.power_start = None if power_start is None else power_start.data_ptr()
     return p
+
+
+def sigma_form(L: torch.Tensor, T: int, dtype: str = "f32", row_scale: torch.Tensor | None = None):
+    """Sigma = L L^T (n x ld FP32, ld = n rounded up to 4) from the n x ld factor
+    (mv_sigma_form: tcgen05, upper tiles only, both triangles written)."""
+    n = L.shape[0]
+    mu = torch.zeros(n, dtype=torch.float64, device=L.device)
+    p = make_problem(L, mu, 0.0, T, 0.0, dtype, row_scale)
+    nb = lib().mv_sigma_workspace_size(C.byref(p))
+    if nb == 0:
+        raise MvError(MV_ERR_INVALID_ARG, "mv_sigma_workspace_size")
+    ws = _workspace(nb, L.device)
+    ldS = (n + 3) // 4 * 4
+    S = torch.zeros((n, ldS), dtype=torch.float32, device=L.device)
+    _check(lib().mv_sigma_form(C.byref(p), _ptr(S), ldS, _ptr(ws), ws.numel(), _stream()), "mv_sigma_form")
+    return S
 
 
 def solve_opts(**kw) -> SolveOpts:
@@ -323,6 +345,7 @@ class Solver:
     def gradient(self, y: torch.Tensor, with_z: bool = True):
         """(z, g); with ``with_z=False`` z is None and g comes from the fused
         single pass over L where that applies."""
+        with_z = with_z and self.problem.layout != MV_LAYOUT_SIGMA
         z = torch.empty(self.problem.T, dtype=torch.float32, device=y.device) if with_z else None
         g = torch.empty_like(y)
         _check(lib().mv_gradient(C.byref(self.problem), _ptr(y), _ptr(z) if with_z else None, _ptr(g),
