@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--no-frontier", action="store_true", help="skip the 64-target frontier measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem uneven batch")
+    ap.add_argument("--no-sigma", action="store_true", help="skip the explicit-covariance measurement")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
@@ -92,6 +93,15 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM, "fallback"
+
+
+def peaks_tensor():
+    """Measured dense BF16 tensor peak (burst; the formation GEMM is timed alone)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return 1900.0
 
 
 # kernel -> (committed ncu summary, source file whose hash the summary records)
@@ -286,14 +296,24 @@ def main():
     L, rs, mu, tr = mv.center_factor(R_dev, args.dtype, layout=args.layout)
     Rt = float(np.percentile(mu.cpu().numpy(), 60))
     r0 = torch.from_numpy(power_start(model.n)).to(dev)
+    # The timed solves replay each chunk of kkt_every iterations as one CUDA
+    # graph (the product path); a separate solve issues every launch from the
+    # host between CUDA events for the per-kernel breakdown and the roofline.
     solver = mv.Solver(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
-                       timing=1, layout=args.layout, two_pass=1 if args.two_pass else 0)
+                       layout=args.layout, two_pass=1 if args.two_pass else 0)
     del R_dev
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+
+    def launch_profile(*a, **kw):
+        sv = mv.Solver(*a, timing=1, **kw)
+        sv.solve()
+        out = [sv.solve()[1] for _ in range(2)]
+        del sv
+        return out
 
     for _ in range(args.warmup):
         solver.solve()
@@ -315,9 +335,11 @@ def main():
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
+    tinfos = launch_profile(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
+                            layout=args.layout, two_pass=1 if args.two_pass else 0)
 
     # roofline of the dominant kernel (per-launch CUDA events around every loop launch)
-    roof = roofline(infos, model, args.dtype, args.layout)
+    roof = roofline(tinfos, model, args.dtype, args.layout)
     es = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
     nT = model.n * model.T
 
@@ -383,12 +405,13 @@ def main():
         for name, LL, rr, lay, two in ((f"{args.dtype}_{args.layout}_two_pass", L, rs, args.layout, 1),
                                        (f"{args.dtype}_{other}_fused", Lo, rso, other, 0),
                                        (f"{args.dtype}_{other}_two_pass", Lo, rso, other, 1)):
-            sv = mv.Solver(LL, mu, Rt, model.T, dtype=args.dtype, row_scale=rr, power_start=r0, eps=args.eps,
-                           timing=1, two_pass=two, layout=lay)
+            kw = dict(dtype=args.dtype, row_scale=rr, power_start=r0, eps=args.eps, two_pass=two, layout=lay)
+            sv = mv.Solver(LL, mu, Rt, model.T, **kw)
             t, vinfos = timed_solves(sv)
+            pinfos = launch_profile(LL, mu, Rt, model.T, **kw)
             variants[name] = {"value": t, "unit": "s", "iterations": vinfos[-1]["iterations"],
                               "kkt": vinfos[-1]["kkt"], "objective": vinfos[-1]["objective"],
-                              "fused": vinfos[-1]["fused"], "roofline": roofline(vinfos, model, args.dtype, lay)}
+                              "fused": vinfos[-1]["fused"], "roofline": roofline(pinfos, model, args.dtype, lay)}
             del sv
         del Lo, rso
     if not args.no_variants and args.dtype == "f32":
@@ -413,6 +436,56 @@ def main():
                 "rel_obj_vs_fp32": (vi["objective"] - infos[-1]["objective"]) / infos[-1]["objective"]}
             del Llo, rslo, rsv
         del R_dev
+
+    # Explicit covariance (Sec. 3 remark): Sigma = L L^T once on tcgen05, then
+    # NPGA with one symmetric pass over the upper triangle of Sigma per iteration.
+    sigma = None
+    if not args.no_sigma and args.dtype == "f32":
+        R_dev = torch.from_numpy(R32).to(dev)
+        sigma = {}
+        peak_tf = peaks_tensor()
+        for sdt in ("f32", "bf16"):
+            Lx, rsx, _, _ = mv.center_factor(R_dev, sdt, layout="nt")
+            S = mv.sigma_form(Lx, model.T, sdt, rsx)              # warm-up (attributes, tensor maps)
+            ft = []
+            for _ in range(3):
+                f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                f0.record(stream)
+                S = mv.sigma_form(Lx, model.T, sdt, rsx)
+                f1.record(stream)
+                torch.cuda.synchronize()
+                ft.append(f0.elapsed_time(f1) / 1e3)
+            t_form = float(np.median(ft))
+            nb = -(-model.n // 128)
+            segs = 3 if sdt == "f32" else 1
+            flops = nb * (nb + 1) // 2 * 128 * 128 * (-(-model.T // 64) * 64) * 2 * segs
+            entry = {"form_s": t_form,
+                     "form_roofline": {"bound": "tensor", "achieved": round(flops / t_form / 1e12, 1),
+                                       "peak": peak_tf, "unit": "TFLOP/s",
+                                       "frac": round(flops / t_form / 1e12 / peak_tf, 4), "traffic": None,
+                                       "kernel": "sigma_gemm", "flops_per_launch": flops,
+                                       "note": "executed BF16 tile flops (upper tiles x segments)"}}
+            sv = mv.Solver(S, mu, Rt, model.T, power_start=r0, eps=args.eps, layout="sigma")
+            t_solve, vinfos = timed_solves(sv)
+            pinfos = launch_profile(S, mu, Rt, model.T, power_start=r0, eps=args.eps, layout="sigma")
+            pairs = max(sum(i["timed_pairs"] for i in pinfos), 1)
+            symv_us = sum(i["t_fused_ms"] for i in pinfos) / pairs * 1e3
+            tri = model.n * (model.n + 1) // 2 * 4
+            entry.update({"solve_s": t_solve, "total_s": t_form + t_solve,
+                          "iterations": vinfos[-1]["iterations"], "kkt": vinfos[-1]["kkt"],
+                          "objective": vinfos[-1]["objective"],
+                          "rel_obj_vs_factor_solve": (vinfos[-1]["objective"] - infos[-1]["objective"])
+                          / infos[-1]["objective"],
+                          "symv": {"avg_launch_us": round(symv_us, 2), "tri_bytes": tri,
+                                   "GBps": round(tri / (symv_us * 1e-6) / 1e9, 1),
+                                   "note": "upper triangle of Sigma per launch; event-timed host-issued "
+                                           "launches (includes enqueue gaps; the ncu launch list has "
+                                           "device durations)"},
+                          "step_kernel_avg_us": round(sum(i["t_step_ms"] for i in pinfos) / pairs * 1e3, 2)})
+            sigma[sdt + "_L"] = entry
+            del sv, S, Lx, rsx
+        del R_dev
+        torch.cuda.empty_cache()
 
     # Sketch (tcgen05 BF16 GEMM) + FP64 truncation + NPGA on the STR model.
     str_res = None
@@ -592,7 +665,8 @@ def main():
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "variants": variants, "str": str_res, "frontier": frontier, "adjoint": adj, "batch": batch}
+                "variants": variants, "sigma": sigma, "str": str_res, "frontier": frontier, "adjoint": adj,
+                "batch": batch}
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

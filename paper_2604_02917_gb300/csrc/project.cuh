@@ -35,6 +35,14 @@
 //    one thread per block.
 // The warm start (nu, tau of the previous call) only changes where the
 // search begins, never the point it returns: the projection is unique.
+// Warm-start shortcut: the support S0 at the hint gives, from the same
+// reduction, the exact solution (nu*, tau*) of the budget and return rows on
+// S0 (tau* alone at nu = 0 when the hint says the return row is inactive).
+// The next reduction, at (nu*, tau*), also counts the elements whose
+// membership differs from S0; none means S0 is the support at (nu*, tau*),
+// so (nu*, tau*) is exact and the search ends after two reductions (the
+// general search needs four when the support does not move).  Otherwise the
+// general search continues from (nu*, tau*).
 #pragma once
 
 #include <cooperative_groups.h>
@@ -135,6 +143,9 @@ struct ProjSmem {
     double nu, tau, dbcast, dmin, dmax;
     double mpart[2][kProjMaxCL][2];
     float nu32, tau32;
+    double nu0, tau0;                   // hint whose support a verifying step compares against
+    float nu032, tau032;
+    int verify;
     int done, status, steps;
     int s_v, s_m, s_mv, s_mm;
     double p_v, p_m, p_mv, p_mm;        // 2^-s of the four scales
@@ -143,7 +154,10 @@ struct ProjSmem {
 
 // Must run once per block before the first reduction (all threads).
 __device__ inline void proj_smem_init(ProjSmem *sh) {
-    if (threadIdx.x == 0) sh->parity = 0;
+    if (threadIdx.x == 0) {
+        sh->parity = 0;
+        sh->verify = 0;
+    }
     __syncthreads();
 }
 
@@ -415,27 +429,38 @@ struct ClusterProj {
         __syncthreads();
     }
 
+    // i in S(nu, tau), i.e. fma(nu, mu_i, v_i) > tau in FP64, screened in FP32
+    // with a proven margin (the FP64 test runs only inside it).
+    __device__ __forceinline__ bool member(int i, double nu, double tau, float nu32, float tau32, float anu,
+                                           float atau, bool &nan) const {
+        const float c = 2.384185791015625e-07f;   // 2^-22
+        const float v32 = el.v32[i], m32 = el.mu32[i];
+        const float d = fmaf(nu32, m32, v32) - tau32;
+        const float margin = c * (fmaf(anu, fabsf(m32), fabsf(v32)) + atau);
+        if (d > margin) return true;
+        if (d < -margin) return false;
+        const double w = fma(nu, el.mu[i], el.v[i]);
+        if (!(w == w)) nan = true;
+        return w > tau;
+    }
+
     // Sums over S = {i : fma(nu, mu_i, v_i) > tau}; totals valid in thread 0.
+    // Slot 5: .lo counts NaNs met, .hi (when sh->verify) the elements whose
+    // membership differs from S(sh->nu0, sh->tau0).
     __device__ void support_sums(double nu, double tau, float nu32, float tau32, I128 (&out)[6]) {
         I128 a[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) a[k] = I128{0ull, 0ll};
         const float anu = fabsf(nu32), atau = isinf(tau32) ? 0.f : fabsf(tau32);
-        const float c = 2.384185791015625e-07f;   // 2^-22
+        const bool verify = sh->verify != 0;
+        const double nu0 = sh->nu0, tau0 = sh->tau0;
+        const float nu032 = sh->nu032, tau032 = sh->tau032;
+        const float anu0 = fabsf(nu032), atau0 = isinf(tau032) ? 0.f : fabsf(tau032);
+        bool nan = false;
+        long long diff = 0;
         for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-            const float v32 = el.v32[i], m32 = el.mu32[i];
-            const float d = fmaf(nu32, m32, v32) - tau32;
-            const float margin = c * (fmaf(anu, fabsf(m32), fabsf(v32)) + atau);
-            bool in;
-            if (d > margin) {
-                in = true;
-            } else if (d < -margin) {
-                in = false;
-            } else {
-                const double w = fma(nu, el.mu[i], el.v[i]);   // exact decision in FP64
-                in = (w > tau);
-                if (!(w == w)) a[5].lo = 1;                      // NaN seen
-            }
+            const bool in = member(i, nu, tau, nu32, tau32, anu, atau, nan);
+            if (verify && in != member(i, nu0, tau0, nu032, tau032, anu0, atau0, nan)) ++diff;
             if (in) {
                 a[0].lo += 1;
                 add128(a[1], el.V[i]);
@@ -444,6 +469,8 @@ struct ClusterProj {
                 add128(a[4], el.MM[i]);
             }
         }
+        a[5].lo = nan ? 1ull : 0ull;
+        a[5].hi = diff;
         reduce6(a, out);
     }
 
@@ -453,11 +480,13 @@ struct ClusterProj {
         // Thread-0-owned search state.
         double lo = -INFINITY, hi = INFINITY, nu = 0.0, tau = -INFINITY, prev_cnt = -1.0;
         bool have_lo = false, have_hi = false, zero_done = false, first = true;
+        bool try_fast = true, verifying = false;
         int outer = 0, inner = 0, status = MV_OK;
         const bool ge = (mode == MV_RETURN_GE);
         if (threadIdx.x == 0) {
             sh->steps = 0;
             sh->done = 0;
+            sh->verify = 0;
             if (!(R <= mu_max) || (!ge && !(R >= mu_min))) {
                 sh->done = 1;
                 sh->status = MV_ERR_INFEASIBLE;
@@ -490,11 +519,53 @@ struct ClusterProj {
                 const double sm = i128_to_double(S[2]) * sh->p_m;
                 const double smv = i128_to_double(S[3]) * sh->p_mv;
                 const double smm = i128_to_double(S[4]) * sh->p_mm;
-                bool finish = false;
+                bool finish = false, handled = false;
                 double next_nu = enu, next_tau = etau;
                 if (S[5].lo != 0) {
                     status = MV_ERR_NUMERIC;
                     finish = true;
+                    handled = true;
+                } else if (verifying) {
+                    // the candidate was built on S(nu0, tau0); it is exact iff the support is unchanged
+                    verifying = false;
+                    sh->verify = 0;
+                    if (S[5].hi == 0) {
+                        nu = enu;
+                        tau = etau;
+                        finish = true;
+                        handled = true;
+                    }
+                } else if (try_fast && cnt > 0.0) {
+                    try_fast = false;
+                    const double a = cnt, b = sm, c = smm;
+                    double nc = NAN, tc = NAN;
+                    bool ok = false;
+                    if (ge && enu == 0.0) {            // hint: return row inactive; simplex threshold on S0
+                        tc = (sv - 1.0) / a;
+                        nc = 0.0;
+                        ok = (smv - tc * b) - R >= 0.0;
+                    } else {
+                        const double det = a * c - b * b;
+                        if (det > 1e-13 * a * c) {
+                            nc = (b * (sv - 1.0) - a * (smv - R)) / det;
+                            tc = (fma(nc, b, sv) - 1.0) / a;
+                            ok = !ge || nc >= 0.0;
+                        }
+                    }
+                    if (ok && nc == nc && tc == tc && isfinite(nc) && isfinite(tc)) {
+                        sh->nu0 = enu;
+                        sh->tau0 = etau;
+                        sh->nu032 = enu32;
+                        sh->tau032 = etau32;
+                        sh->verify = 1;
+                        verifying = true;
+                        next_nu = nc;
+                        next_tau = tc;
+                        handled = true;
+                    }
+                }
+                if (handled) {
+                    // decided above
                 } else if (cnt == 0.0) {               // tau >= max w: restart from the left
                     next_tau = -INFINITY;
                     first = true;

@@ -9,11 +9,13 @@
 // and a diagonal tile gives Sigma_II y_I.  Block row b thus receives exactly
 // nb partial vectors, one per tile it meets; tile (I, J) stores its two into
 // slot J of block I and slot I of block J.  The CTA that brings a block
-// row's ticket to nb sums its nb slots in slot order in FP64 (fixed order:
-// the result does not depend on CTA timing) and resets the ticket.
+// row's ticket to nb sums its nb slots in slot order (FP32 with a
+// compensation term; fixed order: the result does not depend on CTA timing)
+// and resets the ticket.
 //
 // Per CTA: 8 warps x 16 rows, a lane owns 4 consecutive columns (one 16-byte
-// load per row, 512 contiguous bytes per warp-row).  Column sums over a
+// load per row, 512 contiguous bytes per warp-row); a thread issues its 16
+// loads back to back before using any of them.  Column sums over a
 // warp's 16 rows stay in registers and are added across warps through
 // shared memory; the 16 row dot products of a warp are reduced across lanes
 // by halving exchanges (8 + 4 + 2 + 1 + 1 shuffles for 16 rows).
@@ -45,42 +47,39 @@ inline size_t symv_part_bytes(int n) {
     return (size_t)nb * (size_t)(nb * kSymTile) * 4;
 }
 
-__device__ __forceinline__ float4 symv_load(const float *S, int64_t ld, int r, int c, int n) {
-    if (r >= n || c >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
+// L2 policy for Sigma: evict last, so the triangle stays resident from one
+// iteration to the next.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ float4 symv_ld(const float *p, uint64_t pol) {
     float4 v;
-    asm("ld.global.nc.v4.f32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
         : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-        : "l"(S + (int64_t)r * ld + c));
-    // columns past n (inside the leading dimension) are not part of Sigma
-    if (c + 3 >= n) {
-        if (c + 1 >= n) v.y = 0.f;
-        if (c + 2 >= n) v.z = 0.f;
-        if (c + 3 >= n) v.w = 0.f;
-    }
+        : "l"(p), "l"(pol));
     return v;
 }
 
-// Sum the nb slots of block row b in slot order (FP64) and publish.
+// Sum the nb slots of block row b in slot order and publish.  FP32 with a
+// compensation term (the partials are FP32; FP64 arithmetic is scarce on
+// this part), one conversion to FP64 at the end.
 __device__ __forceinline__ void symv_finish_block(const SymvArgs &a, int b) {
     const int stride = a.nb * kSymTile;
     for (int i = threadIdx.x; i < kSymTile; i += kSymThreads) {
         const int r = b * kSymTile + i;
         if (r >= a.n) continue;
-        double s = 0.0;
-        int j = 0;
-        for (; j + 4 <= a.nb; j += 4) {
-            const float p0 = __ldcg(a.part + (int64_t)j * stride + r);
-            const float p1 = __ldcg(a.part + (int64_t)(j + 1) * stride + r);
-            const float p2 = __ldcg(a.part + (int64_t)(j + 2) * stride + r);
-            const float p3 = __ldcg(a.part + (int64_t)(j + 3) * stride + r);
-            s += (double)p0;
-            s += (double)p1;
-            s += (double)p2;
-            s += (double)p3;
+        float s = 0.f, c = 0.f;
+        for (int j = 0; j < a.nb; ++j) {
+            const float y = __ldcg(a.part + (int64_t)j * stride + r) - c;
+            const float t = s + y;
+            c = (t - s) - y;
+            s = t;
         }
-        for (; j < a.nb; ++j) s += (double)__ldcg(a.part + (int64_t)j * stride + r);
-        a.out64[r] = s;
-        if (a.out32) a.out32[r] = (float)s;
+        a.out64[r] = (double)s - (double)c;
+        if (a.out32) a.out32[r] = s;
     }
 }
 
@@ -105,15 +104,32 @@ __global__ void __launch_bounds__(kSymThreads) symv_kernel(SymvArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int rw = warp * kSymRowsPerWarp;
     const int col = c0 + 4 * lane;
+    // All 16 loads are issued before any use: addresses are clamped into the
+    // matrix (row n-1, the last 4-column group), and what the clamp brings in
+    // is cancelled below (zero y entries for rows, masks for columns).
+    const uint64_t pol = l2_evict_last();
+    const int cl = min(col, (a.n - 1) & ~3);
     float4 v[kSymRowsPerWarp];
 #pragma unroll
-    for (int j = 0; j < kSymRowsPerWarp; ++j) v[j] = symv_load(a.S, a.ld, r0 + rw + j, col, a.n);
+    for (int j = 0; j < kSymRowsPerWarp; ++j) {
+        const int r = min(r0 + rw + j, a.n - 1);
+        v[j] = symv_ld(a.S + (int64_t)r * a.ld + cl, pol);
+    }
+    if (col + 3 >= a.n) {          // the last column block only: columns past n are not Sigma's
+#pragma unroll
+        for (int j = 0; j < kSymRowsPerWarp; ++j) {
+            v[j].x = col + 0 < a.n ? v[j].x : 0.f;
+            v[j].y = col + 1 < a.n ? v[j].y : 0.f;
+            v[j].z = col + 2 < a.n ? v[j].z : 0.f;
+            v[j].w = col + 3 < a.n ? v[j].w : 0.f;
+        }
+    }
     const float4 yj = *reinterpret_cast<const float4 *>(&yJ[4 * lane]);
     float cx = 0.f, cy = 0.f, cz = 0.f, cw = 0.f;
     float rp[kSymRowsPerWarp];
 #pragma unroll
     for (int j = 0; j < kSymRowsPerWarp; ++j) {
-        const float yi = yI[rw + j];
+        const float yi = yI[rw + j];          // 0 for rows past n
         cx = fmaf(v[j].x, yi, cx);
         cy = fmaf(v[j].y, yi, cy);
         cz = fmaf(v[j].z, yi, cz);
