@@ -2,6 +2,10 @@
 
 * ``sketch``      -- tilde L = L Phi (Sec. 2.3 / 2.5 step 1).  Phi is handed
   in as its transpose (s x T, one sketch column per row).
+* ``countsketch_matrix`` / ``countsketch`` -- the sparse map of Sec. 2.3,
+  construction (2): Phi(t, h(t)) = s_t, every other entry 0, and
+  tilde L = L Phi, i.e. column j of tilde L is the signed sum of the
+  columns t of L hashed to j.
 * ``truncate``    -- thin SVD of tilde L kept to rank l (Sec. 2.5 step 2),
   computed here from the eigendecomposition of tilde L tilde L^T (n x n):
   its eigenvalues are sigma_i^2 and its eigenvectors are U.  The effective
@@ -21,6 +25,20 @@ import numpy as np
 
 def sketch(L, Phi_t):
     return np.asarray(L, dtype=np.float64) @ np.asarray(Phi_t, dtype=np.float64).T
+
+
+def countsketch_matrix(h, sign, s):
+    """Dense T x s matrix Phi with Phi[t, h[t]] = sign[t] (one nonzero per row)."""
+    h = np.asarray(h)
+    T = h.shape[0]
+    Phi = np.zeros((T, s))
+    Phi[np.arange(T), h] = np.asarray(sign, dtype=np.float64)
+    return Phi
+
+
+def countsketch(L, h, sign, s):
+    """tilde L = L Phi for the CountSketch Phi of (h, sign), in FP64."""
+    return np.asarray(L, dtype=np.float64) @ countsketch_matrix(h, sign, s)
 
 
 def truncate(Ltilde, k):

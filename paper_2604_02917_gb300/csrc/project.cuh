@@ -20,11 +20,14 @@
 //
 // Arithmetic designed for GB300, whose FP64 rate is ~2 lane-ops/clk/SM:
 //  * every step is one reduction of |S|, sum_S v, sum_S mu, sum_S mu v,
-//    sum_S mu^2; the sums are EXACT 128-bit integer additions of fixed-point
-//    images of the FP64 values (62-bit magnitudes scaled by the largest
-//    element, converted with integer bit operations, so each image carries
-//    the full FP64 mantissa), so no FP64 add runs per element or in the
-//    reduction tree and the sums are at least as accurate as FP64 ones;
+//    sum_S mu^2; the sums are EXACT integer additions of fixed-point images
+//    of the FP64 values (62-bit magnitudes scaled by the largest element,
+//    converted with integer bit operations, so each image carries the full
+//    FP64 mantissa), so no FP64 add runs per element or in the reduction
+//    tree and the sums are at least as accurate as FP64 ones.  A thread
+//    keeps each image as four 16-bit limbs summed in 32-bit registers; a
+//    warp adds each limb with one redux.sync, and the limbs are recombined
+//    into 128 bits only for the few cross-warp and cross-block additions;
 //  * membership w_i > tau is decided in FP32 with a proven error margin;
 //    only elements inside the margin repeat the test in FP64 (same result as
 //    an FP64 evaluation of fma(nu, mu_i, v_i) > tau);
@@ -121,8 +124,40 @@ __device__ __forceinline__ I128 warp_sum_128(I128 v) {
     }
     return v;
 }
-struct ProjSums {
+// Warp-wide sum of a 32-bit integer (one instruction).
+__device__ __forceinline__ int redux_add(int v) {
+    int r;
+    asm volatile("redux.sync.add.s32 %0, %1, 0xffffffff;" : "=r"(r) : "r"(v));
+    return r;
+}
+// v * 2^s as a 128-bit value, s in {0, 16, 32, 48}.
+__device__ __forceinline__ I128 shl128(long long v, int s) {
+    I128 r;
+    r.lo = (unsigned long long)v << s;
+    r.hi = s == 0 ? (v >> 63) : (v >> (64 - s));
+    return r;
+}
+// Adds the four 16-bit limbs of a fixed-point image (|x| < 2^62: the top
+// limb, arithmetic, lies in [-2^14, 2^14]) to per-thread 32-bit sums.
+__device__ __forceinline__ void add_limbs(int (&l)[4], long long x) {
+    l[0] += (int)(x & 0xffff);
+    l[1] += (int)((x >> 16) & 0xffff);
+    l[2] += (int)((x >> 32) & 0xffff);
+    l[3] += (int)(x >> 48);
+}
+// Recombines warp totals of the four limbs.
+__device__ __forceinline__ I128 from_limbs(const int (&t)[4]) {
+    I128 r = shl128(t[0], 0);
+    add128(r, shl128(t[1], 16));
+    add128(r, shl128(t[2], 32));
+    add128(r, shl128(t[3], 48));
+    return r;
+}
+
+// Cluster totals of one support step, as thread 0 of every block holds them.
+struct SupportSums {
     double cnt, sv, sm, smv, smm;
+    long long nan, diff;
 };
 
 struct ProjOut {
@@ -229,24 +264,17 @@ struct ClusterProj {
     ProjSmem *sh;
     ProjElems el;
 
-    // Block-then-cluster sum of 6 128-bit values; lane 0 of warp 0 of every
-    // block ends with the same totals in `out` (integer sums: exact, so the
-    // order of addition does not matter).  Warp 0 does the cross-warp and
-    // cross-block steps in parallel: lane k < 6 adds value k over the warps,
-    // lane r < CL stores the totals into block r, lane r then loads block r's
-    // slot and a shuffle tree adds them.
-    __device__ void reduce6(I128 (&a)[6], I128 (&out)[6]) {
+    // Block-then-cluster sum of the 6 per-warp 128-bit partials in
+    // sh->wred (after a __syncthreads); lane k < 6 of warp 0 of every block
+    // ends with total k (integer sums: exact, so the order of addition does
+    // not matter).  Lane k < 6 adds value k over the warps, lane r < CL
+    // stores the block totals into block r, then lane k adds value k over
+    // the CL blocks.
+    __device__ I128 reduce_partials() {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-        for (int k = 0; k < 6; ++k) a[k] = warp_sum_128(a[k]);
-        if (lane == 0) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) sh->wred[warp][k] = a[k];
-        }
-        __syncthreads();
         const int par = sh->parity;
+        I128 t{0ull, 0ll};
         if (warp == 0) {
-            I128 t{0ull, 0ll};
             if (lane < 6)
                 for (int w = 0; w < kProjNT / kWarp; ++w) add128(t, sh->wred[w][lane]);
             const int me = cluster_rank<CL>();
@@ -268,16 +296,15 @@ struct ClusterProj {
             }
         }
         cluster_barrier<CL>();
+        t = I128{0ull, 0ll};
         if (warp == 0) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                I128 v = lane < CL ? sh->part[par][lane][k] : I128{0ull, 0ll};
-                out[k] = warp_sum_128(v);
-            }
+            if (lane < 6)
+                for (int r = 0; r < CL; ++r) add128(t, sh->part[par][r][lane]);
             if (lane == 0) sh->parity = par ^ 1;
         }
         // The next exchange writes the other parity; the one after reuses this
         // one only after another cluster barrier, so no reader is overtaken.
+        return t;
     }
 
     // Cluster sum of one double per thread, added in a fixed order (every
@@ -445,33 +472,72 @@ struct ClusterProj {
     }
 
     // Sums over S = {i : fma(nu, mu_i, v_i) > tau}; totals valid in thread 0.
-    // Slot 5: .lo counts NaNs met, .hi (when sh->verify) the elements whose
+    // Also counts NaNs met and (when sh->verify) the elements whose
     // membership differs from S(sh->nu0, sh->tau0).
-    __device__ void support_sums(double nu, double tau, float nu32, float tau32, I128 (&out)[6]) {
-        I128 a[6];
+    __device__ SupportSums support_sums(double nu, double tau, float nu32, float tau32) {
+        int lb[4][4];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) a[k] = I128{0ull, 0ll};
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) lb[k][q] = 0;
+        int cnt = 0, diff = 0;
         const float anu = fabsf(nu32), atau = isinf(tau32) ? 0.f : fabsf(tau32);
         const bool verify = sh->verify != 0;
         const double nu0 = sh->nu0, tau0 = sh->tau0;
         const float nu032 = sh->nu032, tau032 = sh->tau032;
         const float anu0 = fabsf(nu032), atau0 = isinf(tau032) ? 0.f : fabsf(tau032);
         bool nan = false;
-        long long diff = 0;
         for (int i = threadIdx.x; i < el.n; i += kProjNT) {
             const bool in = member(i, nu, tau, nu32, tau32, anu, atau, nan);
             if (verify && in != member(i, nu0, tau0, nu032, tau032, anu0, atau0, nan)) ++diff;
             if (in) {
-                a[0].lo += 1;
-                add128(a[1], el.V[i]);
-                add128(a[2], el.M[i]);
-                add128(a[3], el.MV[i]);
-                add128(a[4], el.MM[i]);
+                ++cnt;
+                add_limbs(lb[0], el.V[i]);
+                add_limbs(lb[1], el.M[i]);
+                add_limbs(lb[2], el.MV[i]);
+                add_limbs(lb[3], el.MM[i]);
             }
         }
-        a[5].lo = nan ? 1ull : 0ull;
-        a[5].hi = diff;
-        reduce6(a, out);
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        int tl[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) tl[k][q] = redux_add(lb[k][q]);
+        const int tcnt = redux_add(cnt), tdiff = redux_add(diff), tnan = redux_add(nan ? 1 : 0);
+        if (lane < 6) {
+            I128 w;
+            if (lane == 0) {
+                w = I128{(unsigned long long)tcnt, 0ll};
+            } else if (lane == 5) {
+                w = I128{(unsigned long long)tnan, (long long)tdiff};
+            } else {
+                // lane k (1..4) recombines image k-1; the branch-free select keeps tl in registers
+                int t4[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    t4[q] = lane == 1 ? tl[0][q] : (lane == 2 ? tl[1][q] : (lane == 3 ? tl[2][q] : tl[3][q]));
+                w = from_limbs(t4);
+            }
+            sh->wred[warp][lane] = w;
+        }
+        __syncthreads();
+        const I128 t = reduce_partials();
+        // lane k converts total k to FP64 (the four images with their scales)
+        double d = 0.0;
+        if (warp == 0 && lane < 5) {
+            const double p = lane == 1 ? sh->p_v : (lane == 2 ? sh->p_m : (lane == 3 ? sh->p_mv : sh->p_mm));
+            d = lane == 0 ? (double)t.lo : i128_to_double(t) * p;
+        }
+        SupportSums out;
+        out.cnt = __shfl_sync(0xffffffffu, d, 0);
+        out.sv = __shfl_sync(0xffffffffu, d, 1);
+        out.sm = __shfl_sync(0xffffffffu, d, 2);
+        out.smv = __shfl_sync(0xffffffffu, d, 3);
+        out.smm = __shfl_sync(0xffffffffu, d, 4);
+        out.nan = (long long)__shfl_sync(0xffffffffu, t.lo, 5);
+        out.diff = __shfl_sync(0xffffffffu, t.hi, 5);
+        return out;
     }
 
     // Full search.  Returns (nu, tau, status) identically in all threads.
@@ -510,18 +576,13 @@ struct ClusterProj {
             if (sh->done) break;                       // uniform: read after a barrier
             const double enu = sh->nu, etau = sh->tau;
             const float enu32 = sh->nu32, etau32 = sh->tau32;
-            I128 S[6];
-            support_sums(enu, etau, enu32, etau32, S);
+            const SupportSums S = support_sums(enu, etau, enu32, etau32);
             if (threadIdx.x == 0) {
                 sh->steps += 1;
-                const double cnt = (double)S[0].lo;
-                const double sv = i128_to_double(S[1]) * sh->p_v;
-                const double sm = i128_to_double(S[2]) * sh->p_m;
-                const double smv = i128_to_double(S[3]) * sh->p_mv;
-                const double smm = i128_to_double(S[4]) * sh->p_mm;
+                const double cnt = S.cnt, sv = S.sv, sm = S.sm, smv = S.smv, smm = S.smm;
                 bool finish = false, handled = false;
                 double next_nu = enu, next_tau = etau;
-                if (S[5].lo != 0) {
+                if (S.nan != 0) {
                     status = MV_ERR_NUMERIC;
                     finish = true;
                     handled = true;
@@ -529,7 +590,7 @@ struct ClusterProj {
                     // the candidate was built on S(nu0, tau0); it is exact iff the support is unchanged
                     verifying = false;
                     sh->verify = 0;
-                    if (S[5].hi == 0) {
+                    if (S.diff == 0) {
                         nu = enu;
                         tau = etau;
                         finish = true;

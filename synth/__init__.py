@@ -119,6 +119,16 @@ def gaussian_sketch(T: int, s: int, seed: int = 2, dtype=np.float64) -> np.ndarr
     return out
 
 
+def countsketch_hash(T: int, s: int, seed: int = 2):
+    """The random draws of a CountSketch map (Sec. 2.3, construction (2)):
+    bucket h(t) uniform in [0, s) and sign s_t uniform in {-1, +1} for each
+    period t.  Returns (h int32 [T], sign int8 [T])."""
+    rng = np.random.default_rng(seed)
+    h = rng.integers(0, s, size=T, dtype=np.int64).astype(np.int32)
+    sign = (2 * rng.integers(0, 2, size=T, dtype=np.int64) - 1).astype(np.int8)
+    return h, sign
+
+
 def uneven_problem_sizes(count: int = 256, seed: int = 1000,
                          n_range=(500, 5000), T_range=(2000, 20000)):
     """Shapes of a batch of independent problems of uneven size.

@@ -12,7 +12,7 @@ import os
 import numpy as np
 import pytest
 
-from synth import CFG_SMALL, factor_returns, gaussian_sketch, power_start
+from synth import CFG_SMALL, countsketch_hash, factor_returns, gaussian_sketch, power_start
 from oracle.center import center_factor
 from oracle.projection import (PROJ_BRACKET, PROJ_INFEASIBLE, PROJ_OK, active_set, project_F,
                                project_F_dykstra, project_F_safeguarded, project_halfspace,
@@ -463,6 +463,39 @@ def test_sketch_embedding_bound_and_moments():
     x = np.random.default_rng(1).dirichlet(np.ones(80))
     q, qt = x @ Sigma @ x, np.sum((Lt.T @ x) ** 2)
     assert (1 - eps) * q <= qt <= (1 + eps) * q
+
+
+def test_countsketch_map_and_embedding():
+    """CountSketch (Sec. 2.3 (2)): one signed nonzero per row of Phi; an
+    injective hash makes Phi a signed partial permutation, so the sketch keeps
+    the covariance exactly; over independent draws tilde L tilde L^T is
+    unbiased for L L^T (E[Phi Phi^T] = I); per column, tilde L is the signed
+    bucket sum checked element by element on a hand case."""
+    h, sg = countsketch_hash(5000, 64, seed=4)
+    assert h.min() >= 0 and h.max() < 64 and set(np.unique(sg)) == {-1, 1}
+    assert abs(np.mean(sg)) < 0.05 and np.all(np.bincount(h, minlength=64) > 0)
+    Phi = strmodel.countsketch_matrix(h, sg, 64)
+    assert np.array_equal((Phi != 0).sum(axis=1), np.ones(5000))
+    # hand case: T = 5, s = 3
+    L = np.array([[1.0, 2.0, 3.0, 4.0, 5.0], [0.5, -1.0, 0.0, 2.0, 1.0]])
+    hh, ss = np.array([2, 0, 2, 1, 0]), np.array([1, -1, -1, 1, 1])
+    np.testing.assert_array_equal(strmodel.countsketch(L, hh, ss, 3),
+                                  [[-2.0 + 5.0, 4.0, 1.0 - 3.0], [1.0 + 1.0, 2.0, 0.5]])
+    # injective hash: exact covariance
+    _, _, L, _ = small_problem(20, 80, seed=6)
+    perm = np.random.default_rng(1).permutation(100)[:80]
+    sgn = np.where(np.random.default_rng(2).random(80) < 0.5, -1, 1)
+    Lt = strmodel.countsketch(L, perm, sgn, 100)
+    np.testing.assert_allclose(Lt @ Lt.T, L @ L.T, rtol=1e-12, atol=1e-20)
+    # unbiased over draws (Monte Carlo, 400 draws, s = 40 < T = 80)
+    acc = np.zeros((20, 20))
+    for d in range(400):
+        hh, ss = countsketch_hash(80, 40, seed=100 + d)
+        Lt = strmodel.countsketch(L, hh, ss, 40)
+        acc += Lt @ Lt.T
+    acc /= 400
+    S = L @ L.T
+    assert np.max(np.abs(acc - S)) <= 0.02 * np.max(np.abs(S))      # dropping the signs gives 0.035
 
 
 def test_knee_rank_and_kappa_ridge():
