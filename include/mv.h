@@ -374,6 +374,31 @@ int mv_sketch(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_
               int64_t ldP, float *d_L_sketch, int64_t ldS, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
+ * 4b. CountSketch (Sec. 2.3, construction (2)): the sparse alternative to
+ *     the Gaussian sketch.  Phi (T x m) has one nonzero per row,
+ *     Phi(t, h(t)) = s_t in {-1, +1}, so column j of tilde L = L Phi is the
+ *     signed sum of the columns t of L with h(t) = j.  O(nT) work, no GEMM:
+ *     L is read once (HBM-bound).
+ *
+ *  d_L        [in]  the factor, dtype F32 / BF16 / FP8 e4m3 (with d_row_scale),
+ *                   MV_LAYOUT_TN (L^T, T x n, ldL >= n) or MV_LAYOUT_NT
+ *                   (n x T, ldL >= T; T x element size at most 200 KB).
+ *  d_hash     [in]  T int32 buckets h(t) in [0, m) (device).
+ *  d_sign     [in]  T int8 signs s_t, -1 or +1 (device; any negative value is -1).
+ *  d_L_sketch [out] n x m FP32, row-major, leading dim ldS >= m.
+ *  d_ws       [in]  mv_countsketch_workspace_size(T, m) bytes, 256-byte aligned.
+ *  Each output is summed over its bucket's periods in ascending order
+ *  (deterministic).  Blocking.  MV_ERR_INVALID_ARG for a bucket outside
+ *  [0, m); MV_ERR_UNSUPPORTED for a bucket of more than 4096 periods or an
+ *  NT row that does not fit shared memory.  The result feeds
+ *  mv_str_truncate unchanged.
+ * ------------------------------------------------------------------------ */
+size_t mv_countsketch_workspace_size(int64_t T, int64_t m);
+int mv_countsketch(const void *d_L, int32_t dtype, int32_t layout, const float *d_row_scale, int64_t n,
+                   int64_t T, int64_t ldL, const int32_t *d_hash, const int8_t *d_sign, int64_t m,
+                   float *d_L_sketch, int64_t ldS, void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/* ------------------------------------------------------------------------
  * 3d. Truncate + ridge (Sec. 2.5 steps 2-3; App. D.3), FP64.
  *
  *  From tilde L (n x m FP32) computes the k largest eigenpairs of the FP64

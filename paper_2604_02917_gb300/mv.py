@@ -36,7 +36,7 @@ EXPORTS = [
     "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
     "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch", "mv_center_host_workspace_size",
     "mv_center_factor_host", "mv_batch_tiles", "mv_str_truncate_knee", "mv_sigma_workspace_size",
-    "mv_sigma_form",
+    "mv_sigma_form", "mv_countsketch_workspace_size", "mv_countsketch",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -103,6 +103,10 @@ def lib():
         L.mv_center_workspace_size.argtypes = [i64, i64]
         L.mv_center_factor.restype = i32
         L.mv_center_factor.argtypes = [vp, i64, i64, i64, i32, i32, vp, i64, vp, vp, vp, vp, sz, vp]
+        L.mv_countsketch_workspace_size.restype = sz
+        L.mv_countsketch_workspace_size.argtypes = [i64, i64]
+        L.mv_countsketch.restype = i32
+        L.mv_countsketch.argtypes = [vp, i32, i32, vp, i64, i64, i64, vp, vp, i64, vp, i64, vp, sz, vp]
         L.mv_sigma_workspace_size.restype = sz
         L.mv_sigma_workspace_size.argtypes = [C.POINTER(Problem)]
         L.mv_sigma_form.restype = i32
@@ -427,6 +431,23 @@ def bf16_rows(A, ld=None) -> torch.Tensor:
     ld = (c + 7) // 8 * 8 if ld is None else ld
     out = torch.zeros((r, ld), dtype=torch.bfloat16, device="cuda")
     out[:, :c] = A.to(device="cuda", dtype=torch.bfloat16)
+    return out
+
+
+def countsketch(L: torch.Tensor, n: int, T: int, h: torch.Tensor, sign: torch.Tensor, m: int, dtype: str = "f32",
+                row_scale: torch.Tensor | None = None, layout: str = "nt"):
+    """tilde L = L Phi for the CountSketch Phi of (h, sign) (mv_countsketch):
+    n x m FP32.  L as center_factor returns it (n x ld for "nt", T x ld for "tn")."""
+    assert h.dtype == torch.int32 and sign.dtype == torch.int8 and h.is_cuda and sign.is_cuda
+    nb = lib().mv_countsketch_workspace_size(T, m)
+    if nb == 0:
+        raise MvError(MV_ERR_INVALID_ARG, "mv_countsketch_workspace_size")
+    ws = _workspace(nb, L.device)
+    ldS = (m + 3) // 4 * 4
+    out = torch.zeros((n, ldS), dtype=torch.float32, device=L.device)
+    _check(lib().mv_countsketch(_ptr(L), DTYPES[dtype], LAYOUTS[layout], _ptr(row_scale) if row_scale is not None
+                                else None, n, T, L.stride(0), _ptr(h), _ptr(sign), m, _ptr(out), ldS, _ptr(ws),
+                                ws.numel(), _stream()), "mv_countsketch")
     return out
 
 
