@@ -95,6 +95,20 @@ def peaks():
         return FALLBACK_HBM, "fallback"
 
 
+def jsonable(o, path="line"):
+    """Plain JSON values; a stray 0-d tensor or NumPy scalar is converted (and reported)."""
+    if isinstance(o, dict):
+        return {k: jsonable(v, f"{path}.{k}") for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [jsonable(v, f"{path}[{i}]") for i, v in enumerate(o)]
+    if o is None or isinstance(o, (bool, int, float, str)):
+        return o
+    if hasattr(o, "item"):
+        sys.stderr.write(f"bench: {path} was a {type(o).__name__}; converted\n")
+        return o.item()
+    return o
+
+
 def peaks_tensor():
     """Measured dense BF16 tensor peak (burst; the formation GEMM is timed alone)."""
     try:
@@ -439,10 +453,10 @@ def main():
 
     # Explicit covariance (Sec. 3 remark): Sigma = L L^T once on tcgen05, then
     # NPGA with one symmetric pass over the upper triangle of Sigma per iteration.
-    sigma = None
+    sigma_res = None
     if not args.no_sigma and args.dtype == "f32":
         R_dev = torch.from_numpy(R32).to(dev)
-        sigma = {}
+        sigma_res = {}
         peak_tf = peaks_tensor()
         for sdt in ("f32", "bf16"):
             Lx, rsx, _, _ = mv.center_factor(R_dev, sdt, layout="nt")
@@ -482,7 +496,7 @@ def main():
                                            "launches (includes enqueue gaps; the ncu launch list has "
                                            "device durations)"},
                           "step_kernel_avg_us": round(sum(i["t_step_ms"] for i in pinfos) / pairs * 1e3, 2)})
-            sigma[sdt + "_L"] = entry
+            sigma_res[sdt + "_L"] = entry
             del sv, S, Lx, rsx
         del R_dev
         torch.cuda.empty_cache()
@@ -540,6 +554,29 @@ def main():
                    "full_model_gap": (f_str_full - f_full) / f_full,
                    "build_plus_solve_s": (min(sk_ms) + tr_ms + s_ms) / 1e3}
         del Lb, Phi_t, Ls, L_eff, ssv
+        # CountSketch alternative (Sec. 2.3 (2)) on the headline factor: one HBM pass over L.
+        from synth import countsketch_hash
+        hh, sg = countsketch_hash(model.T, args.sketch_m, seed=2)
+        hh, sg = torch.from_numpy(hh).to(dev), torch.from_numpy(sg).to(dev)
+        es_h = {"f32": 4, "bf16": 2, "fp8": 1}[args.dtype]
+        mv.countsketch(L, model.n, model.T, hh, sg, args.sketch_m, args.dtype, rs, args.layout)   # warm-up
+        cs_ms = []
+        for _ in range(3):
+            e[0].record(stream)
+            Lc = mv.countsketch(L, model.n, model.T, hh, sg, args.sketch_m, args.dtype, rs, args.layout)
+            e[1].record(stream)
+            torch.cuda.synchronize()
+            cs_ms.append(e[0].elapsed_time(e[1]))
+        cs_bytes = model.n * model.T * es_h + 5 * model.T + 4 * model.n * args.sketch_m
+        peak, peak_kind = peaks()
+        cs_gbs = cs_bytes / (min(cs_ms) * 1e-3) / 1e9
+        str_res["countsketch"] = {"m": args.sketch_m, "layout": args.layout, "dtype": args.dtype,
+                                  "ms": min(cs_ms), "alg_bytes": cs_bytes,
+                                  "roofline": {"bound": "hbm", "achieved": round(cs_gbs, 1), "peak": peak,
+                                               "unit": "GB/s", "frac": round(cs_gbs / peak, 4),
+                                               "peak_source": peak_kind, "traffic": None,
+                                               "note": "whole call (bucket lists + gather), event-timed"}}
+        del Lc, hh, sg
 
     # 64-point efficient frontier (shared BF16 factor, skinny tcgen05 GEMMs).
     frontier = None
@@ -665,9 +702,9 @@ def main():
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "variants": variants, "sigma": sigma, "str": str_res, "frontier": frontier, "adjoint": adj,
+                "variants": variants, "sigma": sigma_res, "str": str_res, "frontier": frontier, "adjoint": adj,
                 "batch": batch}
-        print(json.dumps(line), flush=True)
+        print(json.dumps(jsonable(line)), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
 

@@ -72,6 +72,7 @@ __device__ __forceinline__ void symv_finish_block(const SymvArgs &a, int b) {
         const int r = b * kSymTile + i;
         if (r >= a.n) continue;
         float s = 0.f, c = 0.f;
+#pragma unroll 8
         for (int j = 0; j < a.nb; ++j) {
             const float y = __ldcg(a.part + (int64_t)j * stride + r) - c;
             const float t = s + y;
@@ -181,9 +182,11 @@ __global__ void __launch_bounds__(kSymThreads) symv_kernel(SymvArgs a) {
         }
     }
     // tickets: the last of the nb contributors of a block row reduces it
-    __threadfence();
+    // (the block barrier, then one thread's device fence, publishes every
+    // thread's partials before the ticket)
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         s_last[0] = atomicAdd(&a.tickets[I], 1u) == (unsigned)(a.nb - 1);
         s_last[1] = (I != J) && atomicAdd(&a.tickets[J], 1u) == (unsigned)(a.nb - 1);
     }
