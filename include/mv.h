@@ -212,6 +212,22 @@ typedef struct {
     int32_t two_pass;         /* 1: always stream L twice per product (z = L^T y, then
                                  L z); 0 (default): use the fused single pass for
                                  L L^T y where it applies (see below)                   */
+    /* Step and momentum variants of Sec. 3.1 (mv_npga_solve only): */
+    int32_t momentum;         /* 0 (default): the t_k-based FISTA update of Algorithm 1;
+                                 1: the strongly convex specialisation, beta fixed at
+                                 (1 - sqrt(alpha m_f)) / (1 + sqrt(alpha m_f))          */
+    int32_t backtrack;        /* 1: accelerated backtracking from the trial step
+                                 bt_alpha0 (<= 0: the power-method step times
+                                 1 / bt_rho^4), shrunk by bt_rho until
+                                 ||L^T d||^2 + gamma ||d||^2 <= ||d||^2 / (2 alpha),
+                                 d = x+ - y; the step never grows again              */
+    double m_f;               /* lower curvature bound for momentum = 1 (> 0; <= 0 takes
+                                 2 gamma, which needs gamma > 0)                        */
+    double bt_rho;            /* shrink factor in (0, 1) (default 0.5)                    */
+    double bt_alpha0;         /* first trial step (see backtrack)                         */
+    int32_t proj_budget;      /* outer steps of each projection's scalar search before
+                                 the Dykstra safeguard takes over (default 100)         */
+    int32_t dykstra_iters;    /* sweeps of the Dykstra safeguard (default 2000; 0: off)   */
 } mv_solve_opts;
 
 typedef struct {
@@ -235,6 +251,8 @@ typedef struct {
                                  2: the symmetric pass over an explicit Sigma; 0: two
                                  passes over L                                            */
     double t_fused_ms;        /* summed device time of the timed single-pass products    */
+    int32_t backtracks;       /* rejected trial steps (backtrack = 1)                     */
+    int32_t dykstra;          /* projections finished through the Dykstra safeguard       */
 } mv_solve_info;
 
 void mv_solve_opts_default(mv_solve_opts *opts);

@@ -164,6 +164,7 @@ struct ProjOut {
     double nu, tau;
     int status;
     int steps;
+    int dykstra;      // 1 if the Dykstra safeguard ran
 };
 
 // Shared-memory workspace of one block of the projector.
@@ -263,6 +264,10 @@ template <int CL>
 struct ClusterProj {
     ProjSmem *sh;
     ProjElems el;
+    // Dykstra safeguard: 4 el.n doubles of global scratch for this block
+    // (v, x, p, q) and the sweep budget; without scratch the safeguard is off.
+    double *dyk = nullptr;
+    int dyk_iters = 0;
 
     // Block-then-cluster sum of the 6 per-warp 128-bit partials in
     // sh->wred (after a __syncthreads); lane k < 6 of warp 0 of every block
@@ -541,7 +546,7 @@ struct ClusterProj {
     }
 
     // Full search.  Returns (nu, tau, status) identically in all threads.
-    __device__ ProjOut solve(double R, int mode, double mu_min, double mu_max, double nu_hint, double tau_hint,
+    __device__ ProjOut search(double R, int mode, double mu_min, double mu_max, double nu_hint, double tau_hint,
                              int budget) {
         // Thread-0-owned search state.
         double lo = -INFINITY, hi = INFINITY, nu = 0.0, tau = -INFINITY, prev_cnt = -1.0;
@@ -723,7 +728,105 @@ struct ClusterProj {
         o.tau = sh->tau;
         o.status = sh->status;
         o.steps = sh->steps;
+        o.dykstra = 0;
         __syncthreads();   // all threads read the result before the slots are reused
+        return o;
+    }
+
+    // Dykstra's alternating projections between Delta and H (the safeguard
+    // of Sec. 3.1), started at the v held in el.v: x = v, p = q = 0, then
+    //   y = Pi_Delta(x + p), p <- x + p - y;  w = y + q,
+    //   x = w + theta mu (theta = max(0, (R - mu^T w) / ||mu||^2), any sign
+    //   in equality mode), q <- w - x = -theta mu,
+    // until x and y agree and stop moving (1e-10 max(1, |v|_inf)) or the
+    // sweep budget is spent.  Pi_Delta is the scalar search at nu = 0 with
+    // the return row dropped (R = -inf).  Returns theta, the return-row
+    // multiplier of the limit, and in tau_out the threshold it implies
+    // (tau = v_i + theta mu_i - x_i on the support, averaged); el.v and its
+    // fixed-point images are restored.
+    __device__ double dykstra(double R, int mode, double mu_min, double mu_max, int budget, int &sweeps,
+                              double &tau_out) {
+        const int n = el.n;
+        double *v0 = dyk, *x = dyk + n, *p = dyk + 2 * n, *q = dyk + 3 * n;
+        double vmax = 0.0, mm = 0.0;
+        for (int i = threadIdx.x; i < n; i += kProjNT) {
+            const double v = el.v[i];
+            v0[i] = v;
+            x[i] = v;
+            p[i] = 0.0;
+            q[i] = 0.0;
+            vmax = fmax(vmax, fabs(v));
+            mm = fma(el.mu[i], el.mu[i], mm);
+        }
+        mm = reduce_double(mm);
+        double lo = 0.0, hi = vmax;
+        reduce_minmax(lo, hi);
+        const double tol = 1e-10 * fmax(1.0, hi);
+        double theta = 0.0;
+        sweeps = 0;
+        for (int it = 0; it < dyk_iters; ++it) {
+            for (int i = threadIdx.x; i < n; i += kProjNT) el.v[i] = x[i] + p[i];
+            __syncthreads();
+            prepare();
+            const ProjOut s = search(-INFINITY, MV_RETURN_GE, mu_min, mu_max, 0.0, -INFINITY, budget);
+            // el.v holds x + p: y = Pi_Delta(x + p), p <- x + p - y, w = y + q (parked in q)
+            double c = 0.0;
+            for (int i = threadIdx.x; i < n; i += kProjNT) {
+                const double y = fmax(el.v[i] - s.tau, 0.0);
+                p[i] = el.v[i] - y;
+                const double w = y + q[i];
+                q[i] = w;
+                c = fma(el.mu[i], w, c);
+            }
+            c = reduce_double(c);
+            double th = mm > 0.0 ? (R - c) / mm : 0.0;
+            if (mode == MV_RETURN_GE) th = fmax(th, 0.0);
+            // x <- w + theta mu, q <- w - x; measure |x_new - x_old| and |x_new - y|
+            double dev = 0.0;
+            for (int i = threadIdx.x; i < n; i += kProjNT) {
+                const double w = q[i];
+                const double y = fmax(el.v[i] - s.tau, 0.0);
+                const double xn = fma(th, el.mu[i], w);
+                dev = fmax(dev, fmax(fabs(xn - x[i]), fabs(xn - y)));
+                x[i] = xn;
+                q[i] = w - xn;
+            }
+            double a = -dev, b = fabs(th - theta) * sqrt(mm);
+            reduce_minmax(a, b);
+            theta = th;
+            sweeps = it + 1;
+            if (s.status != MV_OK) break;
+            if (-a <= tol && b <= tol) break;
+        }
+        double st = 0.0, sc = 0.0;
+        for (int i = threadIdx.x; i < n; i += kProjNT) {
+            el.v[i] = v0[i];
+            if (x[i] > 0.0) {
+                st += fma(theta, el.mu[i], v0[i]) - x[i];
+                sc += 1.0;
+            }
+        }
+        st = reduce_double(st);
+        sc = reduce_double(sc);
+        tau_out = sc > 0.0 ? st / sc : -INFINITY;
+        prepare();
+        return theta;
+    }
+
+    // The projection: the scalar search, and the Dykstra safeguard when the
+    // search does not finish within its budget (scratch permitting), whose
+    // (theta, tau) restarts the exact search, with at least 100 outer steps.
+    __device__ ProjOut solve(double R, int mode, double mu_min, double mu_max, double nu_hint, double tau_hint,
+                             int budget) {
+        ProjOut o = search(R, mode, mu_min, mu_max, nu_hint, tau_hint, budget);
+        if (o.status != MV_ERR_NOT_CONVERGED || dyk == nullptr || dyk_iters <= 0) return o;
+        int sweeps = 0;
+        double tau_d = -INFINITY;
+        const double theta = dykstra(R, mode, mu_min, mu_max, budget, sweeps, tau_d);
+        const int steps = o.steps;
+        o = search(R, mode, mu_min, mu_max, theta, tau_d, budget > 100 ? budget : 100);
+        o.steps += steps;
+        o.dykstra = 1;
         return o;
     }
 };

@@ -36,6 +36,8 @@ struct SolveState {
     double kkt, nu, tau, nu_kkt, tau_kkt;
     double mu_min, mu_max;
     double objective;
+    double beta_c;                         // constant momentum (momentum = 1)
+    int bt_started, backtracks, dykstra, pad3;
 };
 
 struct Plan {
@@ -52,6 +54,7 @@ struct Plan {
     bool sig;                              // explicit Sigma (symv.cuh) instead of a factor
     int snb;                               // Sigma tile rows
     size_t o_spart, o_stick, o_gobj;
+    size_t o_dyk, o_gd, o_xp;              // Dykstra scratch; backtracking L L^T d and candidate
     // workspace offsets (bytes)
     size_t o_state, o_x, o_y, o_gx, o_gy, o_g32, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
     size_t o_llt, o_err, o_zd;
@@ -145,6 +148,10 @@ static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows
         p.lp = llt_plan(dt, n, T, true, tn);
         p.use_llt = p.lp.ok;
     }
+    const int nl = (int)((n + p.cl - 1) / p.cl);
+    p.o_dyk = take(8 * 4 * (size_t)nl * p.cl);
+    p.o_gd = take(8 * (size_t)n);
+    p.o_xp = take(8 * (size_t)n);
     p.o_err = take(16);
     p.total = off;
     return p;
@@ -184,6 +191,10 @@ static Plan make_plan_sigma(int64_t n, int64_t ld) {
     p.o_spart = take(symv_part_bytes((int)n));
     p.o_stick = take(4 * (size_t)p.snb);
     p.o_z = p.o_zpart = p.o_gpart = p.o_tick_t = p.o_tick_n = p.o_g32;   // unused by this form
+    const int nl = (int)((n + p.cl - 1) / p.cl);
+    p.o_dyk = take(8 * 4 * (size_t)nl * p.cl);
+    p.o_gd = take(8 * (size_t)n);
+    p.o_xp = take(8 * (size_t)n);
     p.o_err = take(16);
     p.total = off;
     return p;
@@ -195,6 +206,11 @@ static T_ *at(void *ws, size_t off) {
 }
 
 // ------------------------------------------------------------------ kernels
+// This block's slice of the Dykstra scratch (4 arrays of nl doubles).
+__device__ __forceinline__ double *dyk_slice(double *base, int rank, int nl) {
+    return base ? base + (size_t)rank * 4 * nl : nullptr;
+}
+
 __device__ __forceinline__ void setup_body(SolveState *st, const double *__restrict__ mu, const double *__restrict__ r0,
              const float *__restrict__ row_scale, float *__restrict__ y32, int n) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
@@ -320,7 +336,8 @@ __device__ __forceinline__ void init_x_body(SolveState *st, const double *__rest
                                             const double *__restrict__ x_in, double *__restrict__ x,
                                             double *__restrict__ y, float *__restrict__ y32,
                                             const float *__restrict__ row_scale, int n, double R, int mode,
-                                            unsigned char *dsm, ProjSmem &psm) {
+                                            unsigned char *dsm, ProjSmem &psm, double *dyk = nullptr,
+                                            int dyk_iters = 0, int budget = kProjBudget) {
     const int rank = cluster_rank<CL>();
     const int nl = (n + CL - 1) / CL;
     const int r0 = min(n, rank * nl);
@@ -336,8 +353,10 @@ __device__ __forceinline__ void init_x_body(SolveState *st, const double *__rest
         }
         __syncthreads();
         ClusterProj<CL> P{&psm, el};
+        P.dyk = dyk_slice(dyk, rank, nl);
+        P.dyk_iters = dyk_iters;
         P.prepare();
-        const ProjOut o = P.solve(R, mode, mn, mx, 0.0, -INFINITY, kProjBudget);
+        const ProjOut o = P.solve(R, mode, mn, mx, 0.0, -INFINITY, budget);
         for (int i = threadIdx.x; i < el.n; i += kProjNT) {
             const double xi = o.status == MV_ERR_INFEASIBLE ? NAN : fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
             x[r0 + i] = xi;
@@ -350,6 +369,7 @@ __device__ __forceinline__ void init_x_body(SolveState *st, const double *__rest
             st->tau = o.tau;
             st->nu_kkt = o.nu;
             st->tau_kkt = o.tau;
+            st->dykstra += o.dykstra;
         }
         cluster_barrier<CL>();
     } else {
@@ -382,10 +402,11 @@ template <int CL>
 __global__ void __launch_bounds__(kProjNT)
 init_x_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ x_in,
               double *__restrict__ x, double *__restrict__ y, float *__restrict__ y32,
-              const float *__restrict__ row_scale, int n, double R, int mode) {
+              const float *__restrict__ row_scale, int n, double R, int mode, double *dyk, int dyk_iters,
+              int budget) {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ ProjSmem psm;
-    init_x_body<CL>(st, mu, x_in, x, y, y32, row_scale, n, R, mode, dsm, psm);
+    init_x_body<CL>(st, mu, x_in, x, y, y32, row_scale, n, R, mode, dsm, psm, dyk, dyk_iters, budget);
 }
 
 struct StepArgs {
@@ -397,7 +418,19 @@ struct StepArgs {
     const float *row_scale;
     int n, mode, kkt_every, max_iter;
     double R, gamma, eps;
+    // Sec. 3.1 variants and the projection safeguard
+    double *dyk = nullptr;                 // 4 (n + CL) doubles of Dykstra scratch, or none
+    int dyk_iters = 0;
+    int budget = kProjBudget;
+    int momentum = 0;                      // 1: beta fixed at st->beta_c
+    int pad = 0;
+    double bt_rho = 0.5;
+    double m_f = 0.0;                      // curvature bound of the constant momentum
+    double *gyw = nullptr;                 // backtracking: L L^T y (written), L L^T d, candidate x+
+    const double *gd = nullptr;
+    double *xp = nullptr;
 };
+
 
 // One NPGA step on a cluster of CL blocks; block r owns assets [r0, r1).
 template <int CL>
@@ -422,9 +455,14 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
     __shared__ double sc[4];
     if (threadIdx.x == 0) {
         sc[0] = 1.0 / (1.0 + beta_prev);
-        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-        sc[1] = tn;
-        sc[2] = (t - 1.0) / tn;
+        if (a.momentum == 1) {             // strongly convex specialisation: t unused, beta fixed
+            sc[1] = t;
+            sc[2] = st->beta_c;
+        } else {
+            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+            sc[1] = tn;
+            sc[2] = (t - 1.0) / tn;
+        }
     }
     proj_smem_init(&psm);
     const double inv1pb = sc[0], tn = sc[1], beta = sc[2];
@@ -444,9 +482,11 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
     }
     __syncthreads();
     ClusterProj<CL> P{&psm, el};
+    P.dyk = dyk_slice(a.dyk, rank, nl);
+    P.dyk_iters = a.dyk_iters;
     if (check) {
         P.prepare();
-        const ProjOut o = P.solve(a.R, a.mode, mn, mx, nuk0, tauk0, kProjBudget);
+        const ProjOut o = P.solve(a.R, a.mode, mn, mx, nuk0, tauk0, a.budget);
         double r2 = 0.0;
         for (int i = threadIdx.x; i < el.n; i += kProjNT) {
             const double p = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
@@ -462,6 +502,7 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
             st->nu_kkt = o.nu;
             st->tau_kkt = o.tau;
             st->proj_steps += o.steps;
+            st->dykstra += o.dykstra;
             if (o.status != MV_OK) st->proj_fail += 1;
             if (stop) {
                 st->done = 1;
@@ -482,7 +523,7 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
     }
     __syncthreads();
     P.prepare();
-    const ProjOut o = P.solve(a.R, a.mode, mn, mx, nu0, tau0, kProjBudget);
+    const ProjOut o = P.solve(a.R, a.mode, mn, mx, nu0, tau0, a.budget);
     for (int i = threadIdx.x; i < el.n; i += kProjNT) {
         const int gi = r0 + i;
         const double xn = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
@@ -500,6 +541,7 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
         st->tau = o.tau;
         if (o.status != MV_OK) st->proj_fail += 1;
         st->proj_steps += o.steps;
+        st->dykstra += o.dykstra;
         if (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC) {
             st->done = 1;
             st->status = o.status;
@@ -522,6 +564,199 @@ __global__ void __launch_bounds__(kProjNT) npga_step_grouped(const StepArgs *__r
     __shared__ ProjSmem psm;
     const StepArgs a = args[blockIdx.x / CL];
     npga_step_body<CL>(a, dsm, psm);
+}
+
+// Sets up the Sec. 3.1 variants once alpha is known: the first backtracking
+// trial step (alpha0, or the power-method step / rho^4 when alpha0 <= 0)
+// and the constant momentum beta = (1 - q) / (1 + q), q = sqrt(alpha m_f)
+// (clamped to q <= 1).
+__device__ __forceinline__ double const_beta(double alpha, double m_f) {
+    const double q = fmin(sqrt(alpha * m_f), 1.0);
+    return (1.0 - q) / (1.0 + q);
+}
+
+__global__ void variant_setup_kernel(SolveState *st, int momentum, double m_f, int backtrack, double alpha0,
+                                     double rho) {
+    if (threadIdx.x != 0) return;
+    if (backtrack) st->alpha = alpha0 > 0.0 ? alpha0 : st->alpha / (rho * rho * rho * rho);
+    if (momentum) st->beta_c = const_beta(st->alpha, m_f);
+    st->bt_started = 0;
+}
+
+// One backtracking step (Sec. 3.1, adaptive backtracking) on a cluster of
+// CL blocks.  The pending candidate x+ = Pi_F(y - alpha grad f(y)) was
+// projected by the previous launch, and the product between the two
+// launches formed L L^T d for d = x+ - y.  The sufficient-decrease test
+//     f(x+) <= f(y) + <grad f(y), d> + ||d||^2 / (2 alpha)
+// is exactly d^T L L^T d + gamma ||d||^2 <= ||d||^2 / (2 alpha) for this
+// quadratic f, evaluated in that form (the difference of objective values
+// cancels to rounding noise near the solution).  Accepted: x <- x+,
+// L L^T x <- L L^T y + L L^T d, the momentum step, and L L^T y for the new
+// y by linearity, with the KKT test every kkt_every accepted iterations.
+// Rejected: alpha <- rho alpha.  Either way the next candidate is projected
+// from y and d is written as the next product's FP32 input.
+template <int CL>
+__device__ __forceinline__ void npga_bt_step_body(const StepArgs &a, unsigned char *dsm, ProjSmem &psm) {
+    SolveState *st = a.st;
+    if (*(volatile int *)&st->done) return;
+    const int n = a.n;
+    const int rank = cluster_rank<CL>();
+    const int nl = (n + CL - 1) / CL;
+    const int r0 = min(n, rank * nl);
+    const int r1 = min(n, r0 + nl);
+    const int k = st->k;
+    const double t = st->t, mn = st->mu_min, mx = st->mu_max;
+    const bool started = st->bt_started != 0;
+    double alpha = st->alpha;
+    const double gamma = a.gamma;
+    ProjElems el = carve_elems(dsm, nl);
+    el.n = r1 - r0;
+    proj_smem_init(&psm);
+    ClusterProj<CL> P{&psm, el};
+    P.dyk = dyk_slice(a.dyk, rank, nl);
+    P.dyk_iters = a.dyk_iters;
+    __shared__ double sc[2];
+    int kn = k;
+    double tn = t, beta = st->beta_prev;
+    bool accepted = false, rejected = false, numeric = false;
+    for (int i = threadIdx.x; i < el.n; i += kProjNT) el.mu[i] = a.mu[r0 + i];
+    if (started) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            const int gi = r0 + i;
+            const double d = a.xp[gi] - a.y[gi];
+            s1 = fma(d, a.gd[gi], s1);
+            s2 = fma(d, d, s2);
+        }
+        s1 = P.reduce_double(s1);
+        s2 = P.reduce_double(s2);
+        const double q = s1 + gamma * s2;
+        if (!(q == q) || !(s2 == s2)) {
+            numeric = true;
+        } else if (s2 == 0.0 || q <= s2 / (2.0 * alpha)) {
+            accepted = true;
+        } else {
+            rejected = true;
+        }
+    }
+    if (accepted) {
+        if (threadIdx.x == 0) {
+            if (a.momentum == 1) {
+                sc[0] = t;
+                sc[1] = st->beta_c;
+            } else {
+                const double tt = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+                sc[0] = tt;
+                sc[1] = (t - 1.0) / tt;
+            }
+        }
+        __syncthreads();
+        tn = sc[0];
+        beta = sc[1];
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            const int gi = r0 + i;
+            const double gxp = a.gyw[gi] + a.gd[gi];            // L L^T x+
+            const double xo = a.x[gi], xn = a.xp[gi];
+            a.gyw[gi] = (1.0 + beta) * gxp - beta * a.gx[gi];     // L L^T y_new
+            a.x[gi] = xn;
+            a.gx[gi] = gxp;
+            a.y[gi] = xn + beta * (xn - xo);
+        }
+        kn = k + 1;
+        const bool check = (a.kkt_every > 0 && kn % a.kkt_every == 0) || kn >= a.max_iter;
+        if (check) {
+            for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+                const int gi = r0 + i;
+                const double xi = a.x[gi];
+                el.v[i] = xi - alpha * (2.0 * a.gx[gi] + 2.0 * gamma * xi);
+            }
+            __syncthreads();
+            P.prepare();
+            const ProjOut o = P.solve(a.R, a.mode, mn, mx, st->nu_kkt, st->tau_kkt, a.budget);
+            double r2 = 0.0;
+            for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+                const double pi = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
+                const double dd = pi - a.x[r0 + i];
+                r2 = fma(dd, dd, r2);
+            }
+            r2 = P.reduce_double(r2);
+            const bool conv = r2 <= a.eps * a.eps;
+            const bool stop = conv || kn >= a.max_iter || !(r2 == r2);
+            if (rank == 0 && threadIdx.x == 0) {
+                st->kkt = sqrt(r2);
+                st->nu_kkt = o.nu;
+                st->tau_kkt = o.tau;
+                st->proj_steps += o.steps;
+                st->dykstra += o.dykstra;
+                if (o.status != MV_OK) st->proj_fail += 1;
+                st->k = kn;
+                st->t = tn;
+                st->beta_prev = beta;
+                if (stop) {
+                    st->done = 1;
+                    st->converged = conv ? 1 : 0;
+                    st->status = conv ? MV_OK : (!(r2 == r2) ? MV_ERR_NUMERIC : MV_ERR_NOT_CONVERGED);
+                }
+            }
+            if (stop) {
+                cluster_barrier<CL>();
+                return;
+            }
+            __syncthreads();
+        }
+    }
+    if (rejected) alpha *= a.bt_rho;
+    if (numeric || !(alpha > 1e-300)) {
+        if (rank == 0 && threadIdx.x == 0) {
+            st->done = 1;
+            st->status = MV_ERR_NUMERIC;
+        }
+        cluster_barrier<CL>();
+        return;
+    }
+    // next candidate from y
+    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+        const int gi = r0 + i;
+        const double yi = a.y[gi];
+        el.v[i] = yi - alpha * (2.0 * a.gyw[gi] + 2.0 * gamma * yi);
+    }
+    __syncthreads();
+    P.prepare();
+    const ProjOut o = P.solve(a.R, a.mode, mn, mx, st->nu, st->tau, a.budget);
+    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+        const int gi = r0 + i;
+        const double xpn = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
+        a.xp[gi] = xpn;
+        a.y32[gi] = (float)((xpn - a.y[gi]) * (a.row_scale ? (double)a.row_scale[gi] : 1.0));
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+        st->k = kn;
+        st->t = tn;
+        st->beta_prev = beta;
+        st->alpha = alpha;
+        if (rejected) {
+            st->backtracks += 1;
+            if (a.momentum == 1) st->beta_c = const_beta(alpha, a.m_f);
+        }
+        st->bt_started = 1;
+        st->nu = o.nu;
+        st->tau = o.tau;
+        st->proj_steps += o.steps;
+        st->dykstra += o.dykstra;
+        if (o.status != MV_OK) st->proj_fail += 1;
+        if (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC) {
+            st->done = 1;
+            st->status = o.status;
+        }
+    }
+    cluster_barrier<CL>();
+}
+
+template <int CL>
+__global__ void __launch_bounds__(kProjNT) npga_bt_step_kernel(StepArgs a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ ProjSmem psm;
+    npga_bt_step_body<CL>(a, dsm, psm);
 }
 
 // FP64 n-vector -> scaled FP32 gemv input.
@@ -698,6 +933,9 @@ static int set_kernel_attrs() {
         ok = ok && cluster_attrs(npga_step_kernel<1>, 1) && cluster_attrs(npga_step_kernel<2>, 2) &&
              cluster_attrs(npga_step_kernel<4>, 4) && cluster_attrs(npga_step_kernel<8>, 8) &&
              cluster_attrs(npga_step_kernel<16>, 16);
+        ok = ok && cluster_attrs(npga_bt_step_kernel<1>, 1) && cluster_attrs(npga_bt_step_kernel<2>, 2) &&
+             cluster_attrs(npga_bt_step_kernel<4>, 4) && cluster_attrs(npga_bt_step_kernel<8>, 8) &&
+             cluster_attrs(npga_bt_step_kernel<16>, 16);
         ok = ok && cluster_attrs(init_x_kernel<1>, 1) && cluster_attrs(init_x_kernel<2>, 2) &&
              cluster_attrs(init_x_kernel<4>, 4) && cluster_attrs(init_x_kernel<8>, 8) &&
              cluster_attrs(init_x_kernel<16>, 16);
@@ -752,7 +990,26 @@ static void launch_step(const Plan &p, const mv_problem *P, const mv_solve_opts 
     a.R = P->R_target;
     a.gamma = P->gamma;
     a.eps = O->eps;
+    a.dyk = O->dykstra_iters > 0 ? at<double>(ws, p.o_dyk) : nullptr;
+    a.dyk_iters = O->dykstra_iters;
+    a.budget = O->proj_budget;
+    a.momentum = O->momentum;
+    a.bt_rho = O->bt_rho;
+    a.m_f = O->m_f > 0.0 ? O->m_f : 2.0 * P->gamma;
+    a.gyw = at<double>(ws, p.o_gy);
+    a.gd = at<double>(ws, p.o_gd);
+    a.xp = at<double>(ws, p.o_xp);
     const size_t sm = step_smem(p.n, p.cl);
+    if (O->backtrack) {
+        switch (p.cl) {
+            case 1: launch_cluster(npga_bt_step_kernel<1>, 1, sm, s, a); break;
+            case 2: launch_cluster(npga_bt_step_kernel<2>, 2, sm, s, a); break;
+            case 4: launch_cluster(npga_bt_step_kernel<4>, 4, sm, s, a); break;
+            case 8: launch_cluster(npga_bt_step_kernel<8>, 8, sm, s, a); break;
+            default: launch_cluster(npga_bt_step_kernel<16>, 16, sm, s, a); break;
+        }
+        return;
+    }
     switch (p.cl) {
         case 1: launch_cluster(npga_step_kernel<1>, 1, sm, s, a); break;
         case 2: launch_cluster(npga_step_kernel<2>, 2, sm, s, a); break;
@@ -762,19 +1019,25 @@ static void launch_step(const Plan &p, const mv_problem *P, const mv_solve_opts 
     }
 }
 
-static void launch_init_x(const Plan &p, const mv_problem *P, const double *x_in, void *ws, cudaStream_t s) {
+static void launch_init_x(const Plan &p, const mv_problem *P, const mv_solve_opts *O, const double *x_in, void *ws,
+                          cudaStream_t s) {
     SolveState *st = at<SolveState>(ws, p.o_state);
     const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
     double *x = at<double>(ws, p.o_x), *y = at<double>(ws, p.o_y);
     float *y32 = at<float>(ws, p.o_y32);
+    double *dyk = O->dykstra_iters > 0 ? at<double>(ws, p.o_dyk) : nullptr;
+    const int di = O->dykstra_iters, bud = O->proj_budget;
     const size_t sm = step_smem(p.n, p.cl);
+#define MV_INIT_X(CL_) launch_cluster(init_x_kernel<CL_>, CL_, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, \
+                                      P->mode, dyk, di, bud)
     switch (p.cl) {
-        case 1: launch_cluster(init_x_kernel<1>, 1, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
-        case 2: launch_cluster(init_x_kernel<2>, 2, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
-        case 4: launch_cluster(init_x_kernel<4>, 4, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
-        case 8: launch_cluster(init_x_kernel<8>, 8, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
-        default: launch_cluster(init_x_kernel<16>, 16, sm, s, st, P->mu, x_in, x, y, y32, rs, p.n, P->R_target, P->mode); break;
+        case 1: MV_INIT_X(1); break;
+        case 2: MV_INIT_X(2); break;
+        case 4: MV_INIT_X(4); break;
+        case 8: MV_INIT_X(8); break;
+        default: MV_INIT_X(16); break;
     }
+#undef MV_INIT_X
 }
 
 // Sigma y32 -> out64 (and out32) over the upper tiles of Sigma.
@@ -794,6 +1057,18 @@ static void launch_symv(const Plan &p, const mv_problem *P, const float *y32, vo
     symv_launch(a, s);
 }
 
+// L L^T y32 -> out64 by whichever product the plan uses (capturable).
+static int launch_product(const Plan &p, const mv_problem *P, const float *y32, void *ws, double *out64,
+                          cudaStream_t s) {
+    if (p.sig) {
+        launch_symv(p, P, y32, ws, nullptr, out64, nullptr, s);
+        return MV_OK;
+    }
+    if (p.use_llt) return launch_llt(p, P, y32, ws, nullptr, out64, nullptr, s);
+    gemv_pair(p, P, y32, ws, nullptr, out64, s);
+    return MV_OK;
+}
+
 // One loop iteration.  With `ev` non-null, events ev[0..3] bracket gemv_t,
 // gemv_n and the step kernel (ev[3] is the next iteration's ev[0]); with the
 // fused pass, ev[0..1] bracket it and ev[1..2] is empty.
@@ -801,7 +1076,8 @@ static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_o
                             cudaStream_t s, const cudaEvent_t *ev) {
     SolveState *st = at<SolveState>(ws, p.o_state);
     const float *y32 = at<float>(ws, p.o_y32);
-    double *gy = at<double>(ws, p.o_gy);
+    // the product: L L^T y for the step, L L^T d for a backtracking trial
+    double *gy = O->backtrack ? at<double>(ws, p.o_gd) : at<double>(ws, p.o_gy);
     const int *done = &st->done;
     if (ev) cudaEventRecord(ev[0], s);
     if (p.use_llt || p.sig) {
@@ -847,10 +1123,14 @@ struct GraphKey {
     int dt, mode, kkt_every, max_iter, chunk, fused;
     double R, gamma, eps;
     const void *ev;
+    int momentum, backtrack, budget, dyk_iters;
+    double bt_rho, m_f;
     bool operator==(const GraphKey &o) const {
         return L == o.L && mu == o.mu && rs == o.rs && ws == o.ws && n == o.n && T == o.T && ld == o.ld &&
                dt == o.dt && mode == o.mode && kkt_every == o.kkt_every && max_iter == o.max_iter &&
-               chunk == o.chunk && fused == o.fused && R == o.R && gamma == o.gamma && eps == o.eps && ev == o.ev;
+               chunk == o.chunk && fused == o.fused && R == o.R && gamma == o.gamma && eps == o.eps && ev == o.ev &&
+               momentum == o.momentum && backtrack == o.backtrack && budget == o.budget &&
+               dyk_iters == o.dyk_iters && bt_rho == o.bt_rho && m_f == o.m_f;
     }
 };
 struct GraphKeyHash {
@@ -866,7 +1146,8 @@ static std::unordered_map<GraphKey, cudaGraphExec_t, GraphKeyHash> g_graphs;
 static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
                            const cudaEvent_t *ev, cudaGraphExec_t *out) {
     GraphKey key{P->L, P->mu, P->row_scale, ws, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
-                 O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? 1 : 0), P->R_target, P->gamma, O->eps, (const void *)ev};
+                 O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? 1 : 0), P->R_target, P->gamma, O->eps, (const void *)ev,
+                 O->momentum, O->backtrack, O->proj_budget, O->dykstra_iters, O->bt_rho, O->m_f};
     int dev = 0;
     cudaGetDevice(&dev);
     std::lock_guard<std::mutex> lock(g_graph_mu);
@@ -924,6 +1205,13 @@ void mv_solve_opts_default(mv_solve_opts *o) {
     o->timing = 0;
     o->checkpoint_every = 50;
     o->two_pass = 0;
+    o->momentum = 0;
+    o->backtrack = 0;
+    o->m_f = 0.0;
+    o->bt_rho = 0.5;
+    o->bt_alpha0 = 0.0;
+    o->proj_budget = 100;
+    o->dykstra_iters = 2000;
 }
 
 size_t mv_npga_workspace_size(const mv_problem *P) {
@@ -969,6 +1257,12 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
+    if ((O.momentum != 0 && O.momentum != 1) || (O.backtrack != 0 && O.backtrack != 1) || O.proj_budget < 1 ||
+        O.dykstra_iters < 0)
+        return MV_ERR_INVALID_ARG;
+    if (O.momentum == 1 && !(O.m_f > 0.0) && !(P->gamma > 0.0))
+        return record_message(MV_ERR_INVALID_ARG, "constant momentum needs m_f > 0 or gamma > 0");
+    if (O.backtrack == 1 && !(O.bt_rho > 0.0 && O.bt_rho < 1.0)) return MV_ERR_INVALID_ARG;
     const Plan p = plan_for(P, O.two_pass == 0);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
@@ -1013,7 +1307,20 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     else
         step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0) ? 0 : p.T, P->gamma,
                                                     O.power_safety, O.alpha);
-    launch_init_x(p, P, O.warm_start ? d_x_inout : nullptr, d_ws, s);
+    if (O.momentum || O.backtrack) {
+        variant_setup_kernel<<<1, 32, 0, s>>>(st, O.momentum, O.m_f > 0.0 ? O.m_f : 2.0 * P->gamma, O.backtrack,
+                                              O.bt_alpha0, O.bt_rho);
+        launches += 1;
+    }
+    launch_init_x(p, P, &O, O.warm_start ? d_x_inout : nullptr, d_ws, s);
+    if (O.backtrack) {
+        // L L^T y^0 (= L L^T x^0), then the first trial candidate
+        MV_TRY(launch_product(p, P, y32, d_ws, at<double>(d_ws, p.o_gy), s));
+        MV_CUDA_TRY(cudaMemcpyAsync(at<double>(d_ws, p.o_gx), at<double>(d_ws, p.o_gy), 8 * (size_t)p.n,
+                                    cudaMemcpyDeviceToDevice, s));
+        launch_step(p, P, &O, d_ws, s);
+        launches += 3;
+    }
     MV_CUDA_TRY(cudaGetLastError());
 
     const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
@@ -1025,7 +1332,10 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     cudaGraphExec_t exec = nullptr;
     if (O.use_graph && !O.timing) MV_TRY(get_chunk_graph(p, P, &O, d_ws, chunk, nullptr, &exec));
     // max_iter + 1 iterations may run: the last one only evaluates the KKT residual.
-    const int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
+    int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
+    // rejected trial steps take loop slots without advancing k; the step only
+    // shrinks, so rejections are few (log(alpha0 / alpha) / log(1 / rho))
+    if (O.backtrack) max_chunks += 64 / chunk + 2;
     SolveState hs{};
     int k_prev = 0, timed = 0;
     double t_t = 0.0, t_n = 0.0, t_s = 0.0;
@@ -1099,6 +1409,8 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     h_info->fused = p.sig ? 2 : (p.use_llt ? 1 : 0);
     h_info->t_step_ms = t_s;
     h_info->proj_steps = hs.proj_steps;
+    h_info->backtracks = hs.backtracks;
+    h_info->dykstra = hs.dykstra;
     return h_info->status;
 }
 
@@ -1484,6 +1796,8 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
+    if (O.momentum != 0 || O.backtrack != 0)
+        return record_message(MV_ERR_UNSUPPORTED, "frontier solve: fixed step and FISTA momentum only");
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);   // power method: fused pass
     const FPlan f = make_fplan(p, n_targets);
     MV_TRY(check_ws(d_ws, ws_bytes, f.total));
@@ -1838,6 +2152,9 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 1 || O.checkpoint_every < 1 || O.power_iters < 0) return MV_ERR_INVALID_ARG;
+    if (O.momentum != 0 || O.backtrack != 0)
+        return record_message(MV_ERR_UNSUPPORTED, "mv_npga_backward: differentiates the fixed-step FISTA loop only");
+    if (O.proj_budget < 1 || O.dykstra_iters < 0) return MV_ERR_INVALID_ARG;
     O.kkt_every = 0;          // unrolled: no early stop inside the K iterations
     O.eps = 0.0;
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
@@ -1865,7 +2182,7 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     }
     step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(ws, p.o_z), (O.alpha > 0.0) ? 0 : T, P->gamma,
                                                 O.power_safety, O.alpha);
-    launch_init_x(p, P, d_x0, ws, s);
+    launch_init_x(p, P, &O, d_x0, ws, s);
     auto save_cp = [&](int c) -> int {
         MV_CUDA_TRY(cudaMemcpyAsync(at<SolveState>(ws, b.o_cp_state) + c, st, sizeof(SolveState),
                                     cudaMemcpyDeviceToDevice, s));
@@ -2363,6 +2680,8 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
     if (O.power_iters == 0 && !(O.alpha > 0.0)) return MV_ERR_INVALID_ARG;
+    if (O.momentum != 0 || O.backtrack != 0)
+        return record_message(MV_ERR_UNSUPPORTED, "batch solve: fixed step and FISTA momentum only");
     BatchLayout Lo;
     MV_TRY(batch_layout(probs, count, &Lo));
     MV_TRY(check_ws(d_ws, ws_bytes, Lo.total));

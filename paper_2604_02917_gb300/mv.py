@@ -69,7 +69,9 @@ class SolveOpts(C.Structure):
     _fields_ = [("max_iter", C.c_int32), ("kkt_every", C.c_int32), ("power_iters", C.c_int32),
                 ("warm_start", C.c_int32), ("eps", C.c_double), ("power_safety", C.c_double),
                 ("alpha", C.c_double), ("use_graph", C.c_int32), ("timing", C.c_int32),
-                ("checkpoint_every", C.c_int32), ("two_pass", C.c_int32)]
+                ("checkpoint_every", C.c_int32), ("two_pass", C.c_int32), ("momentum", C.c_int32),
+                ("backtrack", C.c_int32), ("m_f", C.c_double), ("bt_rho", C.c_double), ("bt_alpha0", C.c_double),
+                ("proj_budget", C.c_int32), ("dykstra_iters", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -78,7 +80,8 @@ class SolveInfo(C.Structure):
                 ("alpha", C.c_double), ("lambda_hat", C.c_double), ("nu", C.c_double),
                 ("launches", C.c_int32), ("timed_pairs", C.c_int32), ("t_gemv_t_ms", C.c_double),
                 ("t_gemv_n_ms", C.c_double), ("t_step_ms", C.c_double), ("proj_steps", C.c_int32),
-                ("refine_iterations", C.c_int32), ("fused", C.c_int32), ("t_fused_ms", C.c_double)]
+                ("refine_iterations", C.c_int32), ("fused", C.c_int32), ("t_fused_ms", C.c_double),
+                ("backtracks", C.c_int32), ("dykstra", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
