@@ -386,6 +386,9 @@ def main():
             torch.cuda.synchronize()
             if i >= 2:
                 e_times.append(a0.elapsed_time(a1))
+            # release this step's factor before the next upload: the next one
+            # reuses the same device block (and the solver's cached graph)
+            e_solver._keep = None
             del L2, mu2, rs2
         e2e = {"value": float(np.mean(e_times)) / 1e3, "unit": "s",
                "h2d_bytes_per_step": int(R32.nbytes), "d2h_bytes_per_step": int(model.n * 8)}
