@@ -32,13 +32,43 @@ constexpr int kSigChunk = 16;                 // k-steps (of 64) per tensor-memo
 using SigCfg = GemmCfg<kSigTile>;
 constexpr size_t kSigSmem = 1024 + (size_t)SigCfg::S * SigCfg::STAGE + (2 * SigCfg::S + 4) * 8 + 16;
 
+// Tile order: the upper triangle is walked in super-blocks of kSigGroup x
+// kSigGroup tiles (row-major inside each, super-blocks row-major over the
+// upper triangle), so the ~150 CTAs that run at the same time share about
+// 2 kSigGroup operand panels and read them from L2 rather than HBM.
+constexpr int kSigGroup = 12;
+
 __device__ __forceinline__ void tile_of(int t, int nb, int &I, int &J) {
-    I = 0;
-    while (t >= nb - I) {
-        t -= nb - I;
-        ++I;
+    const int nsb = (nb + kSigGroup - 1) / kSigGroup;
+    for (int P = 0; P < nsb; ++P) {
+        const int i0 = P * kSigGroup, ri = min(nb, i0 + kSigGroup) - i0;
+        for (int Q = P; Q < nsb; ++Q) {
+            const int j0 = Q * kSigGroup, rj = min(nb, j0 + kSigGroup) - j0;
+            if (Q == P) {                             // triangle of ri (ri + 1) / 2 tiles
+                const int cnt = ri * (ri + 1) / 2;
+                if (t < cnt) {
+                    int a = 0;
+                    while (t >= ri - a) {
+                        t -= ri - a;
+                        ++a;
+                    }
+                    I = i0 + a;
+                    J = i0 + a + t;
+                    return;
+                }
+                t -= cnt;
+            } else {                                  // rectangle of ri x rj tiles
+                const int cnt = ri * rj;
+                if (t < cnt) {
+                    I = i0 + t / rj;
+                    J = j0 + t % rj;
+                    return;
+                }
+                t -= cnt;
+            }
+        }
     }
-    J = I + t;
+    I = J = 0;                                        // not reached: t < nb (nb + 1) / 2
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {

@@ -1041,8 +1041,8 @@ static void launch_init_x(const Plan &p, const mv_problem *P, const mv_solve_opt
 }
 
 // Sigma y32 -> out64 (and out32) over the upper tiles of Sigma.
-static void launch_symv(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *out64,
-                        float *out32, cudaStream_t s) {
+static int launch_symv(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *out64,
+                       float *out32, cudaStream_t s) {
     SymvArgs a;
     a.S = reinterpret_cast<const float *>(P->L);
     a.ld = P->ld;
@@ -1054,16 +1054,14 @@ static void launch_symv(const Plan &p, const mv_problem *P, const float *y32, vo
     a.out64 = out64;
     a.out32 = out32;
     a.done = done;
-    symv_launch(a, s);
+    a.err = at<int>(ws, p.o_err);
+    return symv_launch(a, s);
 }
 
 // L L^T y32 -> out64 by whichever product the plan uses (capturable).
 static int launch_product(const Plan &p, const mv_problem *P, const float *y32, void *ws, double *out64,
                           cudaStream_t s) {
-    if (p.sig) {
-        launch_symv(p, P, y32, ws, nullptr, out64, nullptr, s);
-        return MV_OK;
-    }
+    if (p.sig) return launch_symv(p, P, y32, ws, nullptr, out64, nullptr, s);
     if (p.use_llt) return launch_llt(p, P, y32, ws, nullptr, out64, nullptr, s);
     gemv_pair(p, P, y32, ws, nullptr, out64, s);
     return MV_OK;
@@ -1082,7 +1080,7 @@ static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_o
     if (ev) cudaEventRecord(ev[0], s);
     if (p.use_llt || p.sig) {
         if (p.sig)
-            launch_symv(p, P, y32, ws, done, gy, nullptr, s);
+            MV_TRY(launch_symv(p, P, y32, ws, done, gy, nullptr, s));
         else
             MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s));
         if (ev) cudaEventRecord(ev[1], s);
@@ -1236,7 +1234,8 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
     to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(d_y, rs, y32, p.n);
     if (p.sig) {
         MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_stick), 0, 4 * (size_t)p.snb, s));
-        launch_symv(p, P, y32, d_ws, nullptr, lz, nullptr, s);
+        MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
+        MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, lz, nullptr, s));
     } else if (p.use_llt) {
         MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
         MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
@@ -1284,7 +1283,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     if (!(O.alpha > 0.0)) {
         for (int it = 0; it < O.power_iters; ++it) {
             if (p.sig) {
-                launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s);
+                MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
                 launches += 2;
             } else if (p.use_llt) {
                 MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
@@ -1296,7 +1295,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
             power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
         }
         if (p.sig)
-            launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), nullptr, s);
+            MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), nullptr, s));
         else
             gemv_t_only(p, P, y32, d_ws, s);
         launches += 1;
@@ -1372,7 +1371,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     // Objective of the returned iterate: one more pass z = L^T x (or Sigma x).
     to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(at<double>(d_ws, p.o_x), rs, y32, p.n);
     if (p.sig) {
-        launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gobj), nullptr, s);
+        MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gobj), nullptr, s));
         objective_sigma_kernel<<<1, kStepThreads, 0, s>>>(st, at<double>(d_ws, p.o_x), at<double>(d_ws, p.o_gobj), p.n,
                                                           P->gamma);
     } else {
@@ -1390,7 +1389,7 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     h_info->status = hs.done ? hs.status : MV_ERR_NOT_CONVERGED;
     if (xerr != 0) {
         char msg[96];
-        snprintf(msg, sizeof(msg), "fused L L^T pass: pipeline wait timed out (code %d)", xerr);
+        snprintf(msg, sizeof(msg), "single-pass product: a bounded wait timed out (code %d)", xerr);
         h_info->status = record_message(MV_ERR_TIMEOUT, msg);
     }
     h_info->converged = hs.converged;

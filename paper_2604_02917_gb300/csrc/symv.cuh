@@ -39,6 +39,7 @@ struct SymvArgs {
     double *out64;           // n FP64: Sigma y
     float *out32;            // optional n FP32 copy
     const int *done;         // optional: return at once when set
+    int *err;                // error word of the caller (no wait here can time out)
 };
 
 __host__ __device__ inline int64_t symv_tiles(int nb) { return (int64_t)nb * (nb + 1) / 2; }
@@ -203,8 +204,10 @@ __global__ void __launch_bounds__(kSymThreads) symv_kernel(SymvArgs a) {
     }
 }
 
-inline void symv_launch(const SymvArgs &a, cudaStream_t s) {
+// Enqueue Sigma y (capturable): one CTA per upper tile.
+inline int symv_launch(const SymvArgs &a, cudaStream_t s) {
     symv_kernel<<<(unsigned)symv_tiles(a.nb), kSymThreads, 0, s>>>(a);
+    return MV_OK;
 }
 
 }  // namespace mv
