@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-row-oracles", action="store_true", help="skip the oracle timings of the further rows")
     return ap.parse_args()
 
 
@@ -263,6 +264,107 @@ def cpu_baseline(model, gpu_iters, power_iters, eps, R32=None, budget_s=25.0):
             "sample": f"FP64 NumPy oracle on the full {model.n}x{model.T} matrix: {p} power iterations "
                       f"({t_pow:.3f} s each) and {k} NPGA iterations with 2 literal KKT checks "
                       f"({t_k:.3f} s each), scaled to {power_iters} power + {gpu_iters} NPGA iterations"}
+
+
+def row_oracles(model, R32, res):
+    """The FP64 oracle timed beside each further row, on bounded samples of
+    the same workloads, each scaled to the full row by the stated factor
+    (host cores, as it stands; roughly 30-60 s in all)."""
+    from synth import CFG_SMALL, countsketch_hash, gaussian_sketch, power_start
+    from oracle.center import center_factor
+    from oracle.npga import gradient, gradient_sigma, initial_point, npga, power_norm2, step_size
+    from oracle.projection import project_F
+    from oracle import adjoint as oadj
+    from oracle import strmodel
+    cores = os.cpu_count()
+    out = {}
+    n, T, m = model.n, model.T, 8192
+
+    def entry(t_sample, scale, sample):
+        return {"value": t_sample * scale, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
+                "sample_s": round(t_sample, 3), "scale": round(scale, 2)}
+
+    mu, L, _ = center_factor(R32.astype(np.float64))
+    rows, Ts = 64, 6000
+    Ls = L[:rows, :Ts]
+    # a8 Gaussian sketch L Phi: 64 rows x 6000 periods of the full product
+    Phi_t = gaussian_sketch(Ts, m, seed=2)
+    t0 = time.perf_counter()
+    strmodel.sketch(Ls, Phi_t)
+    out["sketch"] = entry(time.perf_counter() - t0, (n / rows) * (T / Ts),
+                          f"L Phi on {rows} rows x {Ts} periods, m = {m}, scaled by rows and periods")
+    del Phi_t
+    # f2 CountSketch (dense Phi, as the oracle states it)
+    h, sg = countsketch_hash(Ts, m, seed=2)
+    t0 = time.perf_counter()
+    strmodel.countsketch(Ls, h, sg, m)
+    out["countsketch"] = entry(time.perf_counter() - t0, (n / rows) * (T / Ts),
+                               f"L Phi (dense CountSketch Phi) on {rows} rows x {Ts} periods, scaled")
+    # a9 truncation: eigh of tilde L tilde L^T at n' = 1360, scaled by (n / n')^3
+    nt = 1360
+    Lt = np.random.default_rng(3).standard_normal((nt, 2048)) * 1e-3
+    t0 = time.perf_counter()
+    strmodel.truncate(Lt, 512)
+    out["truncate"] = entry(time.perf_counter() - t0, (n / nt) ** 3,
+                            f"K = tilde L tilde L^T and eigh at n' = {nt}, scaled by (n / n')^3")
+    # f1 explicit Sigma: formation on 64 rows (scaled by n / 64) + 3 iterations on the full Sigma
+    t0 = time.perf_counter()
+    L[:rows] @ L.T
+    t_form = (time.perf_counter() - t0) * (n / rows)
+    # the solve's per-iteration cost only depends on n: time it on a synthetic SPD Sigma of the same size
+    A = np.random.default_rng(4).standard_normal((n, 256)) * 1e-2
+    Sig = A @ A.T + 1e-4 * np.eye(n)
+    Rt = float(np.percentile(mu, 60))
+    y = initial_point(mu, Rt)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        g = gradient_sigma(Sig, 0.0, y)
+        project_F(y - 1e-3 * g, mu, Rt)
+    t_it = (time.perf_counter() - t0) / 3
+    iters = res.get("sigma_iters", 50)
+    out["sigma"] = {"value": t_form + t_it * (50 + iters), "unit": "s", "cores": cores, "kind": "oracle",
+                    "sample": f"L L^T on 64 rows scaled by n / 64 ({t_form:.1f} s) + 3 iterations (Sigma y and the "
+                              f"projection, {t_it * 1e3:.0f} ms each) scaled to 50 power + {iters} NPGA iterations"}
+    del Sig, A
+    # a11 frontier: 2 of the 64 targets at 200 x 1000, scaled by 32
+    Rf = factor_returns_small()
+    muf, Lf, _ = center_factor(Rf)
+    tg = np.linspace(np.percentile(muf, 10), np.percentile(muf, 90), 64)
+    lam = power_norm2(Lf, power_start(Lf.shape[0]), 50)
+    t0 = time.perf_counter()
+    for r in tg[:2]:
+        npga(Lf, 0.0, muf, float(r), initial_point(muf, float(r)), step_size(lam, 0.0), eps=1e-6, max_iter=20000)
+    out["frontier_200x1000"] = entry(time.perf_counter() - t0, 32.0, "2 of the 64 targets at 200 x 1000, scaled by 32")
+    # a13 adjoint: 20 of the 500 unrolled iterations at 2000 x 10000 (forward + reverse), scaled by 25
+    am = CFG_SMALL.scaled(2000, 10000, seed=0)
+    from synth import factor_returns
+    mua, La, _ = center_factor(factor_returns(am, np.float32).astype(np.float64))
+    Rta = float(np.percentile(mua, 60))
+    x0 = initial_point(mua, Rta)
+    a = step_size(power_norm2(La, power_start(am.n), 50), 0.0)
+    t0 = time.perf_counter()
+    x, tape, betas = oadj.unrolled_forward(La, 0.0, mua, Rta, x0, a, 20, record=True)
+    oadj.backward(La, 0.0, mua, a, tape, betas, np.ones(am.n))
+    out["adjoint"] = entry(time.perf_counter() - t0, 25.0, "forward + reverse of 20 of the 500 iterations, scaled by 25")
+    # a12 batch: the oracle's per-iteration cost is proportional to n T; time 3 iterations at 1000 x 4000
+    # and scale by the batch's sum over problems of n_j T_j (50 power + its iterations)
+    if res.get("batch_elem_iters"):
+        Lb = La[:1000, :4000]
+        mub = mua[:1000]
+        Rtb = float(np.percentile(mub, 60))
+        yb = initial_point(mub, Rtb)
+        t0 = time.perf_counter()
+        for _ in range(3):
+            project_F(yb - 1e-3 * gradient(Lb, 0.0, yb), mub, Rtb)
+        t_el = (time.perf_counter() - t0) / 3 / (1000 * 4000)
+        out["batch"] = {"value": t_el * res["batch_elem_iters"], "unit": "s", "cores": cores, "kind": "oracle",
+                        "sample": "3 iterations at 1000 x 4000, scaled by sum_j n_j T_j (50 + iterations_j)"}
+    return out
+
+
+def factor_returns_small():
+    from synth import CFG_SMALL, factor_returns
+    return factor_returns(CFG_SMALL, np.float32).astype(np.float64)
 
 
 def reference_arm(args):
@@ -606,6 +708,14 @@ def main():
             entry = {"targets": 64, "value": f0.elapsed_time(f1) / reps / 1e3, "unit": "s",
                      "max_iterations": max(i["iterations"] for i in finfo),
                      "all_converged": all(i["converged"] == 1 for i in finfo), "dtype": fdt}
+            # algorithmic bytes: 50 fused power passes over L + two GEMMs (L^T and L) per loop iteration
+            fe = 2 if fdt == "bf16" else 1
+            fbytes = fm.n * fm.T * fe * (50 + 2 * (entry["max_iterations"] + 1))
+            peak, peak_kind = peaks()
+            fgbs = fbytes / entry["value"] / 1e9
+            entry["roofline"] = {"bound": "hbm", "achieved": round(fgbs, 1), "peak": peak, "unit": "GB/s",
+                                 "frac": round(fgbs / peak, 4), "peak_source": peak_kind, "traffic": None,
+                                 "note": "L is L2-resident at 200 x 1000" if fm is not model else "algorithmic"}
             if tag == "200x1000":
                 # the same 64 targets as independent FP32 solves, one after another
                 Lf32, _, _, _ = mv.center_factor(Rfd, "f32")
@@ -645,6 +755,7 @@ def main():
 
     # 256 independent problems, n ~ U[500,5000], T ~ U[2000,20000] (grouped launches).
     batch = None
+    batch_elem_iters = 0
     if not args.no_batch and args.dtype == "f32":
         from synth import factor_returns_device, uneven_problem_sizes
         models = uneven_problem_sizes(args.batch_count)
@@ -677,7 +788,12 @@ def main():
         iters = [i["iterations"] for i in binfos]
         # bytes streamed: 2 passes of every L per power iteration (50) and per NPGA iteration it ran
         moved = sum(2 * 4 * bm.n * bm.T * (50 + it + 1) for bm, it in zip(models, iters))
+        batch_elem_iters = sum(bm.n * bm.T * (50 + it + 1) for bm, it in zip(models, iters))
+        peak, peak_kind = peaks()
         batch = {"problems": len(models), "elements": elems, "value": bt, "unit": "s",
+                 "roofline": {"bound": "hbm", "achieved": round(moved / bt / 1e9, 1), "peak": peak, "unit": "GB/s",
+                              "frac": round(moved / bt / 1e9 / peak, 4), "peak_source": peak_kind, "traffic": None,
+                              "note": "two passes of every L per power and NPGA iteration (algorithmic)"},
                  "problems_per_s": len(models) / bt, "all_converged": all(i["converged"] == 1 for i in binfos),
                  "iterations_min": min(iters), "iterations_max": max(iters),
                  "aggregate_GBps": moved / bt / 1e9, "data": "synthetic, drawn on the GPU (torch seeded stream)",
@@ -691,6 +807,22 @@ def main():
         del L
         torch.cuda.empty_cache()
         cb = cpu_baseline(model, iters, 50, args.eps, R32=R32)
+        if not args.no_row_oracles:
+            res = {"sigma_iters": sigma_res["f32_L"]["iterations"] if sigma_res else 50,
+                   "batch_elem_iters": batch_elem_iters}
+            row_cpu = row_oracles(model, R32, res)
+            if str_res is not None:
+                for k in ("sketch", "countsketch", "truncate"):
+                    if k in str_res:
+                        str_res[k]["cpu_oracle"] = row_cpu[k]
+            if sigma_res is not None:
+                sigma_res["cpu_oracle"] = row_cpu["sigma"]
+            if frontier is not None and "200x1000" in frontier:
+                frontier["200x1000"]["cpu_oracle"] = row_cpu["frontier_200x1000"]
+            if adj is not None:
+                adj["cpu_oracle"] = row_cpu["adjoint"]
+            if batch is not None and "batch" in row_cpu:
+                batch["cpu_oracle"] = row_cpu["batch"]
     if rank == 0:
         last = infos[-1]
         line = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
