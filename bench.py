@@ -76,6 +76,17 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value, world, device):
+    """The largest of every rank's value (the whole job waits for its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload(args, rank):
     from synth import CFG_FULL, CFG_SMALL
     base = CFG_FULL if args.config == "full" else CFG_SMALL
@@ -446,11 +457,7 @@ def main():
     ev1.record(stream)
     barrier()
     clocks = clk.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     tinfos = launch_profile(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
                             layout=args.layout, two_pass=1 if args.two_pass else 0)
 

@@ -1,0 +1,55 @@
+"""Multi-rank host logic of bench.py, on the CPU with gloo (world size 2).
+
+Every GPU run here has one GPU, so the N > 1 path is replicas (one
+independent problem per rank, weak scaling); what it adds on the host is
+checked here: the max-over-ranks time, distinct per-rank workloads, and the
+reference arm running on rank 0 only.
+"""
+import os
+import socket
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as tmp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        r, w, _ = bench.dist_env()
+        assert (r, w) == (rank, world)
+        m = bench.max_over_ranks(10.0 + 5.0 * rank, world, torch.device("cpu"))
+        class A:
+            config, shape = "small", None
+        wl = bench.workload(A, rank)
+        ref = bench.reference_arm(type("B", (), {"gpus": world, "steps": 1, "warmup": 0, "eps": 1e-6,
+                                                 "config": "small", "shape": None})) if rank == 1 else None
+        out[rank] = (m, wl.seed, wl.n, wl.T, ref)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_gloo():
+    world = 2
+    mgr = tmp.Manager()
+    out = mgr.dict()
+    tmp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    (m0, s0, n0, T0, _), (m1, s1, n1, T1, ref1) = out[0], out[1]
+    assert m0 == m1 == 15.0                     # both ranks see the slowest rank's time
+    assert s0 != s1 and (n0, T0) == (n1, T1)     # same shape, independent problems (weak scaling)
+    assert ref1 is None                          # the reference arm prints on rank 0 only
