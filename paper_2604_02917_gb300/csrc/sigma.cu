@@ -13,9 +13,10 @@
 //            the workspace, one segment; the epilogue multiplies by
 //            s_i s_j, since Sigma = diag(s) Q Q^T diag(s);
 //   MV_F32   L = H + D with H = bf16(L), D = bf16(L - H) in the workspace;
-//            Sigma ~= H H^T + H D^T + D H^T as three K-segments accumulated
-//            into one tile (the dropped D D^T and the rounding of D are
-//            below 2^-16 |L_i| |L_j| per product term).
+//            Sigma ~= H H^T + H D^T + D H^T: each k-step stages the four
+//            boxes H_I, D_I, H_J, D_J once and issues the three products
+//            into one accumulator (the dropped D D^T and the rounding of D
+//            are below 2^-16 |L_i| |L_j| per product term).
 //
 // Pipeline per CTA as in gemm.cuh: warp 0 (one thread) TMA producer over a
 // 6-stage ring, warp 1 (one thread) MMA issuer (128 x 128 x 16 per
@@ -28,9 +29,17 @@
 namespace mv {
 
 constexpr int kSigTile = 128;                 // BM = BN
-constexpr int kSigChunk = 16;                 // k-steps (of 64) per tensor-memory partial sum
-using SigCfg = GemmCfg<kSigTile>;
-constexpr size_t kSigSmem = 1024 + (size_t)SigCfg::S * SigCfg::STAGE + (2 * SigCfg::S + 4) * 8 + 16;
+constexpr uint32_t kSigBox = kSigTile * kBK * 2;   // one 128 x 64 BF16 operand box (16 KB)
+// Stage geometry by number of products per k-step: one (BF16, FP8) = boxes
+// A, B and 6 stages; three (FP32 split) = boxes H_I, D_I, H_J, D_J and 3 stages.
+// A tensor-memory partial sums at most 64 MMAs (16 k-steps x 4, or 5 x 12).
+template <int NSEG> struct SigGeo {
+    static constexpr int BOXES = NSEG == 3 ? 4 : 2;
+    static constexpr int S = NSEG == 3 ? 3 : 6;
+    static constexpr uint32_t STAGE = BOXES * kSigBox;
+    static constexpr int CHUNK = NSEG == 3 ? 5 : 16;
+};
+constexpr size_t kSigSmem = 1024 + 6 * (size_t)2 * kSigBox + (2 * 6 + 4) * 8 + 16;   // the larger of the two
 
 // Tile order: the upper triangle is walked in super-blocks of kSigGroup x
 // kSigGroup tiles (row-major inside each, super-blocks row-major over the
@@ -79,7 +88,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // accumulator with a rounding that loses up to about an ulp of the running
 // sum, with one sign when the terms have one sign (the diagonal of Sigma):
 // over thousands of MMAs that is a bias of order 1e-4.  So a tile is
-// accumulated in chunks of kSigChunk k-steps, alternately into two
+// accumulated in chunks of at most 64 MMAs (SigGeo::CHUNK k-steps), alternately into two
 // 128-column tensor-memory buffers; the epilogue warps add every finished
 // chunk into FP32 registers (round-to-nearest, fixed order) while the MMA
 // warp fills the other buffer.
@@ -87,23 +96,23 @@ template <int NSEG>
 __global__ void __launch_bounds__(kGemmThreads, 1)
 sigma_gemm_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmD, int n, int K,
                   int nb, const float *__restrict__ rs, float *__restrict__ Sig, int64_t ldS) {
-    constexpr int S = SigCfg::S;
+    using Geo = SigGeo<NSEG>;
+    constexpr int S = Geo::S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    uint8_t *sA = smem;
-    uint8_t *sB = smem + S * SigCfg::A_BYTES;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * SigCfg::STAGE);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * Geo::STAGE);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * S + 4);
     const uint32_t full0 = umma::smem_u32(bars), empty0 = umma::smem_u32(bars + S);
     const uint32_t accf0 = umma::smem_u32(bars + 2 * S), acce0 = umma::smem_u32(bars + 2 * S + 2);
+    // box b of stage s
+    auto box = [&](int st, int b) { return umma::smem_u32(smem + (size_t)st * Geo::STAGE + (size_t)b * kSigBox); };
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int I, J;
     tile_of(blockIdx.x, nb, I, J);
     const int m0 = I * kSigTile, n0 = J * kSigTile;
-    const int nk = (K + kBK - 1) / kBK;
-    const int steps = NSEG * nk;
-    const int nchunks = (steps + kSigChunk - 1) / kSigChunk;
+    const int steps = (K + kBK - 1) / kBK;
+    const int nchunks = (steps + Geo::CHUNK - 1) / Geo::CHUNK;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
@@ -136,13 +145,17 @@ sigma_gemm_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant
                     atomicExch(&g_gemm_err, 1);
                     break;
                 }
-                const int seg = g / nk, kt = g - seg * nk;
-                // segments: (H, H), (H, D), (D, H)
-                const CUtensorMap *ma = seg == 2 ? &tmD : &tmH;
-                const CUtensorMap *mb = seg == 1 ? &tmD : &tmH;
-                umma::mbar_arrive_expect_tx(full0 + 8 * s, SigCfg::STAGE);
-                umma::tma_load_2d(umma::smem_u32(sA + s * SigCfg::A_BYTES), ma, kt * kBK, m0, full0 + 8 * s);
-                umma::tma_load_2d(umma::smem_u32(sB + s * SigCfg::B_BYTES), mb, kt * kBK, n0, full0 + 8 * s);
+                const uint32_t fb = full0 + 8 * s;
+                umma::mbar_arrive_expect_tx(fb, Geo::STAGE);
+                if (NSEG == 3) {                       // H_I, D_I, H_J, D_J
+                    umma::tma_load_2d(box(s, 0), &tmH, g * kBK, m0, fb);
+                    umma::tma_load_2d(box(s, 1), &tmD, g * kBK, m0, fb);
+                    umma::tma_load_2d(box(s, 2), &tmH, g * kBK, n0, fb);
+                    umma::tma_load_2d(box(s, 3), &tmD, g * kBK, n0, fb);
+                } else {                               // A_I, A_J
+                    umma::tma_load_2d(box(s, 0), &tmH, g * kBK, m0, fb);
+                    umma::tma_load_2d(box(s, 1), &tmH, g * kBK, n0, fb);
+                }
             }
         }
         __syncwarp();
@@ -158,7 +171,7 @@ sigma_gemm_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant
                 }
                 umma::fence_after_sync();
                 const uint32_t acc = tmem + (uint32_t)(b * kSigTile);
-                const int g0 = c * kSigChunk, g1 = min(steps, g0 + kSigChunk);
+                const int g0 = c * Geo::CHUNK, g1 = min(steps, g0 + Geo::CHUNK);
                 for (int g = g0; g < g1; ++g) {
                     const int s = g % S;
                     const uint32_t ph = (uint32_t)(g / S) & 1u;
@@ -168,11 +181,22 @@ sigma_gemm_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant
                         break;
                     }
                     umma::fence_after_sync();
-                    const uint64_t da = umma::desc_kmajor_sw128(umma::smem_u32(sA + s * SigCfg::A_BYTES));
-                    const uint64_t db = umma::desc_kmajor_sw128(umma::smem_u32(sB + s * SigCfg::B_BYTES));
+                    if (NSEG == 3) {
+                        // H_I H_J^T + H_I D_J^T + D_I H_J^T from the one stage
+                        const uint64_t hi = umma::desc_kmajor_sw128(box(s, 0)), di = umma::desc_kmajor_sw128(box(s, 1));
+                        const uint64_t hj = umma::desc_kmajor_sw128(box(s, 2)), dj = umma::desc_kmajor_sw128(box(s, 3));
 #pragma unroll
-                    for (int k = 0; k < kBK / 16; ++k)
-                        umma::mma_bf16(acc, da + 2 * k, db + 2 * k, idesc, (g != g0 || k != 0) ? 1u : 0u);
+                        for (int k = 0; k < kBK / 16; ++k) {
+                            umma::mma_bf16(acc, hi + 2 * k, hj + 2 * k, idesc, (g != g0 || k != 0) ? 1u : 0u);
+                            umma::mma_bf16(acc, hi + 2 * k, dj + 2 * k, idesc, 1u);
+                            umma::mma_bf16(acc, di + 2 * k, hj + 2 * k, idesc, 1u);
+                        }
+                    } else {
+                        const uint64_t da = umma::desc_kmajor_sw128(box(s, 0)), db = umma::desc_kmajor_sw128(box(s, 1));
+#pragma unroll
+                        for (int k = 0; k < kBK / 16; ++k)
+                            umma::mma_bf16(acc, da + 2 * k, db + 2 * k, idesc, (g != g0 || k != 0) ? 1u : 0u);
+                    }
                     umma::mma_commit(empty0 + 8 * s);
                 }
                 if (ok) umma::mma_commit(accf0 + 8 * b);

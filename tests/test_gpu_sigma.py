@@ -6,7 +6,7 @@ grad f = 2 Sigma y + 2 gamma y).
   arithmetic, in units of (|L_q| |L_q|^T)_ij and u = 2^-24: the tensor core
   accumulates at most 64 MMAs (1024 k-columns) into one FP32 partial, losing
   up to about an ulp of the partial per MMA (128 u); the nc partials
-  (nc = segments * ceil(T / 64) / 16) are added in FP32 with
+  (nc = ceil(T / 64) / 5 for FP32 L, ceil(T / 64) / 16 else) are added in FP32 with
   round-to-nearest (nc u); for FP32 L the BF16 hi/lo split drops terms below
   3 * 2^-18; for FP8 the row-scale product adds two roundings.  Sigma must
   be exactly symmetric.  Before partials were promoted to registers the
@@ -66,8 +66,8 @@ def held(L, rs, n, T, dt):
 
 
 def form_rel(T, dt):
-    segs = 3 if dt == "f32" else 1
-    nc = -(-segs * -(-T // 64) // 16)
+    # FP32: three products per k-step, chunks of 5 k-steps (60 MMAs); else chunks of 16 (64 MMAs)
+    nc = -(-(-(-T // 64)) // (5 if dt == "f32" else 16))
     rel = (128 + nc + 16) * U
     if dt == "f32":
         rel += 3.0 * 2.0 ** -18
