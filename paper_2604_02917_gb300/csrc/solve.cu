@@ -1141,13 +1141,10 @@ struct GraphKeyHash {
 static std::mutex g_graph_mu;
 static std::unordered_map<GraphKey, cudaGraphExec_t, GraphKeyHash> g_graphs;
 
-static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
-                           const cudaEvent_t *ev, cudaGraphExec_t *out) {
-    GraphKey key{P->L, P->mu, P->row_scale, ws, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
-                 O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? 1 : 0), P->R_target, P->gamma, O->eps, (const void *)ev,
-                 O->momentum, O->backtrack, O->proj_budget, O->dykstra_iters, O->bt_rho, O->m_f};
-    int dev = 0;
-    cudaGetDevice(&dev);
+// Returns the cached executable graph of `key`, capturing `enqueue(stream)`
+// into it on first use.
+template <typename F>
+static int cached_graph(const GraphKey &key, F &&enqueue, cudaGraphExec_t *out) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it != g_graphs.end()) {
@@ -1161,8 +1158,7 @@ static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_op
         cudaStreamDestroy(cs);
         return MV_ERR_CUDA;
     }
-    int lst = MV_OK;
-    for (int c = 0; c < chunk && lst == MV_OK; ++c) lst = launch_iteration(p, P, O, ws, cs, ev ? ev + 3 * c : nullptr);
+    const int lst = enqueue(cs);
     cudaError_t e = cudaStreamEndCapture(cs, &graph);
     cudaStreamDestroy(cs);
     if (lst != MV_OK) {
@@ -1180,8 +1176,60 @@ static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_op
     }
     g_graphs.emplace(key, exec);
     *out = exec;
-    (void)dev;
     return MV_OK;
+}
+
+static GraphKey graph_key(const Plan &p, const mv_problem *P, const mv_solve_opts *O, int chunk, const void *ev) {
+    return GraphKey{P->L, P->mu, P->row_scale, nullptr, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
+                    O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? 1 : 0), P->R_target, P->gamma, O->eps, ev,
+                    O->momentum, O->backtrack, O->proj_budget, O->dykstra_iters, O->bt_rho, O->m_f};
+}
+
+static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
+                           const cudaEvent_t *ev, cudaGraphExec_t *out) {
+    GraphKey key = graph_key(p, P, O, chunk, (const void *)ev);
+    key.ws = ws;
+    return cached_graph(key, [&](cudaStream_t cs) {
+        int lst = MV_OK;
+        for (int c = 0; c < chunk && lst == MV_OK; ++c) lst = launch_iteration(p, P, O, ws, cs, ev ? ev + 3 * c : nullptr);
+        return lst;
+    }, out);
+}
+
+// The power method of Sec. 3.1: u <- L L^T u / ||L L^T u|| power_iters
+// times from the y32 that setup wrote, then the product that lambda_hat
+// reads (z = L^T u, or Sigma u); capturable.  Adds the launches to *count.
+static int launch_power(const Plan &p, const mv_problem *P, int power_iters, void *ws, cudaStream_t s, int *count) {
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    float *y32 = at<float>(ws, p.o_y32);
+    for (int it = 0; it < power_iters; ++it) {
+        if (p.sig) {
+            MV_TRY(launch_symv(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), at<float>(ws, p.o_g32), s));
+            *count += 2;
+        } else if (p.use_llt) {
+            MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), at<float>(ws, p.o_g32), s));
+            *count += 2;
+        } else {
+            gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), s, at<float>(ws, p.o_g32));
+            *count += 3;
+        }
+        power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(ws, p.o_g32), rs, y32, p.n);
+    }
+    if (p.sig)
+        MV_TRY(launch_symv(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), nullptr, s));
+    else
+        gemv_t_only(p, P, y32, ws, s);
+    *count += 1;
+    return cudaGetLastError() == cudaSuccess ? MV_OK : MV_ERR_CUDA;
+}
+
+static int get_power_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
+                           cudaGraphExec_t *out) {
+    GraphKey key = graph_key(p, P, O, -1 - O->power_iters, nullptr);
+    key.ws = ws;
+    int dummy = 0;
+    return cached_graph(key, [&](cudaStream_t cs) { return launch_power(p, P, O->power_iters, ws, cs, &dummy); },
+                        out);
 }
 
 }  // namespace mv
@@ -1278,27 +1326,20 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     if (p.use_llt) MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
     if (p.sig) MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_stick), 0, 4 * (size_t)p.snb, s));
     setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
-    // Power method for ||L_eff||_2^2 (skipped when the step is given).
+    // Power method for ||L_eff||_2^2 (skipped when the step is given): one
+    // cached graph of all its launches, or host-issued when graphs are off.
     int launches = 4;
     if (!(O.alpha > 0.0)) {
-        for (int it = 0; it < O.power_iters; ++it) {
-            if (p.sig) {
-                MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
-                launches += 2;
-            } else if (p.use_llt) {
-                MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
-                launches += 2;
-            } else {
-                gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
-                launches += 3;
-            }
-            power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
+        if (O.use_graph && !O.timing) {
+            cudaGraphExec_t pexec = nullptr;
+            MV_TRY(get_power_graph(p, P, &O, d_ws, &pexec));
+            MV_CUDA_TRY(cudaGraphLaunch(pexec, s));
+            int cnt = 0;
+            for (int it = 0; it < O.power_iters; ++it) cnt += (p.sig || p.use_llt) ? 2 : 3;
+            launches += cnt + 1;
+        } else {
+            MV_TRY(launch_power(p, P, O.power_iters, d_ws, s, &launches));
         }
-        if (p.sig)
-            MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), nullptr, s));
-        else
-            gemv_t_only(p, P, y32, d_ws, s);
-        launches += 1;
     }
     if (p.sig)
         step_size_sigma_kernel<<<1, kStepThreads, 0, s>>>(st, y32, at<double>(d_ws, p.o_gy), (O.alpha > 0.0) ? 0 : p.n,
