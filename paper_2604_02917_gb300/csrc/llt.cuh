@@ -58,6 +58,7 @@ struct LltArgs {
     double *gq;                // [groups x n] group sums
     double *g;                 // n: L L^T y (row-scaled)
     float *g32;                // n or null
+    float *z;                  // T or null: z = L^T y, the slices the exchange forms anyway
     unsigned *tick1;           // [C x kLltMaxGroups], zero between launches
     unsigned *tick2;           // [C], zero between launches
     int *err;                  // error word (0 = fine)
@@ -391,6 +392,8 @@ llt_kernel(const __grid_constant__ CUtensorMap tmL, const LltArgs a) {
 #pragma unroll
                 for (int k = 0; k < C * NG; ++k) z += sl[k * W];
                 zc[tid] = z;
+                const int zcol = (cid + j * a.G) * W + tid;
+                if (a.z != nullptr && rank == 0 && zcol < a.T) a.z[zcol] = z;
                 if (tid == 0 && j + kLltSlots < nj) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
             }
             llt::bar_consumers();
@@ -616,6 +619,8 @@ lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
 #pragma unroll
                     for (int hh = 0; hh < WPR; ++hh) z += sl[r * NP + hh * W + tid];
                 zc[tid] = z;
+                const int zcol = (cid + j * a.G) * W + tid;
+                if (a.z != nullptr && rank == 0 && zcol < a.T) a.z[zcol] = z;
                 if (tid == 0 && j + kLltSlots < nj) umma::mbar_arrive_expect_tx(xchg0 + 8 * q, xbytes);
             }
             llt::bar_consumers();

@@ -43,9 +43,11 @@ LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device, bool tn = false
 
 // Enqueues g = L L^T y (row-scaled; FP8 y32 pre-multiplied by the scale) on
 // stream s; capturable.  done (nullable): the launch returns at once if *done.
+// z (nullable): also writes z = L^T y (T floats), which the pass forms anyway.
 // For a transposed plan, L points at L^T (T x n, leading dim ld).
 int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
-               const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s);
+               const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s,
+               float *z = nullptr);
 
 // Per-dtype entry points (llt_<dtype>.cu).
 int llt_max_clusters_f32(int C, int RB, size_t smem);

@@ -115,7 +115,8 @@ LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device, bool tn) {
 }
 
 int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
-               const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s) {
+               const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s,
+               float *z) {
     if (!lp.ok) return MV_ERR_UNSUPPORTED;
     CUtensorMap map;
     if (lp.tn)
@@ -129,6 +130,7 @@ int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, i
     a.gq = sc.gq;
     a.g = g;
     a.g32 = g32;
+    a.z = z;
     a.tick1 = sc.tickets;
     a.tick2 = sc.tickets + (size_t)kLltMaxCluster * kLltMaxGroups;
     a.err = sc.err;

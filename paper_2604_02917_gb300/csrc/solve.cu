@@ -50,6 +50,7 @@ struct Plan {
     int t_blocks, t_splits, t_rows;        // gemv_t grid
     int n_groups, n_splits, n_cols;        // gemv_n grid
     bool use_llt;                          // fused single-pass L L^T y (llt.cuh)
+    bool want_z;                           // the loop's fused pass also writes z = L^T y to o_z
     LltPlan lp;
     bool sig;                              // explicit Sigma (symv.cuh) instead of a factor
     int snb;                               // Sigma tile rows
@@ -902,11 +903,11 @@ static void launch_g(const Plan &p, const mv_problem *P, const float *z, void *w
 
 // g = L L^T y (row-scaled) in one pass over L; capturable (no synchronisation).
 static int launch_llt(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
-                      float *g32, cudaStream_t s) {
+                      float *g32, cudaStream_t s, float *z = nullptr) {
     LltScratch sc = llt_scratch(at<char>(ws, p.o_llt), p.n);
     sc.err = at<int>(ws, p.o_err);             // read back by the solve
     return llt_launch(p.lp, p.dt, P->L, p.n, p.T, p.ld, y32, P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr, sc,
-                      done, g_out, g32, s);
+                      done, g_out, g32, s, z);
 }
 
 // Kernel attributes are set once per process, before any stream capture.
@@ -1082,7 +1083,7 @@ static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_o
         if (p.sig)
             MV_TRY(launch_symv(p, P, y32, ws, done, gy, nullptr, s));
         else
-            MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s));
+            MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s, p.want_z ? at<float>(ws, p.o_z) : nullptr));
         if (ev) cudaEventRecord(ev[1], s);
         if (ev) cudaEventRecord(ev[2], s);
         launch_step(p, P, O, ws, s);
@@ -1123,12 +1124,13 @@ struct GraphKey {
     const void *ev;
     int momentum, backtrack, budget, dyk_iters;
     double bt_rho, m_f;
+    double aux = 0.0;                    // any further scalar baked into the graph (the adjoint's alpha)
     bool operator==(const GraphKey &o) const {
         return L == o.L && mu == o.mu && rs == o.rs && ws == o.ws && n == o.n && T == o.T && ld == o.ld &&
                dt == o.dt && mode == o.mode && kkt_every == o.kkt_every && max_iter == o.max_iter &&
                chunk == o.chunk && fused == o.fused && R == o.R && gamma == o.gamma && eps == o.eps && ev == o.ev &&
                momentum == o.momentum && backtrack == o.backtrack && budget == o.budget &&
-               dyk_iters == o.dyk_iters && bt_rho == o.bt_rho && m_f == o.m_f;
+               dyk_iters == o.dyk_iters && bt_rho == o.bt_rho && m_f == o.m_f && aux == o.aux;
     }
 };
 struct GraphKeyHash {
@@ -1181,7 +1183,7 @@ static int cached_graph(const GraphKey &key, F &&enqueue, cudaGraphExec_t *out) 
 
 static GraphKey graph_key(const Plan &p, const mv_problem *P, const mv_solve_opts *O, int chunk, const void *ev) {
     return GraphKey{P->L, P->mu, P->row_scale, nullptr, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
-                    O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? 1 : 0), P->R_target, P->gamma, O->eps, ev,
+                    O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? (p.want_z ? 3 : 1) : 0), P->R_target, P->gamma, O->eps, ev,
                     O->momentum, O->backtrack, O->proj_budget, O->dykstra_iters, O->bt_rho, O->m_f};
 }
 
@@ -1269,7 +1271,7 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
                 mv_stream_t stream) {
     MV_TRY(validate_problem(P));
     if (d_y == nullptr || d_g == nullptr || (is_sigma(P) && d_z != nullptr)) return MV_ERR_INVALID_ARG;
-    const Plan p = plan_for(P, d_z == nullptr);
+    const Plan p = plan_for(P, true);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();
@@ -1287,7 +1289,7 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
     } else if (p.use_llt) {
         MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
         MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
-        MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, lz, nullptr, s));
+        MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, lz, nullptr, s, d_z ? at<float>(d_ws, p.o_z) : nullptr));
     } else {
         gemv_pair(p, P, y32, d_ws, nullptr, lz, s);
     }
@@ -2047,9 +2049,13 @@ __device__ void cluster_sums(ProjSmem *sh, double (&v)[NV], double *dslots /* [2
 
 struct AdjArgs {
     const double *x1;          // x_{k+1} (support and values)
-    double nu;                 // return-row multiplier of that projection
-    int active;                // 1 if the return row is tight
-    double beta;               // beta_k
+    // nu_j (the return-row multiplier of that projection) and beta_{k0 + j}
+    // are read on the device, so a captured segment replays for any k0
+    const double *nu_tape;     // segment tape of nu
+    const double *betas;       // beta_k, k = 0 .. K-1
+    const int *k0;             // first iteration of the segment
+    int j;                     // position in the segment
+    int eq;                    // 1: equality mode (the return row always tight)
     double *xbar, *ybar, *mubar;
     double *vbar;              // out: v_bar (FP64)
     float *vbar32;             // out: v_bar as the gemv input
@@ -2065,11 +2071,13 @@ __global__ void __launch_bounds__(kProjNT) adj_proj_kernel(AdjArgs a) {
     __shared__ double dsl[2 * kProjMaxCL * 5];
     const int rank = cluster_rank<CL>();
     const int n = a.n, nl = (n + CL - 1) / CL, r0 = min(n, rank * nl), r1 = min(n, r0 + nl);
+    const double nu = a.nu_tape[a.j], beta = a.betas[*a.k0 + a.j];
+    const bool active = a.eq || nu != 0.0;
     proj_smem_init(&psm);
     double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // |S|, sum mu, sum mu^2, sum a, sum mu a
     for (int i = r0 + threadIdx.x; i < r1; i += kProjNT) {
         if (a.x1[i] > 0.0) {
-            const double m = a.mu[i], ab = a.xbar[i] + (1.0 + a.beta) * a.ybar[i];
+            const double m = a.mu[i], ab = a.xbar[i] + (1.0 + beta) * a.ybar[i];
             s[0] += 1.0;
             s[1] += m;
             s[2] = fma(m, m, s[2]);
@@ -2082,7 +2090,7 @@ __global__ void __launch_bounds__(kProjNT) adj_proj_kernel(AdjArgs a) {
     const double det = s[0] * s[2] - s[1] * s[1];
     // With mu constant on S (or |S| = 1) the return row adds nothing to the
     // budget row: project on span(1) only (x does not move with mu there).
-    const bool two = a.active && det > 1e-14 * s[0] * s[2];
+    const bool two = active && det > 1e-14 * s[0] * s[2];
     if (two) {
         c1 = (s[2] * s[3] - s[1] * s[4]) / det;
         c2 = (s[0] * s[4] - s[1] * s[3]) / det;
@@ -2090,14 +2098,14 @@ __global__ void __launch_bounds__(kProjNT) adj_proj_kernel(AdjArgs a) {
         c1 = s[3] / s[0];
     }
     for (int i = r0 + threadIdx.x; i < r1; i += kProjNT) {
-        const double ab = a.xbar[i] + (1.0 + a.beta) * a.ybar[i];
+        const double ab = a.xbar[i] + (1.0 + beta) * a.ybar[i];
         const double xi = a.x1[i];
         double vb = 0.0;
         if (xi > 0.0) {
             vb = ab - c1 - c2 * a.mu[i];
-            if (two) a.mubar[i] += a.nu * vb - xi * c2;
+            if (two) a.mubar[i] += nu * vb - xi * c2;
         }
-        a.xbar[i] = -a.beta * a.ybar[i];
+        a.xbar[i] = -beta * a.ybar[i];
         a.vbar[i] = vb;
         a.vbar32[i] = (float)vb;
         a.vrec[i] = (float)vb;
@@ -2138,7 +2146,7 @@ struct BPlan {
     int K, C, ncp;
     size_t o_cp_state, o_cp_x, o_cp_y, o_cp_gx, o_cp_y32;   // checkpoints
     size_t o_x1, o_vy, o_zw, o_nu;                          // segment tape
-    size_t o_xbar, o_ybar, o_mubar, o_vbar, total;
+    size_t o_xbar, o_ybar, o_mubar, o_vbar, o_betas, o_k0, total;
 };
 
 static BPlan make_bplan(const Plan &p, int K, int C) {
@@ -2165,6 +2173,8 @@ static BPlan make_bplan(const Plan &p, int K, int C) {
     b.o_ybar = take(8 * (size_t)p.n);
     b.o_mubar = take(8 * (size_t)p.n);
     b.o_vbar = take(8 * (size_t)p.n);
+    b.o_betas = take(8 * (size_t)K);
+    b.o_k0 = take(16);
     b.total = off;
     return b;
 }
@@ -2178,7 +2188,7 @@ size_t mv_backward_workspace_size(const mv_problem *P, const mv_solve_opts *O_in
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 1 || O.checkpoint_every < 1) return 0;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
     return make_bplan(p, O.max_iter, O.checkpoint_every).total;
 }
 
@@ -2197,7 +2207,9 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     if (O.proj_budget < 1 || O.dykstra_iters < 0) return MV_ERR_INVALID_ARG;
     O.kkt_every = 0;          // unrolled: no early stop inside the K iterations
     O.eps = 0.0;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld);
+    // one pass over L per product, which also returns z = L^T y for the dL update
+    Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
+    p.want_z = true;
     const BPlan b = make_bplan(p, O.max_iter, O.checkpoint_every);
     MV_TRY(check_ws(d_ws, ws_bytes, b.total));
     MV_TRY(set_kernel_attrs());
@@ -2212,13 +2224,21 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     // ---- forward to x_K, checkpointing the state before iterations 0, C, 2C, ...
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_err), 0, 16, s));
+    if (p.use_llt) MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
     setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, nullptr, y32, n);
     if (!(O.alpha > 0.0)) {
         for (int it = 0; it < O.power_iters; ++it) {
-            gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), s, at<float>(ws, p.o_g32));
+            if (p.use_llt)
+                MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), at<float>(ws, p.o_g32), s));
+            else
+                gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), s, at<float>(ws, p.o_g32));
             power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(ws, p.o_g32), nullptr, y32, n);
         }
-        gemv_t_only(p, P, y32, ws, s);
+        if (p.use_llt)
+            MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), nullptr, s, at<float>(ws, p.o_z)));
+        else
+            gemv_t_only(p, P, y32, ws, s);
     }
     step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(ws, p.o_z), (O.alpha > 0.0) ? 0 : T, P->gamma,
                                                 O.power_safety, O.alpha);
@@ -2250,10 +2270,18 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
         return MV_OK;
     };
     int launches = 4;
-    for (int k = 0; k < K; ++k) {
-        if (k % C == 0) MV_TRY(save_cp(k / C));
-        MV_TRY(launch_iteration(p, P, &O, ws, s, nullptr));
-        launches += 3;
+    const int per_it = p.use_llt ? 2 : 3;
+    for (int c = 0; c < b.ncp; ++c) {
+        MV_TRY(save_cp(c));
+        const int len = std::min(K, (c + 1) * C) - c * C;
+        if (len == C && O.use_graph) {               // a full segment: one cached graph
+            cudaGraphExec_t exec = nullptr;
+            MV_TRY(get_chunk_graph(p, P, &O, ws, C, nullptr, &exec));
+            MV_CUDA_TRY(cudaGraphLaunch(exec, s));
+        } else {
+            for (int j = 0; j < len; ++j) MV_TRY(launch_iteration(p, P, &O, ws, s, nullptr));
+        }
+        launches += per_it * len;
     }
     MV_CUDA_TRY(cudaGetLastError());
     SolveState hs{};
@@ -2285,31 +2313,34 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     MV_CUDA_TRY(cudaMemsetAsync(ybar, 0, 8 * (size_t)n, s));
     MV_CUDA_TRY(cudaMemsetAsync(mubar, 0, 8 * (size_t)n, s));
     MV_CUDA_TRY(cudaMemset2DAsync(d_dL, 4 * (size_t)ldD, 0, 4 * (size_t)T, (size_t)n, s));
-    std::vector<double> hnu(C);
-    for (int seg = b.ncp - 1; seg >= 0; --seg) {
-        const int k0 = seg * C, k1 = std::min(K, k0 + C), len = k1 - k0;
-        // recompute the segment forward, recording y_k, z_k, x_{k+1}, nu_k
-        MV_TRY(load_cp(seg));
+    double *betas = at<double>(ws, b.o_betas);
+    int *k0d = at<int>(ws, b.o_k0);
+    MV_CUDA_TRY(cudaMemcpyAsync(betas, beta.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, s));
+    std::vector<int> k0s(b.ncp);
+    for (int seg = 0; seg < b.ncp; ++seg) k0s[seg] = seg * C;
+    // recompute a segment forward from its checkpoint, recording y_k, z_k, x_{k+1}, nu_k
+    auto recompute = [&](cudaStream_t cs, int len) -> int {
         for (int j = 0; j < len; ++j) {
-            MV_CUDA_TRY(cudaMemcpyAsync(VY + (size_t)(len + j) * n, y32, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
-            MV_TRY(launch_iteration(p, P, &O, ws, s, nullptr));
+            MV_CUDA_TRY(cudaMemcpyAsync(VY + (size_t)(len + j) * n, y32, 4 * (size_t)n, cudaMemcpyDeviceToDevice, cs));
+            MV_TRY(launch_iteration(p, P, &O, ws, cs, nullptr));
             MV_CUDA_TRY(cudaMemcpyAsync(ZW + (size_t)j * T, at<float>(ws, p.o_z), 4 * (size_t)T,
-                                        cudaMemcpyDeviceToDevice, s));
+                                        cudaMemcpyDeviceToDevice, cs));
             MV_CUDA_TRY(cudaMemcpyAsync(X1 + (size_t)j * n, at<double>(ws, p.o_x), 8 * (size_t)n,
-                                        cudaMemcpyDeviceToDevice, s));
-            MV_CUDA_TRY(cudaMemcpyAsync(NU + j, &st->nu, 8, cudaMemcpyDeviceToDevice, s));
-            launches += 3;
+                                        cudaMemcpyDeviceToDevice, cs));
+            MV_CUDA_TRY(cudaMemcpyAsync(NU + j, &st->nu, 8, cudaMemcpyDeviceToDevice, cs));
         }
-        MV_CUDA_TRY(cudaMemcpyAsync(hnu.data(), NU, 8 * (size_t)len, cudaMemcpyDeviceToHost, s));
-        MV_CUDA_TRY(cudaStreamSynchronize(s));
-        // backward through the segment
+        return MV_OK;
+    };
+    // backward through the segment (iteration k0 + j, j = len - 1 .. 0)
+    auto reverse = [&](cudaStream_t cs, int len) -> int {
         for (int j = len - 1; j >= 0; --j) {
-            const int k = k0 + j;
             AdjArgs a;
             a.x1 = X1 + (size_t)j * n;
-            a.nu = hnu[j];
-            a.active = (P->mode == MV_RETURN_EQ || hnu[j] != 0.0) ? 1 : 0;
-            a.beta = beta[k];
+            a.nu_tape = NU;
+            a.betas = betas;
+            a.k0 = k0d;
+            a.j = j;
+            a.eq = P->mode == MV_RETURN_EQ ? 1 : 0;
             a.xbar = xbar;
             a.ybar = ybar;
             a.mubar = mubar;
@@ -2318,21 +2349,53 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
             a.vrec = VY + (size_t)j * n;
             a.mu = P->mu;
             a.n = n;
-            MV_CUDA_TRY(launch_adj_proj(p.cl, a, s));
-            gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), s);   // w = L^T v_bar (z buffer), L w
+            MV_CUDA_TRY(launch_adj_proj(p.cl, a, cs));
+            // w = L^T v_bar (z buffer) and L w
+            if (p.use_llt)
+                MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), nullptr, cs, at<float>(ws, p.o_z)));
+            else
+                gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), cs);
             MV_CUDA_TRY(cudaMemcpyAsync(ZW + (size_t)(len + j) * T, at<float>(ws, p.o_z), 4 * (size_t)T,
-                                        cudaMemcpyDeviceToDevice, s));
-            adj_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(vbar, at<double>(ws, p.o_gy), alpha, P->gamma, ybar, n);
-            launches += 4;
+                                        cudaMemcpyDeviceToDevice, cs));
+            adj_finish_kernel<<<(n + 255) / 256, 256, 0, cs>>>(vbar, at<double>(ws, p.o_gy), alpha, P->gamma, ybar, n);
         }
+        return cudaGetLastError() == cudaSuccess ? MV_OK : MV_ERR_CUDA;
+    };
+    for (int seg = b.ncp - 1; seg >= 0; --seg) {
+        const int k0 = seg * C, k1 = std::min(K, k0 + C), len = k1 - k0;
+        MV_TRY(load_cp(seg));
+        MV_CUDA_TRY(cudaMemcpyAsync(k0d, &k0s[seg], sizeof(int), cudaMemcpyHostToDevice, s));
+        if (len == C && O.use_graph) {                // full segments replay two cached graphs
+            GraphKey kr = graph_key(p, P, &O, -1000000 - C, nullptr), kb = graph_key(p, P, &O, -2000000 - C, nullptr);
+            kr.ws = kb.ws = ws;
+            kb.aux = alpha;                           // adj_finish bakes the step in
+            cudaGraphExec_t er = nullptr, eb = nullptr;
+            MV_TRY(cached_graph(kr, [&](cudaStream_t cs) { return recompute(cs, C); }, &er));
+            MV_TRY(cached_graph(kb, [&](cudaStream_t cs) { return reverse(cs, C); }, &eb));
+            MV_CUDA_TRY(cudaGraphLaunch(er, s));
+            MV_CUDA_TRY(cudaGraphLaunch(eb, s));
+        } else {
+            MV_TRY(recompute(s, len));
+            MV_TRY(reverse(s, len));
+        }
+        launches += len * (per_it + 4);
         // dL += -2 alpha (V Z^T + Y W^T) over the segment: one FP32 GEMM with
         // A = [z_k; w_k] rows (T x 2len col-major) and B = [v_bar_k; y_k] rows.
         MV_TRY(linalg_sgemm_nt(s, T, n, 2 * len, (float)(-2.0 * alpha), ZW, T, VY, n, 1.0f, d_dL, (int)ldD));
         MV_CUDA_TRY(cudaGetLastError());
     }
     MV_CUDA_TRY(cudaMemcpyAsync(d_dmu, mubar, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    int xerr = 0;
+    MV_CUDA_TRY(cudaMemcpyAsync(&xerr, at<int>(ws, p.o_err), sizeof(int), cudaMemcpyDeviceToHost, s));
     MV_CUDA_TRY(cudaStreamSynchronize(s));
     MV_CUDA_TRY(cudaGetLastError());
+    if (xerr != 0) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "mv_npga_backward: a bounded wait of the fused pass timed out (code %d)", xerr);
+        *h_info = mv_solve_info{};
+        h_info->status = record_message(MV_ERR_TIMEOUT, msg);
+        return h_info->status;
+    }
     *h_info = mv_solve_info{};
     h_info->iterations = K;
     h_info->status = MV_OK;

@@ -166,11 +166,14 @@ def test_gradient_fused_parity(mv, dt, shape):
     gamma = 1e-5
     zf, gf = mv.gradient(L, gpu(y), T, gamma, dt, rs, with_z=False)
     assert zf is None
-    _, g2 = mv.gradient(L, gpu(y), T, gamma, dt, rs, with_z=True)
+    # with z requested the same single pass also writes the slices of z = L^T y it forms
+    z2, g2 = mv.gradient(L, gpu(y), T, gamma, dt, rs, with_z=True)
     g_o = gradient(Lq, gamma, y)
+    z_o = Lq.T @ y
     gf = gf.cpu().numpy()
     assert np.max(np.abs(gf - g_o)) <= 2e-5 * np.max(np.abs(g_o))
-    assert np.max(np.abs(gf - g2.cpu().numpy())) <= 2e-5 * np.max(np.abs(g_o))
+    assert np.array_equal(gf, g2.cpu().numpy())
+    assert np.max(np.abs(z2.cpu().numpy() - z_o)) <= 2e-5 * np.max(np.abs(z_o))
     # deterministic: the same bits on a second call
     _, gf2 = mv.gradient(L, gpu(y), T, gamma, dt, rs, with_z=False)
     assert np.array_equal(gf, gf2.cpu().numpy())
