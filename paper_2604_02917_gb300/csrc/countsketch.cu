@@ -24,6 +24,7 @@ namespace mv {
 
 constexpr int kCsThreads = 256;
 constexpr int kCsGroup = 8;                   // buckets per CTA (TN)
+constexpr int kCsLoads = 4;                   // row slices in flight per thread (TN)
 constexpr int kCsNtThreads = 512;
 constexpr size_t kCsNtMaxRow = 200 * 1024;    // staged row bytes (NT)
 constexpr int kCsMaxBucket = 4096;            // periods per bucket the in-place sort accepts
@@ -96,25 +97,51 @@ __global__ void cs_fill_kernel(const int *__restrict__ h, const int8_t *__restri
     }
 }
 
-// Ascending periods within each bucket (insertion sort: a uniform hash
-// leaves buckets of a few periods; a bucket above kCsMaxBucket is refused).
+__device__ __forceinline__ unsigned cs_key(unsigned e) { return e & 0x7fffffffu; }
+
+// Ascending periods within one bucket of nb entries at list[p0..): up to 16
+// in registers through a fixed 16-input odd-even transposition network (a
+// uniform hash leaves a few periods per bucket), more by insertion in place.
+__device__ __forceinline__ void cs_sort_bucket(unsigned *__restrict__ list, int p0, int nb) {
+    if (nb <= 16) {
+        unsigned v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = i < nb ? list[p0 + i] : 0xffffffffu;   // padding sorts last
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+#pragma unroll
+            for (int i = r & 1; i + 1 < 16; i += 2) {
+                const unsigned x = v[i], y = v[i + 1];
+                const bool sw = cs_key(x) > cs_key(y);
+                v[i] = sw ? y : x;
+                v[i + 1] = sw ? x : y;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+            if (i < nb) list[p0 + i] = v[i];
+        return;
+    }
+    for (int p = p0 + 1; p < p0 + nb; ++p) {
+        const unsigned x = list[p];
+        int q = p - 1;
+        while (q >= p0 && cs_key(list[q]) > cs_key(x)) {
+            list[q + 1] = list[q];
+            --q;
+        }
+        list[q + 1] = x;
+    }
+}
+
+// Sort every bucket (a bucket above kCsMaxBucket periods is refused).
 __global__ void cs_sort_kernel(const int *__restrict__ off, int m, unsigned *__restrict__ list, int *__restrict__ err) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < m; b += gridDim.x * blockDim.x) {
-        const int p0 = off[b], p1 = off[b + 1];
-        if (p1 - p0 > kCsMaxBucket) {
+        const int p0 = off[b], nb = off[b + 1] - p0;
+        if (nb > kCsMaxBucket) {
             atomicExch(err, 2);
             continue;
         }
-        for (int p = p0 + 1; p < p1; ++p) {
-            const unsigned x = list[p];
-            const unsigned key = x & 0x7fffffffu;
-            int q = p - 1;
-            while (q >= p0 && (list[q] & 0x7fffffffu) > key) {
-                list[q + 1] = list[q];
-                --q;
-            }
-            list[q + 1] = x;
-        }
+        cs_sort_bucket(list, p0, nb);
     }
 }
 
@@ -130,25 +157,41 @@ cs_tn_kernel(const void *__restrict__ Lt, int64_t ld, int n, int m, const int *_
     const int a0 = blockIdx.y * CHUNK;
     const int my = a0 + threadIdx.x * VEC;
     const char *base = reinterpret_cast<const char *>(Lt);
+    // the 9 bucket boundaries of the group, loaded together up front
+    int bnd[kCsGroup + 1];
+#pragma unroll
+    for (int g = 0; g <= kCsGroup; ++g) bnd[g] = __ldg(off + min(j0 + g, m));
+#pragma unroll
     for (int g = 0; g < kCsGroup; ++g) {
-        const int j = j0 + g;
         float acc[VEC];
 #pragma unroll
         for (int q = 0; q < VEC; ++q) acc[q] = 0.f;
-        if (j < m && my < n) {
-            const int p1 = off[j + 1];
-            for (int p = off[j]; p < p1; ++p) {
-                const unsigned e = __ldg(list + p);
-                const int64_t t = (int64_t)(e & 0x7fffffffu);
-                const uint4 u = ld_stream16(base + (t * ld + my) * (int64_t)sizeof(typename St::elem));
-                float f[VEC];
-                St::unpack(u, f);
-                if (e & 0x80000000u) {
+        if (my < n) {
+            const int p1 = bnd[g + 1];
+            // kCsLoads list entries, then kCsLoads row slices in flight; the
+            // additions keep the ascending period order
+            for (int p = bnd[g]; p < p1; p += kCsLoads) {
+                unsigned e[kCsLoads];
+                uint4 u[kCsLoads];
 #pragma unroll
-                    for (int q = 0; q < VEC; ++q) acc[q] -= f[q];
-                } else {
+                for (int k = 0; k < kCsLoads; ++k) e[k] = p + k < p1 ? __ldg(list + p + k) : 0u;
 #pragma unroll
-                    for (int q = 0; q < VEC; ++q) acc[q] += f[q];
+                for (int k = 0; k < kCsLoads; ++k)
+                    u[k] = p + k < p1 ? ld_stream16(base + ((int64_t)(e[k] & 0x7fffffffu) * ld + my) *
+                                                              (int64_t)sizeof(typename St::elem))
+                                      : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int k = 0; k < kCsLoads; ++k) {
+                    if (p + k >= p1) break;
+                    float f[VEC];
+                    St::unpack(u[k], f);
+                    if (e[k] & 0x80000000u) {
+#pragma unroll
+                        for (int q = 0; q < VEC; ++q) acc[q] -= f[q];
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < VEC; ++q) acc[q] += f[q];
+                    }
                 }
             }
         }

@@ -447,7 +447,9 @@ def countsketch(L: torch.Tensor, n: int, T: int, h: torch.Tensor, sign: torch.Te
         raise MvError(MV_ERR_INVALID_ARG, "mv_countsketch_workspace_size")
     ws = _workspace(nb, L.device)
     ldS = (m + 3) // 4 * 4
-    out = torch.zeros((n, ldS), dtype=torch.float32, device=L.device)
+    out = torch.empty((n, ldS), dtype=torch.float32, device=L.device)
+    if ldS > m:
+        out[:, m:].zero_()                                   # padding columns; the kernels write every j < m
     _check(lib().mv_countsketch(_ptr(L), DTYPES[dtype], LAYOUTS[layout], _ptr(row_scale) if row_scale is not None
                                 else None, n, T, L.stride(0), _ptr(h), _ptr(sign), m, _ptr(out), ldS, _ptr(ws),
                                 ws.numel(), _stream()), "mv_countsketch")

@@ -116,3 +116,41 @@ def test_countsketch_full_size_and_str(mv):
     lam = np.sort(np.linalg.eigvalsh(K @ K.T))[::-1][:64]
     s = sigma.cpu().numpy()
     assert np.max(np.abs(s ** 2 - lam)) <= 1e-6 * lam[0]
+
+
+@pytest.mark.parametrize("layout", ["tn", "nt"])
+def test_countsketch_many_buckets(mv, layout):
+    """20000 buckets for 30011 periods (about 1.5 per bucket, many empty):
+    the sums match the oracle and every empty bucket's column is zero."""
+    n, T, m = 150, 30011, 20000
+    R = gpu(factor_returns(CFG_SMALL.scaled(n, T, seed=41), np.float32))
+    L, rs, _, _ = mv.center_factor(R, "f32", layout=layout)
+    h, sg = countsketch_hash(T, m, seed=5)
+    out = mv.countsketch(L, n, T, gpu(h), gpu(sg), m, "f32", rs, layout)
+    Lq = held_nt(L, rs, n, T, "f32", layout)
+    ref = strmodel.countsketch(Lq, h, sg, m)
+    got = out[:, :m].double().cpu().numpy()
+    assert np.all(np.abs(got - ref) <= bound(Lq, h, m))
+    empty = np.bincount(h, minlength=m) == 0
+    assert empty.any() and np.all(got[:, empty] == 0.0)
+
+
+@pytest.mark.parametrize("m", [100, 20000])
+def test_countsketch_crowded_bucket(mv, m):
+    """One bucket of 3000 periods, sorted in place rather than by the
+    16-input register network, beside short buckets (m = 20000) or beside
+    buckets of about 240 periods (m = 100); both layouts give identical bits."""
+    n, T = 96, 24007
+    R = gpu(factor_returns(CFG_SMALL.scaled(n, T, seed=43), np.float32))
+    h, sg = countsketch_hash(T, m, seed=8)
+    h[5000:8000] = 7
+    outs = []
+    for layout in ("tn", "nt"):
+        L, _, _, _ = mv.center_factor(R, "f32", layout=layout)
+        out = mv.countsketch(L, n, T, gpu(h), gpu(sg), m, "f32", None, layout)
+        Lq = held_nt(L, None, n, T, "f32", layout)
+        ref = strmodel.countsketch(Lq, h, sg, m)
+        got = out[:, :m].double().cpu().numpy()
+        assert np.all(np.abs(got - ref) <= bound(Lq, h, m))
+        outs.append(out)
+    assert torch.equal(outs[0], outs[1])
