@@ -194,7 +194,7 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     } else {
         // Epilogue: warp w owns TMEM lanes 32*(w%4) .. +31, i.e. tile rows.
         bool ok = umma::mbar_wait(accum, 0, 4 * kWaitNs);
-        if (EPI == kEpiF32 && gridDim.z > 1) ok = epilogue_all(ok);   // split-K barriers need one verdict
+        if (EPI == kEpiF32 && gridDim.z > 1) ok = epilogue_all(ok);   // split-K barriers need one shared outcome
         __syncwarp();
         umma::fence_after_sync();
         if (ok) {

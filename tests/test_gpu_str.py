@@ -1,6 +1,6 @@
 """GPU parity of the STR build (Sec. 2.5; App. D.3) and the STR-model NPGA.
 
-Truncation parity is judged on quantities that are unique even when the
+Truncation parity is checked on quantities that are unique even when the
 spectrum is flat around k: eigenvalues (Weyl: perturbing tilde L by its FP32
 accumulation error moves each sigma_i^2 by at most ~1e-5 sigma_1^2 here),
 the diagonal structure L_eff^T L_eff = diag(sigma^2), and the eigen-residual
