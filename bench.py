@@ -540,6 +540,19 @@ def main():
                               "fused": vinfos[-1]["fused"], "roofline": roofline(pinfos, model, args.dtype, lay)}
             del sv
         del Lo, rso
+        # A shorter power method (Sec. 3.1 remark: a handful of iterations is
+        # usually enough for the step estimate): the headline solve with 10.
+        kw = dict(dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps, layout=args.layout,
+                  two_pass=1 if args.two_pass else 0, power_iters=10)
+        sv = mv.Solver(L, mu, Rt, model.T, **kw)
+        t, vinfos = timed_solves(sv)
+        vi = vinfos[-1]
+        variants[f"{args.dtype}_{args.layout}_power10"] = {
+            "value": t, "unit": "s", "power_iters": 10, "iterations": vi["iterations"], "kkt": vi["kkt"],
+            "converged": vi["converged"], "objective": vi["objective"],
+            "lambda_hat_over_power50": vi["lambda_hat"] / infos[-1]["lambda_hat"],
+            "rel_obj_vs_power50": (vi["objective"] - infos[-1]["objective"]) / infos[-1]["objective"]}
+        del sv
     if not args.no_variants and args.dtype == "f32":
         R_dev = torch.from_numpy(R32).to(dev)
         for vdt in ("bf16", "fp8"):

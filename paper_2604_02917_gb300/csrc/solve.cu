@@ -469,7 +469,9 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
     const double inv1pb = sc[0], tn = sc[1], beta = sc[2];
     const bool check = (a.kkt_every > 0 && k % a.kkt_every == 0) || (k >= a.max_iter);
 
-    // L L^T x^k by linearity from the product at y^k; KKT point x - alpha grad f(x).
+    // L L^T x^k by linearity from the product at y^k; the point to project:
+    // x - alpha grad f(x) on a KKT test, else the gradient step from y^k
+    // (one pass over the vectors either way).
     for (int i = threadIdx.x; i < el.n; i += kProjNT) {
         const int gi = r0 + i;
         el.mu[i] = a.mu[gi];
@@ -479,6 +481,9 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
         if (check) {
             const double xi = a.x[gi];
             el.v[i] = xi - alpha * (2.0 * gxi + 2.0 * gamma * xi);
+        } else {
+            const double yi = a.y[gi];
+            el.v[i] = yi - alpha * (2.0 * gyi + 2.0 * gamma * yi);
         }
     }
     __syncthreads();
@@ -516,13 +521,13 @@ __device__ __forceinline__ void npga_step_body(const StepArgs &a, unsigned char 
             return;
         }
         __syncthreads();
+        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
+            const int gi = r0 + i;
+            const double yi = a.y[gi];
+            el.v[i] = yi - alpha * (2.0 * a.gy[gi] + 2.0 * gamma * yi);
+        }
+        __syncthreads();
     }
-    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-        const int gi = r0 + i;
-        const double yi = a.y[gi];
-        el.v[i] = yi - alpha * (2.0 * a.gy[gi] + 2.0 * gamma * yi);
-    }
-    __syncthreads();
     P.prepare();
     const ProjOut o = P.solve(a.R, a.mode, mn, mx, nu0, tau0, a.budget);
     for (int i = threadIdx.x; i < el.n; i += kProjNT) {
@@ -785,9 +790,9 @@ objective_kernel(SolveState *st, const float *__restrict__ z, int T, const doubl
     objective_body(st, z, T, x, n, gamma);
 }
 
-// Explicit Sigma: f(x) = x^T (Sigma x) + gamma ||x||^2.
+// f(x) = x^T w + gamma ||x||^2 for w = Sigma x or w = L L^T x.
 __global__ void __launch_bounds__(kStepThreads)
-objective_sigma_kernel(SolveState *st, const double *__restrict__ x, const double *__restrict__ sx, int n, double gamma) {
+objective_dot_kernel(SolveState *st, const double *__restrict__ x, const double *__restrict__ sx, int n, double gamma) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
     double v[2] = {0.0, 0.0};
     for (int i = threadIdx.x; i < n; i += kStepThreads) {
@@ -1410,17 +1415,29 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
         k_prev = hs.k;
         if (hs.done) break;
     }
-    launches += 3;
-    // Objective of the returned iterate: one more pass z = L^T x (or Sigma x).
-    to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(at<double>(d_ws, p.o_x), rs, y32, p.n);
-    if (p.sig) {
-        MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gobj), nullptr, s));
-        objective_sigma_kernel<<<1, kStepThreads, 0, s>>>(st, at<double>(d_ws, p.o_x), at<double>(d_ws, p.o_gobj), p.n,
-                                                          P->gamma);
+    // Objective of the returned iterate.  A solve that stopped at a KKT test
+    // returns the iterate that test evaluated, and the step kept L L^T x
+    // there (gx, by linearity from the products at y): f = x^T gx +
+    // gamma ||x||^2 with no further pass over L.  Otherwise (an error stop,
+    // the iteration budget of the host loop, backtracking) one more pass
+    // z = L^T x (or Sigma x).
+    const bool at_test = hs.done && !O.backtrack && (hs.status == MV_OK || hs.status == MV_ERR_NOT_CONVERGED);
+    if (at_test) {
+        objective_dot_kernel<<<1, kStepThreads, 0, s>>>(st, at<double>(d_ws, p.o_x), at<double>(d_ws, p.o_gx), p.n,
+                                                        P->gamma);
+        launches += 1;
     } else {
-        gemv_t_only(p, P, y32, d_ws, s);
-        objective_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), p.T, at<double>(d_ws, p.o_x), p.n,
-                                                    P->gamma);
+        launches += 3;
+        to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(at<double>(d_ws, p.o_x), rs, y32, p.n);
+        if (p.sig) {
+            MV_TRY(launch_symv(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gobj), nullptr, s));
+            objective_dot_kernel<<<1, kStepThreads, 0, s>>>(st, at<double>(d_ws, p.o_x), at<double>(d_ws, p.o_gobj),
+                                                            p.n, P->gamma);
+        } else {
+            gemv_t_only(p, P, y32, d_ws, s);
+            objective_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), p.T, at<double>(d_ws, p.o_x), p.n,
+                                                        P->gamma);
+        }
     }
     MV_CUDA_TRY(cudaMemcpyAsync(d_x_inout, at<double>(d_ws, p.o_x), 8 * (size_t)p.n, cudaMemcpyDeviceToDevice, s));
     MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));

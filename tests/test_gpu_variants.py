@@ -21,7 +21,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from synth import CFG_FULL, factor_returns, power_start
-from oracle.npga import initial_point, npga, npga_sigma, power_norm2, step_size
+from oracle.npga import initial_point, npga, npga_sigma, objective, power_norm2, step_size
 
 pytestmark = pytest.mark.gpu
 
@@ -68,6 +68,8 @@ def test_constant_momentum_parity(mv, gamma):
     assert abs(info["iterations"] - ref.iters) <= 10
     exact = npga(Lq, gamma, mu_o, Rt, initial_point(mu_o, Rt), a, eps=1e-11, max_iter=200000)
     assert np.max(np.abs(x.cpu().numpy() - exact.x)) <= 1e-4
+    # objective from the kept L L^T x of the last KKT test
+    assert info["objective"] == pytest.approx(objective(Lq, gamma, x.cpu().numpy()), rel=1e-5)
     # the FISTA run of the same problem lands on the same point
     xf, _ = mv.npga_solve(L, mu, Rt, T, gamma=gamma, eps=1e-6, power_start=gpu(r0))
     assert np.max(np.abs(xf.cpu().numpy() - x.cpu().numpy())) <= 2e-4
@@ -96,6 +98,8 @@ def test_backtracking_parity(mv, path):
                backtrack=(a0, rho))
     assert ref.converged
     assert np.max(np.abs(x.cpu().numpy() - ref.x)) <= 1e-4
+    # objective by one more product at the returned x (the backtracking path)
+    assert info["objective"] == pytest.approx(objective(Lq, 0.0, x.cpu().numpy()), rel=1e-5)
 
 
 def test_backtracking_default_trial_and_constant_momentum(mv):
