@@ -31,6 +31,7 @@ namespace mv {
 
 constexpr int kGemmThreads = 192;
 constexpr int kBM = 128, kBK = 64;
+constexpr int kRasterRows = 16;               // row tiles per raster group (plain F32 GEMMs)
 constexpr uint64_t kWaitNs = 2000000000ull;   // 2 s per wait
 
 static __device__ int g_gemm_err;
@@ -129,7 +130,20 @@ gemm_bf16_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_consta
     const uint32_t full0 = umma::smem_u32(bars), empty0 = umma::smem_u32(bars + S), accum = umma::smem_u32(bars + 2 * S);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN;
+    // Tile of this CTA.  Plain F32 GEMMs (no split-K) take a grouped raster:
+    // CTAs in launch order sweep kRasterRows row tiles before the next column
+    // tile, so a wave of co-resident CTAs touches about 16 A and 10 B
+    // operand panels instead of every A panel.
+    int rt = blockIdx.x, ct = blockIdx.y;
+    if (EPI == kEpiF32 && gridDim.z == 1 && (int)gridDim.x > kRasterRows) {
+        const int nrt = (int)gridDim.x, nct = (int)gridDim.y;
+        const int lin = (int)blockIdx.x + nrt * (int)blockIdx.y;
+        const int per = kRasterRows * nct, g = lin / per, first = g * kRasterRows;
+        const int gh = min(nrt - first, kRasterRows), rem = lin - g * per;
+        rt = first + rem % gh;
+        ct = rem / gh;
+    }
+    const int m0 = rt * kBM, n0 = ct * BN;
     const int nk_all = (K + kBK - 1) / kBK, Z = gridDim.z;
     const int kb = (int)((int64_t)blockIdx.z * nk_all / Z), ke = (int)((int64_t)(blockIdx.z + 1) * nk_all / Z);
     const int nk = ke - kb;                    // k-steps of this CTA (all of them without split-K)
