@@ -9,9 +9,9 @@
 // and a diagonal tile gives Sigma_II y_I.  Block row b thus receives exactly
 // nb partial vectors, one per tile it meets; tile (I, J) stores its two into
 // slot J of block I and slot I of block J.  The CTA that brings a block
-// row's ticket to nb sums its nb slots in slot order (FP32 with a
-// compensation term; fixed order: the result does not depend on CTA timing)
-// and resets the ticket.
+// row's ticket to nb sums its nb slots (two halves in slot order, FP32 with a
+// compensation term, added in FP64; fixed order: the result does not depend
+// on CTA timing) and resets the ticket.
 //
 // Per CTA: 8 warps x 16 rows, a lane owns 4 consecutive columns (one 16-byte
 // load per row, 512 contiguous bytes per warp-row); a thread issues its 16
@@ -64,25 +64,40 @@ __device__ __forceinline__ float4 symv_ld(const float *p, uint64_t pol) {
     return v;
 }
 
-// Sum the nb slots of block row b in slot order and publish.  FP32 with a
-// compensation term (the partials are FP32; FP64 arithmetic is scarce on
-// this part), one conversion to FP64 at the end.
-__device__ __forceinline__ void symv_finish_block(const SymvArgs &a, int b) {
+// Sum the nb slots of block row b and publish: the 256 threads take the
+// 128 rows twice, the first half of the slots and the second, each half in
+// slot order in FP32 with a compensation term (the partials are FP32; FP64
+// arithmetic is scarce on this part); the two halves are added in FP64.
+// Fixed order: the result does not depend on CTA timing.  Called by the
+// whole block (block-uniform condition); uses red[2][kSymTile] of shared
+// memory.
+__device__ __forceinline__ void symv_finish_block(const SymvArgs &a, int b, float (*red)[kSymTile]) {
+    static_assert(kSymThreads == 2 * kSymTile, "two threads per row");
     const int stride = a.nb * kSymTile;
-    for (int i = threadIdx.x; i < kSymTile; i += kSymThreads) {
-        const int r = b * kSymTile + i;
-        if (r >= a.n) continue;
-        float s = 0.f, c = 0.f;
+    const int i = threadIdx.x & (kSymTile - 1), h = threadIdx.x / kSymTile;
+    const int r = b * kSymTile + i;
+    const int jh = (a.nb + 1) / 2, j0 = h * jh, j1 = min(a.nb, j0 + jh);
+    float s = 0.f, c = 0.f;
+    if (r < a.n) {
 #pragma unroll 8
-        for (int j = 0; j < a.nb; ++j) {
+        for (int j = j0; j < j1; ++j) {
             const float y = __ldcg(a.part + (int64_t)j * stride + r) - c;
             const float t = s + y;
             c = (t - s) - y;
             s = t;
         }
-        a.out64[r] = (double)s - (double)c;
-        if (a.out32) a.out32[r] = s;
     }
+    if (h == 1) {
+        red[0][i] = s;
+        red[1][i] = c;
+    }
+    __syncthreads();
+    if (h == 0 && r < a.n) {
+        const double v = ((double)s - (double)c) + ((double)red[0][i] - (double)red[1][i]);
+        a.out64[r] = v;
+        if (a.out32) a.out32[r] = (float)v;
+    }
+    __syncthreads();                  // red is reused by a second finish
 }
 
 __global__ void __launch_bounds__(kSymThreads) symv_kernel(SymvArgs a) {
@@ -194,12 +209,12 @@ __global__ void __launch_bounds__(kSymThreads) symv_kernel(SymvArgs a) {
     __syncthreads();
     if (s_last[0]) {
         __threadfence();
-        symv_finish_block(a, I);
+        symv_finish_block(a, I, colred);
         if (threadIdx.x == 0) a.tickets[I] = 0u;
     }
     if (s_last[1]) {
         __threadfence();
-        symv_finish_block(a, J);
+        symv_finish_block(a, J, colred);
         if (threadIdx.x == 0) a.tickets[J] = 0u;
     }
 }
