@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-str", action="store_true", help="skip the sketch / STR measurement")
     ap.add_argument("--sketch-m", type=int, default=8192)
     ap.add_argument("--no-frontier", action="store_true", help="skip the 64-target frontier measurement")
+    ap.add_argument("--no-small", action="store_true", help="skip the 200 x 1000, 2000-iteration solve")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-problem uneven batch")
     ap.add_argument("--no-sigma", action="store_true", help="skip the explicit-covariance measurement")
@@ -346,6 +347,18 @@ def row_oracles(model, R32, res):
     for r in tg[:2]:
         npga(Lf, 0.0, muf, float(r), initial_point(muf, float(r)), step_size(lam, 0.0), eps=1e-6, max_iter=20000)
     out["frontier_200x1000"] = entry(time.perf_counter() - t0, 32.0, "2 of the 64 targets at 200 x 1000, scaled by 32")
+    # plain NPGA at 200 x 1000: the whole 2000-iteration run, and the GPU's x against it
+    if res.get("small_x") is not None:
+        Rt1 = float(np.percentile(muf, 60))
+        t0 = time.perf_counter()
+        lam1 = power_norm2(Lf, power_start(Lf.shape[0]), 50)
+        ref = npga(Lf, 0.0, muf, Rt1, initial_point(muf, Rt1), step_size(lam1, 0.0), eps=0.0, max_iter=2000)
+        t1 = time.perf_counter() - t0
+        xg = np.asarray(res["small_x"], dtype=np.float64)
+        fo = float(np.sum((Lf.T @ ref.x) ** 2))
+        fg = float(np.sum((Lf.T @ xg) ** 2))
+        out["small_200x1000"] = dict(entry(t1, 1.0, "the whole solve: 50 power + 2000 NPGA iterations"),
+                                     x_inf_err=float(np.max(np.abs(xg - ref.x))), rel_obj_err=(fg - fo) / fo)
     # a13 adjoint: 20 of the 500 unrolled iterations at 2000 x 10000 (forward + reverse), scaled by 25
     am = CFG_SMALL.scaled(2000, 10000, seed=0)
     from synth import factor_returns
@@ -703,6 +716,25 @@ def main():
                                                "note": "whole call (bucket lists + gather), event-timed"}}
         del Lc, hh, sg
 
+    # Plain NPGA at 200 x 1000 (5 factors, seed 0): 2000 iterations, no early
+    # stop; L (800 KB) stays on chip, so this measures per-iteration latency.
+    small = None
+    if not args.no_small and args.dtype == "f32":
+        from synth import CFG_SMALL
+        Rs = torch.from_numpy(factor_returns(CFG_SMALL, np.float32)).to(dev)
+        Lsm, _, musm, _ = mv.center_factor(Rs, "f32")
+        del Rs
+        Rts = float(np.percentile(musm.cpu().numpy(), 60))
+        r0s = torch.from_numpy(power_start(CFG_SMALL.n)).to(dev)
+        ssv = mv.Solver(Lsm, musm, Rts, CFG_SMALL.T, power_start=r0s, eps=0.0, max_iter=2000)
+        t, sinfos = timed_solves(ssv)
+        xs, _ = ssv.solve()
+        small = {"n": CFG_SMALL.n, "T": CFG_SMALL.T, "iterations": sinfos[-1]["iterations"], "value": t, "unit": "s",
+                 "us_per_iteration": t / 2000 * 1e6, "kkt": sinfos[-1]["kkt"], "objective": sinfos[-1]["objective"],
+                 "note": "whole solve (50 power iterations + 2000 NPGA iterations + objective), KKT test every 5"}
+        small_x = xs.cpu().numpy()
+        del ssv, Lsm, musm, r0s, xs
+
     # 64-point efficient frontier (shared BF16 factor, skinny tcgen05 GEMMs).
     frontier = None
     if not args.no_frontier and args.dtype == "f32":
@@ -829,7 +861,7 @@ def main():
         cb = cpu_baseline(model, iters, 50, args.eps, R32=R32)
         if not args.no_row_oracles:
             res = {"sigma_iters": sigma_res["f32_L"]["iterations"] if sigma_res else 50,
-                   "batch_elem_iters": batch_elem_iters}
+                   "batch_elem_iters": batch_elem_iters, "small_x": small_x if small is not None else None}
             row_cpu = row_oracles(model, R32, res)
             if str_res is not None:
                 for k in ("sketch", "countsketch", "truncate"):
@@ -841,6 +873,8 @@ def main():
                 frontier["200x1000"]["cpu_oracle"] = row_cpu["frontier_200x1000"]
             if adj is not None:
                 adj["cpu_oracle"] = row_cpu["adjoint"]
+            if small is not None and "small_200x1000" in row_cpu:
+                small["cpu_oracle"] = row_cpu["small_200x1000"]
             if batch is not None and "batch" in row_cpu:
                 batch["cpu_oracle"] = row_cpu["batch"]
     if rank == 0:
@@ -857,8 +891,8 @@ def main():
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
-                "variants": variants, "sigma": sigma_res, "str": str_res, "frontier": frontier, "adjoint": adj,
-                "batch": batch}
+                "variants": variants, "sigma": sigma_res, "str": str_res, "small_200x1000": small,
+                "frontier": frontier, "adjoint": adj, "batch": batch}
         print(json.dumps(jsonable(line)), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
