@@ -506,3 +506,32 @@ def test_knee_rank_and_kappa_ridge():
     assert strmodel.knee_rank(lam, 1e-2, 0.6) == 6
     g = strmodel.gamma_for_kappa(10.0, 101.0)
     assert (100.0 + g) / g == pytest.approx(101.0)
+
+
+def test_product_at_x_by_linearity_along_the_iterates():
+    """Sec. 3.1 tests the KKT condition at x^k while Algorithm 1 forms the
+    gradient at y^k.  Since y^k = (1 + beta_{k-1}) x^k - beta_{k-1} x^{k-1},
+    L L^T x^k = (L L^T y^k + beta_{k-1} L L^T x^{k-1}) / (1 + beta_{k-1}) with
+    L L^T x^0 = L L^T y^0; the objective x^T (L L^T x) + gamma ||x||^2 follows
+    from the same product.  Checked along a recorded FISTA run against the
+    direct products (a beta off by one iteration fails it)."""
+    rng = np.random.default_rng(11)
+    n, T, gamma = 30, 80, 1e-3
+    L = rng.standard_normal((n, T)) * 0.1
+    mu = rng.uniform(-2e-4, 6e-4, n)
+    R = float(np.percentile(mu, 60))
+    a = step_size(power_norm2(L, rng.standard_normal(n), 50), gamma)
+    res = npga(L, gamma, mu, R, initial_point(mu, R), a, eps=0.0, max_iter=40, record=True)
+    X = res.trajectory
+    assert len(X) == 41
+    t, beta_prev, gx = 1.0, 0.0, None
+    for k, xk in enumerate(X):
+        y = xk if k == 0 else xk + beta_prev * (xk - X[k - 1])
+        gy = L @ (L.T @ y)
+        gx = gy if k == 0 else (gy + beta_prev * gx) / (1.0 + beta_prev)
+        direct = L @ (L.T @ xk)
+        assert np.max(np.abs(gx - direct)) <= 1e-12 * np.max(np.abs(direct))
+        assert xk @ gx + gamma * (xk @ xk) == pytest.approx(objective(L, gamma, xk), rel=1e-12)
+        t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
+        beta_prev, t = (t - 1.0) / t_new, t_new
+    assert beta_prev > 0.5                      # momentum well away from 0 by the end
