@@ -275,6 +275,25 @@ def project(v: torch.Tensor, mu: torch.Tensor, R_target, mode: str = "ge"):
     return (x[0], out[0]) if squeeze else (x, out)
 
 
+def shape_error(layout: str, dtype: str, L_shape, L_esize: int, n: int, T: int, mu_numel: int,
+                rs_numel: int | None = None, ps_numel: int | None = None) -> str | None:
+    """Why the arrays cannot hold the problem, or None.  The kernels read an
+    n x T block of L ("nt"), T x n ("tn") or n x n ("sigma") and n entries
+    of mu, the row scales and the power-method start; the C ABI only sees
+    pointers, so the sizes are checked here."""
+    want = _ESIZE[DTYPES[dtype]]
+    if L_esize != want:
+        return f"L holds {L_esize}-byte elements; dtype {dtype} stores {want}-byte ones"
+    rows, cols = int(L_shape[0]), int(L_shape[1])
+    need = {"nt": (n, T), "tn": (T, n), "sigma": (n, n)}[layout]
+    if rows < need[0] or cols < need[1]:
+        return f"L is {rows} x {cols}; layout {layout} with n = {n}, T = {T} reads {need[0]} x {need[1]}"
+    for name, k in (("mu", mu_numel), ("row_scale", rs_numel), ("power_start", ps_numel)):
+        if k is not None and k < n:
+            return f"{name} has {k} entries; the problem has n = {n}"
+    return None
+
+
 def make_problem(L: torch.Tensor, mu: torch.Tensor, R_target: float, T: int, gamma: float = 0.0,
                  dtype: str = "f32", row_scale: torch.Tensor | None = None, mode: str = "ge",
                  power_start: torch.Tensor | None = None, layout: str = "nt") -> Problem:
@@ -289,6 +308,11 @@ def make_problem(L: torch.Tensor, mu: torch.Tensor, R_target: float, T: int, gam
     p.reserved = 0
     p.row_scale = None if row_scale is None else row_scale.data_ptr()
     n = L.shape[0] if p.layout == MV_LAYOUT_NT else mu.shape[0]
+    err = shape_error(layout, dtype, L.shape, L.element_size(), n, max(1, int(T)) if layout != "sigma" else 1,
+                      mu.numel(), None if row_scale is None else row_scale.numel(),
+                      None if power_start is None else power_start.numel())
+    if err is not None:
+        raise ValueError(err)
     p.n, p.T, p.ld = n, max(1, int(T)), L.stride(0)
     p.gamma = float(gamma)
     p.mu = mu.data_ptr()
@@ -352,6 +376,8 @@ class Solver:
     def gradient(self, y: torch.Tensor, with_z: bool = True):
         """(z, g); with ``with_z=False`` z is None and g comes from the fused
         single pass over L where that applies."""
+        if y.numel() < self.problem.n:
+            raise ValueError(f"y has {y.numel()} entries; the problem has n = {self.problem.n}")
         with_z = with_z and self.problem.layout != MV_LAYOUT_SIGMA
         z = torch.empty(self.problem.T, dtype=torch.float32, device=y.device) if with_z else None
         g = torch.empty_like(y)

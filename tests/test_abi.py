@@ -126,3 +126,21 @@ def test_padded_ld(mvmod):
     assert mvmod.padded_ld(48374, mvmod.MV_BF16) == 48376
     assert mvmod.padded_ld(48374, mvmod.MV_FP8_E4M3) == 48384
     assert mvmod.padded_ld(1000, mvmod.MV_F32) == 1000
+
+
+def test_problem_shape_checks(mvmod):
+    """The binding refuses arrays too small for the problem before any pointer
+    reaches the library (which only sees pointers and sizes)."""
+    se = mvmod.shape_error
+    assert se("nt", "f32", (100, 1004), 4, 100, 1000, 100) is None          # padded leading dim
+    assert se("tn", "bf16", (1000, 104), 2, 100, 1000, 100, None, 100) is None
+    assert se("sigma", "f32", (100, 100), 4, 100, 1, 100) is None
+    assert se("nt", "fp8", (100, 1008), 1, 100, 1000, 100, 100) is None
+    assert "reads 100 x 1000" in se("nt", "f32", (100, 999), 4, 100, 1000, 100)
+    assert "reads 1000 x 100" in se("tn", "f32", (999, 100), 4, 100, 1000, 100)
+    assert "reads 1000 x 100" in se("tn", "f32", (1000, 99), 4, 100, 1000, 100)
+    assert "reads 100 x 100" in se("sigma", "f32", (100, 99), 4, 100, 1, 100)
+    assert "2-byte" in se("nt", "f32", (100, 1000), 2, 100, 1000, 100)
+    assert se("nt", "f32", (100, 1000), 4, 100, 1000, 99).startswith("mu has 99")
+    assert se("nt", "fp8", (100, 1000), 1, 100, 1000, 100, 50).startswith("row_scale has 50")
+    assert se("nt", "f32", (100, 1000), 4, 100, 1000, 100, None, 3).startswith("power_start has 3")
