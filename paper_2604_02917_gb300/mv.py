@@ -445,6 +445,8 @@ def sketch(L_bf16: torch.Tensor, T: int, Phi_t: torch.Tensor) -> torch.Tensor:
     n x m FP32 product (tcgen05 BF16 GEMM, FP32 accumulation).  Blocking."""
     assert L_bf16.dtype == torch.bfloat16 and Phi_t.dtype == torch.bfloat16
     n, m = L_bf16.shape[0], Phi_t.shape[0]
+    if L_bf16.shape[1] < T or Phi_t.shape[1] < T:
+        raise ValueError(f"L ({L_bf16.shape[1]} columns) and Phi_t ({Phi_t.shape[1]}) must hold T = {T} periods")
     ldS = (m + 3) // 4 * 4
     out = torch.empty((n, ldS), dtype=torch.float32, device=L_bf16.device)
     _check(lib().mv_sketch(_ptr(L_bf16), n, T, L_bf16.stride(0), _ptr(Phi_t), m, Phi_t.stride(0), _ptr(out), ldS,
@@ -468,6 +470,12 @@ def countsketch(L: torch.Tensor, n: int, T: int, h: torch.Tensor, sign: torch.Te
     """tilde L = L Phi for the CountSketch Phi of (h, sign) (mv_countsketch):
     n x m FP32.  L as center_factor returns it (n x ld for "nt", T x ld for "tn")."""
     assert h.dtype == torch.int32 and sign.dtype == torch.int8 and h.is_cuda and sign.is_cuda
+    err = shape_error(layout, dtype, L.shape, L.element_size(), n, T, n,
+                      None if row_scale is None else row_scale.numel())
+    if err is None and (h.numel() < T or sign.numel() < T):
+        err = f"h ({h.numel()}) and sign ({sign.numel()}) must hold T = {T} entries"
+    if err is not None:
+        raise ValueError(err)
     nb = lib().mv_countsketch_workspace_size(T, m)
     if nb == 0:
         raise MvError(MV_ERR_INVALID_ARG, "mv_countsketch_workspace_size")
