@@ -133,7 +133,8 @@ def peaks_tensor():
 
 # kernel -> (committed ncu summary, source file whose hash the summary records)
 TRAFFIC_FILES = {"gemv_t": ("gemv_traffic.txt", "gemv.cuh"), "gemv_n": ("gemv_traffic.txt", "gemv.cuh"),
-                 "llt": ("llt_traffic.txt", "llt.cuh"), "llt_tn": ("llt_traffic.txt", "llt.cuh")}
+                 "llt": ("llt_traffic.txt", "llt.cuh"), "llt_tn": ("llt_traffic.txt", "llt.cuh"),
+                 "cs_tn": ("countsketch_traffic.txt", "countsketch.cu"), "sketch": ("sketch_traffic.txt", "gemm.cuh")}
 
 
 def committed_traffic(kernel, layout="nt"):
@@ -641,6 +642,8 @@ def main():
 
     # Sketch (tcgen05 BF16 GEMM) + FP64 truncation + NPGA on the STR model.
     str_res = None
+    # the committed ncu traffic of the sketch and CountSketch kernels was taken at this shape
+    full_cs_shape = (model.n, model.T, args.sketch_m) == (5440, 48374, 8192)
     if not args.no_str and args.dtype == "f32":
         from synth import gaussian_sketch
         R_dev = torch.from_numpy(R32).to(dev)
@@ -683,7 +686,8 @@ def main():
         tflops = flop / (min(sk_ms) * 1e-3) / 1e12
         str_res = {"sketch": {"m": args.sketch_m, "ms": min(sk_ms), "tflop": flop / 1e12,
                               "achieved_tflops": round(tflops, 1), "peak_tflops": bf16_peak,
-                              "frac": round(tflops / bf16_peak, 4), "bound": "tensor"},
+                              "frac": round(tflops / bf16_peak, 4), "bound": "tensor",
+                              "traffic": committed_traffic("sketch") if full_cs_shape else None},
                    "truncate": {"k": args.str_k, "ms": tr_ms, "first_call_s": round(t_first, 3), "gamma": gamma,
                                 "sigma_1": float(sigma[0]),
                                 "sigma_k": float(sigma[-1])},
@@ -712,8 +716,11 @@ def main():
                                   "ms": min(cs_ms), "alg_bytes": cs_bytes,
                                   "roofline": {"bound": "hbm", "achieved": round(cs_gbs, 1), "peak": peak,
                                                "unit": "GB/s", "frac": round(cs_gbs / peak, 4),
-                                               "peak_source": peak_kind, "traffic": None,
-                                               "note": "whole call (bucket lists + gather), event-timed"}}
+                                               "peak_source": peak_kind,
+                                               "traffic": committed_traffic("cs_tn") if full_cs_shape and
+                                               args.layout == "tn" and args.dtype == "f32" else None,
+                                               "note": "whole call (bucket lists + gather), event-timed; "
+                                                       "traffic: the gather kernel's ncu DRAM bytes"}}
         del Lc, hh, sg
 
     # Plain NPGA at 200 x 1000 (5 factors, seed 0): 2000 iterations, no early

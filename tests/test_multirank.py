@@ -53,3 +53,24 @@ def test_two_ranks_gloo():
     assert m0 == m1 == 15.0                     # both ranks see the slowest rank's time
     assert s0 != s1 and (n0, T0) == (n1, T1)     # same shape, independent problems (weak scaling)
     assert ref1 is None                          # the reference arm prints on rank 0 only
+
+
+def test_committed_traffic_lookup(tmp_path, monkeypatch):
+    """The bench reports an ncu traffic figure only while the kernel source
+    still hashes to the one the summary records."""
+    import shutil
+    import bench
+    for k in bench.TRAFFIC_FILES:
+        v = bench.committed_traffic(k, "tn" if k.endswith("_tn") else "nt")
+        assert v is None or v > 0
+    # a copy of the tree with one source byte changed: no figure
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "paper_2604_02917_gb300" / "csrc").mkdir(parents=True)
+    shutil.copy(os.path.join(bench.ROOT, "profiles", "countsketch_traffic.txt"), tmp_path / "profiles")
+    src = open(os.path.join(bench.ROOT, "paper_2604_02917_gb300", "csrc", "countsketch.cu"), "rb").read()
+    (tmp_path / "paper_2604_02917_gb300" / "csrc" / "countsketch.cu").write_bytes(src)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    same = bench.committed_traffic("cs_tn", "tn")
+    (tmp_path / "paper_2604_02917_gb300" / "csrc" / "countsketch.cu").write_bytes(src + b"\n")
+    assert bench.committed_traffic("cs_tn", "tn") is None
+    assert same is None or same > 0
