@@ -134,6 +134,7 @@ def peaks_tensor():
 # kernel -> (committed ncu summary, source file whose hash the summary records)
 TRAFFIC_FILES = {"gemv_t": ("gemv_traffic.txt", "gemv.cuh"), "gemv_n": ("gemv_traffic.txt", "gemv.cuh"),
                  "llt": ("llt_traffic.txt", "llt.cuh"), "llt_tn": ("llt_traffic.txt", "llt.cuh"),
+                 "sigma_gemm": ("sigma_traffic.txt", "sigma.cu"),
                  "cs_tn": ("countsketch_traffic.txt", "countsketch.cu"), "sketch": ("sketch_traffic.txt", "gemm.cuh")}
 
 
@@ -615,7 +616,9 @@ def main():
             entry = {"form_s": t_form,
                      "form_roofline": {"bound": "tensor", "achieved": round(flops / t_form / 1e12, 1),
                                        "peak": peak_tf, "unit": "TFLOP/s",
-                                       "frac": round(flops / t_form / 1e12 / peak_tf, 4), "traffic": None,
+                                       "frac": round(flops / t_form / 1e12 / peak_tf, 4),
+                                       "traffic": committed_traffic("sigma_gemm") if sdt == "f32" and
+                                       (model.n, model.T) == (5440, 48374) else None,
                                        "kernel": "sigma_gemm", "flops_per_launch": flops,
                                        "note": "executed BF16 tile flops (upper tiles x segments)"}}
             sv = mv.Solver(S, mu, Rt, model.T, power_start=r0, eps=args.eps, layout="sigma")
