@@ -24,6 +24,7 @@ the max over ranks.
 from __future__ import annotations
 
 import argparse
+import datetime
 import json
 import os
 import subprocess
@@ -200,23 +201,66 @@ def roofline(infos, model, dtype, layout="nt"):
     return roof
 
 
-class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+
+def parse_clock_samples(lines, t0=None, t1=None, margin=0.1):
+    """Summarise nvidia-smi lines (timestamp, index, clocks.sm, clocks.max.sm,
+    power.draw, active mask, then the four reasons of CLOCK_REASONS): the
+    samples stamped within [t0 - margin, t1 + margin] (host epoch seconds),
+    or all of them when none is."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            ts = None
+        try:
+            sm, mx = float(parts[2]), float(parts[3])
+        except ValueError:
+            continue
+        act = {nm for nm, val in zip(CLOCK_REASONS, parts[6:10]) if val.lower().startswith("active")}
+        rows.append((ts, sm, mx, act))
+    if not rows:
+        return None
+    window = "timed region"
+    keep = [r for r in rows if t0 is not None and t1 is not None and r[0] is not None
+            and t0 - margin <= r[0] <= t1 + margin]
+    if not keep:
+        keep, window = rows, "whole sampling (no sample inside the timed region)"
+    reasons = set().union(*(r[3] for r in keep))
+    return {"sm_mhz": float(np.median([r[1] for r in keep])), "sm_max_mhz": float(max(r[2] for r in keep)),
+            "reasons": sorted(reasons), "samples": len(keep), "window": window}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons around the timed
+    region: sampling starts before the warm-up (every 50 ms), ``mark()``
+    notes the host time at which the timed region starts, and ``stop()``
+    keeps the samples stamped between then and its own call."""
+
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, dev_index):
+    def __init__(self, dev_index, period_ms=50):
+        self.t0 = None
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-i", str(dev_index), "-lms", "200"], stdout=self.f,
+                                       "-i", str(dev_index), "-lms", str(period_ms)], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
 
+    def mark(self):
+        self.t0 = time.time()
+
     def stop(self):
+        t1 = time.time()
         if self.p is None:
             return None
         self.p.terminate()
@@ -226,25 +270,9 @@ class Clocks:
             self.p.kill()
         self.f.flush()
         self.f.seek(0)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.f.read().strip().splitlines():
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, parts[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(nm)
+        out = parse_clock_samples(self.f.read().strip().splitlines(), self.t0, t1)
         os.unlink(self.f.name)
-        if not sm:
-            return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return out
 
 
 def cpu_baseline(model, gpu_iters, power_iters, eps, R32=None, budget_s=25.0):
@@ -457,14 +485,15 @@ def main():
         del sv
         return out
 
+    clk = Clocks(local)
     for _ in range(args.warmup):
         solver.solve()
     barrier()
-    clk = Clocks(local)
     stream = torch.cuda.current_stream()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     infos = []
     barrier()
+    clk.mark()
     ev0.record(stream)
     for _ in range(args.steps):
         _, info = solver.solve()

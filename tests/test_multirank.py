@@ -74,3 +74,24 @@ def test_committed_traffic_lookup(tmp_path, monkeypatch):
     (tmp_path / "paper_2604_02917_gb300" / "csrc" / "countsketch.cu").write_bytes(src + b"\n")
     assert bench.committed_traffic("cs_tn", "tn") is None
     assert same is None or same > 0
+
+
+def test_clock_samples_window():
+    """Clock samples are summarised over the timed region only (fallback: all)."""
+    import datetime
+    import bench
+    base = datetime.datetime(2026, 1, 2, 3, 4, 5, 0)
+
+    def line(dt_s, sm, pcap="Not Active", hw="Not Active"):
+        ts = (base + datetime.timedelta(seconds=dt_s)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {sm}, 2070, 900.5, 0x0, {hw}, Not Active, Not Active, {pcap}"
+
+    lines = [line(0.0, 1200), line(1.0, 2070), line(1.05, 2040, pcap="Active"), line(3.0, 900, hw="Active")]
+    t0 = base.timestamp() + 0.95
+    out = bench.parse_clock_samples(lines, t0, t0 + 0.2)
+    assert out["samples"] == 2 and out["window"] == "timed region"
+    assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0 and out["reasons"] == ["sw_power_cap"]
+    every = bench.parse_clock_samples(lines, t0 + 10.0, t0 + 11.0)
+    assert every["samples"] == 4 and every["window"].startswith("whole")
+    assert "hw_slowdown" in every["reasons"]
+    assert bench.parse_clock_samples(["garbage"], None, None) is None
