@@ -144,3 +144,59 @@ def test_problem_shape_checks(mvmod):
     assert se("nt", "f32", (100, 1000), 4, 100, 1000, 99).startswith("mu has 99")
     assert se("nt", "fp8", (100, 1000), 1, 100, 1000, 100, 50).startswith("row_scale has 50")
     assert se("nt", "f32", (100, 1000), 4, 100, 1000, 100, None, 3).startswith("power_start has 3")
+
+
+def test_host_side_argument_errors_sketches_and_sigma(mvmod):
+    """CountSketch, explicit Sigma and the knee rule refuse bad arguments on
+    the host, before any launch."""
+    lib = mvmod.lib()
+    E, W, U = mvmod.MV_ERR_INVALID_ARG, mvmod.MV_ERR_WORKSPACE, mvmod.MV_ERR_UNSUPPORTED
+    assert lib.mv_countsketch_workspace_size(0, 8) == 0
+    assert lib.mv_countsketch_workspace_size(8, 0) == 0
+    assert lib.mv_countsketch_workspace_size(1 << 31, 8) == 0
+    assert lib.mv_countsketch_workspace_size(100, 16) > 0
+    f, odd = C.c_void_p(4096), C.c_void_p(4100)
+    NT, TN, SG = mvmod.MV_LAYOUT_NT, mvmod.MV_LAYOUT_TN, mvmod.MV_LAYOUT_SIGMA
+    F32, FP8 = mvmod.MV_F32, mvmod.MV_FP8_E4M3
+
+    def cs(L=f, dt=F32, lay=TN, rs=None, n=64, T=300, ld=64, m=32, ldS=32, ws=None, wsb=0):
+        return lib.mv_countsketch(L, dt, lay, rs, n, T, ld, f, f, m, f, ldS, ws, wsb, None)
+
+    assert cs(L=None) == E
+    assert cs(dt=9) == E
+    assert cs(lay=SG) == E
+    assert cs(ldS=31) == E
+    assert cs(ld=63) == E                                   # TN: ld >= n
+    assert cs(lay=NT, ld=296) == E                          # NT: ld >= T
+    assert cs(L=odd) == E                                   # 16-byte alignment
+    assert cs(dt=FP8) == E                                  # FP8 needs row scales
+    assert cs(lay=NT, T=60000, ld=60000) == U               # n x T row above 200 KB
+    assert cs() == W                                       # no workspace
+    # explicit Sigma: the problem must be a factor in the n x T layout
+    p = mvmod.Problem()
+    p.L, p.mu, p.n, p.T, p.ld, p.dtype, p.layout = 4096, 4096, 10, 7, 8, F32, NT
+    assert lib.mv_sigma_workspace_size(C.byref(p)) > 0
+    p.layout = TN
+    assert lib.mv_sigma_workspace_size(C.byref(p)) == 0
+    p.layout, p.ld = NT, 4
+    assert lib.mv_sigma_workspace_size(C.byref(p)) == 0     # ld < T
+    p.ld, p.n = 8, 40000
+    assert lib.mv_sigma_workspace_size(C.byref(p)) == 0     # n above 32768
+    p.n, p.dtype, p.ld = 10, FP8, 16
+    assert lib.mv_sigma_workspace_size(C.byref(p)) == 0     # FP8 needs row scales
+    p.dtype, p.ld = F32, 8
+    assert lib.mv_sigma_form(C.byref(p), None, 12, None, 0, None) == E
+    assert lib.mv_sigma_form(C.byref(p), f, 9, None, 0, None) == E      # ldS < n
+    assert lib.mv_sigma_form(C.byref(p), f, 12, None, 0, None) == W
+    # knee rule: tau > 0, 0 < rho < 1, kappa target <= 0 (off) or > 1
+    k, g = C.c_int64(0), C.c_double(0.0)
+
+    def knee(tau=0.1, rho=0.5, kmax=4, kappa=0.0, n=10):
+        return lib.mv_str_truncate_knee(f, n, 16, 16, tau, rho, kmax, kappa, -1.0, 1.0, f, 4, f, C.byref(k),
+                                        C.byref(g), None, 0, None)
+
+    assert knee(tau=0.0) == E
+    assert knee(rho=1.0) == E
+    assert knee(kappa=0.5) == E
+    assert knee(kmax=11) == E
+    assert knee(n=1) == E
