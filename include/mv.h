@@ -236,7 +236,8 @@ typedef struct {
     int32_t converged;        /* 1 if kkt <= eps                                         */
     int32_t proj_failures;    /* projections that hit their step budget                  */
     double kkt;               /* residual of the returned x                              */
-    double objective;         /* f(x) = ||L^T x||^2 + gamma ||x||^2 (one extra pass)     */
+    double objective;         /* f(x) = ||L^T x||^2 + gamma ||x||^2: x^T (L L^T x) from  */
+                              /* the product the last KKT test kept, else one more pass  */
     double alpha;             /* step used                                               */
     double lambda_hat;        /* power-method estimate of ||L_eff||_2^2 (0 if overridden)*/
     double nu;                /* return-row multiplier of the last projection            */
