@@ -13,8 +13,8 @@ L L^T y streams at copy speed; ``--layout nt`` keeps it n x T.
 Printed JSON (one line, rank 0): value = seconds per solve (lower is
 better), e2e = the same through host buffers (upload R, center, solve,
 download x), roofline = the dominant gemv kernel's HBM throughput measured
-with CUDA events around every launch of the loop, cpu_baseline = the FP64
-oracle on this host's cores (bounded sample, extrapolated per solve).
+with CUDA events around every launch of the loop, cpu_baseline = one complete
+solve of the same workload by the FP64 oracle on this host's cores.
 
 ``--impl reference`` times the FP64 oracle (the CPU restatement of the
 method) instead, as the reference arm.  Multi-GPU (torchrun): every rank
@@ -275,46 +275,60 @@ class Clocks:
         return out
 
 
-def cpu_baseline(model, gpu_iters, power_iters, eps, R32=None, budget_s=25.0):
-    """FP64 oracle on this host, timed on a bounded sample and scaled to one solve.
-
-    Sample: p power iterations and k NPGA iterations (with one literal KKT
-    check) on the full matrix; the per-iteration times are scaled to the GPU
-    solve's 50 power iterations and its iteration count.
-    """
+def oracle_problem(model, R32=None):
+    """The FP64 oracle's inputs for the headline workload: mu and L from its
+    own centering of the same FP32-rounded panel, the return target and the
+    power-method start."""
     from synth import factor_returns, power_start
     from oracle.center import center_factor
-    from oracle.npga import initial_point, npga, power_norm2, step_size
     if R32 is None:
         R32 = factor_returns(model, np.float32)
     mu, L, _ = center_factor(R32.astype(np.float64))
-    del R32
-    Rt = float(np.percentile(mu, 60))
-    r0 = power_start(model.n)
-    t0 = time.perf_counter()
-    p = 2
-    lam = power_norm2(L, r0, p)
-    t_pow = (time.perf_counter() - t0) / p
-    a = step_size(lam, 0.0)
-    x0 = initial_point(mu, Rt)
-    k = 5
-    t0 = time.perf_counter()
-    npga(L, 0.0, mu, Rt, x0, a, eps=0.0, max_iter=k, kkt_every=5)
-    t_k = (time.perf_counter() - t0) / k        # includes the k=0 and k=5 literal KKT checks
-    per_solve = power_iters * t_pow + gpu_iters * t_k
-    return {"value": per_solve, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"FP64 NumPy oracle on the full {model.n}x{model.T} matrix: {p} power iterations "
-                      f"({t_pow:.3f} s each) and {k} NPGA iterations with 2 literal KKT checks "
-                      f"({t_k:.3f} s each), scaled to {power_iters} power + {gpu_iters} NPGA iterations"}
+    return mu, L, float(np.percentile(mu, 60)), power_start(model.n)
 
 
-def row_oracles(model, R32, res):
-    """The FP64 oracle timed beside each further row, on bounded samples of
-    the same workloads, each scaled to the full row by the stated factor
-    (host cores, as it stands; roughly 30-60 s in all)."""
+def oracle_solve(mu, L, Rt, r0, eps, power_iters=50):
+    """One complete FP64 oracle solve, timed: the power method, Algorithm 1
+    with the literal KKT test every 5 iterations until the residual is <= eps,
+    and the objective (the work of one GPU step; the centering, like the
+    GPU's, is outside the timed region)."""
+    from oracle.npga import initial_point, npga, power_norm2, step_size
+    t0 = time.perf_counter()
+    lam = power_norm2(L, r0, power_iters)
+    res = npga(L, 0.0, mu, Rt, initial_point(mu, Rt), step_size(lam, 0.0), eps=eps, max_iter=100000, kkt_every=5)
+    return time.perf_counter() - t0, res
+
+
+def cpu_baseline(model, eps, R32=None, x_gpu=None, f_gpu=None, prob=None):
+    """The FP64 oracle on this host's cores: one complete solve of the
+    headline workload (not a sample), with its own iteration count and its
+    distance to the GPU's answer."""
+    mu, L, Rt, r0 = oracle_problem(model, R32) if prob is None else prob
+    t, res = oracle_solve(mu, L, Rt, r0, eps)
+    out = {"value": t, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"full solve: FP64 NumPy oracle on the whole {model.n}x{model.T} matrix, 50 power iterations "
+                     f"+ Algorithm 1 with the literal KKT test every 5 iterations to {eps:g} "
+                     f"({res.iters} iterations, KKT {res.kkt:.2e}) + objective",
+           "iterations": res.iters, "kkt": res.kkt, "objective": res.f}
+    if x_gpu is not None:
+        out["x_inf_vs_gpu"] = float(np.max(np.abs(np.asarray(x_gpu) - res.x)))
+    if f_gpu is not None:
+        out["rel_obj_gpu_vs_oracle"] = (f_gpu - res.f) / res.f
+    return out
+
+
+def row_oracles(model, R32, res, prob=None):
+    """The FP64 oracle timed beside each further row, on the host cores, as it
+    stands.  Each row runs the whole workload where that takes well under a
+    minute (the sketch, the CountSketch, the truncation, the explicit-Sigma
+    formation and solve, the 64-target frontier at 200 x 1000, the adjoint);
+    the frontier at the full shape and the uneven batch would take several
+    minutes, so they are timed on a stated sample and scaled (marked
+    "scaled": true)."""
     from synth import CFG_SMALL, countsketch_hash, gaussian_sketch, power_start
     from oracle.center import center_factor
-    from oracle.npga import gradient, gradient_sigma, initial_point, npga, power_norm2, step_size
+    from oracle.npga import (gradient, initial_point, npga, npga_sigma, power_norm2, power_norm2_sigma,
+                             sigma_from_factor, step_size)
     from oracle.projection import project_F
     from oracle import adjoint as oadj
     from oracle import strmodel
@@ -322,61 +336,59 @@ def row_oracles(model, R32, res):
     out = {}
     n, T, m = model.n, model.T, 8192
 
-    def entry(t_sample, scale, sample):
-        return {"value": t_sample * scale, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
-                "sample_s": round(t_sample, 3), "scale": round(scale, 2)}
+    def full(t, sample):
+        return {"value": t, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample, "scaled": False}
 
-    mu, L, _ = center_factor(R32.astype(np.float64))
-    rows, Ts = 64, 6000
-    Ls = L[:rows, :Ts]
-    # a8 Gaussian sketch L Phi: 64 rows x 6000 periods of the full product
-    Phi_t = gaussian_sketch(Ts, m, seed=2)
+    def scaled(t_sample, scale, sample):
+        return {"value": t_sample * scale, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample,
+                "sample_s": round(t_sample, 3), "scale": round(scale, 2), "scaled": True}
+
+    mu, L, Rt, r0 = oracle_problem(model, R32) if prob is None else prob
+    # a8 Gaussian sketch L Phi, whole product
+    Phi_t = gaussian_sketch(T, m, seed=2)
     t0 = time.perf_counter()
-    strmodel.sketch(Ls, Phi_t)
-    out["sketch"] = entry(time.perf_counter() - t0, (n / rows) * (T / Ts),
-                          f"L Phi on {rows} rows x {Ts} periods, m = {m}, scaled by rows and periods")
+    Lt = strmodel.sketch(L, Phi_t)
+    out["sketch"] = full(time.perf_counter() - t0, f"the whole L Phi: {n} x {T} times {T} x {m} in FP64")
     del Phi_t
-    # f2 CountSketch (dense Phi, as the oracle states it)
-    h, sg = countsketch_hash(Ts, m, seed=2)
-    t0 = time.perf_counter()
-    strmodel.countsketch(Ls, h, sg, m)
-    out["countsketch"] = entry(time.perf_counter() - t0, (n / rows) * (T / Ts),
-                               f"L Phi (dense CountSketch Phi) on {rows} rows x {Ts} periods, scaled")
-    # a9 truncation: eigh of tilde L tilde L^T at n' = 1360, scaled by (n / n')^3
-    nt = 1360
-    Lt = np.random.default_rng(3).standard_normal((nt, 2048)) * 1e-3
+    # a9 truncation of that sketch: K = tilde L tilde L^T and eigh (all n pairs), top 512 kept
     t0 = time.perf_counter()
     strmodel.truncate(Lt, 512)
-    out["truncate"] = entry(time.perf_counter() - t0, (n / nt) ** 3,
-                            f"K = tilde L tilde L^T and eigh at n' = {nt}, scaled by (n / n')^3")
-    # f1 explicit Sigma: formation on 64 rows (scaled by n / 64) + 3 iterations on the full Sigma
+    out["truncate"] = full(time.perf_counter() - t0, f"K = tilde L tilde L^T ({n} x {n}) and eigh, k = 512")
+    del Lt
+    # f2 CountSketch (dense Phi, as the oracle states it), whole product
+    h, sg = countsketch_hash(T, m, seed=2)
     t0 = time.perf_counter()
-    L[:rows] @ L.T
-    t_form = (time.perf_counter() - t0) * (n / rows)
-    # the solve's per-iteration cost only depends on n: time it on a synthetic SPD Sigma of the same size
-    A = np.random.default_rng(4).standard_normal((n, 256)) * 1e-2
-    Sig = A @ A.T + 1e-4 * np.eye(n)
-    Rt = float(np.percentile(mu, 60))
-    y = initial_point(mu, Rt)
+    strmodel.countsketch(L, h, sg, m)
+    out["countsketch"] = full(time.perf_counter() - t0, f"the whole L Phi with the dense {T} x {m} CountSketch Phi")
+    # f1 explicit Sigma: formation + the whole solve (50 power iterations on Sigma + Algorithm 1 to 1e-6)
     t0 = time.perf_counter()
-    for _ in range(3):
-        g = gradient_sigma(Sig, 0.0, y)
-        project_F(y - 1e-3 * g, mu, Rt)
-    t_it = (time.perf_counter() - t0) / 3
-    iters = res.get("sigma_iters", 50)
-    out["sigma"] = {"value": t_form + t_it * (50 + iters), "unit": "s", "cores": cores, "kind": "oracle",
-                    "sample": f"L L^T on 64 rows scaled by n / 64 ({t_form:.1f} s) + 3 iterations (Sigma y and the "
-                              f"projection, {t_it * 1e3:.0f} ms each) scaled to 50 power + {iters} NPGA iterations"}
-    del Sig, A
-    # a11 frontier: 2 of the 64 targets at 200 x 1000, scaled by 32
+    Sig = sigma_from_factor(L)
+    t_form = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rs_ = npga_sigma(Sig, 0.0, mu, Rt, initial_point(mu, Rt), step_size(power_norm2_sigma(Sig, r0, 50), 0.0),
+                     eps=1e-6, max_iter=100000)
+    t_solve = time.perf_counter() - t0
+    out["sigma"] = dict(full(t_form + t_solve, f"Sigma = L L^T in FP64 ({t_form:.1f} s) + the whole solve on it "
+                                               f"({t_solve:.2f} s, {rs_.iters} iterations)"),
+                        form_s=t_form, solve_s=t_solve)
+    del Sig
+    # a11 frontier at 200 x 1000: all 64 targets, each a full solve
     Rf = factor_returns_small()
     muf, Lf, _ = center_factor(Rf)
     tg = np.linspace(np.percentile(muf, 10), np.percentile(muf, 90), 64)
-    lam = power_norm2(Lf, power_start(Lf.shape[0]), 50)
     t0 = time.perf_counter()
-    for r in tg[:2]:
+    lam = power_norm2(Lf, power_start(Lf.shape[0]), 50)
+    for r in tg:
         npga(Lf, 0.0, muf, float(r), initial_point(muf, float(r)), step_size(lam, 0.0), eps=1e-6, max_iter=20000)
-    out["frontier_200x1000"] = entry(time.perf_counter() - t0, 32.0, "2 of the 64 targets at 200 x 1000, scaled by 32")
+    out["frontier_200x1000"] = full(time.perf_counter() - t0, "all 64 targets at 200 x 1000, each solved to 1e-6")
+    # a11 frontier at the full shape: 2 of the 64 targets solved in full, scaled by 32
+    tgf = np.linspace(np.percentile(mu, 10), np.percentile(mu, 90), 64)
+    t0 = time.perf_counter()
+    lamf = power_norm2(L, r0, 50)
+    for r in (tgf[0], tgf[63]):
+        npga(L, 0.0, mu, float(r), initial_point(mu, float(r)), step_size(lamf, 0.0), eps=1e-6, max_iter=100000)
+    out["frontier_full_shape"] = scaled(time.perf_counter() - t0, 32.0,
+                                        "targets 1 and 64 of 64 at the full shape, each a full solve, scaled by 32")
     # plain NPGA at 200 x 1000: the whole 2000-iteration run, and the GPU's x against it
     if res.get("small_x") is not None:
         Rt1 = float(np.percentile(muf, 60))
@@ -387,9 +399,9 @@ def row_oracles(model, R32, res):
         xg = np.asarray(res["small_x"], dtype=np.float64)
         fo = float(np.sum((Lf.T @ ref.x) ** 2))
         fg = float(np.sum((Lf.T @ xg) ** 2))
-        out["small_200x1000"] = dict(entry(t1, 1.0, "the whole solve: 50 power + 2000 NPGA iterations"),
+        out["small_200x1000"] = dict(full(t1, "the whole solve: 50 power + 2000 NPGA iterations"),
                                      x_inf_err=float(np.max(np.abs(xg - ref.x))), rel_obj_err=(fg - fo) / fo)
-    # a13 adjoint: 20 of the 500 unrolled iterations at 2000 x 10000 (forward + reverse), scaled by 25
+    # a13 adjoint: the whole 500-iteration forward (with its tape) and reverse sweep at 2000 x 10000
     am = CFG_SMALL.scaled(2000, 10000, seed=0)
     from synth import factor_returns
     mua, La, _ = center_factor(factor_returns(am, np.float32).astype(np.float64))
@@ -397,9 +409,13 @@ def row_oracles(model, R32, res):
     x0 = initial_point(mua, Rta)
     a = step_size(power_norm2(La, power_start(am.n), 50), 0.0)
     t0 = time.perf_counter()
-    x, tape, betas = oadj.unrolled_forward(La, 0.0, mua, Rta, x0, a, 20, record=True)
+    x, tape, betas = oadj.unrolled_forward(La, 0.0, mua, Rta, x0, a, 500, record=True)
+    t_f = time.perf_counter() - t0
     oadj.backward(La, 0.0, mua, a, tape, betas, np.ones(am.n))
-    out["adjoint"] = entry(time.perf_counter() - t0, 25.0, "forward + reverse of 20 of the 500 iterations, scaled by 25")
+    t_all = time.perf_counter() - t0
+    out["adjoint"] = dict(full(t_all, f"forward ({t_f:.1f} s) + reverse of all 500 iterations at 2000 x 10000"),
+                          forward_s=t_f, backward_s=t_all - t_f)
+    del tape
     # a12 batch: the oracle's per-iteration cost is proportional to n T; time 3 iterations at 1000 x 4000
     # and scale by the batch's sum over problems of n_j T_j (50 power + its iterations)
     if res.get("batch_elem_iters"):
@@ -411,8 +427,8 @@ def row_oracles(model, R32, res):
         for _ in range(3):
             project_F(yb - 1e-3 * gradient(Lb, 0.0, yb), mub, Rtb)
         t_el = (time.perf_counter() - t0) / 3 / (1000 * 4000)
-        out["batch"] = {"value": t_el * res["batch_elem_iters"], "unit": "s", "cores": cores, "kind": "oracle",
-                        "sample": "3 iterations at 1000 x 4000, scaled by sum_j n_j T_j (50 + iterations_j)"}
+        out["batch"] = scaled(t_el * 1000 * 4000, res["batch_elem_iters"] / (1000 * 4000),
+                              "3 iterations at 1000 x 4000, scaled by sum_j n_j T_j (50 + iterations_j)")
     return out
 
 
@@ -422,20 +438,24 @@ def factor_returns_small():
 
 
 def reference_arm(args):
+    """The reference arm: the FP64 oracle (the CPU restatement of the method)
+    on the host cores, each step one complete solve of the same workload."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    from synth import factor_returns
     model = workload(args, 0)
-    R32 = factor_returns(model, np.float32)
-    gpu_iters_est = 60            # typical iteration count of this workload (mv arm reports its own)
+    prob = oracle_problem(model)
     vals = []
+    res = None
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(model, gpu_iters_est, 50, args.eps, R32=R32)
+        t, res = oracle_solve(*prob, args.eps)
         if i >= args.warmup:
-            vals.append(cb["value"])
+            vals.append(t)
     v = float(np.mean(vals))
-    cb["value"] = v
+    cb = {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": f"each step one full solve: 50 power iterations + Algorithm 1 with the literal KKT test every 5 "
+                    f"iterations to {args.eps:g} ({res.iters} iterations) on the whole {model.n}x{model.T} matrix",
+          "iterations": res.iters, "kkt": res.kkt}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -501,6 +521,7 @@ def main():
     ev1.record(stream)
     barrier()
     clocks = clk.stop()
+    x_head = solver.x.cpu().numpy()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     tinfos = launch_profile(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
                             layout=args.layout, two_pass=1 if args.two_pass else 0)
@@ -894,14 +915,14 @@ def main():
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        iters = int(np.median([i["iterations"] for i in infos]))
         del L
         torch.cuda.empty_cache()
-        cb = cpu_baseline(model, iters, 50, args.eps, R32=R32)
+        prob = oracle_problem(model, R32)
+        cb = cpu_baseline(model, args.eps, x_gpu=x_head, f_gpu=infos[-1]["objective"], prob=prob)
         if not args.no_row_oracles:
             res = {"sigma_iters": sigma_res["f32_L"]["iterations"] if sigma_res else 50,
                    "batch_elem_iters": batch_elem_iters, "small_x": small_x if small is not None else None}
-            row_cpu = row_oracles(model, R32, res)
+            row_cpu = row_oracles(model, R32, res, prob)
             if str_res is not None:
                 for k in ("sketch", "countsketch", "truncate"):
                     if k in str_res:
@@ -910,6 +931,8 @@ def main():
                 sigma_res["cpu_oracle"] = row_cpu["sigma"]
             if frontier is not None and "200x1000" in frontier:
                 frontier["200x1000"]["cpu_oracle"] = row_cpu["frontier_200x1000"]
+            if frontier is not None and "full_shape" in frontier:
+                frontier["full_shape"]["cpu_oracle"] = row_cpu["frontier_full_shape"]
             if adj is not None:
                 adj["cpu_oracle"] = row_cpu["adjoint"]
             if small is not None and "small_200x1000" in row_cpu:

@@ -392,6 +392,40 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
 int mv_sketch(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m,
               int64_t ldP, float *d_L_sketch, int64_t ldS, mv_stream_t stream);
 
+/*  The same for a factor stored in any mv_dtype (MV_LAYOUT_NT, n x T, leading
+ *  dim ldL >= T):
+ *    MV_BF16      as mv_sketch (no workspace);
+ *    MV_F32       L = H + D split into two BF16 parts in the workspace; both
+ *                 are multiplied against each staged Phi tile into one
+ *                 accumulator, so the only rounding of L is that of H + D
+ *                 (below 2^-18 |L_it| per term);
+ *    MV_FP8_E4M3  the stored values are expanded exactly to BF16 in the
+ *                 workspace and row i of the result is scaled by
+ *                 d_row_scale[i].
+ *  Workspace: mv_sketch_workspace_size(dtype, n, T) bytes, 256-byte aligned
+ *  (0 for BF16).  Blocking. */
+size_t mv_sketch_workspace_size(int32_t dtype, int64_t n, int64_t T);
+int mv_sketch_dtype(const void *d_L, int32_t dtype, const float *d_row_scale, int64_t n, int64_t T, int64_t ldL,
+                    const void *d_Phi_t, int64_t m, int64_t ldP, float *d_L_sketch, int64_t ldS,
+                    void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
+/*  Seeded draws of the sketch maps of Sec. 2.3, made on the device.  The
+ *  generator is Philox4x32-10 (Salmon et al., SC'11), counter-based, with the
+ *  key (seed mod 2^32, seed div 2^32):
+ *  mv_gaussian_sketch writes Phi^T (m x T BF16, leading dim ldP >= T, ldP a
+ *    multiple of 8, columns T..ldP-1 zero): entry (j, t) is the Box--Muller
+ *    normal of the Philox block at counter (t div 4, j, 0, 0) -- words w_0..w_3
+ *    give u = ((w_a >> 8) + 1) 2^-24 (a = 0, 2) and v = (w_b >> 8) 2^-24
+ *    (b = 1, 3); r = sqrt(-2 ln u); (r cos 2 pi v, r sin 2 pi v) for (u_0, v_1)
+ *    and (u_2, v_3) are the normals for t mod 4 = 0, 1, 2, 3 -- times
+ *    1/sqrt(m), computed in FP32 and rounded to BF16.
+ *  mv_countsketch_draw writes the CountSketch hash and signs (T entries
+ *    each) from the block at counter (t, 0, 1, 0): h(t) = (w_0 m) >> 32 and
+ *    s_t = 1 - 2 (w_1 & 1); they feed mv_countsketch unchanged.
+ *  Asynchronous; deterministic for a given seed. */
+int mv_gaussian_sketch(uint64_t seed, int64_t m, int64_t T, void *d_Phi_t, int64_t ldP, mv_stream_t stream);
+int mv_countsketch_draw(uint64_t seed, int64_t T, int64_t m, int32_t *d_hash, int8_t *d_sign, mv_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * 4b. CountSketch (Sec. 2.3, construction (2)): the sparse alternative to
  *     the Gaussian sketch.  Phi (T x m) has one nonzero per row,
@@ -452,11 +486,26 @@ int mv_str_truncate_knee(const float *d_L_sketch, int64_t n, int64_t m, int64_t 
                          int64_t ldE, double *d_sigma, int64_t *h_k_out, double *h_gamma_out, void *d_ws,
                          size_t ws_bytes, mv_stream_t stream);
 
-/*  mv_sketch followed by mv_str_truncate (the whole STR build of Sec. 2.5);
- *  d_L_sketch receives tilde L.  Workspace as mv_str_workspace_size.  Blocking. */
-int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m,
-                  int64_t ldP, int64_t k, double gamma, double trace_sigma, float *d_L_sketch, int64_t ldS,
-                  float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out, void *d_ws,
+/* ------------------------------------------------------------------------
+ * 3h. The whole STR build of Sec. 2.5 from a seed: (1) Phi drawn on the
+ *     device by mv_gaussian_sketch(seed, m, T) (Gaussian JL, N(0, 1/m)),
+ *     (2) tilde L = L Phi by mv_sketch_dtype, (3) truncation to rank k and
+ *     the ridge by mv_str_truncate.
+ *
+ *  d_L          [in]  the factor, dtype F32 / BF16 / FP8 e4m3 (d_row_scale
+ *                     then holds the n row scales), n x T, leading dim ldL.
+ *  d_L_sketch   [out] n x m FP32 (leading dim ldS >= m), or NULL: tilde L is
+ *                     then kept in the workspace only.
+ *  d_L_eff, ldE, d_sigma, h_gamma_out: as mv_str_truncate.
+ *  Workspace: mv_sketch_str_workspace_size(dtype, n, T, m, k, own_sketch)
+ *  bytes, own_sketch = 1 when d_L_sketch is NULL.  The sketch stage (Phi^T,
+ *  m T BF16, and the BF16 copy of L) and the truncation reuse the same bytes.
+ *  Blocking.
+ * ------------------------------------------------------------------------ */
+size_t mv_sketch_str_workspace_size(int32_t dtype, int64_t n, int64_t T, int64_t m, int64_t k, int32_t own_sketch);
+int mv_sketch_str(const void *d_L, int32_t dtype, const float *d_row_scale, int64_t n, int64_t T, int64_t ldL,
+                  int64_t m, uint64_t seed, int64_t k, double gamma, double trace_sigma, float *d_L_sketch,
+                  int64_t ldS, float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out, void *d_ws,
                   size_t ws_bytes, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
@@ -474,9 +523,12 @@ int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void
  *  checkpoints taken every opts->checkpoint_every iterations; each backward
  *  step applies the projection's Jacobian on the active set
  *  (P = I - C (C^T C)^{-1} C^T on the support, C = [1, mu] or [1]) and the
- *  transposed products (two GEMV passes); dL accumulates
- *  -2 alpha (v_bar z_k^T + y_k (L^T v_bar)^T) per segment with one FP32 GEMM
- *  (cuBLAS SGEMM, loaded at run time).  FP32 factor only.  Blocking.
+ *  transposed products (one pass over L each); dL accumulates
+ *  -2 alpha (v_bar z_k^T + y_k (L^T v_bar)^T) per segment as one tcgen05
+ *  GEMM whose FP32 operands are split into three BF16 pieces (six piece
+ *  products, FP32-accurate), added into d_dL in place.  d_dL 16-byte
+ *  aligned with ldD a multiple of 4 for the vector path (any other pitch is
+ *  handled element by element).  FP32 factor only.  Blocking.
  * ------------------------------------------------------------------------ */
 size_t mv_backward_workspace_size(const mv_problem *P, const mv_solve_opts *opts);
 int mv_npga_backward(const mv_problem *P, const mv_solve_opts *opts, const double *d_x0,
@@ -508,12 +560,21 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
  *  MV_NOALLOC_SCRATCH_BYTES inside the library, which every GPU that loads
  *  the library keeps until the process exits.  The call allocates nothing
  *  (no cudaMalloc, cudaFree or allocating library routine).
- *  - Limit: problems whose workspace (mv_npga_workspace_size) exceeds
- *    MV_NOALLOC_SCRATCH_BYTES are rejected on the host with
- *    MV_ERR_UNSUPPORTED before anything is launched; mv_last_error() then
- *    states the bytes needed.  (5440 x 48374 FP32 fits.)
- *  - The first call on a device looks up the array's device address with
- *    that device current; make that first call before any stream capture.
+ *  - Limit: the call always runs the two-pass GEMV product (never the fused
+ *    single pass), and its scratch is that path's: the vectors plus the
+ *    partial sums of the row splits, whose count follows the device's SM
+ *    count.  mv_gradient_noalloc_scratch_size(P) returns that figure for
+ *    the current device (0 for an invalid problem); problems for which it
+ *    exceeds MV_NOALLOC_SCRATCH_BYTES are rejected on the host with
+ *    MV_ERR_UNSUPPORTED before anything is launched, and mv_last_error()
+ *    then states the bytes needed.  On a 152-SM GB300 the 5440 x 48374 FP32
+ *    problem needs about 8 MiB in either layout.
+ *  - Device address: the array's host-side name is not a device address, so
+ *    the call looks the address up with the device current.  The first call
+ *    on a device does this set-up; make it before any stream capture.
+ *    Later calls made outside stream capture repeat the look-up, so they
+ *    stay right across a device reset (which reloads the library's module
+ *    at a new address).
  *  - Every call on a device shares the one array and leaves its contents
  *    behind; the call clears what must start at zero.  Calls whose work
  *    overlaps on the GPU (different streams, or different host threads)
@@ -522,6 +583,7 @@ int mv_gradient(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
  * ------------------------------------------------------------------------ */
 #define MV_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 
+size_t mv_gradient_noalloc_scratch_size(const mv_problem *P);
 int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
                         mv_stream_t stream);
 

@@ -207,7 +207,8 @@ static int center_args(const void *R, int64_t n, int64_t T, int64_t ldR, int out
         return MV_ERR_INVALID_ARG;
     if (dtype_size(out_dtype) == 0) return MV_ERR_INVALID_ARG;
     if (out_dtype == MV_FP8_E4M3 && d_row_scale == nullptr) return MV_ERR_INVALID_ARG;
-    if (tn && (ldL + kTile - 1) / kTile > 65535) return MV_ERR_UNSUPPORTED;
+    if (tn && (ldL + kTile - 1) / kTile > 65535)
+        return record_message(MV_ERR_UNSUPPORTED, "mv_center_factor: the transposed output needs ldL <= 65535 * 32");
     return MV_OK;
 }
 

@@ -300,7 +300,8 @@ int mv_countsketch(const void *d_L, int32_t dtype, int32_t layout, const float *
     if (layout != MV_LAYOUT_NT && layout != MV_LAYOUT_TN) return MV_ERR_INVALID_ARG;
     if (n < 1 || T < 1 || m < 1 || ldS < m) return MV_ERR_INVALID_ARG;
     if (ldL < (layout == MV_LAYOUT_TN ? n : T)) return MV_ERR_INVALID_ARG;
-    if (n >= (1LL << 31) || T >= (1LL << 31) || m >= (1LL << 30)) return MV_ERR_UNSUPPORTED;
+    if (n >= (1LL << 31) || T >= (1LL << 31) || m >= (1LL << 30))
+        return record_message(MV_ERR_UNSUPPORTED, "mv_countsketch: n and T must be below 2^31 and m below 2^30");
     const int es = dtype_size(dtype);
     if (((uintptr_t)d_L) % 16 != 0 || (ldL * es) % 16 != 0 || ((uintptr_t)d_L_sketch) % 16 != 0) return MV_ERR_INVALID_ARG;
     if (dtype == MV_FP8_E4M3 && d_row_scale == nullptr) return MV_ERR_INVALID_ARG;

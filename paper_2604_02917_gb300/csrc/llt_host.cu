@@ -117,7 +117,7 @@ LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device, bool tn) {
 int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
                const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s,
                float *z) {
-    if (!lp.ok) return MV_ERR_UNSUPPORTED;
+    if (!lp.ok) return record_message(MV_ERR_UNSUPPORTED, "fused pass: no cluster shape fits this n and T");
     CUtensorMap map;
     if (lp.tn)
         MV_TRY(make_map_lltt(&map, dt, L, n, T, ld, lp.box_rows));

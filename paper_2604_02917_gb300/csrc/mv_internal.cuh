@@ -18,9 +18,6 @@ constexpr int kWarp = 32;
 int record_cuda_error(cudaError_t e, const char *what, const char *file, int line);
 // Records a message for mv_last_error() and returns `status`.
 int record_message(int status, const char *msg);
-// Column-major C (m x n) = alpha A B^T + beta C (cuBLAS SGEMM, str.cu).
-int linalg_sgemm_nt(cudaStream_t s, int m, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
-                    float beta, float *C, int ldc);
 
 #define MV_CUDA_TRY(expr)                                                     \
     do {                                                                      \

@@ -311,7 +311,8 @@ static int sigma_check(const mv_problem *P) {
     if (P->dtype != MV_F32 && P->dtype != MV_BF16 && P->dtype != MV_FP8_E4M3) return MV_ERR_INVALID_ARG;
     if (P->layout != MV_LAYOUT_NT) return MV_ERR_INVALID_ARG;
     if (P->n < 1 || P->T < 1 || P->ld < P->T) return MV_ERR_INVALID_ARG;
-    if (P->n > 32768 || P->T >= (1LL << 31)) return MV_ERR_UNSUPPORTED;
+    if (P->n > 32768 || P->T >= (1LL << 31))
+        return record_message(MV_ERR_UNSUPPORTED, "mv_sigma_form: n must be <= 32768 and T below 2^31");
     const int es = dtype_size(P->dtype);
     if (((uintptr_t)P->L) % 16 != 0 || (P->ld * es) % 16 != 0) return MV_ERR_INVALID_ARG;
     if (P->dtype == MV_FP8_E4M3 && P->row_scale == nullptr) return MV_ERR_INVALID_ARG;

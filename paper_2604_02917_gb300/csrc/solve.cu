@@ -819,7 +819,8 @@ static int validate_problem(const mv_problem *P) {
         return MV_ERR_INVALID_ARG;
     if (P->layout == MV_LAYOUT_SIGMA && P->dtype != MV_F32) return MV_ERR_INVALID_ARG;
     if (P->n < 1 || P->T < 1 || P->ld < (P->layout == MV_LAYOUT_NT ? P->T : P->n)) return MV_ERR_INVALID_ARG;
-    if (P->n > kProjMaxN || P->T > (1LL << 31) - 1) return MV_ERR_UNSUPPORTED;
+    if (P->n > kProjMaxN || P->T > (1LL << 31) - 1)
+        return record_message(MV_ERR_UNSUPPORTED, "problem: n must be <= 32768 and T below 2^31");
     const int es = dtype_size(P->dtype);
     if (((uintptr_t)P->L) % 16 != 0 || (P->ld * es) % 16 != 0) return MV_ERR_INVALID_ARG;
     if (P->dtype == MV_FP8_E4M3 && P->row_scale == nullptr) return MV_ERR_INVALID_ARG;
@@ -2161,9 +2162,12 @@ static cudaError_t launch_adj_proj(int CL, const AdjArgs &a, cudaStream_t s) {
 
 struct BPlan {
     int K, C, ncp;
+    int W;                                                  // columns per piece segment of the dL GEMM operands
     size_t o_cp_state, o_cp_x, o_cp_y, o_cp_gx, o_cp_y32;   // checkpoints
     size_t o_x1, o_vy, o_zw, o_nu;                          // segment tape
-    size_t o_xbar, o_ybar, o_mubar, o_vbar, o_betas, o_k0, total;
+    size_t o_xbar, o_ybar, o_mubar, o_vbar, o_betas, o_k0;
+    size_t o_ga, o_gb;                                      // split operands of the dL update (BF16, K-major)
+    size_t total;
 };
 
 static BPlan make_bplan(const Plan &p, int K, int C) {
@@ -2192,8 +2196,30 @@ static BPlan make_bplan(const Plan &p, int K, int C) {
     b.o_vbar = take(8 * (size_t)p.n);
     b.o_betas = take(8 * (size_t)K);
     b.o_k0 = take(16);
+    b.W = (2 * C + kBK - 1) / kBK * kBK;
+    b.o_ga = take(2 * (size_t)p.n * kSplit3 * b.W);
+    b.o_gb = take(2 * (size_t)p.T * kSplit3 * b.W);
     b.total = off;
     return b;
+}
+
+// dL += -2 alpha sum_k (v_bar_k z_k^T + y_k w_k^T) over one segment as ONE
+// tcgen05 GEMM: with R = 2 len stacked vectors, A = [v_bar_k; y_k]^T (n x R)
+// and B = [z_k; w_k]^T (T x R) are split into three BF16 pieces each
+// (split3_t_kernel) and C = d_dL accumulates alpha A' B'^T (FP32-accurate).
+static int adjoint_dl_update(const BPlan &b, int n, int T, int len, const float *VY, const float *ZW, double alpha,
+                             void *ws, float *d_dL, int64_t ldD, cudaStream_t s) {
+    const int R = 2 * len, KW = kSplit3 * b.W;
+    __nv_bfloat16 *ga = at<__nv_bfloat16>(ws, b.o_ga), *gb = at<__nv_bfloat16>(ws, b.o_gb);
+    split3_t_kernel<<<dim3((n + 31) / 32, (b.W + 31) / 32), 256, 0, s>>>(VY, R, n, n, b.W, 0, ga, KW);
+    split3_t_kernel<<<dim3((T + 31) / 32, (b.W + 31) / 32), 256, 0, s>>>(ZW, R, T, T, b.W, 1, gb, KW);
+    CUtensorMap ta, tb;
+    MV_TRY(make_map_bf16(&ta, ga, n, KW, KW, kBM));
+    MV_TRY(make_map_bf16(&tb, gb, T, KW, KW, 256));
+    gemm_launch<256, kEpiAccF32>(ta, tb, n, T, KW, d_dL, ldD, nullptr, 0, s, 1, nullptr, nullptr,
+                                 (float)(-2.0 * alpha));
+    MV_CUDA_TRY(cudaGetLastError());
+    return MV_OK;
 }
 
 }  // namespace mv
@@ -2231,12 +2257,17 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     MV_TRY(check_ws(d_ws, ws_bytes, b.total));
     MV_TRY(set_kernel_attrs());
     MV_TRY(adj_attrs());
+    MV_TRY((gemm_set_attrs<256, kEpiAccF32>()));
     (void)cudaGetLastError();
     cudaStream_t s = (cudaStream_t)stream;
     void *ws = d_ws;
     SolveState *st = at<SolveState>(ws, p.o_state);
     float *y32 = at<float>(ws, p.o_y32);
     const int n = p.n, T = p.T, K = b.K, C = b.C;
+    {
+        int zero = 0;
+        MV_CUDA_TRY(cudaMemcpyToSymbolAsync(g_gemm_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+    }
 
     // ---- forward to x_K, checkpointing the state before iterations 0, C, 2C, ...
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
@@ -2396,16 +2427,20 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
             MV_TRY(reverse(s, len));
         }
         launches += len * (per_it + 4);
-        // dL += -2 alpha (V Z^T + Y W^T) over the segment: one FP32 GEMM with
-        // A = [z_k; w_k] rows (T x 2len col-major) and B = [v_bar_k; y_k] rows.
-        MV_TRY(linalg_sgemm_nt(s, T, n, 2 * len, (float)(-2.0 * alpha), ZW, T, VY, n, 1.0f, d_dL, (int)ldD));
-        MV_CUDA_TRY(cudaGetLastError());
+        // dL += -2 alpha (V Z^T + Y W^T) over the segment: one tcgen05 GEMM.
+        MV_TRY(adjoint_dl_update(b, n, T, len, VY, ZW, alpha, ws, d_dL, ldD, s));
     }
     MV_CUDA_TRY(cudaMemcpyAsync(d_dmu, mubar, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    int xerr = 0;
+    int xerr = 0, gerr = 0;
     MV_CUDA_TRY(cudaMemcpyAsync(&xerr, at<int>(ws, p.o_err), sizeof(int), cudaMemcpyDeviceToHost, s));
+    MV_CUDA_TRY(cudaMemcpyFromSymbolAsync(&gerr, g_gemm_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
     MV_CUDA_TRY(cudaStreamSynchronize(s));
     MV_CUDA_TRY(cudaGetLastError());
+    if (gerr != 0) {
+        *h_info = mv_solve_info{};
+        h_info->status = record_message(MV_ERR_TIMEOUT, "mv_npga_backward: the dL GEMM pipeline wait timed out");
+        return h_info->status;
+    }
     if (xerr != 0) {
         char msg[96];
         snprintf(msg, sizeof(msg), "mv_npga_backward: a bounded wait of the fused pass timed out (code %d)", xerr);
@@ -2546,7 +2581,8 @@ static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo,
         max_ncols = std::max(max_ncols, p.n_cols);
         Lo->plans.push_back(p);
     }
-    if (ntt >= (1LL << 31) || nnt >= (1LL << 31)) return MV_ERR_UNSUPPORTED;
+    if (ntt >= (1LL << 31) || nnt >= (1LL << 31))
+        return record_message(MV_ERR_UNSUPPORTED, "batch: the tile list exceeds 2^31 entries");
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -2972,30 +3008,51 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[MV_NOALLOC_SCRA
 static std::mutex g_noalloc_mu;
 static void *g_noalloc_addr[128];   // device address of the array, per device ordinal
 
-// Set-up, once per device, with that device current: the host-side name of
-// the array is only a stand-in, so its device address is looked up here.
-static int noalloc_scratch(void **out) {
+// The host-side name of the array is only a stand-in, so its device address
+// is looked up with the device current.  A call outside stream capture looks
+// it up every time (cheap once the module is loaded), so the address stays
+// right after a device reset, which reloads the module at a new address.
+// Inside a capture no look-up is made and the device's last address is used.
+static int noalloc_scratch(cudaStream_t s, void **out) {
     int dev = 0;
     MV_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) return record_message(MV_ERR_UNSUPPORTED, "mv_gradient_noalloc: device ordinal >= 128");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    MV_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_addr[dev] == nullptr) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         MV_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         g_noalloc_addr[dev] = p;
+    } else if (g_noalloc_addr[dev] == nullptr) {
+        return record_message(MV_ERR_UNSUPPORTED,
+                              "mv_gradient_noalloc: the first call on a device must come before stream capture");
     }
     *out = g_noalloc_addr[dev];
     return MV_OK;
 }
 
+// The scratch this call needs: the plan of the two-pass GEMV path (its row
+// splits follow the device's SM count, so the figure is per device).
+static int noalloc_plan(const mv_problem *P, Plan *out) {
+    MV_TRY(validate_problem(P));
+    if (is_sigma(P)) return record_message(MV_ERR_UNSUPPORTED, "mv_gradient_noalloc: explicit Sigma is not supported");
+    *out = make_plan(P->dtype, P->n, P->T, P->ld, 0, false, is_tn(P));
+    return MV_OK;
+}
+
 }  // namespace mv
+
+extern "C" size_t mv_gradient_noalloc_scratch_size(const mv_problem *P) {
+    Plan p{};
+    return noalloc_plan(P, &p) == MV_OK ? p.total : 0;
+}
 
 extern "C" int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
                                    mv_stream_t stream) {
-    MV_TRY(validate_problem(P));
+    Plan p{};
+    MV_TRY(noalloc_plan(P, &p));
     if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
-    if (is_sigma(P)) return record_message(MV_ERR_UNSUPPORTED, "mv_gradient_noalloc: explicit Sigma is not supported");
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, false, is_tn(P));
     if (p.total > MV_NOALLOC_SCRATCH_BYTES) {
         char msg[200];
         snprintf(msg, sizeof(msg),
@@ -3003,11 +3060,11 @@ extern "C" int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float
                  p.total, (size_t)MV_NOALLOC_SCRATCH_BYTES);
         return record_message(MV_ERR_UNSUPPORTED, msg);
     }
+    cudaStream_t s = (cudaStream_t)stream;
     void *ws = nullptr;
-    MV_TRY(noalloc_scratch(&ws));
+    MV_TRY(noalloc_scratch(s, &ws));
     MV_TRY(set_kernel_attrs());
     (void)cudaGetLastError();
-    cudaStream_t s = (cudaStream_t)stream;
     float *y32 = at<float>(ws, p.o_y32);
     double *lz = at<double>(ws, p.o_gy);
     // The array keeps the previous call's contents: the gemv tickets must start at zero.

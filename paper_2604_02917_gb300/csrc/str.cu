@@ -28,8 +28,6 @@ typedef int (*fn_cublasCreate)(void **);
 typedef int (*fn_cublasSetStream)(void *, cudaStream_t);
 typedef int (*fn_cublasDsyrk)(void *, int, int, int, int, const double *, const double *, int, const double *,
                               double *, int);
-typedef int (*fn_cublasSgemm)(void *, int, int, int, int, int, const float *, const float *, int, const float *, int,
-                              const float *, float *, int);
 typedef int (*fn_cusolverCreate)(void **);
 typedef int (*fn_cusolverSetStream)(void *, cudaStream_t);
 typedef int (*fn_syevd_bs)(void *, int, int, int, const double *, int, const double *, int *);
@@ -42,7 +40,6 @@ struct Linalg {
     void *hb = nullptr, *hs = nullptr;
     fn_cublasSetStream b_set_stream = nullptr;
     fn_cublasDsyrk dsyrk = nullptr;
-    fn_cublasSgemm sgemm = nullptr;
     fn_cusolverSetStream s_set_stream = nullptr;
     fn_syevd_bs syevd_bs = nullptr;
     fn_syevd syevd = nullptr;
@@ -70,30 +67,17 @@ static Linalg *linalg() {
         auto bcreate = (fn_cublasCreate)dlsym(lb, "cublasCreate_v2");
         L.b_set_stream = (fn_cublasSetStream)dlsym(lb, "cublasSetStream_v2");
         L.dsyrk = (fn_cublasDsyrk)dlsym(lb, "cublasDsyrk_v2");
-        L.sgemm = (fn_cublasSgemm)dlsym(lb, "cublasSgemm_v2");
         auto screate = (fn_cusolverCreate)dlsym(ls, "cusolverDnCreate");
         L.s_set_stream = (fn_cusolverSetStream)dlsym(ls, "cusolverDnSetStream");
         L.syevd_bs = (fn_syevd_bs)dlsym(ls, "cusolverDnDsyevd_bufferSize");
         L.syevd = (fn_syevd)dlsym(ls, "cusolverDnDsyevd");
-        if (!bcreate || !L.b_set_stream || !L.dsyrk || !L.sgemm || !screate || !L.s_set_stream || !L.syevd_bs ||
+        if (!bcreate || !L.b_set_stream || !L.dsyrk || !screate || !L.s_set_stream || !L.syevd_bs ||
             !L.syevd)
             return;
         if (bcreate(&L.hb) != 0 || screate(&L.hs) != 0) return;
         L.ok = true;
     });
     return L.ok ? &L : nullptr;
-}
-
-// Column-major C (m x n) = alpha A B^T + beta C with A m x k, B n x k
-// (cuBLAS SGEMM; a plain library GEMM used by the adjoint's dL update).
-int linalg_sgemm_nt(cudaStream_t s, int m, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
-                    float beta, float *C, int ldc) {
-    Linalg *L = linalg();
-    if (!L) return record_message(MV_ERR_UNSUPPORTED, "cuBLAS not found");
-    if (L->b_set_stream(L->hb, s) != 0) return record_message(MV_ERR_CUDA, "cublasSetStream failed");
-    if (L->sgemm(L->hb, 0, kOpT, m, n, k, &alpha, A, lda, B, ldb, &beta, C, ldc) != 0)
-        return record_message(MV_ERR_CUDA, "cublasSgemm failed");
-    return MV_OK;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -288,12 +272,57 @@ int mv_str_truncate_knee(const float *d_L_sketch, int64_t n, int64_t m, int64_t 
 }
 
 
-int mv_sketch_str(const void *d_L, int64_t n, int64_t T, int64_t ldL, const void *d_Phi_t, int64_t m, int64_t ldP,
-                  int64_t k, double gamma, double trace_sigma, float *d_L_sketch, int64_t ldS, float *d_L_eff,
-                  int64_t ldE, double *d_sigma, double *h_gamma_out, void *d_ws, size_t ws_bytes, mv_stream_t stream) {
-    MV_TRY(mv_sketch(d_L, n, T, ldL, d_Phi_t, m, ldP, d_L_sketch, ldS, stream));
-    return mv_str_truncate(d_L_sketch, n, m, ldS, k, gamma, trace_sigma, d_L_eff, ldE, d_sigma, h_gamma_out, d_ws,
-                           ws_bytes, stream);
+// Workspace of the whole STR build: tilde L (when the caller passes none),
+// then either the sketch stage (Phi^T and the BF16 copy of L) or the
+// truncation, which reuse the same bytes one after the other.
+struct SkPlan {
+    int64_t ldP, ldS;
+    size_t o_ls, o_phi, o_conv, o_str, total;
+};
+
+static SkPlan sk_plan(int dtype, int64_t n, int64_t T, int64_t m, int64_t k, bool own_ls) {
+    SkPlan p{};
+    p.ldP = (T + 7) / 8 * 8;
+    p.ldS = (m + 3) / 4 * 4;
+    size_t off = 0;
+    p.o_ls = off;
+    if (own_ls) off = align_up(4 * (size_t)n * p.ldS, 256);
+    p.o_phi = off;
+    p.o_conv = align_up(p.o_phi + 2 * (size_t)m * p.ldP, 256);
+    const size_t sketch_end = p.o_conv + mv_sketch_workspace_size(dtype, n, T);
+    p.o_str = off;
+    const size_t str_end = p.o_str + mv_str_workspace_size(n, m, k);
+    p.total = align_up(sketch_end > str_end ? sketch_end : str_end, 256);
+    return p;
+}
+
+size_t mv_sketch_str_workspace_size(int32_t dtype, int64_t n, int64_t T, int64_t m, int64_t k, int32_t own_sketch) {
+    if (n < 1 || T < 1 || m < 1 || k < 1 || k > n || mv_str_workspace_size(n, m, k) == 0) return 0;
+    if (dtype != MV_F32 && dtype != MV_BF16 && dtype != MV_FP8_E4M3) return 0;
+    return sk_plan(dtype, n, T, m, k, own_sketch != 0).total;
+}
+
+int mv_sketch_str(const void *d_L, int32_t dtype, const float *d_row_scale, int64_t n, int64_t T, int64_t ldL,
+                  int64_t m, uint64_t seed, int64_t k, double gamma, double trace_sigma, float *d_L_sketch,
+                  int64_t ldS, float *d_L_eff, int64_t ldE, double *d_sigma, double *h_gamma_out, void *d_ws,
+                  size_t ws_bytes, mv_stream_t stream) {
+    if (!d_L || !d_L_eff || !d_sigma) return MV_ERR_INVALID_ARG;
+    if (dtype != MV_F32 && dtype != MV_BF16 && dtype != MV_FP8_E4M3) return MV_ERR_INVALID_ARG;
+    if (n < 1 || T < 1 || m < 1 || k < 1 || k > n || ldL < T || ldE < k) return MV_ERR_INVALID_ARG;
+    if (d_L_sketch != nullptr && ldS < m) return MV_ERR_INVALID_ARG;
+    const size_t need = mv_sketch_str_workspace_size(dtype, n, T, m, k, d_L_sketch == nullptr ? 1 : 0);
+    if (need == 0) return MV_ERR_INVALID_ARG;
+    if (d_ws == nullptr || ws_bytes < need || ((uintptr_t)d_ws) % 256) return MV_ERR_WORKSPACE;
+    const SkPlan p = sk_plan(dtype, n, T, m, k, d_L_sketch == nullptr);
+    char *ws = reinterpret_cast<char *>(d_ws);
+    float *Ls = d_L_sketch ? d_L_sketch : reinterpret_cast<float *>(ws + p.o_ls);
+    const int64_t lds = d_L_sketch ? ldS : p.ldS;
+    // (1) Phi^T drawn from the seed, (2) tilde L = L Phi, (3) truncation + ridge
+    MV_TRY(mv_gaussian_sketch(seed, m, T, ws + p.o_phi, p.ldP, stream));
+    MV_TRY(mv_sketch_dtype(d_L, dtype, d_row_scale, n, T, ldL, ws + p.o_phi, m, p.ldP, Ls, lds, ws + p.o_conv,
+                           need - p.o_conv, stream));
+    return mv_str_truncate(Ls, n, m, lds, k, gamma, trace_sigma, d_L_eff, ldE, d_sigma, h_gamma_out, ws + p.o_str,
+                           need - p.o_str, stream);
 }
 
 }  // extern "C"

@@ -36,7 +36,9 @@ EXPORTS = [
     "mv_sketch_str", "mv_frontier_workspace_size", "mv_npga_solve_frontier", "mv_backward_workspace_size",
     "mv_npga_backward", "mv_batch_workspace_size", "mv_npga_solve_batch", "mv_center_host_workspace_size",
     "mv_center_factor_host", "mv_batch_tiles", "mv_str_truncate_knee", "mv_sigma_workspace_size",
-    "mv_sigma_form", "mv_countsketch_workspace_size", "mv_countsketch",
+    "mv_sigma_form", "mv_countsketch_workspace_size", "mv_countsketch", "mv_gradient_noalloc_scratch_size",
+    "mv_sketch_workspace_size", "mv_sketch_dtype", "mv_gaussian_sketch", "mv_countsketch_draw",
+    "mv_sketch_str_workspace_size",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -142,9 +144,20 @@ def lib():
         L.mv_str_truncate_knee.restype = i32
         L.mv_str_truncate_knee.argtypes = [vp, i64, i64, i64, dbl, dbl, i64, dbl, dbl, dbl, vp, i64, vp,
                                            C.POINTER(C.c_int64), C.POINTER(C.c_double), vp, sz, vp]
+        u64 = C.c_uint64
         L.mv_sketch_str.restype = i32
-        L.mv_sketch_str.argtypes = [vp, i64, i64, i64, vp, i64, i64, i64, dbl, dbl, vp, i64, vp, i64, vp,
+        L.mv_sketch_str.argtypes = [vp, i32, vp, i64, i64, i64, i64, u64, i64, dbl, dbl, vp, i64, vp, i64, vp,
                                     C.POINTER(C.c_double), vp, sz, vp]
+        L.mv_sketch_str_workspace_size.restype = sz
+        L.mv_sketch_str_workspace_size.argtypes = [i32, i64, i64, i64, i64, i32]
+        L.mv_sketch_workspace_size.restype = sz
+        L.mv_sketch_workspace_size.argtypes = [i32, i64, i64]
+        L.mv_sketch_dtype.restype = i32
+        L.mv_sketch_dtype.argtypes = [vp, i32, vp, i64, i64, i64, vp, i64, i64, vp, i64, vp, sz, vp]
+        L.mv_gaussian_sketch.restype = i32
+        L.mv_gaussian_sketch.argtypes = [u64, i64, i64, vp, i64, vp]
+        L.mv_countsketch_draw.restype = i32
+        L.mv_countsketch_draw.argtypes = [u64, i64, i64, vp, vp, vp]
         L.mv_frontier_workspace_size.restype = sz
         L.mv_frontier_workspace_size.argtypes = [C.POINTER(Problem), i64]
         L.mv_npga_solve_frontier.restype = i32
@@ -164,6 +177,8 @@ def lib():
         L.mv_sketch.argtypes = [vp, i64, i64, i64, vp, i64, i64, vp, i64, vp]
         L.mv_gradient_noalloc.restype = i32
         L.mv_gradient_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp, vp]
+        L.mv_gradient_noalloc_scratch_size.restype = sz
+        L.mv_gradient_noalloc_scratch_size.argtypes = [C.POINTER(Problem)]
         _lib = L
     return _lib
 
@@ -345,6 +360,16 @@ def solve_opts(**kw) -> SolveOpts:
     return o
 
 
+def _check_y(y: torch.Tensor, n: int, device) -> None:
+    """The gradient calls read y as n FP64 values on L's device."""
+    if not isinstance(y, torch.Tensor) or y.dtype != torch.float64:
+        raise ValueError("y must be a float64 tensor")
+    if y.device != torch.device(device):
+        raise ValueError(f"y is on {y.device}; L is on {device}")
+    if y.dim() != 1 or y.numel() != n or not y.is_contiguous():
+        raise ValueError(f"y must be a contiguous vector of n = {n} entries (got shape {tuple(y.shape)})")
+
+
 class Solver:
     """Holds a problem, its workspace and the device solution buffer.
 
@@ -376,11 +401,10 @@ class Solver:
     def gradient(self, y: torch.Tensor, with_z: bool = True):
         """(z, g); with ``with_z=False`` z is None and g comes from the fused
         single pass over L where that applies."""
-        if y.numel() < self.problem.n:
-            raise ValueError(f"y has {y.numel()} entries; the problem has n = {self.problem.n}")
+        _check_y(y, self.problem.n, self.ws.device)
         with_z = with_z and self.problem.layout != MV_LAYOUT_SIGMA
         z = torch.empty(self.problem.T, dtype=torch.float32, device=y.device) if with_z else None
-        g = torch.empty_like(y)
+        g = torch.empty(self.problem.n, dtype=torch.float64, device=y.device)
         _check(lib().mv_gradient(C.byref(self.problem), _ptr(y), _ptr(z) if with_z else None, _ptr(g),
                                  _ptr(self.ws), self.ws.numel(), _stream()), "mv_gradient")
         return z, g
@@ -422,21 +446,33 @@ def npga_solve(L, mu, R_target, T, gamma=0.0, dtype="f32", row_scale=None, mode=
 def gradient(L, y, T, gamma=0.0, dtype="f32", row_scale=None, with_z=True, layout="nt"):
     """(z, g) with z = L^T y (FP32) and g = 2 L z + 2 gamma y (FP64).
     ``with_z=False``: z is None and g uses the fused single pass where it applies."""
-    mu = torch.zeros(y.shape[0], dtype=torch.float64, device=L.device)
+    n = L.shape[0] if layout == "nt" else y.shape[0]
+    mu = torch.zeros(n, dtype=torch.float64, device=L.device)
     s = Solver(L, mu, 0.0, T, gamma, dtype, row_scale, layout=layout)
     return s.gradient(y, with_z)
 
 
-def gradient_noalloc(L, y, T, gamma=0.0, dtype="f32", row_scale=None, layout="nt"):
+def gradient_noalloc(L, y, T, gamma=0.0, dtype="f32", row_scale=None, layout="nt", with_z=True):
     """(z, g) as ``gradient`` but through mv_gradient_noalloc: the library uses
     its fixed scratch array instead of a workspace (outputs still come from
     PyTorch here).  Calls overlapping on the GPU race on that array."""
-    mu = torch.zeros(y.shape[0], dtype=torch.float64, device=L.device)
+    n = L.shape[0] if layout == "nt" else y.shape[0]
+    mu = torch.zeros(n, dtype=torch.float64, device=L.device)
     p = make_problem(L, mu, 0.0, T, gamma, dtype, row_scale, layout=layout)
-    z = torch.empty(T, dtype=torch.float32, device=y.device)
-    g = torch.empty_like(y)
+    _check_y(y, p.n, L.device)
+    z = torch.empty(T, dtype=torch.float32, device=y.device) if with_z else None
+    g = torch.empty(p.n, dtype=torch.float64, device=y.device)
     _check(lib().mv_gradient_noalloc(C.byref(p), _ptr(y), _ptr(z), _ptr(g), _stream()), "mv_gradient_noalloc")
     return z, g
+
+
+def gradient_noalloc_scratch_size(L, T, dtype="f32", row_scale=None, layout="nt", n=None) -> int:
+    """Bytes of the library's fixed array that mv_gradient_noalloc needs for
+    this problem on the current device (0 if the problem is invalid)."""
+    n = L.shape[0] if layout == "nt" else int(n)
+    mu = torch.zeros(n, dtype=torch.float64, device=L.device)
+    p = make_problem(L, mu, 0.0, T, 0.0, dtype, row_scale, layout=layout)
+    return int(lib().mv_gradient_noalloc_scratch_size(C.byref(p)))
 
 
 def sketch(L_bf16: torch.Tensor, T: int, Phi_t: torch.Tensor) -> torch.Tensor:
@@ -452,6 +488,74 @@ def sketch(L_bf16: torch.Tensor, T: int, Phi_t: torch.Tensor) -> torch.Tensor:
     _check(lib().mv_sketch(_ptr(L_bf16), n, T, L_bf16.stride(0), _ptr(Phi_t), m, Phi_t.stride(0), _ptr(out), ldS,
                            _stream()), "mv_sketch")
     return out[:, :m]
+
+
+def sketch_dtype(L: torch.Tensor, T: int, Phi_t: torch.Tensor, dtype: str = "f32",
+                 row_scale: torch.Tensor | None = None) -> torch.Tensor:
+    """tilde L = L Phi for an n x ld factor stored as "f32", "bf16" or "fp8"
+    (mv_sketch_dtype); Phi_t is m x ldP BF16.  Returns n x m FP32."""
+    assert Phi_t.dtype == torch.bfloat16
+    dt = DTYPES[dtype]
+    n, m = L.shape[0], Phi_t.shape[0]
+    err = shape_error("nt", dtype, L.shape, L.element_size(), n, T, n,
+                      None if row_scale is None else row_scale.numel())
+    if err is None and Phi_t.shape[1] < T:
+        err = f"Phi_t has {Phi_t.shape[1]} columns; T = {T}"
+    if err is not None:
+        raise ValueError(err)
+    ws = _workspace(lib().mv_sketch_workspace_size(dt, n, T), L.device)
+    ldS = (m + 3) // 4 * 4
+    out = torch.empty((n, ldS), dtype=torch.float32, device=L.device)
+    _check(lib().mv_sketch_dtype(_ptr(L), dt, _ptr(row_scale), n, T, L.stride(0), _ptr(Phi_t), m, Phi_t.stride(0),
+                                 _ptr(out), ldS, _ptr(ws), ws.numel(), _stream()), "mv_sketch_dtype")
+    return out[:, :m]
+
+
+def gaussian_sketch(seed: int, m: int, T: int, device=None) -> torch.Tensor:
+    """Phi^T (m x ldP BF16, ldP = T rounded up to 8) drawn on the device from
+    ``seed`` (mv_gaussian_sketch: Philox4x32-10 + Box--Muller, N(0, 1/m))."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    ldP = (T + 7) // 8 * 8
+    out = torch.empty((m, ldP), dtype=torch.bfloat16, device=dev)
+    _check(lib().mv_gaussian_sketch(int(seed), m, T, _ptr(out), ldP, _stream()), "mv_gaussian_sketch")
+    return out
+
+
+def countsketch_draw(seed: int, T: int, m: int, device=None):
+    """(h int32 [T], sign int8 [T]) drawn on the device from ``seed`` (mv_countsketch_draw)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    h = torch.empty(T, dtype=torch.int32, device=dev)
+    sg = torch.empty(T, dtype=torch.int8, device=dev)
+    _check(lib().mv_countsketch_draw(int(seed), T, m, _ptr(h), _ptr(sg), _stream()), "mv_countsketch_draw")
+    return h, sg
+
+
+def sketch_str(L: torch.Tensor, T: int, m: int, seed: int, k: int, dtype: str = "bf16",
+               row_scale: torch.Tensor | None = None, gamma: float = -1.0, trace_sigma: float = 0.0,
+               keep_sketch: bool = True):
+    """The whole STR build from a seed (mv_sketch_str): returns (L_eff n x k
+    FP32, sigma k FP64, gamma, tilde L n x m FP32 or None)."""
+    dt = DTYPES[dtype]
+    n = L.shape[0]
+    err = shape_error("nt", dtype, L.shape, L.element_size(), n, T, n,
+                      None if row_scale is None else row_scale.numel())
+    if err is not None:
+        raise ValueError(err)
+    nb = lib().mv_sketch_str_workspace_size(dt, n, T, m, k, 0 if keep_sketch else 1)
+    if nb == 0:
+        raise MvError(MV_ERR_INVALID_ARG, "mv_sketch_str_workspace_size")
+    dev = L.device
+    ws = _workspace(nb, dev)
+    ldS = (m + 3) // 4 * 4
+    Ls = torch.empty((n, ldS), dtype=torch.float32, device=dev) if keep_sketch else None
+    ldE = (k + 3) // 4 * 4
+    L_eff = torch.zeros((n, ldE), dtype=torch.float32, device=dev)
+    sigma = torch.empty(k, dtype=torch.float64, device=dev)
+    g = C.c_double(0.0)
+    _check(lib().mv_sketch_str(_ptr(L), dt, _ptr(row_scale), n, T, L.stride(0), m, int(seed), k, float(gamma),
+                               float(trace_sigma), _ptr(Ls), ldS, _ptr(L_eff), ldE, _ptr(sigma), C.byref(g),
+                               _ptr(ws), ws.numel(), _stream()), "mv_sketch_str")
+    return L_eff[:, :k], sigma, g.value, (Ls[:, :m] if keep_sketch else None)
 
 
 def bf16_rows(A, ld=None) -> torch.Tensor:

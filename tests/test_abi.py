@@ -200,3 +200,24 @@ def test_host_side_argument_errors_sketches_and_sigma(mvmod):
     assert knee(kappa=0.5) == E
     assert knee(kmax=11) == E
     assert knee(n=1) == E
+
+
+def test_unsupported_status_carries_its_own_message(mvmod):
+    """Every MV_ERR_UNSUPPORTED return records its own reason, so the message
+    read after it never belongs to an earlier, unrelated call."""
+    lib = mvmod.lib()
+    # 1: a sketch dimension beyond 2^31 (checked before any launch)
+    st = lib.mv_sketch(C.c_void_p(4096), 1 << 31, 8, 8, C.c_void_p(4096), 8, 8, C.c_void_p(4096), 8, None)
+    assert st == mvmod.MV_ERR_UNSUPPORTED
+    assert "mv_sketch" in lib.mv_last_error().decode()
+    # 2: then a problem with n above the projector's limit: its own message, not the sketch's
+    p = mvmod.Problem()
+    p.L, p.mu, p.n, p.T, p.ld, p.dtype = 4096, 4096, 40000, 64, 64, mvmod.MV_F32
+    st = lib.mv_gradient_noalloc(C.byref(p), C.c_void_p(4096), None, C.c_void_p(4096), None)
+    assert st == mvmod.MV_ERR_UNSUPPORTED
+    msg = lib.mv_last_error().decode()
+    assert "n must be <= 32768" in msg and "mv_sketch" not in msg
+    with pytest.raises(mvmod.MvError) as e:
+        mvmod._check(st, "mv_gradient_noalloc")
+    assert "n must be <= 32768" in str(e.value)
+    assert lib.mv_gradient_noalloc_scratch_size(C.byref(p)) == 0

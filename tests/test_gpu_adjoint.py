@@ -3,7 +3,23 @@ FP64 oracle adjoint on the same FP32 factor, step and start, and against
 central finite differences of the oracle's FP64 forward (h = 1e-4 times the
 RMS of each variable, 32 directions; directions whose +-h forwards change an
 active set are kinks and are skipped).  The loss is the negative Sharpe-like
-ratio of the returned portfolio on a held-out block of periods."""
+ratio of the returned portfolio on a held-out block of periods.
+
+Tolerances.  d mu and d L are compared element by element, relative to the
+largest entry of the oracle's gradient.  Every product of the GPU's forward
+and reverse sweeps is one pass over L with FP32 terms and compensated
+per-row sums, good to a few units of 2^-24 relative; the reverse recursion
+applies projectors (the projection's Jacobian) and the contraction
+I - 2 alpha L L^T to those errors, so they do not grow with K; the dL
+update is a GEMM over three-piece BF16 splits (FP32-accurate).  The errors
+therefore stay at a few 1e-7 of the largest entry (2.6e-7 was the largest
+measured at K = 100, 4.4e-7 at K = 500); ADJ_TOL = 5e-6 leaves a factor of
+ten.  The directional derivative sums n T products of d L with a random
+direction, whose cancellation magnifies the relative error (up to 9e-6
+measured); the finite-difference check, whose own truncation error
+(h = 1e-4 of each variable's RMS: O(h^2) = 1e-8) and rounding error
+(1e-16 / h of the loss) are far smaller, uses FD_TOL = 1e-4.
+"""
 import numpy as np
 import pytest
 
@@ -15,6 +31,14 @@ from oracle.npga import initial_point
 from oracle import adjoint
 
 pytestmark = pytest.mark.gpu
+
+ADJ_TOL = 5e-6
+FD_TOL = 1e-4
+
+
+def max_rel(a, ref):
+    """Largest element-wise error relative to the largest entry of ref."""
+    return float(np.max(np.abs(a - ref)) / np.max(np.abs(ref)))
 
 
 @pytest.fixture(scope="module")
@@ -54,14 +78,16 @@ def test_adjoint_parity_and_finite_differences(mv, K, C, mode):
     mub_o, Lb_o = adjoint.backward(L64, 0.0, mu_o, alpha, tape, betas, gx)
     dmu = dmu.cpu().numpy()
     dL = dL[:, :T].double().cpu().numpy()
-    assert np.linalg.norm(dmu - mub_o) <= 1e-3 * np.linalg.norm(mub_o)
-    assert np.linalg.norm(dL - Lb_o) <= 1e-3 * np.linalg.norm(Lb_o)
+    e_mu, e_L = max_rel(dmu, mub_o), max_rel(dL, Lb_o)
+    print(f"adjoint K={K} C={C} {mode}: d mu {e_mu:.2e}, d L {e_L:.2e} (element-wise, of max)")
+    assert e_mu <= ADJ_TOL and e_L <= ADJ_TOL
     # central differences of the FP64 forward on random directions
     loss = lambda xx: adjoint.sharpe_loss(xx, mu_t, L_t)
     rng = np.random.default_rng(3)
     h = 1e-4
     rms_mu, rms_L = np.sqrt(np.mean(mu_o ** 2)), np.sqrt(np.mean(L64 ** 2))
     checked = 0
+    worst = 0.0
     for _ in range(32):
         dm = rng.standard_normal(n)
         dm *= rms_mu / np.linalg.norm(dm)
@@ -75,8 +101,10 @@ def test_adjoint_parity_and_finite_differences(mv, K, C, mode):
             continue
         fd = (loss(tp[-1]["x1"]) - loss(tm[-1]["x1"])) / (2 * h)
         an = dmu @ dm + np.sum(dL * dD)
-        assert an == pytest.approx(fd, rel=2e-3, abs=1e-6 * abs(fd) + 1e-10)
+        worst = max(worst, abs(an - fd) / abs(fd))
+        assert an == pytest.approx(fd, rel=FD_TOL, abs=1e-10)
         checked += 1
+    print(f"finite differences: {checked} directions, worst relative error {worst:.2e}")
     assert checked >= 16
 
 
@@ -110,6 +138,7 @@ def test_adjoint_full_config(mv):
     gx = adjoint.sharpe_loss_grad(xo, mu_t, L_t)
     dmu, dL, _ = mv.npga_backward(L, mu, Rt, T, torch.from_numpy(gx).cuda(), K, checkpoint_every=50)
     mub_o, Lb_o = adjoint.backward(L64, 0.0, mu_o, alpha, tape, betas, gx)
-    assert np.linalg.norm(dmu.cpu().numpy() - mub_o) <= 1e-3 * np.linalg.norm(mub_o)
     dL = dL[:, :T].double().cpu().numpy()
-    assert np.linalg.norm(dL - Lb_o) <= 1e-3 * np.linalg.norm(Lb_o)
+    e_mu, e_L = max_rel(dmu.cpu().numpy(), mub_o), max_rel(dL, Lb_o)
+    print(f"adjoint 2000x10000 K=500: d mu {e_mu:.2e}, d L {e_L:.2e} (element-wise, of max)")
+    assert e_mu <= ADJ_TOL and e_L <= ADJ_TOL

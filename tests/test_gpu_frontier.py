@@ -76,3 +76,46 @@ def test_frontier_fp8_parity(mv, model, nt):
         ref = oracle_opt(L8, mu_o, targets[b])
         assert np.max(np.abs(X[b] - ref.x)) <= 1e-4
         assert (f[b] - ref.f) / ref.f <= 1e-5
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dt", ["bf16", "fp8"])
+def test_frontier_full_shape_against_oracle(mv, dt):
+    """The 64-target frontier at 5440 x 48374, launched as the benchmark
+    launches it (targets evenly spaced between the 10th and 90th percentiles
+    of mu, KKT 1e-6).  Three targets -- the 10th percentile, the middle of the
+    grid and the 90th percentile -- are checked against the oracle's optimum
+    on the same low-precision matrix: Algorithm 1 in FP64 on Sigma = L L^T
+    from Pi_F(1/n 1) to a KKT residual of 1e-10.  Tolerances as for the
+    single solves: x within 1e-4 (infinity norm), objective within 1e-5
+    relative, and f(x) - f* within the Frank--Wolfe gap at x."""
+    from oracle.npga import fw_gap, npga_sigma, objective_sigma, power_norm2_sigma, sigma_from_factor
+    m = CFG_FULL
+    R = factor_returns(m, np.float32)
+    Lq_d, rs, mu, _ = mv.center_factor(torch.from_numpy(R).cuda(), dt)
+    mu_o = center_factor(R.astype(np.float64))[0]
+    del R
+    targets = np.linspace(np.percentile(mu_o, 10), np.percentile(mu_o, 90), 64)
+    fs = mv.FrontierSolver(Lq_d, mu, targets, m.T, eps=1e-6, dtype=dt, row_scale=rs)
+    X, infos = fs.solve()
+    X = X.cpu().numpy()
+    assert all(i["converged"] == 1 for i in infos)
+    if dt == "bf16":
+        Lq = Lq_d[:, :m.T].float().double().cpu().numpy()
+    else:
+        q = Lq_d[:, :m.T].cpu().view(torch.float8_e4m3fn).float().double().numpy()
+        Lq = q * rs.double().cpu().numpy()[:, None]
+    del fs, Lq_d
+    Sig = sigma_from_factor(Lq)
+    alpha = 1.0 / (2.0 * power_norm2_sigma(Sig, power_start(m.n), 100) * (1 + 1e-3))
+    for b in (0, 32, 63):
+        ref = npga_sigma(Sig, 0.0, mu_o, targets[b], initial_point(mu_o, targets[b]), alpha, eps=1e-10,
+                         max_iter=50000)
+        assert ref.converged
+        x = X[b]
+        assert x.min() >= 0 and abs(x.sum() - 1) < 1e-12 and mu_o @ x >= targets[b] - 1e-15
+        f = objective_sigma(Sig, 0.0, x)
+        assert np.max(np.abs(x - ref.x)) <= 1e-4
+        assert (f - ref.f) / ref.f <= 1e-5
+        assert -1e-14 * ref.f <= f - ref.f <= fw_gap(Lq, 0.0, mu_o, targets[b], x) + 1e-12 * ref.f
+        assert infos[b]["objective"] == pytest.approx(f, rel=1e-4)

@@ -535,3 +535,74 @@ def test_product_at_x_by_linearity_along_the_iterates():
         t_new = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * t * t))
         beta_prev, t = (t - 1.0) / t_new, t_new
     assert beta_prev > 0.5                      # momentum well away from 0 by the end
+
+
+# ------------------------------------------------------------------ counter-based draws (oracle/rng.py)
+def test_philox_known_answers():
+    """Philox4x32-10 known-answer vectors published with the generator
+    (Salmon et al., SC'11; the Random123 known-answer tests): zero counter
+    and key, all-ones counter and key, and the pi-digit counter and key."""
+    from oracle.rng import philox4x32_10
+    cases = [((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+             ((0xFFFFFFFF,) * 4, (0xFFFFFFFF, 0xFFFFFFFF), (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+             ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+              (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1))]
+    for ctr, key, want in cases:
+        got = tuple(int(w) for w in philox4x32_10(*ctr, key))
+        assert got == want
+
+
+def test_gaussian_sketch_draw_is_a_jl_gaussian():
+    """Entries of Phi are i.i.d. N(0, 1/s) (Sec. 2.3): mean, variance and the
+    normal law (Kolmogorov--Smirnov), E[Phi Phi^T] = I over the s columns, one
+    seed gives one matrix (any subset of rows reproduces it) and another
+    seed another one."""
+    from scipy import stats
+    from oracle.rng import gaussian_sketch_t
+    s, T = 256, 4003
+    P = gaussian_sketch_t(11, s, T)
+    assert P.shape == (s, T) and np.all(np.isfinite(P))
+    z = P.reshape(-1) * np.sqrt(s)
+    N = z.size
+    assert abs(z.mean()) < 5.0 / np.sqrt(N)
+    assert abs(z.var() - 1.0) < 5.0 * np.sqrt(2.0 / N)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    # the four normals of one Philox block are independent: no correlation between t mod 4 lanes
+    lanes = z[: (N // 4) * 4].reshape(-1, 4)
+    C = np.corrcoef(lanes.T)
+    assert np.max(np.abs(C - np.eye(4))) < 5.0 / np.sqrt(lanes.shape[0])
+    G = P.T[:64] @ P.T[:64].T                  # rows of Phi (periods): E[Phi Phi^T] = I
+    assert np.max(np.abs(np.diag(G) - 1.0)) < 6.0 * np.sqrt(2.0 / s)
+    np.testing.assert_array_equal(gaussian_sketch_t(11, s, T, rows=[3, 200]), P[[3, 200]])
+    np.testing.assert_array_equal(gaussian_sketch_t(11, s, T), P)
+    assert not np.array_equal(gaussian_sketch_t(12, 4, T), P[:4])
+
+
+def test_countsketch_draw_uniform_buckets_and_signs():
+    """h(t) uniform on [0, s), s_t = +-1 with probability 1/2 each, and one
+    draw per seed."""
+    from scipy import stats
+    from oracle.rng import countsketch_draw
+    T, s = 200000, 64
+    h, sg = countsketch_draw(9, T, s)
+    assert h.min() >= 0 and h.max() < s and set(np.unique(sg)) == {-1, 1}
+    assert stats.chisquare(np.bincount(h, minlength=s)).pvalue > 1e-3
+    assert abs(sg.mean()) < 5.0 / np.sqrt(T)
+    h2, sg2 = countsketch_draw(9, T, s)
+    assert np.array_equal(h, h2) and np.array_equal(sg, sg2)
+    assert not np.array_equal(countsketch_draw(10, T, s)[0], h)
+
+
+def test_round_bf16_nearest_even():
+    """round_bf16 keeps 8 significant bits, rounds to the nearest such value
+    and breaks ties to the even one (hand-made ties and random values)."""
+    from oracle.rng import round_bf16
+    x = np.random.default_rng(5).standard_normal(20000) * 10.0 ** np.random.default_rng(6).integers(-8, 8, 20000)
+    r = round_bf16(x)
+    m, e = np.frexp(r)
+    assert np.all(m * 256.0 == np.rint(m * 256.0))                 # 8 significant bits
+    half = np.ldexp(1.0, np.frexp(x)[1] - 9)                        # half a BF16 step at x
+    assert np.all(np.abs(r - x) <= half)
+    # ties: 1 + 2^-8 lies halfway between 1 and 1 + 2^-7 -> even (1); 1 + 3 * 2^-8 -> 1 + 2^-6
+    assert round_bf16(1.0 + 2.0 ** -8) == 1.0 and round_bf16(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert round_bf16(-(1.0 + 2.0 ** -8)) == -1.0 and round_bf16(0.0) == 0.0
