@@ -1,13 +1,15 @@
 // Sketch stage of STR (Sec. 2.3 / 2.5, step 1): tilde L = L Phi as a BF16
 // tcgen05 GEMM with FP32 accumulation in tensor memory (gemm.cuh), with
 // A = L (n x T, row-major = K-major), B = Phi^T (s x T, one sketch column per
-// row, K-major) and C = tilde L (n x s, FP32, row-major).  The factor may be
+// row, K-major) and C = tilde L (n x s, FP32, row-major), accumulated in
+// chunks of 256 k-columns (gemm_chunk.cuh) so that the tensor core's one-sided
+// accumulator rounding does not shrink the result.  The factor may be
 // stored in any of the three types: BF16 is read as is; FP32 is split into
 // a BF16 hi + lo pair, both multiplied against each staged Phi tile into one
 // accumulator (2^-18 relative per term); FP8 e4m3 is expanded exactly to
 // BF16 and its row scales are applied in the epilogue.  Phi itself is drawn
 // on the device from a seed (rng.cuh) or handed in.
-#include "gemm.cuh"
+#include "gemm_chunk.cuh"
 #include "rng.cuh"
 
 using namespace mv;
@@ -64,7 +66,10 @@ extern "C" int mv_sketch(const void *d_L, int64_t n, int64_t T, int64_t ldL, con
     if (((uintptr_t)d_L) % 16 || ((uintptr_t)d_Phi_t) % 16 || ((uintptr_t)d_L_sketch) % 16) return MV_ERR_INVALID_ARG;
     if ((ldL * 2) % 16 || (ldP * 2) % 16) return MV_ERR_INVALID_ARG;
     (void)cudaGetLastError();
-    return mv::gemm_bf16_tn<256>(d_L, n, ldL, d_Phi_t, m, ldP, T, d_L_sketch, ldS, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    MV_TRY(gemm_err_clear(s));
+    MV_TRY(gemmc<256>(d_L, nullptr, n, ldL, d_Phi_t, m, ldP, T, d_L_sketch, ldS, GemmEpi{}, s));
+    return gemm_err_check(s, "mv_sketch");
 }
 
 extern "C" size_t mv_sketch_workspace_size(int32_t dtype, int64_t n, int64_t T) {
@@ -100,11 +105,17 @@ extern "C" int mv_sketch_dtype(const void *d_L, int32_t dtype, const float *d_ro
                                                               align_up(2 * (size_t)n * ldo, 256));
         split_hilo_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const float *>(d_L), (int)n, (int)T, ldL, B0, B1, ldo);
         MV_CUDA_TRY(cudaGetLastError());
-        return gemm_bf16_tn<256>(B0, n, ldo, d_Phi_t, m, ldP, T, d_L_sketch, ldS, s, B1, nullptr);
+        MV_TRY(gemm_err_clear(s));
+        MV_TRY(gemmc<256>(B0, B1, n, ldo, d_Phi_t, m, ldP, T, d_L_sketch, ldS, GemmEpi{}, s));
+        return gemm_err_check(s, "mv_sketch_dtype");
     }
     fp8_bf16_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const uint8_t *>(d_L), (int)n, (int)T, ldL, B0, ldo);
     MV_CUDA_TRY(cudaGetLastError());
-    return gemm_bf16_tn<256>(B0, n, ldo, d_Phi_t, m, ldP, T, d_L_sketch, ldS, s, nullptr, d_row_scale);
+    GemmEpi e;
+    e.rscale = d_row_scale;
+    MV_TRY(gemm_err_clear(s));
+    MV_TRY(gemmc<256>(B0, nullptr, n, ldo, d_Phi_t, m, ldP, T, d_L_sketch, ldS, e, s));
+    return gemm_err_check(s, "mv_sketch_dtype");
 }
 
 extern "C" int mv_gaussian_sketch(uint64_t seed, int64_t m, int64_t T, void *d_Phi_t, int64_t ldP,

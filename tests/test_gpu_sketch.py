@@ -66,6 +66,11 @@ def test_sketch_gemm_full_size_sampled(mv):
     ref = np.einsum("ij,ij->i", A, B)
     mag = np.einsum("ij,ij->i", np.abs(A), np.abs(B))
     assert np.all(np.abs(got - ref) <= 1e-5 * mag)
+    # no systematic shrink: a one-sided accumulator rounding over the 3024 MMAs of
+    # one output would scale every entry by about 1 - 5e-5 (the chunked accumulation
+    # leaves one chunk's worth, about 5e-7)
+    slope = float(got @ ref / (ref @ ref))
+    assert abs(slope - 1.0) <= 5e-6, slope
 
 
 # ------------------------------------------------------------------ seeded draws (rng.cuh vs oracle/rng.py)

@@ -92,10 +92,11 @@ def test_str_full_size_against_oracle(mv):
     diag(sigma^2) and sampled eigen-residuals on the GPU's own tilde L must
     be below 1e-5 sigma_1^2.  Solve: the GPU's STR-model solve against the
     oracle's Algorithm 1 on the same L_eff and ridge, run from its own start
-    to a KKT residual of 1e-10 -- at the benchmark's tolerance (1e-6: the
-    objective within 1e-5 relative and f - f* within the Frank--Wolfe gap)
-    and at 1e-8, where x must also lie within 1e-4 in the infinity norm
-    (kappa(hat Sigma) is about 4e4, so 1e-6 does not pin x to 1e-4)."""
+    to a KKT residual of 1e-10.  kappa(hat Sigma) is about 4e4, so a KKT
+    residual of 1e-6 leaves the objective about 2e-3 above the optimum and
+    1e-8 still 3e-5 (the Frank--Wolfe certificate holds at both); the
+    benchmark therefore solves the STR model to 1e-9, where x must lie within
+    1e-4 of x* in the infinity norm and the objective within 1e-5 relative."""
     n, T, m, k = CFG_FULL.n, CFG_FULL.T, 8192, 512
     R, Lb, L32, mu, Phi_t, Ls, L_eff, sigma, gamma = build(mv, n, T, m, k, seed=CFG_FULL.seed)
     del L32
@@ -126,15 +127,16 @@ def test_str_full_size_against_oracle(mv):
     assert ref.converged
     Le = torch.zeros((n, k), dtype=torch.float32, device="cuda")
     Le[:, :] = L_eff
-    for eps in (1e-6, 1e-8):
+    for eps in (1e-6, 1e-9):
         x, info = mv.npga_solve(Le, mu, Rt, k, gamma=gamma, eps=eps, power_start=torch.from_numpy(power_start(n)).cuda())
         assert info["converged"] == 1 and info["kkt"] <= eps
         x = x.cpu().numpy()
         f = objective(E, gamma, x)
-        assert (f - ref.f) / ref.f <= 1e-5
+        # any feasible point: its suboptimality is bounded by its Frank--Wolfe gap
         assert -1e-14 * ref.f <= f - ref.f <= fw_gap(E, gamma, mu_o, Rt, x) + 1e-12 * ref.f
-        if eps <= 1e-8:
+        if eps <= 1e-9:
             assert np.max(np.abs(x - ref.x)) <= 1e-4
+            assert (f - ref.f) / ref.f <= 1e-5
 
 
 @pytest.mark.parametrize("tau,rho,kappa", [(1e-3, 0.9, 500.0), (3e-2, 0.8, 0.0)])
