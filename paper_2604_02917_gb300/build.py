@@ -20,7 +20,8 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libmv.so")
 
 SOURCES = ["center.cu", "project.cu", "solve.cu", "sketch.cu", "str.cu", "llt_host.cu", "llt_f32.cu", "llt_bf16.cu",
-           "llt_fp8.cu", "sigma.cu", "countsketch.cu", "trunc.cu"]
+           "llt_fp8.cu", "sigma.cu", "countsketch.cu", "trunc.cu", "frontier.cu",
+           "adjoint.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

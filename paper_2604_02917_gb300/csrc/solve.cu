@@ -10,60 +10,11 @@
 // replayed; every kernel returns at once when the device-side `done` flag is
 // set, so a chunk that overruns convergence costs only empty launches.  The
 // host reads the flag once per chunk.
-#include <stdlib.h>
-
-#include <mutex>
-#include <unordered_map>
-#include <vector>
-
-#include "gemm.cuh"
-#include "gemm_q8.cuh"
-#include "gemv.cuh"
-#include "llt_api.h"
-#include "project.cuh"
-#include "symv.cuh"
+#include "solve_internal.cuh"
 
 namespace mv {
 
-constexpr int kStepThreads = 512;
-constexpr int kProjBudget = 100;
-
-struct SolveState {
-    int k, done, converged, status;
-    int proj_fail, proj_steps, pad1, pad2;
-    double t, beta_prev;
-    double alpha, lambda_hat;
-    double kkt, nu, tau, nu_kkt, tau_kkt;
-    double mu_min, mu_max;
-    double objective;
-    double beta_c;                         // constant momentum (momentum = 1)
-    int bt_started, backtracks, dykstra, pad3;
-};
-
-struct Plan {
-    int dt, vec, esize;
-    int n, T;
-    int64_t ld;
-    bool tn;                               // L stored transposed (T x n)
-    int gr, gc;                            // rows and columns of the stored matrix
-    int cl;                                // cluster size of the step kernel
-    int t_blocks, t_splits, t_rows;        // gemv_t grid
-    int n_groups, n_splits, n_cols;        // gemv_n grid
-    bool use_llt;                          // fused single-pass L L^T y (llt.cuh)
-    bool want_z;                           // the loop's fused pass also writes z = L^T y to o_z
-    LltPlan lp;
-    bool sig;                              // explicit Sigma (symv.cuh) instead of a factor
-    int snb;                               // Sigma tile rows
-    size_t o_spart, o_stick, o_gobj;
-    size_t o_dyk, o_gd, o_xp;              // Dykstra scratch; backtracking L L^T d and candidate
-    // workspace offsets (bytes)
-    size_t o_state, o_x, o_y, o_gx, o_gy, o_g32, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
-    size_t o_llt, o_err, o_zd;
-    int64_t zstride;                       // row pitch (floats) of the gemv_t partials
-    size_t total;
-};
-
-static int sm_count() {
+int sm_count() {
     static int cached = 0;
     if (cached == 0) {
         int dev = 0;
@@ -75,15 +26,13 @@ static int sm_count() {
     return cached;
 }
 
-static constexpr int kRW = 4;   // rows per warp in gemv_n
 
 // The fused pass pays a cluster exchange per 128-byte column block, so it is
 // used where a block holds many rows and there are many blocks.
 // gemv_t (column sums) and gemv_n (row dots) run over the stored matrix:
 // L (n x T) for MV_LAYOUT_NT, where z = L^T y is gemv_t and g = L z is
 // gemv_n; L^T (T x n) for MV_LAYOUT_TN, where the two swap roles.
-static Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows = 0, bool fused = false,
-                      bool tn = false, int n_bytes = 16384) {
+Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows, bool fused, bool tn, int n_bytes) {
     Plan p{};
     p.dt = dt;
     p.esize = dtype_size(dt);
@@ -201,10 +150,6 @@ static Plan make_plan_sigma(int64_t n, int64_t ld) {
     return p;
 }
 
-template <typename T_>
-static T_ *at(void *ws, size_t off) {
-    return reinterpret_cast<T_ *>(reinterpret_cast<char *>(ws) + off);
-}
 
 // ------------------------------------------------------------------ kernels
 // This block's slice of the Dykstra scratch (4 arrays of nl doubles).
@@ -811,7 +756,7 @@ __global__ void grad_finish_kernel(const double *__restrict__ lz, const double *
 }
 
 // ------------------------------------------------------------------ host
-static int validate_problem(const mv_problem *P) {
+int validate_problem(const mv_problem *P) {
     if (P == nullptr || P->L == nullptr || P->mu == nullptr) return MV_ERR_INVALID_ARG;
     if (P->dtype != MV_F32 && P->dtype != MV_BF16 && P->dtype != MV_FP8_E4M3) return MV_ERR_INVALID_ARG;
     if (P->mode != MV_RETURN_GE && P->mode != MV_RETURN_EQ) return MV_ERR_INVALID_ARG;
@@ -828,8 +773,6 @@ static int validate_problem(const mv_problem *P) {
     return MV_OK;
 }
 
-static bool is_tn(const mv_problem *P) { return P->layout == MV_LAYOUT_TN; }
-static bool is_sigma(const mv_problem *P) { return P->layout == MV_LAYOUT_SIGMA; }
 
 // The plan of a single-problem call: explicit Sigma, or a factor in either layout.
 static Plan plan_for(const mv_problem *P, bool fused) {
@@ -838,14 +781,14 @@ static Plan plan_for(const mv_problem *P, bool fused) {
 }
 
 // The calls that read L only through the NT-layout kernels.
-static int require_nt(const mv_problem *P, const char *what) {
+int require_nt(const mv_problem *P, const char *what) {
     if (P->layout == MV_LAYOUT_NT) return MV_OK;
     char msg[128];
     snprintf(msg, sizeof(msg), "%s: the factor must be stored n x T (MV_LAYOUT_NT)", what);
     return record_message(MV_ERR_UNSUPPORTED, msg);
 }
 
-static int check_ws(void *ws, size_t ws_bytes, size_t need) {
+int check_ws(void *ws, size_t ws_bytes, size_t need) {
     if (need == 0) return MV_OK;
     if (ws == nullptr || ws_bytes < need || ((uintptr_t)ws) % 256 != 0) return MV_ERR_WORKSPACE;
     return MV_OK;
@@ -908,8 +851,8 @@ static void launch_g(const Plan &p, const mv_problem *P, const float *z, void *w
 }
 
 // g = L L^T y (row-scaled) in one pass over L; capturable (no synchronisation).
-static int launch_llt(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
-                      float *g32, cudaStream_t s, float *z = nullptr) {
+int launch_llt(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
+               float *g32, cudaStream_t s, float *z) {
     LltScratch sc = llt_scratch(at<char>(ws, p.o_llt), p.n);
     sc.err = at<int>(ws, p.o_err);             // read back by the solve
     return llt_launch(p.lp, p.dt, P->L, p.n, p.T, p.ld, y32, P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr, sc,
@@ -917,16 +860,7 @@ static int launch_llt(const Plan &p, const mv_problem *P, const float *y32, void
 }
 
 // Kernel attributes are set once per process, before any stream capture.
-template <typename Kern>
-static bool cluster_attrs(Kern k, int CL) {
-    const int smem = (int)proj_elem_bytes(kProjMaxLocal);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
-    if (CL > 8 && cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-        return false;
-    return true;
-}
-
-static int set_kernel_attrs() {
+int set_kernel_attrs() {
     static std::once_flag once;
     static int status = MV_OK;
     std::call_once(once, [] {
@@ -951,31 +885,14 @@ static int set_kernel_attrs() {
     return status;
 }
 
-static void gemv_pair(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done,
-                      double *g_out, cudaStream_t s, float *g32 = nullptr) {
+void gemv_pair(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
+               cudaStream_t s, float *g32) {
     launch_z(p, P, y32, ws, done, s);
     launch_g(p, P, at<float>(ws, p.o_z), ws, done, g_out, g32, s);
 }
 
-static void gemv_t_only(const Plan &p, const mv_problem *P, const float *y32, void *ws, cudaStream_t s) {
+void gemv_t_only(const Plan &p, const mv_problem *P, const float *y32, void *ws, cudaStream_t s) {
     launch_z(p, P, y32, ws, nullptr, s);
-}
-
-template <typename Kern, typename... Args>
-static cudaError_t launch_cluster(Kern kern, int CL, size_t smem, cudaStream_t s, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)CL);
-    cfg.blockDim = dim3(kProjNT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 static size_t step_smem(int n, int CL) { return proj_elem_bytes((n + CL - 1) / CL); }
@@ -1026,7 +943,7 @@ static void launch_step(const Plan &p, const mv_problem *P, const mv_solve_opts 
     }
 }
 
-static void launch_init_x(const Plan &p, const mv_problem *P, const mv_solve_opts *O, const double *x_in, void *ws,
+void launch_init_x(const Plan &p, const mv_problem *P, const mv_solve_opts *O, const double *x_in, void *ws,
                           cudaStream_t s) {
     SolveState *st = at<SolveState>(ws, p.o_state);
     const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
@@ -1077,7 +994,7 @@ static int launch_product(const Plan &p, const mv_problem *P, const float *y32, 
 // One loop iteration.  With `ev` non-null, events ev[0..3] bracket gemv_t,
 // gemv_n and the step kernel (ev[3] is the next iteration's ev[0]); with the
 // fused pass, ev[0..1] bracket it and ev[1..2] is empty.
-static int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
+int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
                             cudaStream_t s, const cudaEvent_t *ev) {
     SolveState *st = at<SolveState>(ws, p.o_state);
     const float *y32 = at<float>(ws, p.o_y32);
@@ -1121,38 +1038,10 @@ static int timing_events(int count, const cudaEvent_t **out) {
     return MV_OK;
 }
 
-// One cached graph per distinct (problem, options, workspace) triple.
-struct GraphKey {
-    const void *L, *mu, *rs, *ws;
-    int64_t n, T, ld;
-    int dt, mode, kkt_every, max_iter, chunk, fused;
-    double R, gamma, eps;
-    const void *ev;
-    int momentum, backtrack, budget, dyk_iters;
-    double bt_rho, m_f;
-    double aux = 0.0;                    // any further scalar baked into the graph (the adjoint's alpha)
-    bool operator==(const GraphKey &o) const {
-        return L == o.L && mu == o.mu && rs == o.rs && ws == o.ws && n == o.n && T == o.T && ld == o.ld &&
-               dt == o.dt && mode == o.mode && kkt_every == o.kkt_every && max_iter == o.max_iter &&
-               chunk == o.chunk && fused == o.fused && R == o.R && gamma == o.gamma && eps == o.eps && ev == o.ev &&
-               momentum == o.momentum && backtrack == o.backtrack && budget == o.budget &&
-               dyk_iters == o.dyk_iters && bt_rho == o.bt_rho && m_f == o.m_f && aux == o.aux;
-    }
-};
-struct GraphKeyHash {
-    size_t operator()(const GraphKey &k) const {
-        size_t h = (size_t)k.L ^ ((size_t)k.ws << 1) ^ ((size_t)k.n * 1315423911u) ^ ((size_t)k.T << 7);
-        h ^= std::hash<double>()(k.R) + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
-        return h;
-    }
-};
 static std::mutex g_graph_mu;
 static std::unordered_map<GraphKey, cudaGraphExec_t, GraphKeyHash> g_graphs;
 
-// Returns the cached executable graph of `key`, capturing `enqueue(stream)`
-// into it on first use.
-template <typename F>
-static int cached_graph(const GraphKey &key, F &&enqueue, cudaGraphExec_t *out) {
+int cached_graph(const GraphKey &key, const std::function<int(cudaStream_t)> &enqueue, cudaGraphExec_t *out) {
     std::lock_guard<std::mutex> lock(g_graph_mu);
     auto it = g_graphs.find(key);
     if (it != g_graphs.end()) {
@@ -1187,13 +1076,13 @@ static int cached_graph(const GraphKey &key, F &&enqueue, cudaGraphExec_t *out) 
     return MV_OK;
 }
 
-static GraphKey graph_key(const Plan &p, const mv_problem *P, const mv_solve_opts *O, int chunk, const void *ev) {
+GraphKey graph_key(const Plan &p, const mv_problem *P, const mv_solve_opts *O, int chunk, const void *ev) {
     return GraphKey{P->L, P->mu, P->row_scale, nullptr, P->n, P->T, P->ld, P->dtype, P->mode, O->kkt_every,
                     O->max_iter, chunk, p.sig ? 2 : (p.use_llt ? (p.want_z ? 3 : 1) : 0), P->R_target, P->gamma, O->eps, ev,
                     O->momentum, O->backtrack, O->proj_budget, O->dykstra_iters, O->bt_rho, O->m_f};
 }
 
-static int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
+int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
                            const cudaEvent_t *ev, cudaGraphExec_t *out) {
     GraphKey key = graph_key(p, P, O, chunk, (const void *)ev);
     key.ws = ws;
@@ -1238,6 +1127,24 @@ static int get_power_graph(const Plan &p, const mv_problem *P, const mv_solve_op
     int dummy = 0;
     return cached_graph(key, [&](cudaStream_t cs) { return launch_power(p, P, O->power_iters, ws, cs, &dummy); },
                         out);
+}
+
+void launch_setup(SolveState *st, const double *mu, const double *r0, const float *rs, float *y32, int n,
+                  cudaStream_t s) {
+    setup_kernel<<<1, kStepThreads, 0, s>>>(st, mu, r0, rs, y32, n);
+}
+void launch_power_norm(const float *g32, const float *rs, float *y32, int n, cudaStream_t s) {
+    power_norm_kernel<<<1, kStepThreads, 0, s>>>(g32, rs, y32, n);
+}
+void launch_step_size(SolveState *st, const float *z, int T, double gamma, double safety, double alpha,
+                      cudaStream_t s) {
+    step_size_kernel<<<1, kStepThreads, 0, s>>>(st, z, T, gamma, safety, alpha);
+}
+void launch_to_y32(const double *x, const float *rs, float *y32, int n, cudaStream_t s) {
+    to_y32_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, rs, y32, n);
+}
+void launch_grad_finish(const double *lz, const double *y, double gamma, double *g, int n, cudaStream_t s) {
+    grad_finish_kernel<<<(n + 255) / 256, 256, 0, s>>>(lz, y, gamma, g, n);
 }
 
 }  // namespace mv
@@ -1472,990 +1379,6 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     h_info->backtracks = hs.backtracks;
     h_info->dykstra = hs.dykstra;
     return h_info->status;
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Efficient frontier: B targets R_b share one factor L (BF16, or FP8 e4m3
-// with row scales s: then the GEMMs read FP8 tiles expanded to BF16 in
-// shared memory (gemm_q8.cuh), s multiplies the split Y operand, since
-// L^T Y = L_q^T (s o Y), and the rows of G, since L Z = s o (L_q Z)).  The two
-// half-products of all B gradients become skinny tensor-core GEMMs:
-//   Z (T x B) = L^T Y,   G (n x B) = L Z,
-// run on tcgen05 (gemm.cuh) with the n x B and T x B operands carried as a
-// BF16 hi + lo pair (2B columns; the GEMM epilogue adds each pair), so the
-// only rounding beyond FP32 accumulation is the BF16 storage of L itself.
-// L^T is materialised once per call in the workspace so that both GEMMs
-// read K-major operands.  Each target then takes its own NPGA step (a
-// cluster per target) with its own KKT test and stops independently.
-namespace mv {
-
-struct FState {
-    int k, done, converged, status;
-    int proj_fail, proj_steps, pad0, pad1;
-    double t, beta_prev, kkt, nu, tau, nu_kkt, tau_kkt, objective;
-};
-
-struct FArgs {
-    FState *fs;
-    const SolveState *st;       // alpha, mu_min, mu_max of the shared factor
-    const float *G;             // n x 2B: hi and lo halves of L Z
-    int ldG, B;
-    double *X, *Y, *GX;         // B x n (row b = target b)
-    __nv_bfloat16 *Ysplit;      // 2B x ldY: BF16 hi rows 0..B-1, lo rows B..2B-1
-    int64_t ldY;
-    const float *row_scale;     // FP8 factor: n scales (else null)
-    const double *mu, *Rt;
-    int n, mode, kkt_every, max_iter;
-    double gamma, eps;
-};
-
-__device__ __forceinline__ void write_split(__nv_bfloat16 *Ys, int64_t ldY, int B, int b, int i, double y,
-                                            const float *rs = nullptr) {
-    const float yf = (float)(rs != nullptr ? y * (double)rs[i] : y);
-    const __nv_bfloat16 hi = __float2bfloat16_rn(yf);
-    Ys[(int64_t)b * ldY + i] = hi;
-    Ys[(int64_t)(B + b) * ldY + i] = __float2bfloat16_rn(yf - __bfloat162float(hi));
-}
-
-template <int CL>
-__global__ void __launch_bounds__(kProjNT) frontier_init_kernel(FArgs a) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ ProjSmem psm;
-    const int b = blockIdx.x / CL, rank = cluster_rank<CL>();
-    const int n = a.n, nl = (n + CL - 1) / CL, r0 = min(n, rank * nl), r1 = min(n, r0 + nl);
-    ProjElems el = carve_elems(dsm, nl);
-    el.n = r1 - r0;
-    proj_smem_init(&psm);
-    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-        el.v[i] = 1.0 / n;
-        el.mu[i] = a.mu[r0 + i];
-    }
-    __syncthreads();
-    ClusterProj<CL> P{&psm, el};
-    P.prepare();
-    const ProjOut o = P.solve(a.Rt[b], a.mode, a.st->mu_min, a.st->mu_max, 0.0, -INFINITY, kProjBudget);
-    const bool bad = (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC);
-    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-        const int gi = r0 + i;
-        const double xi = bad ? 0.0 : fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
-        a.X[(int64_t)b * n + gi] = xi;
-        a.Y[(int64_t)b * n + gi] = xi;
-        write_split(a.Ysplit, a.ldY, a.B, b, gi, xi, a.row_scale);
-    }
-    if (rank == 0 && threadIdx.x == 0) {
-        FState f{};
-        f.t = 1.0;
-        f.nu = f.nu_kkt = o.nu;
-        f.tau = f.tau_kkt = o.tau;
-        f.kkt = INFINITY;
-        f.status = bad ? o.status : (a.st->status != MV_OK ? a.st->status : MV_OK);
-        f.done = (f.status != MV_OK) ? 1 : 0;
-        a.fs[b] = f;
-    }
-    cluster_barrier<CL>();
-}
-
-template <int CL>
-__global__ void __launch_bounds__(kProjNT) frontier_step_kernel(FArgs a) {
-    extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ ProjSmem psm;
-    __shared__ double sc[4];
-    const int b = blockIdx.x / CL, rank = cluster_rank<CL>();
-    FState *fs = a.fs + b;
-    if (*(volatile int *)&fs->done) return;      // uniform over the cluster (see npga_step_kernel)
-    const int n = a.n, nl = (n + CL - 1) / CL, r0 = min(n, rank * nl), r1 = min(n, r0 + nl);
-    const int k = fs->k;
-    const double beta_prev = fs->beta_prev, t = fs->t, alpha = a.st->alpha;
-    const double mn = a.st->mu_min, mx = a.st->mu_max;
-    const double nu0 = fs->nu, tau0 = fs->tau, nuk0 = fs->nu_kkt, tauk0 = fs->tau_kkt;
-    const double gamma = a.gamma, R = a.Rt[b];
-    if (threadIdx.x == 0) {
-        sc[0] = 1.0 / (1.0 + beta_prev);
-        const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-        sc[1] = tn;
-        sc[2] = (t - 1.0) / tn;
-    }
-    ProjElems el = carve_elems(dsm, nl);
-    el.n = r1 - r0;
-    proj_smem_init(&psm);
-    const double inv1pb = sc[0], tn = sc[1], beta = sc[2];
-    const bool check = (a.kkt_every > 0 && k % a.kkt_every == 0) || (k >= a.max_iter);
-    double *Xb = a.X + (int64_t)b * n, *Yb = a.Y + (int64_t)b * n, *GXb = a.GX + (int64_t)b * n;
-    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-        const int gi = r0 + i;
-        el.mu[i] = a.mu[gi];
-        const double gyi = ((double)a.G[(int64_t)gi * a.ldG + b] + (double)a.G[(int64_t)gi * a.ldG + a.B + b]) *
-                           (a.row_scale != nullptr ? (double)a.row_scale[gi] : 1.0);
-        const double gxi = (k == 0) ? gyi : (gyi + beta_prev * GXb[gi]) * inv1pb;
-        GXb[gi] = gxi;
-        if (check) {
-            const double xi = Xb[gi];
-            el.v[i] = xi - alpha * (2.0 * gxi + 2.0 * gamma * xi);
-        }
-    }
-    __syncthreads();
-    ClusterProj<CL> P{&psm, el};
-    if (check) {
-        P.prepare();
-        const ProjOut o = P.solve(R, a.mode, mn, mx, nuk0, tauk0, kProjBudget);
-        double r2 = 0.0;
-        for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-            const double p = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
-            const double d = p - Xb[r0 + i];
-            r2 = fma(d, d, r2);
-        }
-        r2 = P.reduce_double(r2);
-        const bool conv = r2 <= a.eps * a.eps;
-        const bool stop = conv || k >= a.max_iter || !(r2 == r2);
-        if (rank == 0 && threadIdx.x == 0) {
-            fs->kkt = sqrt(r2);
-            fs->nu_kkt = o.nu;
-            fs->tau_kkt = o.tau;
-            fs->proj_steps += o.steps;
-            if (o.status != MV_OK) fs->proj_fail += 1;
-            if (stop) {
-                fs->done = 1;
-                fs->converged = conv ? 1 : 0;
-                fs->status = conv ? MV_OK : (!(r2 == r2) ? MV_ERR_NUMERIC : MV_ERR_NOT_CONVERGED);
-            }
-        }
-        if (stop) {
-            cluster_barrier<CL>();
-            return;
-        }
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-        const int gi = r0 + i;
-        const double gyi = ((double)a.G[(int64_t)gi * a.ldG + b] + (double)a.G[(int64_t)gi * a.ldG + a.B + b]) *
-                           (a.row_scale != nullptr ? (double)a.row_scale[gi] : 1.0);
-        const double yi = Yb[gi];
-        el.v[i] = yi - alpha * (2.0 * gyi + 2.0 * gamma * yi);
-    }
-    __syncthreads();
-    P.prepare();
-    const ProjOut o = P.solve(R, a.mode, mn, mx, nu0, tau0, kProjBudget);
-    for (int i = threadIdx.x; i < el.n; i += kProjNT) {
-        const int gi = r0 + i;
-        const double xn = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
-        const double xo = Xb[gi];
-        const double yn = xn + beta * (xn - xo);
-        Xb[gi] = xn;
-        Yb[gi] = yn;
-        write_split(a.Ysplit, a.ldY, a.B, b, gi, yn, a.row_scale);
-    }
-    if (rank == 0 && threadIdx.x == 0) {
-        fs->t = tn;
-        fs->beta_prev = beta;
-        fs->k = k + 1;
-        fs->nu = o.nu;
-        fs->tau = o.tau;
-        fs->proj_steps += o.steps;
-        if (o.status != MV_OK) fs->proj_fail += 1;
-        if (o.status == MV_ERR_INFEASIBLE || o.status == MV_ERR_NUMERIC) {
-            fs->done = 1;
-            fs->status = o.status;
-        }
-    }
-    cluster_barrier<CL>();
-}
-
-// L (n x T, ld ldL) -> L^T (T x n, ld ldT), BF16, 32x32 tiles through shared memory.
-template <typename E>
-__global__ void transpose_elem_kernel(const E *__restrict__ L, int n, int T, int64_t ldL, E *__restrict__ Lt,
-                                      int64_t ldT) {
-    __shared__ E tile[32][33];
-    const int t0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int i = i0 + r, t = t0 + threadIdx.x;
-        tile[r][threadIdx.x] = (i < n && t < T) ? L[(int64_t)i * ldL + t] : E{};
-    }
-    __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int t = t0 + r, i = i0 + threadIdx.x;
-        if (t < T && i < n) Lt[(int64_t)t * ldT + i] = tile[threadIdx.x][r];
-    }
-}
-
-// Rows of X (B x n, FP64) -> the BF16 hi/lo operand rows (2B x ldY).
-__global__ void split_rows_kernel(const double *__restrict__ X, int B, int n, __nv_bfloat16 *__restrict__ Ys,
-                                  int64_t ldY, const float *__restrict__ rs) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)B * n) return;
-    const int b = (int)(idx / n), i = (int)(idx - (int64_t)b * n);
-    write_split(Ys, ldY, B, b, i, X[idx], rs);
-}
-
-// f_b = ||L^T x_b||^2 + gamma ||x_b||^2 from Z = L^T X carried as BF16 hi + lo rows.
-__global__ void __launch_bounds__(kStepThreads)
-frontier_objective_kernel(const __nv_bfloat16 *__restrict__ Zt, int64_t ldZ, int B, int T,
-                          const double *__restrict__ X, int n, double gamma, FState *fs) {
-    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
-    const int b = blockIdx.x;
-    float s = 0.f, c = 0.f;
-    for (int t = threadIdx.x; t < T; t += kStepThreads) {
-        const float z = __bfloat162float(Zt[(int64_t)b * ldZ + t]) + __bfloat162float(Zt[(int64_t)(B + b) * ldZ + t]);
-        const float y = fmaf(z, z, -c);
-        const float u = s + y;
-        c = (u - s) - y;
-        s = u;
-    }
-    double v[2] = {(double)s - (double)c, 0.0};
-    if (gamma != 0.0)
-        for (int i = threadIdx.x; i < n; i += kStepThreads) v[1] = fma(X[(int64_t)b * n + i], X[(int64_t)b * n + i], v[1]);
-    block_sum<2, kStepThreads>(v, red);
-    if (threadIdx.x == 0) fs[b].objective = v[0] + gamma * v[1];
-}
-
-template <int CL>
-static cudaError_t launch_frontier_kernel(bool init, const FArgs &a, int B, int n, cudaStream_t s) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(B * CL));
-    cfg.blockDim = dim3(kProjNT);
-    cfg.dynamicSmemBytes = proj_elem_bytes((n + CL - 1) / CL);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if (init) return cudaLaunchKernelEx(&cfg, frontier_init_kernel<CL>, a);
-    return cudaLaunchKernelEx(&cfg, frontier_step_kernel<CL>, a);
-}
-
-static cudaError_t launch_frontier(bool init, int CL, const FArgs &a, cudaStream_t s) {
-    switch (CL) {
-        case 1: return launch_frontier_kernel<1>(init, a, a.B, a.n, s);
-        case 2: return launch_frontier_kernel<2>(init, a, a.B, a.n, s);
-        case 4: return launch_frontier_kernel<4>(init, a, a.B, a.n, s);
-        case 8: return launch_frontier_kernel<8>(init, a, a.B, a.n, s);
-        default: return launch_frontier_kernel<16>(init, a, a.B, a.n, s);
-    }
-}
-
-static int frontier_attrs() {
-    static std::once_flag once;
-    static int st = MV_OK;
-    std::call_once(once, [] {
-        bool ok = cluster_attrs(frontier_init_kernel<1>, 1) && cluster_attrs(frontier_init_kernel<2>, 2) &&
-                  cluster_attrs(frontier_init_kernel<4>, 4) && cluster_attrs(frontier_init_kernel<8>, 8) &&
-                  cluster_attrs(frontier_init_kernel<16>, 16) && cluster_attrs(frontier_step_kernel<1>, 1) &&
-                  cluster_attrs(frontier_step_kernel<2>, 2) && cluster_attrs(frontier_step_kernel<4>, 4) &&
-                  cluster_attrs(frontier_step_kernel<8>, 8) && cluster_attrs(frontier_step_kernel<16>, 16);
-        ok = ok && gemm_set_attrs<64, kEpiF32>() == MV_OK && gemm_set_attrs<128, kEpiF32>() == MV_OK &&
-             gemm_set_attrs<256, kEpiF32>() == MV_OK && gemm_set_attrs<64, kEpiPairSplitT>() == MV_OK &&
-             gemm_set_attrs<128, kEpiPairSplitT>() == MV_OK && gemm_set_attrs<256, kEpiPairSplitT>() == MV_OK;
-        ok = ok && gemm_q8_set_attrs<64, kEpiF32>() == MV_OK && gemm_q8_set_attrs<128, kEpiF32>() == MV_OK &&
-             gemm_q8_set_attrs<256, kEpiF32>() == MV_OK && gemm_q8_set_attrs<64, kEpiPairSplitT>() == MV_OK &&
-             gemm_q8_set_attrs<128, kEpiPairSplitT>() == MV_OK && gemm_q8_set_attrs<256, kEpiPairSplitT>() == MV_OK;
-        if (!ok) st = record_cuda_error(cudaGetLastError(), "frontier kernel attributes", __FILE__, __LINE__);
-    });
-    return st;
-}
-
-struct FPlan {
-    int B;          // padded target count (32, 64 or 128)
-    int BN;         // 2B: GEMM tile width
-    int splits;     // K-splits of G = L Z (43 row tiles at n = 5440 would leave SMs idle)
-    int64_t ldLt, ldY, ldZ;
-    size_t o_lt, o_y, o_z, o_g, o_x, o_yd, o_gx, o_fs, o_rt, o_gpart, o_gtick, total;
-};
-
-static FPlan make_fplan(const Plan &p, int64_t nb) {
-    FPlan f{};
-    f.B = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
-    f.BN = 2 * f.B;
-    f.ldLt = (p.n + 15) / 16 * 16;                    // row pitch a multiple of 16 bytes for BF16 and FP8
-    f.ldY = f.ldLt;
-    f.ldZ = ((int64_t)p.T + 7) / 8 * 8;
-    size_t off = p.total;
-    auto take = [&](size_t bytes) {
-        size_t o = off;
-        off = align_up(off + bytes, 256);
-        return o;
-    };
-    f.o_lt = take((size_t)p.esize * p.T * f.ldLt);
-    f.o_y = take(2 * (size_t)f.BN * f.ldY);
-    f.o_z = take(2 * (size_t)f.BN * f.ldZ);
-    f.o_g = take(4 * (size_t)p.n * f.BN);
-    f.o_x = take(8 * (size_t)f.B * p.n);
-    f.o_yd = take(8 * (size_t)f.B * p.n);
-    f.o_gx = take(8 * (size_t)f.B * p.n);
-    f.o_fs = take(sizeof(FState) * (size_t)f.B);
-    f.o_rt = take(8 * (size_t)f.B);
-    f.splits = gemm_splits(p.n, f.BN, p.T, f.BN, sm_count());
-    f.o_gpart = take(4 * (size_t)f.splits * p.n * f.BN);
-    f.o_gtick = take(4 * (size_t)((p.n + kBM - 1) / kBM) + 64);
-    f.total = off;
-    return f;
-}
-
-template <int BN>
-static void frontier_gemms(const CUtensorMap &tLt, const CUtensorMap &tY, const CUtensorMap &tL, const CUtensorMap &tZ,
-                           const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
-    float *gpart = at<float>(ws, f.o_gpart);
-    unsigned *gtick = at<unsigned>(ws, f.o_gtick);
-    if (p.dt == MV_FP8_E4M3) {
-        gemm_q8_launch<BN, kEpiPairSplitT>(tLt, tY, p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(ws, f.o_z), f.ldZ,
-                                           s);
-        gemm_q8_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s, f.splits,
-                                    gpart, gtick);
-        return;
-    }
-    gemm_launch<BN, kEpiPairSplitT>(tLt, tY, p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(ws, f.o_z), f.ldZ, s);
-    gemm_launch<BN, kEpiF32>(tL, tZ, p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s, f.splits, gpart,
-                             gtick);
-}
-
-static void frontier_gemm_pair(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
-    if (f.BN == 64) frontier_gemms<64>(maps[0], maps[1], maps[2], maps[3], p, f, ws, s);
-    else if (f.BN == 128) frontier_gemms<128>(maps[0], maps[1], maps[2], maps[3], p, f, ws, s);
-    else frontier_gemms<256>(maps[0], maps[1], maps[2], maps[3], p, f, ws, s);
-}
-
-// L^T X for the objectives, X already written as the split operand.
-static void frontier_ltx(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
-    __nv_bfloat16 *Zt = at<__nv_bfloat16>(ws, f.o_z);
-    if (p.dt == MV_FP8_E4M3) {
-        if (f.BN == 64) gemm_q8_launch<64, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
-        else if (f.BN == 128)
-            gemm_q8_launch<128, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
-        else gemm_q8_launch<256, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
-        return;
-    }
-    if (f.BN == 64) gemm_launch<64, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
-    else if (f.BN == 128) gemm_launch<128, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
-    else gemm_launch<256, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
-}
-
-}  // namespace mv
-
-extern "C" {
-
-size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets) {
-    if (validate_problem(P) != MV_OK || P->layout != MV_LAYOUT_NT || P->dtype == MV_F32 || n_targets < 1 ||
-        n_targets > 128)
-        return 0;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
-    return make_fplan(p, n_targets).total;
-}
-
-int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64_t n_targets,
-                           const mv_solve_opts *O_in, double *d_X, mv_solve_info *h_infos, void *d_ws, size_t ws_bytes,
-                           mv_stream_t stream) {
-    MV_TRY(validate_problem(P));
-    MV_TRY(require_nt(P, "frontier solve"));
-    if (P->dtype == MV_F32)
-        return record_message(MV_ERR_UNSUPPORTED, "frontier solve: L must be BF16 or FP8 (the tensor-core operand)");
-    if (d_R_targets == nullptr || d_X == nullptr || h_infos == nullptr || n_targets < 1 || n_targets > 128)
-        return MV_ERR_INVALID_ARG;
-    mv_solve_opts O;
-    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
-    if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
-    if (O.momentum != 0 || O.backtrack != 0)
-        return record_message(MV_ERR_UNSUPPORTED, "frontier solve: fixed step and FISTA momentum only");
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);   // power method: fused pass
-    const FPlan f = make_fplan(p, n_targets);
-    MV_TRY(check_ws(d_ws, ws_bytes, f.total));
-    MV_TRY(set_kernel_attrs());
-    MV_TRY(frontier_attrs());
-    (void)cudaGetLastError();
-    cudaStream_t s = (cudaStream_t)stream;
-    SolveState *st = at<SolveState>(d_ws, p.o_state);
-    float *y32 = at<float>(d_ws, p.o_y32);
-    const int B = f.B, nt = (int)n_targets;
-
-    // Targets: the caller's n_targets, padded to B by repeating the last one (padded targets are ignored).
-    double *Rt = at<double>(d_ws, f.o_rt);
-    MV_CUDA_TRY(cudaMemcpyAsync(Rt, d_R_targets, 8 * (size_t)nt, cudaMemcpyDeviceToDevice, s));
-    for (int b = nt; b < B; ++b)
-        MV_CUDA_TRY(cudaMemcpyAsync(Rt + b, d_R_targets + nt - 1, 8, cudaMemcpyDeviceToDevice, s));
-
-    // Shared step size from the power method on L (the single-problem GEMV path).
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
-    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
-    setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
-    if (p.use_llt) {
-        MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
-        MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
-    }
-    for (int it = 0; it < O.power_iters; ++it) {
-        if (p.use_llt)
-            MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
-        else
-            gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
-        power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(d_ws, p.o_g32), rs, y32, p.n);
-    }
-    if (O.power_iters > 0) gemv_t_only(p, P, y32, d_ws, s);
-    step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0 || O.power_iters == 0) ? 0 : p.T,
-                                                P->gamma, O.power_safety, O.alpha);
-    const dim3 tgrid((unsigned)((p.T + 31) / 32), (unsigned)((p.n + 31) / 32));
-    if (P->dtype == MV_FP8_E4M3)
-        transpose_elem_kernel<uint8_t><<<tgrid, dim3(32, 8), 0, s>>>(
-            reinterpret_cast<const uint8_t *>(P->L), p.n, p.T, P->ld, at<uint8_t>(d_ws, f.o_lt), f.ldLt);
-    else
-        transpose_elem_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, s>>>(
-            reinterpret_cast<const __nv_bfloat16 *>(P->L), p.n, p.T, P->ld, at<__nv_bfloat16>(d_ws, f.o_lt), f.ldLt);
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_y), 0, 2 * (size_t)f.BN * f.ldY, s));
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_gtick), 0, 4 * (size_t)((p.n + kBM - 1) / kBM) + 64, s));
-    MV_CUDA_TRY(cudaGetLastError());
-
-    FArgs a;
-    a.fs = at<FState>(d_ws, f.o_fs);
-    a.st = st;
-    a.G = at<float>(d_ws, f.o_g);
-    a.ldG = f.BN;
-    a.B = B;
-    a.X = at<double>(d_ws, f.o_x);
-    a.Y = at<double>(d_ws, f.o_yd);
-    a.GX = at<double>(d_ws, f.o_gx);
-    a.Ysplit = at<__nv_bfloat16>(d_ws, f.o_y);
-    a.ldY = f.ldY;
-    a.row_scale = rs;
-    a.mu = P->mu;
-    a.Rt = Rt;
-    a.n = p.n;
-    a.mode = P->mode;
-    a.kkt_every = O.kkt_every;
-    a.max_iter = O.max_iter;
-    a.gamma = P->gamma;
-    a.eps = O.eps;
-    MV_CUDA_TRY(launch_frontier(true, p.cl, a, s));
-
-    CUtensorMap maps[4];
-    if (P->dtype == MV_FP8_E4M3) {
-        MV_TRY(make_map_u8(&maps[0], at<void>(d_ws, f.o_lt), p.T, p.n, f.ldLt, kBM));
-        MV_TRY(make_map_u8(&maps[2], P->L, p.n, p.T, P->ld, kBM));
-    } else {
-        MV_TRY(make_map_bf16(&maps[0], at<void>(d_ws, f.o_lt), p.T, p.n, f.ldLt, kBM));
-        MV_TRY(make_map_bf16(&maps[2], P->L, p.n, p.T, P->ld, kBM));
-    }
-    MV_TRY(make_map_bf16(&maps[1], at<void>(d_ws, f.o_y), f.BN, p.n, f.ldY, f.BN));
-    MV_TRY(make_map_bf16(&maps[3], at<void>(d_ws, f.o_z), f.BN, p.T, f.ldZ, f.BN));
-    int zero = 0;
-    MV_CUDA_TRY(cudaMemcpyToSymbolAsync(g_gemm_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
-
-    const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
-    int launches = 3 + 3 * O.power_iters + 1 + 2;
-    cudaGraphExec_t exec = nullptr;
-    if (O.use_graph) {
-        cudaStream_t cs;
-        MV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph;
-        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            for (int c = 0; c < chunk; ++c) {
-                frontier_gemm_pair(maps, p, f, d_ws, cs);
-                launch_frontier(false, p.cl, a, cs);
-            }
-            if (cudaStreamEndCapture(cs, &graph) == cudaSuccess) {
-                if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
-                cudaGraphDestroy(graph);
-            }
-        }
-        cudaStreamDestroy(cs);
-        (void)cudaGetLastError();
-    }
-    std::vector<FState> hf(B);
-    const int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
-    for (int64_t c = 0; c < max_chunks; ++c) {
-        if (exec) {
-            MV_CUDA_TRY(cudaGraphLaunch(exec, s));
-        } else {
-            for (int i = 0; i < chunk; ++i) {
-                frontier_gemm_pair(maps, p, f, d_ws, s);
-                MV_CUDA_TRY(launch_frontier(false, p.cl, a, s));
-            }
-        }
-        launches += 3 * chunk;
-        MV_CUDA_TRY(cudaMemcpyAsync(hf.data(), a.fs, sizeof(FState) * B, cudaMemcpyDeviceToHost, s));
-        MV_CUDA_TRY(cudaStreamSynchronize(s));
-        bool all = true;
-        for (int b = 0; b < nt; ++b) all = all && hf[b].done;
-        if (all) break;
-    }
-    if (exec) cudaGraphExecDestroy(exec);
-    // Objectives: one more L^T X product with X written as the split operand.
-    split_rows_kernel<<<(unsigned)((B * (int64_t)p.n + 255) / 256), 256, 0, s>>>(a.X, B, p.n, a.Ysplit, f.ldY, rs);
-    frontier_ltx(maps, p, f, d_ws, s);
-    frontier_objective_kernel<<<B, kStepThreads, 0, s>>>(at<__nv_bfloat16>(d_ws, f.o_z), f.ldZ, B, p.T, a.X, p.n,
-                                                         P->gamma, a.fs);
-    launches += 3;
-    MV_CUDA_TRY(cudaGetLastError());
-    MV_CUDA_TRY(cudaMemcpyAsync(hf.data(), a.fs, sizeof(FState) * B, cudaMemcpyDeviceToHost, s));
-    int err = 0;
-    MV_CUDA_TRY(cudaMemcpyFromSymbolAsync(&err, g_gemm_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
-    MV_CUDA_TRY(cudaMemcpy2DAsync(d_X, 8 * (size_t)p.n, a.X, 8 * (size_t)p.n, 8 * (size_t)p.n, (size_t)nt,
-                                  cudaMemcpyDeviceToDevice, s));
-    SolveState hs{};
-    MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-    MV_CUDA_TRY(cudaStreamSynchronize(s));
-    if (err != 0) return record_message(MV_ERR_TIMEOUT, "frontier GEMM pipeline wait timed out");
-    int worst = MV_OK;
-    for (int b = 0; b < nt; ++b) {
-        mv_solve_info &I = h_infos[b];
-        I = mv_solve_info{};
-        I.iterations = hf[b].k;
-        I.status = hf[b].done ? hf[b].status : MV_ERR_NOT_CONVERGED;
-        I.converged = hf[b].converged;
-        I.proj_failures = hf[b].proj_fail;
-        I.proj_steps = hf[b].proj_steps;
-        I.kkt = hf[b].kkt;
-        I.objective = hf[b].objective;
-        I.alpha = hs.alpha;
-        I.lambda_hat = hs.lambda_hat;
-        I.nu = hf[b].nu;
-        I.launches = launches;
-        if (I.status != MV_OK && worst == MV_OK) worst = I.status;
-    }
-    return worst;
-}
-
-}  // extern "C"
-
-// ---------------------------------------------------------------------------
-// Adjoint of the unrolled solve (reverse sweep with checkpointed recompute).
-namespace mv {
-
-// Cluster-wide FP64 sums of NV values per thread, added in a fixed order.
-template <int CL, int NV>
-__device__ void cluster_sums(ProjSmem *sh, double (&v)[NV], double *dslots /* [2][CL][NV] smem */) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ double wsum[kProjNT / kWarp][NV];
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) wsum[warp][k] = v[k];
-    __syncthreads();
-    const int par = sh->parity;
-    if (threadIdx.x == 0) {
-        double t[NV];
-#pragma unroll
-        for (int k = 0; k < NV; ++k) t[k] = 0.0;
-        for (int w = 0; w < kProjNT / kWarp; ++w)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) t[k] += wsum[w][k];
-        const int me = cluster_rank<CL>();
-        for (int r = 0; r < CL; ++r) {
-            double *dst = dslots + ((size_t)par * CL + me) * NV;
-            if constexpr (CL > 1) dst = cg::this_cluster().map_shared_rank(dst, r);
-#pragma unroll
-            for (int k = 0; k < NV; ++k) dst[k] = t[k];
-        }
-    }
-    cluster_barrier<CL>();
-    __shared__ double res[NV];
-    if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double a = 0.0;
-            for (int r = 0; r < CL; ++r) a += dslots[((size_t)par * CL + r) * NV + k];
-            res[k] = a;
-        }
-        sh->parity = par ^ 1;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = res[k];
-    __syncthreads();
-}
-
-struct AdjArgs {
-    const double *x1;          // x_{k+1} (support and values)
-    // nu_j (the return-row multiplier of that projection) and beta_{k0 + j}
-    // are read on the device, so a captured segment replays for any k0
-    const double *nu_tape;     // segment tape of nu
-    const double *betas;       // beta_k, k = 0 .. K-1
-    const int *k0;             // first iteration of the segment
-    int j;                     // position in the segment
-    int eq;                    // 1: equality mode (the return row always tight)
-    double *xbar, *ybar, *mubar;
-    double *vbar;              // out: v_bar (FP64)
-    float *vbar32;             // out: v_bar as the gemv input
-    float *vrec;               // out: v_bar row of the dL update
-    const double *mu;
-    int n;
-};
-
-// One backward step through the projection and the momentum update.
-template <int CL>
-__global__ void __launch_bounds__(kProjNT) adj_proj_kernel(AdjArgs a) {
-    __shared__ ProjSmem psm;
-    __shared__ double dsl[2 * kProjMaxCL * 5];
-    const int rank = cluster_rank<CL>();
-    const int n = a.n, nl = (n + CL - 1) / CL, r0 = min(n, rank * nl), r1 = min(n, r0 + nl);
-    const double nu = a.nu_tape[a.j], beta = a.betas[*a.k0 + a.j];
-    const bool active = a.eq || nu != 0.0;
-    proj_smem_init(&psm);
-    double s[5] = {0.0, 0.0, 0.0, 0.0, 0.0};   // |S|, sum mu, sum mu^2, sum a, sum mu a
-    for (int i = r0 + threadIdx.x; i < r1; i += kProjNT) {
-        if (a.x1[i] > 0.0) {
-            const double m = a.mu[i], ab = a.xbar[i] + (1.0 + beta) * a.ybar[i];
-            s[0] += 1.0;
-            s[1] += m;
-            s[2] = fma(m, m, s[2]);
-            s[3] += ab;
-            s[4] = fma(m, ab, s[4]);
-        }
-    }
-    cluster_sums<CL, 5>(&psm, s, dsl);
-    double c1 = 0.0, c2 = 0.0;
-    const double det = s[0] * s[2] - s[1] * s[1];
-    // With mu constant on S (or |S| = 1) the return row adds nothing to the
-    // budget row: project on span(1) only (x does not move with mu there).
-    const bool two = active && det > 1e-14 * s[0] * s[2];
-    if (two) {
-        c1 = (s[2] * s[3] - s[1] * s[4]) / det;
-        c2 = (s[0] * s[4] - s[1] * s[3]) / det;
-    } else if (s[0] > 0.0) {
-        c1 = s[3] / s[0];
-    }
-    for (int i = r0 + threadIdx.x; i < r1; i += kProjNT) {
-        const double ab = a.xbar[i] + (1.0 + beta) * a.ybar[i];
-        const double xi = a.x1[i];
-        double vb = 0.0;
-        if (xi > 0.0) {
-            vb = ab - c1 - c2 * a.mu[i];
-            if (two) a.mubar[i] += nu * vb - xi * c2;
-        }
-        a.xbar[i] = -beta * a.ybar[i];
-        a.vbar[i] = vb;
-        a.vbar32[i] = (float)vb;
-        a.vrec[i] = (float)vb;
-    }
-    cluster_barrier<CL>();
-}
-
-// y_bar = v_bar - alpha (2 L L^T v_bar + 2 gamma v_bar).
-__global__ void adj_finish_kernel(const double *__restrict__ vbar, const double *__restrict__ llv, double alpha,
-                                  double gamma, double *__restrict__ ybar, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) ybar[i] = vbar[i] - alpha * (2.0 * llv[i] + 2.0 * gamma * vbar[i]);
-}
-
-static int adj_attrs() {
-    static std::once_flag once;
-    static int st = MV_OK;
-    std::call_once(once, [] {
-        bool ok = true;
-        if (cudaFuncSetAttribute(adj_proj_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-            ok = false;
-        if (!ok) st = record_cuda_error(cudaGetLastError(), "adjoint kernel attributes", __FILE__, __LINE__);
-    });
-    return st;
-}
-
-static cudaError_t launch_adj_proj(int CL, const AdjArgs &a, cudaStream_t s) {
-    switch (CL) {
-        case 1: return launch_cluster(adj_proj_kernel<1>, 1, 0, s, a);
-        case 2: return launch_cluster(adj_proj_kernel<2>, 2, 0, s, a);
-        case 4: return launch_cluster(adj_proj_kernel<4>, 4, 0, s, a);
-        case 8: return launch_cluster(adj_proj_kernel<8>, 8, 0, s, a);
-        default: return launch_cluster(adj_proj_kernel<16>, 16, 0, s, a);
-    }
-}
-
-struct BPlan {
-    int K, C, ncp;
-    int W;                                                  // columns per piece segment of the dL GEMM operands
-    size_t o_cp_state, o_cp_x, o_cp_y, o_cp_gx, o_cp_y32;   // checkpoints
-    size_t o_x1, o_vy, o_zw, o_nu;                          // segment tape
-    size_t o_xbar, o_ybar, o_mubar, o_vbar, o_betas, o_k0;
-    size_t o_ga, o_gb;                                      // split operands of the dL update (BF16, K-major)
-    size_t total;
-};
-
-static BPlan make_bplan(const Plan &p, int K, int C) {
-    BPlan b{};
-    b.K = K;
-    b.C = C;
-    b.ncp = (K + C - 1) / C;
-    size_t off = p.total;
-    auto take = [&](size_t bytes) {
-        size_t o = off;
-        off = align_up(off + bytes, 256);
-        return o;
-    };
-    b.o_cp_state = take(sizeof(SolveState) * (size_t)b.ncp);
-    b.o_cp_x = take(8 * (size_t)p.n * b.ncp);
-    b.o_cp_y = take(8 * (size_t)p.n * b.ncp);
-    b.o_cp_gx = take(8 * (size_t)p.n * b.ncp);
-    b.o_cp_y32 = take(4 * (size_t)p.n * b.ncp);
-    b.o_x1 = take(8 * (size_t)p.n * C);
-    b.o_vy = take(4 * (size_t)p.n * 2 * C);        // rows 0..C-1: v_bar_k, rows C..2C-1: y_k
-    b.o_zw = take(4 * (size_t)p.T * 2 * C);        // rows 0..C-1: z_k,     rows C..2C-1: w_k
-    b.o_nu = take(8 * (size_t)C);
-    b.o_xbar = take(8 * (size_t)p.n);
-    b.o_ybar = take(8 * (size_t)p.n);
-    b.o_mubar = take(8 * (size_t)p.n);
-    b.o_vbar = take(8 * (size_t)p.n);
-    b.o_betas = take(8 * (size_t)K);
-    b.o_k0 = take(16);
-    b.W = (2 * C + kBK - 1) / kBK * kBK;
-    b.o_ga = take(2 * (size_t)p.n * kSplit3 * b.W);
-    b.o_gb = take(2 * (size_t)p.T * kSplit3 * b.W);
-    b.total = off;
-    return b;
-}
-
-// dL += -2 alpha sum_k (v_bar_k z_k^T + y_k w_k^T) over one segment as ONE
-// tcgen05 GEMM: with R = 2 len stacked vectors, A = [v_bar_k; y_k]^T (n x R)
-// and B = [z_k; w_k]^T (T x R) are split into three BF16 pieces each
-// (split3_t_kernel) and C = d_dL accumulates alpha A' B'^T (FP32-accurate).
-static int adjoint_dl_update(const BPlan &b, int n, int T, int len, const float *VY, const float *ZW, double alpha,
-                             void *ws, float *d_dL, int64_t ldD, cudaStream_t s) {
-    const int R = 2 * len, KW = kSplit3 * b.W;
-    __nv_bfloat16 *ga = at<__nv_bfloat16>(ws, b.o_ga), *gb = at<__nv_bfloat16>(ws, b.o_gb);
-    split3_t_kernel<<<dim3((n + 31) / 32, (b.W + 31) / 32), 256, 0, s>>>(VY, R, n, n, b.W, 0, ga, KW);
-    split3_t_kernel<<<dim3((T + 31) / 32, (b.W + 31) / 32), 256, 0, s>>>(ZW, R, T, T, b.W, 1, gb, KW);
-    CUtensorMap ta, tb;
-    MV_TRY(make_map_bf16(&ta, ga, n, KW, KW, kBM));
-    MV_TRY(make_map_bf16(&tb, gb, T, KW, KW, 256));
-    gemm_launch<256, kEpiAccF32>(ta, tb, n, T, KW, d_dL, ldD, nullptr, 0, s, 1, nullptr, nullptr,
-                                 (float)(-2.0 * alpha));
-    MV_CUDA_TRY(cudaGetLastError());
-    return MV_OK;
-}
-
-}  // namespace mv
-
-extern "C" {
-
-size_t mv_backward_workspace_size(const mv_problem *P, const mv_solve_opts *O_in) {
-    if (validate_problem(P) != MV_OK || P->layout != MV_LAYOUT_NT || P->dtype != MV_F32) return 0;
-    mv_solve_opts O;
-    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
-    if (O.max_iter < 1 || O.checkpoint_every < 1) return 0;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
-    return make_bplan(p, O.max_iter, O.checkpoint_every).total;
-}
-
-int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const double *d_x0, const double *d_dloss_dx,
-                     double *d_dmu, float *d_dL, int64_t ldD, mv_solve_info *h_info, void *d_ws, size_t ws_bytes,
-                     mv_stream_t stream) {
-    MV_TRY(validate_problem(P));
-    MV_TRY(require_nt(P, "mv_npga_backward"));
-    if (P->dtype != MV_F32) return record_message(MV_ERR_UNSUPPORTED, "mv_npga_backward: FP32 factor only");
-    if (!d_dloss_dx || !d_dmu || !d_dL || !h_info || ldD < P->T) return MV_ERR_INVALID_ARG;
-    mv_solve_opts O;
-    if (O_in) O = *O_in; else mv_solve_opts_default(&O);
-    if (O.max_iter < 1 || O.checkpoint_every < 1 || O.power_iters < 0) return MV_ERR_INVALID_ARG;
-    if (O.momentum != 0 || O.backtrack != 0)
-        return record_message(MV_ERR_UNSUPPORTED, "mv_npga_backward: differentiates the fixed-step FISTA loop only");
-    if (O.proj_budget < 1 || O.dykstra_iters < 0) return MV_ERR_INVALID_ARG;
-    O.kkt_every = 0;          // unrolled: no early stop inside the K iterations
-    O.eps = 0.0;
-    // one pass over L per product, which also returns z = L^T y for the dL update
-    Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
-    p.want_z = true;
-    const BPlan b = make_bplan(p, O.max_iter, O.checkpoint_every);
-    MV_TRY(check_ws(d_ws, ws_bytes, b.total));
-    MV_TRY(set_kernel_attrs());
-    MV_TRY(adj_attrs());
-    MV_TRY((gemm_set_attrs<256, kEpiAccF32>()));
-    (void)cudaGetLastError();
-    cudaStream_t s = (cudaStream_t)stream;
-    void *ws = d_ws;
-    SolveState *st = at<SolveState>(ws, p.o_state);
-    float *y32 = at<float>(ws, p.o_y32);
-    const int n = p.n, T = p.T, K = b.K, C = b.C;
-    {
-        int zero = 0;
-        MV_CUDA_TRY(cudaMemcpyToSymbolAsync(g_gemm_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
-    }
-
-    // ---- forward to x_K, checkpointing the state before iterations 0, C, 2C, ...
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_err), 0, 16, s));
-    if (p.use_llt) MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
-    setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, nullptr, y32, n);
-    if (!(O.alpha > 0.0)) {
-        for (int it = 0; it < O.power_iters; ++it) {
-            if (p.use_llt)
-                MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), at<float>(ws, p.o_g32), s));
-            else
-                gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), s, at<float>(ws, p.o_g32));
-            power_norm_kernel<<<1, kStepThreads, 0, s>>>(at<float>(ws, p.o_g32), nullptr, y32, n);
-        }
-        if (p.use_llt)
-            MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), nullptr, s, at<float>(ws, p.o_z)));
-        else
-            gemv_t_only(p, P, y32, ws, s);
-    }
-    step_size_kernel<<<1, kStepThreads, 0, s>>>(st, at<float>(ws, p.o_z), (O.alpha > 0.0) ? 0 : T, P->gamma,
-                                                O.power_safety, O.alpha);
-    launch_init_x(p, P, &O, d_x0, ws, s);
-    auto save_cp = [&](int c) -> int {
-        MV_CUDA_TRY(cudaMemcpyAsync(at<SolveState>(ws, b.o_cp_state) + c, st, sizeof(SolveState),
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(at<double>(ws, b.o_cp_x) + (size_t)c * n, at<double>(ws, p.o_x), 8 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(at<double>(ws, b.o_cp_y) + (size_t)c * n, at<double>(ws, p.o_y), 8 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(at<double>(ws, b.o_cp_gx) + (size_t)c * n, at<double>(ws, p.o_gx), 8 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(at<float>(ws, b.o_cp_y32) + (size_t)c * n, y32, 4 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        return MV_OK;
-    };
-    auto load_cp = [&](int c) -> int {
-        MV_CUDA_TRY(cudaMemcpyAsync(st, at<SolveState>(ws, b.o_cp_state) + c, sizeof(SolveState),
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(at<double>(ws, p.o_x), at<double>(ws, b.o_cp_x) + (size_t)c * n, 8 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(at<double>(ws, p.o_y), at<double>(ws, b.o_cp_y) + (size_t)c * n, 8 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(at<double>(ws, p.o_gx), at<double>(ws, b.o_cp_gx) + (size_t)c * n, 8 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        MV_CUDA_TRY(cudaMemcpyAsync(y32, at<float>(ws, b.o_cp_y32) + (size_t)c * n, 4 * (size_t)n,
-                                    cudaMemcpyDeviceToDevice, s));
-        return MV_OK;
-    };
-    int launches = 4;
-    const int per_it = p.use_llt ? 2 : 3;
-    for (int c = 0; c < b.ncp; ++c) {
-        MV_TRY(save_cp(c));
-        const int len = std::min(K, (c + 1) * C) - c * C;
-        if (len == C && O.use_graph) {               // a full segment: one cached graph
-            cudaGraphExec_t exec = nullptr;
-            MV_TRY(get_chunk_graph(p, P, &O, ws, C, nullptr, &exec));
-            MV_CUDA_TRY(cudaGraphLaunch(exec, s));
-        } else {
-            for (int j = 0; j < len; ++j) MV_TRY(launch_iteration(p, P, &O, ws, s, nullptr));
-        }
-        launches += per_it * len;
-    }
-    MV_CUDA_TRY(cudaGetLastError());
-    SolveState hs{};
-    MV_CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
-    MV_CUDA_TRY(cudaStreamSynchronize(s));
-    if (hs.status != MV_OK && hs.status != MV_ERR_NOT_CONVERGED) {
-        *h_info = mv_solve_info{};
-        h_info->status = hs.status;
-        return hs.status;
-    }
-    const double alpha = hs.alpha;
-    // FISTA betas, the same recurrence in FP64 as the step kernel.
-    std::vector<double> beta(K);
-    {
-        double t = 1.0;
-        for (int k = 0; k < K; ++k) {
-            const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
-            beta[k] = (t - 1.0) / tn;
-            t = tn;
-        }
-    }
-
-    // ---- reverse sweep, segment by segment
-    double *xbar = at<double>(ws, b.o_xbar), *ybar = at<double>(ws, b.o_ybar), *mubar = at<double>(ws, b.o_mubar);
-    double *vbar = at<double>(ws, b.o_vbar);
-    float *VY = at<float>(ws, b.o_vy), *ZW = at<float>(ws, b.o_zw);
-    double *X1 = at<double>(ws, b.o_x1), *NU = at<double>(ws, b.o_nu);
-    MV_CUDA_TRY(cudaMemcpyAsync(xbar, d_dloss_dx, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    MV_CUDA_TRY(cudaMemsetAsync(ybar, 0, 8 * (size_t)n, s));
-    MV_CUDA_TRY(cudaMemsetAsync(mubar, 0, 8 * (size_t)n, s));
-    MV_CUDA_TRY(cudaMemset2DAsync(d_dL, 4 * (size_t)ldD, 0, 4 * (size_t)T, (size_t)n, s));
-    double *betas = at<double>(ws, b.o_betas);
-    int *k0d = at<int>(ws, b.o_k0);
-    MV_CUDA_TRY(cudaMemcpyAsync(betas, beta.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, s));
-    std::vector<int> k0s(b.ncp);
-    for (int seg = 0; seg < b.ncp; ++seg) k0s[seg] = seg * C;
-    // recompute a segment forward from its checkpoint, recording y_k, z_k, x_{k+1}, nu_k
-    auto recompute = [&](cudaStream_t cs, int len) -> int {
-        for (int j = 0; j < len; ++j) {
-            MV_CUDA_TRY(cudaMemcpyAsync(VY + (size_t)(len + j) * n, y32, 4 * (size_t)n, cudaMemcpyDeviceToDevice, cs));
-            MV_TRY(launch_iteration(p, P, &O, ws, cs, nullptr));
-            MV_CUDA_TRY(cudaMemcpyAsync(ZW + (size_t)j * T, at<float>(ws, p.o_z), 4 * (size_t)T,
-                                        cudaMemcpyDeviceToDevice, cs));
-            MV_CUDA_TRY(cudaMemcpyAsync(X1 + (size_t)j * n, at<double>(ws, p.o_x), 8 * (size_t)n,
-                                        cudaMemcpyDeviceToDevice, cs));
-            MV_CUDA_TRY(cudaMemcpyAsync(NU + j, &st->nu, 8, cudaMemcpyDeviceToDevice, cs));
-        }
-        return MV_OK;
-    };
-    // backward through the segment (iteration k0 + j, j = len - 1 .. 0)
-    auto reverse = [&](cudaStream_t cs, int len) -> int {
-        for (int j = len - 1; j >= 0; --j) {
-            AdjArgs a;
-            a.x1 = X1 + (size_t)j * n;
-            a.nu_tape = NU;
-            a.betas = betas;
-            a.k0 = k0d;
-            a.j = j;
-            a.eq = P->mode == MV_RETURN_EQ ? 1 : 0;
-            a.xbar = xbar;
-            a.ybar = ybar;
-            a.mubar = mubar;
-            a.vbar = vbar;
-            a.vbar32 = y32;
-            a.vrec = VY + (size_t)j * n;
-            a.mu = P->mu;
-            a.n = n;
-            MV_CUDA_TRY(launch_adj_proj(p.cl, a, cs));
-            // w = L^T v_bar (z buffer) and L w
-            if (p.use_llt)
-                MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), nullptr, cs, at<float>(ws, p.o_z)));
-            else
-                gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), cs);
-            MV_CUDA_TRY(cudaMemcpyAsync(ZW + (size_t)(len + j) * T, at<float>(ws, p.o_z), 4 * (size_t)T,
-                                        cudaMemcpyDeviceToDevice, cs));
-            adj_finish_kernel<<<(n + 255) / 256, 256, 0, cs>>>(vbar, at<double>(ws, p.o_gy), alpha, P->gamma, ybar, n);
-        }
-        return cudaGetLastError() == cudaSuccess ? MV_OK : MV_ERR_CUDA;
-    };
-    for (int seg = b.ncp - 1; seg >= 0; --seg) {
-        const int k0 = seg * C, k1 = std::min(K, k0 + C), len = k1 - k0;
-        MV_TRY(load_cp(seg));
-        MV_CUDA_TRY(cudaMemcpyAsync(k0d, &k0s[seg], sizeof(int), cudaMemcpyHostToDevice, s));
-        if (len == C && O.use_graph) {                // full segments replay two cached graphs
-            GraphKey kr = graph_key(p, P, &O, -1000000 - C, nullptr), kb = graph_key(p, P, &O, -2000000 - C, nullptr);
-            kr.ws = kb.ws = ws;
-            kb.aux = alpha;                           // adj_finish bakes the step in
-            cudaGraphExec_t er = nullptr, eb = nullptr;
-            MV_TRY(cached_graph(kr, [&](cudaStream_t cs) { return recompute(cs, C); }, &er));
-            MV_TRY(cached_graph(kb, [&](cudaStream_t cs) { return reverse(cs, C); }, &eb));
-            MV_CUDA_TRY(cudaGraphLaunch(er, s));
-            MV_CUDA_TRY(cudaGraphLaunch(eb, s));
-        } else {
-            MV_TRY(recompute(s, len));
-            MV_TRY(reverse(s, len));
-        }
-        launches += len * (per_it + 4);
-        // dL += -2 alpha (V Z^T + Y W^T) over the segment: one tcgen05 GEMM.
-        MV_TRY(adjoint_dl_update(b, n, T, len, VY, ZW, alpha, ws, d_dL, ldD, s));
-    }
-    MV_CUDA_TRY(cudaMemcpyAsync(d_dmu, mubar, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s));
-    int xerr = 0, gerr = 0;
-    MV_CUDA_TRY(cudaMemcpyAsync(&xerr, at<int>(ws, p.o_err), sizeof(int), cudaMemcpyDeviceToHost, s));
-    MV_CUDA_TRY(cudaMemcpyFromSymbolAsync(&gerr, g_gemm_err, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
-    MV_CUDA_TRY(cudaStreamSynchronize(s));
-    MV_CUDA_TRY(cudaGetLastError());
-    if (gerr != 0) {
-        *h_info = mv_solve_info{};
-        h_info->status = record_message(MV_ERR_TIMEOUT, "mv_npga_backward: the dL GEMM pipeline wait timed out");
-        return h_info->status;
-    }
-    if (xerr != 0) {
-        char msg[96];
-        snprintf(msg, sizeof(msg), "mv_npga_backward: a bounded wait of the fused pass timed out (code %d)", xerr);
-        *h_info = mv_solve_info{};
-        h_info->status = record_message(MV_ERR_TIMEOUT, msg);
-        return h_info->status;
-    }
-    *h_info = mv_solve_info{};
-    h_info->iterations = K;
-    h_info->status = MV_OK;
-    h_info->alpha = alpha;
-    h_info->lambda_hat = hs.lambda_hat;
-    h_info->kkt = hs.kkt;
-    h_info->launches = launches;
-    return MV_OK;
 }
 
 }  // extern "C"
@@ -2995,86 +1918,3 @@ int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const 
 
 }  // extern "C"
 
-// ---------------------------------------------------------------------------
-// Allocation-free gradient: mv_gradient with its scratch in a fixed device
-// array rather than a caller workspace, for callers that may not allocate
-// device memory (they only receive input and output buffers from a host
-// framework that owns the memory pool, or cannot pay cudaMalloc's implicit
-// synchronisation in a latency-bound loop).
-namespace mv {
-
-static __device__ __align__(256) unsigned char g_noalloc_scratch[MV_NOALLOC_SCRATCH_BYTES];
-
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_addr[128];   // device address of the array, per device ordinal
-
-// The host-side name of the array is only a stand-in, so its device address
-// is looked up with the device current.  A call outside stream capture looks
-// it up every time (cheap once the module is loaded), so the address stays
-// right after a device reset, which reloads the module at a new address.
-// Inside a capture no look-up is made and the device's last address is used.
-static int noalloc_scratch(cudaStream_t s, void **out) {
-    int dev = 0;
-    MV_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) return record_message(MV_ERR_UNSUPPORTED, "mv_gradient_noalloc: device ordinal >= 128");
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    MV_CUDA_TRY(cudaStreamIsCapturing(s, &cap));
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (cap == cudaStreamCaptureStatusNone) {
-        void *p = nullptr;
-        MV_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = p;
-    } else if (g_noalloc_addr[dev] == nullptr) {
-        return record_message(MV_ERR_UNSUPPORTED,
-                              "mv_gradient_noalloc: the first call on a device must come before stream capture");
-    }
-    *out = g_noalloc_addr[dev];
-    return MV_OK;
-}
-
-// The scratch this call needs: the plan of the two-pass GEMV path (its row
-// splits follow the device's SM count, so the figure is per device).
-static int noalloc_plan(const mv_problem *P, Plan *out) {
-    MV_TRY(validate_problem(P));
-    if (is_sigma(P)) return record_message(MV_ERR_UNSUPPORTED, "mv_gradient_noalloc: explicit Sigma is not supported");
-    *out = make_plan(P->dtype, P->n, P->T, P->ld, 0, false, is_tn(P));
-    return MV_OK;
-}
-
-}  // namespace mv
-
-extern "C" size_t mv_gradient_noalloc_scratch_size(const mv_problem *P) {
-    Plan p{};
-    return noalloc_plan(P, &p) == MV_OK ? p.total : 0;
-}
-
-extern "C" int mv_gradient_noalloc(const mv_problem *P, const double *d_y, float *d_z, double *d_g,
-                                   mv_stream_t stream) {
-    Plan p{};
-    MV_TRY(noalloc_plan(P, &p));
-    if (d_y == nullptr || d_g == nullptr) return MV_ERR_INVALID_ARG;
-    if (p.total > MV_NOALLOC_SCRATCH_BYTES) {
-        char msg[200];
-        snprintf(msg, sizeof(msg),
-                 "mv_gradient_noalloc: this problem needs %zu bytes of scratch; the fixed array holds %zu",
-                 p.total, (size_t)MV_NOALLOC_SCRATCH_BYTES);
-        return record_message(MV_ERR_UNSUPPORTED, msg);
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    void *ws = nullptr;
-    MV_TRY(noalloc_scratch(s, &ws));
-    MV_TRY(set_kernel_attrs());
-    (void)cudaGetLastError();
-    float *y32 = at<float>(ws, p.o_y32);
-    double *lz = at<double>(ws, p.o_gy);
-    // The array keeps the previous call's contents: the gemv tickets must start at zero.
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
-    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
-    to_y32_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(d_y, rs, y32, p.n);
-    gemv_pair(p, P, y32, ws, nullptr, lz, s);
-    grad_finish_kernel<<<(p.n + 255) / 256, 256, 0, s>>>(lz, d_y, P->gamma, d_g, p.n);
-    if (d_z) MV_CUDA_TRY(cudaMemcpyAsync(d_z, at<float>(ws, p.o_z), 4 * (size_t)p.T, cudaMemcpyDeviceToDevice, s));
-    MV_CUDA_TRY(cudaGetLastError());
-    return MV_OK;
-}

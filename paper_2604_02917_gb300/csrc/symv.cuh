@@ -100,7 +100,7 @@ __device__ __forceinline__ void symv_finish_block(const SymvArgs &a, int b, floa
     __syncthreads();                  // red is reused by a second finish
 }
 
-__global__ void __launch_bounds__(kSymThreads) symv_kernel(SymvArgs a) {
+static __global__ void __launch_bounds__(kSymThreads) symv_kernel(SymvArgs a) {
     if (a.done && *(volatile const int *)a.done) return;
     __shared__ float yI[kSymTile], yJ[kSymTile];
     __shared__ float colred[kSymThreads / kWarp][kSymTile];
