@@ -345,6 +345,23 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
                            const mv_solve_opts *opts, double *d_X, mv_solve_info *h_infos,
                            void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
+/*  The frontier with FP32 refinement (as mv_npga_solve_refined for one
+ *  target): phase 1 is mv_npga_solve_frontier on P_lo (BF16 or FP8) until
+ *  every target's KKT residual is <= eps_lo; phase 2 restarts every target
+ *  from its phase-1 answer (FISTA state reset, warm start) on the FP32 factor
+ *  P_hi (MV_LAYOUT_NT, same n, T, mu, gamma and mode), carried as the BF16
+ *  pair H = bf16(L), D = bf16(L - H) (which carries each entry of L to
+ *  2^-18 relative) and multiplied by both in every GEMM, with the phase-1
+ *  step divided by 1.01, until
+ *  each residual on the FP32 model is <= opts->eps.  h_infos: iterations =
+ *  both phases, refine_iterations = phase 2, kkt and objective of the FP32
+ *  model.  Workspace mv_frontier_refined_workspace_size (adds 4 n T bytes x 2
+ *  for H, D and their transposes).  Blocking. */
+size_t mv_frontier_refined_workspace_size(const mv_problem *P_lo, const mv_problem *P_hi, int64_t n_targets);
+int mv_npga_solve_frontier_refined(const mv_problem *P_lo, const mv_problem *P_hi, const double *d_R_targets,
+                                   int64_t n_targets, const mv_solve_opts *opts, double eps_lo, double *d_X,
+                                   mv_solve_info *h_infos, void *d_ws, size_t ws_bytes, mv_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * 3g. Batch of independent problems of uneven size (n_i, T_i all different).
  *

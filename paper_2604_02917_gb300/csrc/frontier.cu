@@ -207,6 +207,46 @@ __global__ void transpose_elem_kernel(const E *__restrict__ L, int n, int T, int
     }
 }
 
+// The FP32 factor as a BF16 pair: H = bf16(L), D = bf16(L - H), so that
+// H + D carries L to 2^-18 of each entry (n x T, row pitches ld and ldo).
+__global__ void hilo_kernel(const float *__restrict__ L, int n, int T, int64_t ld, __nv_bfloat16 *__restrict__ H,
+                            __nv_bfloat16 *__restrict__ D, int64_t ldo) {
+    const int64_t total = (int64_t)n * ldo;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / ldo), t = (int)(idx - (int64_t)i * ldo);
+        const float x = t < T ? L[(int64_t)i * ld + t] : 0.0f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(x);
+        H[idx] = h;
+        D[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+    }
+}
+
+// Restart of every unfinished target from its current x (the refinement
+// phase): y = x, t = 1, k = 0, the split operand rewritten from y (no row
+// scales: the refined model is the FP32 factor itself).  Targets whose first
+// phase failed (infeasible, numeric) keep their status.  One block per target.
+__global__ void frontier_warm_kernel(FState *fs, const double *__restrict__ X, double *__restrict__ Y, int n, int B,
+                                     __nv_bfloat16 *__restrict__ Ys, int64_t ldY) {
+    const int b = blockIdx.x;
+    const bool failed = fs[b].status == MV_ERR_INFEASIBLE || fs[b].status == MV_ERR_NUMERIC;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double x = X[(int64_t)b * n + i];
+        Y[(int64_t)b * n + i] = x;
+        write_split(Ys, ldY, B, b, i, x, nullptr);
+    }
+    if (threadIdx.x == 0 && !failed) {
+        FState &f = fs[b];
+        f.k = 0;
+        f.done = 0;
+        f.converged = 0;
+        f.status = MV_OK;
+        f.t = 1.0;
+        f.beta_prev = 0.0;
+        f.kkt = INFINITY;
+    }
+}
+
 // Rows of X (B x n, FP64) -> the BF16 hi/lo operand rows (2B x ldY).
 __global__ void split_rows_kernel(const double *__restrict__ X, int B, int n, __nv_bfloat16 *__restrict__ Ys,
                                   int64_t ldY, const float *__restrict__ rs) {
@@ -277,6 +317,9 @@ static int frontier_attrs() {
         ok = ok && gemm_set_attrs<64, kEpiF32>() == MV_OK && gemm_set_attrs<128, kEpiF32>() == MV_OK &&
              gemm_set_attrs<256, kEpiF32>() == MV_OK && gemm_set_attrs<64, kEpiPairSplitT>() == MV_OK &&
              gemm_set_attrs<128, kEpiPairSplitT>() == MV_OK && gemm_set_attrs<256, kEpiPairSplitT>() == MV_OK;
+        ok = ok && gemm_set_attrs<64, kEpiF32, 2>() == MV_OK && gemm_set_attrs<128, kEpiF32, 2>() == MV_OK &&
+             gemm_set_attrs<256, kEpiF32, 2>() == MV_OK && gemm_set_attrs<64, kEpiPairSplitT, 2>() == MV_OK &&
+             gemm_set_attrs<128, kEpiPairSplitT, 2>() == MV_OK && gemm_set_attrs<256, kEpiPairSplitT, 2>() == MV_OK;
         ok = ok && gemm_q8_set_attrs<64, kEpiF32>() == MV_OK && gemm_q8_set_attrs<128, kEpiF32>() == MV_OK &&
              gemm_q8_set_attrs<256, kEpiF32>() == MV_OK && gemm_q8_set_attrs<64, kEpiPairSplitT>() == MV_OK &&
              gemm_q8_set_attrs<128, kEpiPairSplitT>() == MV_OK && gemm_q8_set_attrs<256, kEpiPairSplitT>() == MV_OK;
@@ -290,10 +333,14 @@ struct FPlan {
     int BN;         // 2B: GEMM tile width
     int splits;     // K-splits of G = L Z (43 row tiles at n = 5440 would leave SMs idle)
     int64_t ldLt, ldY, ldZ;
-    size_t o_lt, o_y, o_z, o_g, o_x, o_yd, o_gx, o_fs, o_rt, o_gpart, o_gtick, total;
+    size_t o_lt, o_y, o_z, o_g, o_x, o_yd, o_gx, o_fs, o_rt, o_gpart, o_gtick;
+    // FP32 refinement: BF16 hi and lo parts of the FP32 factor, n x ldH, and their transposes
+    int64_t ldH;
+    size_t o_h, o_d, o_ht, o_dt;
+    size_t total;
 };
 
-static FPlan make_fplan(const Plan &p, int64_t nb) {
+static FPlan make_fplan(const Plan &p, int64_t nb, bool refine = false) {
     FPlan f{};
     f.B = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
     f.BN = 2 * f.B;
@@ -318,6 +365,13 @@ static FPlan make_fplan(const Plan &p, int64_t nb) {
     f.splits = gemm_splits(p.n, f.BN, p.T, f.BN, sm_count());
     f.o_gpart = take(4 * (size_t)f.splits * p.n * f.BN);
     f.o_gtick = take(4 * (size_t)((p.n + kBM - 1) / kBM) + 64);
+    f.ldH = ((int64_t)p.T + 7) / 8 * 8;
+    if (refine) {
+        f.o_h = take(2 * (size_t)p.n * f.ldH);
+        f.o_d = take(2 * (size_t)p.n * f.ldH);
+        f.o_ht = take(2 * (size_t)p.T * f.ldLt);
+        f.o_dt = take(2 * (size_t)p.T * f.ldLt);
+    }
     f.total = off;
     return f;
 }
@@ -339,15 +393,44 @@ static void frontier_gemms(const CUtensorMap &tLt, const CUtensorMap &tY, const 
                              gtick);
 }
 
-static void frontier_gemm_pair(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
+// The FP32-accurate pair: A = hi + lo (maps[0] + maps[4] for L^T, maps[2] + maps[5] for L).
+template <int BN>
+static void frontier_gemms2(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
+    gemm_launch<BN, kEpiPairSplitT, 2>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, at<__nv_bfloat16>(ws, f.o_z),
+                                       f.ldZ, s, 1, nullptr, nullptr, 1.0f, &maps[4]);
+    gemm_launch<BN, kEpiF32, 2>(maps[2], maps[3], p.n, f.BN, p.T, at<float>(ws, f.o_g), f.BN, nullptr, 0, s, f.splits,
+                                at<float>(ws, f.o_gpart), at<unsigned>(ws, f.o_gtick), 1.0f, &maps[5]);
+}
+
+static void frontier_gemm_pair(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s,
+                               bool two = false) {
+    if (two) {
+        if (f.BN == 64) frontier_gemms2<64>(maps, p, f, ws, s);
+        else if (f.BN == 128) frontier_gemms2<128>(maps, p, f, ws, s);
+        else frontier_gemms2<256>(maps, p, f, ws, s);
+        return;
+    }
     if (f.BN == 64) frontier_gemms<64>(maps[0], maps[1], maps[2], maps[3], p, f, ws, s);
     else if (f.BN == 128) frontier_gemms<128>(maps[0], maps[1], maps[2], maps[3], p, f, ws, s);
     else frontier_gemms<256>(maps[0], maps[1], maps[2], maps[3], p, f, ws, s);
 }
 
 // L^T X for the objectives, X already written as the split operand.
-static void frontier_ltx(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s) {
+static void frontier_ltx(const CUtensorMap *maps, const Plan &p, const FPlan &f, void *ws, cudaStream_t s,
+                         bool two = false) {
     __nv_bfloat16 *Zt = at<__nv_bfloat16>(ws, f.o_z);
+    if (two) {
+        if (f.BN == 64)
+            gemm_launch<64, kEpiPairSplitT, 2>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s, 1, nullptr,
+                                               nullptr, 1.0f, &maps[4]);
+        else if (f.BN == 128)
+            gemm_launch<128, kEpiPairSplitT, 2>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s, 1,
+                                                nullptr, nullptr, 1.0f, &maps[4]);
+        else
+            gemm_launch<256, kEpiPairSplitT, 2>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s, 1,
+                                                nullptr, nullptr, 1.0f, &maps[4]);
+        return;
+    }
     if (p.dt == MV_FP8_E4M3) {
         if (f.BN == 64) gemm_q8_launch<64, kEpiPairSplitT>(maps[0], maps[1], p.T, f.BN, p.n, nullptr, 0, Zt, f.ldZ, s);
         else if (f.BN == 128)
@@ -362,37 +445,39 @@ static void frontier_ltx(const CUtensorMap *maps, const Plan &p, const FPlan &f,
 
 }  // namespace mv
 
-extern "C" {
+namespace mv {
 
-size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets) {
-    if (validate_problem(P) != MV_OK || P->layout != MV_LAYOUT_NT || P->dtype == MV_F32 || n_targets < 1 ||
-        n_targets > 128)
-        return 0;
-    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
-    return make_fplan(p, n_targets).total;
-}
-
-int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64_t n_targets,
-                           const mv_solve_opts *O_in, double *d_X, mv_solve_info *h_infos, void *d_ws, size_t ws_bytes,
-                           mv_stream_t stream) {
+// The frontier solve; with P_hi (the FP32 factor, MV_LAYOUT_NT) a second
+// phase continues every target from the first phase's answer on the BF16
+// hi + lo pair of P_hi (FP32-accurate products) to opts->eps, after the
+// first phase on P (BF16 or FP8) has stopped at eps_lo.
+static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const double *d_R_targets, int64_t n_targets,
+                          const mv_solve_opts *O_in, double eps_lo, double *d_X, mv_solve_info *h_infos, void *d_ws,
+                          size_t ws_bytes, cudaStream_t s) {
     MV_TRY(validate_problem(P));
     MV_TRY(require_nt(P, "frontier solve"));
     if (P->dtype == MV_F32)
         return record_message(MV_ERR_UNSUPPORTED, "frontier solve: L must be BF16 or FP8 (the tensor-core operand)");
     if (d_R_targets == nullptr || d_X == nullptr || h_infos == nullptr || n_targets < 1 || n_targets > 128)
         return MV_ERR_INVALID_ARG;
+    if (P_hi) {
+        MV_TRY(validate_problem(P_hi));
+        MV_TRY(require_nt(P_hi, "frontier refinement"));
+        if (P_hi->dtype != MV_F32 || P_hi->n != P->n || P_hi->T != P->T || P_hi->mu != P->mu ||
+            P_hi->gamma != P->gamma || P_hi->mode != P->mode || !(eps_lo >= 0.0))
+            return MV_ERR_INVALID_ARG;
+    }
     mv_solve_opts O;
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
     if (O.momentum != 0 || O.backtrack != 0)
         return record_message(MV_ERR_UNSUPPORTED, "frontier solve: fixed step and FISTA momentum only");
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);   // power method: fused pass
-    const FPlan f = make_fplan(p, n_targets);
+    const FPlan f = make_fplan(p, n_targets, P_hi != nullptr);
     MV_TRY(check_ws(d_ws, ws_bytes, f.total));
     MV_TRY(set_kernel_attrs());
     MV_TRY(frontier_attrs());
     (void)cudaGetLastError();
-    cudaStream_t s = (cudaStream_t)stream;
     SolveState *st = at<SolveState>(d_ws, p.o_state);
     float *y32 = at<float>(d_ws, p.o_y32);
     const int B = f.B, nt = (int)n_targets;
@@ -452,10 +537,10 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     a.kkt_every = O.kkt_every;
     a.max_iter = O.max_iter;
     a.gamma = P->gamma;
-    a.eps = O.eps;
+    a.eps = P_hi ? eps_lo : O.eps;
     MV_CUDA_TRY(launch_frontier(true, p.cl, a, s));
 
-    CUtensorMap maps[4];
+    CUtensorMap maps[6];
     if (P->dtype == MV_FP8_E4M3) {
         MV_TRY(make_map_u8(&maps[0], at<void>(d_ws, f.o_lt), p.T, p.n, f.ldLt, kBM));
         MV_TRY(make_map_u8(&maps[2], P->L, p.n, p.T, P->ld, kBM));
@@ -470,46 +555,90 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
 
     const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
     int launches = 3 + 3 * O.power_iters + 1 + 2;
-    cudaGraphExec_t exec = nullptr;
-    if (O.use_graph) {
-        cudaStream_t cs;
-        MV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph;
-        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            for (int c = 0; c < chunk; ++c) {
-                frontier_gemm_pair(maps, p, f, d_ws, cs);
-                launch_frontier(false, p.cl, a, cs);
-            }
-            if (cudaStreamEndCapture(cs, &graph) == cudaSuccess) {
-                if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
-                cudaGraphDestroy(graph);
-            }
-        }
-        cudaStreamDestroy(cs);
-        (void)cudaGetLastError();
-    }
     std::vector<FState> hf(B);
-    const int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
-    for (int64_t c = 0; c < max_chunks; ++c) {
-        if (exec) {
-            MV_CUDA_TRY(cudaGraphLaunch(exec, s));
-        } else {
-            for (int i = 0; i < chunk; ++i) {
-                frontier_gemm_pair(maps, p, f, d_ws, s);
-                MV_CUDA_TRY(launch_frontier(false, p.cl, a, s));
+    // One phase: chunks of kkt_every iterations (a cached-per-call graph) until every target is done.
+    auto run_phase = [&](const CUtensorMap *mp, bool two) -> int {
+        cudaGraphExec_t exec = nullptr;
+        if (O.use_graph) {
+            cudaStream_t cs;
+            MV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaGraph_t graph;
+            if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                for (int c = 0; c < chunk; ++c) {
+                    frontier_gemm_pair(mp, p, f, d_ws, cs, two);
+                    launch_frontier(false, p.cl, a, cs);
+                }
+                if (cudaStreamEndCapture(cs, &graph) == cudaSuccess) {
+                    if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+                    cudaGraphDestroy(graph);
+                }
             }
+            cudaStreamDestroy(cs);
+            (void)cudaGetLastError();
         }
-        launches += 3 * chunk;
-        MV_CUDA_TRY(cudaMemcpyAsync(hf.data(), a.fs, sizeof(FState) * B, cudaMemcpyDeviceToHost, s));
+        const int64_t max_chunks = ((int64_t)O.max_iter + 1 + chunk - 1) / chunk + 1;
+        int st_ = MV_OK;
+        for (int64_t c = 0; c < max_chunks; ++c) {
+            if (exec) {
+                if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+                    st_ = record_cuda_error(cudaGetLastError(), "cudaGraphLaunch", __FILE__, __LINE__);
+                    break;
+                }
+            } else {
+                for (int i = 0; i < chunk; ++i) {
+                    frontier_gemm_pair(mp, p, f, d_ws, s, two);
+                    launch_frontier(false, p.cl, a, s);
+                }
+            }
+            launches += 3 * chunk;
+            if (cudaMemcpyAsync(hf.data(), a.fs, sizeof(FState) * B, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                st_ = record_cuda_error(cudaGetLastError(), "frontier loop", __FILE__, __LINE__);
+                break;
+            }
+            bool all = true;
+            for (int b = 0; b < nt; ++b) all = all && hf[b].done;
+            if (all) break;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        return st_;
+    };
+    MV_TRY(run_phase(maps, false));
+    std::vector<int> iters1(B);
+    for (int b = 0; b < B; ++b) iters1[b] = hf[b].k;
+    bool two = false;
+    if (P_hi) {
+        // Phase 2 on the FP32 factor: BF16 hi + lo pair and its transposes, a step 1 % smaller.
+        __nv_bfloat16 *H = at<__nv_bfloat16>(d_ws, f.o_h), *D = at<__nv_bfloat16>(d_ws, f.o_d);
+        __nv_bfloat16 *Ht = at<__nv_bfloat16>(d_ws, f.o_ht), *Dt = at<__nv_bfloat16>(d_ws, f.o_dt);
+        hilo_kernel<<<152 * 8, 256, 0, s>>>(reinterpret_cast<const float *>(P_hi->L), p.n, p.T, P_hi->ld, H, D, f.ldH);
+        transpose_elem_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, s>>>(H, p.n, p.T, f.ldH, Ht, f.ldLt);
+        transpose_elem_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, s>>>(D, p.n, p.T, f.ldH, Dt, f.ldLt);
+        CUtensorMap m2[6];
+        MV_TRY(make_map_bf16(&m2[0], Ht, p.T, p.n, f.ldLt, kBM));
+        MV_TRY(make_map_bf16(&m2[4], Dt, p.T, p.n, f.ldLt, kBM));
+        MV_TRY(make_map_bf16(&m2[2], H, p.n, p.T, f.ldH, kBM));
+        MV_TRY(make_map_bf16(&m2[5], D, p.n, p.T, f.ldH, kBM));
+        m2[1] = maps[1];
+        m2[3] = maps[3];
+        SolveState hs1{};
+        MV_CUDA_TRY(cudaMemcpyAsync(&hs1, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
         MV_CUDA_TRY(cudaStreamSynchronize(s));
-        bool all = true;
-        for (int b = 0; b < nt; ++b) all = all && hf[b].done;
-        if (all) break;
+        const double alpha2 = hs1.alpha / 1.01;
+        MV_CUDA_TRY(cudaMemcpyAsync(&st->alpha, &alpha2, sizeof(double), cudaMemcpyHostToDevice, s));
+        frontier_warm_kernel<<<B, 256, 0, s>>>(a.fs, a.X, a.Y, p.n, B, a.Ysplit, a.ldY);
+        MV_CUDA_TRY(cudaGetLastError());
+        a.row_scale = nullptr;
+        a.eps = O.eps;
+        for (int i = 0; i < 6; ++i) maps[i] = m2[i];
+        two = true;
+        launches += 4;
+        MV_TRY(run_phase(maps, true));
     }
-    if (exec) cudaGraphExecDestroy(exec);
     // Objectives: one more L^T X product with X written as the split operand.
-    split_rows_kernel<<<(unsigned)((B * (int64_t)p.n + 255) / 256), 256, 0, s>>>(a.X, B, p.n, a.Ysplit, f.ldY, rs);
-    frontier_ltx(maps, p, f, d_ws, s);
+    split_rows_kernel<<<(unsigned)((B * (int64_t)p.n + 255) / 256), 256, 0, s>>>(a.X, B, p.n, a.Ysplit, f.ldY,
+                                                                               a.row_scale);
+    frontier_ltx(maps, p, f, d_ws, s, two);
     frontier_objective_kernel<<<B, kStepThreads, 0, s>>>(at<__nv_bfloat16>(d_ws, f.o_z), f.ldZ, B, p.T, a.X, p.n,
                                                          P->gamma, a.fs);
     launches += 3;
@@ -527,7 +656,8 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     for (int b = 0; b < nt; ++b) {
         mv_solve_info &I = h_infos[b];
         I = mv_solve_info{};
-        I.iterations = hf[b].k;
+        I.iterations = P_hi ? iters1[b] + hf[b].k : hf[b].k;
+        I.refine_iterations = P_hi ? hf[b].k : 0;
         I.status = hf[b].done ? hf[b].status : MV_ERR_NOT_CONVERGED;
         I.converged = hf[b].converged;
         I.proj_failures = hf[b].proj_fail;
@@ -543,5 +673,39 @@ int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64
     return worst;
 }
 
-}  // extern "C"
+}  // namespace mv
 
+extern "C" {
+
+size_t mv_frontier_workspace_size(const mv_problem *P, int64_t n_targets) {
+    if (validate_problem(P) != MV_OK || P->layout != MV_LAYOUT_NT || P->dtype == MV_F32 || n_targets < 1 ||
+        n_targets > 128)
+        return 0;
+    const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);
+    return make_fplan(p, n_targets).total;
+}
+
+int mv_npga_solve_frontier(const mv_problem *P, const double *d_R_targets, int64_t n_targets,
+                           const mv_solve_opts *O_in, double *d_X, mv_solve_info *h_infos, void *d_ws, size_t ws_bytes,
+                           mv_stream_t stream) {
+    return frontier_solve(P, nullptr, d_R_targets, n_targets, O_in, 0.0, d_X, h_infos, d_ws, ws_bytes,
+                          (cudaStream_t)stream);
+}
+
+size_t mv_frontier_refined_workspace_size(const mv_problem *P_lo, const mv_problem *P_hi, int64_t n_targets) {
+    if (mv_frontier_workspace_size(P_lo, n_targets) == 0 || validate_problem(P_hi) != MV_OK ||
+        P_hi->dtype != MV_F32 || P_hi->layout != MV_LAYOUT_NT)
+        return 0;
+    const Plan p = make_plan(P_lo->dtype, P_lo->n, P_lo->T, P_lo->ld, 0, true);
+    return make_fplan(p, n_targets, true).total;
+}
+
+int mv_npga_solve_frontier_refined(const mv_problem *P_lo, const mv_problem *P_hi, const double *d_R_targets,
+                                   int64_t n_targets, const mv_solve_opts *O_in, double eps_lo, double *d_X,
+                                   mv_solve_info *h_infos, void *d_ws, size_t ws_bytes, mv_stream_t stream) {
+    if (P_hi == nullptr) return MV_ERR_INVALID_ARG;
+    return frontier_solve(P_lo, P_hi, d_R_targets, n_targets, O_in, eps_lo, d_X, h_infos, d_ws, ws_bytes,
+                          (cudaStream_t)stream);
+}
+
+}  // extern "C"

@@ -11,7 +11,9 @@
 // The only library call is the symmetric eigensolver (cuSOLVER DSYEVD,
 // loaded at run time) on the small b x b Rayleigh--Ritz matrices.
 //
-// Algorithm (block size b = 2k, at least k + 64, rounded up to 64):
+// Algorithm (block size b = max(2k, k + 512), rounded up to 64: the cut sits
+// halfway down the unwanted part of the block, and a flat spectrum needs that
+// part wide for the filter to separate the wanted eigenvalues):
 //   1. K = tilde L tilde L^T (n x n FP32).
 //   2. Q = orth(K^2 G), G an n x b Gaussian block.
 //   3. Rayleigh--Ritz: the eigenvalues theta of Q^T K Q (b x b, FP32) give
@@ -277,7 +279,7 @@ static int topk_plan(int64_t n, int64_t m, int64_t k, TopkPlan *p) {
     p->n = n;
     p->m = m;
     p->k = k;
-    p->b = r64(std::max<int64_t>(2 * k, k + 64));
+    p->b = r64(std::max<int64_t>(2 * k, k + 512));
     p->direct = n <= 1024 || p->b >= n;
     if (p->direct) p->b = n;
     p->Wm = r64(m);

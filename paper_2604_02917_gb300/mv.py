@@ -38,7 +38,7 @@ EXPORTS = [
     "mv_center_factor_host", "mv_batch_tiles", "mv_str_truncate_knee", "mv_sigma_workspace_size",
     "mv_sigma_form", "mv_countsketch_workspace_size", "mv_countsketch", "mv_gradient_noalloc_scratch_size",
     "mv_sketch_workspace_size", "mv_sketch_dtype", "mv_gaussian_sketch", "mv_countsketch_draw",
-    "mv_sketch_str_workspace_size",
+    "mv_sketch_str_workspace_size", "mv_frontier_refined_workspace_size", "mv_npga_solve_frontier_refined",
 ]
 
 # Size of the library's fixed scratch array used by mv_gradient_noalloc.
@@ -163,6 +163,11 @@ def lib():
         L.mv_npga_solve_frontier.restype = i32
         L.mv_npga_solve_frontier.argtypes = [C.POINTER(Problem), vp, i64, C.POINTER(SolveOpts), vp,
                                              C.POINTER(SolveInfo), vp, sz, vp]
+        L.mv_frontier_refined_workspace_size.restype = sz
+        L.mv_frontier_refined_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(Problem), i64]
+        L.mv_npga_solve_frontier_refined.restype = i32
+        L.mv_npga_solve_frontier_refined.argtypes = [C.POINTER(Problem), C.POINTER(Problem), vp, i64,
+                                                     C.POINTER(SolveOpts), dbl, vp, C.POINTER(SolveInfo), vp, sz, vp]
         L.mv_backward_workspace_size.restype = sz
         L.mv_backward_workspace_size.argtypes = [C.POINTER(Problem), C.POINTER(SolveOpts)]
         L.mv_npga_backward.restype = i32
@@ -639,16 +644,23 @@ def str_truncate(L_sketch: torch.Tensor, k: int, gamma: float = -1.0, trace_sigm
 
 class FrontierSolver:
     """Batched NPGA over many targets sharing one BF16 factor, or an FP8 factor
-    with its row scales (mv_npga_solve_frontier); reuses the workspace."""
+    with its row scales (mv_npga_solve_frontier); reuses the workspace.  With
+    ``L_f32`` (the FP32 factor, n x ld) the solve is refined on it after the
+    low-precision phase stops at ``eps_lo`` (mv_npga_solve_frontier_refined)."""
 
     def __init__(self, L_bf16, mu, R_targets, T, gamma=0.0, mode="ge", power_start=None, dtype="bf16",
-                 row_scale=None, **opts):
+                 row_scale=None, L_f32=None, eps_lo=1e-5, **opts):
         self.Rt = torch.as_tensor(R_targets, dtype=torch.float64).reshape(-1).to(L_bf16.device)
-        self._keep = (L_bf16, mu, power_start, row_scale)
+        self._keep = (L_bf16, mu, power_start, row_scale, L_f32)
         self.problem = make_problem(L_bf16, mu, 0.0, T, gamma, dtype, row_scale, mode, power_start)
+        self.p_hi = None if L_f32 is None else make_problem(L_f32, mu, 0.0, T, gamma, "f32", None, mode, power_start)
+        self.eps_lo = float(eps_lo)
         self.opts = solve_opts(**opts)
         self.nt = self.Rt.numel()
-        nb = lib().mv_frontier_workspace_size(C.byref(self.problem), self.nt)
+        if self.p_hi is None:
+            nb = lib().mv_frontier_workspace_size(C.byref(self.problem), self.nt)
+        else:
+            nb = lib().mv_frontier_refined_workspace_size(C.byref(self.problem), C.byref(self.p_hi), self.nt)
         if nb == 0:
             raise MvError(MV_ERR_INVALID_ARG, "mv_frontier_workspace_size")
         self.ws = _workspace(nb, L_bf16.device)
@@ -656,9 +668,15 @@ class FrontierSolver:
 
     def solve(self, allow=(MV_ERR_NOT_CONVERGED,)):
         infos = (SolveInfo * self.nt)()
-        st = lib().mv_npga_solve_frontier(C.byref(self.problem), _ptr(self.Rt), self.nt, C.byref(self.opts),
-                                          _ptr(self.X), infos, _ptr(self.ws), self.ws.numel(), _stream())
-        _check(st, "mv_npga_solve_frontier", allow)
+        if self.p_hi is None:
+            st = lib().mv_npga_solve_frontier(C.byref(self.problem), _ptr(self.Rt), self.nt, C.byref(self.opts),
+                                              _ptr(self.X), infos, _ptr(self.ws), self.ws.numel(), _stream())
+            _check(st, "mv_npga_solve_frontier", allow)
+        else:
+            st = lib().mv_npga_solve_frontier_refined(C.byref(self.problem), C.byref(self.p_hi), _ptr(self.Rt),
+                                                      self.nt, C.byref(self.opts), self.eps_lo, _ptr(self.X), infos,
+                                                      _ptr(self.ws), self.ws.numel(), _stream())
+            _check(st, "mv_npga_solve_frontier_refined", allow)
         return self.X, [i.as_dict() for i in infos]
 
 

@@ -99,7 +99,11 @@ def test_countsketch_rejects_bad_bucket(mv):
 
 def test_countsketch_full_size_and_str(mv):
     """5440 x 48374 FP32 L^T, m = 8192: sampled rows against the oracle, then
-    the FP64 truncation of this sketch (sigma^2 are eigenvalues of tilde L tilde L^T)."""
+    the truncation of this sketch: sigma^2 are the top eigenvalues of
+    tilde L tilde L^T within 1e-5 sigma_1^2, the STR tests' tolerance (the
+    truncation forms the Gram matrix from three-piece BF16 products to FP32
+    accuracy, about 1e-6 sigma_1^2 on the eigenvalues, and solves its small
+    Rayleigh--Ritz problem in FP64)."""
     n, T, m = 5440, 48374, 8192
     R = gpu(factor_returns(CFG_FULL, np.float32))
     Lt, _, _, _ = mv.center_factor(R, "f32", layout="tn")
@@ -115,7 +119,7 @@ def test_countsketch_full_size_and_str(mv):
     K = out[:, :m].double().cpu().numpy()
     lam = np.sort(np.linalg.eigvalsh(K @ K.T))[::-1][:64]
     s = sigma.cpu().numpy()
-    assert np.max(np.abs(s ** 2 - lam)) <= 1e-6 * lam[0]
+    assert np.max(np.abs(s ** 2 - lam)) <= 1e-5 * lam[0]
 
 
 @pytest.mark.parametrize("layout", ["tn", "nt"])
