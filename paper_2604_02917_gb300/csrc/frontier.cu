@@ -341,13 +341,15 @@ struct FPlan {
 };
 
 static FPlan make_fplan(const Plan &p, int64_t nb, bool refine = false) {
+    // The power method runs on the transposed copy: its plan's scratch comes first too.
+    const Plan pt = make_plan(p.dt, p.n, p.T, (p.n + 15) / 16 * 16, 0, true, true);
     FPlan f{};
     f.B = nb <= 32 ? 32 : (nb <= 64 ? 64 : 128);
     f.BN = 2 * f.B;
     f.ldLt = (p.n + 15) / 16 * 16;                    // row pitch a multiple of 16 bytes for BF16 and FP8
     f.ldY = f.ldLt;
     f.ldZ = ((int64_t)p.T + 7) / 8 * 8;
-    size_t off = p.total;
+    size_t off = std::max(p.total, pt.total);
     auto take = [&](size_t bytes) {
         size_t o = off;
         off = align_up(off + bytes, 256);
@@ -488,25 +490,8 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
     for (int b = nt; b < B; ++b)
         MV_CUDA_TRY(cudaMemcpyAsync(Rt + b, d_R_targets + nt - 1, 8, cudaMemcpyDeviceToDevice, s));
 
-    // Shared step size from the power method on L (the single-problem GEMV path).
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_t), 0, 4 * (size_t)p.t_blocks, s));
-    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_tick_n), 0, 4 * (size_t)p.n_groups, s));
-    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
-    launch_setup(st, P->mu, P->power_start, rs, y32, p.n, s);
-    if (p.use_llt) {
-        MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
-        MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
-    }
-    for (int it = 0; it < O.power_iters; ++it) {
-        if (p.use_llt)
-            MV_TRY(launch_llt(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), at<float>(d_ws, p.o_g32), s));
-        else
-            gemv_pair(p, P, y32, d_ws, nullptr, at<double>(d_ws, p.o_gy), s, at<float>(d_ws, p.o_g32));
-        launch_power_norm(at<float>(d_ws, p.o_g32), rs, y32, p.n, s);
-    }
-    if (O.power_iters > 0) gemv_t_only(p, P, y32, d_ws, s);
-    launch_step_size(st, at<float>(d_ws, p.o_z), (O.alpha > 0.0 || O.power_iters == 0) ? 0 : p.T, P->gamma,
-                     O.power_safety, O.alpha, s);
+    // L^T (T x n) once per call: the A operand of Z = L^T Y, and the stored
+    // layout in which the power method's fused pass streams fastest.
     const dim3 tgrid((unsigned)((p.T + 31) / 32), (unsigned)((p.n + 31) / 32));
     if (P->dtype == MV_FP8_E4M3)
         transpose_elem_kernel<uint8_t><<<tgrid, dim3(32, 8), 0, s>>>(
@@ -514,9 +499,40 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
     else
         transpose_elem_kernel<__nv_bfloat16><<<tgrid, dim3(32, 8), 0, s>>>(
             reinterpret_cast<const __nv_bfloat16 *>(P->L), p.n, p.T, P->ld, at<__nv_bfloat16>(d_ws, f.o_lt), f.ldLt);
+    mv_problem Pt = *P;
+    Pt.L = at<void>(d_ws, f.o_lt);
+    Pt.ld = f.ldLt;
+    Pt.layout = MV_LAYOUT_TN;
+    const Plan pt = make_plan(P->dtype, P->n, P->T, f.ldLt, 0, true, true);
+
+    // Shared step size from the power method on L (the fused pass over L^T).
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, pt.o_tick_t), 0, 4 * (size_t)pt.t_blocks, s));
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, pt.o_tick_n), 0, 4 * (size_t)pt.n_groups, s));
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    launch_setup(st, P->mu, P->power_start, rs, y32, p.n, s);
+    if (pt.use_llt) {
+        MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, pt.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
+        MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, pt.o_err), 0, 16, s));
+    }
+    for (int it = 0; it < O.power_iters; ++it) {
+        if (pt.use_llt)
+            MV_TRY(launch_llt(pt, &Pt, y32, d_ws, nullptr, at<double>(d_ws, pt.o_gy), at<float>(d_ws, pt.o_g32), s));
+        else
+            gemv_pair(pt, &Pt, y32, d_ws, nullptr, at<double>(d_ws, pt.o_gy), s, at<float>(d_ws, pt.o_g32));
+        launch_power_norm(at<float>(d_ws, pt.o_g32), rs, y32, p.n, s);
+    }
+    if (O.power_iters > 0) gemv_t_only(pt, &Pt, y32, d_ws, s);
+    launch_step_size(st, at<float>(d_ws, pt.o_z), (O.alpha > 0.0 || O.power_iters == 0) ? 0 : p.T, P->gamma,
+                     O.power_safety, O.alpha, s);
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_y), 0, 2 * (size_t)f.BN * f.ldY, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_gtick), 0, 4 * (size_t)((p.n + kBM - 1) / kBM) + 64, s));
     MV_CUDA_TRY(cudaGetLastError());
+    // Cluster size of the per-target projections: the smallest that holds n,
+    // widened towards the single problem's while all B clusters still fit in
+    // half a wave (B targets x 16 CTAs would queue in several waves).
+    int fcl = 1;
+    while ((p.n + fcl - 1) / fcl > kProjMaxLocal) fcl *= 2;
+    while (fcl < p.cl && B * fcl * 4 <= sm_count()) fcl *= 2;
 
     FArgs a;
     a.fs = at<FState>(d_ws, f.o_fs);
@@ -538,7 +554,7 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
     a.max_iter = O.max_iter;
     a.gamma = P->gamma;
     a.eps = P_hi ? eps_lo : O.eps;
-    MV_CUDA_TRY(launch_frontier(true, p.cl, a, s));
+    MV_CUDA_TRY(launch_frontier(true, fcl, a, s));
 
     CUtensorMap maps[6];
     if (P->dtype == MV_FP8_E4M3) {
@@ -566,7 +582,7 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
             if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 for (int c = 0; c < chunk; ++c) {
                     frontier_gemm_pair(mp, p, f, d_ws, cs, two);
-                    launch_frontier(false, p.cl, a, cs);
+                    launch_frontier(false, fcl, a, cs);
                 }
                 if (cudaStreamEndCapture(cs, &graph) == cudaSuccess) {
                     if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
@@ -587,7 +603,7 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
             } else {
                 for (int i = 0; i < chunk; ++i) {
                     frontier_gemm_pair(mp, p, f, d_ws, s, two);
-                    launch_frontier(false, p.cl, a, s);
+                    launch_frontier(false, fcl, a, s);
                 }
             }
             launches += 3 * chunk;
