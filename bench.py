@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-row-oracles", action="store_true", help="skip the oracle timings of the further rows")
+    ap.add_argument("--profile", default=None, choices=["sketch", "frontier"],
+                    help="run one instance of that workload at --shape (for ncu) and exit, printing its time")
     return ap.parse_args()
 
 
@@ -136,7 +138,7 @@ def peaks_tensor():
 TRAFFIC_FILES = {"gemv_t": ("gemv_traffic.txt", "gemv.cuh"), "gemv_n": ("gemv_traffic.txt", "gemv.cuh"),
                  "llt": ("llt_traffic.txt", "llt.cuh"), "llt_tn": ("llt_traffic.txt", "llt.cuh"),
                  "sigma_gemm": ("sigma_traffic.txt", "sigma.cu"),
-                 "cs_tn": ("countsketch_traffic.txt", "countsketch.cu"), "sketch": ("sketch_traffic.txt", "gemm.cuh")}
+                 "cs_tn": ("countsketch_traffic.txt", "countsketch.cu"), "sketch": ("sketch_traffic.txt", "gemm_chunk.cuh")}
 
 
 def committed_traffic(kernel, layout="nt"):
@@ -466,10 +468,40 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def profile_run(args):
+    """One instance of a workload for a profiler: the sketch GEMM (L in BF16
+    times a Phi drawn from seed 2, m = --sketch-m) or one 64-target frontier
+    solve (BF16, targets between the 10th and 90th percentiles of mu)."""
+    import torch
+    from paper_2604_02917_gb300 import mv
+    from synth import factor_returns
+    model = workload(args, 0)
+    R = torch.from_numpy(factor_returns(model, np.float32)).cuda()
+    L, rs, mu, _ = mv.center_factor(R, "bf16")
+    del R
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile == "sketch":
+        Phi = mv.gaussian_sketch(2, args.sketch_m, model.T)
+        e0.record()
+        mv.sketch(L, model.T, Phi)
+        e1.record()
+    else:
+        muh = mu.cpu().numpy()
+        tg = np.linspace(np.percentile(muh, 10), np.percentile(muh, 90), 64)
+        fs = mv.FrontierSolver(L, mu, tg, model.T, eps=args.eps)
+        e0.record()
+        fs.solve()
+        e1.record()
+    torch.cuda.synchronize()
+    print(f"{args.profile} {model.n}x{model.T}: {e0.elapsed_time(e1):.3f} ms", flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.profile:
+        return profile_run(args)
     import torch
     from paper_2604_02917_gb300 import mv
     from synth import factor_returns, power_start

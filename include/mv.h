@@ -469,18 +469,29 @@ int mv_countsketch(const void *d_L, int32_t dtype, int32_t layout, const float *
                    float *d_L_sketch, int64_t ldS, void *d_ws, size_t ws_bytes, mv_stream_t stream);
 
 /* ------------------------------------------------------------------------
- * 3d. Truncate + ridge (Sec. 2.5 steps 2-3; App. D.3), FP64.
+ * 3d. Truncate + ridge (Sec. 2.5 steps 2-3; App. D.3).
  *
- *  From tilde L (n x m FP32) computes the k largest eigenpairs of the FP64
- *  Gram matrix K = tilde L tilde L^T (eigenvalues sigma_i^2, eigenvectors U)
- *  and writes L_eff = U_k diag(sigma_k) (n x k FP32, row-major, columns in
+ *  From tilde L (n x m FP32) computes the k largest eigenpairs of the Gram
+ *  matrix K = tilde L tilde L^T (eigenvalues sigma_i^2, eigenvectors U) and
+ *  writes L_eff = U_k diag(sigma_k) (n x k FP32, row-major, columns in
  *  descending sigma) and sigma (k FP64, descending).  The ridge returned in
  *  *h_gamma_out is `gamma` if gamma >= 0, else 1e-4 * trace_sigma / n.
- *  One-time step; uses cuBLAS (DSYRK) and cuSOLVER (DSYEVD) loaded at run
- *  time: MV_ERR_UNSUPPORTED if they cannot be loaded.  Workspace:
- *  mv_str_workspace_size(n, m, k) bytes (FP64 copies of tilde L and K plus
- *  the eigensolver's buffer).  Blocking.  MV_ERR_NUMERIC if the eigensolver
- *  reports a failure.
+ *  Method (the partial decomposition the paper's complexity discussion of
+ *  STR points to): K formed FP32-accurate on the tensor cores (three-piece
+ *  BF16 splits, chunked accumulation), then Chebyshev-filtered subspace
+ *  iteration on a block of b = max(2k, k + 512) columns (rounded up to 64)
+ *  with Lowdin orthonormalisation, and a final Rayleigh--Ritz step whose
+ *  b x b eigenproblem is solved in FP64.  For n <= 1024, or b >= n, all n
+ *  eigenpairs of K come from a dense FP64 eigensolver instead.  The small
+ *  eigenproblems use cuSOLVER (DSYEVD / SSYEVD) loaded at run time:
+ *  MV_ERR_UNSUPPORTED if it cannot be loaded.  Accuracy: eigenvalues within
+ *  about 1e-6 sigma_1^2 of those of the exact K of the given tilde L, and
+ *  L_eff^T L_eff = diag(sigma^2) to FP32 rounding.  Workspace:
+ *  mv_str_workspace_size(n, m, k) bytes (K, the n x b panels and the
+ *  eigensolver's buffer).  Blocking; the first call on a device also
+ *  captures the orthonormalisation into a CUDA graph that later calls of the
+ *  same shape and workspace replay.  MV_ERR_NUMERIC if the eigensolver
+ *  reports a failure or the iteration produces a non-finite value.
  * ------------------------------------------------------------------------ */
 size_t mv_str_workspace_size(int64_t n, int64_t m, int64_t k);
 int mv_str_truncate(const float *d_L_sketch, int64_t n, int64_t m, int64_t ldS, int64_t k, double gamma,

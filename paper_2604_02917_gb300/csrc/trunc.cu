@@ -41,6 +41,7 @@
 // all its eigenpairs by DSYEVD on the n x n matrix.
 #include <dlfcn.h>
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 
 #include <algorithm>
@@ -454,6 +455,12 @@ static int syevd(const TopkPlan &p, char *ws, double *Hd, int64_t dim, double *W
         snprintf(msg, sizeof(msg), "cusolverDnDsyevd: info=%d", hinfo);
         return record_message(MV_ERR_NUMERIC, msg);
     }
+    // a non-finite entry upstream would otherwise reach sigma as sqrt(max(NaN, 0)) = 0
+    std::vector<double> w((size_t)dim);
+    MV_CUDA_TRY(cudaMemcpyAsync(w.data(), W, 8 * (size_t)dim, cudaMemcpyDeviceToHost, s));
+    MV_CUDA_TRY(cudaStreamSynchronize(s));
+    for (double v : w)
+        if (!std::isfinite(v)) return record_message(MV_ERR_NUMERIC, "STR truncation: non-finite eigenvalue");
     return MV_OK;
 }
 
