@@ -937,52 +937,75 @@ def main():
         del La, Ra
 
     # 256 independent problems, n ~ U[500,5000], T ~ U[2000,20000] (grouped launches).
+    # Headline: every factor stored transposed, the grouped single pass (L read
+    # once per product); beside it the same batch stored n x T on the grouped
+    # GEMV pair (L read twice), with the autotuned and the default tiles.
     batch = None
     batch_elem_iters = 0
     if not args.no_batch and args.dtype == "f32":
         from synth import factor_returns_device, uneven_problem_sizes
         models = uneven_problem_sizes(args.batch_count)
-        probs = []
-        for bm in models:
-            Rb = factor_returns_device(bm, dev)
-            Lb_, _, mub, _ = mv.center_factor(Rb, "f32")
-            del Rb
-            Rtb = float(torch.quantile(mub, 0.6).item())
-            probs.append({"L": Lb_, "mu": mub, "R_target": Rtb, "T": bm.T})
-        bsv = mv.BatchSolver(probs, eps=args.eps)
 
-        def timed_batch():
+        def build(layout):
+            probs = []
+            for bm in models:
+                Rb = factor_returns_device(bm, dev)
+                Lb_, _, mub, _ = mv.center_factor(Rb, "f32", layout=layout)
+                del Rb
+                Rtb = float(torch.quantile(mub, 0.6).item())
+                probs.append({"L": Lb_, "mu": mub, "R_target": Rtb, "T": bm.T, "layout": layout})
+            return probs
+
+        def timed_batch(bsv):
             b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             b0.record(stream)
-            _, bi = bsv.solve()
+            xs_, bi = bsv.solve()
             b1.record(stream)
             torch.cuda.synchronize()
-            return b0.elapsed_time(b1) / 1e3, bi
+            return b0.elapsed_time(b1) / 1e3, bi, [x.clone() for x in xs_]
 
+        probs = build("tn")
+        bsv = mv.BatchSolver(probs, eps=args.eps)
+        bsv.solve()
+        bt, binfos, bx_tn = timed_batch(bsv)
+        del probs, bsv
+        torch.cuda.empty_cache()
+        probs = build("nt")
+        bsv = mv.BatchSolver(probs, eps=args.eps)
         os.environ["MV_BATCH_AUTOTUNE"] = "0"            # the untuned default tiles, for comparison
         bsv.solve()
-        bt_default, _ = timed_batch()
+        bt_default, _, _ = timed_batch(bsv)
         del os.environ["MV_BATCH_AUTOTUNE"]
         bsv.solve()                                      # the first tuned solve times the tile candidates
         torch.cuda.synchronize()
-        bt, binfos = timed_batch()
+        bt_nt, binfos_nt, bx_nt = timed_batch(bsv)
         t_rows, n_bytes, tuned = bsv.tiles()
+        del probs, bsv
+        torch.cuda.empty_cache()
         elems = sum(bm.n * bm.T for bm in models)
         iters = [i["iterations"] for i in binfos]
-        # bytes streamed: 2 passes of every L per power iteration (50) and per NPGA iteration it ran
-        moved = sum(2 * 4 * bm.n * bm.T * (50 + it + 1) for bm, it in zip(models, iters))
+        iters_nt = [i["iterations"] for i in binfos_nt]
+        # algorithmic bytes: every L once per product on the transposed layout
+        # (50 power steps, the lambda_hat pass, each NPGA iteration, the
+        # objective pass); on n x T twice per product and once per z-only pass
+        moved = sum(4 * bm.n * bm.T * (50 + 1 + it + 1) for bm, it in zip(models, iters))
+        moved_nt = sum(4 * bm.n * bm.T * (2 * 50 + 1 + 2 * it + 1) for bm, it in zip(models, iters_nt))
         batch_elem_iters = sum(bm.n * bm.T * (50 + it + 1) for bm, it in zip(models, iters))
         peak, peak_kind = peaks()
-        batch = {"problems": len(models), "elements": elems, "value": bt, "unit": "s",
+        dx = max(float(torch.max(torch.abs(a - b)).item()) for a, b in zip(bx_tn, bx_nt))
+        batch = {"problems": len(models), "elements": elems, "value": bt, "unit": "s", "layout": "tn (grouped single pass)",
                  "roofline": {"bound": "hbm", "achieved": round(moved / bt / 1e9, 1), "peak": peak, "unit": "GB/s",
                               "frac": round(moved / bt / 1e9 / peak, 4), "peak_source": peak_kind, "traffic": None,
-                              "note": "two passes of every L per power and NPGA iteration (algorithmic)"},
+                              "note": "one pass of every L per product (algorithmic)"},
                  "problems_per_s": len(models) / bt, "all_converged": all(i["converged"] == 1 for i in binfos),
                  "iterations_min": min(iters), "iterations_max": max(iters),
                  "aggregate_GBps": moved / bt / 1e9, "data": "synthetic, drawn on the GPU (torch seeded stream)",
-                 "tiles": {"gemv_t_rows_per_split": t_rows, "gemv_n_bytes_per_split": n_bytes, "tuned": tuned},
-                 "default_tiles_s": bt_default}
-        del probs, bsv
+                 "nt_two_pass": {"value": bt_nt, "unit": "s", "default_tiles_s": bt_default,
+                                 "all_converged": all(i["converged"] == 1 for i in binfos_nt),
+                                 "roofline_frac": round(moved_nt / bt_nt / 1e9 / peak, 4),
+                                 "tiles": {"gemv_t_rows_per_split": t_rows, "gemv_n_bytes_per_split": n_bytes,
+                                           "tuned": tuned}},
+                 "x_inf_tn_vs_nt": dx}
 
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:

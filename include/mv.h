@@ -365,14 +365,23 @@ int mv_npga_solve_frontier_refined(const mv_problem *P_lo, const mv_problem *P_h
 /* ------------------------------------------------------------------------
  * 3g. Batch of independent problems of uneven size (n_i, T_i all different).
  *
- *  Solves count problems (same dtype; each with its own L, n, T, ld, gamma,
- *  mu, R_target, mode and power start) with the semantics of mv_npga_solve,
- *  in lock-step: each GEMV half-product is ONE grouped launch over a tile
- *  list that spans every problem's grid (row splits of 512 rows), and each
- *  projection step is one launch with one thread-block cluster per problem.
- *  Each problem has its own step size, FISTA state and KKT test; a converged
- *  problem's tiles return at once.  Chunks of kkt_every iterations replay as
- *  one CUDA graph.
+ *  Solves count problems (same dtype; each with its own L, n, T, ld, layout,
+ *  gamma, mu, R_target, mode and power start) with the semantics of
+ *  mv_npga_solve, in lock-step.  Problems stored transposed (MV_LAYOUT_TN,
+ *  L^T as T x n) take the fused single pass of mv_gradient, grouped: one
+ *  launch per cluster size (1, 2, 4 or 8 CTAs, the smallest whose asset
+ *  share fits shared memory) over a list of (problem, cluster) pairs, each
+ *  problem with about 8 MB of L per cluster, its own tensor map and its own
+ *  fixed-order reduction -- L is read once per product.  Problems stored
+ *  n x T (MV_LAYOUT_NT) take two grouped GEMV launches per product over a
+ *  tile list that spans their grids (row splits of 512 rows).  The two kinds
+ *  may share a batch.  Each projection step is one launch with one
+ *  thread-block cluster per problem.  Each problem has its own step size,
+ *  FISTA state and KKT test; a converged problem's clusters and tiles
+ *  return at once.  Chunks of kkt_every iterations replay as one CUDA graph.
+ *  MV_ERR_UNSUPPORTED for MV_LAYOUT_SIGMA problems, and for a transposed
+ *  problem whose n fits no cluster size (n above 24576).
+ *  MV_ERR_TIMEOUT if a bounded wait of the fused pass gave up.
  *  h_x_dev [in]  host array of count device pointers; x_i (n_i FP64) is
  *                written to h_x_dev[i] on return.
  *  h_infos [out] count host mv_solve_info.
@@ -386,7 +395,8 @@ int mv_npga_solve_frontier_refined(const mv_problem *P_lo, const mv_problem *P_h
  *  (environment MV_BATCH_AUTOTUNE=0 keeps 512 rows x 16 KB).  The workspace
  *  has room for every candidate.  mv_batch_tiles reports the tiles a shape
  *  runs with: MV_OK once tuned, MV_ERR_NOT_CONVERGED (and the defaults)
- *  before. */
+ *  before.  A batch of transposed problems only has nothing to tune and
+ *  keeps the defaults. */
 int mv_batch_tiles(const mv_problem *probs, int64_t count, int32_t *h_t_rows, int32_t *h_n_split_bytes);
 size_t mv_batch_workspace_size(const mv_problem *probs, int64_t count);
 int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_opts *opts,

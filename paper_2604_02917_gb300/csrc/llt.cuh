@@ -469,9 +469,12 @@ __host__ __device__ inline LltSmem lltt_smem_layout(int npc, int C) {
     return m;
 }
 
-template <int DT, int C>
-__global__ void __launch_bounds__(kLltThreads, 1)
-lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
+// The transposed pass of cluster cid (of a.G) over the tensor map tm.  With
+// kGlobalMap the map lives in global memory (one per problem of a grouped
+// launch) and the producer orders the tensor-map proxy after the host's
+// copy of it before its first load.
+template <int DT, int C, bool kGlobalMap>
+__device__ __forceinline__ void lltt_body(const CUtensorMap *tm, const LltArgs &a, const int cid) {
     using S = Store<DT>;
     constexpr int ES = (int)sizeof(typename S::elem);
     constexpr int EPC = S::VEC;                          // elements per 16-byte chunk
@@ -499,7 +502,6 @@ lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
 
     cg::cluster_group cluster = cg::this_cluster();
     const int rank = (int)cluster.block_rank();
-    const int cid = blockIdx.x / C;
     const int col0 = rank * npc;
     const int nj = (a.nb - cid + a.G - 1) / a.G;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -523,10 +525,13 @@ lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
         const uint32_t dst = umma::smem_u32(sm + (size_t)s * L.stage);
         umma::mbar_arrive_expect_tx(full0 + 8 * s, stage_tx);
         for (int k = 0; k < a.nbox; ++k)
-            umma::tma_load_2d(dst + (uint32_t)(k * BOXB), &tmM, col0 + k * kLltBoxCols, b * W, full0 + 8 * s);
+            umma::tma_load_2d(dst + (uint32_t)(k * BOXB), tm, col0 + k * kLltBoxCols, b * W, full0 + 8 * s);
     };
     if (warp == kLltConsumerWarps && lane == 0) {          // first stages before the cluster barrier
-        umma::prefetch_tensormap(&tmM);
+        if constexpr (kGlobalMap)
+            asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tm))
+                         : "memory");
+        umma::prefetch_tensormap(tm);
         for (int j = 0; j < kLltStages && j < nj; ++j) issue(j);
     }
     for (int i = tid; i < npc; i += kLltThreads) s_y[i] = col0 + i < a.n ? a.y32[col0 + i] : 0.f;
@@ -669,6 +674,33 @@ lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
     }
     llt_final_reduce(a, cid, rank, col0);
     cluster.sync();
+}
+
+template <int DT, int C>
+__global__ void __launch_bounds__(kLltThreads, 1)
+lltt_kernel(const __grid_constant__ CUtensorMap tmM, const LltArgs a) {
+    lltt_body<DT, C, false>(&tmM, a, (int)(blockIdx.x / C));
+}
+
+// Grouped transposed pass: many problems (each its own L^T, n, T, vectors
+// and scratch) in one launch.  Cluster c works on problem clusters[c].x as
+// its cluster clusters[c].y of that problem's G.  Descriptors keep the
+// tensor map's alignment (at least the 64 bytes TMA requires; the
+// workspace places the array on a 256-byte boundary) and are written by the
+// host before the launch.
+struct LltGroup {
+    CUtensorMap map;
+    LltArgs a;
+};
+static_assert(alignof(LltGroup) >= 64 && sizeof(LltGroup) % 64 == 0, "tensor-map descriptors must stay aligned");
+
+template <int DT, int C>
+__global__ void __launch_bounds__(kLltThreads, 1)
+lltt_grouped_kernel(const LltGroup *__restrict__ groups, const int2 *__restrict__ clusters) {
+    const int2 w = clusters[blockIdx.x / C];
+    const LltGroup *gd = groups + w.x;
+    const LltArgs a = gd->a;
+    lltt_body<DT, C, true>(&gd->map, a, w.y);
 }
 
 // ------------------------------------------------------------------ host

@@ -49,6 +49,30 @@ int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, i
                const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s,
                float *z = nullptr);
 
+// ---- grouped transposed pass: many problems (each L^T stored T x n) in one
+// launch per cluster size; the batch solve's product.
+struct LltGroupPlan {
+    int C;                     // cluster size (the transposed plan's)
+    int G;                     // clusters of this problem
+    int npc, nb;               // asset columns per CTA, column blocks
+    size_t smem;               // dynamic shared memory per CTA
+    double est_us;             // estimated time of one cluster (longest first)
+};
+// Geometry of one problem (ok = false where no cluster size fits n).
+bool llt_group_plan(int dt, int64_t n, int64_t T, LltGroupPlan *gp);
+size_t llt_group_bytes();                                   // one descriptor (64-byte multiple)
+size_t llt_group_scratch_bytes(int64_t n, int G);           // per-problem partials and tickets
+size_t llt_group_ticket_offset(int64_t n, int G);           // tickets inside that scratch
+// Writes the descriptor of one problem (tensor map + arguments) into host
+// memory dst (llt_group_bytes() bytes).  done, z: nullable as in llt_launch.
+int llt_group_write(void *dst, const LltGroupPlan &gp, int dt, const void *L, int64_t n, int64_t T, int64_t ld,
+                    const float *y32, const float *row_scale, void *scratch, int *err, const int *done, double *g,
+                    float *g32, float *z);
+// One grouped launch over nclusters clusters of size C (descriptors and the
+// (problem, cluster) list in device memory).
+cudaError_t llt_launch_grouped(int dt, int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
+                               cudaStream_t s);
+
 // Per-dtype entry points (llt_<dtype>.cu).
 int llt_max_clusters_f32(int C, int RB, size_t smem);
 int llt_max_clusters_bf16(int C, int RB, size_t smem);
@@ -63,5 +87,11 @@ int llt_max_clusters_tn_fp8(int C, size_t smem);
 cudaError_t llt_launch_tn_f32(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
 cudaError_t llt_launch_tn_bf16(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
 cudaError_t llt_launch_tn_fp8(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
+cudaError_t llt_launch_grouped_f32(int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
+                                   cudaStream_t s);
+cudaError_t llt_launch_grouped_bf16(int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
+                                    cudaStream_t s);
+cudaError_t llt_launch_grouped_fp8(int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
+                                   cudaStream_t s);
 
 }  // namespace mv

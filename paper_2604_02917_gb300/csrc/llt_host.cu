@@ -1,7 +1,11 @@
 // Host side of the fused single-pass Gram product (llt.cuh): shape choice,
 // device occupancy query, tensor map and launch.
+#include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
+
+#include <cmath>
 
 #include <algorithm>
 #include <mutex>
@@ -153,6 +157,85 @@ int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, i
                             : llt_launch_fp8(lp.C, lp.RB, lp.G, lp.smem, &map, a, s);
     if (e != cudaSuccess) return record_cuda_error(e, "fused L L^T pass launch", __FILE__, __LINE__);
     return MV_OK;
+}
+
+// ------------------------------------------------------------------ grouped transposed pass
+// Clusters per problem: about 8 MB of the factor and at most 64 column
+// blocks each, so no cluster runs long enough to leave a tail, and the fixed
+// cost of a cluster (two stage fills, the partial of g) stays a few percent.
+constexpr double kGroupBytesPerCluster = 8.0 * 1024 * 1024;
+constexpr int kGroupMaxBlocks = 64;
+
+bool llt_group_plan(int dt, int64_t n, int64_t T, LltGroupPlan *gp) {
+    const int es = dtype_size(dt);
+    if (es == 0 || n < 1 || T < 1) return false;
+    for (int C = 1; C <= kLltMaxCluster; C *= 2) {
+        LltPlan q{};
+        if (!lltt_shape(n, T, es, C, &q)) continue;
+        const double bytes = (double)n * (double)T * es;
+        int64_t G = std::max<int64_t>((int64_t)std::ceil(bytes / kGroupBytesPerCluster),
+                                      (q.nb + kGroupMaxBlocks - 1) / kGroupMaxBlocks);
+        G = std::max<int64_t>(1, std::min<int64_t>(G, std::min<int64_t>(kLltMaxClusters, q.nb)));
+        gp->C = C;
+        gp->G = (int)G;
+        gp->npc = q.rpc;
+        gp->nb = q.nb;
+        gp->smem = q.smem;
+        // a block's stage is 32 bytes x npc per CTA; below ~40 KB a block costs
+        // about a microsecond of latency whatever its size
+        const int64_t per = (q.nb + G - 1) / G;
+        gp->est_us = (double)per * std::max(1.0, 32.0 * q.rpc / 40000.0);
+        return true;
+    }
+    return false;
+}
+
+size_t llt_group_bytes() { return sizeof(LltGroup); }
+
+size_t llt_group_ticket_offset(int64_t n, int G) {
+    const int ngrp = (G + kLltFan - 1) / kLltFan;
+    return align_up(4 * (size_t)n * G, 256) + align_up(8 * (size_t)n * ngrp, 256);
+}
+
+size_t llt_group_scratch_bytes(int64_t n, int G) { return llt_group_ticket_offset(n, G) + align_up(llt_ticket_bytes(), 256); }
+
+int llt_group_write(void *dst, const LltGroupPlan &gp, int dt, const void *L, int64_t n, int64_t T, int64_t ld,
+                    const float *y32, const float *row_scale, void *scratch, int *err, const int *done, double *g,
+                    float *g32, float *z) {
+    LltGroup d;
+    memset(&d, 0, sizeof(d));
+    MV_TRY(make_map_lltt(&d.map, dt, L, n, T, ld, 32 / dtype_size(dt)));
+    char *sp = reinterpret_cast<char *>(scratch);
+    LltArgs &a = d.a;
+    a.y32 = y32;
+    a.row_scale = row_scale;
+    a.gpart = reinterpret_cast<float *>(sp);
+    a.gq = reinterpret_cast<double *>(sp + align_up(4 * (size_t)n * gp.G, 256));
+    unsigned *tickets = reinterpret_cast<unsigned *>(sp + llt_group_ticket_offset(n, gp.G));
+    a.tick1 = tickets;
+    a.tick2 = tickets + (size_t)kLltMaxCluster * kLltMaxGroups;
+    a.g = g;
+    a.g32 = g32;
+    a.z = z;
+    a.err = err;
+    a.done = done;
+    a.n = (int)n;
+    a.T = (int)T;
+    a.rpc = gp.npc;
+    a.box_rows = 32 / dtype_size(dt);
+    a.nbox = gp.npc / kLltBoxCols;
+    a.nb = gp.nb;
+    a.G = gp.G;
+    memcpy(dst, &d, sizeof(d));
+    return MV_OK;
+}
+
+cudaError_t llt_launch_grouped(int dt, int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
+                               cudaStream_t s) {
+    if (nclusters < 1) return cudaSuccess;
+    if (dt == MV_F32) return llt_launch_grouped_f32(C, nclusters, smem, groups, clusters, s);
+    if (dt == MV_BF16) return llt_launch_grouped_bf16(C, nclusters, smem, groups, clusters, s);
+    return llt_launch_grouped_fp8(C, nclusters, smem, groups, clusters, s);
 }
 
 }  // namespace mv

@@ -99,6 +99,31 @@ cudaError_t launch_tn(int G, size_t smem, const void *map, const LltArgs &a, cud
     return cudaLaunchKernelEx(&cfg, lltt_kernel<MV_LLT_DT, C>, *reinterpret_cast<const CUtensorMap *>(map), a);
 }
 
+template <int C>
+int attrs_grouped() {
+    static int st = -1;
+    if (st < 0) {
+        const int smem = (int)(kLltSmemCap + 256);
+        st = (cudaFuncSetAttribute(lltt_grouped_kernel<MV_LLT_DT, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   smem) == cudaSuccess &&
+              cudaFuncSetAttribute(lltt_grouped_kernel<MV_LLT_DT, C>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                   1) == cudaSuccess)
+                 ? MV_OK
+                 : MV_ERR_CUDA;
+        if (st != MV_OK) (void)cudaGetLastError();
+    }
+    return st;
+}
+
+template <int C>
+cudaError_t launch_grouped(int nclusters, size_t smem, const void *groups, const int2 *clusters, cudaStream_t s) {
+    if (attrs_grouped<C>() != MV_OK) return cudaErrorInvalidValue;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = config(C, nclusters, smem, s, attr);
+    return cudaLaunchKernelEx(&cfg, lltt_grouped_kernel<MV_LLT_DT, C>, reinterpret_cast<const LltGroup *>(groups),
+                              clusters);
+}
+
 }  // namespace
 
 // The instantiated shapes (kLltShapes).
@@ -135,6 +160,12 @@ int MV_LLT_CAT(llt_max_clusters_tn_, MV_LLT_SUFFIX)(int C, size_t smem) {
 cudaError_t MV_LLT_CAT(llt_launch_tn_, MV_LLT_SUFFIX)(int C, int G, size_t smem, const void *map, const LltArgs &a,
                                                        cudaStream_t s) {
     MV_LLT_SWITCH_TN(C, launch_tn, G, smem, map, a, s)
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t MV_LLT_CAT(llt_launch_grouped_, MV_LLT_SUFFIX)(int C, int nclusters, size_t smem, const void *groups,
+                                                            const int2 *clusters, cudaStream_t s) {
+    MV_LLT_SWITCH_TN(C, launch_grouped, nclusters, smem, groups, clusters, s)
     return cudaErrorInvalidValue;
 }
 

@@ -1479,31 +1479,64 @@ constexpr BatchTiles kBatchDefault = {512, 16384};
 constexpr BatchTiles kBatchCandidates[] = {{256, 8192}, {256, 16384}, {256, 32768}, {512, 8192}, {512, 16384},
                                            {512, 32768}, {1024, 8192}, {1024, 16384}, {1024, 32768}};
 
+// Problems stored transposed (MV_LAYOUT_TN) take the fused single pass,
+// grouped: one launch per cluster size over a list of (problem, cluster)
+// pairs; problems stored n x T take the grouped GEMV pair.  Both can share
+// a batch.
+constexpr int kGroupSizes = 4;                       // cluster sizes 1, 2, 4, 8
 struct BatchLayout {
     std::vector<Plan> plans;
     std::vector<size_t> base;       // workspace offset of each problem's plan
+    std::vector<LltGroupPlan> gpl;  // grouped-pass geometry (TN problems)
+    std::vector<size_t> o_lsc;      // grouped-pass scratch of each TN problem
     size_t o_gp, o_gp_all, o_sa, o_one, o_tt, o_tn, o_zero;
+    size_t o_lgrp, o_lgrp_all, o_lcl, o_lerr;
     int nt_tiles, nn_tiles, cl, max_ncols, max_n;
+    int n_tn, n_lcl;
+    int lstart[kGroupSizes], lcount[kGroupSizes];
+    size_t lsmem[kGroupSizes];
     size_t total;
 };
+
+static int group_index(int C) { return C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3; }
 
 static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo, BatchTiles tiles = kBatchDefault) {
     Lo->plans.clear();
     Lo->base.clear();
-    int64_t ntt = 0, nnt = 0;
-    int max_n = 1, max_ncols = 0;
+    Lo->gpl.assign((size_t)count, LltGroupPlan{});
+    Lo->o_lsc.assign((size_t)count, 0);
+    int64_t ntt = 0, nnt = 0, ncl = 0;
+    int max_n = 1, max_ncols = 0, n_tn = 0;
+    for (int g = 0; g < kGroupSizes; ++g) {
+        Lo->lstart[g] = Lo->lcount[g] = 0;
+        Lo->lsmem[g] = 0;
+    }
     for (int64_t i = 0; i < count; ++i) {
         MV_TRY(validate_problem(probs + i));
-        MV_TRY(require_nt(probs + i, "batch solve"));
+        if (is_sigma(probs + i)) return record_message(MV_ERR_UNSUPPORTED, "batch solve: factor layouts only");
         if (probs[i].dtype != probs[0].dtype) return record_message(MV_ERR_INVALID_ARG, "batch: mixed dtypes");
-        Plan p = make_plan(probs[i].dtype, probs[i].n, probs[i].T, probs[i].ld, tiles.t_rows, false, false,
+        const bool tn = is_tn(probs + i);
+        Plan p = make_plan(probs[i].dtype, probs[i].n, probs[i].T, probs[i].ld, tiles.t_rows, false, tn,
                            tiles.n_bytes);
-        ntt += (int64_t)p.t_blocks * p.t_splits;
-        nnt += (int64_t)p.n_groups * p.n_splits;
+        if (tn) {
+            LltGroupPlan gp{};
+            if (!llt_group_plan(probs[i].dtype, probs[i].n, probs[i].T, &gp))
+                return record_message(MV_ERR_UNSUPPORTED, "batch: no cluster shape of the fused pass fits this n");
+            Lo->gpl[(size_t)i] = gp;
+            const int gi = group_index(gp.C);
+            Lo->lcount[gi] += gp.G;
+            Lo->lsmem[gi] = std::max(Lo->lsmem[gi], gp.smem);
+            ncl += gp.G;
+            ++n_tn;
+        } else {
+            ntt += (int64_t)p.t_blocks * p.t_splits;
+            nnt += (int64_t)p.n_groups * p.n_splits;
+            max_ncols = std::max(max_ncols, p.n_cols);
+        }
         max_n = std::max(max_n, p.n);
-        max_ncols = std::max(max_ncols, p.n_cols);
         Lo->plans.push_back(p);
     }
+    for (int g = 1; g < kGroupSizes; ++g) Lo->lstart[g] = Lo->lstart[g - 1] + Lo->lcount[g - 1];
     if (ntt >= (1LL << 31) || nnt >= (1LL << 31))
         return record_message(MV_ERR_UNSUPPORTED, "batch: the tile list exceeds 2^31 entries");
     size_t off = 0;
@@ -1519,9 +1552,18 @@ static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo,
     Lo->o_tt = take(sizeof(int4) * (size_t)ntt);
     Lo->o_tn = take(sizeof(int4) * (size_t)nnt);
     Lo->o_zero = take(sizeof(int));
-    for (int64_t i = 0; i < count; ++i) Lo->base.push_back(take(Lo->plans[i].total));
+    Lo->o_lgrp = take(llt_group_bytes() * (size_t)count);
+    Lo->o_lgrp_all = take(llt_group_bytes() * (size_t)count);
+    Lo->o_lcl = take(sizeof(int2) * (size_t)std::max<int64_t>(ncl, 1));
+    Lo->o_lerr = take(16);
+    for (int64_t i = 0; i < count; ++i) {
+        Lo->base.push_back(take(Lo->plans[i].total));
+        if (is_tn(probs + i)) Lo->o_lsc[(size_t)i] = take(llt_group_scratch_bytes(probs[i].n, Lo->gpl[(size_t)i].G));
+    }
     Lo->nt_tiles = (int)ntt;
     Lo->nn_tiles = (int)nnt;
+    Lo->n_tn = n_tn;
+    Lo->n_lcl = (int)ncl;
     Lo->cl = proj_cluster_size(max_n);
     Lo->max_ncols = max_ncols;
     Lo->max_n = max_n;
@@ -1532,15 +1574,30 @@ static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo,
 template <int DT>
 static void batch_gemv(const BatchLayout &Lo, void *ws, bool all, bool with_n, cudaStream_t s) {
     const GemvProb *gp = at<GemvProb>(ws, all ? Lo.o_gp_all : Lo.o_gp);
-    gemv_t_grouped<DT><<<Lo.nt_tiles, kGemvThreads, 0, s>>>(gp, at<int4>(ws, Lo.o_tt));
-    if (with_n)
+    if (Lo.nt_tiles > 0) gemv_t_grouped<DT><<<Lo.nt_tiles, kGemvThreads, 0, s>>>(gp, at<int4>(ws, Lo.o_tt));
+    if (with_n && Lo.nn_tiles > 0)
         gemv_n_grouped<DT, kRW><<<Lo.nn_tiles, kGemvThreads, (size_t)Lo.max_ncols * 4, s>>>(gp, at<int4>(ws, Lo.o_tn));
 }
 
-static void batch_gemv_any(int dt, const BatchLayout &Lo, void *ws, bool all, bool with_n, cudaStream_t s) {
+// One product for every problem: the grouped GEMV pair over the n x T
+// problems (z only when !with_n) and, unless gemv_only, the grouped fused
+// pass over the transposed ones (which always forms both z and g).  all:
+// every problem, converged or not (the power method and the objectives);
+// else converged problems return at once.
+static int batch_gemv_any(int dt, const BatchLayout &Lo, void *ws, bool all, bool with_n, cudaStream_t s,
+                          bool gemv_only = false) {
     if (dt == MV_F32) batch_gemv<MV_F32>(Lo, ws, all, with_n, s);
     else if (dt == MV_BF16) batch_gemv<MV_BF16>(Lo, ws, all, with_n, s);
     else batch_gemv<MV_FP8_E4M3>(Lo, ws, all, with_n, s);
+    if (gemv_only || Lo.n_tn == 0) return MV_OK;
+    const void *groups = at<char>(ws, all ? Lo.o_lgrp_all : Lo.o_lgrp);
+    const int2 *cl = at<int2>(ws, Lo.o_lcl);
+    for (int g = 0; g < kGroupSizes; ++g)
+        if (Lo.lcount[g] > 0) {
+            const cudaError_t e = llt_launch_grouped(dt, 1 << g, Lo.lcount[g], Lo.lsmem[g], groups, cl + Lo.lstart[g], s);
+            if (e != cudaSuccess) return record_cuda_error(e, "grouped fused pass launch", __FILE__, __LINE__);
+        }
+    return MV_OK;
 }
 
 static cudaError_t batch_step(const BatchLayout &Lo, void *ws, int count, cudaStream_t s) {
@@ -1566,6 +1623,9 @@ static int batch_setup(const BatchLayout &Lo, const mv_problem *probs, int64_t c
     std::vector<int4> tt, tn;
     tt.reserve(Lo.nt_tiles);
     tn.reserve(Lo.nn_tiles);
+    const size_t gbytes = llt_group_bytes();
+    std::vector<unsigned char> lg(Lo.n_tn > 0 ? gbytes * (size_t)cnt : 0), lga(lg.size());
+    std::vector<int> tn_order[kGroupSizes];
     const int *zero = at<int>(ws, Lo.o_zero);
     for (int i = 0; i < cnt; ++i) {
         const Plan &p = Lo.plans[i];
@@ -1632,6 +1692,18 @@ static int batch_setup(const BatchLayout &Lo, const mv_problem *probs, int64_t c
         o.alpha_override = O.alpha > 0.0 ? O.alpha : 0.0;
         o.R = P.R_target;
         one[i] = o;
+        if (is_tn(&P)) {
+            const LltGroupPlan &q = Lo.gpl[(size_t)i];
+            char *sc = reinterpret_cast<char *>(ws) + Lo.o_lsc[(size_t)i];
+            int *err = at<int>(ws, Lo.o_lerr);
+            MV_TRY(llt_group_write(lg.data() + (size_t)i * gbytes, q, P.dtype, P.L, p.n, p.T, P.ld, g.y32, rs, sc, err,
+                                   &st->done, g.gy, g.g32, nullptr));
+            MV_TRY(llt_group_write(lga.data() + (size_t)i * gbytes, q, P.dtype, P.L, p.n, p.T, P.ld, g.y32, rs, sc, err,
+                                   nullptr, g.gy, g.g32, g.z));
+            MV_CUDA_TRY(cudaMemsetAsync(sc + llt_group_ticket_offset(p.n, q.G), 0, llt_ticket_bytes(), s));
+            tn_order[group_index(q.C)].push_back(i);
+            continue;
+        }
         for (int b = 0; b < p.t_blocks; ++b)
             for (int sp = 0; sp < p.t_splits; ++sp) tt.push_back(make_int4(i, b, sp, 0));
         for (int gq = 0; gq < p.n_groups; ++gq)
@@ -1639,14 +1711,36 @@ static int batch_setup(const BatchLayout &Lo, const mv_problem *probs, int64_t c
         MV_CUDA_TRY(cudaMemsetAsync(w + p.o_tick_t, 0, 4 * (size_t)p.t_blocks, s));
         MV_CUDA_TRY(cudaMemsetAsync(w + p.o_tick_n, 0, 4 * (size_t)p.n_groups, s));
     }
+    // The grouped pass's cluster list: per cluster size, the problems whose
+    // clusters take longest first (the short ones fill the last wave), each
+    // problem's clusters adjacent (neighbouring row blocks of its L^T).
+    std::vector<int2> lcl;
+    lcl.reserve((size_t)Lo.n_lcl);
+    for (int gi = 0; gi < kGroupSizes; ++gi) {
+        std::vector<int> &ord = tn_order[gi];
+        std::stable_sort(ord.begin(), ord.end(),
+                         [&](int a, int b) { return Lo.gpl[(size_t)a].est_us > Lo.gpl[(size_t)b].est_us; });
+        for (int i : ord)
+            for (int c = 0; c < Lo.gpl[(size_t)i].G; ++c) lcl.push_back(make_int2(i, c));
+    }
+    if ((int)lcl.size() != Lo.n_lcl) return record_message(MV_ERR_UNSUPPORTED, "batch: cluster list size");
+    if (Lo.n_tn > 0) {
+        MV_CUDA_TRY(cudaMemcpyAsync(at<char>(ws, Lo.o_lgrp), lg.data(), lg.size(), cudaMemcpyHostToDevice, s));
+        MV_CUDA_TRY(cudaMemcpyAsync(at<char>(ws, Lo.o_lgrp_all), lga.data(), lga.size(), cudaMemcpyHostToDevice, s));
+        MV_CUDA_TRY(cudaMemcpyAsync(at<int2>(ws, Lo.o_lcl), lcl.data(), sizeof(int2) * lcl.size(),
+                                    cudaMemcpyHostToDevice, s));
+    }
+    MV_CUDA_TRY(cudaMemsetAsync(at<char>(ws, Lo.o_lerr), 0, 16, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<int>(ws, Lo.o_zero), 0, sizeof(int), s));
     MV_CUDA_TRY(cudaMemcpyAsync(at<GemvProb>(ws, Lo.o_gp), gp.data(), sizeof(GemvProb) * cnt, cudaMemcpyHostToDevice, s));
     MV_CUDA_TRY(cudaMemcpyAsync(at<GemvProb>(ws, Lo.o_gp_all), gpa.data(), sizeof(GemvProb) * cnt,
                                 cudaMemcpyHostToDevice, s));
     MV_CUDA_TRY(cudaMemcpyAsync(at<StepArgs>(ws, Lo.o_sa), sa.data(), sizeof(StepArgs) * cnt, cudaMemcpyHostToDevice, s));
     MV_CUDA_TRY(cudaMemcpyAsync(at<GOne>(ws, Lo.o_one), one.data(), sizeof(GOne) * cnt, cudaMemcpyHostToDevice, s));
-    MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tt), tt.data(), sizeof(int4) * tt.size(), cudaMemcpyHostToDevice, s));
-    MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tn), tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, s));
+    if (!tt.empty())
+        MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tt), tt.data(), sizeof(int4) * tt.size(), cudaMemcpyHostToDevice, s));
+    if (!tn.empty())
+        MV_CUDA_TRY(cudaMemcpyAsync(at<int4>(ws, Lo.o_tn), tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, s));
     MV_CUDA_TRY(cudaStreamSynchronize(s));   // host descriptor buffers may now be released
     return MV_OK;
 }
@@ -1662,6 +1756,7 @@ static uint64_t batch_key(const mv_problem *probs, int64_t count) {
         mix((uint64_t)probs[i].n);
         mix((uint64_t)probs[i].T);
         mix((uint64_t)probs[i].ld);
+        mix((uint64_t)probs[i].layout);
     }
     return key;
 }
@@ -1699,12 +1794,13 @@ static int batch_tune(const mv_problem *probs, int64_t count, const mv_solve_opt
         st = batch_layout(probs, count, &Lo, c);
         if (st != MV_OK) break;
         if (Lo.total > ws_bytes) continue;
+        if (Lo.nt_tiles == 0) break;                     // every problem takes the fused pass: nothing to tune
         st = batch_setup(Lo, probs, count, O, ws, s);
         if (st != MV_OK) break;
         setup_grouped<<<(int)count, kStepThreads, 0, s>>>(at<GOne>(ws, Lo.o_one));
-        batch_gemv_any(probs[0].dtype, Lo, ws, true, true, s);
+        batch_gemv_any(probs[0].dtype, Lo, ws, true, true, s, true);
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 2; ++r) batch_gemv_any(probs[0].dtype, Lo, ws, true, true, s);
+        for (int r = 0; r < 2; ++r) batch_gemv_any(probs[0].dtype, Lo, ws, true, true, s, true);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess) {
             st = record_cuda_error(cudaGetLastError(), "batch tile tuning", __FILE__, __LINE__);
@@ -1779,15 +1875,21 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
     const GOne *d_one = at<GOne>(ws, Lo.o_one);
     int launches = 0;
     setup_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
+    // kernels per product: the GEMV pair (or z alone) over the n x T
+    // problems, one grouped fused launch per cluster size over the others
+    int fused_launches = 0;
+    for (int g = 0; g < kGroupSizes; ++g) fused_launches += Lo.lcount[g] > 0 ? 1 : 0;
+    const int per_pair = (Lo.nt_tiles > 0 ? 1 : 0) + (Lo.nn_tiles > 0 ? 1 : 0) + fused_launches;
+    const int per_z = (Lo.nt_tiles > 0 ? 1 : 0) + fused_launches;
     if (!(O.alpha > 0.0)) {
         for (int it = 0; it < O.power_iters; ++it) {
-            batch_gemv_any(dt, Lo, ws, true, true, s);
+            MV_TRY(batch_gemv_any(dt, Lo, ws, true, true, s));
             power_norm_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
-            launches += 3;
+            launches += per_pair + 1;
         }
         if (O.power_iters > 0) {
-            batch_gemv_any(dt, Lo, ws, true, false, s);
-            ++launches;
+            MV_TRY(batch_gemv_any(dt, Lo, ws, true, false, s));
+            launches += per_z;
         }
     }
     step_size_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
@@ -1813,12 +1915,13 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
         MV_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
         cudaGraph_t graph;
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            for (int c = 0; c < chunk; ++c) {
-                batch_gemv_any(dt, Lo, ws, false, true, cs);
-                batch_step(Lo, ws, cnt, cs);
+            int cst = MV_OK;
+            for (int c = 0; c < chunk && cst == MV_OK; ++c) {
+                cst = batch_gemv_any(dt, Lo, ws, false, true, cs);
+                if (cst == MV_OK && batch_step(Lo, ws, cnt, cs) != cudaSuccess) cst = MV_ERR_CUDA;
             }
             if (cudaStreamEndCapture(cs, &graph) == cudaSuccess) {
-                if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
+                if (cst != MV_OK || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) exec = nullptr;
                 cudaGraphDestroy(graph);
             }
         }
@@ -1832,11 +1935,11 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
             MV_CUDA_TRY(cudaGraphLaunch(exec, s));
         } else {
             for (int i = 0; i < chunk; ++i) {
-                batch_gemv_any(dt, Lo, ws, false, true, s);
+                MV_TRY(batch_gemv_any(dt, Lo, ws, false, true, s));
                 MV_CUDA_TRY(batch_step(Lo, ws, cnt, s));
             }
         }
-        launches += 3 * chunk;
+        launches += (per_pair + 1) * chunk;
         for (int i = 0; i < cnt; ++i)
             MV_CUDA_TRY(cudaMemcpyAsync(&hs[i], reinterpret_cast<char *>(ws) + Lo.base[i] + Lo.plans[i].o_state,
                                         sizeof(SolveState), cudaMemcpyDeviceToHost, s));
@@ -1848,10 +1951,12 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
     if (exec) cudaGraphExecDestroy(exec);
     // objectives: z = L^T x for every problem, then ||z||^2 + gamma ||x||^2
     to_y32_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
-    batch_gemv_any(dt, Lo, ws, true, false, s);
+    MV_TRY(batch_gemv_any(dt, Lo, ws, true, false, s));
     objective_grouped<<<cnt, kStepThreads, 0, s>>>(d_one);
-    launches += 3;
+    launches += per_z + 2;
     MV_CUDA_TRY(cudaGetLastError());
+    int lerr = 0;
+    MV_CUDA_TRY(cudaMemcpyAsync(&lerr, at<int>(ws, Lo.o_lerr), sizeof(int), cudaMemcpyDeviceToHost, s));
     for (int i = 0; i < cnt; ++i) {
         MV_CUDA_TRY(cudaMemcpyAsync(h_x_dev[i], reinterpret_cast<char *>(ws) + Lo.base[i] + Lo.plans[i].o_x,
                                     8 * (size_t)Lo.plans[i].n, cudaMemcpyDeviceToDevice, s));
@@ -1874,7 +1979,13 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
         I.lambda_hat = hs[i].lambda_hat;
         I.nu = hs[i].nu;
         I.launches = launches;
+        if (lerr != 0 && Lo.gpl[(size_t)i].G > 0) I.status = MV_ERR_TIMEOUT;
         if (I.status != MV_OK && worst == MV_OK) worst = I.status;
+    }
+    if (lerr != 0) {
+        char msg[96];
+        snprintf(msg, sizeof(msg), "grouped single-pass product: a bounded wait timed out (code %d)", lerr);
+        return record_message(MV_ERR_TIMEOUT, msg);
     }
     return worst;
 }

@@ -726,7 +726,9 @@ class BatchSolver:
     """Independent problems of uneven size solved together (mv_npga_solve_batch).
 
     ``problems`` is a list of dicts with keys L, mu, R_target, T and optional
-    gamma, row_scale, power_start, mode; all L share one dtype."""
+    gamma, row_scale, power_start, mode and layout ("nt": L is n x ld, the
+    grouped GEMV pair; "tn": L^T is T x ld, the grouped single pass); all L
+    share one dtype."""
 
     def __init__(self, problems, dtype="f32", **opts):
         self._keep = problems
@@ -734,14 +736,15 @@ class BatchSolver:
         self.probs = (Problem * self.count)()
         for i, q in enumerate(problems):
             self.probs[i] = make_problem(q["L"], q["mu"], q["R_target"], q["T"], q.get("gamma", 0.0), dtype,
-                                         q.get("row_scale"), q.get("mode", "ge"), q.get("power_start"))
+                                         q.get("row_scale"), q.get("mode", "ge"), q.get("power_start"),
+                                         q.get("layout", "nt"))
         self.opts = solve_opts(**opts)
         nb = lib().mv_batch_workspace_size(self.probs, self.count)
         if nb == 0:
             raise MvError(MV_ERR_INVALID_ARG, "mv_batch_workspace_size")
         dev = problems[0]["L"].device
         self.ws = _workspace(nb, dev)
-        self.xs = [torch.zeros(q["L"].shape[0], dtype=torch.float64, device=dev) for q in problems]
+        self.xs = [torch.zeros(q["mu"].shape[0], dtype=torch.float64, device=dev) for q in problems]
         self._xp = (C.c_void_p * self.count)(*[x.data_ptr() for x in self.xs])
 
     def solve(self, allow=(MV_ERR_NOT_CONVERGED,)):
