@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-row-oracles", action="store_true", help="skip the oracle timings of the further rows")
-    ap.add_argument("--profile", default=None, choices=["sketch", "frontier"],
+    ap.add_argument("--profile", default=None, choices=["sketch", "frontier", "batch"],
                     help="run one instance of that workload at --shape (for ncu) and exit, printing its time")
     return ap.parse_args()
 
@@ -126,12 +126,13 @@ def jsonable(o, path="line"):
 
 
 def peaks_tensor():
-    """Measured dense BF16 tensor peak (burst; the formation GEMM is timed alone)."""
+    """(dense BF16 tensor peak in TFLOP/s, "measured" | "fallback"): the burst
+    figure (the GEMMs are timed alone), else the 1.9 PFLOP/s fallback."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"])
+            return float(json.load(f)["bf16_tflops"]), "measured"
     except Exception:
-        return 1900.0
+        return 1900.0, "fallback"
 
 
 # kernel -> (committed ncu summary, source file whose hash the summary records)
@@ -470,11 +471,33 @@ def reference_arm(args):
 
 def profile_run(args):
     """One instance of a workload for a profiler: the sketch GEMM (L in BF16
-    times a Phi drawn from seed 2, m = --sketch-m) or one 64-target frontier
-    solve (BF16, targets between the 10th and 90th percentiles of mu)."""
+    times a Phi drawn from seed 2, m = --sketch-m), one 64-target frontier
+    solve (BF16, targets between the 10th and 90th percentiles of mu), or
+    one solve of the first --batch-count problems of the uneven batch (FP32,
+    L stored transposed; a warm-up solve first)."""
     import torch
     from paper_2604_02917_gb300 import mv
     from synth import factor_returns
+    if args.profile == "batch":
+        from synth import factor_returns_device, uneven_problem_sizes
+        probs = []
+        for bm in uneven_problem_sizes(args.batch_count):
+            Rb = factor_returns_device(bm, torch.device("cuda"))
+            Lb, _, mub, _ = mv.center_factor(Rb, "f32", layout="tn")
+            del Rb
+            probs.append({"L": Lb, "mu": mub, "R_target": float(torch.quantile(mub, 0.6).item()), "T": bm.T,
+                          "layout": "tn"})
+        bsv = mv.BatchSolver(probs, eps=args.eps)
+        bsv.solve()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, infos = bsv.solve()
+        e1.record()
+        torch.cuda.synchronize()
+        its = sorted(i["iterations"] for i in infos)
+        print(f"batch {len(probs)} problems: {e0.elapsed_time(e1):.3f} ms; iterations " + " ".join(map(str, its)),
+              flush=True)
+        return
     model = workload(args, 0)
     R = torch.from_numpy(factor_returns(model, np.float32)).cuda()
     L, rs, mu, _ = mv.center_factor(R, "bf16")
@@ -679,7 +702,7 @@ def main():
     if not args.no_sigma and args.dtype == "f32":
         R_dev = torch.from_numpy(R32).to(dev)
         sigma_res = {}
-        peak_tf = peaks_tensor()
+        peak_tf, peak_tf_src = peaks_tensor()
         for sdt in ("f32", "bf16"):
             Lx, rsx, _, _ = mv.center_factor(R_dev, sdt, layout="nt")
             S = mv.sigma_form(Lx, model.T, sdt, rsx)              # warm-up (attributes, tensor maps)
@@ -697,7 +720,7 @@ def main():
             flops = nb * (nb + 1) // 2 * 128 * 128 * (-(-model.T // 64) * 64) * 2 * segs
             entry = {"form_s": t_form,
                      "form_roofline": {"bound": "tensor", "achieved": round(flops / t_form / 1e12, 1),
-                                       "peak": peak_tf, "unit": "TFLOP/s",
+                                       "peak": peak_tf, "peak_source": peak_tf_src, "unit": "TFLOP/s",
                                        "frac": round(flops / t_form / 1e12 / peak_tf, 4),
                                        "traffic": committed_traffic("sigma_gemm") if sdt == "f32" and
                                        (model.n, model.T) == (5440, 48374) else None,
@@ -775,13 +798,12 @@ def main():
         _, gfull = mv.gradient(L, xs, model.T, layout=args.layout, with_z=False)  # 2 L L^T x, full FP32 model
         f_str_full = float(torch.dot(xs, gfull).item()) / 2.0
         f_full = infos[-1]["objective"]
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            bf16_peak = float(json.load(f).get("bf16_tflops", 1900.0))
+        bf16_peak, bf16_src = peaks_tensor()
         tflops = flop / (min(sk_ms) * 1e-3) / 1e12
         str_res = {"gaussian_draw": {"ms": gen_ms, "entries": args.sketch_m * model.T, "seed": 2,
                                      "note": "Phi^T drawn on the device (Philox4x32-10 + Box-Muller, BF16)"},
                    "sketch": {"m": args.sketch_m, "ms": min(sk_ms), "tflop": flop / 1e12,
-                              "achieved_tflops": round(tflops, 1), "peak_tflops": bf16_peak,
+                              "achieved_tflops": round(tflops, 1), "peak_tflops": bf16_peak, "peak_source": bf16_src,
                               "frac": round(tflops / bf16_peak, 4), "bound": "tensor",
                               "traffic": committed_traffic("sketch") if full_cs_shape else None},
                    "truncate": {"k": args.str_k, "ms": tr_ms, "first_call_s": round(t_first, 3), "gamma": gamma,

@@ -28,6 +28,8 @@
 // translation unit's g_gemm_err and the CTA winds down.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "gemm.cuh"
 
 namespace mv {
@@ -59,6 +61,51 @@ struct GemmEpi {
     float gamma = 0.0f;
     const float *rscale = nullptr;      // row i of the product scaled by rscale[i]
 };
+
+// Epilogue store of one tile row: 128 columns from cb of the FP32 running
+// sums acc, C[row][cb + j] = alpha rowscale[row] acc[j] + beta X1 + gamma X2.
+__device__ __forceinline__ void chunk_store(const float (&acc)[128], int row, int cb, int N, float *__restrict__ C,
+                                            int64_t ldc, const GemmEpi &e) {
+    const float sc = e.rscale ? e.rscale[row] * e.alpha : e.alpha;
+    float *crow = C + (int64_t)row * ldc;
+    const float *x1 = e.X1 ? e.X1 + (int64_t)row * e.ld1 : nullptr;
+    const float *x2 = e.X2 ? e.X2 + (int64_t)row * e.ld2 : nullptr;
+    const bool vec = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0 &&
+                     (!x1 || ((e.ld1 & 3) == 0 && (reinterpret_cast<uintptr_t>(e.X1) & 15) == 0)) &&
+                     (!x2 || ((e.ld2 & 3) == 0 && (reinterpret_cast<uintptr_t>(e.X2) & 15) == 0));
+#pragma unroll
+    for (int qq = 0; qq < 32; ++qq) {
+        const int col = cb + 4 * qq;
+        if (vec && col + 4 <= N) {
+            float4 v = make_float4(sc * acc[4 * qq], sc * acc[4 * qq + 1], sc * acc[4 * qq + 2],
+                                   sc * acc[4 * qq + 3]);
+            if (x1) {
+                const float4 w = *reinterpret_cast<const float4 *>(x1 + col);
+                v.x = fmaf(e.beta, w.x, v.x);
+                v.y = fmaf(e.beta, w.y, v.y);
+                v.z = fmaf(e.beta, w.z, v.z);
+                v.w = fmaf(e.beta, w.w, v.w);
+            }
+            if (x2) {
+                const float4 w = *reinterpret_cast<const float4 *>(x2 + col);
+                v.x = fmaf(e.gamma, w.x, v.x);
+                v.y = fmaf(e.gamma, w.y, v.y);
+                v.z = fmaf(e.gamma, w.z, v.z);
+                v.w = fmaf(e.gamma, w.w, v.w);
+            }
+            *reinterpret_cast<float4 *>(crow + col) = v;
+        } else {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (col + u >= N) break;
+                float v = sc * acc[4 * qq + u];
+                if (x1) v = fmaf(e.beta, x1[col + u], v);
+                if (x2) v = fmaf(e.gamma, x2[col + u], v);
+                crow[col + u] = v;
+            }
+        }
+    }
+}
 
 template <int BN, int NA>
 __global__ void __launch_bounds__(GemmChunkCfg<BN, NA>::THREADS, 1)
@@ -196,52 +243,193 @@ gemm_chunk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         if (!ok) {
             if (lane == 0) atomicExch(&g_gemm_err, 14);
         } else if (row < M) {
-            const float sc = e.rscale ? e.rscale[row] * e.alpha : e.alpha;
-            const int cb = n0 + g * 128;
-            float *crow = C + (int64_t)row * ldc;
-            const float *x1 = e.X1 ? e.X1 + (int64_t)row * e.ld1 : nullptr;
-            const float *x2 = e.X2 ? e.X2 + (int64_t)row * e.ld2 : nullptr;
-            const bool vec = (ldc & 3) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0 &&
-                             (!x1 || ((e.ld1 & 3) == 0 && (reinterpret_cast<uintptr_t>(e.X1) & 15) == 0)) &&
-                             (!x2 || ((e.ld2 & 3) == 0 && (reinterpret_cast<uintptr_t>(e.X2) & 15) == 0));
-#pragma unroll
-            for (int qq = 0; qq < 32; ++qq) {
-                const int col = cb + 4 * qq;
-                if (vec && col + 4 <= N) {
-                    float4 v = make_float4(sc * acc[4 * qq], sc * acc[4 * qq + 1], sc * acc[4 * qq + 2],
-                                           sc * acc[4 * qq + 3]);
-                    if (x1) {
-                        const float4 w = *reinterpret_cast<const float4 *>(x1 + col);
-                        v.x = fmaf(e.beta, w.x, v.x);
-                        v.y = fmaf(e.beta, w.y, v.y);
-                        v.z = fmaf(e.beta, w.z, v.z);
-                        v.w = fmaf(e.beta, w.w, v.w);
-                    }
-                    if (x2) {
-                        const float4 w = *reinterpret_cast<const float4 *>(x2 + col);
-                        v.x = fmaf(e.gamma, w.x, v.x);
-                        v.y = fmaf(e.gamma, w.y, v.y);
-                        v.z = fmaf(e.gamma, w.z, v.z);
-                        v.w = fmaf(e.gamma, w.w, v.w);
-                    }
-                    *reinterpret_cast<float4 *>(crow + col) = v;
-                } else {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        if (col + u >= N) break;
-                        float v = sc * acc[4 * qq + u];
-                        if (x1) v = fmaf(e.beta, x1[col + u], v);
-                        if (x2) v = fmaf(e.gamma, x2[col + u], v);
-                        crow[col + u] = v;
-                    }
-                }
-            }
+            chunk_store(acc, row, n0 + g * 128, N, C, ldc, e);
         }
     }
     umma::fence_before_sync();
     __syncthreads();
     umma::fence_after_sync();
     if (warp == 1) umma::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ CTA-pair form
+// The same product on 256 x 256 tiles, each run by a pair of CTAs (a cluster
+// of 2) with cta_group::2 MMAs: CTA r of the pair loads rows 128 r .. of the
+// A tile and rows 128 r .. of the B tile (half of it), rank 0 issues the
+// 256 x 256 x 16 MMAs over both CTAs' shared memory, and each CTA's tensor
+// memory accumulates its own 128 rows x 256 columns.  Per CTA and k-step
+// that is 32 KB of operands for 128 x 256 x 64 multiply-adds, against 48 KB
+// for the one-CTA 128 x 256 tile: a third fewer L2 -> SM bytes per MMA.
+// Barriers: rank 0's full[s] counts both CTAs' bytes (the peer's TMA
+// completes on it); a multicast commit frees stage s in both CTAs and hands
+// buffer b to both epilogues; both CTAs' epilogue warps arrive on rank 0's
+// tempty[b].  A cluster barrier opens and closes the kernel, so no CTA
+// addresses a peer that has not started or has already left.
+template <int NA>
+struct GemmPairCfg {
+    static constexpr int BN = 256;                           // columns of the pair's tile
+    static constexpr int EPI_WARPS = 8;                      // 128 rows x 2 column groups
+    static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+    static constexpr uint32_t A_BYTES = kBM * kBK * 2;       // this CTA's 128 rows
+    static constexpr uint32_t B_BYTES = (BN / 2) * kBK * 2;  // this CTA's half of B
+    static constexpr uint32_t STAGE = NA * A_BYTES + B_BYTES;
+    static constexpr int S = (int)((196608u / STAGE) < 8u ? (196608u / STAGE) : 8u);
+    static constexpr int NBAR = 2 * S + 4;
+    static constexpr size_t SMEM = 1024 + (size_t)S * STAGE + NBAR * 8 + 16;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;
+};
+
+template <int NA>
+__global__ void __launch_bounds__(GemmPairCfg<NA>::THREADS, 1)
+gemm_chunk_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       const __grid_constant__ CUtensorMap tmA2, float *__restrict__ C, int M, int N, int K,
+                       int64_t ldc, GemmEpi e, int raster) {
+    using Cfg = GemmPairCfg<NA>;
+    constexpr int S = Cfg::S;
+    constexpr int CH = kChunkSteps;
+    constexpr int BN = Cfg::BN;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = smem;
+    uint8_t *sB = smem + S * NA * Cfg::A_BYTES;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S * Cfg::STAGE);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + Cfg::NBAR);
+    const uint32_t full0 = umma::smem_u32(bars), empty0 = umma::smem_u32(bars + S);
+    const uint32_t tfull0 = umma::smem_u32(bars + 2 * S), tempty0 = umma::smem_u32(bars + 2 * S + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = umma::cluster_ctarank();            // 0: issues the MMAs
+    // the pair's tile (pr, ct); grouped raster over pairs as in gemm.cuh
+    const int npr = (int)gridDim.x >> 1, nct = (int)gridDim.y;
+    int pr = (int)blockIdx.x >> 1, ct = (int)blockIdx.y;
+    if (raster && npr > kRasterRows / 2) {
+        const int rows = kRasterRows / 2;
+        const int lin = pr + npr * (int)blockIdx.y;
+        const int per = rows * nct, g = lin / per, first = g * rows;
+        const int gh = min(npr - first, rows), rem = lin - g * per;
+        pr = first + rem % gh;
+        ct = rem / gh;
+    }
+    const int m0 = (2 * pr + (int)rank) * kBM;                // this CTA's rows of A and of D
+    const int n0 = ct * BN;                                    // the pair's columns
+    const int nb0 = n0 + (int)rank * (BN / 2);                 // this CTA's half of B
+    const int nk = (K + kBK - 1) / kBK;
+    const int nch = (nk + CH - 1) / CH;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            umma::mbar_init(full0 + 8 * s, 1);
+            umma::mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            umma::mbar_init(tfull0 + 8 * b, 1);
+            umma::mbar_init(tempty0 + 8 * b, 2 * Cfg::EPI_WARPS);
+        }
+        umma::mbar_fence_init();
+    }
+    if (warp == 1) {
+        umma::tmem_alloc_pair(umma::smem_u32(tmem_slot), Cfg::TMEM_COLS);
+        umma::tmem_relinquish_pair();
+    }
+    umma::fence_before_sync();
+    cooperative_groups::this_cluster().sync();                                 // both CTAs' barriers exist
+    umma::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t full_r0 = umma::mapa_rank(full0, 0);         // rank 0's full[0], cluster address
+
+    if (warp == 0) {
+        if (lane == 0) {
+            umma::prefetch_tensormap(&tmA);
+            umma::prefetch_tensormap(&tmB);
+            if (NA > 1) umma::prefetch_tensormap(&tmA2);
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % S;
+                const uint32_t ph = (uint32_t)(kt / S) & 1u;
+                if (!umma::mbar_wait(empty0 + 8 * s, ph ^ 1u, kWaitNs)) {
+                    atomicExch(&g_gemm_err, 21);
+                    break;
+                }
+                const uint32_t fb = full_r0 + 8u * (uint32_t)s;
+                if (rank == 0) umma::mbar_arrive_expect_tx(full0 + 8 * s, 2 * Cfg::STAGE);
+                umma::tma_load_2d_pair(umma::smem_u32(sA + s * NA * Cfg::A_BYTES), &tmA, kt * kBK, m0, fb);
+                if (NA > 1)
+                    umma::tma_load_2d_pair(umma::smem_u32(sA + (s * NA + 1) * Cfg::A_BYTES), &tmA2, kt * kBK, m0,
+                                           fb);
+                umma::tma_load_2d_pair(umma::smem_u32(sB + s * Cfg::B_BYTES), &tmB, kt * kBK, nb0, fb);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            constexpr uint32_t idesc = umma::idesc_bf16_f32(2 * kBM, BN);
+            for (int kt = 0; kt < nk; ++kt) {
+                const int c = kt / CH, j = kt - c * CH, b = c & 1;
+                if (j == 0 && c >= 2) {            // buffer b drained by both epilogues (chunk c - 2)
+                    if (!umma::mbar_wait(tempty0 + 8 * b, (uint32_t)((c >> 1) - 1) & 1u, 2 * kWaitNs)) {
+                        atomicExch(&g_gemm_err, 22);
+                        break;
+                    }
+                    umma::fence_after_sync();
+                }
+                const int s = kt % S;
+                const uint32_t ph = (uint32_t)(kt / S) & 1u;
+                if (!umma::mbar_wait(full0 + 8 * s, ph, kWaitNs)) {
+                    atomicExch(&g_gemm_err, 23);
+                    break;
+                }
+                umma::fence_after_sync();
+                const uint32_t dst = tmem + (uint32_t)(b * BN);
+                const uint64_t db = umma::desc_kmajor_sw128(umma::smem_u32(sB + s * Cfg::B_BYTES));
+#pragma unroll
+                for (int a = 0; a < NA; ++a) {
+                    const uint64_t da = umma::desc_kmajor_sw128(umma::smem_u32(sA + (s * NA + a) * Cfg::A_BYTES));
+#pragma unroll
+                    for (int k = 0; k < kBK / 16; ++k)
+                        umma::mma_bf16_pair(dst, da + 2 * k, db + 2 * k, idesc, (j | k | a) != 0 ? 1u : 0u);
+                }
+                umma::mma_commit_pair(empty0 + 8 * s, (uint16_t)3);
+                if (j == CH - 1 || kt == nk - 1) umma::mma_commit_pair(tfull0 + 8 * b, (uint16_t)3);
+            }
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3, g = (warp - 2) >> 2;
+        const int row = m0 + 32 * q + lane;
+        const uint32_t tempty_r0 = umma::mapa_rank(tempty0, 0);
+        float acc[128];
+#pragma unroll
+        for (int i = 0; i < 128; ++i) acc[i] = 0.0f;
+        bool ok = true;
+        for (int c = 0; c < nch; ++c) {
+            const int b = c & 1;
+            if (!umma::mbar_wait(tfull0 + 8 * b, (uint32_t)(c >> 1) & 1u, 4 * kWaitNs)) {
+                ok = false;
+                break;
+            }
+            umma::fence_after_sync();
+            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * BN + g * 128);
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                uint32_t r[32];
+                umma::tmem_ld_32x32b_x32(ta + (uint32_t)(qq * 32), r);
+                umma::tmem_ld_wait();
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) acc[qq * 32 + jj] += __uint_as_float(r[jj]);
+            }
+            umma::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) umma::mbar_arrive_cluster(tempty_r0 + 8u * (uint32_t)b);
+        }
+        if (!ok) {
+            if (lane == 0) atomicExch(&g_gemm_err, 24);
+        } else if (row < M) {
+            chunk_store(acc, row, n0 + g * 128, N, C, ldc, e);
+        }
+    }
+    umma::fence_before_sync();
+    cooperative_groups::this_cluster().sync();                                 // the peer no longer reads or signals us
+    umma::fence_after_sync();
+    if (warp == 1) umma::tmem_dealloc_pair(tmem, Cfg::TMEM_COLS);
 }
 
 // Row-wise three-piece split (the non-transposed companion of split3_t_kernel
@@ -283,11 +471,65 @@ static void gemmc_launch(const CUtensorMap &ta, const CUtensorMap &tb, const CUt
                                                                     (int)K, ldc, e, raster);
 }
 
+template <int NA>
+static int gemmc_pair_set_attrs() {
+    static int st = -1;
+    if (st < 0)
+        st = cudaFuncSetAttribute(gemm_chunk_pair_kernel<NA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)GemmPairCfg<NA>::SMEM) == cudaSuccess
+                 ? MV_OK
+                 : record_message(MV_ERR_CUDA, "chunked pair GEMM: shared-memory attribute refused");
+    return st;
+}
+
+// gemmc<256> on CTA pairs (256 x 256 tiles; clusters of 2 along M).  Tensor
+// maps: A boxes of 128 rows, B boxes of 128 rows (half a tile).
+static int gemmc_pair(const void *A, const void *A2, int64_t M, int64_t lda, const void *B, int64_t N, int64_t ldb,
+                      int64_t K, float *C, int64_t ldc, const GemmEpi &e, cudaStream_t s, int raster = 1) {
+    if (K < 1) return record_message(MV_ERR_INVALID_ARG, "chunked GEMM: K must be >= 1");
+    CUtensorMap ta, tb, ta2;
+    MV_TRY(make_map_bf16(&ta, A, M, K, lda, kBM));
+    MV_TRY(make_map_bf16(&tb, B, N, K, ldb, 128));
+    if (A2) MV_TRY(make_map_bf16(&ta2, A2, M, K, lda, kBM));
+    const unsigned pairs = (unsigned)((M + 2 * kBM - 1) / (2 * kBM));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * pairs, (unsigned)((N + 255) / 256));
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t err;
+    if (A2) {
+        MV_TRY(gemmc_pair_set_attrs<2>());
+        cfg.blockDim = dim3(GemmPairCfg<2>::THREADS);
+        cfg.dynamicSmemBytes = GemmPairCfg<2>::SMEM;
+        err = cudaLaunchKernelEx(&cfg, gemm_chunk_pair_kernel<2>, ta, tb, ta2, C, (int)M, (int)N, (int)K, ldc, e,
+                                 raster);
+    } else {
+        MV_TRY(gemmc_pair_set_attrs<1>());
+        cfg.blockDim = dim3(GemmPairCfg<1>::THREADS);
+        cfg.dynamicSmemBytes = GemmPairCfg<1>::SMEM;
+        err = cudaLaunchKernelEx(&cfg, gemm_chunk_pair_kernel<1>, ta, tb, ta, C, (int)M, (int)N, (int)K, ldc, e,
+                                 raster);
+    }
+    if (err != cudaSuccess) return record_cuda_error(err, "chunked pair GEMM launch", __FILE__, __LINE__);
+    return MV_OK;
+}
+
+// 256-column tiles run on CTA pairs.
+constexpr bool kChunkPairs = true;
+
 // Tensor maps + launch, no synchronisation.  A2 non-NULL: (A + A2) B^T.
+// BN = 256 takes the CTA-pair kernel (kChunkPairs).
 template <int BN>
 static int gemmc(const void *A, const void *A2, int64_t M, int64_t lda, const void *B, int64_t N, int64_t ldb,
                  int64_t K, float *C, int64_t ldc, const GemmEpi &e, cudaStream_t s, int raster = 1) {
     if (K < 1) return record_message(MV_ERR_INVALID_ARG, "chunked GEMM: K must be >= 1");
+    if (BN == 256 && kChunkPairs) return gemmc_pair(A, A2, M, lda, B, N, ldb, K, C, ldc, e, s, raster);
     CUtensorMap ta, tb, ta2;
     MV_TRY(make_map_bf16(&ta, A, M, K, lda, kBM));
     MV_TRY(make_map_bf16(&tb, B, N, K, ldb, BN));

@@ -45,9 +45,13 @@ LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device, bool tn = false
 // stream s; capturable.  done (nullable): the launch returns at once if *done.
 // z (nullable): also writes z = L^T y (T floats), which the pass forms anyway.
 // For a transposed plan, L points at L^T (T x n, leading dim ld).
+// pdl (transposed plans): launch as a programmatic dependent of the previous
+// kernel, whose early trigger lets the pass stream its first blocks of L
+// while that kernel finishes.  Only where no predecessor since the last
+// ordinary launch writes L.
 int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
                const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s,
-               float *z = nullptr);
+               float *z = nullptr, bool pdl = false);
 
 // ---- grouped transposed pass: many problems (each L^T stored T x n) in one
 // launch per cluster size; the batch solve's product.
@@ -65,13 +69,15 @@ size_t llt_group_scratch_bytes(int64_t n, int G);           // per-problem parti
 size_t llt_group_ticket_offset(int64_t n, int G);           // tickets inside that scratch
 // Writes the descriptor of one problem (tensor map + arguments) into host
 // memory dst (llt_group_bytes() bytes).  done, z: nullable as in llt_launch.
+// early: the descriptor is for launches with pdl (see llt_launch).
 int llt_group_write(void *dst, const LltGroupPlan &gp, int dt, const void *L, int64_t n, int64_t T, int64_t ld,
                     const float *y32, const float *row_scale, void *scratch, int *err, const int *done, double *g,
-                    float *g32, float *z);
+                    float *g32, float *z, bool early = false);
 // One grouped launch over nclusters clusters of size C (descriptors and the
-// (problem, cluster) list in device memory).
+// (problem, cluster) list in device memory); pdl as in llt_launch, with
+// descriptors written with early = true.
 cudaError_t llt_launch_grouped(int dt, int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
-                               cudaStream_t s);
+                               cudaStream_t s, bool pdl = false);
 
 // Per-dtype entry points (llt_<dtype>.cu).
 int llt_max_clusters_f32(int C, int RB, size_t smem);
@@ -88,10 +94,10 @@ cudaError_t llt_launch_tn_f32(int C, int G, size_t smem, const void *map, const 
 cudaError_t llt_launch_tn_bf16(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
 cudaError_t llt_launch_tn_fp8(int C, int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s);
 cudaError_t llt_launch_grouped_f32(int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool pdl);
 cudaError_t llt_launch_grouped_bf16(int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
-                                    cudaStream_t s);
+                                    cudaStream_t s, bool pdl);
 cudaError_t llt_launch_grouped_fp8(int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
-                                   cudaStream_t s);
+                                   cudaStream_t s, bool pdl);
 
 }  // namespace mv

@@ -120,7 +120,7 @@ LltPlan llt_plan(int dt, int64_t n, int64_t T, bool with_device, bool tn) {
 
 int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, int64_t ld, const float *y32,
                const float *row_scale, const LltScratch &sc, const int *done, double *g, float *g32, cudaStream_t s,
-               float *z) {
+               float *z, bool pdl) {
     if (!lp.ok) return record_message(MV_ERR_UNSUPPORTED, "fused pass: no cluster shape fits this n and T");
     CUtensorMap map;
     if (lp.tn)
@@ -146,6 +146,7 @@ int llt_launch(const LltPlan &lp, int dt, const void *L, int64_t n, int64_t T, i
     a.nbox = lp.nbox;
     a.nb = lp.nb;
     a.G = lp.G;
+    a.early = (pdl && lp.tn) ? 1 : 0;
     cudaError_t e;
     if (lp.tn)
         e = dt == MV_F32    ? llt_launch_tn_f32(lp.C, lp.G, lp.smem, &map, a, s)
@@ -201,7 +202,7 @@ size_t llt_group_scratch_bytes(int64_t n, int G) { return llt_group_ticket_offse
 
 int llt_group_write(void *dst, const LltGroupPlan &gp, int dt, const void *L, int64_t n, int64_t T, int64_t ld,
                     const float *y32, const float *row_scale, void *scratch, int *err, const int *done, double *g,
-                    float *g32, float *z) {
+                    float *g32, float *z, bool early) {
     LltGroup d;
     memset(&d, 0, sizeof(d));
     MV_TRY(make_map_lltt(&d.map, dt, L, n, T, ld, 32 / dtype_size(dt)));
@@ -226,16 +227,17 @@ int llt_group_write(void *dst, const LltGroupPlan &gp, int dt, const void *L, in
     a.nbox = gp.npc / kLltBoxCols;
     a.nb = gp.nb;
     a.G = gp.G;
+    a.early = early ? 1 : 0;
     memcpy(dst, &d, sizeof(d));
     return MV_OK;
 }
 
 cudaError_t llt_launch_grouped(int dt, int C, int nclusters, size_t smem, const void *groups, const int2 *clusters,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool pdl) {
     if (nclusters < 1) return cudaSuccess;
-    if (dt == MV_F32) return llt_launch_grouped_f32(C, nclusters, smem, groups, clusters, s);
-    if (dt == MV_BF16) return llt_launch_grouped_bf16(C, nclusters, smem, groups, clusters, s);
-    return llt_launch_grouped_fp8(C, nclusters, smem, groups, clusters, s);
+    if (dt == MV_F32) return llt_launch_grouped_f32(C, nclusters, smem, groups, clusters, s, pdl);
+    if (dt == MV_BF16) return llt_launch_grouped_bf16(C, nclusters, smem, groups, clusters, s, pdl);
+    return llt_launch_grouped_fp8(C, nclusters, smem, groups, clusters, s, pdl);
 }
 
 }  // namespace mv

@@ -26,7 +26,9 @@ int attrs() {
     return st;
 }
 
-cudaLaunchConfig_t config(int C, int G, size_t smem, cudaStream_t s, cudaLaunchAttribute *attr) {
+// attr: room for two attributes.  pdl: launch as a programmatic dependent
+// of the previous kernel in the stream (the kernel's early-load path).
+cudaLaunchConfig_t config(int C, int G, size_t smem, cudaStream_t s, cudaLaunchAttribute *attr, bool pdl = false) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * G));
     cfg.blockDim = dim3(kLltThreads);
@@ -38,13 +40,18 @@ cudaLaunchConfig_t config(int C, int G, size_t smem, cudaStream_t s, cudaLaunchA
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (pdl) {
+        attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[1].val.programmaticStreamSerializationAllowed = 1;
+        cfg.numAttrs = 2;
+    }
     return cfg;
 }
 
 template <int C, int RB>
 int max_clusters(size_t smem) {
     if (attrs<C, RB>() != MV_OK) return 0;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     const cudaLaunchConfig_t cfg = config(C, kLltMaxClusters, smem, nullptr, attr);
     int num = 0;
     if (cudaOccupancyMaxActiveClusters(&num, llt_kernel<MV_LLT_DT, C, RB>, &cfg) != cudaSuccess) {
@@ -57,7 +64,7 @@ int max_clusters(size_t smem) {
 template <int C, int RB>
 cudaError_t launch(int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s) {
     if (attrs<C, RB>() != MV_OK) return cudaErrorInvalidValue;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     const cudaLaunchConfig_t cfg = config(C, G, smem, s, attr);
     return cudaLaunchKernelEx(&cfg, llt_kernel<MV_LLT_DT, C, RB>, *reinterpret_cast<const CUtensorMap *>(map), a);
 }
@@ -81,7 +88,7 @@ int attrs_tn() {
 template <int C>
 int max_clusters_tn(size_t smem) {
     if (attrs_tn<C>() != MV_OK) return 0;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     const cudaLaunchConfig_t cfg = config(C, kLltMaxClusters, smem, nullptr, attr);
     int num = 0;
     if (cudaOccupancyMaxActiveClusters(&num, lltt_kernel<MV_LLT_DT, C>, &cfg) != cudaSuccess) {
@@ -94,8 +101,8 @@ int max_clusters_tn(size_t smem) {
 template <int C>
 cudaError_t launch_tn(int G, size_t smem, const void *map, const LltArgs &a, cudaStream_t s) {
     if (attrs_tn<C>() != MV_OK) return cudaErrorInvalidValue;
-    cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = config(C, G, smem, s, attr);
+    cudaLaunchAttribute attr[2];
+    const cudaLaunchConfig_t cfg = config(C, G, smem, s, attr, a.early != 0);
     return cudaLaunchKernelEx(&cfg, lltt_kernel<MV_LLT_DT, C>, *reinterpret_cast<const CUtensorMap *>(map), a);
 }
 
@@ -116,10 +123,11 @@ int attrs_grouped() {
 }
 
 template <int C>
-cudaError_t launch_grouped(int nclusters, size_t smem, const void *groups, const int2 *clusters, cudaStream_t s) {
+cudaError_t launch_grouped(int nclusters, size_t smem, const void *groups, const int2 *clusters, cudaStream_t s,
+                           bool pdl) {
     if (attrs_grouped<C>() != MV_OK) return cudaErrorInvalidValue;
-    cudaLaunchAttribute attr[1];
-    const cudaLaunchConfig_t cfg = config(C, nclusters, smem, s, attr);
+    cudaLaunchAttribute attr[2];
+    const cudaLaunchConfig_t cfg = config(C, nclusters, smem, s, attr, pdl);
     return cudaLaunchKernelEx(&cfg, lltt_grouped_kernel<MV_LLT_DT, C>, reinterpret_cast<const LltGroup *>(groups),
                               clusters);
 }
@@ -164,8 +172,8 @@ cudaError_t MV_LLT_CAT(llt_launch_tn_, MV_LLT_SUFFIX)(int C, int G, size_t smem,
 }
 
 cudaError_t MV_LLT_CAT(llt_launch_grouped_, MV_LLT_SUFFIX)(int C, int nclusters, size_t smem, const void *groups,
-                                                            const int2 *clusters, cudaStream_t s) {
-    MV_LLT_SWITCH_TN(C, launch_grouped, nclusters, smem, groups, clusters, s)
+                                                            const int2 *clusters, cudaStream_t s, bool pdl) {
+    MV_LLT_SWITCH_TN(C, launch_grouped, nclusters, smem, groups, clusters, s, pdl)
     return cudaErrorInvalidValue;
 }
 

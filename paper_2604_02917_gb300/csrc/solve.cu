@@ -220,6 +220,7 @@ __device__ __forceinline__ void power_norm_body(const float *__restrict__ g32, c
 __global__ void __launch_bounds__(kStepThreads)
 power_norm_kernel(const float *__restrict__ g32, const float *__restrict__ row_scale, float *__restrict__ y32,
                   int n) {
+    umma::launch_dependents();     // the next fused pass may start streaming L
     power_norm_body(g32, row_scale, y32, n);
 }
 
@@ -505,6 +506,7 @@ template <int CL>
 __global__ void __launch_bounds__(kProjNT) npga_step_kernel(StepArgs a) {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ ProjSmem psm;
+    umma::launch_dependents();     // the next fused pass may start streaming L
     npga_step_body<CL>(a, dsm, psm);
 }
 
@@ -707,6 +709,7 @@ template <int CL>
 __global__ void __launch_bounds__(kProjNT) npga_bt_step_kernel(StepArgs a) {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ ProjSmem psm;
+    umma::launch_dependents();
     npga_bt_step_body<CL>(a, dsm, psm);
 }
 
@@ -850,13 +853,17 @@ static void launch_g(const Plan &p, const mv_problem *P, const float *z, void *w
     }
 }
 
+// The solve loop and the power graph launch the fused pass as a
+// programmatic dependent of the step / normalisation kernel before it.
+constexpr bool kFusedPdl = true;
+
 // g = L L^T y (row-scaled) in one pass over L; capturable (no synchronisation).
 int launch_llt(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
-               float *g32, cudaStream_t s, float *z) {
+               float *g32, cudaStream_t s, float *z, bool pdl) {
     LltScratch sc = llt_scratch(at<char>(ws, p.o_llt), p.n);
     sc.err = at<int>(ws, p.o_err);             // read back by the solve
     return llt_launch(p.lp, p.dt, P->L, p.n, p.T, p.ld, y32, P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr, sc,
-                      done, g_out, g32, s, z);
+                      done, g_out, g32, s, z, pdl);
 }
 
 // Kernel attributes are set once per process, before any stream capture.
@@ -1006,7 +1013,8 @@ int launch_iteration(const Plan &p, const mv_problem *P, const mv_solve_opts *O,
         if (p.sig)
             MV_TRY(launch_symv(p, P, y32, ws, done, gy, nullptr, s));
         else
-            MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s, p.want_z ? at<float>(ws, p.o_z) : nullptr));
+            MV_TRY(launch_llt(p, P, y32, ws, done, gy, nullptr, s, p.want_z ? at<float>(ws, p.o_z) : nullptr,
+                              kFusedPdl && ev == nullptr));   // timed runs keep launches apart
         if (ev) cudaEventRecord(ev[1], s);
         if (ev) cudaEventRecord(ev[2], s);
         launch_step(p, P, O, ws, s);
@@ -1104,7 +1112,10 @@ static int launch_power(const Plan &p, const mv_problem *P, int power_iters, voi
             MV_TRY(launch_symv(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), at<float>(ws, p.o_g32), s));
             *count += 2;
         } else if (p.use_llt) {
-            MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), at<float>(ws, p.o_g32), s));
+            // after the previous power normalisation (the first launch has no
+            // kernel before it in the captured graph)
+            MV_TRY(launch_llt(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), at<float>(ws, p.o_g32), s, nullptr,
+                              kFusedPdl));
             *count += 2;
         } else {
             gemv_pair(p, P, y32, ws, nullptr, at<double>(ws, p.o_gy), s, at<float>(ws, p.o_g32));
@@ -1594,7 +1605,10 @@ static int batch_gemv_any(int dt, const BatchLayout &Lo, void *ws, bool all, boo
     const int2 *cl = at<int2>(ws, Lo.o_lcl);
     for (int g = 0; g < kGroupSizes; ++g)
         if (Lo.lcount[g] > 0) {
-            const cudaError_t e = llt_launch_grouped(dt, 1 << g, Lo.lcount[g], Lo.lsmem[g], groups, cl + Lo.lstart[g], s);
+            // ordinary launches: early launch measured slower here (the
+            // waiting clusters hold SMs the multi-wave step grid needs)
+            const cudaError_t e =
+                llt_launch_grouped(dt, 1 << g, Lo.lcount[g], Lo.lsmem[g], groups, cl + Lo.lstart[g], s, false);
             if (e != cudaSuccess) return record_cuda_error(e, "grouped fused pass launch", __FILE__, __LINE__);
         }
     return MV_OK;

@@ -104,8 +104,10 @@ int require_nt(const mv_problem *P, const char *what);
 int check_ws(void *ws, size_t ws_bytes, size_t need);
 int set_kernel_attrs();
 // g = L L^T y (row-scaled) in one pass over L; capturable (no synchronisation).
+// pdl: launched as a programmatic dependent of the previous kernel (which
+// must not write L; see llt_launch).
 int launch_llt(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
-               float *g32, cudaStream_t s, float *z = nullptr);
+               float *g32, cudaStream_t s, float *z = nullptr, bool pdl = false);
 void gemv_pair(const Plan &p, const mv_problem *P, const float *y32, void *ws, const int *done, double *g_out,
                cudaStream_t s, float *g32 = nullptr);
 void gemv_t_only(const Plan &p, const mv_problem *P, const float *y32, void *ws, cudaStream_t s);
