@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-row-oracles", action="store_true", help="skip the oracle timings of the further rows")
-    ap.add_argument("--profile", default=None, choices=["sketch", "frontier", "batch"],
+    ap.add_argument("--profile", default=None, choices=["sketch", "frontier", "batch", "str"],
                     help="run one instance of that workload at --shape (for ncu) and exit, printing its time")
     return ap.parse_args()
 
@@ -474,7 +474,9 @@ def profile_run(args):
     times a Phi drawn from seed 2, m = --sketch-m), one 64-target frontier
     solve (BF16, targets between the 10th and 90th percentiles of mu), or
     one solve of the first --batch-count problems of the uneven batch (FP32,
-    L stored transposed; a warm-up solve first)."""
+    L stored transposed; a warm-up solve first), or one STR build from the
+    seed (mv_sketch_str: draw, sketch, truncation to --str-k; a warm-up build
+    first)."""
     import torch
     from paper_2604_02917_gb300 import mv
     from synth import factor_returns
@@ -507,6 +509,12 @@ def profile_run(args):
         Phi = mv.gaussian_sketch(2, args.sketch_m, model.T)
         e0.record()
         mv.sketch(L, model.T, Phi)
+        e1.record()
+    elif args.profile == "str":
+        mv.sketch_str(L, model.T, args.sketch_m, 2, args.str_k, "bf16")
+        torch.cuda.synchronize()
+        e0.record()
+        mv.sketch_str(L, model.T, args.sketch_m, 2, args.str_k, "bf16")
         e1.record()
     else:
         muh = mu.cpu().numpy()

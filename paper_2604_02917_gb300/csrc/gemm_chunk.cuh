@@ -529,20 +529,23 @@ template <int BN>
 static int gemmc(const void *A, const void *A2, int64_t M, int64_t lda, const void *B, int64_t N, int64_t ldb,
                  int64_t K, float *C, int64_t ldc, const GemmEpi &e, cudaStream_t s, int raster = 1) {
     if (K < 1) return record_message(MV_ERR_INVALID_ARG, "chunked GEMM: K must be >= 1");
-    if (BN == 256 && kChunkPairs) return gemmc_pair(A, A2, M, lda, B, N, ldb, K, C, ldc, e, s, raster);
-    CUtensorMap ta, tb, ta2;
-    MV_TRY(make_map_bf16(&ta, A, M, K, lda, kBM));
-    MV_TRY(make_map_bf16(&tb, B, N, K, ldb, BN));
-    if (A2) {
-        MV_TRY(make_map_bf16(&ta2, A2, M, K, lda, kBM));
-        MV_TRY((gemmc_set_attrs<BN, 2>()));
-        gemmc_launch<BN, 2>(ta, tb, &ta2, M, N, K, C, ldc, e, s, raster);
+    if constexpr (BN == 256 && kChunkPairs) {
+        return gemmc_pair(A, A2, M, lda, B, N, ldb, K, C, ldc, e, s, raster);
     } else {
-        MV_TRY((gemmc_set_attrs<BN, 1>()));
-        gemmc_launch<BN, 1>(ta, tb, nullptr, M, N, K, C, ldc, e, s, raster);
+        CUtensorMap ta, tb, ta2;
+        MV_TRY(make_map_bf16(&ta, A, M, K, lda, kBM));
+        MV_TRY(make_map_bf16(&tb, B, N, K, ldb, BN));
+        if (A2) {
+            MV_TRY(make_map_bf16(&ta2, A2, M, K, lda, kBM));
+            MV_TRY((gemmc_set_attrs<BN, 2>()));
+            gemmc_launch<BN, 2>(ta, tb, &ta2, M, N, K, C, ldc, e, s, raster);
+        } else {
+            MV_TRY((gemmc_set_attrs<BN, 1>()));
+            gemmc_launch<BN, 1>(ta, tb, nullptr, M, N, K, C, ldc, e, s, raster);
+        }
+        MV_CUDA_TRY(cudaGetLastError());
+        return MV_OK;
     }
-    MV_CUDA_TRY(cudaGetLastError());
-    return MV_OK;
 }
 
 // The translation unit's GEMM error word: clear before, read after (blocking).

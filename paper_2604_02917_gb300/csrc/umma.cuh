@@ -139,9 +139,11 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
     return r;
 }
-// Arrive on an mbarrier of another CTA of the cluster (release, cluster scope).
+// Arrive on an mbarrier of a CTA of the cluster, given its shared::cluster
+// address (default semantics; a release at cluster scope added a memory
+// barrier per arrival that held back the epilogue).
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 // TMA load into this CTA's shared memory whose completion is counted on an
 // mbarrier that may belong to the peer CTA of the pair.
