@@ -273,11 +273,13 @@ struct GemmPairCfg {
     static constexpr uint32_t A_BYTES = kBM * kBK * 2;       // this CTA's 128 rows
     static constexpr uint32_t B_BYTES = (BN / 2) * kBK * 2;  // this CTA's half of B
     static constexpr uint32_t STAGE = NA * A_BYTES + B_BYTES;
-    static constexpr int S = (int)((196608u / STAGE) < 8u ? (196608u / STAGE) : 8u);
+    static constexpr uint32_t BUDGET = 196608u;               // 192 KB of stages (7 measured the same)
+    static constexpr int S = (int)((BUDGET / STAGE) < 8u ? (BUDGET / STAGE) : 8u);
     static constexpr int NBAR = 2 * S + 4;
     static constexpr size_t SMEM = 1024 + (size_t)S * STAGE + NBAR * 8 + 16;
     static constexpr uint32_t TMEM_COLS = 2 * BN;
 };
+static_assert(GemmPairCfg<1>::SMEM <= 232448 && GemmPairCfg<2>::SMEM <= 232448, "pair GEMM exceeds 227 KB");
 
 template <int NA>
 __global__ void __launch_bounds__(GemmPairCfg<NA>::THREADS, 1)

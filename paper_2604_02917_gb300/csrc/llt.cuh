@@ -459,7 +459,7 @@ __host__ __device__ inline LltSmem lltt_smem_layout(int npc, int C) {
     m.stage = (size_t)npc * 32;                  // W rows x npc elements, W * esize = 32 bytes
     size_t off = m.stage * kLltStages;
     m.o_slots = off;
-    off += (size_t)kLltSlots * C * 32 * 4;       // [2][C][16 warps x RW <= 32 floats]
+    off += (size_t)kLltSlots * C * 64 * 4;       // [2][C][16 warps x RW <= 64 floats]
     m.o_y = off;
     off += (size_t)npc * 4;
     m.o_zc = off;
@@ -481,8 +481,14 @@ __device__ __forceinline__ void lltt_body(const CUtensorMap *tm, const LltArgs &
     constexpr int ES = (int)sizeof(typename S::elem);
     constexpr int EPC = S::VEC;                          // elements per 16-byte chunk
     constexpr int W = 32 / ES;                           // periods per column block
-    constexpr int RW = W > kLltConsumerWarps ? W / kLltConsumerWarps : 1;      // rows per warp (phase A)
-    constexpr int WPR = W < kLltConsumerWarps ? kLltConsumerWarps / W : 1;     // warps per row (phase A)
+    // Phase A: a warp dots RW rows of the block with the same chunks of y,
+    // so each y load (EPC FP32 values per 16-byte chunk of L) serves RW rows;
+    // WPR warps share a row's chunks.  (One row per warp made the BF16 and
+    // FP8 passes load as many bytes of y from shared memory as of L.)
+    constexpr int RW = (ES == 4) ? 2 : 4;                // rows per warp
+    constexpr int WPR = kLltConsumerWarps * RW / W;      // warps per row: 4 (FP32, BF16), 2 (FP8)
+    constexpr int NGR = W / RW;                          // row groups
+    static_assert(NGR * WPR == kLltConsumerWarps && RW * kLltConsumerWarps <= 64, "phase A split");
     constexpr int NP = kLltConsumerWarps * RW;           // partials per rank and block
     constexpr int CPB = kLltBoxCols * ES / 16;           // 16-byte chunks per box row
     constexpr int BOXB = W * kLltBoxCols * ES;           // bytes of one box
@@ -595,7 +601,7 @@ __device__ __forceinline__ void lltt_body(const CUtensorMap *tm, const LltArgs &
                 float acc[RW];
 #pragma unroll
                 for (int r = 0; r < RW; ++r) acc[r] = 0.f;
-                const int w0 = (WPR > 1) ? (warp % W) : warp * RW, h = (WPR > 1) ? warp / W : 0;
+                const int w0 = (warp % NGR) * RW, h = warp / NGR;
 #pragma unroll 2
                 for (int c = h * 32 + lane; c < nch; c += 32 * WPR) {
                     const int off = (c / CPB) * BOXB + (c % CPB) * 16;
@@ -625,10 +631,10 @@ __device__ __forceinline__ void lltt_body(const CUtensorMap *tm, const LltArgs &
                 if (lane < C) {
                     const uint32_t local = slots_u32 + (uint32_t)(((q * C + rank) * NP + warp * RW) * 4);
                     const uint32_t rdst = llt::mapa(local, (uint32_t)lane), rbar = llt::mapa(xchg0 + 8 * q, (uint32_t)lane);
-                    if constexpr (RW == 1)
-                        llt::st_async_f32(rdst, acc[0], rbar);
+                    if constexpr (RW == 2)
+                        llt::st_async_v2(rdst, acc[0], acc[1], rbar);
                     else
-                        llt::st_async_v2(rdst, acc[0], acc[RW - 1], rbar);
+                        llt::st_async_v4(rdst, make_float4(acc[0], acc[1], acc[2], acc[3]), rbar);
                 }
             }
             // Receive: z_b[w] = sum over ranks and the row's warps, fixed order.
