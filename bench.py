@@ -472,7 +472,8 @@ def reference_arm(args):
 def profile_run(args):
     """One instance of a workload for a profiler: the sketch GEMM (L in BF16
     times a Phi drawn from seed 2, m = --sketch-m), one 64-target frontier
-    solve (BF16, targets between the 10th and 90th percentiles of mu), or
+    solve (BF16, or FP8 with --dtype fp8; targets between the 10th and 90th
+    percentiles of mu), or
     one solve of the first --batch-count problems of the uneven batch (FP32,
     L stored transposed; a warm-up solve first), or one STR build from the
     seed (mv_sketch_str: draw, sketch, truncation to --str-k; a warm-up build
@@ -502,7 +503,8 @@ def profile_run(args):
         return
     model = workload(args, 0)
     R = torch.from_numpy(factor_returns(model, np.float32)).cuda()
-    L, rs, mu, _ = mv.center_factor(R, "bf16")
+    low = "fp8" if (args.profile == "frontier" and args.dtype == "fp8") else "bf16"
+    L, rs, mu, _ = mv.center_factor(R, low)
     del R
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if args.profile == "sketch":
@@ -519,7 +521,7 @@ def profile_run(args):
     else:
         muh = mu.cpu().numpy()
         tg = np.linspace(np.percentile(muh, 10), np.percentile(muh, 90), 64)
-        fs = mv.FrontierSolver(L, mu, tg, model.T, eps=args.eps)
+        fs = mv.FrontierSolver(L, mu, tg, model.T, eps=args.eps, dtype=low, row_scale=rs)
         e0.record()
         fs.solve()
         e1.record()

@@ -453,13 +453,17 @@ llt_kernel(const __grid_constant__ CUtensorMap tmL, const LltArgs a) {
 //      pushed to every rank (RW floats per warp);
 //   B. one thread per 16-byte column chunk: g[cols] += sum_w M[bW+w, cols] z_b[w].
 constexpr int kLltBoxCols = 256;                 // elements per TMA box row
+// Phase A rows per warp of the transposed pass: FP32 (8 periods per block),
+// BF16 and FP8 (16 and 32 periods).
+constexpr int kLltRowsA32 = 2, kLltRowsA16 = 4;
+constexpr int kLltMaxRowsA = 8;                  // bound the exchange slots are sized for
 
 __host__ __device__ inline LltSmem lltt_smem_layout(int npc, int C) {
     LltSmem m{};
     m.stage = (size_t)npc * 32;                  // W rows x npc elements, W * esize = 32 bytes
     size_t off = m.stage * kLltStages;
     m.o_slots = off;
-    off += (size_t)kLltSlots * C * 64 * 4;       // [2][C][16 warps x RW <= 64 floats]
+    off += (size_t)kLltSlots * C * kLltConsumerWarps * kLltMaxRowsA * 4;   // [2][C][16 warps x RW floats]
     m.o_y = off;
     off += (size_t)npc * 4;
     m.o_zc = off;
@@ -485,10 +489,10 @@ __device__ __forceinline__ void lltt_body(const CUtensorMap *tm, const LltArgs &
     // so each y load (EPC FP32 values per 16-byte chunk of L) serves RW rows;
     // WPR warps share a row's chunks.  (One row per warp made the BF16 and
     // FP8 passes load as many bytes of y from shared memory as of L.)
-    constexpr int RW = (ES == 4) ? 2 : 4;                // rows per warp
-    constexpr int WPR = kLltConsumerWarps * RW / W;      // warps per row: 4 (FP32, BF16), 2 (FP8)
+    constexpr int RW = (ES == 4) ? kLltRowsA32 : kLltRowsA16;   // rows per warp
+    constexpr int WPR = kLltConsumerWarps * RW / W;      // warps per row
     constexpr int NGR = W / RW;                          // row groups
-    static_assert(NGR * WPR == kLltConsumerWarps && RW * kLltConsumerWarps <= 64, "phase A split");
+    static_assert(NGR * WPR == kLltConsumerWarps && RW <= kLltMaxRowsA && RW % 2 == 0, "phase A split");
     constexpr int NP = kLltConsumerWarps * RW;           // partials per rank and block
     constexpr int CPB = kLltBoxCols * ES / 16;           // 16-byte chunks per box row
     constexpr int BOXB = W * kLltBoxCols * ES;           // bytes of one box
@@ -631,10 +635,14 @@ __device__ __forceinline__ void lltt_body(const CUtensorMap *tm, const LltArgs &
                 if (lane < C) {
                     const uint32_t local = slots_u32 + (uint32_t)(((q * C + rank) * NP + warp * RW) * 4);
                     const uint32_t rdst = llt::mapa(local, (uint32_t)lane), rbar = llt::mapa(xchg0 + 8 * q, (uint32_t)lane);
-                    if constexpr (RW == 2)
+                    if constexpr (RW == 2) {
                         llt::st_async_v2(rdst, acc[0], acc[1], rbar);
-                    else
-                        llt::st_async_v4(rdst, make_float4(acc[0], acc[1], acc[2], acc[3]), rbar);
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < RW; v += 4)
+                            llt::st_async_v4(llt::mapa(local + (uint32_t)(4 * v), (uint32_t)lane),
+                                             make_float4(acc[v], acc[v + 1], acc[v + 2], acc[v + 3]), rbar);
+                    }
                 }
             }
             // Receive: z_b[w] = sum over ranks and the row's warps, fixed order.

@@ -35,10 +35,7 @@
 // 1e-5 of its norm (the Gram matrix of an ill-conditioned panel in FP32 can
 // have slightly negative eigenvalues, on which the iteration diverges); three
 // passes with shifts 1e-5, 1e-7 and 0, the later ones restoring
-// orthogonality to working precision.  Only the last panel, which the final
-// Rayleigh--Ritz step uses, gets all three; the panels the filter steps
-// start from get the first pass, whose products keep the three leading
-// piece products (about 2^-16 relative, enough for a 1e-5 shift).
+// orthogonality to working precision.
 //
 // Small problems (n <= 1024, or b >= n) take the direct route: K and then
 // all its eigenpairs by DSYEVD on the n x n matrix.
@@ -377,9 +374,8 @@ static int split_t(const Ctx &c, const float *X, int64_t R, int64_t cols, int64_
 // C (M x N) = epilogue(A' B'^T) over piece operands of segment width W.
 template <int BN>
 static int gemm6(const Ctx &c, const __nv_bfloat16 *A, int64_t M, const __nv_bfloat16 *B, int64_t N, int64_t W,
-                 float *C, int64_t ldc, const GemmEpi &e = GemmEpi{}, int products = kSplit3) {
-    // products = 3 keeps the piece pairs (h,h) (h,m) (m,h): about 2^-16 relative
-    return gemmc<BN>(A, nullptr, M, 6 * W, B, N, 6 * W, products * W, C, ldc, e, c.s);
+                 float *C, int64_t ldc, const GemmEpi &e = GemmEpi{}) {
+    return gemmc<BN>(A, nullptr, M, 6 * W, B, N, 6 * W, 6 * W, C, ldc, e, c.s);
 }
 
 // Q = Y (Y^T Y)^{-1/2} (n x b panels, row pitch Wb): Lowdin passes with the
@@ -387,16 +383,10 @@ static int gemm6(const Ctx &c, const __nv_bfloat16 *A, int64_t M, const __nv_bfl
 struct OrthPass {
     float delta;
     int its;
-    int products;                          // piece products of the Newton--Schulz GEMMs
 };
-// The first pass (shift 1e-5) only has to reach about 1e-5, which the
-// three leading piece products (2^-16) already give; the later passes run
-// FP32-accurate.  Panels between filter steps only need the first pass (the
-// next filter step starts from them; only the last panel feeds the final
-// Rayleigh--Ritz step).
-constexpr OrthPass kOrthPasses[3] = {{1e-5f, 22, 3}, {1e-7f, 14, kSplit3}, {0.0f, 8, kSplit3}};
+constexpr OrthPass kOrthPasses[3] = {{1e-5f, 22}, {1e-7f, 14}, {0.0f, 8}};
 
-static int orth(const Ctx &c, const float *Y, float *Q, bool full) {
+static int orth(const Ctx &c, const float *Y, float *Q) {
     const TopkPlan &p = c.p;
     const int64_t n = p.n, b = p.b, Wb = p.Wb, Wn = p.Wn;
     float *G = c.at<float>(p.o_sm[0]), *A = c.at<float>(p.o_sm[1]), *Z = c.at<float>(p.o_sm[2]);
@@ -406,8 +396,7 @@ static int orth(const Ctx &c, const float *Y, float *Q, bool full) {
     __nv_bfloat16 *xr = c.at<__nv_bfloat16>(p.o_xr);
     float *D = c.at<float>(p.o_D), *rows = c.at<float>(p.o_rows), *sc = c.at<float>(p.o_s);
     const float *src = Y;
-    for (int pass = 0; pass < (full ? 3 : 1); ++pass) {
-        const OrthPass &ps = kOrthPasses[pass];
+    for (const OrthPass &ps : kOrthPasses) {
         // G = src^T src
         MV_TRY(split_t(c, src, n, b, Wb, Wn, 0, yt0));
         MV_TRY(split_t(c, src, n, b, Wb, Wn, 1, yt1));
@@ -423,14 +412,14 @@ static int orth(const Ctx &c, const float *Y, float *Q, bool full) {
             // symmetry that rounding only keeps approximately.
             MV_TRY(split_rows(c, Z, b, b, Wb, Wb, 0, sp0));
             MV_TRY(split_t(c, Ya, b, b, Wb, Wb, 1, sp1));
-            MV_TRY(gemm6<128>(c, sp0, b, sp1, b, Wb, P, Wb, GemmEpi{}, ps.products));
+            MV_TRY(gemm6<128>(c, sp0, b, sp1, b, Wb, P, Wb));
             ns_t_kernel<<<grid_for(b * b), 256, 0, c.s>>>(P, (int)b, Wb, Tm);
             MV_TRY(split_rows(c, Ya, b, b, Wb, Wb, 0, sp0));
             MV_TRY(split_t(c, Tm, b, b, Wb, Wb, 1, sp1));
-            MV_TRY(gemm6<128>(c, sp0, b, sp1, b, Wb, Yb, Wb, GemmEpi{}, ps.products));
+            MV_TRY(gemm6<128>(c, sp0, b, sp1, b, Wb, Yb, Wb));
             MV_TRY(split_rows(c, Tm, b, b, Wb, Wb, 0, sp0));
             MV_TRY(split_t(c, Z, b, b, Wb, Wb, 1, sp1));
-            MV_TRY(gemm6<128>(c, sp0, b, sp1, b, Wb, P, Wb, GemmEpi{}, ps.products));   // P = T Z
+            MV_TRY(gemm6<128>(c, sp0, b, sp1, b, Wb, P, Wb));      // P = T Z
             std::swap(Ya, Yb);
             std::swap(Z, P);
         }
@@ -482,19 +471,18 @@ struct OrthKey {
     const void *ws, *src, *dst;
     int64_t n, b, Wn, Wb;
     int dev;
-    bool full;
     bool operator==(const OrthKey &o) const {
         return ws == o.ws && src == o.src && dst == o.dst && n == o.n && b == o.b && Wn == o.Wn && Wb == o.Wb &&
-               dev == o.dev && full == o.full;
+               dev == o.dev;
     }
 };
 static std::mutex g_orth_mu;
 static std::vector<std::pair<OrthKey, cudaGraphExec_t>> g_orth_graphs;
 
-static int orth_graph(const Ctx &c, const float *Y, float *Q, bool full) {
+static int orth_graph(const Ctx &c, const float *Y, float *Q) {
     int dev = 0;
     MV_CUDA_TRY(cudaGetDevice(&dev));
-    const OrthKey key{c.ws, Y, Q, c.p.n, c.p.b, c.p.Wn, c.p.Wb, dev, full};
+    const OrthKey key{c.ws, Y, Q, c.p.n, c.p.b, c.p.Wn, c.p.Wb, dev};
     std::lock_guard<std::mutex> lock(g_orth_mu);
     cudaGraphExec_t exec = nullptr;
     for (auto &kv : g_orth_graphs)
@@ -508,7 +496,7 @@ static int orth_graph(const Ctx &c, const float *Y, float *Q, bool full) {
             return record_message(MV_ERR_CUDA, "STR truncation: stream capture refused");
         }
         const Ctx cc{c.p, c.ws, cs};
-        const int st = orth(cc, Y, Q, full);
+        const int st = orth(cc, Y, Q);
         cudaGraph_t graph;
         const cudaError_t e = cudaStreamEndCapture(cs, &graph);
         cudaStreamDestroy(cs);
@@ -612,7 +600,7 @@ int topk_eigen(const float *Ls, int64_t n, int64_t m, int64_t ldS, int64_t k, fl
         MV_TRY(split_t(c, src, n, b, Wb, Wn, 1, yt1));
         MV_TRY(gemm6<128>(c, kp, n, yt1, b, Wn, dst, Wb));
     }
-    MV_TRY(orth_graph(c, Y[0], Y[0], false));
+    MV_TRY(orth_graph(c, Y[0], Y[0]));
     // 3. the cut from the Ritz values
     double *Wv = c.at<double>(p.o_Wb);
     MV_TRY(rayleigh(c, Y[0], Y[1]));
@@ -625,9 +613,7 @@ int topk_eigen(const float *Ls, int64_t n, int64_t m, int64_t ldS, int64_t k, fl
     if (!(cut > 0.0)) return record_message(MV_ERR_NUMERIC, "STR truncation: non-positive Ritz value at the cut");
     const double e = 0.5 * cut, h = 0.5 * cut;
     // 4. Chebyshev filtering on [0, cut]
-    constexpr int nf = (int)(sizeof(kDegrees) / sizeof(kDegrees[0]));
-    for (int f = 0; f < nf; ++f) {
-        const int d = kDegrees[f];
+    for (int d : kDegrees) {
         float *prev = Y[0], *cur = Y[1], *nxt = Y[2];
         GemmEpi e1;
         e1.alpha = (float)(1.0 / h);
@@ -652,7 +638,7 @@ int topk_eigen(const float *Ls, int64_t n, int64_t m, int64_t ldS, int64_t k, fl
             cur = nxt;
             nxt = t;
         }
-        MV_TRY(orth_graph(c, cur, Y[0], f + 1 == nf));     // only the last panel fully
+        MV_TRY(orth_graph(c, cur, Y[0]));
     }
     // 5. final Rayleigh--Ritz
     MV_TRY(rayleigh(c, Y[0], Y[1]));
