@@ -1511,6 +1511,17 @@ struct BatchLayout {
 
 static int group_index(int C) { return C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3; }
 
+// Cluster size of the batch's step launch, which holds one cluster per
+// problem: the smallest one whose blocks take at most kBatchStepElems
+// elements, so that the launch stays near one wave (a lone problem prefers
+// more, smaller blocks: proj_cluster_size).
+constexpr int kBatchStepElems = 1536;
+static int batch_cluster_size(int max_n) {
+    int c = 1;
+    while (c < kProjMaxCL && (max_n + c - 1) / c > kBatchStepElems) c *= 2;
+    return c;
+}
+
 static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo, BatchTiles tiles = kBatchDefault) {
     Lo->plans.clear();
     Lo->base.clear();
@@ -1575,7 +1586,7 @@ static int batch_layout(const mv_problem *probs, int64_t count, BatchLayout *Lo,
     Lo->nn_tiles = (int)nnt;
     Lo->n_tn = n_tn;
     Lo->n_lcl = (int)ncl;
-    Lo->cl = proj_cluster_size(max_n);
+    Lo->cl = batch_cluster_size(max_n);
     Lo->max_ncols = max_ncols;
     Lo->max_n = max_n;
     Lo->total = off;
