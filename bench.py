@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--str-k", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-row-oracles", action="store_true", help="skip the oracle timings of the further rows")
-    ap.add_argument("--profile", default=None, choices=["sketch", "frontier", "batch", "str"],
+    ap.add_argument("--profile", default=None, choices=["sketch", "frontier", "batch", "str", "adjoint"],
                     help="run one instance of that workload at --shape (for ncu) and exit, printing its time")
     return ap.parse_args()
 
@@ -477,10 +477,27 @@ def profile_run(args):
     one solve of the first --batch-count problems of the uneven batch (FP32,
     L stored transposed; a warm-up solve first), or one STR build from the
     seed (mv_sketch_str: draw, sketch, truncation to --str-k; a warm-up build
-    first)."""
+    first), or one reverse sweep of 500 unrolled iterations at 2000 x 10000
+    (checkpoints every 50; a warm-up sweep first)."""
     import torch
     from paper_2604_02917_gb300 import mv
     from synth import factor_returns
+    if args.profile == "adjoint":
+        from synth import CFG_SMALL
+        am = CFG_SMALL.scaled(2000, 10000, seed=0)
+        La, _, mua, _ = mv.center_factor(torch.from_numpy(factor_returns(am, np.float32)).cuda(), "f32")
+        Rta = float(np.percentile(mua.cpu().numpy(), 60))
+        g = torch.randn(am.n, dtype=torch.float64, device="cuda",
+                        generator=torch.Generator(device="cuda").manual_seed(0))
+        mv.npga_backward(La, mua, Rta, am.T, g, 500, checkpoint_every=50)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mv.npga_backward(La, mua, Rta, am.T, g, 500, checkpoint_every=50)
+        e1.record()
+        torch.cuda.synchronize()
+        print(f"adjoint 2000x10000, 500 iterations: backward {e0.elapsed_time(e1):.3f} ms", flush=True)
+        return
     if args.profile == "batch":
         from synth import factor_returns_device, uneven_problem_sizes
         probs = []
