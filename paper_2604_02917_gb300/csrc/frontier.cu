@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kProjNT) frontier_step_kernel(FArgs a) {
     const int k = fs->k;
     const double beta_prev = fs->beta_prev, t = fs->t, alpha = a.st->alpha;
     const double mn = a.st->mu_min, mx = a.st->mu_max;
-    const double nu0 = fs->nu, tau0 = fs->tau, nuk0 = fs->nu_kkt, tauk0 = fs->tau_kkt;
+    const double nu0 = fs->nu, tau0 = fs->tau;
     const double gamma = a.gamma, R = a.Rt[b];
     if (threadIdx.x == 0) {
         sc[0] = 1.0 / (1.0 + beta_prev);
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kProjNT) frontier_step_kernel(FArgs a) {
     ClusterProj<CL> P{&psm, el};
     if (check) {
         P.prepare();
-        const ProjOut o = P.solve(R, a.mode, mn, mx, nuk0, tauk0, kProjBudget);
+        const ProjOut o = P.solve(R, a.mode, mn, mx, nu0, tau0, kProjBudget);   // see npga_step_body
         double r2 = 0.0;
         for (int i = threadIdx.x; i < el.n; i += kProjNT) {
             const double p = fmax(fma(o.nu, el.mu[i], el.v[i]) - o.tau, 0.0);
