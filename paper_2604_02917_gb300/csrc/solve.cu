@@ -1512,6 +1512,10 @@ struct BatchLayout {
     int lstart[kGroupSizes], lcount[kGroupSizes];
     size_t lsmem[kGroupSizes];
     size_t total;
+    // a second stream (and fork/join events) on which one of two or more
+    // grouped fused launches runs beside the others; null: one stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 static int group_index(int C) { return C == 1 ? 0 : C == 2 ? 1 : C == 4 ? 2 : 3; }
@@ -1619,16 +1623,49 @@ static int batch_gemv_any(int dt, const BatchLayout &Lo, void *ws, bool all, boo
     if (gemv_only || Lo.n_tn == 0) return MV_OK;
     const void *groups = at<char>(ws, all ? Lo.o_lgrp_all : Lo.o_lgrp);
     const int2 *cl = at<int2>(ws, Lo.o_lcl);
+    int ng = 0;
+    for (int g = 0; g < kGroupSizes; ++g) ng += Lo.lcount[g] > 0 ? 1 : 0;
+    // With two or more cluster sizes the first launch runs on the side
+    // stream beside the others, so their last waves overlap.
+    const bool fork = ng >= 2 && Lo.side != nullptr;
+    if (fork) {
+        MV_CUDA_TRY(cudaEventRecord(Lo.fork, s));
+        MV_CUDA_TRY(cudaStreamWaitEvent(Lo.side, Lo.fork, 0));
+    }
+    bool first = true;
     for (int g = 0; g < kGroupSizes; ++g)
         if (Lo.lcount[g] > 0) {
             // ordinary launches: early launch measured slower here (the
             // waiting clusters hold SMs the multi-wave step grid needs)
+            const cudaStream_t gs = (fork && first) ? Lo.side : s;
+            first = false;
             const cudaError_t e =
-                llt_launch_grouped(dt, 1 << g, Lo.lcount[g], Lo.lsmem[g], groups, cl + Lo.lstart[g], s, false);
+                llt_launch_grouped(dt, 1 << g, Lo.lcount[g], Lo.lsmem[g], groups, cl + Lo.lstart[g], gs, false);
             if (e != cudaSuccess) return record_cuda_error(e, "grouped fused pass launch", __FILE__, __LINE__);
         }
+    if (fork) {
+        MV_CUDA_TRY(cudaEventRecord(Lo.join, Lo.side));
+        MV_CUDA_TRY(cudaStreamWaitEvent(s, Lo.join, 0));
+    }
     return MV_OK;
 }
+
+// The side stream and events of a batch solve, released on every return.
+struct BatchSide {
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    int create() {
+        MV_CUDA_TRY(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+        MV_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        MV_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        return MV_OK;
+    }
+    ~BatchSide() {
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (side) cudaStreamDestroy(side);
+    }
+};
 
 static cudaError_t batch_step(const BatchLayout &Lo, void *ws, int count, cudaStream_t s) {
     const size_t smem = proj_elem_bytes((Lo.max_n + Lo.cl - 1) / Lo.cl);
@@ -1901,6 +1938,13 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
     MV_TRY(check_ws(d_ws, ws_bytes, Lo.total));
     const int cnt = (int)count, dt = probs[0].dtype;
     MV_TRY(batch_setup(Lo, probs, count, O, ws, s));
+    BatchSide side;
+    if (Lo.n_tn > 0) {
+        MV_TRY(side.create());
+        Lo.side = side.side;
+        Lo.fork = side.fork;
+        Lo.join = side.join;
+    }
 
     const GOne *d_one = at<GOne>(ws, Lo.o_one);
     int launches = 0;
