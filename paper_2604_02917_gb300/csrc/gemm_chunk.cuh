@@ -265,8 +265,6 @@ gemm_chunk_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 // buffer b to both epilogues; both CTAs' epilogue warps arrive on rank 0's
 // tempty[b].  A cluster barrier opens and closes the kernel, so no CTA
 // addresses a peer that has not started or has already left.
-constexpr int kPairRasterPairs = 8;      // pairs (256-row tiles) per raster group (4, 16, none: slower)
-
 template <int NA>
 struct GemmPairCfg {
     static constexpr int BN = 256;                           // columns of the pair's tile
@@ -306,8 +304,8 @@ gemm_chunk_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_con
     // the pair's tile (pr, ct); grouped raster over pairs as in gemm.cuh
     const int npr = (int)gridDim.x >> 1, nct = (int)gridDim.y;
     int pr = (int)blockIdx.x >> 1, ct = (int)blockIdx.y;
-    if (raster && npr > kPairRasterPairs) {
-        const int rows = kPairRasterPairs;
+    if (raster && npr > kRasterRows / 2) {
+        const int rows = kRasterRows / 2;
         const int lin = pr + npr * (int)blockIdx.y;
         const int per = rows * nct, g = lin / per, first = g * rows;
         const int gh = min(npr - first, rows), rem = lin - g * per;
