@@ -822,6 +822,18 @@ def main():
         e[1].record(stream)
         torch.cuda.synchronize()
         s_ms = e[0].elapsed_time(e[1]) / args.steps
+        # the same solve to the headline's KKT tolerance
+        ssv6 = mv.Solver(L_eff, mu, Rt, args.str_k, gamma=gamma, power_start=r0, eps=args.eps)
+        for _ in range(args.warmup):
+            ssv6.solve()
+        torch.cuda.synchronize()
+        e[0].record(stream)
+        for _ in range(args.steps):
+            _, si6 = ssv6.solve()
+        e[1].record(stream)
+        torch.cuda.synchronize()
+        s6_ms = e[0].elapsed_time(e[1]) / args.steps
+        del ssv6
         _, gfull = mv.gradient(L, xs, model.T, layout=args.layout, with_z=False)  # 2 L L^T x, full FP32 model
         f_str_full = float(torch.dot(xs, gfull).item()) / 2.0
         f_full = infos[-1]["objective"]
@@ -838,6 +850,8 @@ def main():
                                 "sigma_k": float(sigma[-1])},
                    "solve": {"value": s_ms / 1e3, "unit": "s", "iterations": si["iterations"], "kkt": si["kkt"],
                              "kkt_eps": str_eps},
+                   "solve_headline_eps": {"value": s6_ms / 1e3, "unit": "s", "iterations": si6["iterations"],
+                                          "kkt": si6["kkt"], "kkt_eps": args.eps},
                    "full_model_gap": (f_str_full - f_full) / f_full,
                    "build_ms": build_ms,
                    "build_plus_solve_s": (build_ms + s_ms) / 1e3,
