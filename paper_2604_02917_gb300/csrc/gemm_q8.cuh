@@ -49,7 +49,9 @@ gemm_q8_tn_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     using Cfg = Q8Cfg<BN>;
     constexpr int S = Cfg::S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // aligned up to 1024 bytes by pointer arithmetic on the shared array (an
+    // integer round trip would hide from the compiler that it is shared memory)
+    uint8_t *smem = smem_raw + ((1024u - (uint32_t)(reinterpret_cast<uintptr_t>(smem_raw) & 1023u)) & 1023u);
     uint8_t *sA = smem;                                        // S x A16
     uint8_t *sB = sA + S * Cfg::A16_BYTES;                     // S x B
     uint8_t *sA8 = sB + S * Cfg::B_BYTES;                      // S x A8

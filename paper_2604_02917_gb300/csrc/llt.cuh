@@ -268,7 +268,9 @@ llt_kernel(const __grid_constant__ CUtensorMap tmL, const LltArgs a) {
     if (a.done != nullptr && *(const volatile int *)a.done) return;
 
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // aligned up to 1024 bytes by pointer arithmetic on the shared array (an
+    // integer round trip would hide from the compiler that it is shared memory)
+    uint8_t *sm = smem_raw + ((1024u - (uint32_t)(reinterpret_cast<uintptr_t>(smem_raw) & 1023u)) & 1023u);
     const LltSmem L = llt_smem_layout(a.rpc, RB, W, C);
     float *slots = reinterpret_cast<float *>(sm + L.o_slots);       // [2][C][NG][W]
     float *s_y = reinterpret_cast<float *>(sm + L.o_y);
@@ -501,7 +503,9 @@ __device__ __forceinline__ void lltt_body(const CUtensorMap *tm, const LltArgs &
     if (a.done != nullptr && *(const volatile int *)a.done) return;
 
     extern __shared__ uint8_t smem_raw[];
-    uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // aligned up to 1024 bytes by pointer arithmetic on the shared array (an
+    // integer round trip would hide from the compiler that it is shared memory)
+    uint8_t *sm = smem_raw + ((1024u - (uint32_t)(reinterpret_cast<uintptr_t>(smem_raw) & 1023u)) & 1023u);
     const int npc = a.rpc;                               // asset columns of this CTA
     const LltSmem L = lltt_smem_layout(npc, C);
     float *slots = reinterpret_cast<float *>(sm + L.o_slots);       // [2][C][NP]
