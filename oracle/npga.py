@@ -5,6 +5,17 @@
 * ``power_norm2`` -- the power method of the Sec. 3.1 remark:
   u <- L(L^T u)/||L(L^T u)||, u^0 = r/||r||; returns ||L^T u||^2, an
   estimate of ||L_eff||_2^2.
+* ``lanczos_norm2`` -- the other estimate the Sec. 3.1 fixed step names,
+  the largest singular value of L_eff, taken as the largest eigenvalue of
+  the k x k tridiagonal matrix that k steps of the Lanczos three-term
+  recurrence build for A = L L^T from q_1 = r/||r||:
+  alpha_j = q_j^T A q_j, r_j = A q_j - alpha_j q_j - beta_j q_{j-1},
+  beta_{j+1} = ||r_j||, q_{j+1} = r_j / beta_{j+1}; no reorthogonalisation.
+  It stops early when beta_{j+1} vanishes (K_j is invariant under A and the
+  estimate is exact).  Its k-step value is the largest Rayleigh quotient over
+  the Krylov space K_k(A, r), so it is never below the power method's
+  estimate after k - 1 steps (a vector of that space) and never above
+  ||L||_2^2.
 * ``step_size`` -- fixed step alpha = 1/L_f with L_f = 2(||L_eff||_2^2 + gamma)
   (Sec. 3.1, fixed step).  Reading: the power estimate is raised by a safety
   factor (1 + safety) because the power method approaches ||L||^2 from below.
@@ -50,6 +61,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.linalg
 
 from .projection import PROJ_OK, project_F
 
@@ -75,6 +87,48 @@ def power_norm2(Leff, r, iters: int = 50):
         u = w / nw
     z = Leff.T @ u
     return float(z @ z)
+
+
+def _lanczos_top(apply_a, r, steps: int):
+    """k-step Lanczos on the symmetric operator apply_a from r; returns the
+    largest eigenvalue of the tridiagonal matrix and the steps taken."""
+    q = np.asarray(r, dtype=np.float64)
+    nr = np.linalg.norm(q)
+    if steps < 1 or nr == 0.0:
+        return 0.0, 0
+    q = q / nr
+    q_prev = np.zeros_like(q)
+    alphas, betas = [], []
+    beta = 0.0
+    for _ in range(steps):
+        w = apply_a(q)
+        a = float(q @ w)
+        w = w - a * q - beta * q_prev
+        alphas.append(a)
+        beta_next = float(np.linalg.norm(w))
+        if not beta_next > 1e-12 * (abs(a) + beta):
+            break                                   # K_j invariant: the Ritz values are eigenvalues
+        betas.append(beta_next)
+        q_prev, q, beta = q, w / beta_next, beta_next
+    k = len(alphas)
+    off = np.array(betas[:k - 1])
+    if k == 1:
+        return alphas[0], 1
+    top = scipy.linalg.eigh_tridiagonal(np.array(alphas), off, eigvals_only=True)[-1]
+    return float(top), k
+
+
+def lanczos_norm2(Leff, r, steps: int = 25):
+    """Lanczos estimate of ||L_eff||_2^2 (largest eigenvalue of L L^T) from
+    ``steps`` products L(L^T q)."""
+    Leff = np.asarray(Leff, dtype=np.float64)
+    return _lanczos_top(lambda q: Leff @ (Leff.T @ q), r, steps)[0]
+
+
+def lanczos_norm2_sigma(Sigma, r, steps: int = 25):
+    """The same Lanczos estimate with the explicit Sigma u as the product."""
+    Sigma = np.asarray(Sigma, dtype=np.float64)
+    return _lanczos_top(lambda q: Sigma @ q, r, steps)[0]
 
 
 def step_size(lam_hat, gamma, safety: float = 1e-3):

@@ -17,10 +17,10 @@ from oracle.center import center_factor
 from oracle.projection import (PROJ_BRACKET, PROJ_INFEASIBLE, PROJ_OK, active_set, project_F,
                                project_F_dykstra, project_F_safeguarded, project_halfspace,
                                project_simplex)
-from oracle.npga import (fw_gap, gradient, gradient_sigma, initial_point, kkt_residual,
-                         kkt_residual_sigma, lin_min_F, npga, npga_sigma, objective, objective_sigma,
-                         power_norm2, power_norm2_sigma, sigma_from_factor, solver_gap, step_size,
-                         vertices_F)
+from oracle.npga import (_lanczos_top, fw_gap, gradient, gradient_sigma, initial_point, kkt_residual,
+                         kkt_residual_sigma, lanczos_norm2, lanczos_norm2_sigma, lin_min_F, npga, npga_sigma,
+                         objective, objective_sigma, power_norm2, power_norm2_sigma, sigma_from_factor,
+                         solver_gap, step_size, vertices_F)
 from oracle.bruteforce import project_bruteforce, qp_bruteforce
 from oracle import strmodel
 
@@ -188,6 +188,52 @@ def test_power_method_approaches_lambda_max_from_below():
     # The top eigenvalues of this panel are clustered, so convergence is slow.
     assert prev == pytest.approx(lam_max, rel=1e-9)
     assert step_size(lam_max, 0.0, 0.0) == pytest.approx(1.0 / (2.0 * lam_max))
+
+
+def test_lanczos_exact_after_n_steps():
+    # In exact arithmetic n Lanczos steps span R^n, so the tridiagonal matrix
+    # is similar to A and its top eigenvalue is lambda_max; a dropped
+    # beta q_{j-1} term or a wrong alpha_j breaks that.
+    rng = np.random.default_rng(5)
+    for n in (1, 2, 6, 9):
+        L = rng.standard_normal((n, 3 * n + 1))
+        lam_max = np.linalg.eigvalsh(L @ L.T)[-1]
+        r = rng.standard_normal(n)
+        assert lanczos_norm2(L, r, n) == pytest.approx(lam_max, rel=1e-10)
+        # more steps than n: the recurrence stops at the invariant space
+        assert lanczos_norm2(L, r, n + 5) == pytest.approx(lam_max, rel=1e-10)
+
+
+def test_lanczos_breakdown_on_invariant_krylov_space():
+    # A = diag(9, 4, 0, 0, 0): from r = 1 the Krylov space has dimension 3
+    # (one direction per distinct eigenvalue), so beta_4 = 0 and the estimate
+    # is exactly 9 after three steps.
+    L = np.zeros((5, 2))
+    L[0, 0], L[1, 1] = 3.0, 2.0
+    top, k = _lanczos_top(lambda q: L @ (L.T @ q), np.ones(5), 25)
+    assert k == 3
+    assert top == pytest.approx(9.0, rel=1e-14)
+    assert lanczos_norm2(L, np.zeros(5), 10) == 0.0        # zero start: no direction
+
+
+def test_lanczos_bounds_power_method_and_lambda_max():
+    # The k-step value maximises the Rayleigh quotient over K_k(A, r), which
+    # holds the power iterate after k - 1 steps, and lies below lambda_max.
+    _, _, L, _ = small_problem(CFG_SMALL.n, CFG_SMALL.T)
+    lam_max = np.linalg.eigvalsh(L @ L.T)[-1]
+    r = power_start(L.shape[0])
+    prev = 0.0
+    for k in (1, 2, 3, 5, 8, 12, 20, 30):
+        lz = lanczos_norm2(L, r, k)
+        assert lz >= power_norm2(L, r, k - 1) * (1 - 1e-12)
+        assert lz <= lam_max * (1 + 1e-12)
+        assert lz >= prev * (1 - 1e-12)
+        prev = lz
+    # far fewer products than the power method for the same accuracy on
+    # this clustered spectrum
+    assert lanczos_norm2(L, r, 30) >= power_norm2(L, r, 200) * (1 - 1e-12)
+    S = sigma_from_factor(L)
+    assert lanczos_norm2_sigma(S, r, 12) == pytest.approx(lanczos_norm2(L, r, 12), rel=1e-10)
 
 
 def test_npga_hand_case():
