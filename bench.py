@@ -54,6 +54,10 @@ def parse():
                     help="stream L twice per product (z = L^T y, then L z) instead of the fused single pass")
     ap.add_argument("--config", default="full", choices=["full", "small"])
     ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--step-estimate", default="lanczos", choices=["lanczos", "power"],
+                    help="lambda_hat for the fixed step (Sec. 3.1): Lanczos steps or power iterations on L L^T")
+    ap.add_argument("--step-iters", type=int, default=None,
+                    help="products spent on lambda_hat (default: 25 Lanczos steps, or 50 power iterations)")
     ap.add_argument("--shape", default=None, help="n,T override (profiling runs on a smaller case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the BF16/FP8 + FP32-refinement lines")
@@ -71,6 +75,15 @@ def parse():
     ap.add_argument("--profile", default=None, choices=["sketch", "frontier", "batch", "str", "adjoint"],
                     help="run one instance of that workload at --shape (for ncu) and exit, printing its time")
     return ap.parse_args()
+
+
+def step_opts(args):
+    """Solver options of the step estimate, and its label."""
+    if args.step_estimate == "lanczos":
+        k = args.step_iters or 25
+        return {"lanczos": 1, "power_iters": k}, f"{k} Lanczos steps"
+    k = args.step_iters or 50
+    return {"power_iters": k}, f"{k} power iterations"
 
 
 def dist_env():
@@ -290,26 +303,27 @@ def oracle_problem(model, R32=None):
     return mu, L, float(np.percentile(mu, 60)), power_start(model.n)
 
 
-def oracle_solve(mu, L, Rt, r0, eps, power_iters=50):
-    """One complete FP64 oracle solve, timed: the power method, Algorithm 1
-    with the literal KKT test every 5 iterations until the residual is <= eps,
-    and the objective (the work of one GPU step; the centering, like the
-    GPU's, is outside the timed region)."""
-    from oracle.npga import initial_point, npga, power_norm2, step_size
+def oracle_solve(mu, L, Rt, r0, eps, power_iters=50, lanczos=0):
+    """One complete FP64 oracle solve, timed: the step estimate (the power
+    method, or Lanczos steps with ``lanczos=1``), Algorithm 1 with the literal
+    KKT test every 5 iterations until the residual is <= eps, and the
+    objective (the work of one GPU step; the centering, like the GPU's, is
+    outside the timed region)."""
+    from oracle.npga import initial_point, lanczos_norm2, npga, power_norm2, step_size
     t0 = time.perf_counter()
-    lam = power_norm2(L, r0, power_iters)
+    lam = lanczos_norm2(L, r0, power_iters) if lanczos else power_norm2(L, r0, power_iters)
     res = npga(L, 0.0, mu, Rt, initial_point(mu, Rt), step_size(lam, 0.0), eps=eps, max_iter=100000, kkt_every=5)
     return time.perf_counter() - t0, res
 
 
-def cpu_baseline(model, eps, R32=None, x_gpu=None, f_gpu=None, prob=None):
+def cpu_baseline(model, eps, R32=None, x_gpu=None, f_gpu=None, prob=None, sopts=None, slabel="50 power iterations"):
     """The FP64 oracle on this host's cores: one complete solve of the
     headline workload (not a sample), with its own iteration count and its
     distance to the GPU's answer."""
     mu, L, Rt, r0 = oracle_problem(model, R32) if prob is None else prob
-    t, res = oracle_solve(mu, L, Rt, r0, eps)
+    t, res = oracle_solve(mu, L, Rt, r0, eps, **(sopts or {}))
     out = {"value": t, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-           "sample": f"full solve: FP64 NumPy oracle on the whole {model.n}x{model.T} matrix, 50 power iterations "
+           "sample": f"full solve: FP64 NumPy oracle on the whole {model.n}x{model.T} matrix, {slabel} "
                      f"+ Algorithm 1 with the literal KKT test every 5 iterations to {eps:g} "
                      f"({res.iters} iterations, KKT {res.kkt:.2e}) + objective",
            "iterations": res.iters, "kkt": res.kkt, "objective": res.f}
@@ -320,7 +334,7 @@ def cpu_baseline(model, eps, R32=None, x_gpu=None, f_gpu=None, prob=None):
     return out
 
 
-def row_oracles(model, R32, res, prob=None):
+def row_oracles(model, R32, res, prob=None, sopts=None):
     """The FP64 oracle timed beside each further row, on the host cores, as it
     stands.  Each row runs the whole workload where that takes well under a
     minute (the sketch, the CountSketch, the truncation, the explicit-Sigma
@@ -330,14 +344,21 @@ def row_oracles(model, R32, res, prob=None):
     "scaled": true)."""
     from synth import CFG_SMALL, countsketch_hash, gaussian_sketch, power_start
     from oracle.center import center_factor
-    from oracle.npga import (gradient, initial_point, npga, npga_sigma, power_norm2, power_norm2_sigma,
-                             sigma_from_factor, step_size)
+    from oracle.npga import (gradient, initial_point, lanczos_norm2, npga, npga_sigma, power_norm2,
+                             power_norm2_sigma, sigma_from_factor, step_size)
     from oracle.projection import project_F
     from oracle import adjoint as oadj
     from oracle import strmodel
     cores = os.cpu_count()
     out = {}
     n, T, m = model.n, model.T, 8192
+    sopts = sopts or {"power_iters": 50}
+
+    def lam_est(Lx, rx):
+        """The step estimate the GPU rows use (Lanczos steps or power iterations)."""
+        if sopts.get("lanczos", 0):
+            return lanczos_norm2(Lx, rx, sopts["power_iters"])
+        return power_norm2(Lx, rx, sopts["power_iters"])
 
     def full(t, sample):
         return {"value": t, "unit": "s", "cores": cores, "kind": "oracle", "sample": sample, "scaled": False}
@@ -380,14 +401,14 @@ def row_oracles(model, R32, res, prob=None):
     muf, Lf, _ = center_factor(Rf)
     tg = np.linspace(np.percentile(muf, 10), np.percentile(muf, 90), 64)
     t0 = time.perf_counter()
-    lam = power_norm2(Lf, power_start(Lf.shape[0]), 50)
+    lam = lam_est(Lf, power_start(Lf.shape[0]))
     for r in tg:
         npga(Lf, 0.0, muf, float(r), initial_point(muf, float(r)), step_size(lam, 0.0), eps=1e-6, max_iter=20000)
     out["frontier_200x1000"] = full(time.perf_counter() - t0, "all 64 targets at 200 x 1000, each solved to 1e-6")
     # a11 frontier at the full shape: 2 of the 64 targets solved in full, scaled by 32
     tgf = np.linspace(np.percentile(mu, 10), np.percentile(mu, 90), 64)
     t0 = time.perf_counter()
-    lamf = power_norm2(L, r0, 50)
+    lamf = lam_est(L, r0)
     for r in (tgf[0], tgf[63]):
         npga(L, 0.0, mu, float(r), initial_point(mu, float(r)), step_size(lamf, 0.0), eps=1e-6, max_iter=100000)
     out["frontier_full_shape"] = scaled(time.perf_counter() - t0, 32.0,
@@ -448,22 +469,23 @@ def reference_arm(args):
         return
     model = workload(args, 0)
     prob = oracle_problem(model)
+    sopts, slabel = step_opts(args)
     vals = []
     res = None
     for i in range(args.warmup + args.steps):
-        t, res = oracle_solve(*prob, args.eps)
+        t, res = oracle_solve(*prob, args.eps, **sopts)
         if i >= args.warmup:
             vals.append(t)
     v = float(np.mean(vals))
     cb = {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-          "sample": f"each step one full solve: 50 power iterations + Algorithm 1 with the literal KKT test every 5 "
+          "sample": f"each step one full solve: {slabel} + Algorithm 1 with the literal KKT test every 5 "
                     f"iterations to {args.eps:g} ({res.iters} iterations) on the whole {model.n}x{model.T} matrix",
           "iterations": res.iters, "kkt": res.kkt}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"npga full model n={model.n} T={model.T}, FP64 oracle", "n": model.n,
-                       "T": model.T, "kkt_eps": args.eps},
+            "config": {"workload": f"npga full model n={model.n} T={model.T}, FP64 oracle, step from {slabel}",
+                       "n": model.n, "T": model.T, "kkt_eps": args.eps, "step_estimate": slabel},
             "cpu_baseline": cb,
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -568,11 +590,12 @@ def main():
     L, rs, mu, tr = mv.center_factor(R_dev, args.dtype, layout=args.layout)
     Rt = float(np.percentile(mu.cpu().numpy(), 60))
     r0 = torch.from_numpy(power_start(model.n)).to(dev)
+    sopts, slabel = step_opts(args)
     # The timed solves replay each chunk of kkt_every iterations as one CUDA
     # graph (the product path); a separate solve issues every launch from the
     # host between CUDA events for the per-kernel breakdown and the roofline.
     solver = mv.Solver(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
-                       layout=args.layout, two_pass=1 if args.two_pass else 0)
+                       layout=args.layout, two_pass=1 if args.two_pass else 0, **sopts)
     del R_dev
 
     def barrier():
@@ -606,7 +629,7 @@ def main():
     x_head = solver.x.cpu().numpy()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
     tinfos = launch_profile(L, mu, Rt, model.T, dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps,
-                            layout=args.layout, two_pass=1 if args.two_pass else 0)
+                            layout=args.layout, two_pass=1 if args.two_pass else 0, **sopts)
 
     # roofline of the dominant kernel (per-launch CUDA events around every loop launch)
     roof = roofline(tinfos, model, args.dtype, args.layout)
@@ -620,17 +643,19 @@ def main():
         x_host = torch.empty(model.n, dtype=torch.float64).pin_memory()
         cws = torch.empty(mv.lib().mv_center_host_workspace_size(model.n, model.T), dtype=torch.uint8, device=dev)
         e_solver = None
-        e_times = []
+        e_times, e_up = [], []
         for i in range(2 + 3):
             torch.cuda.synchronize()
             a0 = torch.cuda.Event(enable_timing=True)
+            am = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
             # upload of R overlapped with its centering, chunk by chunk (mv_center_factor_host)
             L2, rs2, mu2, _ = mv.center_factor_host(R_pin, args.dtype, layout=args.layout, device=dev, ws=cws)
+            am.record(stream)
             if e_solver is None:
                 e_solver = mv.Solver(L2, mu2, Rt, model.T, dtype=args.dtype, row_scale=rs2, power_start=r0,
-                                     eps=args.eps, layout=args.layout)
+                                     eps=args.eps, layout=args.layout, **sopts)
             else:
                 e_solver.problem.L = L2.data_ptr()
                 e_solver.problem.mu = mu2.data_ptr()
@@ -642,12 +667,15 @@ def main():
             torch.cuda.synchronize()
             if i >= 2:
                 e_times.append(a0.elapsed_time(a1))
+                e_up.append(a0.elapsed_time(am))
             # release this step's factor before the next upload: the next one
             # reuses the same device block (and the solver's cached graph)
             e_solver._keep = None
             del L2, mu2, rs2
         e2e = {"value": float(np.mean(e_times)) / 1e3, "unit": "s",
-               "h2d_bytes_per_step": int(R32.nbytes), "d2h_bytes_per_step": int(model.n * 8)}
+               "h2d_bytes_per_step": int(R32.nbytes), "d2h_bytes_per_step": int(model.n * 8),
+               "upload_center_s": float(np.mean(e_up)) / 1e3,
+               "upload_GBps": R32.nbytes / (float(np.mean(e_up)) / 1e3) / 1e9}
         del R_pin, cws
 
     # Low-precision storage + FP32 refinement on the same workload and GPU.
@@ -678,7 +706,7 @@ def main():
         for name, LL, rr, lay, two in ((f"{args.dtype}_{args.layout}_two_pass", L, rs, args.layout, 1),
                                        (f"{args.dtype}_{other}_fused", Lo, rso, other, 0),
                                        (f"{args.dtype}_{other}_two_pass", Lo, rso, other, 1)):
-            kw = dict(dtype=args.dtype, row_scale=rr, power_start=r0, eps=args.eps, two_pass=two, layout=lay)
+            kw = dict(dtype=args.dtype, row_scale=rr, power_start=r0, eps=args.eps, two_pass=two, layout=lay, **sopts)
             sv = mv.Solver(LL, mu, Rt, model.T, **kw)
             t, vinfos = timed_solves(sv)
             pinfos = launch_profile(LL, mu, Rt, model.T, **kw)
@@ -687,26 +715,27 @@ def main():
                               "fused": vinfos[-1]["fused"], "roofline": roofline(pinfos, model, args.dtype, lay)}
             del sv
         del Lo, rso
-        # A shorter power method (Sec. 3.1 remark: a handful of iterations is
-        # usually enough for the step estimate): the headline solve with 10.
-        kw = dict(dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps, layout=args.layout,
-                  two_pass=1 if args.two_pass else 0, power_iters=10)
-        sv = mv.Solver(L, mu, Rt, model.T, **kw)
-        t, vinfos = timed_solves(sv)
-        vi = vinfos[-1]
-        variants[f"{args.dtype}_{args.layout}_power10"] = {
-            "value": t, "unit": "s", "power_iters": 10, "iterations": vi["iterations"], "kkt": vi["kkt"],
-            "converged": vi["converged"], "objective": vi["objective"],
-            "lambda_hat_over_power50": vi["lambda_hat"] / infos[-1]["lambda_hat"],
-            "rel_obj_vs_power50": (vi["objective"] - infos[-1]["objective"]) / infos[-1]["objective"]}
-        del sv
+        # The headline solve with the power method of the Sec. 3.1 remark for
+        # lambda_hat: 50 iterations, and 10 (the remark's "a handful").
+        for it in (50, 10):
+            kw = dict(dtype=args.dtype, row_scale=rs, power_start=r0, eps=args.eps, layout=args.layout,
+                      two_pass=1 if args.two_pass else 0, power_iters=it)
+            sv = mv.Solver(L, mu, Rt, model.T, **kw)
+            t, vinfos = timed_solves(sv)
+            vi = vinfos[-1]
+            variants[f"{args.dtype}_{args.layout}_power{it}"] = {
+                "value": t, "unit": "s", "power_iters": it, "iterations": vi["iterations"], "kkt": vi["kkt"],
+                "converged": vi["converged"], "objective": vi["objective"], "lambda_hat": vi["lambda_hat"],
+                "lambda_hat_over_headline": vi["lambda_hat"] / infos[-1]["lambda_hat"],
+                "rel_obj_vs_headline": (vi["objective"] - infos[-1]["objective"]) / infos[-1]["objective"]}
+            del sv
     if not args.no_variants and args.dtype == "f32":
         R_dev = torch.from_numpy(R32).to(dev)
         for vdt in ("bf16", "fp8"):
             # low-precision copy n x T (its faster layout), FP32 refinement on the headline L
             Llo, rslo, _, _ = mv.center_factor(R_dev, vdt, layout="nt")
             rsv = mv.RefinedSolver(Llo, L, mu, Rt, model.T, dtype=vdt, row_scale=rslo, power_start=r0,
-                                   eps_lo=1e-5, eps=args.eps, layout="nt", layout_hi=args.layout)
+                                   eps_lo=1e-5, eps=args.eps, layout="nt", layout_hi=args.layout, **sopts)
             for _ in range(args.warmup):
                 rsv.solve()
             torch.cuda.synchronize()
@@ -918,7 +947,7 @@ def main():
             muh = muf.cpu().numpy()
             targets = np.linspace(np.percentile(muh, 10), np.percentile(muh, 90), 64)
             fsv = mv.FrontierSolver(Lfb, muf, targets, fm.T, eps=args.eps, dtype=fdt, row_scale=rsf, L_f32=Lhi,
-                                    eps_lo=1e-5)
+                                    eps_lo=1e-5, **sopts)
             fsv.solve()
             torch.cuda.synchronize()
             reps = 3 if tag.startswith("full_shape") else 5
@@ -931,18 +960,19 @@ def main():
             entry = {"targets": 64, "value": f0.elapsed_time(f1) / reps / 1e3, "unit": "s",
                      "max_iterations": max(i["iterations"] for i in finfo),
                      "all_converged": all(i["converged"] == 1 for i in finfo), "dtype": fdt,
-                     "kkt_eps": args.eps, "model": "fp32 (refined)" if refine else fdt}
+                     "kkt_eps": args.eps, "model": "fp32 (refined)" if refine else fdt, "step_estimate": slabel}
             if refine:
                 entry["max_refine_iterations"] = max(i["refine_iterations"] for i in finfo)
                 entry["note"] = ("BF16 frontier to KKT 1e-5, then every target refined on the FP32 factor "
                                  "(BF16 hi + lo pair) to the KKT tolerance on the FP32 model")
-            # algorithmic bytes: 50 fused power passes over L + two GEMMs (L^T and L) per loop iteration
+            # algorithmic bytes: the step estimate's fused passes over L + two GEMMs (L^T and L) per loop iteration
             fe = 2 if fdt == "bf16" else 1
+            kp = sopts["power_iters"]
             if refine:       # phase 2 reads both BF16 parts in each GEMM
                 it2 = entry["max_refine_iterations"]
-                fbytes = fm.n * fm.T * 2 * (50 + 2 * (entry["max_iterations"] - it2 + 1) + 4 * (it2 + 1))
+                fbytes = fm.n * fm.T * 2 * (kp + 2 * (entry["max_iterations"] - it2 + 1) + 4 * (it2 + 1))
             else:
-                fbytes = fm.n * fm.T * fe * (50 + 2 * (entry["max_iterations"] + 1))
+                fbytes = fm.n * fm.T * fe * (kp + 2 * (entry["max_iterations"] + 1))
             peak, peak_kind = peaks()
             fgbs = fbytes / entry["value"] / 1e9
             entry["roofline"] = {"bound": "hbm", "achieved": round(fgbs, 1), "peak": peak, "unit": "GB/s",
@@ -953,7 +983,7 @@ def main():
                 Lf32, _, _, _ = mv.center_factor(Rfd, "f32")
                 t0 = time.perf_counter()
                 for r in targets:
-                    mv.npga_solve(Lf32, muf, float(r), fm.T, eps=args.eps)
+                    mv.npga_solve(Lf32, muf, float(r), fm.T, eps=args.eps, **sopts)
                 torch.cuda.synchronize()
                 entry["fp32_sequential_64_solves_s"] = time.perf_counter() - t0
                 del Lf32
@@ -961,7 +991,7 @@ def main():
                 # the same 64 targets as independent FP32 solves of the headline factor, one after another
                 # (launches issued from the host: each target would otherwise capture its own graphs)
                 ssv = mv.Solver(L, mu, float(targets[0]), model.T, power_start=r0, eps=args.eps, layout=args.layout,
-                                two_pass=1 if args.two_pass else 0, use_graph=0)
+                                two_pass=1 if args.two_pass else 0, use_graph=0, **sopts)
                 ssv.solve()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
@@ -1075,11 +1105,13 @@ def main():
         del L
         torch.cuda.empty_cache()
         prob = oracle_problem(model, R32)
-        cb = cpu_baseline(model, args.eps, x_gpu=x_head, f_gpu=infos[-1]["objective"], prob=prob)
+        cb = cpu_baseline(model, args.eps, x_gpu=x_head, f_gpu=infos[-1]["objective"], prob=prob,
+                          sopts={"lanczos": sopts.get("lanczos", 0), "power_iters": sopts["power_iters"]},
+                          slabel=slabel)
         if not args.no_row_oracles:
             res = {"sigma_iters": sigma_res["f32_L"]["iterations"] if sigma_res else 50,
                    "batch_elem_iters": batch_elem_iters, "small_x": small_x if small is not None else None}
-            row_cpu = row_oracles(model, R32, res, prob)
+            row_cpu = row_oracles(model, R32, res, prob, sopts)
             if str_res is not None:
                 for k in ("sketch", "countsketch", "truncate"):
                     if k in str_res:
@@ -1103,11 +1135,13 @@ def main():
                 "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
                 "config": {"workload": f"npga full model n={model.n} T={model.T} {args.dtype} L "
                                        f"({'L^T stored T x n' if args.layout == 'tn' else 'n x T'}), "
-                                       f"KKT eps={args.eps}, 50 power iterations",
+                                       f"KKT eps={args.eps}, step from {slabel}",
                            "n": model.n, "T": model.T, "kkt_eps": args.eps, "layout": args.layout,
+                           "step_estimate": slabel,
                            "l2": "inputs larger than L2 (L is %.2f GB)" % (nT * es / 1e9),
                            "parallelism": "replicas" if world > 1 else "single"},
                 "iterations": last["iterations"], "kkt": last["kkt"], "objective": last["objective"],
+                "lambda_hat": last["lambda_hat"], "alpha": last["alpha"],
                 "gpu_launches": int(sum(i["launches"] for i in infos)),
                 "roofline": roof, "cpu_baseline": cb, "e2e": e2e, "clocks": clocks,
                 "variants": variants, "sigma": sigma_res, "str": str_res, "small_200x1000": small,

@@ -233,6 +233,7 @@ int mv_npga_backward(const mv_problem *P, const mv_solve_opts *O_in, const doubl
     if (O.max_iter < 1 || O.checkpoint_every < 1 || O.power_iters < 0) return MV_ERR_INVALID_ARG;
     if (O.momentum != 0 || O.backtrack != 0)
         return record_message(MV_ERR_UNSUPPORTED, "mv_npga_backward: differentiates the fixed-step FISTA loop only");
+    if (O.lanczos != 0) return record_message(MV_ERR_UNSUPPORTED, "mv_npga_backward: power-method step only");
     if (O.proj_budget < 1 || O.dykstra_iters < 0) return MV_ERR_INVALID_ARG;
     O.kkt_every = 0;          // unrolled: no early stop inside the K iterations
     O.eps = 0.0;

@@ -474,6 +474,10 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
     if (O.momentum != 0 || O.backtrack != 0)
         return record_message(MV_ERR_UNSUPPORTED, "frontier solve: fixed step and FISTA momentum only");
+    if (O.lanczos != 0 && O.lanczos != 1) return MV_ERR_INVALID_ARG;
+    const bool lanczos = O.lanczos == 1 && !(O.alpha > 0.0);
+    if (lanczos && (O.power_iters < 1 || O.power_iters > kMaxLanczos))
+        return record_message(MV_ERR_INVALID_ARG, "Lanczos step size: power_iters must be in 1..512");
     const Plan p = make_plan(P->dtype, P->n, P->T, P->ld, 0, true);   // power method: fused pass
     const FPlan f = make_fplan(p, n_targets, P_hi != nullptr);
     MV_TRY(check_ws(d_ws, ws_bytes, f.total));
@@ -505,25 +509,38 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
     Pt.layout = MV_LAYOUT_TN;
     const Plan pt = make_plan(P->dtype, P->n, P->T, f.ldLt, 0, true, true);
 
-    // Shared step size from the power method on L (the fused pass over L^T).
+    // Shared step size from the power method (or Lanczos steps) on L, the
+    // fused pass over L^T; the Lanczos vectors use the transposed plan's x
+    // and y buffers, which the frontier leaves unused.
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, pt.o_tick_t), 0, 4 * (size_t)pt.t_blocks, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, pt.o_tick_n), 0, 4 * (size_t)pt.n_groups, s));
     const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
-    launch_setup(st, P->mu, P->power_start, rs, y32, p.n, s);
+    launch_setup(st, P->mu, P->power_start, rs, y32, p.n, s, lanczos ? at<float>(d_ws, pt.o_x) : nullptr,
+                 lanczos ? at<double>(d_ws, pt.o_lan) : nullptr);
     if (pt.use_llt) {
         MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, pt.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
         MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, pt.o_err), 0, 16, s));
     }
-    for (int it = 0; it < O.power_iters; ++it) {
+    const int est_iters = (O.alpha > 0.0) ? 0 : O.power_iters;
+    float *qv[2] = {at<float>(d_ws, pt.o_x), at<float>(d_ws, pt.o_y)};
+    for (int it = 0; it < est_iters; ++it) {
         if (pt.use_llt)
             MV_TRY(launch_llt(pt, &Pt, y32, d_ws, nullptr, at<double>(d_ws, pt.o_gy), at<float>(d_ws, pt.o_g32), s));
         else
             gemv_pair(pt, &Pt, y32, d_ws, nullptr, at<double>(d_ws, pt.o_gy), s, at<float>(d_ws, pt.o_g32));
-        launch_power_norm(at<float>(d_ws, pt.o_g32), rs, y32, p.n, s);
+        if (lanczos)
+            launch_lanczos_step(at<float>(d_ws, pt.o_g32), qv[it & 1], qv[(it + 1) & 1], at<double>(d_ws, pt.o_lan),
+                                rs, y32, p.n, it, s);
+        else
+            launch_power_norm(at<float>(d_ws, pt.o_g32), rs, y32, p.n, s);
     }
-    if (O.power_iters > 0) gemv_t_only(pt, &Pt, y32, d_ws, s);
-    launch_step_size(st, at<float>(d_ws, pt.o_z), (O.alpha > 0.0 || O.power_iters == 0) ? 0 : p.T, P->gamma,
-                     O.power_safety, O.alpha, s);
+    if (lanczos) {
+        launch_lanczos_step_size(st, at<double>(d_ws, pt.o_lan), P->gamma, O.power_safety, O.alpha, s);
+    } else {
+        if (est_iters > 0) gemv_t_only(pt, &Pt, y32, d_ws, s);
+        launch_step_size(st, at<float>(d_ws, pt.o_z), est_iters == 0 ? 0 : p.T, P->gamma, O.power_safety, O.alpha,
+                         s);
+    }
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_y), 0, 2 * (size_t)f.BN * f.ldY, s));
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, f.o_gtick), 0, 4 * (size_t)((p.n + kBM - 1) / kBM) + 64, s));
     MV_CUDA_TRY(cudaGetLastError());
@@ -570,7 +587,7 @@ static int frontier_solve(const mv_problem *P, const mv_problem *P_hi, const dou
     MV_CUDA_TRY(cudaMemcpyToSymbolAsync(g_gemm_err, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
 
     const int chunk = O.kkt_every > 0 ? O.kkt_every : 8;
-    int launches = 3 + 3 * O.power_iters + 1 + 2;
+    int launches = 3 + 3 * est_iters + (lanczos ? 0 : 1) + 2;
     std::vector<FState> hf(B);
     // One phase: chunks of kkt_every iterations (a cached-per-call graph) until every target is done.
     auto run_phase = [&](const CUtensorMap *mp, bool two) -> int {

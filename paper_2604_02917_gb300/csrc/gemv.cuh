@@ -33,9 +33,9 @@ constexpr int kGemvUnroll = 8;
 constexpr int kMaxRowsPerSplit = 2048;
 
 // One block of z = L^T y: column strip `strip`, row split `split` of `nsplits`.
-// The result goes to z (FP32, may be NULL) and, when z64 is non-NULL, also
-// to z64 in FP64 multiplied by cscale[col] (if non-NULL): the transposed
-// layout uses this kernel for g = L z with the FP8 asset scales.
+// The result, multiplied by cscale[col] if cscale is non-NULL, goes to z
+// (FP32, may be NULL) and, when z64 is non-NULL, also to z64 in FP64: the
+// transposed layout uses this kernel for g = L z with the FP8 asset scales.
 template <int DT>
 __device__ __forceinline__ void gemv_t_body(const void *__restrict__ L, int64_t ld, int n, int T,
                                             const float *__restrict__ y32, float *__restrict__ zpart, int64_t zstride,
@@ -150,9 +150,12 @@ __device__ __forceinline__ void gemv_t_body(const void *__restrict__ L, int64_t 
             }
         }
         if (z != nullptr) {
+            float o[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) o[e] = cscale != nullptr ? sacc[e] * cscale[col + e] : sacc[e];
 #pragma unroll
             for (int e = 0; e < VEC; e += 4)
-                *reinterpret_cast<float4 *>(z + col + e) = make_float4(sacc[e], sacc[e + 1], sacc[e + 2], sacc[e + 3]);
+                *reinterpret_cast<float4 *>(z + col + e) = make_float4(o[e], o[e + 1], o[e + 2], o[e + 3]);
         }
         if (z64 != nullptr) {
 #pragma unroll
@@ -165,7 +168,7 @@ __device__ __forceinline__ void gemv_t_body(const void *__restrict__ L, int64_t 
             if (col + e < T) {
                 float sm = 0.f;
                 for (int sp = 0; sp < splits; ++sp) sm += __ldcg(zpart + (int64_t)sp * zstride + col + e);
-                if (z != nullptr) z[col + e] = sm;
+                if (z != nullptr) z[col + e] = cscale != nullptr ? sm * cscale[col + e] : sm;
                 if (z64 != nullptr) z64[col + e] = (double)sm * (cscale != nullptr ? (double)cscale[col + e] : 1.0);
             }
         }

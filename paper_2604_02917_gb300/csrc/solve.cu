@@ -10,6 +10,8 @@
 // replayed; every kernel returns at once when the device-side `done` flag is
 // set, so a chunk that overruns convergence costs only empty launches.  The
 // host reads the flag once per chunk.
+#include <cfloat>
+
 #include "solve_internal.cuh"
 
 namespace mv {
@@ -102,6 +104,7 @@ Plan make_plan(int dt, int64_t n, int64_t T, int64_t ld, int grouped_rows, bool 
     p.o_dyk = take(8 * 4 * (size_t)nl * p.cl);
     p.o_gd = take(8 * (size_t)n);
     p.o_xp = take(8 * (size_t)n);
+    p.o_lan = take(8 * kLanczosDoubles);
     p.o_err = take(16);
     p.total = off;
     return p;
@@ -145,6 +148,7 @@ static Plan make_plan_sigma(int64_t n, int64_t ld) {
     p.o_dyk = take(8 * 4 * (size_t)nl * p.cl);
     p.o_gd = take(8 * (size_t)n);
     p.o_xp = take(8 * (size_t)n);
+    p.o_lan = take(8 * kLanczosDoubles);
     p.o_err = take(16);
     p.total = off;
     return p;
@@ -157,8 +161,11 @@ __device__ __forceinline__ double *dyk_slice(double *base, int rank, int nl) {
     return base ? base + (size_t)rank * 4 * nl : nullptr;
 }
 
+// With q0 != nullptr the FP64 start vector of the Lanczos recurrence is also
+// written there and its record `lan` cleared.
 __device__ __forceinline__ void setup_body(SolveState *st, const double *__restrict__ mu, const double *__restrict__ r0,
-             const float *__restrict__ row_scale, float *__restrict__ y32, int n) {
+             const float *__restrict__ row_scale, float *__restrict__ y32, int n,
+             float *__restrict__ q0 = nullptr, double *__restrict__ lan = nullptr) {
     __shared__ double red[(kStepThreads / kWarp + 1) * 5];
     double mn = INFINITY, mx = -INFINITY, ss = 0.0;
     for (int i = threadIdx.x; i < n; i += kStepThreads) {
@@ -178,7 +185,9 @@ __device__ __forceinline__ void setup_body(SolveState *st, const double *__restr
         const double r = r0 ? r0[i] : 1.0;
         const double s = row_scale ? (double)row_scale[i] : 1.0;
         y32[i] = (float)(r * inv * s);
+        if (q0) q0[i] = (float)(r * inv);
     }
+    if (lan && threadIdx.x < 2) lan[threadIdx.x] = 0.0;
     if (threadIdx.x == 0) {
         SolveState z{};
         z.mu_min = mn;
@@ -191,8 +200,9 @@ __device__ __forceinline__ void setup_body(SolveState *st, const double *__restr
 
 __global__ void __launch_bounds__(kStepThreads)
 setup_kernel(SolveState *st, const double *__restrict__ mu, const double *__restrict__ r0,
-             const float *__restrict__ row_scale, float *__restrict__ y32, int n) {
-    setup_body(st, mu, r0, row_scale, y32, n);
+             const float *__restrict__ row_scale, float *__restrict__ y32, int n, float *__restrict__ q0 = nullptr,
+             double *__restrict__ lan = nullptr) {
+    setup_body(st, mu, r0, row_scale, y32, n, q0, lan);
 }
 
 // u <- g / ||g|| (power method) from the FP32 copy of g, written as the FP32
@@ -274,6 +284,136 @@ step_size_sigma_kernel(SolveState *st, const float *__restrict__ u, const double
     for (int i = threadIdx.x; i < n; i += kStepThreads) v[0] = fma((double)u[i], su[i], v[0]);
     block_sum<1, kStepThreads>(v, red);
     if (threadIdx.x == 0) set_step(st, v[0], gamma, safety, alpha_override);
+}
+
+// One step of the Lanczos recurrence on A = L L^T, for the largest singular
+// value of L_eff that the fixed step of Sec. 3.1 may use.  w = A q_j arrives
+// as the FP32 copy of the product of y32 = q_j:
+//   alpha_j = q_j^T w,  r = w - alpha_j q_j - beta_j q_{j-1},
+//   beta_{j+1} = ||r||,  q_{j+1} = r / beta_{j+1},
+// q_{j+1} overwriting q_{j-1} and going out as the next product input.
+// Vectors and per-thread sums in FP32 (FP64 is scarce on this part and the
+// products carry FP32 rounding anyway), alpha and beta combined and kept in
+// FP64.  The recurrence stops (and later steps return at once) when
+// beta_{j+1} is negligible against alpha_j + beta_j: K_{j+1} is then
+// invariant under A and the Ritz values are eigenvalues.  No
+// reorthogonalisation: a lost orthogonality only repeats converged Ritz
+// values.
+__global__ void __launch_bounds__(kStepThreads)
+lanczos_kernel(const float *__restrict__ w, const float *__restrict__ qj, float *__restrict__ qprev,
+               double *__restrict__ lan, const float *__restrict__ row_scale, float *__restrict__ y32, int n, int j) {
+    umma::launch_dependents();     // the next fused pass may start streaming L
+    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    if (lan[1] != 0.0) return;     // the same value in every thread: written below, after the barriers
+    const double b = j > 0 ? lan[2 + kMaxLanczos + j - 1] : 0.0;
+    const float bf = (float)b;
+    float pa = 0.f;
+    for (int i = threadIdx.x; i < n; i += kStepThreads) pa = fmaf(qj[i], w[i], pa);
+    double v[1] = {(double)pa};
+    block_sum<1, kStepThreads>(v, red);
+    const double a = v[0];
+    const float af = (float)a;
+    float ps = 0.f;
+    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+        float r = fmaf(-af, qj[i], w[i]);
+        if (j > 0) r = fmaf(-bf, qprev[i], r);
+        ps = fmaf(r, r, ps);
+    }
+    double ss[1] = {(double)ps};
+    block_sum<1, kStepThreads>(ss, red);
+    const double bn = sqrt(ss[0]);
+    const bool stop = !(bn > 1e-12 * (fabs(a) + b));
+    if (!stop) {
+        const float inv = (float)(1.0 / bn);
+        for (int i = threadIdx.x; i < n; i += kStepThreads) {
+            float r = fmaf(-af, qj[i], w[i]);
+            if (j > 0) r = fmaf(-bf, qprev[i], r);
+            const float q = r * inv;
+            qprev[i] = q;
+            y32[i] = row_scale ? q * row_scale[i] : q;
+        }
+    }
+    if (threadIdx.x == 0) {
+        lan[2 + j] = a;
+        lan[2 + kMaxLanczos + j] = bn;
+        lan[0] = (double)(j + 1);
+        if (stop) lan[1] = 1.0;
+    }
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal matrix with
+// diagonal a[0..k) and squared off-diagonal b2[i] (coupling i and i + 1):
+// the negative pivots of the LDL^T factorisation of T - x I (Sturm count).
+__device__ __forceinline__ int sturm_count(const double *a, const double *b2, int k, double x, double pivmin) {
+    int c = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+        d = (a[i] - x) - (i > 0 ? b2[i - 1] / d : 0.0);
+        if (fabs(d) < pivmin) d = -pivmin;
+        c += d < 0.0;
+    }
+    return c;
+}
+
+// lambda_hat = the largest eigenvalue of the Lanczos tridiagonal matrix
+// (diagonal alpha_0..alpha_{k-1}, off-diagonal beta_1..beta_{k-1}), in FP64
+// by multisection on one warp: each round the bracket [lo, hi] (Gershgorin
+// bounds at the start) is cut at 32 points, one Sturm count per lane, and
+// narrowed to the piece where the count reaches k.  One warp because FP64
+// throughput per SM is low here: wider multisection costs more than its
+// fewer rounds save.
+constexpr int kLanczosEigRounds = 12;      // 33^12 > 2^60: past FP64 resolution
+
+__global__ void __launch_bounds__(kWarp)
+lanczos_step_size_kernel(SolveState *st, const double *__restrict__ lan, double gamma, double safety,
+                         double alpha_override) {
+    __shared__ double a[kMaxLanczos], b2[kMaxLanczos];
+    const int lane = threadIdx.x;
+    const int k = min(kMaxLanczos, (int)lan[0]);
+    bool bad = false;
+    double bmax2 = 0.0;
+    for (int i = lane; i < k; i += kWarp) {
+        a[i] = lan[2 + i];
+        const double b = lan[2 + kMaxLanczos + i];
+        b2[i] = b * b;
+        bad = bad || !isfinite(a[i]) || !isfinite(b);
+        if (i + 1 < k) bmax2 = fmax(bmax2, b2[i]);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    bmax2 = warp_max(bmax2);
+    __syncwarp();
+    double lo = INFINITY, hi = -INFINITY;
+    for (int i = lane; i < k; i += kWarp) {
+        const double r = (i > 0 ? sqrt(b2[i - 1]) : 0.0) + (i + 1 < k ? sqrt(b2[i]) : 0.0);
+        lo = fmin(lo, a[i] - r);
+        hi = fmax(hi, a[i] + r);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    const double pivmin = DBL_MIN * fmax(1.0, bmax2);
+    double lam = 0.0;
+    if (bad) {
+        lam = NAN;
+    } else if (k == 1) {
+        lam = a[0];                // the 1 x 1 matrix: its entry, exactly
+    } else if (k > 1) {
+        const double pad = 1e-9 * (fabs(lo) + fabs(hi)) + 1e-300;
+        lo -= pad;
+        hi += pad;
+        for (int round = 0; round < kLanczosEigRounds && hi - lo > 0.0; ++round) {
+            const double h = (hi - lo) / (double)(kWarp + 1);
+            const double x = lo + h * (double)(lane + 1);
+            // the lanes whose point has at most k - 1 eigenvalues below it form a prefix
+            const unsigned below = __ballot_sync(0xffffffffu, sturm_count(a, b2, k, x, pivmin) <= k - 1);
+            const int t = below ? 31 - __clz((int)below) : -1;
+            const double nlo = t >= 0 ? lo + h * (double)(t + 1) : lo;
+            const double nhi = t + 1 < kWarp ? lo + h * (double)(t + 2) : hi;
+            lo = nlo;
+            hi = nhi;
+        }
+        lam = 0.5 * (lo + hi);
+    }
+    if (lane == 0) set_step(st, lam, gamma, safety, alpha_override);
 }
 
 // x^0: Pi_F(1/n 1), or the caller's x^0 when warm-starting; y^0 = x^0.
@@ -1136,18 +1276,55 @@ static int launch_power(const Plan &p, const mv_problem *P, int power_iters, voi
     return cudaGetLastError() == cudaSuccess ? MV_OK : MV_ERR_CUDA;
 }
 
+// The Lanczos alternative: `steps` products L L^T q_j, each followed by one
+// step of the recurrence (FP32 q_j alternates between the x and y buffers,
+// free until x^0 is set); capturable.  Adds the launches to *count.
+static int launch_lanczos(const Plan &p, const mv_problem *P, int steps, void *ws, cudaStream_t s, int *count) {
+    const float *rs = P->dtype == MV_FP8_E4M3 ? P->row_scale : nullptr;
+    float *y32 = at<float>(ws, p.o_y32);
+    double *wd = at<double>(ws, p.o_gy);
+    float *w = at<float>(ws, p.o_g32);
+    float *q[2] = {at<float>(ws, p.o_x), at<float>(ws, p.o_y)};
+    for (int j = 0; j < steps; ++j) {
+        if (p.sig) {
+            MV_TRY(launch_symv(p, P, y32, ws, nullptr, wd, w, s));
+            *count += 2;
+        } else if (p.use_llt) {
+            MV_TRY(launch_llt(p, P, y32, ws, nullptr, wd, w, s, nullptr, kFusedPdl));
+            *count += 2;
+        } else {
+            gemv_pair(p, P, y32, ws, nullptr, wd, s, w);
+            *count += 3;
+        }
+        lanczos_kernel<<<1, kStepThreads, 0, s>>>(w, q[j & 1], q[(j + 1) & 1], at<double>(ws, p.o_lan), rs, y32,
+                                                  p.n, j);
+    }
+    return cudaGetLastError() == cudaSuccess ? MV_OK : MV_ERR_CUDA;
+}
+
 static int get_power_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws,
                            cudaGraphExec_t *out) {
-    GraphKey key = graph_key(p, P, O, -1 - O->power_iters, nullptr);
+    const bool lz = O->lanczos == 1;
+    GraphKey key = graph_key(p, P, O, (lz ? -(1 << 20) : -1) - O->power_iters, nullptr);
     key.ws = ws;
     int dummy = 0;
-    return cached_graph(key, [&](cudaStream_t cs) { return launch_power(p, P, O->power_iters, ws, cs, &dummy); },
-                        out);
+    return cached_graph(key, [&](cudaStream_t cs) {
+        return lz ? launch_lanczos(p, P, O->power_iters, ws, cs, &dummy)
+                  : launch_power(p, P, O->power_iters, ws, cs, &dummy);
+    }, out);
 }
 
 void launch_setup(SolveState *st, const double *mu, const double *r0, const float *rs, float *y32, int n,
-                  cudaStream_t s) {
-    setup_kernel<<<1, kStepThreads, 0, s>>>(st, mu, r0, rs, y32, n);
+                  cudaStream_t s, float *q0, double *lan) {
+    setup_kernel<<<1, kStepThreads, 0, s>>>(st, mu, r0, rs, y32, n, q0, lan);
+}
+void launch_lanczos_step(const float *w, const float *qj, float *qprev, double *lan, const float *rs, float *y32,
+                         int n, int j, cudaStream_t s) {
+    lanczos_kernel<<<1, kStepThreads, 0, s>>>(w, qj, qprev, lan, rs, y32, n, j);
+}
+void launch_lanczos_step_size(SolveState *st, const double *lan, double gamma, double safety, double alpha,
+                              cudaStream_t s) {
+    lanczos_step_size_kernel<<<1, kWarp, 0, s>>>(st, lan, gamma, safety, alpha);
 }
 void launch_power_norm(const float *g32, const float *rs, float *y32, int n, cudaStream_t s) {
     power_norm_kernel<<<1, kStepThreads, 0, s>>>(g32, rs, y32, n);
@@ -1189,6 +1366,8 @@ void mv_solve_opts_default(mv_solve_opts *o) {
     o->bt_alpha0 = 0.0;
     o->proj_budget = 100;
     o->dykstra_iters = 2000;
+    o->lanczos = 0;
+    o->reserved_opts = 0;
 }
 
 size_t mv_npga_workspace_size(const mv_problem *P) {
@@ -1241,6 +1420,10 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     if (O.momentum == 1 && !(O.m_f > 0.0) && !(P->gamma > 0.0))
         return record_message(MV_ERR_INVALID_ARG, "constant momentum needs m_f > 0 or gamma > 0");
     if (O.backtrack == 1 && !(O.bt_rho > 0.0 && O.bt_rho < 1.0)) return MV_ERR_INVALID_ARG;
+    if (O.lanczos != 0 && O.lanczos != 1) return MV_ERR_INVALID_ARG;
+    const bool lanczos = O.lanczos == 1 && !(O.alpha > 0.0);
+    if (lanczos && (O.power_iters < 1 || O.power_iters > kMaxLanczos))
+        return record_message(MV_ERR_INVALID_ARG, "Lanczos step size: power_iters must be in 1..512");
     const Plan p = plan_for(P, O.two_pass == 0);
     MV_TRY(check_ws(d_ws, ws_bytes, p.total));
     MV_TRY(set_kernel_attrs());
@@ -1256,9 +1439,12 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
     MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_err), 0, 16, s));
     if (p.use_llt) MV_CUDA_TRY(cudaMemsetAsync(llt_scratch(at<char>(d_ws, p.o_llt), p.n).tickets, 0, llt_ticket_bytes(), s));
     if (p.sig) MV_CUDA_TRY(cudaMemsetAsync(at<char>(d_ws, p.o_stick), 0, 4 * (size_t)p.snb, s));
-    setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n);
-    // Power method for ||L_eff||_2^2 (skipped when the step is given): one
-    // cached graph of all its launches, or host-issued when graphs are off.
+    setup_kernel<<<1, kStepThreads, 0, s>>>(st, P->mu, P->power_start, rs, y32, p.n,
+                                            lanczos ? at<float>(d_ws, p.o_x) : nullptr,
+                                            lanczos ? at<double>(d_ws, p.o_lan) : nullptr);
+    // Power method (or Lanczos) for ||L_eff||_2^2, skipped when the step is
+    // given: one cached graph of all its launches, or host-issued when graphs
+    // are off.
     int launches = 4;
     if (!(O.alpha > 0.0)) {
         if (O.use_graph && !O.timing) {
@@ -1267,12 +1453,16 @@ int mv_npga_solve(const mv_problem *P, const mv_solve_opts *O_in, double *d_x_in
             MV_CUDA_TRY(cudaGraphLaunch(pexec, s));
             int cnt = 0;
             for (int it = 0; it < O.power_iters; ++it) cnt += (p.sig || p.use_llt) ? 2 : 3;
-            launches += cnt + 1;
+            launches += cnt + (lanczos ? 0 : 1);
+        } else if (lanczos) {
+            MV_TRY(launch_lanczos(p, P, O.power_iters, d_ws, s, &launches));
         } else {
             MV_TRY(launch_power(p, P, O.power_iters, d_ws, s, &launches));
         }
     }
-    if (p.sig)
+    if (lanczos)
+        lanczos_step_size_kernel<<<1, kWarp, 0, s>>>(st, at<double>(d_ws, p.o_lan), P->gamma, O.power_safety, O.alpha);
+    else if (p.sig)
         step_size_sigma_kernel<<<1, kStepThreads, 0, s>>>(st, y32, at<double>(d_ws, p.o_gy), (O.alpha > 0.0) ? 0 : p.n,
                                                           P->gamma, O.power_safety, O.alpha);
     else
@@ -1922,6 +2112,7 @@ int mv_npga_solve_batch(const mv_problem *probs, int64_t count, const mv_solve_o
     if (O_in) O = *O_in; else mv_solve_opts_default(&O);
     if (O.max_iter < 0 || O.kkt_every < 0 || O.power_iters < 0 || !(O.eps >= 0.0)) return MV_ERR_INVALID_ARG;
     if (O.power_iters == 0 && !(O.alpha > 0.0)) return MV_ERR_INVALID_ARG;
+    if (O.lanczos != 0) return record_message(MV_ERR_UNSUPPORTED, "batched solve: power-method step only");
     if (O.momentum != 0 || O.backtrack != 0)
         return record_message(MV_ERR_UNSUPPORTED, "batch solve: fixed step and FISTA momentum only");
     BatchLayout Lo;

@@ -22,6 +22,10 @@ namespace mv {
 
 constexpr int kStepThreads = 512;
 constexpr int kProjBudget = 100;
+constexpr int kMaxLanczos = 512;           // Lanczos steps of the step-size estimate
+// Lanczos record (FP64): [0] steps taken, [1] 1 once stopped, alpha_j at
+// [2 + j], beta_{j+1} at [2 + kMaxLanczos + j].
+constexpr size_t kLanczosDoubles = 2 + 2 * (size_t)kMaxLanczos;
 
 struct SolveState {
     int k, done, converged, status;
@@ -54,6 +58,7 @@ struct Plan {
     // workspace offsets (bytes)
     size_t o_state, o_x, o_y, o_gx, o_gy, o_g32, o_y32, o_z, o_zpart, o_gpart, o_tick_t, o_tick_n;
     size_t o_llt, o_err, o_zd;
+    size_t o_lan;                          // Lanczos record (kLanczosDoubles)
     int64_t zstride;                       // row pitch (floats) of the gemv_t partials
     size_t total;
 };
@@ -120,9 +125,14 @@ GraphKey graph_key(const Plan &p, const mv_problem *P, const mv_solve_opts *O, i
 int cached_graph(const GraphKey &key, const std::function<int(cudaStream_t)> &enqueue, cudaGraphExec_t *out);
 int get_chunk_graph(const Plan &p, const mv_problem *P, const mv_solve_opts *O, void *ws, int chunk,
                     const cudaEvent_t *ev, cudaGraphExec_t *out);
-// Kernel launches of solve.cu's set-up, power-method and step-size kernels.
+// Kernel launches of solve.cu's set-up, power-method, Lanczos and step-size
+// kernels (q0 / lan: the Lanczos start vector and record, or nullptr).
 void launch_setup(SolveState *st, const double *mu, const double *r0, const float *rs, float *y32, int n,
-                  cudaStream_t s);
+                  cudaStream_t s, float *q0 = nullptr, double *lan = nullptr);
+void launch_lanczos_step(const float *w, const float *qj, float *qprev, double *lan, const float *rs, float *y32,
+                         int n, int j, cudaStream_t s);
+void launch_lanczos_step_size(SolveState *st, const double *lan, double gamma, double safety, double alpha,
+                              cudaStream_t s);
 void launch_power_norm(const float *g32, const float *rs, float *y32, int n, cudaStream_t s);
 void launch_step_size(SolveState *st, const float *z, int T, double gamma, double safety, double alpha,
                       cudaStream_t s);

@@ -73,7 +73,8 @@ class SolveOpts(C.Structure):
                 ("alpha", C.c_double), ("use_graph", C.c_int32), ("timing", C.c_int32),
                 ("checkpoint_every", C.c_int32), ("two_pass", C.c_int32), ("momentum", C.c_int32),
                 ("backtrack", C.c_int32), ("m_f", C.c_double), ("bt_rho", C.c_double), ("bt_alpha0", C.c_double),
-                ("proj_budget", C.c_int32), ("dykstra_iters", C.c_int32)]
+                ("proj_budget", C.c_int32), ("dykstra_iters", C.c_int32), ("lanczos", C.c_int32),
+                ("reserved_opts", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

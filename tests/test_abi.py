@@ -57,7 +57,8 @@ def _c_layout(tmp_path):
                        "power_start", "layout", "reserved"],
         "mv_solve_opts": ["max_iter", "kkt_every", "power_iters", "warm_start", "eps", "power_safety",
                           "alpha", "use_graph", "timing", "checkpoint_every", "two_pass", "momentum",
-                          "backtrack", "m_f", "bt_rho", "bt_alpha0", "proj_budget", "dykstra_iters"],
+                          "backtrack", "m_f", "bt_rho", "bt_alpha0", "proj_budget", "dykstra_iters",
+                          "lanczos", "reserved_opts"],
         "mv_solve_info": ["iterations", "status", "converged", "proj_failures", "kkt", "objective",
                           "alpha", "lambda_hat", "nu", "launches", "timed_pairs", "t_gemv_t_ms",
                           "t_gemv_n_ms", "t_step_ms", "proj_steps", "refine_iterations", "fused",
@@ -89,7 +90,7 @@ def test_struct_layouts_match_header(mvmod, tmp_path):
     assert o.max_iter == 10000 and o.kkt_every == 5 and o.power_iters == 50
     assert o.eps == 1e-6 and o.power_safety == 1e-3 and o.use_graph == 1
     assert o.momentum == 0 and o.backtrack == 0 and o.bt_rho == 0.5 and o.proj_budget == 100
-    assert o.dykstra_iters == 2000
+    assert o.dykstra_iters == 2000 and o.lanczos == 0 and o.reserved_opts == 0
 
 
 def test_host_side_argument_errors(mvmod):
