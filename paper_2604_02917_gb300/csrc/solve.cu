@@ -298,34 +298,40 @@ step_size_sigma_kernel(SolveState *st, const float *__restrict__ u, const double
 // beta_{j+1} is negligible against alpha_j + beta_j: K_{j+1} is then
 // invariant under A and the Ritz values are eigenvalues.  No
 // reorthogonalisation: a lost orthogonality only repeats converged Ritz
-// values.
-__global__ void __launch_bounds__(kStepThreads)
+// values.  One block of kLanczosThreads; the loops are unrolled so that
+// each thread keeps several loads in flight (the vectors sit in L2).
+constexpr int kLanczosThreads = 1024;
+
+__global__ void __launch_bounds__(kLanczosThreads)
 lanczos_kernel(const float *__restrict__ w, const float *__restrict__ qj, float *__restrict__ qprev,
                double *__restrict__ lan, const float *__restrict__ row_scale, float *__restrict__ y32, int n, int j) {
     umma::launch_dependents();     // the next fused pass may start streaming L
-    __shared__ double red[(kStepThreads / kWarp + 1) * 5];
+    __shared__ double red[kLanczosThreads / kWarp + 1];
     if (lan[1] != 0.0) return;     // the same value in every thread: written below, after the barriers
     const double b = j > 0 ? lan[2 + kMaxLanczos + j - 1] : 0.0;
     const float bf = (float)b;
     float pa = 0.f;
-    for (int i = threadIdx.x; i < n; i += kStepThreads) pa = fmaf(qj[i], w[i], pa);
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n; i += kLanczosThreads) pa = fmaf(qj[i], w[i], pa);
     double v[1] = {(double)pa};
-    block_sum<1, kStepThreads>(v, red);
+    block_sum<1, kLanczosThreads>(v, red);
     const double a = v[0];
     const float af = (float)a;
     float ps = 0.f;
-    for (int i = threadIdx.x; i < n; i += kStepThreads) {
+#pragma unroll 4
+    for (int i = threadIdx.x; i < n; i += kLanczosThreads) {
         float r = fmaf(-af, qj[i], w[i]);
         if (j > 0) r = fmaf(-bf, qprev[i], r);
         ps = fmaf(r, r, ps);
     }
     double ss[1] = {(double)ps};
-    block_sum<1, kStepThreads>(ss, red);
+    block_sum<1, kLanczosThreads>(ss, red);
     const double bn = sqrt(ss[0]);
     const bool stop = !(bn > 1e-12 * (fabs(a) + b));
     if (!stop) {
         const float inv = (float)(1.0 / bn);
-        for (int i = threadIdx.x; i < n; i += kStepThreads) {
+#pragma unroll 4
+        for (int i = threadIdx.x; i < n; i += kLanczosThreads) {
             float r = fmaf(-af, qj[i], w[i]);
             if (j > 0) r = fmaf(-bf, qprev[i], r);
             const float q = r * inv;
@@ -344,74 +350,75 @@ lanczos_kernel(const float *__restrict__ w, const float *__restrict__ qj, float 
 // Number of eigenvalues below x of the symmetric tridiagonal matrix with
 // diagonal a[0..k) and squared off-diagonal b2[i] (coupling i and i + 1):
 // the negative pivots of the LDL^T factorisation of T - x I (Sturm count).
-__device__ __forceinline__ int sturm_count(const double *a, const double *b2, int k, double x, double pivmin) {
+__device__ __forceinline__ int sturm_count(const float *a, const float *b2, int k, float x, float pivmin) {
     int c = 0;
-    double d = 1.0;
+    float d = 1.f;
     for (int i = 0; i < k; ++i) {
-        d = (a[i] - x) - (i > 0 ? b2[i - 1] / d : 0.0);
-        if (fabs(d) < pivmin) d = -pivmin;
-        c += d < 0.0;
+        d = (a[i] - x) - (i > 0 ? b2[i - 1] / d : 0.f);
+        if (fabsf(d) < pivmin) d = -pivmin;
+        c += d < 0.f;
     }
     return c;
 }
 
 // lambda_hat = the largest eigenvalue of the Lanczos tridiagonal matrix
-// (diagonal alpha_0..alpha_{k-1}, off-diagonal beta_1..beta_{k-1}), in FP64
-// by multisection on one warp: each round the bracket [lo, hi] (Gershgorin
-// bounds at the start) is cut at 32 points, one Sturm count per lane, and
-// narrowed to the piece where the count reaches k.  One warp because FP64
-// throughput per SM is low here: wider multisection costs more than its
-// fewer rounds save.
-constexpr int kLanczosEigRounds = 12;      // 33^12 > 2^60: past FP64 resolution
+// (diagonal alpha_0..alpha_{k-1}, off-diagonal beta_1..beta_{k-1}) by
+// multisection on one warp: the matrix is scaled by its Gershgorin bound s
+// (FP64) so that every entry lies in [-1, 1], and each round the bracket
+// [lo, hi] is cut at 32 points, one FP32 Sturm count per lane, and narrowed
+// to the piece where the count reaches k, down to FP32 resolution: the
+// estimate carries a relative error of order k * 2^-24, far inside the
+// step's safety factor.  FP32 because FP64 division is a long-latency
+// sequence on this part: the same multisection in FP64 (12 rounds) measured
+// 154 us per launch at k = 25.
+constexpr int kLanczosEigRounds = 6;       // 33^6 > 2^30: past FP32 resolution
 
 __global__ void __launch_bounds__(kWarp)
 lanczos_step_size_kernel(SolveState *st, const double *__restrict__ lan, double gamma, double safety,
                          double alpha_override) {
-    __shared__ double a[kMaxLanczos], b2[kMaxLanczos];
+    __shared__ float a[kMaxLanczos], b2[kMaxLanczos];
     const int lane = threadIdx.x;
     const int k = min(kMaxLanczos, (int)lan[0]);
     bool bad = false;
-    double bmax2 = 0.0;
-    for (int i = lane; i < k; i += kWarp) {
-        a[i] = lan[2 + i];
-        const double b = lan[2 + kMaxLanczos + i];
-        b2[i] = b * b;
-        bad = bad || !isfinite(a[i]) || !isfinite(b);
-        if (i + 1 < k) bmax2 = fmax(bmax2, b2[i]);
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    bmax2 = warp_max(bmax2);
-    __syncwarp();
     double lo = INFINITY, hi = -INFINITY;
     for (int i = lane; i < k; i += kWarp) {
-        const double r = (i > 0 ? sqrt(b2[i - 1]) : 0.0) + (i + 1 < k ? sqrt(b2[i]) : 0.0);
-        lo = fmin(lo, a[i] - r);
-        hi = fmax(hi, a[i] + r);
+        const double ai = lan[2 + i];
+        const double bl = i > 0 ? fabs(lan[2 + kMaxLanczos + i - 1]) : 0.0;
+        const double br = i + 1 < k ? fabs(lan[2 + kMaxLanczos + i]) : 0.0;
+        bad = bad || !isfinite(ai) || !isfinite(bl) || !isfinite(br);
+        lo = fmin(lo, ai - bl - br);
+        hi = fmax(hi, ai + bl + br);
     }
+    bad = __any_sync(0xffffffffu, bad);
     lo = warp_min(lo);
     hi = warp_max(hi);
-    const double pivmin = DBL_MIN * fmax(1.0, bmax2);
+    const double sc = fmax(fabs(lo), fabs(hi));
     double lam = 0.0;
-    if (bad) {
+    if (bad || !isfinite(sc)) {
         lam = NAN;
     } else if (k == 1) {
-        lam = a[0];                // the 1 x 1 matrix: its entry, exactly
-    } else if (k > 1) {
-        const double pad = 1e-9 * (fabs(lo) + fabs(hi)) + 1e-300;
-        lo -= pad;
-        hi += pad;
-        for (int round = 0; round < kLanczosEigRounds && hi - lo > 0.0; ++round) {
-            const double h = (hi - lo) / (double)(kWarp + 1);
-            const double x = lo + h * (double)(lane + 1);
-            // the lanes whose point has at most k - 1 eigenvalues below it form a prefix
-            const unsigned below = __ballot_sync(0xffffffffu, sturm_count(a, b2, k, x, pivmin) <= k - 1);
-            const int t = below ? 31 - __clz((int)below) : -1;
-            const double nlo = t >= 0 ? lo + h * (double)(t + 1) : lo;
-            const double nhi = t + 1 < kWarp ? lo + h * (double)(t + 2) : hi;
-            lo = nlo;
-            hi = nhi;
+        lam = lan[2];              // the 1 x 1 matrix: its entry, exactly
+    } else if (k > 1 && sc > 0.0) {
+        const double inv = 1.0 / sc;
+        for (int i = lane; i < k; i += kWarp) {
+            a[i] = (float)(lan[2 + i] * inv);
+            const double bs = lan[2 + kMaxLanczos + i] * inv;
+            b2[i] = (float)(bs * bs);
         }
-        lam = 0.5 * (lo + hi);
+        __syncwarp();
+        float flo = (float)(lo * inv) - 0x1p-20f, fhi = (float)(hi * inv) + 0x1p-20f;
+        for (int round = 0; round < kLanczosEigRounds && fhi - flo > 0.f; ++round) {
+            const float h = (fhi - flo) / (float)(kWarp + 1);
+            const float x = flo + h * (float)(lane + 1);
+            // the lanes whose point has at most k - 1 eigenvalues below it form a prefix
+            const unsigned below = __ballot_sync(0xffffffffu, sturm_count(a, b2, k, x, FLT_MIN) <= k - 1);
+            const int t = below ? 31 - __clz((int)below) : -1;
+            const float nlo = t >= 0 ? flo + h * (float)(t + 1) : flo;
+            const float nhi = t + 1 < kWarp ? flo + h * (float)(t + 2) : fhi;
+            flo = nlo;
+            fhi = nhi;
+        }
+        lam = sc * (0.5 * ((double)flo + (double)fhi));
     }
     if (lane == 0) set_step(st, lam, gamma, safety, alpha_override);
 }
@@ -1296,7 +1303,7 @@ static int launch_lanczos(const Plan &p, const mv_problem *P, int steps, void *w
             gemv_pair(p, P, y32, ws, nullptr, wd, s, w);
             *count += 3;
         }
-        lanczos_kernel<<<1, kStepThreads, 0, s>>>(w, q[j & 1], q[(j + 1) & 1], at<double>(ws, p.o_lan), rs, y32,
+        lanczos_kernel<<<1, kLanczosThreads, 0, s>>>(w, q[j & 1], q[(j + 1) & 1], at<double>(ws, p.o_lan), rs, y32,
                                                   p.n, j);
     }
     return cudaGetLastError() == cudaSuccess ? MV_OK : MV_ERR_CUDA;
@@ -1320,7 +1327,7 @@ void launch_setup(SolveState *st, const double *mu, const double *r0, const floa
 }
 void launch_lanczos_step(const float *w, const float *qj, float *qprev, double *lan, const float *rs, float *y32,
                          int n, int j, cudaStream_t s) {
-    lanczos_kernel<<<1, kStepThreads, 0, s>>>(w, qj, qprev, lan, rs, y32, n, j);
+    lanczos_kernel<<<1, kLanczosThreads, 0, s>>>(w, qj, qprev, lan, rs, y32, n, j);
 }
 void launch_lanczos_step_size(SolveState *st, const double *lan, double gamma, double safety, double alpha,
                               cudaStream_t s) {
