@@ -841,7 +841,7 @@ def main():
         # kappa(hat Sigma) ~ 4e4: a 1e-6 KKT residual leaves the objective ~2e-3 above the STR optimum
         # (1e-8: 3e-5), so the STR model is solved to 1e-9 (x within 1e-4 of the oracle's, objective 1e-5)
         str_eps = min(args.eps, 1e-9)
-        ssv = mv.Solver(L_eff, mu, Rt, args.str_k, gamma=gamma, power_start=r0, eps=str_eps)
+        ssv = mv.Solver(L_eff, mu, Rt, args.str_k, gamma=gamma, power_start=r0, eps=str_eps, **sopts)
         for _ in range(args.warmup):
             ssv.solve()
         torch.cuda.synchronize()
@@ -852,7 +852,7 @@ def main():
         torch.cuda.synchronize()
         s_ms = e[0].elapsed_time(e[1]) / args.steps
         # the same solve to the headline's KKT tolerance
-        ssv6 = mv.Solver(L_eff, mu, Rt, args.str_k, gamma=gamma, power_start=r0, eps=args.eps)
+        ssv6 = mv.Solver(L_eff, mu, Rt, args.str_k, gamma=gamma, power_start=r0, eps=args.eps, **sopts)
         for _ in range(args.warmup):
             ssv6.solve()
         torch.cuda.synchronize()
@@ -878,7 +878,7 @@ def main():
                                 "sigma_1": float(sigma[0]),
                                 "sigma_k": float(sigma[-1])},
                    "solve": {"value": s_ms / 1e3, "unit": "s", "iterations": si["iterations"], "kkt": si["kkt"],
-                             "kkt_eps": str_eps},
+                             "kkt_eps": str_eps, "step_estimate": slabel},
                    "solve_headline_eps": {"value": s6_ms / 1e3, "unit": "s", "iterations": si6["iterations"],
                                           "kkt": si6["kkt"], "kkt_eps": args.eps},
                    "full_model_gap": (f_str_full - f_full) / f_full,
