@@ -201,7 +201,8 @@ typedef struct {
     double gamma;             /* ridge (0 for the full and sketched models)              */
     const double *mu;         /* d: n FP64 expected returns                              */
     double R_target;          /* target return                                           */
-    const double *power_start;/* d: n FP64 start of the power method; NULL = all ones    */
+    const double *power_start;/* d: n FP64 start of the power method (or Lanczos); NULL =
+                                 all ones                                                */
     int32_t layout;           /* mv_layout of L (MV_LAYOUT_TN: T x n, ld >= n)           */
     int32_t reserved;         /* 0                                                       */
 } mv_problem;
@@ -209,11 +210,11 @@ typedef struct {
 typedef struct {
     int32_t max_iter;         /* iteration budget (default 10000)                        */
     int32_t kkt_every;        /* KKT check period (default 5, Sec. 5.2)                 */
-    int32_t power_iters;      /* power-method steps (default 50)                         */
+    int32_t power_iters;      /* power-method (or Lanczos) steps (default 50)            */
     int32_t warm_start;       /* 1: x_inout holds x^0 in F; 0: x^0 = Pi_F(1/n)           */
     double eps;               /* KKT tolerance (default 1e-6)                            */
     double power_safety;      /* lambda_hat is multiplied by (1 + this); default 1e-3    */
-    double alpha;             /* > 0: fixed step override; <= 0: from the power method   */
+    double alpha;             /* > 0: fixed step override; <= 0: from lambda_hat          */
     int32_t use_graph;        /* 1 (default): replay iterations as a CUDA graph          */
     int32_t timing;           /* 1: time every loop launch with CUDA events (kernels are
                                  then issued from the host instead of a graph)           */
@@ -323,10 +324,10 @@ int mv_sigma_form(const mv_problem *P, float *d_Sigma, int64_t ldS, void *d_ws, 
  *     result is then refined on the FP32 copy of the same factor.
  *
  *  Phase 1: mv_npga_solve(P_lo) to a KKT residual <= eps_lo, with its own
- *  power method.  Phase 2: mv_npga_solve(P_hi) warm-started from that point,
+ *  step estimate (power method, or Lanczos with opts->lanczos).  Phase 2: mv_npga_solve(P_hi) warm-started from that point,
  *  with the fixed step alpha_lo / (1 + 1e-2) (the spectral norms of the two
  *  copies differ by far less than 1%, so the step stays admissible) and no
- *  second power method, until the KKT residual of P_hi is <= opts->eps.
+ *  second estimate, until the KKT residual of P_hi is <= opts->eps.
  *  P_lo and P_hi must describe the same problem (n, T, gamma, mu, target,
  *  mode); P_hi->dtype must be MV_F32.  The two copies may use different
  *  layouts (each its fastest).  Workspace: the larger of the two
@@ -346,7 +347,7 @@ int mv_npga_solve_refined(const mv_problem *P_lo, const mv_problem *P_hi, const 
  *  Z = L^T [y_1..y_B], G = L Z (tcgen05, BF16 operands, FP32 accumulation)
  *  with the vector operands carried as a BF16 hi + lo pair, so accuracy is
  *  that of the BF16 model; L^T is formed once in the workspace.  One shared
- *  power method sets alpha; each target has its own FISTA state, KKT test
+ *  step estimate (power method, or Lanczos with opts->lanczos) sets alpha; each target has its own FISTA state, KKT test
  *  and stopping point; a chunk of kkt_every iterations is replayed as one
  *  CUDA graph.  P->R_target is ignored.
  *  d_R_targets [in]  n_targets FP64 targets (device).
