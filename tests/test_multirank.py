@@ -95,3 +95,21 @@ def test_clock_samples_window():
     assert every["samples"] == 4 and every["window"].startswith("whole")
     assert "hw_slowdown" in every["reasons"]
     assert bench.parse_clock_samples(["garbage"], None, None) is None
+
+
+@pytest.mark.parametrize("est", ["lanczos", "power"])
+def test_reference_arm_step_estimate(est, capsys):
+    """The reference arm (the FP64 oracle) runs the workload with the step
+    estimate the GPU arm uses and labels it; rank 0 prints one JSON line."""
+    import json
+    import bench
+    args = type("B", (), {"gpus": 1, "steps": 1, "warmup": 0, "eps": 1e-6, "config": "small", "shape": None,
+                          "step_estimate": est, "step_iters": None})
+    sopts, label = bench.step_opts(args)
+    assert sopts["power_iters"] == (25 if est == "lanczos" else 50)
+    assert sopts.get("lanczos", 0) == (1 if est == "lanczos" else 0)
+    bench.reference_arm(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["config"]["step_estimate"] == label
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["kkt"] <= 1e-6
+    assert label in line["cpu_baseline"]["sample"]
